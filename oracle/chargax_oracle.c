@@ -1,0 +1,555 @@
+/*
+ * chargax_oracle.c -- CPU oracle for the EV charging-station step.
+ *
+ * TEST INFRASTRUCTURE.  This file exists to check the CUDA library: only the
+ * tests, the smoke check and the benchmark's CPU-baseline leg may build, load
+ * or call it.  It shares no code, header, table or constant generator with the
+ * CUDA path.  It is deliberately plain: one thread, FP64 state and arithmetic,
+ * loops over envs and ports in the order the paper gives (Appendix A.2 "Apply
+ * Actions" -> "Charge Stationed Cars" -> "Departure of Cars" -> "Arrival of new
+ * Cars", then the reward of Appendix A.3).
+ *
+ * Two places are NOT FP64, on purpose:
+ *  - the Poisson count of arriving cars is an integer decided by floating
+ *    point; it is taken in FP32 (the paper's JAX default precision, which is
+ *    also the kernel's) with a fixed operation order, so both sides agree
+ *    bit for bit (see orc_poisson);
+ *  - inputs arrive as float32 arrays (prices, arrival rates, limits) and are
+ *    widened to double.
+ *
+ * Randomness: Philox4x32-10 written from its published definition (Salmon,
+ * Moraes, Dror, Shaw: "Parallel Random Numbers: As Easy as 1, 2, 3", SC 2011),
+ * keyed per env; counters (stream, step, slot, purpose).
+ *
+ * Parity status of each function is recorded next to it ("pinned by ...").
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_KMAX 127          /* largest Poisson count the sampler returns     */
+#define ORC_PURPOSE_ARRIVAL 0u
+#define ORC_PURPOSE_CAR 1u
+#define ORC_PURPOSE_ACTION 2u
+#define ORC_PURPOSE_DAY 3u
+
+typedef struct orc_params {
+    int32_t ep_len;        /* steps per episode (24 h / dt)                     */
+    int32_t n_levels;      /* discrete action levels k = 0..n_levels-1          */
+    double dt_h;           /* step length in hours                              */
+    double tau;            /* bulk/absorption breakpoint of the taper           */
+    double p_sell;         /* price charged to customers, EUR/kWh               */
+    double c_fixed;        /* fixed running cost per step, EUR                  */
+    double alpha_sat, alpha_decl, alpha_con;
+    double soc_target;     /* SoC a user wants at departure                     */
+    double p_max_kw[2];    /* per charger type: 0 = AC, 1 = DC                  */
+    double eta_port[2];
+    double cap_kwh[2];     /* U(lo, hi) battery capacity                        */
+    double soc0[2];        /* U(lo, hi) arrival SoC                             */
+    int32_t stay_steps[2]; /* inclusive integer range of the stay, in steps     */
+    double rbar_kw[2][2];  /* [type][lo, hi] car maximum rate per charger type  */
+} orc_params;
+
+typedef struct orc {
+    orc_params p;
+    int32_t E, n_days, n_classes;
+    int64_t P, G;
+    int64_t *port_off, *group_off;
+    int32_t *n_ports, *n_groups, *group_size, *arrival_class;
+    uint8_t *port_type;
+    int32_t *port_group;                   /* global group index of each port   */
+    double *group_limit, *group_eta, *grid_limit, *grid_eta;
+    float *price, *lam;                    /* [D][T], [C][T] as given           */
+    /* per-port state (car-state + port state, Appendix A.1) */
+    double *soc, *erem, *cap, *rbar, *pw;
+    int32_t *trem;                         /* remaining steps, 0 = empty port   */
+    /* per-env state */
+    int32_t *tod, *day;
+    uint32_t *gstep, *key0, *key1;
+    double *ep_ret, *last_ret;
+    uint32_t *n_episodes;
+    /* per-env running statistics */
+    double *st_arrived, *st_rejected, *st_missing, *st_charged;
+    /* per-env record of the last step (for invariant tests) */
+    int32_t *inf_M, *inf_admitted, *inf_departed;
+    double *inf_csat, *inf_ccon, *inf_enet, *inf_egrid, *inf_price, *inf_req_sum;
+    double *scratch_p;                     /* per-port power within one step    */
+    uint8_t *scratch_leave;                /* port's stay ended in this step    */
+} orc;
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon et al. 2011, Sec. 3.3 and Table 2): ten rounds of  */
+/* two 32x32->64 multiplies on counter words 0 and 2, XOR of the high halves */
+/* into the other words and the key, with the key bumped by the Weyl        */
+/* constants between rounds.  Pinned by the published known-answer values   */
+/* (tests/golden/philox4x32_10_kat.txt).                                    */
+/* ------------------------------------------------------------------------ */
+void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) { k0 += W0; k1 += W1; }
+        uint64_t a = (uint64_t)M0 * (uint64_t)x0;
+        uint64_t b = (uint64_t)M1 * (uint64_t)x2;
+        uint32_t a_hi = (uint32_t)(a >> 32), a_lo = (uint32_t)a;
+        uint32_t b_hi = (uint32_t)(b >> 32), b_lo = (uint32_t)b;
+        uint32_t y0 = b_hi ^ x1 ^ k0;
+        uint32_t y1 = b_lo;
+        uint32_t y2 = a_hi ^ x3 ^ k1;
+        uint32_t y3 = a_lo;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+static void draw(const orc *o, int32_t e, uint32_t c1, uint32_t c2, uint32_t purpose, uint32_t out[4])
+{
+    uint32_t ctr[4] = {(uint32_t)e, c1, c2, purpose};
+    uint32_t key[2] = {o->key0[e], o->key1[e]};
+    orc_philox(ctr, key, out);
+}
+
+/* integer in [0, n): high word of the 64-bit product (exact) */
+static uint32_t to_range(uint32_t w, uint32_t n) { return (uint32_t)(((uint64_t)w * n) >> 32); }
+
+/* uniform in [0, 1) from the top 24 bits (exactly representable in FP32) */
+static double to_unit(uint32_t w) { return (double)(w >> 8) * (1.0 / 16777216.0); }
+
+/* ------------------------------------------------------------------------ */
+/* Arrival count M(t) ~ Poisson(lambda(t)) (Appendix "Practical             */
+/* Considerations": bundled scenarios give mean cars per step, the count is */
+/* drawn from a Poisson).  Inverse transform: the smallest k whose CDF      */
+/* exceeds u.  Because k is an integer chosen by floating point, the        */
+/* decision is taken in FP32 with this exact sequence of correctly rounded  */
+/* operations (exp in double, rounded once).  Pinned against the exact      */
+/* Poisson CDF (tests/test_oracle_pins.py).                                 */
+/* ------------------------------------------------------------------------ */
+int32_t orc_poisson(float lam, uint32_t w)
+{
+    float u = (float)(w >> 8) * 5.9604644775390625e-8f;    /* 2^-24 */
+    float pk = (float)exp(-(double)lam);
+    float cdf = pk;
+    int32_t k = 0;
+    while (u >= cdf && k < ORC_KMAX) {
+        k += 1;
+        float num = pk * lam;
+        pk = num / (float)k;
+        cdf = cdf + pk;
+    }
+    return k;
+}
+
+/* Charging-rate taper r_hat(SoC) (Appendix A.1, Car Profiles): bulk stage at
+ * r_bar up to tau, then linear to zero at SoC = 1.  Pinned by the closed-form
+ * single-car trajectory test. */
+double orc_taper(double soc, double rbar, double tau)
+{
+    if (soc <= tau) return rbar;
+    return (1.0 - soc) * rbar / (1.0 - tau);
+}
+
+static void clear_port(orc *o, int64_t i)
+{
+    o->soc[i] = 0.0; o->erem[i] = 0.0; o->cap[i] = 0.0; o->rbar[i] = 0.0; o->trem[i] = 0;
+}
+
+/* Episode start (Appendix "Practical Considerations", exploring starts): an
+ * empty station at step-of-day 0 and a random day of the price bank. */
+static void start_episode(orc *o, int32_t e, uint32_t c1, uint32_t c2)
+{
+    for (int64_t i = o->port_off[e]; i < o->port_off[e + 1]; ++i) { clear_port(o, i); o->pw[i] = 0.0; }
+    o->tod[e] = 0;
+    uint32_t w[4];
+    draw(o, e, c1, c2, ORC_PURPOSE_DAY, w);
+    o->day[e] = (int32_t)to_range(w[0], (uint32_t)o->n_days);
+}
+
+void orc_reset(orc *o, const int32_t *env_ids, int32_t n, uint64_t seed)
+{
+    int32_t count = env_ids ? n : o->E;
+    for (int32_t j = 0; j < count; ++j) {
+        int32_t e = env_ids ? env_ids[j] : j;
+        o->key0[e] = (uint32_t)seed;
+        o->key1[e] = (uint32_t)(seed >> 32);
+        o->gstep[e] = 0;
+        o->ep_ret[e] = 0.0;
+        start_episode(o, e, 0u, 1u);
+    }
+}
+
+static void *xcalloc(size_t n, size_t sz) { return calloc(n ? n : 1, sz); }
+
+orc *orc_create(const orc_params *prm, int32_t E,
+                const int32_t *n_ports, const uint8_t *port_type,
+                const int32_t *n_groups, const int32_t *group_size,
+                const float *group_limit, const float *group_eta,
+                const float *grid_limit, const float *grid_eta,
+                const int32_t *arrival_class,
+                int32_t n_days, const float *price,
+                int32_t n_classes, const float *lam, uint64_t seed)
+{
+    orc *o = (orc *)xcalloc(1, sizeof(orc));
+    o->p = *prm;
+    o->E = E; o->n_days = n_days; o->n_classes = n_classes;
+    o->port_off = (int64_t *)xcalloc((size_t)E + 1, sizeof(int64_t));
+    o->group_off = (int64_t *)xcalloc((size_t)E + 1, sizeof(int64_t));
+    for (int32_t e = 0; e < E; ++e) {
+        o->port_off[e + 1] = o->port_off[e] + n_ports[e];
+        o->group_off[e + 1] = o->group_off[e] + n_groups[e];
+    }
+    o->P = o->port_off[E]; o->G = o->group_off[E];
+    int64_t P = o->P, G = o->G;
+    o->n_ports = (int32_t *)xcalloc((size_t)E, sizeof(int32_t));
+    o->n_groups = (int32_t *)xcalloc((size_t)E, sizeof(int32_t));
+    o->arrival_class = (int32_t *)xcalloc((size_t)E, sizeof(int32_t));
+    o->grid_limit = (double *)xcalloc((size_t)E, sizeof(double));
+    o->grid_eta = (double *)xcalloc((size_t)E, sizeof(double));
+    o->port_type = (uint8_t *)xcalloc((size_t)P, 1);
+    o->port_group = (int32_t *)xcalloc((size_t)P, sizeof(int32_t));
+    o->group_size = (int32_t *)xcalloc((size_t)G, sizeof(int32_t));
+    o->group_limit = (double *)xcalloc((size_t)G, sizeof(double));
+    o->group_eta = (double *)xcalloc((size_t)G, sizeof(double));
+    memcpy(o->n_ports, n_ports, sizeof(int32_t) * (size_t)E);
+    memcpy(o->n_groups, n_groups, sizeof(int32_t) * (size_t)E);
+    memcpy(o->arrival_class, arrival_class, sizeof(int32_t) * (size_t)E);
+    memcpy(o->port_type, port_type, (size_t)P);
+    memcpy(o->group_size, group_size, sizeof(int32_t) * (size_t)G);
+    for (int32_t e = 0; e < E; ++e) {
+        o->grid_limit[e] = grid_limit[e];
+        o->grid_eta[e] = grid_eta ? grid_eta[e] : 1.0;
+        int64_t port = o->port_off[e];
+        for (int64_t g = o->group_off[e]; g < o->group_off[e + 1]; ++g)
+            for (int32_t k = 0; k < group_size[g]; ++k) o->port_group[port++] = (int32_t)g;
+    }
+    for (int64_t g = 0; g < G; ++g) {
+        o->group_limit[g] = group_limit[g];
+        o->group_eta[g] = group_eta ? group_eta[g] : 1.0;
+    }
+    size_t T = (size_t)prm->ep_len;
+    o->price = (float *)xcalloc((size_t)n_days * T, sizeof(float));
+    o->lam = (float *)xcalloc((size_t)n_classes * T, sizeof(float));
+    memcpy(o->price, price, sizeof(float) * (size_t)n_days * T);
+    memcpy(o->lam, lam, sizeof(float) * (size_t)n_classes * T);
+
+    o->soc = (double *)xcalloc((size_t)P, sizeof(double));
+    o->erem = (double *)xcalloc((size_t)P, sizeof(double));
+    o->cap = (double *)xcalloc((size_t)P, sizeof(double));
+    o->rbar = (double *)xcalloc((size_t)P, sizeof(double));
+    o->pw = (double *)xcalloc((size_t)P, sizeof(double));
+    o->scratch_p = (double *)xcalloc((size_t)P, sizeof(double));
+    o->scratch_leave = (uint8_t *)xcalloc((size_t)P, 1);
+    o->trem = (int32_t *)xcalloc((size_t)P, sizeof(int32_t));
+    o->tod = (int32_t *)xcalloc((size_t)E, sizeof(int32_t));
+    o->day = (int32_t *)xcalloc((size_t)E, sizeof(int32_t));
+    o->gstep = (uint32_t *)xcalloc((size_t)E, sizeof(uint32_t));
+    o->key0 = (uint32_t *)xcalloc((size_t)E, sizeof(uint32_t));
+    o->key1 = (uint32_t *)xcalloc((size_t)E, sizeof(uint32_t));
+    o->ep_ret = (double *)xcalloc((size_t)E, sizeof(double));
+    o->last_ret = (double *)xcalloc((size_t)E, sizeof(double));
+    o->n_episodes = (uint32_t *)xcalloc((size_t)E, sizeof(uint32_t));
+    o->st_arrived = (double *)xcalloc((size_t)E, sizeof(double));
+    o->st_rejected = (double *)xcalloc((size_t)E, sizeof(double));
+    o->st_missing = (double *)xcalloc((size_t)E, sizeof(double));
+    o->st_charged = (double *)xcalloc((size_t)E, sizeof(double));
+    o->inf_M = (int32_t *)xcalloc((size_t)E, sizeof(int32_t));
+    o->inf_admitted = (int32_t *)xcalloc((size_t)E, sizeof(int32_t));
+    o->inf_departed = (int32_t *)xcalloc((size_t)E, sizeof(int32_t));
+    o->inf_csat = (double *)xcalloc((size_t)E, sizeof(double));
+    o->inf_ccon = (double *)xcalloc((size_t)E, sizeof(double));
+    o->inf_enet = (double *)xcalloc((size_t)E, sizeof(double));
+    o->inf_egrid = (double *)xcalloc((size_t)E, sizeof(double));
+    o->inf_price = (double *)xcalloc((size_t)E, sizeof(double));
+    o->inf_req_sum = (double *)xcalloc((size_t)E, sizeof(double));
+    orc_reset(o, NULL, 0, seed);
+    return o;
+}
+
+void orc_destroy(orc *o)
+{
+    if (!o) return;
+    void *ptrs[] = {o->port_off, o->group_off, o->n_ports, o->n_groups, o->arrival_class, o->grid_limit,
+                    o->grid_eta, o->port_type, o->port_group, o->group_size, o->group_limit, o->group_eta,
+                    o->price, o->lam, o->soc, o->erem, o->cap, o->rbar, o->pw, o->scratch_p, o->scratch_leave, o->trem, o->tod,
+                    o->day, o->gstep, o->key0, o->key1, o->ep_ret, o->last_ret, o->n_episodes,
+                    o->st_arrived, o->st_rejected, o->st_missing, o->st_charged, o->inf_M, o->inf_admitted,
+                    o->inf_departed, o->inf_csat, o->inf_ccon, o->inf_enet, o->inf_egrid, o->inf_price,
+                    o->inf_req_sum};
+    for (size_t k = 0; k < sizeof(ptrs) / sizeof(ptrs[0]); ++k) free(ptrs[k]);
+    free(o);
+}
+
+/* Action level of local port q of env e at global step g when no action
+ * array is given: uniform over 0..n_levels-1 from Philox word (g mod 4) of
+ * counter (e, g/4, q, ACTION). */
+int32_t orc_random_action(const orc *o, int32_t e, uint32_t g, int32_t q)
+{
+    uint32_t w[4];
+    draw(o, e, g >> 2, (uint32_t)q, ORC_PURPOSE_ACTION, w);
+    return (int32_t)to_range(w[g & 3u], (uint32_t)o->p.n_levels);
+}
+
+/* ------------------------------------------------------------------------ */
+/* One transition of every env, Appendix A.2 then A.3.                      */
+/* actions: int8 level per port in batch port order with stride `lda`, or   */
+/* NULL for Philox-drawn uniform levels.  reward[E] and done[E] are outputs.*/
+/* ------------------------------------------------------------------------ */
+void orc_step(orc *o, const int8_t *actions, int64_t lda, double *reward, uint8_t *done)
+{
+    const orc_params *p = &o->p;
+    const double dt = p->dt_h;
+    for (int32_t e = 0; e < o->E; ++e) {
+        const int64_t p0 = o->port_off[e], p1 = o->port_off[e + 1];
+        const uint32_t g = o->gstep[e];
+        const int32_t t = o->tod[e];
+
+        /* (i) Apply Actions: requested level clipped by the port capacity and
+         * by the car's current maximum rate r_hat(SoC); the two extra caps
+         * keep SoC <= 1 and the remaining demand >= 0 (SoC in [0,1] and
+         * Delta E_remain >= 0 are the state domains of the "State summary"). */
+        double req_sum = 0.0;
+        for (int64_t i = p0; i < p1; ++i) {
+            double P = 0.0;
+            if (o->trem[i] > 0) {
+                int32_t k = actions ? (int32_t)actions[i * lda] : orc_random_action(o, e, g, (int32_t)(i - p0));
+                int ty = o->port_type[i];
+                double pmax = p->p_max_kw[ty];
+                double preq = (double)k / (double)(p->n_levels - 1) * pmax;
+                double rhat = orc_taper(o->soc[i], o->rbar[i], p->tau);
+                double soc_cap = (1.0 - o->soc[i]) * o->cap[i] / dt;
+                double dem_cap = o->erem[i] / dt;
+                P = preq;
+                if (rhat < P) P = rhat;
+                if (pmax < P) P = pmax;
+                if (soc_cap < P) P = soc_cap;
+                if (dem_cap < P) P = dem_cap;
+                if (P < 0.0) P = 0.0;
+            }
+            o->scratch_p[i] = P;
+            req_sum += P;
+        }
+
+        /* Architecture constraint, Eq. (ArchConst): for every subtree H,
+         * (1/eta_H) * sum of its leaves' power <= I_H.  Violations are
+         * resolved by proportional rescaling of the leaves, bottom-up: the
+         * group nodes first, then the root (grid connection).  The
+         * constraint-violation penalty (Appendix A.3) is measured on the
+         * requested (pre-rescale) power. */
+        double c_con = 0.0;
+        for (int64_t gi = o->group_off[e]; gi < o->group_off[e + 1]; ++gi) {
+            double s = 0.0;
+            for (int64_t i = p0; i < p1; ++i)
+                if (o->port_group[i] == gi) s += o->scratch_p[i];
+            double over = s / o->group_eta[gi] - o->group_limit[gi];
+            if (over > c_con) c_con = over;
+            if (over > 0.0) {
+                double scale = o->group_eta[gi] * o->group_limit[gi] / s;
+                for (int64_t i = p0; i < p1; ++i)
+                    if (o->port_group[i] == gi) o->scratch_p[i] *= scale;
+            }
+        }
+        {
+            double root_over = req_sum / o->grid_eta[e] - o->grid_limit[e];
+            if (root_over > c_con) c_con = root_over;
+            double s = 0.0;
+            for (int64_t i = p0; i < p1; ++i) s += o->scratch_p[i];
+            if (s / o->grid_eta[e] > o->grid_limit[e]) {
+                double scale = o->grid_eta[e] * o->grid_limit[e] / s;
+                for (int64_t i = p0; i < p1; ++i) o->scratch_p[i] *= scale;
+            }
+        }
+
+        /* (ii) Charge Stationed Cars at constant power over dt; energy bought
+         * from the grid includes the port efficiency (Appendix A.3). */
+        double e_net = 0.0, e_grid = 0.0;
+        for (int64_t i = p0; i < p1; ++i) {
+            double P = o->scratch_p[i];
+            o->pw[i] = P;
+            if (o->trem[i] > 0) {
+                double dE = P * dt;
+                double s = o->soc[i] + dE / o->cap[i];
+                o->soc[i] = s > 1.0 ? 1.0 : s;
+                double r = o->erem[i] - dE;
+                o->erem[i] = r < 0.0 ? 0.0 : r;
+                e_net += dE;
+                e_grid += dE / p->eta_port[o->port_type[i]];
+            }
+        }
+
+        /* time moves on: every stationed car has one step less to stay */
+        for (int64_t i = p0; i < p1; ++i) {
+            o->scratch_leave[i] = 0;
+            if (o->trem[i] > 0) {
+                o->trem[i] -= 1;
+                o->scratch_leave[i] = (o->trem[i] == 0);
+            }
+        }
+
+        /* (iii) Departure of Cars: time-sensitive users (u = 0) leave when no
+         * time remains; the satisfaction penalty c_Sat,0 adds their missing
+         * energy. */
+        double c_sat = 0.0;
+        int32_t departed = 0;
+        for (int64_t i = p0; i < p1; ++i) {
+            if (o->scratch_leave[i]) {
+                c_sat += o->erem[i] > 0.0 ? o->erem[i] : 0.0;
+                clear_port(o, i);
+                departed += 1;
+            }
+        }
+
+        /* (iv) Arrival of new Cars: M ~ Poisson(lambda(t)), clipped by the
+         * free ports (first come first served); the rest are rejected.  Car j
+         * parks at the j-th free port in port order and draws its car and
+         * user profile. */
+        uint32_t w[4];
+        draw(o, e, g, 0u, ORC_PURPOSE_ARRIVAL, w);
+        float lam = o->lam[(size_t)o->arrival_class[e] * (size_t)p->ep_len + (size_t)t];
+        int32_t M = orc_poisson(lam, w[0]);
+        int32_t n_free = 0;
+        for (int64_t i = p0; i < p1; ++i) n_free += (o->trem[i] == 0);
+        int32_t m = M < n_free ? M : n_free;
+        int32_t c_decl = M - m;
+        int32_t j = 0;
+        for (int64_t i = p0; i < p1 && j < m; ++i) {
+            if (o->trem[i] != 0) continue;
+            uint32_t c[4];
+            draw(o, e, g, (uint32_t)j, ORC_PURPOSE_CAR, c);
+            int ty = o->port_type[i];
+            double C = p->cap_kwh[0] + (p->cap_kwh[1] - p->cap_kwh[0]) * to_unit(c[0]);
+            double soc0 = p->soc0[0] + (p->soc0[1] - p->soc0[0]) * to_unit(c[1]);
+            uint32_t span = (uint32_t)(p->stay_steps[1] - p->stay_steps[0] + 1);
+            int32_t stay = p->stay_steps[0] + (int32_t)to_range(c[2], span);
+            double rb = p->rbar_kw[ty][0] + (p->rbar_kw[ty][1] - p->rbar_kw[ty][0]) * to_unit(c[3]);
+            double want = p->soc_target - soc0;
+            o->cap[i] = C;
+            o->soc[i] = soc0;
+            o->erem[i] = (want > 0.0 ? want : 0.0) * C;
+            o->rbar[i] = rb;
+            o->trem[i] = stay;
+            j += 1;
+        }
+
+        /* Reward (Appendix A.3): profit with the two-case grid price (no
+         * discharge and no station battery here, so Delta E_grid,net is the
+         * energy bought), minus the weighted penalties. */
+        double price = o->price[(size_t)o->day[e] * (size_t)p->ep_len + (size_t)t];
+        double e_grid_net = e_grid;
+        double profit;
+        if (e_grid_net > 0.0) profit = p->p_sell * e_net - price * e_grid_net - p->c_fixed;
+        else profit = p->p_sell * e_net - price * e_grid_net - p->c_fixed;   /* p_sell,grid = p_buy */
+        double r = profit - p->alpha_sat * c_sat - p->alpha_decl * (double)c_decl - p->alpha_con * c_con;
+
+        o->inf_M[e] = M; o->inf_admitted[e] = m; o->inf_departed[e] = departed;
+        o->inf_csat[e] = c_sat; o->inf_ccon[e] = c_con; o->inf_enet[e] = e_net;
+        o->inf_egrid[e] = e_grid; o->inf_price[e] = price; o->inf_req_sum[e] = req_sum;
+        o->st_arrived[e] += m; o->st_rejected[e] += c_decl;
+        o->st_missing[e] += c_sat; o->st_charged[e] += e_net;
+
+        o->ep_ret[e] += r;
+        reward[e] = r;
+        o->tod[e] = t + 1;
+        o->gstep[e] = g + 1u;
+        done[e] = 0;
+        /* episode end: record the return and start a new episode at once */
+        if (o->tod[e] >= p->ep_len) {
+            done[e] = 1;
+            o->last_ret[e] = o->ep_ret[e];
+            o->ep_ret[e] = 0.0;
+            o->n_episodes[e] += 1;
+            start_episode(o, e, g, 0u);
+        }
+    }
+}
+
+/* Observation (the state of Appendix "State summary" plus time of day, the
+ * episode's day and a weekday flag, as the agent sees them).  Layout per env
+ * at float offset 8*e + 6*port_off[e]: 8 env features, then 6 per port. */
+void orc_observe(const orc *o, double *obs)
+{
+    const orc_params *p = &o->p;
+    const double two_pi = 6.283185307179586476925;
+    for (int32_t e = 0; e < o->E; ++e) {
+        double *ob = obs + 8 * (int64_t)e + 6 * o->port_off[e];
+        int32_t t = o->tod[e], n = o->n_ports[e], occ = 0;
+        for (int64_t i = o->port_off[e]; i < o->port_off[e + 1]; ++i) occ += o->trem[i] > 0;
+        ob[0] = sin(two_pi * t / p->ep_len);
+        ob[1] = cos(two_pi * t / p->ep_len);
+        ob[2] = o->price[(size_t)o->day[e] * (size_t)p->ep_len + (size_t)t];
+        ob[3] = p->p_sell;
+        ob[4] = (double)occ / n;
+        ob[5] = (double)o->day[e] / o->n_days;
+        ob[6] = (double)t / p->ep_len;
+        ob[7] = (o->day[e] % 7) < 5 ? 1.0 : 0.0;
+        for (int32_t q = 0; q < n; ++q) {
+            int64_t i = o->port_off[e] + q;
+            double *op = ob + 8 + 6 * q;
+            double pmax = p->p_max_kw[o->port_type[i]];
+            int on = o->trem[i] > 0;
+            op[0] = on ? 1.0 : 0.0;
+            op[1] = o->soc[i];
+            op[2] = (double)o->trem[i] / p->stay_steps[1];
+            op[3] = on ? orc_taper(o->soc[i], o->rbar[i], p->tau) / pmax : 0.0;
+            op[4] = o->pw[i] / pmax;
+            op[5] = o->erem[i] / p->cap_kwh[1];
+        }
+    }
+}
+
+/* State access in batch order: per port soc, erem, cap, rbar, p, trem; per
+ * env step-of-day, day, global step, key words, running episode return. */
+void orc_get_state(const orc *o, double *soc, double *erem, double *cap, double *rbar, double *pw,
+                   int32_t *trem, int32_t *tod, int32_t *day, uint32_t *gstep, uint32_t *key0,
+                   uint32_t *key1, double *ep_ret)
+{
+    size_t P = (size_t)o->P, E = (size_t)o->E;
+    memcpy(soc, o->soc, P * sizeof(double)); memcpy(erem, o->erem, P * sizeof(double));
+    memcpy(cap, o->cap, P * sizeof(double)); memcpy(rbar, o->rbar, P * sizeof(double));
+    memcpy(pw, o->pw, P * sizeof(double)); memcpy(trem, o->trem, P * sizeof(int32_t));
+    memcpy(tod, o->tod, E * sizeof(int32_t)); memcpy(day, o->day, E * sizeof(int32_t));
+    memcpy(gstep, o->gstep, E * sizeof(uint32_t)); memcpy(key0, o->key0, E * sizeof(uint32_t));
+    memcpy(key1, o->key1, E * sizeof(uint32_t)); memcpy(ep_ret, o->ep_ret, E * sizeof(double));
+}
+
+void orc_set_state(orc *o, const double *soc, const double *erem, const double *cap, const double *rbar,
+                   const double *pw, const int32_t *trem, const int32_t *tod, const int32_t *day,
+                   const uint32_t *gstep, const uint32_t *key0, const uint32_t *key1, const double *ep_ret)
+{
+    size_t P = (size_t)o->P, E = (size_t)o->E;
+    memcpy(o->soc, soc, P * sizeof(double)); memcpy(o->erem, erem, P * sizeof(double));
+    memcpy(o->cap, cap, P * sizeof(double)); memcpy(o->rbar, rbar, P * sizeof(double));
+    memcpy(o->pw, pw, P * sizeof(double)); memcpy(o->trem, trem, P * sizeof(int32_t));
+    memcpy(o->tod, tod, E * sizeof(int32_t)); memcpy(o->day, day, E * sizeof(int32_t));
+    memcpy(o->gstep, gstep, E * sizeof(uint32_t)); memcpy(o->key0, key0, E * sizeof(uint32_t));
+    memcpy(o->key1, key1, E * sizeof(uint32_t)); memcpy(o->ep_ret, ep_ret, E * sizeof(double));
+}
+
+/* Record of the last step per env: M, admitted, departed, c_sat, c_con,
+ * E_net, E_grid, price, and the summed pre-rescale power. */
+void orc_get_info(const orc *o, int32_t *M, int32_t *admitted, int32_t *departed, double *csat,
+                  double *ccon, double *enet, double *egrid, double *price, double *req_sum)
+{
+    size_t E = (size_t)o->E;
+    memcpy(M, o->inf_M, E * sizeof(int32_t)); memcpy(admitted, o->inf_admitted, E * sizeof(int32_t));
+    memcpy(departed, o->inf_departed, E * sizeof(int32_t));
+    memcpy(csat, o->inf_csat, E * sizeof(double)); memcpy(ccon, o->inf_ccon, E * sizeof(double));
+    memcpy(enet, o->inf_enet, E * sizeof(double)); memcpy(egrid, o->inf_egrid, E * sizeof(double));
+    memcpy(price, o->inf_price, E * sizeof(double)); memcpy(req_sum, o->inf_req_sum, E * sizeof(double));
+}
+
+/* Running statistics per env: cars admitted, cars rejected, kWh missing at
+ * departure, kWh charged, finished episodes, last episode return. */
+void orc_get_stats(const orc *o, double *arrived, double *rejected, double *missing, double *charged,
+                   uint32_t *n_episodes, double *last_ret)
+{
+    size_t E = (size_t)o->E;
+    memcpy(arrived, o->st_arrived, E * sizeof(double)); memcpy(rejected, o->st_rejected, E * sizeof(double));
+    memcpy(missing, o->st_missing, E * sizeof(double)); memcpy(charged, o->st_charged, E * sizeof(double));
+    memcpy(n_episodes, o->n_episodes, E * sizeof(uint32_t)); memcpy(last_ret, o->last_ret, E * sizeof(double));
+}
+
+/* the per-step power of each port (after rescaling) of the last step */
+void orc_get_power(const orc *o, double *pw) { memcpy(pw, o->pw, (size_t)o->P * sizeof(double)); }

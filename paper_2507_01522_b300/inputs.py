@@ -1,0 +1,280 @@
+"""Seeded synthetic workloads for the charging-station step.
+
+This module builds the *inputs* of the simulator and nothing else: station
+layouts (the architecture tree of the EV Station Layout section, restricted to
+root -> groups -> ports), the exogenous time series (buy-price bank and
+per-step mean arrival counts, the exogenous state space of Appendix A.1) and
+the environment parameters.  It contains none of the step's arithmetic: no
+clipping, charging, Poisson sampling, Philox or reward.  Both the CUDA library
+and the CPU oracle consume exactly these arrays, so the two sides never share
+method code.
+
+The paper's real datasets (price profiles, car and user distributions,
+arrival frequencies; Table "data-overview") are not available; the generators
+below stand in with fixed synthetic distributions:
+
+* arrivals: mean ``lambda(t) = (N/16) * 0.5 * (1 + sin(2 pi t / T))`` cars per
+  step, t = step of day from midnight, N = number of ports of the station;
+* prices: ``0.1 + 0.05 sin(2 pi t / T) + Normal(0, 0.01)`` EUR/kWh per step, one
+  row per synthetic day (365 days);
+* car/user profiles are *parameters* of uniform distributions (capacity,
+  arrival SoC, stay, maximum rate per charger type) that the step samples
+  itself with its counter-based generator.
+
+All arrays are numpy, C-contiguous, in the dtypes the C interfaces expect.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Dict, List, Optional
+
+import numpy as np
+
+AC, DC = 0, 1
+STEPS_PER_DAY = 288          # 24 h of 5-minute steps (Table "ppo-config")
+
+
+@dataclasses.dataclass
+class EnvParams:
+    """Scalar environment parameters (Table "ppo-config" plus the readings
+    that fill gaps in the paper; every field is plain data)."""
+    ep_len: int = STEPS_PER_DAY
+    n_levels: int = 11            # discretisation 10 -> levels 0,10%,..,100%
+    dt_h: float = 5.0 / 60.0
+    tau: float = 0.8
+    p_sell: float = 0.75
+    c_fixed: float = 0.0
+    alpha_sat: float = 0.1
+    alpha_decl: float = 0.5
+    alpha_con: float = 0.0
+    soc_target: float = 1.0
+    p_max_kw: tuple = (22.0, 150.0)      # per charger type (AC, DC)
+    eta_port: tuple = (0.95, 0.95)
+    cap_kwh: tuple = (40.0, 100.0)       # uniform range
+    soc0: tuple = (0.1, 0.5)             # uniform range
+    stay_steps: tuple = (12, 96)         # inclusive integer range (1 h .. 8 h)
+    rbar_ac_kw: tuple = (7.0, 22.0)
+    rbar_dc_kw: tuple = (50.0, 150.0)
+
+
+@dataclasses.dataclass
+class Stations:
+    """Flat (CSR) description of a batch of stations.
+
+    Ports of station e are ``port_off[e] .. port_off[e+1]-1``; its groups are
+    contiguous port ranges listed in order (``group_size`` sums to the port
+    count), each group node with a power limit (kW) and efficiency.
+    """
+    n_ports: np.ndarray          # int32 [E]
+    port_type: np.ndarray        # uint8 [P]
+    n_groups: np.ndarray         # int32 [E]
+    group_size: np.ndarray       # int32 [G]
+    group_limit_kw: np.ndarray   # float32 [G]
+    group_eta: np.ndarray        # float32 [G]
+    grid_limit_kw: np.ndarray    # float32 [E]
+    grid_eta: np.ndarray         # float32 [E]
+    arrival_class: np.ndarray    # int32 [E]
+
+    @property
+    def n_envs(self) -> int:
+        return int(self.n_ports.shape[0])
+
+    @property
+    def port_off(self) -> np.ndarray:
+        off = np.zeros(self.n_envs + 1, dtype=np.int64)
+        np.cumsum(self.n_ports, out=off[1:])
+        return off
+
+    @property
+    def group_off(self) -> np.ndarray:
+        off = np.zeros(self.n_envs + 1, dtype=np.int64)
+        np.cumsum(self.n_groups, out=off[1:])
+        return off
+
+    @property
+    def total_ports(self) -> int:
+        return int(self.n_ports.sum())
+
+    def subset(self, env_ids) -> "Stations":
+        """Stations ``env_ids`` (in that order) as a new batch."""
+        env_ids = np.asarray(env_ids, dtype=np.int64)
+        po, go = self.port_off, self.group_off
+        pt = np.concatenate([self.port_type[po[e]:po[e + 1]] for e in env_ids]) if len(env_ids) else np.zeros(0, np.uint8)
+        gsl = [slice(go[e], go[e + 1]) for e in env_ids]
+        cat = lambda a, dt: (np.concatenate([a[s] for s in gsl]) if len(env_ids) else np.zeros(0, dt))
+        return Stations(
+            n_ports=self.n_ports[env_ids].copy(), port_type=pt.astype(np.uint8),
+            n_groups=self.n_groups[env_ids].copy(), group_size=cat(self.group_size, np.int32),
+            group_limit_kw=cat(self.group_limit_kw, np.float32), group_eta=cat(self.group_eta, np.float32),
+            grid_limit_kw=self.grid_limit_kw[env_ids].copy(), grid_eta=self.grid_eta[env_ids].copy(),
+            arrival_class=self.arrival_class[env_ids].copy())
+
+
+@dataclasses.dataclass
+class Exo:
+    """Exogenous tables: buy-price bank [D][T] and mean arrivals [C][T]."""
+    price: np.ndarray            # float32 [D, T]
+    arrival_rate: np.ndarray     # float32 [C, T]
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    params: EnvParams
+    stations: Stations
+    exo: Exo
+    seed: int = 0
+
+
+# ----------------------------------------------------------------------------
+# exogenous series
+# ----------------------------------------------------------------------------
+
+def price_bank(n_days: int = 365, ep_len: int = STEPS_PER_DAY, seed: int = 0) -> np.ndarray:
+    """Synthetic day-ahead buy prices: 0.1 + 0.05 sin(2 pi t/T) + N(0, 0.01)."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0x50]))
+    t = np.arange(ep_len, dtype=np.float64)
+    base = 0.1 + 0.05 * np.sin(2.0 * math.pi * t / ep_len)
+    noise = rng.normal(0.0, 0.01, size=(n_days, ep_len))
+    return np.ascontiguousarray((base[None, :] + noise).astype(np.float32))
+
+
+def arrival_rates(port_counts, ep_len: int = STEPS_PER_DAY, base: float = 0.5) -> np.ndarray:
+    """Mean cars per step for each listed station size N:
+    (N/16) * base * (1 + sin(2 pi t / T)).  Row c belongs to ``port_counts[c]``."""
+    t = np.arange(ep_len, dtype=np.float64)
+    shape = base * (1.0 + np.sin(2.0 * math.pi * t / ep_len))
+    rows = [(float(n) / 16.0) * shape for n in port_counts]
+    return np.ascontiguousarray(np.asarray(rows, dtype=np.float64).astype(np.float32).reshape(len(rows), ep_len))
+
+
+# ----------------------------------------------------------------------------
+# station layouts
+# ----------------------------------------------------------------------------
+
+def _random_groups(rng: np.random.Generator, n: int, lo: int = 4, hi: int = 16) -> List[int]:
+    """Sequential group sizes U{lo..hi}; a remainder below ``lo`` joins the
+    previous group (a station smaller than ``lo`` is one group)."""
+    sizes: List[int] = []
+    left = n
+    while left > 0:
+        s = int(rng.integers(lo, hi + 1))
+        s = min(s, left)
+        if s < lo and sizes:
+            sizes[-1] += s
+        else:
+            sizes.append(s)
+        left -= s
+    return sizes
+
+
+def _build(per_env: List[dict], class_of_n: Dict[int, int]) -> Stations:
+    n_ports = np.array([d["n"] for d in per_env], dtype=np.int32)
+    port_type = np.concatenate([np.asarray(d["types"], dtype=np.uint8) for d in per_env])
+    n_groups = np.array([len(d["groups"]) for d in per_env], dtype=np.int32)
+    group_size = np.concatenate([np.asarray(d["groups"], dtype=np.int32) for d in per_env])
+    group_limit = np.concatenate([np.asarray(d["glim"], dtype=np.float32) for d in per_env])
+    group_eta = np.concatenate([np.asarray(d.get("geta", [1.0] * len(d["groups"])), dtype=np.float32) for d in per_env])
+    grid_limit = np.array([d["grid"] for d in per_env], dtype=np.float32)
+    grid_eta = np.array([d.get("grid_eta", 1.0) for d in per_env], dtype=np.float32)
+    arrival_class = np.array([class_of_n[d["n"]] for d in per_env], dtype=np.int32)
+    return Stations(n_ports, port_type, n_groups, group_size, group_limit, group_eta,
+                    grid_limit, grid_eta, arrival_class)
+
+
+def uniform_stations(n_envs: int, n_ports: int, groups: List[int], group_limit_kw: float,
+                     grid_limit_kw: float, port_type: int = AC) -> Stations:
+    d = dict(n=n_ports, types=[port_type] * n_ports, groups=list(groups),
+             glim=[group_limit_kw] * len(groups), grid=grid_limit_kw)
+    return _build([d] * n_envs, {n_ports: 0})
+
+
+def mixed_stations(rng: np.random.Generator, sizes: np.ndarray, p_max_kw, p_dc: float = 0.25,
+                   grid_kw_per_port: float = 9.0, group_frac: float = 0.5,
+                   class_sizes: Optional[List[int]] = None) -> Stations:
+    """Heterogeneous stations: per port DC with probability ``p_dc`` else AC;
+    sequential groups of 4..16 ports, each limited to ``group_frac`` of its
+    ports' summed maximum power; grid limit ``grid_kw_per_port`` x N."""
+    if class_sizes is None:
+        class_sizes = sorted(set(int(n) for n in sizes))
+    class_of_n = {n: i for i, n in enumerate(class_sizes)}
+    per_env = []
+    for n in sizes:
+        n = int(n)
+        types = (rng.random(n) < p_dc).astype(np.uint8)
+        groups = _random_groups(rng, n)
+        glim, o = [], 0
+        for g in groups:
+            glim.append(group_frac * float(sum(p_max_kw[int(x)] for x in types[o:o + g])))
+            o += g
+        per_env.append(dict(n=n, types=types, groups=groups, glim=glim, grid=grid_kw_per_port * n))
+    return _build(per_env, class_of_n)
+
+
+# ----------------------------------------------------------------------------
+# the five workloads
+# ----------------------------------------------------------------------------
+
+def small_uniform(n_envs: int = 16, seed: int = 0) -> Workload:
+    """16 stations x 16 AC chargers of 22 kW, one group, 150 kW grid."""
+    p = EnvParams(p_max_kw=(22.0, 150.0))
+    st = uniform_stations(n_envs, 16, [16], 150.0, 150.0)
+    exo = Exo(price_bank(seed=seed), arrival_rates([16]))
+    return Workload("uniform-16x16", p, st, exo, seed)
+
+
+def fixed_station(n_envs: int = 4096, seed: int = 0) -> Workload:
+    """4096 stations x 16 chargers in 2 groups of 8 (80 kW each), 22 kW ports,
+    150 kW grid."""
+    p = EnvParams(p_max_kw=(22.0, 150.0))
+    st = uniform_stations(n_envs, 16, [8, 8], 80.0, 150.0)
+    exo = Exo(price_bank(seed=seed), arrival_rates([16]))
+    return Workload(f"fixed-{n_envs}x16", p, st, exo, seed)
+
+
+def heterogeneous(n_envs: int = 65536, seed: int = 0, classes=(8, 16, 32, 64)) -> Workload:
+    """Mixed batch: 25 % each of 8/16/32/64-charger stations, randomly
+    interleaved; 11 kW AC / 150 kW DC ports (DC with p = 0.25); grid 9 kW per
+    charger; groups of 4..16 at half their summed port maximum."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0x53]))
+    per = n_envs // len(classes)
+    sizes = np.concatenate([np.full(per + (1 if i < n_envs % len(classes) else 0), c, np.int32)
+                            for i, c in enumerate(classes)])
+    rng.shuffle(sizes)
+    p = EnvParams(p_max_kw=(11.0, 150.0))
+    st = mixed_stations(rng, sizes, p.p_max_kw, class_sizes=list(classes))
+    exo = Exo(price_bank(seed=seed), arrival_rates(list(classes)))
+    return Workload(f"hetero-{n_envs}-8/16/32/64", p, st, exo, seed)
+
+
+def rollout_stations(n_envs: int = 16384, seed: int = 0) -> Workload:
+    """16384 stations x 32 AC chargers (22 kW) in groups of 8 at 80 kW, grid
+    9 kW x 32."""
+    p = EnvParams(p_max_kw=(22.0, 150.0))
+    st = uniform_stations(n_envs, 32, [8, 8, 8, 8], 80.0, 9.0 * 32)
+    exo = Exo(price_bank(seed=seed), arrival_rates([32]))
+    return Workload(f"rollout-{n_envs}x32", p, st, exo, seed)
+
+
+def log_uniform_sizes(rng: np.random.Generator, n_envs: int, lo: int = 8, hi: int = 128) -> np.ndarray:
+    x = np.exp(rng.uniform(math.log(lo), math.log(hi), size=n_envs))
+    return np.clip(np.rint(x), lo, hi).astype(np.int32)
+
+
+def serving_pool(n_envs: int, seed: int = 0) -> Workload:
+    """Stations for the serving loop: N = round(exp(U(ln 8, ln 128))) chargers,
+    groups and limits as in the heterogeneous batch."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0x55]))
+    sizes = log_uniform_sizes(rng, n_envs)
+    p = EnvParams(p_max_kw=(11.0, 150.0))
+    classes = list(range(8, 129))
+    st = mixed_stations(rng, sizes, p.p_max_kw, class_sizes=classes)
+    exo = Exo(price_bank(seed=seed), arrival_rates(classes))
+    return Workload(f"serve-{n_envs}-logU(8,128)", p, st, exo, seed)
+
+
+def random_actions(rng: np.random.Generator, n_ports_total: int, n_levels: int = 11, steps: Optional[int] = None) -> np.ndarray:
+    """Uniform action levels 0..n_levels-1 as int8, shape [P] or [P, steps]."""
+    shape = (n_ports_total,) if steps is None else (n_ports_total, steps)
+    return rng.integers(0, n_levels, size=shape, dtype=np.int64).astype(np.int8)
