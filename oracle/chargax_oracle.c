@@ -283,13 +283,17 @@ void orc_destroy(orc *o)
 }
 
 /* Action level of local port q of env e at global step g when no action
- * array is given: uniform over 0..n_levels-1 from Philox word (g mod 4) of
- * counter (e, g/4, q, ACTION). */
+ * array is given (the random policy of the speed benchmark, Table
+ * "performance"): one Philox call of counter (e, g/8, q, ACTION) serves 8
+ * steps; step g takes the 16-bit half (g mod 2) of word (g/2 mod 4) and maps
+ * it to 0..n_levels-1 by the high half of the product with n_levels. */
 int32_t orc_random_action(const orc *o, int32_t e, uint32_t g, int32_t q)
 {
     uint32_t w[4];
-    draw(o, e, g >> 2, (uint32_t)q, ORC_PURPOSE_ACTION, w);
-    return (int32_t)to_range(w[g & 3u], (uint32_t)o->p.n_levels);
+    draw(o, e, g >> 3, (uint32_t)q, ORC_PURPOSE_ACTION, w);
+    uint32_t word = w[(g >> 1) & 3u];
+    uint32_t half = (g & 1u) ? (word >> 16) : (word & 0xFFFFu);
+    return (int32_t)((half * (uint32_t)o->p.n_levels) >> 16);
 }
 
 /* ------------------------------------------------------------------------ */
