@@ -1,0 +1,354 @@
+#!/usr/bin/env python
+"""Throughput of the batched charging-station step on B300.
+
+One timed step = one full 288-step episode (24 h of 5-minute steps) of every
+station of the heterogeneous batch (65536 stations, 25 % each of 8/16/32/64
+chargers), random 11-level actions drawn in-kernel, run as a CUDA graph of
+fused persistent-kernel launches (steps per launch and warps per block from
+the library's autotuner).  The plain form (one thread per station, one launch
+per step, same graph replay) is timed the same way beside it.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle (the
+plain FP64 C program the library is checked against) on a bounded sample of
+the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "env-steps/s at 64K mixed-size envs vs plain form; p50/p99 serve step latency"
+L2_FLUSH_BYTES = 512 << 20          # > 126 MB L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["b300", "reference"], default="b300")
+    ap.add_argument("--n-envs", type=int, default=65536)
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------
+# helpers
+# ----------------------------------------------------------------------------
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        mx = max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws == 1:
+        return 0, 1, 0
+    import torch
+    import torch.distributed as dist
+    rank, local = int(os.environ["RANK"]), int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl")
+    return rank, ws, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+# Algorithmic work per unit (derivation in DESIGN.md, "Roofline accounting").
+PLAIN_BYTES_PER_PORT_STEP = 34.0     # read trem,meta,soc,erem,cap,rbar (21) + write soc,erem,p,trem (13)
+PLAIN_BYTES_PER_ENV_STEP = 97.0      # station fields read + written, reward + done
+FUSED_OPS_PER_PORT_STEP = 48.0       # algorithmic ALU ops of one charger-step
+FUSED_OPS_PER_ENV_STEP = 130.0       # arrival Philox + Poisson + reward of one station-step
+FUSED_STATE_BYTES_PER_PORT = 54.0    # per launch: state in (21) + out (21) + statics (12)
+FUSED_STATE_BYTES_PER_ENV = 80.0
+LANES_PER_SM = 128
+
+
+def cpu_baseline(w, n_sample_envs, steps):
+    """Time the CPU oracle, as it stands (single thread), on the first
+    ``n_sample_envs`` stations of the workload for ``steps`` steps."""
+    import numpy as np
+    import oracle
+    from paper_2507_01522_b300 import inputs as I
+    ids = np.arange(n_sample_envs)
+    sub = I.Workload(w.name, w.params, w.stations.subset(ids), w.exo, w.seed)
+    o = oracle.Oracle(sub, streams=ids)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        o.step(None)
+    dt = time.perf_counter() - t0
+    ports = int(sub.stations.total_ports)
+    return dict(value=n_sample_envs * steps / dt, unit="env-steps/s", cores=1, kind="oracle",
+                sample=f"first {n_sample_envs} of {w.stations.n_envs} stations ({ports} chargers) x {steps} steps, "
+                       f"Philox actions, FP64, 1 thread", seconds=round(dt, 3),
+                charger_steps_per_s=ports * steps / dt)
+
+
+def calibrate_sample(w, target_s, steps):
+    import numpy as np
+    import oracle
+    from paper_2507_01522_b300 import inputs as I
+    n = 256
+    ids = np.arange(n)
+    sub = I.Workload(w.name, w.params, w.stations.subset(ids), w.exo, w.seed)
+    o = oracle.Oracle(sub, streams=ids)
+    t0 = time.perf_counter()
+    for _ in range(16):
+        o.step(None)
+    per_env_step = (time.perf_counter() - t0) / (n * 16)
+    return int(max(64, min(w.stations.n_envs, target_s / (per_env_step * steps))))
+
+
+# ----------------------------------------------------------------------------
+# reference arm: the CPU oracle
+# ----------------------------------------------------------------------------
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2507_01522_b300 import inputs as I
+    w = I.heterogeneous(n_envs=args.n_envs)
+    T = w.params.ep_len
+    n = calibrate_sample(w, 8.0, T)
+    for _ in range(args.warmup):
+        cpu_baseline(w, max(64, n // 8), 8)
+    vals, secs = [], []
+    for _ in range(args.steps):
+        cb = cpu_baseline(w, n, T)
+        vals.append(cb["value"])
+        secs.append(cb["seconds"])
+    v = sum(vals) / len(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "env-steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / len(secs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "n_envs": w.stations.n_envs, "horizon": T,
+                       "sample_envs_per_step": n, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": v, "unit": "env-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": cb["sample"]},
+            "e2e": {"value": v, "unit": "env-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# the B300 arm
+# ----------------------------------------------------------------------------
+
+def run_b300(args):
+    import numpy as np
+    import torch
+    from paper_2507_01522_b300 import chargax
+    from paper_2507_01522_b300 import inputs as I
+
+    rank, ws, local = dist_init()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = I.heterogeneous(n_envs=args.n_envs, seed=0)
+    T = w.params.ep_len
+    b = chargax.Batch(w, seed=1000 + rank)
+    E, P = b.E, b.P
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    K, W = b.autotune(T)
+    reward = torch.empty(E, T, device=dev)
+    done = torch.empty(E, T, dtype=torch.uint8, device=dev)
+    obs = torch.empty(b.obs_size, device=dev)
+    launches_per_step = math.ceil(T / K)
+
+    def timed(fn, n):
+        times = []
+        for _ in range(n):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            times.append((e0, e1))
+        torch.cuda.synchronize()
+        return [a.elapsed_time(c) for a, c in times]
+
+    fused = lambda: b.rollout(T, reward=reward, done=done, obs=obs)
+    for _ in range(args.warmup):
+        fused()
+    torch.cuda.synchronize()
+    barrier(ws)
+    torch.cuda.synchronize()
+    with Clocks(local) as ck:
+        ms = timed(fused, args.steps)
+        torch.cuda.synchronize()
+        barrier(ws)
+    b.check()
+    total_s = max_over_ranks(sum(ms) / 1e3, ws)
+    ms_step = 1e3 * total_s / args.steps
+    env_steps = E * T * args.steps * ws
+    value = env_steps / total_s
+
+    # roofline of the fused kernel (ALU-bound: state stays in registers)
+    pk, pk_kind = peaks()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_mhz = pk.get("sm_max_mhz", 2032.0)
+    alu_peak = sm_count * LANES_PER_SM * sm_mhz * 1e6 / 1e12       # Tops/s
+    launch_ms = ms_step / launches_per_step
+    ops_launch = (FUSED_OPS_PER_PORT_STEP * P + FUSED_OPS_PER_ENV_STEP * E) * K
+    achieved = ops_launch / (launch_ms * 1e-3) / 1e12
+    fused_bytes_launch = FUSED_STATE_BYTES_PER_PORT * P + FUSED_STATE_BYTES_PER_ENV * E + 5.0 * E * K
+    roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s", "frac": achieved / alu_peak,
+                "traffic": None, "kernel": "k_step_fused", "launch_ms": launch_ms, "steps_per_launch": K,
+                "warps_per_block": W, "ops_per_launch": ops_launch,
+                "peak_source": f"{sm_count} SMs x {LANES_PER_SM} lanes x {sm_mhz:.0f} MHz ({pk_kind} max clock)",
+                "hbm_gbs_algorithmic": fused_bytes_launch / (launch_ms * 1e-3) / 1e9,
+                "hbm_frac_algorithmic": fused_bytes_launch / (launch_ms * 1e-3) / 1e9 / pk["hbm_gbs"]}
+
+    line = {"metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "n_envs": E, "n_chargers": P, "horizon_steps": T,
+                       "form": "fused persistent kernel, CUDA graph", "steps_per_launch": K, "warps_per_block": W,
+                       "actions": "Philox uniform 11 levels in-kernel", "parallelism": f"replicas x{ws}",
+                       "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MB write)"},
+            "charger_steps_per_s": P * T * args.steps * ws / total_s,
+            "roofline": roofline, "gpu_launches": launches_per_step * args.steps}
+
+    # plain form, same protocol: one launch per step, replayed as a graph
+    if not args.no_plain:
+        bp = chargax.Batch(w, seed=1000 + rank)
+        rp = torch.empty(T, E, device=dev)
+        dp = torch.empty(T, E, dtype=torch.uint8, device=dev)
+        bp.step(reward=rp[0], done=dp[0])
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            for k in range(T):
+                bp.step(reward=rp[k], done=dp[k])
+        for _ in range(args.warmup):
+            g.replay()
+        torch.cuda.synchronize()
+        barrier(ws)
+        pms = timed(g.replay, args.steps)
+        bp.check()
+        ptotal = max_over_ranks(sum(pms) / 1e3, ws)
+        pms_step = 1e3 * ptotal / args.steps
+        plain_bytes = PLAIN_BYTES_PER_PORT_STEP * P + PLAIN_BYTES_PER_ENV_STEP * E
+        gbs = plain_bytes / (pms_step * 1e-3 / T) / 1e9
+        line["plain"] = {"value": E * T * args.steps * ws / ptotal, "unit": "env-steps/s", "ms_per_step": pms_step,
+                         "launches_per_step": T,
+                         "roofline": {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                                      "frac": gbs / pk["hbm_gbs"], "traffic": None, "kernel": "k_step_plain",
+                                      "note": "state L2-resident across the 288 launches of a step"}}
+        line["fused_over_plain"] = line["value"] / line["plain"]["value"]
+        line["gpu_launches"] += T * args.steps
+        del bp
+
+    # end to end through the C interface with host buffers
+    if not args.no_e2e:
+        hr = torch.empty(E * T, dtype=torch.float32, pin_memory=True).numpy()
+        hd = torch.empty(E * T, dtype=torch.uint8, pin_memory=True).numpy()
+        ho = torch.empty(b.obs_size, dtype=torch.float32, pin_memory=True).numpy()
+        b.rollout_host(T, hr, hd, ho)
+        torch.cuda.synchronize()
+        barrier(ws)
+        et = []
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            b.rollout_host(T, hr, hd, ho)
+            et.append(time.perf_counter() - t0)
+        etot = max_over_ranks(sum(et), ws)
+        line["e2e"] = {"value": E * T * args.steps * ws / etot, "unit": "env-steps/s",
+                       "h2d_bytes_per_step": 0, "d2h_bytes_per_step": int(hr.nbytes + hd.nbytes + ho.nbytes),
+                       "ms_per_step": 1e3 * etot / args.steps,
+                       "api": "chx_rollout_host (pinned host outputs: reward, done, observation)"}
+        line["gpu_launches"] += launches_per_step * args.steps
+
+    line["clocks"] = ck.summary()
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        n = calibrate_sample(w, 12.0, T)
+        line["cpu_baseline"] = cpu_baseline(w, n, T)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    barrier(ws)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_b300(args)
+
+
+if __name__ == "__main__":
+    main()

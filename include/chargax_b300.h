@@ -1,0 +1,234 @@
+/*
+ * chargax_b300.h -- C interface of the B300 (sm_103a) EV charging-station
+ * simulator: a batch of independent stations stepped on one GPU.
+ *
+ * The operations follow the environment of "Chargax: A JAX Accelerated EV
+ * Charging Simulator" (arXiv 2507.01522):
+ *   - station layout: a tree whose root is the grid connection, inner nodes
+ *     are groups (splitters/cables) with a power limit I_H and efficiency
+ *     eta_H, and leaves are the chargers (Sec. "EV Station Layout");
+ *     this library supports depth-2 trees: root -> groups -> chargers;
+ *   - transition, Appendix A.2, in order: apply actions (per-charger clip),
+ *     architecture constraint Eq. (ArchConst) by proportional rescaling,
+ *     charge stationed cars with the SoC taper of Appendix A.1, time advance,
+ *     departure of time-sensitive users, Poisson arrivals parked first come
+ *     first served;
+ *   - reward, Appendix A.3: profit minus alpha-weighted penalties
+ *     (missing energy at departure, rejected cars, constraint violation);
+ *   - exploring-starts reset (Appendix "Practical Considerations"): an
+ *     empty station at step-of-day 0 and a random day of the price bank.
+ *
+ * Conventions
+ *   - Every function returns CHX_OK (0) or a negative status; no exception
+ *     crosses the interface.  chx_last_error() gives the message of the last
+ *     failure on the calling thread.
+ *   - Pointer names: d_* are device pointers (memory of the handle's GPU),
+ *     h_* are host pointers.  Unprefixed array pointers follow the rule
+ *     stated at the function.
+ *   - "Batch order": envs are numbered 0..n_envs-1 as passed to chx_create;
+ *     per-charger arrays are CSR by station (charger q of env e is element
+ *     port_off[e] + q, port_off = exclusive prefix sum of n_ports).
+ *   - Calls that take a stream are asynchronous on it (cudaStream_t passed as
+ *     void*; NULL = legacy default stream).  Buffers must stay valid until the
+ *     stream reaches the call.  A handle must not be used from two threads at
+ *     once.
+ *   - Units: power kW, energy kWh, time in steps of dt_h hours, prices EUR/kWh.
+ */
+#ifndef CHARGAX_B300_H
+#define CHARGAX_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define CHX_OK 0
+#define CHX_EINVAL (-1)   /* bad argument or configuration                    */
+#define CHX_ENOMEM (-2)   /* device or host allocation failed / over budget   */
+#define CHX_ECUDA (-3)    /* a CUDA call failed                               */
+#define CHX_ETIMEOUT (-4) /* a wait ran out of time                           */
+#define CHX_EFAULT (-5)   /* a kernel flagged bad input (e.g. action level out of range) */
+
+#define CHX_MAX_PORTS 128   /* chargers per station                          */
+#define CHX_MAX_GROUPS 32   /* group nodes per station                       */
+#define CHX_MAX_STAY 255    /* longest stay in steps                         */
+
+/* ---- configuration ----------------------------------------------------- */
+
+/* Scalar environment parameters (Table "ppo-config" and the car/user
+ * profile distributions of Appendix A.1).  Charger type 0 = AC, 1 = DC. */
+typedef struct chx_env_params {
+    int32_t ep_len;          /* steps per episode (288 = 24 h of 5 min)        */
+    int32_t n_levels;        /* action levels: k in 0..n_levels-1 requests
+                                k/(n_levels-1) of the charger maximum          */
+    float dt_h;              /* step length in hours                          */
+    float tau;               /* SoC where the taper starts, (0,1)             */
+    float p_sell;            /* price charged to customers                    */
+    float c_fixed;           /* fixed cost per step                           */
+    float alpha_sat;         /* weight of missing kWh at departure            */
+    float alpha_decl;        /* weight of rejected cars                       */
+    float alpha_con;         /* weight of the constraint-violation penalty    */
+    float soc_target;        /* SoC users want: Delta E = (target - SoC0) C   */
+    float p_max_kw[2];       /* charger maximum power per type                */
+    float eta_port[2];       /* charger efficiency per type, (0,1]            */
+    float cap_kwh[2];        /* car capacity ~ U(lo, hi)                      */
+    float soc0[2];           /* arrival SoC ~ U(lo, hi)                       */
+    int32_t stay_steps[2];   /* stay ~ U{lo..hi} steps, 1 <= lo <= hi <= 255  */
+    float rbar_kw[2][2];     /* car maximum rate ~ U(lo, hi) per charger type */
+} chx_env_params;
+
+/* A batch of stations, CSR.  Groups of a station are contiguous charger
+ * ranges listed in charger order.  All pointers are host pointers, read only
+ * during chx_create. */
+typedef struct chx_stations {
+    int32_t n_envs;
+    const int32_t* h_n_ports;        /* [n_envs], 1..CHX_MAX_PORTS            */
+    const uint8_t* h_port_type;      /* [sum n_ports], 0 AC / 1 DC            */
+    const int32_t* h_n_groups;       /* [n_envs], 1..min(n_ports, 32)         */
+    const int32_t* h_group_size;     /* [sum n_groups], >= 1, sums to n_ports */
+    const float* h_group_limit_kw;   /* [sum n_groups] I_H of the group, > 0  */
+    const float* h_group_eta;        /* [sum n_groups] eta_H in (0,1], or NULL = 1 */
+    const float* h_grid_limit_kw;    /* [n_envs] root limit, > 0              */
+    const float* h_grid_eta;         /* [n_envs] or NULL = 1                  */
+    const int32_t* h_arrival_class;  /* [n_envs] row of the arrival table     */
+} chx_stations;
+
+/* Exogenous tables (host pointers, copied to the device by chx_create). */
+typedef struct chx_exo {
+    int32_t n_days;                  /* rows of the price bank, >= 1          */
+    const float* h_price;            /* [n_days][ep_len] buy price            */
+    int32_t n_arrival_classes;       /* rows of the arrival table, >= 1       */
+    const float* h_arrival_rate;     /* [n_classes][ep_len] mean cars/step, 0..64 */
+} chx_exo;
+
+typedef struct chx_handle chx_handle;
+
+/* ---- lifetime ---------------------------------------------------------- */
+
+/* Create a batch on the current CUDA device and reset every env with `seed`
+ * (per-env Philox key = seed; stream id = env index).  The library allocates
+ * and owns all env state on the device.  Blocks until the state is ready.
+ * Errors: CHX_EINVAL for a configuration outside the documented ranges,
+ * CHX_ENOMEM, CHX_ECUDA. */
+int chx_create(const chx_stations* st, const chx_env_params* params, const chx_exo* exo,
+               uint64_t seed, chx_handle** out);
+int chx_destroy(chx_handle* h);
+
+/* Message of the last failed call on this thread (static storage). */
+const char* chx_last_error(void);
+
+int chx_n_envs(const chx_handle* h, int32_t* out);
+int chx_n_ports_total(const chx_handle* h, int64_t* out);
+/* h_offsets[n_envs+1]: charger offsets in batch order. */
+int chx_port_offsets(const chx_handle* h, int64_t* h_offsets);
+/* Floats of one observation of the whole batch: 8 per env + 6 per charger. */
+int chx_obs_size(const chx_handle* h, int64_t* out);
+
+/* ---- reset, Appendix "Practical Considerations" ---------------------------
+ * Start a new episode for the listed envs (d_env_ids: device int32 [n] in
+ * batch numbering; NULL = all envs): Philox key := seed, global step := 0,
+ * every charger empty, step of day 0, day drawn from the price bank.
+ * Statistics are kept.  CHX_EINVAL for n < 0. */
+int chx_reset(chx_handle* h, const int32_t* d_env_ids, int32_t n, uint64_t seed, void* stream);
+
+/* ---- one step, plain form ------------------------------------------------
+ * One transition of every env, one kernel launch, one thread per env, state
+ * read from and written back to device memory.
+ *   d_actions: device int8, level of charger (port_off[e]+q) at element
+ *              (port_off[e]+q)*lda; NULL = uniform levels drawn in the kernel
+ *              with Philox (counter: env, step/8, charger, 2; 16-bit half of a
+ *              word).  Levels outside 0..n_levels-1 are clamped and flag
+ *              CHX_EFAULT at the next chx_check.
+ *   d_reward:  device float [n_envs]; d_done: device uint8 [n_envs] (1 when
+ *              the episode ended in this step; the env is already reset).
+ * Either output may be NULL. */
+int chx_step(chx_handle* h, const int8_t* d_actions, int64_t lda, float* d_reward, uint8_t* d_done,
+             void* stream);
+
+/* ---- K steps, fused form -------------------------------------------------
+ * k_steps transitions of every env in ONE launch of a persistent kernel:
+ * each warp owns a tile of stations of one size class, keeps their state in
+ * registers across the k steps and reduces over chargers with warp shuffles.
+ * Events (arrivals, departures, episode ends) are identical to k calls of
+ * chx_step with the same actions; floating-point results agree to rounding
+ * (the sums over chargers associate differently).
+ *   d_actions: NULL (Philox levels) or device int8 with the level of charger
+ *              i at step k at element i*lda + k (lda >= k_steps).
+ *   d_reward / d_done: element e*ld_out + k for env e, step k (ld_out >=
+ *              k_steps); either may be NULL.
+ *   d_obs:     NULL or device float [chx_obs_size]: the observation after the
+ *              last step.
+ * Launch shape (warps per block) comes from chx_autotune, or a default. */
+int chx_step_n(chx_handle* h, int32_t k_steps, const int8_t* d_actions, int64_t lda,
+               float* d_reward, uint8_t* d_done, int64_t ld_out, float* d_obs, void* stream);
+
+/* ---- rollout -------------------------------------------------------------
+ * n_steps transitions with Philox actions as a CUDA graph of fused launches
+ * (steps per launch and warps per block (1..8) from chx_autotune; captured on the
+ * first call and re-used while n_steps and the output pointers are the same).
+ * Outputs as chx_step_n with ld_out = n_steps; d_obs after the last step. */
+int chx_rollout(chx_handle* h, int32_t n_steps, float* d_reward, uint8_t* d_done, float* d_obs,
+                void* stream);
+
+/* Same as chx_rollout with HOST outputs: the device results are copied to
+ * h_reward [n_envs*n_steps], h_done [n_envs*n_steps] and h_obs (any may be
+ * NULL; pinned memory gives full copy bandwidth) and the call returns when
+ * they are there. */
+int chx_rollout_host(chx_handle* h, int32_t n_steps, float* h_reward, uint8_t* h_done, float* h_obs,
+                     void* stream);
+
+/* One plain step with HOST buffers: actions are copied in (h_actions NULL =
+ * Philox levels), reward/done/observation copied out; returns when done. */
+int chx_step_host(chx_handle* h, const int8_t* h_actions, float* h_reward, uint8_t* h_done,
+                  float* h_obs, void* stream);
+
+/* Choose steps per launch and warps per block for chx_rollout by timing
+ * candidate shapes on a copy of the state (the state is restored).  Blocks.
+ * h_steps_per_launch / h_warps_per_block receive the choice (may be NULL). */
+int chx_autotune(chx_handle* h, int32_t n_steps, int32_t* h_steps_per_launch, int32_t* h_warps_per_block);
+/* Set the launch shape by hand (0 keeps the current value). */
+int chx_set_launch(chx_handle* h, int32_t steps_per_launch, int32_t warps_per_block);
+
+/* ---- observation -----------------------------------------------------------
+ * d_obs: device float [chx_obs_size].  Env e's block starts at float
+ * 8*e + 6*port_off[e]: [sin, cos of time of day, buy price now, p_sell,
+ * occupied fraction, day/n_days, step/ep_len, weekday flag], then per charger
+ * [occupied, SoC, remaining stay/stay_hi, r_hat/P_max, last power/P_max,
+ * remaining demand/cap_hi]. */
+int chx_observe(chx_handle* h, float* d_obs, void* stream);
+
+/* ---- state, checkpoint, statistics ------------------------------------------
+ * Host arrays in batch order (all blocking).  Per charger [P]: SoC, remaining
+ * demand kWh, capacity kWh, car maximum rate kW, last applied power kW,
+ * remaining stay (0 = empty).  Per env [E]: step of day, day, global step,
+ * Philox key words, running episode return.  NULL skips a field on get and
+ * keeps it on set. */
+int chx_get_state(chx_handle* h, float* h_soc, float* h_erem, float* h_cap, float* h_rbar, float* h_p,
+                  uint8_t* h_trem, int32_t* h_tod, int32_t* h_day, uint32_t* h_gstep, uint32_t* h_key0,
+                  uint32_t* h_key1, float* h_ep_ret);
+int chx_set_state(chx_handle* h, const float* h_soc, const float* h_erem, const float* h_cap,
+                  const float* h_rbar, const float* h_p, const uint8_t* h_trem, const int32_t* h_tod,
+                  const int32_t* h_day, const uint32_t* h_gstep, const uint32_t* h_key0,
+                  const uint32_t* h_key1, const float* h_ep_ret);
+
+/* Per-env running statistics [E]: cars admitted, cars rejected, kWh missing
+ * at departure, kWh charged, finished episodes, return of the last episode. */
+int chx_stats(chx_handle* h, uint32_t* h_arrived, uint32_t* h_rejected, float* h_missing_kwh,
+              float* h_charged_kwh, uint32_t* h_episodes, float* h_last_return);
+
+/* Checkpoint: the full env state (state + statistics) as a byte blob.
+ * chx_save with h_buf NULL writes the needed size to *size. */
+int chx_save(chx_handle* h, void* h_buf, size_t* size);
+int chx_load(chx_handle* h, const void* h_buf, size_t size);
+
+/* Synchronise the handle's work on `stream` and report (then clear) the
+ * device-side fault flag: CHX_EFAULT if a kernel saw bad input. */
+int chx_check(chx_handle* h, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CHARGAX_B300_H */

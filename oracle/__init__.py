@@ -64,6 +64,7 @@ def lib():
         L.orc_get_info.argtypes = [vp] + [vp] * 9
         L.orc_get_stats.argtypes = [vp] + [vp] * 6
         L.orc_get_power.argtypes = [vp, vp]
+        L.orc_set_streams.argtypes = [vp, vp, u64]
         L.orc_philox.argtypes = [vp, vp, vp]
         L.orc_poisson.restype = i32
         L.orc_poisson.argtypes = [C.c_float, C.c_uint32]
@@ -113,7 +114,7 @@ def params_struct(p) -> _Params:
 class Oracle:
     """A batch of envs simulated by the CPU oracle (FP64)."""
 
-    def __init__(self, workload, seed: int | None = None):
+    def __init__(self, workload, seed: int | None = None, streams=None):
         w = workload
         st, exo = w.stations, w.exo
         self.params = w.params
@@ -131,6 +132,10 @@ class Oracle:
         self.h = lib().orc_create(C.byref(self._p), self.E, *[_ptr(a) for a in k[:9]],
                                   int(exo.price.shape[0]), _ptr(k[9]), int(exo.arrival_rate.shape[0]),
                                   _ptr(k[10]), C.c_uint64(seed))
+        if streams is not None:
+            ids = np.ascontiguousarray(streams, dtype=np.uint32)
+            assert ids.shape == (self.E,)
+            lib().orc_set_streams(self.h, _ptr(ids), C.c_uint64(seed))
 
     def __del__(self):
         if getattr(self, "h", None):

@@ -67,6 +67,7 @@ typedef struct orc {
     /* per-env state */
     int32_t *tod, *day;
     uint32_t *gstep, *key0, *key1;
+    uint32_t *stream;                      /* Philox stream id (default: index) */
     double *ep_ret, *last_ret;
     uint32_t *n_episodes;
     /* per-env running statistics */
@@ -108,7 +109,7 @@ void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
 
 static void draw(const orc *o, int32_t e, uint32_t c1, uint32_t c2, uint32_t purpose, uint32_t out[4])
 {
-    uint32_t ctr[4] = {(uint32_t)e, c1, c2, purpose};
+    uint32_t ctr[4] = {o->stream[e], c1, c2, purpose};
     uint32_t key[2] = {o->key0[e], o->key1[e]};
     orc_philox(ctr, key, out);
 }
@@ -248,6 +249,8 @@ orc *orc_create(const orc_params *prm, int32_t E,
     o->gstep = (uint32_t *)xcalloc((size_t)E, sizeof(uint32_t));
     o->key0 = (uint32_t *)xcalloc((size_t)E, sizeof(uint32_t));
     o->key1 = (uint32_t *)xcalloc((size_t)E, sizeof(uint32_t));
+    o->stream = (uint32_t *)xcalloc((size_t)E, sizeof(uint32_t));
+    for (int32_t e = 0; e < E; ++e) o->stream[e] = (uint32_t)e;
     o->ep_ret = (double *)xcalloc((size_t)E, sizeof(double));
     o->last_ret = (double *)xcalloc((size_t)E, sizeof(double));
     o->n_episodes = (uint32_t *)xcalloc((size_t)E, sizeof(uint32_t));
@@ -274,7 +277,7 @@ void orc_destroy(orc *o)
     void *ptrs[] = {o->port_off, o->group_off, o->n_ports, o->n_groups, o->arrival_class, o->grid_limit,
                     o->grid_eta, o->port_type, o->port_group, o->group_size, o->group_limit, o->group_eta,
                     o->price, o->lam, o->soc, o->erem, o->cap, o->rbar, o->pw, o->scratch_p, o->scratch_leave, o->trem, o->tod,
-                    o->day, o->gstep, o->key0, o->key1, o->ep_ret, o->last_ret, o->n_episodes,
+                    o->day, o->gstep, o->key0, o->key1, o->stream, o->ep_ret, o->last_ret, o->n_episodes,
                     o->st_arrived, o->st_rejected, o->st_missing, o->st_charged, o->inf_M, o->inf_admitted,
                     o->inf_departed, o->inf_csat, o->inf_ccon, o->inf_enet, o->inf_egrid, o->inf_price,
                     o->inf_req_sum};
@@ -553,6 +556,14 @@ void orc_get_stats(const orc *o, double *arrived, double *rejected, double *miss
     memcpy(arrived, o->st_arrived, E * sizeof(double)); memcpy(rejected, o->st_rejected, E * sizeof(double));
     memcpy(missing, o->st_missing, E * sizeof(double)); memcpy(charged, o->st_charged, E * sizeof(double));
     memcpy(n_episodes, o->n_episodes, E * sizeof(uint32_t)); memcpy(last_ret, o->last_ret, E * sizeof(double));
+}
+
+/* Give env e the Philox stream id ids[e] (the env's index in a larger batch
+ * when this oracle simulates a subset of it), then reset all envs. */
+void orc_set_streams(orc *o, const uint32_t *ids, uint64_t seed)
+{
+    memcpy(o->stream, ids, (size_t)o->E * sizeof(uint32_t));
+    orc_reset(o, NULL, 0, seed);
 }
 
 /* the per-step power of each port (after rescaling) of the last step */

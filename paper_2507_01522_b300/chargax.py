@@ -1,0 +1,240 @@
+"""Python binding of ``libchargax_b300.so`` (the C interface in
+``include/chargax_b300.h``).
+
+Argument marshalling only: every step of the simulation runs in the CUDA
+library.  Device buffers are torch CUDA tensors (their ``data_ptr()`` is
+passed), host buffers numpy arrays.  If the library has not been built the
+import of this module fails; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import inputs as _inputs
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libchargax_b300.so")
+
+CHX_OK, CHX_EINVAL, CHX_ENOMEM, CHX_ECUDA, CHX_ETIMEOUT, CHX_EFAULT = 0, -1, -2, -3, -4, -5
+
+# every symbol the header declares (checked by the CPU tests)
+EXPORTS = (
+    "chx_create", "chx_destroy", "chx_last_error", "chx_n_envs", "chx_n_ports_total", "chx_port_offsets",
+    "chx_obs_size", "chx_reset", "chx_step", "chx_step_n", "chx_rollout", "chx_rollout_host", "chx_step_host",
+    "chx_autotune", "chx_set_launch", "chx_observe", "chx_get_state", "chx_set_state", "chx_stats", "chx_save",
+    "chx_load", "chx_check",
+)
+
+
+class ChxError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"chargax_b300 error {code}: {msg}")
+        self.code = code
+
+
+class _Params(C.Structure):
+    _fields_ = [
+        ("ep_len", C.c_int32), ("n_levels", C.c_int32),
+        ("dt_h", C.c_float), ("tau", C.c_float), ("p_sell", C.c_float), ("c_fixed", C.c_float),
+        ("alpha_sat", C.c_float), ("alpha_decl", C.c_float), ("alpha_con", C.c_float), ("soc_target", C.c_float),
+        ("p_max_kw", C.c_float * 2), ("eta_port", C.c_float * 2), ("cap_kwh", C.c_float * 2),
+        ("soc0", C.c_float * 2), ("stay_steps", C.c_int32 * 2), ("rbar_kw", (C.c_float * 2) * 2),
+    ]
+
+
+class _Stations(C.Structure):
+    _fields_ = [
+        ("n_envs", C.c_int32), ("h_n_ports", C.c_void_p), ("h_port_type", C.c_void_p), ("h_n_groups", C.c_void_p),
+        ("h_group_size", C.c_void_p), ("h_group_limit_kw", C.c_void_p), ("h_group_eta", C.c_void_p),
+        ("h_grid_limit_kw", C.c_void_p), ("h_grid_eta", C.c_void_p), ("h_arrival_class", C.c_void_p),
+    ]
+
+
+class _Exo(C.Structure):
+    _fields_ = [("n_days", C.c_int32), ("h_price", C.c_void_p), ("n_arrival_classes", C.c_int32),
+                ("h_arrival_rate", C.c_void_p)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load the CUDA library (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -m paper_2507_01522_b300.build`")
+    L = C.CDLL(path)
+    vp, i32, i64, u64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64
+    sig = {
+        "chx_create": [vp, vp, vp, u64, vp], "chx_destroy": [vp], "chx_n_envs": [vp, vp],
+        "chx_n_ports_total": [vp, vp], "chx_port_offsets": [vp, vp], "chx_obs_size": [vp, vp],
+        "chx_reset": [vp, vp, i32, u64, vp], "chx_step": [vp, vp, i64, vp, vp, vp],
+        "chx_step_n": [vp, i32, vp, i64, vp, vp, i64, vp, vp], "chx_rollout": [vp, i32, vp, vp, vp, vp],
+        "chx_rollout_host": [vp, i32, vp, vp, vp, vp], "chx_step_host": [vp, vp, vp, vp, vp, vp],
+        "chx_autotune": [vp, i32, vp, vp], "chx_set_launch": [vp, i32, i32], "chx_observe": [vp, vp, vp],
+        "chx_get_state": [vp] + [vp] * 12, "chx_set_state": [vp] + [vp] * 12, "chx_stats": [vp] + [vp] * 6,
+        "chx_save": [vp, vp, vp], "chx_load": [vp, vp, C.c_size_t], "chx_check": [vp, vp],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = C.c_int
+    L.chx_last_error.restype = C.c_char_p
+    L.chx_last_error.argtypes = []
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != CHX_OK:
+        raise ChxError(rc, _lib.chx_last_error().decode())
+
+
+def _np_ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _dev_ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def params_struct(p: "_inputs.EnvParams") -> _Params:
+    s = _Params()
+    s.ep_len = int(p.ep_len); s.n_levels = int(p.n_levels)
+    s.dt_h = p.dt_h; s.tau = p.tau; s.p_sell = p.p_sell; s.c_fixed = p.c_fixed
+    s.alpha_sat = p.alpha_sat; s.alpha_decl = p.alpha_decl; s.alpha_con = p.alpha_con; s.soc_target = p.soc_target
+    for k in range(2):
+        s.p_max_kw[k] = p.p_max_kw[k]; s.eta_port[k] = p.eta_port[k]; s.cap_kwh[k] = p.cap_kwh[k]
+        s.soc0[k] = p.soc0[k]; s.stay_steps[k] = int(p.stay_steps[k])
+        s.rbar_kw[0][k] = p.rbar_ac_kw[k]; s.rbar_kw[1][k] = p.rbar_dc_kw[k]
+    return s
+
+
+STATE_FIELDS = (("soc", np.float32, "P"), ("erem", np.float32, "P"), ("cap", np.float32, "P"),
+                ("rbar", np.float32, "P"), ("p", np.float32, "P"), ("trem", np.uint8, "P"),
+                ("tod", np.int32, "E"), ("day", np.int32, "E"), ("gstep", np.uint32, "E"),
+                ("key0", np.uint32, "E"), ("key1", np.uint32, "E"), ("ep_ret", np.float32, "E"))
+
+
+class Batch:
+    """A batch of stations on the current CUDA device (one chx_handle)."""
+
+    def __init__(self, workload: "_inputs.Workload", seed: int | None = None):
+        L = load_library()
+        st, exo = workload.stations, workload.exo
+        self.workload = workload
+        self._keep = [np.ascontiguousarray(a) for a in (
+            st.n_ports.astype(np.int32), st.port_type.astype(np.uint8), st.n_groups.astype(np.int32),
+            st.group_size.astype(np.int32), st.group_limit_kw.astype(np.float32), st.group_eta.astype(np.float32),
+            st.grid_limit_kw.astype(np.float32), st.grid_eta.astype(np.float32), st.arrival_class.astype(np.int32),
+            exo.price.astype(np.float32), exo.arrival_rate.astype(np.float32))]
+        k = self._keep
+        s = _Stations(st.n_envs, *[_np_ptr(a) for a in k[:9]])
+        x = _Exo(int(exo.price.shape[0]), _np_ptr(k[9]), int(exo.arrival_rate.shape[0]), _np_ptr(k[10]))
+        self._p = params_struct(workload.params)
+        h = C.c_void_p()
+        seed = workload.seed if seed is None else seed
+        _check(L.chx_create(C.byref(s), C.byref(self._p), C.byref(x), C.c_uint64(seed), C.byref(h)))
+        self.h = h
+        n = C.c_int32(); P = C.c_int64(); O = C.c_int64()
+        _check(L.chx_n_envs(h, C.byref(n)))
+        _check(L.chx_n_ports_total(h, C.byref(P)))
+        _check(L.chx_obs_size(h, C.byref(O)))
+        self.E, self.P, self.obs_size = n.value, P.value, O.value
+        self.port_off = np.zeros(self.E + 1, np.int64)
+        _check(L.chx_port_offsets(h, _np_ptr(self.port_off)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.chx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- stepping -------------------------------------------------------
+    def reset(self, env_ids=None, seed: int = 0, stream=None):
+        n = 0 if env_ids is None else int(env_ids.numel())
+        _check(_lib.chx_reset(self.h, _dev_ptr(env_ids), n, C.c_uint64(seed), _stream_ptr(stream)))
+
+    def step(self, actions=None, reward=None, done=None, lda: int = 1, stream=None):
+        _check(_lib.chx_step(self.h, _dev_ptr(actions), lda, _dev_ptr(reward), _dev_ptr(done), _stream_ptr(stream)))
+
+    def step_n(self, k_steps: int, actions=None, reward=None, done=None, lda: int = 0, ld_out: int = 0, obs=None,
+               stream=None):
+        _check(_lib.chx_step_n(self.h, k_steps, _dev_ptr(actions), lda or k_steps, _dev_ptr(reward), _dev_ptr(done),
+                               ld_out or k_steps, _dev_ptr(obs), _stream_ptr(stream)))
+
+    def rollout(self, n_steps: int, reward=None, done=None, obs=None, stream=None):
+        _check(_lib.chx_rollout(self.h, n_steps, _dev_ptr(reward), _dev_ptr(done), _dev_ptr(obs), _stream_ptr(stream)))
+
+    def rollout_host(self, n_steps: int, reward=None, done=None, obs=None, stream=None):
+        _check(_lib.chx_rollout_host(self.h, n_steps, _np_ptr(reward), _np_ptr(done), _np_ptr(obs),
+                                     _stream_ptr(stream)))
+
+    def step_host(self, actions=None, reward=None, done=None, obs=None, stream=None):
+        _check(_lib.chx_step_host(self.h, _np_ptr(actions), _np_ptr(reward), _np_ptr(done), _np_ptr(obs),
+                                  _stream_ptr(stream)))
+
+    def observe(self, obs, stream=None):
+        _check(_lib.chx_observe(self.h, _dev_ptr(obs), _stream_ptr(stream)))
+
+    def autotune(self, n_steps: int):
+        k = C.c_int32(); w = C.c_int32()
+        _check(_lib.chx_autotune(self.h, n_steps, C.byref(k), C.byref(w)))
+        return k.value, w.value
+
+    def set_launch(self, steps_per_launch: int = 0, warps_per_block: int = 0):
+        _check(_lib.chx_set_launch(self.h, steps_per_launch, warps_per_block))
+
+    def check(self, stream=None):
+        _check(_lib.chx_check(self.h, _stream_ptr(stream)))
+
+    # ---- state ----------------------------------------------------------
+    def get_state(self) -> dict:
+        out = {name: np.zeros(self.P if kind == "P" else self.E, dt) for name, dt, kind in STATE_FIELDS}
+        _check(_lib.chx_get_state(self.h, *[_np_ptr(out[n]) for n, _, _ in STATE_FIELDS]))
+        return out
+
+    def set_state(self, s: dict):
+        arrs = [None if s.get(n) is None else np.ascontiguousarray(s[n], dtype=dt) for n, dt, _ in STATE_FIELDS]
+        _check(_lib.chx_set_state(self.h, *[_np_ptr(a) for a in arrs]))
+
+    def stats(self) -> dict:
+        E = self.E
+        d = dict(arrived=np.zeros(E, np.uint32), rejected=np.zeros(E, np.uint32), missing=np.zeros(E, np.float32),
+                 charged=np.zeros(E, np.float32), n_episodes=np.zeros(E, np.uint32), last_ret=np.zeros(E, np.float32))
+        _check(_lib.chx_stats(self.h, *[_np_ptr(d[k]) for k in
+                                        ("arrived", "rejected", "missing", "charged", "n_episodes", "last_ret")]))
+        return d
+
+    def save(self) -> bytes:
+        n = C.c_size_t()
+        _check(_lib.chx_save(self.h, None, C.byref(n)))
+        buf = np.zeros(n.value, np.uint8)
+        _check(_lib.chx_save(self.h, _np_ptr(buf), C.byref(n)))
+        return buf.tobytes()
+
+    def load(self, blob: bytes):
+        buf = np.frombuffer(blob, np.uint8).copy()
+        _check(_lib.chx_load(self.h, _np_ptr(buf), len(blob)))

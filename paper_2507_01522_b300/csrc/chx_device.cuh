@@ -1,0 +1,210 @@
+// chx_device.cuh -- device-side layout and arithmetic shared by the kernels
+// of the charging-station step (sm_103a).
+//
+// State layout in HBM ("slot space").  Stations are bucketed by size class
+// C in {8,16,32,64,128} (smallest power of two >= their charger count); a
+// class stores its stations back to back, each padded to C charger slots,
+// and its station count is padded to a multiple of 32/C for C < 32 so that
+// a warp always owns whole stations.  Per-charger arrays are SoA float/u8,
+// so a warp's 32*PPL consecutive chargers are one contiguous, aligned span
+// (PPL = C/32 chargers per lane for C >= 64, loaded as float2/float4).
+// Padding chargers and padding stations carry valid = 0 / user id -1.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace chx {
+
+constexpr int kWarp = 32;
+constexpr int kNumClasses = 5;             // 8, 16, 32, 64, 128
+constexpr int kPoissonMax = 127;
+constexpr uint32_t kPurposeArrival = 0u, kPurposeCar = 1u, kPurposeAction = 2u, kPurposeDay = 3u;
+
+// per-charger static bits
+constexpr uint32_t kMetaDC = 1u, kMetaValid = 2u, kMetaHead = 4u, kMetaTail = 8u;
+constexpr int kMetaGroupShift = 4;         // 5 bits: group slot within the warp tile (0..31)
+
+// device error bits
+constexpr uint32_t kErrActionRange = 1u;
+
+struct DevParams {
+    int ep_len, n_levels, n_days;
+    float dt, inv_dt, tau, inv_1m_tau, p_sell, c_fixed, a_sat, a_decl, a_con, soc_target;
+    float pmax0, pmax1, lvl0, lvl1;        // maximum power and power per level, per type
+    float inv_eta0, inv_eta1;              // 1 / charger efficiency, per type
+    float cap_lo, cap_span, soc_lo, soc_span;
+    int stay_lo;
+    uint32_t stay_span;
+    float rb_lo0, rb_span0, rb_lo1, rb_span1;
+    float obs_inv_stay, obs_inv_cap, obs_inv_days, obs_inv_len;
+};
+
+struct DevBatch {
+    // per charger slot
+    float *soc, *erem, *cap, *rbar, *pw;
+    uint8_t* trem;                         // remaining stay in steps, 0 = empty
+    uint32_t* meta;                        // kMeta* bits | group slot << 4
+    float *gcap, *ginv_eta;                // eta_H * I_H of the charger's group, 1/eta_H
+    // per station slot
+    int32_t *user_id, *user_port_off, *n_ports, *arrival_class;
+    float *grid_cap, *grid_inv_eta;        // eta_0 * I_0 of the root, 1/eta_0
+    int32_t *tod, *day;
+    uint32_t *gstep, *key0, *key1;
+    float *ep_ret, *last_ret;
+    uint32_t* n_episodes;
+    uint32_t *st_arrived, *st_rejected;
+    float *st_missing, *st_charged;
+    // exogenous tables
+    const float *price, *lam, *exp_neg_lam;
+    // classes (index 0..4 = size 8..128)
+    int cls_n_env[kNumClasses];            // padded station count
+    int cls_env_base[kNumClasses];
+    long long cls_port_base[kNumClasses];
+    int n_slots;
+    uint32_t* err;
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC 2011): 10 rounds; each round
+// multiplies counter words 0 and 2 by the Philox constants, crosses the high
+// halves into the other words with the round key, and the key advances by the
+// Weyl constants.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 x, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo_a = 0xD2511F53u * x.x, hi_a = __umulhi(0xD2511F53u, x.x);
+        const uint32_t lo_b = 0xCD9E8D57u * x.z, hi_b = __umulhi(0xCD9E8D57u, x.z);
+        x = make_uint4(hi_b ^ x.y ^ k0, lo_b, hi_a ^ x.w ^ k1, lo_a);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return x;
+}
+
+__device__ __forceinline__ uint32_t range_of(uint32_t w, uint32_t n) { return __umulhi(w, n); }
+// uniform [0,1) from the top 24 bits, exact in FP32
+__device__ __forceinline__ float unit_of(uint32_t w) { return __uint2float_rn(w >> 8) * 0x1p-24f; }
+
+__device__ __forceinline__ uint32_t word_of(uint4 v, uint32_t i)
+{
+    return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+}
+
+// level of a random action from the 8-step Philox block of a charger
+__device__ __forceinline__ int random_level(uint4 words, uint32_t g, int n_levels)
+{
+    const uint32_t w = word_of(words, (g >> 1) & 3u);
+    const uint32_t half = (g & 1u) ? (w >> 16) : (w & 0xFFFFu);
+    return (int)((half * (uint32_t)n_levels) >> 16);
+}
+
+// ---------------------------------------------------------------------------
+// Poisson count by inverse transform.  The count is an integer chosen by
+// floating point, so this exact sequence of correctly rounded FP32 operations
+// (explicit _rn intrinsics: no contraction into FMA) is the definition;
+// exp(-lambda) comes precomputed from the host in double, rounded once.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int poisson_count(float lam, float e0, uint32_t w)
+{
+    const float u = __fmul_rn(__uint2float_rn(w >> 8), 0x1p-24f);
+    float pk = e0, cdf = e0;
+    int k = 0;
+    while (u >= cdf && k < kPoissonMax) {
+        k += 1;
+        pk = __fdiv_rn(__fmul_rn(pk, lam), __int2float_rn(k));
+        cdf = __fadd_rn(cdf, pk);
+    }
+    return k;
+}
+
+// taper r_hat(SoC): r_bar in the bulk stage, linear to 0 at SoC = 1 above tau
+__device__ __forceinline__ float taper(float soc, float rbar, const DevParams& p)
+{
+    return soc <= p.tau ? rbar : (1.0f - soc) * rbar * p.inv_1m_tau;
+}
+
+// per-charger clip of Appendix A.2 "Apply Actions" (power form): requested
+// level, car rate r_hat, charger maximum, SoC <= 1 and demand >= 0 caps
+__device__ __forceinline__ float clip_power(int level, bool dc, float soc, float erem, float cap, float rbar,
+                                            const DevParams& p)
+{
+    const float pmax = dc ? p.pmax1 : p.pmax0;
+    const float preq = (float)level * (dc ? p.lvl1 : p.lvl0);
+    const float rhat = taper(soc, rbar, p);
+    const float soc_cap = (1.0f - soc) * cap * p.inv_dt;
+    const float dem_cap = erem * p.inv_dt;
+    float P = fminf(fminf(preq, rhat), fminf(fminf(pmax, soc_cap), dem_cap));
+    return fmaxf(P, 0.0f);
+}
+
+struct Car { float cap, soc, erem, rbar; int stay; };
+
+// car and user profile of the j-th arriving car (one Philox call)
+__device__ __forceinline__ Car draw_car(uint32_t uid, uint32_t g, uint32_t j, uint32_t k0, uint32_t k1, bool dc,
+                                        const DevParams& p)
+{
+    const uint4 w = philox4x32_10(make_uint4(uid, g, j, kPurposeCar), k0, k1);
+    Car c;
+    c.cap = p.cap_lo + p.cap_span * unit_of(w.x);
+    c.soc = p.soc_lo + p.soc_span * unit_of(w.y);
+    c.stay = p.stay_lo + (int)range_of(w.z, p.stay_span);
+    c.rbar = dc ? p.rb_lo1 + p.rb_span1 * unit_of(w.w) : p.rb_lo0 + p.rb_span0 * unit_of(w.w);
+    c.erem = fmaxf(p.soc_target - c.soc, 0.0f) * c.cap;
+    return c;
+}
+
+__device__ __forceinline__ int draw_day(uint32_t uid, uint32_t c1, uint32_t c2, uint32_t k0, uint32_t k1, int n_days)
+{
+    const uint4 w = philox4x32_10(make_uint4(uid, c1, c2, kPurposeDay), k0, k1);
+    return (int)range_of(w.x, (uint32_t)n_days);
+}
+
+__device__ __forceinline__ int arrivals(const DevBatch& b, const DevParams& p, uint32_t uid, uint32_t g, int t, int cls_row,
+                                        uint32_t k0, uint32_t k1)
+{
+    const uint4 w = philox4x32_10(make_uint4(uid, g, 0u, kPurposeArrival), k0, k1);
+    const size_t ix = (size_t)cls_row * (size_t)p.ep_len + (size_t)t;
+    return poisson_count(__ldg(b.lam + ix), __ldg(b.exp_neg_lam + ix), w.x);
+}
+
+// observation features of a station (8 floats) and of one charger (6 floats)
+__device__ __forceinline__ void obs_env(float* o, int t, int day, int occ, int n, const DevBatch& b, const DevParams& p)
+{
+    float s, c;
+    sincospif(2.0f * (float)t * p.obs_inv_len, &s, &c);
+    o[0] = s;
+    o[1] = c;
+    o[2] = __ldg(b.price + (size_t)day * (size_t)p.ep_len + (size_t)t);
+    o[3] = p.p_sell;
+    o[4] = (float)occ / (float)n;
+    o[5] = (float)day * p.obs_inv_days;
+    o[6] = (float)t * p.obs_inv_len;
+    o[7] = (day % 7) < 5 ? 1.0f : 0.0f;
+}
+
+__device__ __forceinline__ void obs_port(float* o, int trem, float soc, float erem, float rbar, float pw, bool dc,
+                                         const DevParams& p)
+{
+    const float inv_pmax = 1.0f / (dc ? p.pmax1 : p.pmax0);
+    const bool on = trem > 0;
+    o[0] = on ? 1.0f : 0.0f;
+    o[1] = soc;
+    o[2] = (float)trem * p.obs_inv_stay;
+    o[3] = on ? taper(soc, rbar, p) * inv_pmax : 0.0f;
+    o[4] = pw * inv_pmax;
+    o[5] = erem * p.obs_inv_cap;
+}
+
+// class of a station slot (classes are consecutive in slot space)
+__device__ __forceinline__ int class_of_slot(const DevBatch& b, int s)
+{
+    int c = 0;
+#pragma unroll
+    for (int i = 1; i < kNumClasses; ++i)
+        if (s >= b.cls_env_base[i]) c = i;
+    return c;
+}
+
+}  // namespace chx

@@ -1,0 +1,71 @@
+// chx_handle.h -- host-side state of a batch (the opaque chx_handle).
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/chargax_b300.h"
+#include "chx_device.cuh"
+#include "chx_kernels.h"
+
+namespace chx {
+
+using Buffers = std::vector<void*>;
+
+struct GraphKey {
+    int n_steps = 0;
+    float* reward = nullptr;
+    uint8_t* done = nullptr;
+    float* obs = nullptr;
+    int k = 0, w = 0;
+    bool valid = false;
+    bool operator==(const GraphKey& o) const
+    {
+        return valid && o.valid && n_steps == o.n_steps && reward == o.reward && done == o.done && obs == o.obs &&
+               k == o.k && w == o.w;
+    }
+};
+
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+}  // namespace chx
+
+struct chx_handle {
+    chx_env_params params{};
+    int E = 0;
+    long long P = 0;
+    int n_days = 0, n_arrival_classes = 0;
+    int device = 0, sm_count = 0;
+    std::vector<long long> user_port_off;      // [E+1] batch-order charger offsets
+    int cls_n_env[chx::kNumClasses] = {};      // padded stations per class
+    int cls_n_real[chx::kNumClasses] = {};
+    int cls_env_base[chx::kNumClasses] = {};
+    long long cls_port_base[chx::kNumClasses] = {};
+    int n_slots = 0;
+    long long n_port_slots = 0;
+    std::vector<int32_t> user_to_slot, slot_user;
+    std::vector<long long> slot_port_base;
+    chx::DevBatch b{};
+    chx::DevParams dp{};
+    chx::Buffers bufs;
+    int32_t* d_user_to_slot = nullptr;
+    int* d_counter = nullptr;
+    chx::FusedIO sched{};
+    int warps_per_block = 8, steps_per_launch = 32;
+    float tuned_ms = 0.f;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    chx::GraphKey graph_key{};
+    void* staging[8] = {};
+    size_t staging_bytes[8] = {};
+};
+
+namespace chx {
+int build_handle(const chx_stations* st, const chx_env_params* prm, const chx_exo* exo, uint64_t seed,
+                 int min_pad_envs_per_class, chx_handle** out);
+int enqueue_fused(chx_handle* h, int k_steps, const int8_t* actions, long long lda, float* reward, uint8_t* done,
+                  long long ld_out, float* obs, int warps, cudaStream_t st);
+void free_graph(chx_handle* h);
+}  // namespace chx

@@ -1,0 +1,39 @@
+// chx_kernels.h -- host-side launchers of the device kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "chx_device.cuh"
+
+namespace chx {
+
+// Arguments of one fused launch.  Tiles are scheduled largest class first:
+// sched_cls[i] is the class of schedule entry i, whose tiles are numbered
+// sched_tile_base[i] .. sched_tile_base[i+1]-1.
+struct FusedIO {
+    int k_steps;
+    const int8_t* actions;
+    long long lda;
+    float* reward;
+    uint8_t* done;
+    long long ld_out;
+    float* obs;
+    int n_sched;
+    int sched_cls[kNumClasses];
+    int sched_tile_base[kNumClasses + 1];
+    int total_tiles;
+    int* counter;                          // work counter, zero at launch
+};
+
+void launch_step_plain(const DevBatch& b, const DevParams& p, const int8_t* actions, long long lda, float* reward,
+                       uint8_t* done, const int* slot_list, int n_list, cudaStream_t st);
+void launch_step_fused(const DevBatch& b, const DevParams& p, const FusedIO& io, int blocks, int threads,
+                       cudaStream_t st);
+int fused_max_blocks_per_sm(int threads);
+
+// reset the stations whose batch ids are listed (NULL = all)
+void launch_reset(const DevBatch& b, const DevParams& p, const int32_t* user_to_slot, const int32_t* env_ids, int n,
+                  uint64_t seed, cudaStream_t st);
+void launch_observe(const DevBatch& b, const DevParams& p, float* obs, cudaStream_t st);
+
+}  // namespace chx

@@ -1,0 +1,938 @@
+// handle.cu -- the C interface (include/chargax_b300.h): batch creation and
+// layout, launches, CUDA-graph rollouts, autotuning, state access.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/chargax_b300.h"
+#include "chx_device.cuh"
+#include "chx_handle.h"
+#include "chx_kernels.h"
+
+using namespace chx;
+
+namespace chx {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg)
+{
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+    return fail(CHX_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+}  // namespace chx
+
+#define CUDA_TRY(expr)                                          \
+    do {                                                        \
+        cudaError_t _e = (expr);                                \
+        if (_e != cudaSuccess) return chx::cuda_fail(_e, #expr); \
+    } while (0)
+
+namespace {
+
+template <class T>
+int dalloc(Buffers& bufs, T** p, size_t n)
+{
+    void* q = nullptr;
+    const size_t bytes = std::max<size_t>(n, 1) * sizeof(T);
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) return fail(CHX_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+    e = cudaMemset(q, 0, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemset");
+    bufs.push_back(q);
+    *p = static_cast<T*>(q);
+    return CHX_OK;
+}
+
+int class_of_ports(int n)
+{
+    int c = 0;
+    while ((8 << c) < n) ++c;
+    return c;
+}
+
+int validate(const chx_stations* st, const chx_env_params* p, const chx_exo* x)
+{
+    if (!st || !p || !x) return fail(CHX_EINVAL, "null configuration pointer");
+    if (st->n_envs < 1 || st->n_envs > (1 << 26)) return fail(CHX_EINVAL, "n_envs out of range");
+    if (!st->h_n_ports || !st->h_port_type || !st->h_n_groups || !st->h_group_size || !st->h_group_limit_kw ||
+        !st->h_grid_limit_kw || !st->h_arrival_class)
+        return fail(CHX_EINVAL, "missing station array");
+    if (p->ep_len < 1 || p->ep_len > (1 << 20)) return fail(CHX_EINVAL, "ep_len out of range");
+    if (p->n_levels < 2 || p->n_levels > 255) return fail(CHX_EINVAL, "n_levels must be in 2..255");
+    if (!(p->dt_h > 0.f) || !std::isfinite(p->dt_h)) return fail(CHX_EINVAL, "dt_h must be > 0");
+    if (!(p->tau > 0.f && p->tau < 1.f)) return fail(CHX_EINVAL, "tau must be in (0,1)");
+    if (p->stay_steps[0] < 1 || p->stay_steps[1] > CHX_MAX_STAY || p->stay_steps[0] > p->stay_steps[1])
+        return fail(CHX_EINVAL, "stay_steps must satisfy 1 <= lo <= hi <= 255");
+    if (!(p->cap_kwh[0] > 0.f) || p->cap_kwh[1] < p->cap_kwh[0]) return fail(CHX_EINVAL, "cap_kwh range invalid");
+    if (p->soc0[0] < 0.f || p->soc0[1] > 1.f || p->soc0[1] < p->soc0[0]) return fail(CHX_EINVAL, "soc0 range invalid");
+    for (int t = 0; t < 2; ++t) {
+        if (!(p->p_max_kw[t] > 0.f)) return fail(CHX_EINVAL, "p_max_kw must be > 0");
+        if (!(p->eta_port[t] > 0.f && p->eta_port[t] <= 1.f)) return fail(CHX_EINVAL, "eta_port must be in (0,1]");
+        if (p->rbar_kw[t][0] < 0.f || p->rbar_kw[t][1] < p->rbar_kw[t][0]) return fail(CHX_EINVAL, "rbar range invalid");
+    }
+    if (x->n_days < 1 || !x->h_price) return fail(CHX_EINVAL, "price bank missing");
+    if (x->n_arrival_classes < 1 || !x->h_arrival_rate) return fail(CHX_EINVAL, "arrival table missing");
+    const size_t nl = (size_t)x->n_arrival_classes * (size_t)p->ep_len;
+    for (size_t i = 0; i < nl; ++i) {
+        const float l = x->h_arrival_rate[i];
+        if (!(l >= 0.f && l <= 64.f)) return fail(CHX_EINVAL, "arrival rates must be in [0, 64]");
+    }
+    long long go = 0, po = 0;
+    for (int e = 0; e < st->n_envs; ++e) {
+        const int n = st->h_n_ports[e], G = st->h_n_groups[e];
+        if (n < 1 || n > CHX_MAX_PORTS) return fail(CHX_EINVAL, "station " + std::to_string(e) + ": n_ports out of 1..128");
+        if (G < 1 || G > std::min(n, CHX_MAX_GROUPS))
+            return fail(CHX_EINVAL, "station " + std::to_string(e) + ": n_groups out of 1..min(n_ports,32)");
+        long long sum = 0;
+        for (int k = 0; k < G; ++k) {
+            const int gs = st->h_group_size[go + k];
+            if (gs < 1) return fail(CHX_EINVAL, "station " + std::to_string(e) + ": empty group");
+            sum += gs;
+            const float L = st->h_group_limit_kw[go + k];
+            if (!(L > 0.f)) return fail(CHX_EINVAL, "station " + std::to_string(e) + ": group limit must be > 0");
+            if (st->h_group_eta) {
+                const float eta = st->h_group_eta[go + k];
+                if (!(eta > 0.f && eta <= 1.f)) return fail(CHX_EINVAL, "group eta must be in (0,1]");
+            }
+        }
+        if (sum != n) return fail(CHX_EINVAL, "station " + std::to_string(e) + ": group sizes do not cover the chargers");
+        if (!(st->h_grid_limit_kw[e] > 0.f)) return fail(CHX_EINVAL, "grid limit must be > 0");
+        if (st->h_grid_eta && !(st->h_grid_eta[e] > 0.f && st->h_grid_eta[e] <= 1.f))
+            return fail(CHX_EINVAL, "grid eta must be in (0,1]");
+        if (st->h_arrival_class[e] < 0 || st->h_arrival_class[e] >= x->n_arrival_classes)
+            return fail(CHX_EINVAL, "arrival_class out of range");
+        for (int q = 0; q < n; ++q)
+            if (st->h_port_type[po + q] > 1) return fail(CHX_EINVAL, "port_type must be 0 or 1");
+        go += G;
+        po += n;
+    }
+    return CHX_OK;
+}
+
+DevParams make_params(const chx_env_params& q, int n_days)
+{
+    DevParams p{};
+    p.ep_len = q.ep_len;
+    p.n_levels = q.n_levels;
+    p.n_days = n_days;
+    p.dt = q.dt_h;
+    p.inv_dt = (float)(1.0 / (double)q.dt_h);
+    p.tau = q.tau;
+    p.inv_1m_tau = (float)(1.0 / (1.0 - (double)q.tau));
+    p.p_sell = q.p_sell;
+    p.c_fixed = q.c_fixed;
+    p.a_sat = q.alpha_sat;
+    p.a_decl = q.alpha_decl;
+    p.a_con = q.alpha_con;
+    p.soc_target = q.soc_target;
+    p.pmax0 = q.p_max_kw[0];
+    p.pmax1 = q.p_max_kw[1];
+    p.lvl0 = (float)((double)q.p_max_kw[0] / (double)(q.n_levels - 1));
+    p.lvl1 = (float)((double)q.p_max_kw[1] / (double)(q.n_levels - 1));
+    p.inv_eta0 = (float)(1.0 / (double)q.eta_port[0]);
+    p.inv_eta1 = (float)(1.0 / (double)q.eta_port[1]);
+    p.cap_lo = q.cap_kwh[0];
+    p.cap_span = q.cap_kwh[1] - q.cap_kwh[0];
+    p.soc_lo = q.soc0[0];
+    p.soc_span = q.soc0[1] - q.soc0[0];
+    p.stay_lo = q.stay_steps[0];
+    p.stay_span = (uint32_t)(q.stay_steps[1] - q.stay_steps[0] + 1);
+    p.rb_lo0 = q.rbar_kw[0][0];
+    p.rb_span0 = q.rbar_kw[0][1] - q.rbar_kw[0][0];
+    p.rb_lo1 = q.rbar_kw[1][0];
+    p.rb_span1 = q.rbar_kw[1][1] - q.rbar_kw[1][0];
+    p.obs_inv_stay = (float)(1.0 / (double)q.stay_steps[1]);
+    p.obs_inv_cap = (float)(1.0 / (double)q.cap_kwh[1]);
+    p.obs_inv_days = (float)(1.0 / (double)n_days);
+    p.obs_inv_len = (float)(1.0 / (double)q.ep_len);
+    return p;
+}
+
+}  // namespace
+
+// ===========================================================================
+// lifetime
+// ===========================================================================
+
+extern "C" const char* chx_last_error(void) { return chx::g_last_error.c_str(); }
+
+namespace chx {
+
+int build_handle(const chx_stations* st, const chx_env_params* prm, const chx_exo* exo, uint64_t seed,
+                 int min_pad_envs_per_class, chx_handle** out)
+{
+    int rc = validate(st, prm, exo);
+    if (rc) return rc;
+    auto* h = new chx_handle();
+    h->params = *prm;
+    h->E = st->n_envs;
+    h->n_days = exo->n_days;
+    h->n_arrival_classes = exo->n_arrival_classes;
+    CUDA_TRY(cudaGetDevice(&h->device));
+    CUDA_TRY(cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device));
+
+    // ---- classes and slot layout
+    const int E = h->E;
+    std::vector<int> cls(E);
+    h->user_port_off.assign(E + 1, 0);
+    std::vector<long long> group_off(E + 1, 0);
+    for (int e = 0; e < E; ++e) {
+        cls[e] = class_of_ports(st->h_n_ports[e]);
+        h->user_port_off[e + 1] = h->user_port_off[e] + st->h_n_ports[e];
+        group_off[e + 1] = group_off[e] + st->h_n_groups[e];
+    }
+    h->P = h->user_port_off[E];
+    int count[kNumClasses] = {0, 0, 0, 0, 0};
+    for (int e = 0; e < E; ++e) count[cls[e]]++;
+    int env_base = 0;
+    long long port_base = 0;
+    for (int c = 0; c < kNumClasses; ++c) {
+        const int C = 8 << c;
+        const int epw = C >= 32 ? 1 : 32 / C;
+        int padded = (count[c] + epw - 1) / epw * epw;
+        if (padded < min_pad_envs_per_class && count[c] > 0) padded = min_pad_envs_per_class;
+        h->cls_n_env[c] = padded;
+        h->cls_n_real[c] = count[c];
+        h->cls_env_base[c] = env_base;
+        h->cls_port_base[c] = port_base;
+        env_base += padded;
+        port_base += (long long)padded * C;
+    }
+    h->n_slots = env_base;
+    h->n_port_slots = port_base;
+    h->user_to_slot.assign(E, -1);
+    h->slot_user.assign(h->n_slots, -1);
+    {
+        int fill[kNumClasses] = {0, 0, 0, 0, 0};
+        for (int e = 0; e < E; ++e) {
+            const int c = cls[e];
+            const int s = h->cls_env_base[c] + fill[c]++;
+            h->user_to_slot[e] = s;
+            h->slot_user[s] = e;
+        }
+    }
+
+    // ---- host images of the static arrays
+    const long long PS = h->n_port_slots;
+    const int NS = h->n_slots;
+    std::vector<uint32_t> meta(PS, 0);
+    std::vector<float> gcap(PS, 0.f), ginv(PS, 0.f);
+    std::vector<int32_t> s_uid(NS, -1), s_uoff(NS, 0), s_n(NS, 0), s_arr(NS, 0);
+    std::vector<float> s_gcap(NS, 0.f), s_ginv(NS, 0.f);
+    h->slot_port_base.assign(NS, 0);
+    for (int s = 0; s < NS; ++s) {
+        int c = 0;
+        for (int i = 1; i < kNumClasses; ++i)
+            if (s >= h->cls_env_base[i]) c = i;
+        h->slot_port_base[s] = h->cls_port_base[c] + (long long)(s - h->cls_env_base[c]) * (8 << c);
+    }
+    for (int e = 0; e < E; ++e) {
+        const int s = h->user_to_slot[e];
+        const long long pb = h->slot_port_base[s];
+        const int n = st->h_n_ports[e];
+        s_uid[s] = e;
+        s_uoff[s] = (int32_t)h->user_port_off[e];
+        s_n[s] = n;
+        s_arr[s] = st->h_arrival_class[e];
+        const double eta0 = st->h_grid_eta ? st->h_grid_eta[e] : 1.0;
+        s_gcap[s] = (float)(eta0 * (double)st->h_grid_limit_kw[e]);
+        s_ginv[s] = (float)(1.0 / eta0);
+        int q = 0;
+        for (int k = 0; k < st->h_n_groups[e]; ++k) {
+            const long long gi = group_off[e] + k;
+            const int gs = st->h_group_size[gi];
+            const double eta = st->h_group_eta ? st->h_group_eta[gi] : 1.0;
+            const float cap = (float)(eta * (double)st->h_group_limit_kw[gi]);
+            const float inv = (float)(1.0 / eta);
+            for (int r = 0; r < gs; ++r, ++q) {
+                uint32_t m = kMetaValid | (uint32_t)k << kMetaGroupShift;
+                if (st->h_port_type[h->user_port_off[e] + q]) m |= kMetaDC;
+                if (r == 0) m |= kMetaHead;
+                if (r == gs - 1) m |= kMetaTail;
+                meta[pb + q] = m;
+                gcap[pb + q] = cap;
+                ginv[pb + q] = inv;
+            }
+        }
+    }
+
+    // ---- device arrays
+    DevBatch& b = h->b;
+    Buffers& B = h->bufs;
+#define ALLOC(ptr, n) \
+    if ((rc = dalloc(B, &(ptr), (n)))) { chx_destroy(h); return rc; }
+    ALLOC(b.soc, PS) ALLOC(b.erem, PS) ALLOC(b.cap, PS) ALLOC(b.rbar, PS) ALLOC(b.pw, PS)
+    ALLOC(b.trem, PS) ALLOC(b.meta, PS) ALLOC(b.gcap, PS) ALLOC(b.ginv_eta, PS)
+    ALLOC(b.user_id, NS) ALLOC(b.user_port_off, NS) ALLOC(b.n_ports, NS) ALLOC(b.arrival_class, NS)
+    ALLOC(b.grid_cap, NS) ALLOC(b.grid_inv_eta, NS) ALLOC(b.tod, NS) ALLOC(b.day, NS) ALLOC(b.gstep, NS)
+    ALLOC(b.key0, NS) ALLOC(b.key1, NS) ALLOC(b.ep_ret, NS) ALLOC(b.last_ret, NS) ALLOC(b.n_episodes, NS)
+    ALLOC(b.st_arrived, NS) ALLOC(b.st_rejected, NS) ALLOC(b.st_missing, NS) ALLOC(b.st_charged, NS)
+    ALLOC(h->d_user_to_slot, E) ALLOC(h->d_counter, 64) ALLOC(b.err, 1)
+    const size_t nprice = (size_t)exo->n_days * prm->ep_len, nlam = (size_t)exo->n_arrival_classes * prm->ep_len;
+    float *price = nullptr, *lam = nullptr, *elam = nullptr;
+    ALLOC(price, nprice) ALLOC(lam, nlam) ALLOC(elam, nlam)
+#undef ALLOC
+    b.price = price;
+    b.lam = lam;
+    b.exp_neg_lam = elam;
+    std::vector<float> e0(nlam);
+    for (size_t i = 0; i < nlam; ++i) e0[i] = (float)std::exp(-(double)exo->h_arrival_rate[i]);
+    CUDA_TRY(cudaMemcpy(price, exo->h_price, nprice * sizeof(float), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(lam, exo->h_arrival_rate, nlam * sizeof(float), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(elam, e0.data(), nlam * sizeof(float), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(b.meta, meta.data(), PS * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(b.gcap, gcap.data(), PS * sizeof(float), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(b.ginv_eta, ginv.data(), PS * sizeof(float), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(b.user_id, s_uid.data(), NS * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(b.user_port_off, s_uoff.data(), NS * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(b.n_ports, s_n.data(), NS * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(b.arrival_class, s_arr.data(), NS * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(b.grid_cap, s_gcap.data(), NS * sizeof(float), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(b.grid_inv_eta, s_ginv.data(), NS * sizeof(float), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(h->d_user_to_slot, h->user_to_slot.data(), E * sizeof(int32_t), cudaMemcpyHostToDevice));
+    for (int c = 0; c < kNumClasses; ++c) {
+        b.cls_n_env[c] = h->cls_n_env[c];
+        b.cls_env_base[c] = h->cls_env_base[c];
+        b.cls_port_base[c] = h->cls_port_base[c];
+    }
+    b.n_slots = NS;
+    h->dp = make_params(*prm, exo->n_days);
+
+    // fused schedule: largest class first
+    h->sched.n_sched = 0;
+    int tb = 0;
+    for (int c = kNumClasses - 1; c >= 0; --c) {
+        if (h->cls_n_env[c] == 0) continue;
+        const int C = 8 << c;
+        const int epw = C >= 32 ? 1 : 32 / C;
+        h->sched.sched_cls[h->sched.n_sched] = c;
+        h->sched.sched_tile_base[h->sched.n_sched] = tb;
+        h->sched.n_sched++;
+        tb += h->cls_n_env[c] / epw;
+    }
+    h->sched.sched_tile_base[h->sched.n_sched] = tb;
+    h->sched.total_tiles = tb;
+    h->sched.counter = h->d_counter;
+    h->warps_per_block = 8;
+    h->steps_per_launch = 32;
+    CUDA_TRY(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+
+    launch_reset(b, h->dp, h->d_user_to_slot, nullptr, E, seed, 0);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaDeviceSynchronize());
+    *out = h;
+    return CHX_OK;
+}
+
+void free_graph(chx_handle* h)
+{
+    if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    h->graph_exec = nullptr;
+    h->graph = nullptr;
+    h->graph_key = GraphKey{};
+}
+
+}  // namespace chx
+
+extern "C" int chx_create(const chx_stations* st, const chx_env_params* params, const chx_exo* exo, uint64_t seed,
+                          chx_handle** out)
+{
+    if (!out) return fail(CHX_EINVAL, "out is null");
+    *out = nullptr;
+    return build_handle(st, params, exo, seed, 0, out);
+}
+
+extern "C" int chx_destroy(chx_handle* h)
+{
+    if (!h) return CHX_OK;
+    free_graph(h);
+    for (void* p : h->bufs) cudaFree(p);
+    for (void* p : h->staging) cudaFree(p);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    delete h;
+    return CHX_OK;
+}
+
+extern "C" int chx_n_envs(const chx_handle* h, int32_t* out)
+{
+    if (!h || !out) return fail(CHX_EINVAL, "null argument");
+    *out = h->E;
+    return CHX_OK;
+}
+
+extern "C" int chx_n_ports_total(const chx_handle* h, int64_t* out)
+{
+    if (!h || !out) return fail(CHX_EINVAL, "null argument");
+    *out = h->P;
+    return CHX_OK;
+}
+
+extern "C" int chx_port_offsets(const chx_handle* h, int64_t* h_offsets)
+{
+    if (!h || !h_offsets) return fail(CHX_EINVAL, "null argument");
+    for (int e = 0; e <= h->E; ++e) h_offsets[e] = h->user_port_off[e];
+    return CHX_OK;
+}
+
+extern "C" int chx_obs_size(const chx_handle* h, int64_t* out)
+{
+    if (!h || !out) return fail(CHX_EINVAL, "null argument");
+    *out = 8LL * h->E + 6LL * h->P;
+    return CHX_OK;
+}
+
+// ===========================================================================
+// reset / step / observe
+// ===========================================================================
+
+extern "C" int chx_reset(chx_handle* h, const int32_t* d_env_ids, int32_t n, uint64_t seed, void* stream)
+{
+    if (!h) return fail(CHX_EINVAL, "null handle");
+    if (n < 0) return fail(CHX_EINVAL, "n < 0");
+    const int count = d_env_ids ? n : h->E;
+    launch_reset(h->b, h->dp, h->d_user_to_slot, d_env_ids, count, seed, (cudaStream_t)stream);
+    CUDA_TRY(cudaGetLastError());
+    return CHX_OK;
+}
+
+extern "C" int chx_step(chx_handle* h, const int8_t* d_actions, int64_t lda, float* d_reward, uint8_t* d_done,
+                        void* stream)
+{
+    if (!h) return fail(CHX_EINVAL, "null handle");
+    if (d_actions && lda < 1) return fail(CHX_EINVAL, "lda must be >= 1");
+    launch_step_plain(h->b, h->dp, d_actions, lda, d_reward, d_done, nullptr, 0, (cudaStream_t)stream);
+    CUDA_TRY(cudaGetLastError());
+    return CHX_OK;
+}
+
+namespace chx {
+
+int enqueue_fused(chx_handle* h, int k_steps, const int8_t* actions, long long lda, float* reward, uint8_t* done,
+                  long long ld_out, float* obs, int warps, cudaStream_t st)
+{
+    FusedIO io = h->sched;
+    io.k_steps = k_steps;
+    io.actions = actions;
+    io.lda = lda;
+    io.reward = reward;
+    io.done = done;
+    io.ld_out = ld_out;
+    io.obs = obs;
+    const int threads = warps * 32;
+    const int per_sm = fused_max_blocks_per_sm(threads);
+    if (per_sm <= 0) return fail(CHX_ECUDA, "fused kernel cannot be resident with this block size");
+    const int tiles_blocks = (io.total_tiles + warps - 1) / warps;
+    const int blocks = std::max(1, std::min(per_sm * h->sm_count, tiles_blocks));
+    CUDA_TRY(cudaMemsetAsync(h->d_counter, 0, sizeof(int), st));
+    launch_step_fused(h->b, h->dp, io, blocks, threads, st);
+    CUDA_TRY(cudaGetLastError());
+    return CHX_OK;
+}
+
+}  // namespace chx
+
+extern "C" int chx_step_n(chx_handle* h, int32_t k_steps, const int8_t* d_actions, int64_t lda, float* d_reward,
+                          uint8_t* d_done, int64_t ld_out, float* d_obs, void* stream)
+{
+    if (!h) return fail(CHX_EINVAL, "null handle");
+    if (k_steps < 1) return fail(CHX_EINVAL, "k_steps must be >= 1");
+    if (d_actions && lda < k_steps) return fail(CHX_EINVAL, "lda must be >= k_steps");
+    if ((d_reward || d_done) && ld_out < k_steps) return fail(CHX_EINVAL, "ld_out must be >= k_steps");
+    return enqueue_fused(h, k_steps, d_actions, lda, d_reward, d_done, ld_out, d_obs, h->warps_per_block,
+                         (cudaStream_t)stream);
+}
+
+extern "C" int chx_observe(chx_handle* h, float* d_obs, void* stream)
+{
+    if (!h || !d_obs) return fail(CHX_EINVAL, "null argument");
+    launch_observe(h->b, h->dp, d_obs, (cudaStream_t)stream);
+    CUDA_TRY(cudaGetLastError());
+    return CHX_OK;
+}
+
+// ===========================================================================
+// rollout (CUDA graph) and autotuning
+// ===========================================================================
+
+namespace chx {
+
+int build_rollout_graph(chx_handle* h, int n_steps, float* reward, uint8_t* done, float* obs)
+{
+    free_graph(h);
+    cudaStream_t cs = h->cap_stream;
+    CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    int rc = CHX_OK;
+    const int K = h->steps_per_launch;
+    for (int k0 = 0; k0 < n_steps && rc == CHX_OK; k0 += K) {
+        const int k = std::min(K, n_steps - k0);
+        const bool last = k0 + k >= n_steps;
+        rc = enqueue_fused(h, k, nullptr, 0, reward ? reward + k0 : nullptr, done ? done + k0 : nullptr, n_steps,
+                           last ? obs : nullptr, h->warps_per_block, cs);
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs, &g);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    h->graph = g;
+    e = cudaGraphInstantiate(&h->graph_exec, g, 0);
+    if (e != cudaSuccess) {
+        free_graph(h);
+        return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    h->graph_key = GraphKey{n_steps, reward, done, obs, h->steps_per_launch, h->warps_per_block, true};
+    return CHX_OK;
+}
+
+int rollout(chx_handle* h, int n_steps, float* reward, uint8_t* done, float* obs, cudaStream_t st)
+{
+    const GraphKey want{n_steps, reward, done, obs, h->steps_per_launch, h->warps_per_block, true};
+    if (!(h->graph_key == want)) {
+        int rc = build_rollout_graph(h, n_steps, reward, done, obs);
+        if (rc) return rc;
+    }
+    CUDA_TRY(cudaGraphLaunch(h->graph_exec, st));
+    return CHX_OK;
+}
+
+void* staging(chx_handle* h, int slot, size_t bytes)
+{
+    if (h->staging_bytes[slot] < bytes) {
+        if (h->staging[slot]) cudaFree(h->staging[slot]);
+        h->staging[slot] = nullptr;
+        h->staging_bytes[slot] = 0;
+        void* p = nullptr;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+        h->staging[slot] = p;
+        h->staging_bytes[slot] = bytes;
+    }
+    return h->staging[slot];
+}
+
+}  // namespace chx
+
+extern "C" int chx_rollout(chx_handle* h, int32_t n_steps, float* d_reward, uint8_t* d_done, float* d_obs,
+                           void* stream)
+{
+    if (!h) return fail(CHX_EINVAL, "null handle");
+    if (n_steps < 1) return fail(CHX_EINVAL, "n_steps must be >= 1");
+    return rollout(h, n_steps, d_reward, d_done, d_obs, (cudaStream_t)stream);
+}
+
+extern "C" int chx_rollout_host(chx_handle* h, int32_t n_steps, float* h_reward, uint8_t* h_done, float* h_obs,
+                                void* stream)
+{
+    if (!h) return fail(CHX_EINVAL, "null handle");
+    if (n_steps < 1) return fail(CHX_EINVAL, "n_steps must be >= 1");
+    const size_t ne = (size_t)h->E * (size_t)n_steps;
+    const size_t nobs = 8 * (size_t)h->E + 6 * (size_t)h->P;
+    float* dr = h_reward ? (float*)staging(h, 0, ne * sizeof(float)) : nullptr;
+    uint8_t* dd = h_done ? (uint8_t*)staging(h, 1, ne) : nullptr;
+    float* dob = h_obs ? (float*)staging(h, 2, nobs * sizeof(float)) : nullptr;
+    if ((h_reward && !dr) || (h_done && !dd) || (h_obs && !dob)) return fail(CHX_ENOMEM, "staging allocation failed");
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = rollout(h, n_steps, dr, dd, dob, st);
+    if (rc) return rc;
+    if (h_reward) CUDA_TRY(cudaMemcpyAsync(h_reward, dr, ne * sizeof(float), cudaMemcpyDeviceToHost, st));
+    if (h_done) CUDA_TRY(cudaMemcpyAsync(h_done, dd, ne, cudaMemcpyDeviceToHost, st));
+    if (h_obs) CUDA_TRY(cudaMemcpyAsync(h_obs, dob, nobs * sizeof(float), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return CHX_OK;
+}
+
+extern "C" int chx_step_host(chx_handle* h, const int8_t* h_actions, float* h_reward, uint8_t* h_done, float* h_obs,
+                             void* stream)
+{
+    if (!h) return fail(CHX_EINVAL, "null handle");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t nobs = 8 * (size_t)h->E + 6 * (size_t)h->P;
+    int8_t* da = h_actions ? (int8_t*)staging(h, 3, (size_t)h->P) : nullptr;
+    float* dr = h_reward ? (float*)staging(h, 4, (size_t)h->E * sizeof(float)) : nullptr;
+    uint8_t* dd = h_done ? (uint8_t*)staging(h, 5, (size_t)h->E) : nullptr;
+    float* dob = h_obs ? (float*)staging(h, 2, nobs * sizeof(float)) : nullptr;
+    if ((h_actions && !da) || (h_reward && !dr) || (h_done && !dd) || (h_obs && !dob))
+        return fail(CHX_ENOMEM, "staging allocation failed");
+    if (h_actions) CUDA_TRY(cudaMemcpyAsync(da, h_actions, (size_t)h->P, cudaMemcpyHostToDevice, st));
+    launch_step_plain(h->b, h->dp, da, 1, dr, dd, nullptr, 0, st);
+    CUDA_TRY(cudaGetLastError());
+    if (h_obs) {
+        launch_observe(h->b, h->dp, dob, st);
+        CUDA_TRY(cudaGetLastError());
+    }
+    if (h_reward) CUDA_TRY(cudaMemcpyAsync(h_reward, dr, (size_t)h->E * sizeof(float), cudaMemcpyDeviceToHost, st));
+    if (h_done) CUDA_TRY(cudaMemcpyAsync(h_done, dd, (size_t)h->E, cudaMemcpyDeviceToHost, st));
+    if (h_obs) CUDA_TRY(cudaMemcpyAsync(h_obs, dob, nobs * sizeof(float), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return CHX_OK;
+}
+
+extern "C" int chx_set_launch(chx_handle* h, int32_t steps_per_launch, int32_t warps_per_block)
+{
+    if (!h) return fail(CHX_EINVAL, "null handle");
+    if (steps_per_launch < 0 || warps_per_block < 0 || warps_per_block > 8)
+        return fail(CHX_EINVAL, "launch shape out of range");
+    if (steps_per_launch) h->steps_per_launch = steps_per_launch;
+    if (warps_per_block) h->warps_per_block = warps_per_block;
+    free_graph(h);
+    return CHX_OK;
+}
+
+namespace chx {
+
+// device-side snapshot of every mutable array, for the autotuner
+struct Snapshot {
+    std::vector<std::pair<void*, size_t>> items;
+    std::vector<void*> copies;
+};
+
+int snapshot_take(chx_handle* h, Snapshot& s)
+{
+    const DevBatch& b = h->b;
+    const size_t PS = h->n_port_slots, NS = h->n_slots;
+    s.items = {{b.soc, PS * 4}, {b.erem, PS * 4}, {b.cap, PS * 4}, {b.rbar, PS * 4}, {b.pw, PS * 4},
+               {b.trem, PS}, {b.tod, NS * 4}, {b.day, NS * 4}, {b.gstep, NS * 4}, {b.key0, NS * 4},
+               {b.key1, NS * 4}, {b.ep_ret, NS * 4}, {b.last_ret, NS * 4}, {b.n_episodes, NS * 4},
+               {b.st_arrived, NS * 4}, {b.st_rejected, NS * 4}, {b.st_missing, NS * 4}, {b.st_charged, NS * 4}};
+    for (auto& it : s.items) {
+        void* c = nullptr;
+        if (cudaMalloc(&c, it.second) != cudaSuccess) return fail(CHX_ENOMEM, "snapshot allocation failed");
+        s.copies.push_back(c);
+        CUDA_TRY(cudaMemcpy(c, it.first, it.second, cudaMemcpyDeviceToDevice));
+    }
+    return CHX_OK;
+}
+
+int snapshot_restore(Snapshot& s)
+{
+    for (size_t i = 0; i < s.copies.size(); ++i)
+        CUDA_TRY(cudaMemcpy(s.items[i].first, s.copies[i], s.items[i].second, cudaMemcpyDeviceToDevice));
+    for (void* c : s.copies) cudaFree(c);
+    s.copies.clear();
+    return CHX_OK;
+}
+
+}  // namespace chx
+
+extern "C" int chx_autotune(chx_handle* h, int32_t n_steps, int32_t* h_steps_per_launch, int32_t* h_warps_per_block)
+{
+    if (!h) return fail(CHX_EINVAL, "null handle");
+    if (n_steps < 1) return fail(CHX_EINVAL, "n_steps must be >= 1");
+    Snapshot snap;
+    int rc = snapshot_take(h, snap);
+    if (rc) return rc;
+    const size_t ne = (size_t)h->E * (size_t)n_steps;
+    float* dr = nullptr;
+    uint8_t* dd = nullptr;
+    if (cudaMalloc(&dr, ne * sizeof(float)) != cudaSuccess || cudaMalloc(&dd, ne) != cudaSuccess) {
+        cudaFree(dr);
+        snapshot_restore(snap);
+        return fail(CHX_ENOMEM, "autotune output allocation failed");
+    }
+    cudaStream_t st = h->cap_stream;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int ks[] = {4, 8, 16, 32, 48, 72, 96, 144, 288};
+    const int ws[] = {2, 4, 8};
+    float best = 1e30f;
+    int best_k = h->steps_per_launch, best_w = h->warps_per_block;
+    const int old_k = h->steps_per_launch, old_w = h->warps_per_block;
+    for (int w : ws) {
+        if (fused_max_blocks_per_sm(w * 32) <= 0) continue;
+        for (int k : ks) {
+            if (k > n_steps && k != ks[0]) continue;
+            h->steps_per_launch = k;
+            h->warps_per_block = w;
+            rc = rollout(h, n_steps, dr, dd, nullptr, st);   // capture + warm-up
+            if (rc) break;
+            float ms_best = 1e30f;
+            for (int rep = 0; rep < 3; ++rep) {
+                cudaEventRecord(e0, st);
+                rollout(h, n_steps, dr, dd, nullptr, st);
+                cudaEventRecord(e1, st);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                ms_best = std::min(ms_best, ms);
+            }
+            if (ms_best < best) {
+                best = ms_best;
+                best_k = k;
+                best_w = w;
+            }
+        }
+        if (rc) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamSynchronize(st);
+    cudaFree(dr);
+    cudaFree(dd);
+    free_graph(h);
+    int rc2 = snapshot_restore(snap);
+    if (rc) {
+        h->steps_per_launch = old_k;
+        h->warps_per_block = old_w;
+        return rc;
+    }
+    if (rc2) return rc2;
+    h->steps_per_launch = best_k;
+    h->warps_per_block = best_w;
+    h->tuned_ms = best;
+    if (h_steps_per_launch) *h_steps_per_launch = best_k;
+    if (h_warps_per_block) *h_warps_per_block = best_w;
+    return CHX_OK;
+}
+
+// ===========================================================================
+// state, statistics, checkpoints
+// ===========================================================================
+
+namespace {
+
+template <class T>
+int fetch(std::vector<T>& v, const T* d, size_t n)
+{
+    v.resize(n);
+    CUDA_TRY(cudaMemcpy(v.data(), d, n * sizeof(T), cudaMemcpyDeviceToHost));
+    return CHX_OK;
+}
+template <class T>
+int push(T* d, const std::vector<T>& v)
+{
+    CUDA_TRY(cudaMemcpy(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return CHX_OK;
+}
+
+// per-charger field: slot array <-> batch-order array
+template <class T>
+int get_port_field(chx_handle* h, T* out, const T* d)
+{
+    if (!out) return CHX_OK;
+    std::vector<T> v;
+    int rc = fetch(v, d, (size_t)h->n_port_slots);
+    if (rc) return rc;
+    for (int e = 0; e < h->E; ++e) {
+        const long long pb = h->slot_port_base[h->user_to_slot[e]];
+        const long long n = h->user_port_off[e + 1] - h->user_port_off[e];
+        std::memcpy(out + h->user_port_off[e], v.data() + pb, n * sizeof(T));
+    }
+    return CHX_OK;
+}
+template <class T>
+int set_port_field(chx_handle* h, const T* in, T* d)
+{
+    if (!in) return CHX_OK;
+    std::vector<T> v;
+    int rc = fetch(v, d, (size_t)h->n_port_slots);
+    if (rc) return rc;
+    for (int e = 0; e < h->E; ++e) {
+        const long long pb = h->slot_port_base[h->user_to_slot[e]];
+        const long long n = h->user_port_off[e + 1] - h->user_port_off[e];
+        std::memcpy(v.data() + pb, in + h->user_port_off[e], n * sizeof(T));
+    }
+    return push(d, v);
+}
+template <class T>
+int get_env_field(chx_handle* h, T* out, const T* d)
+{
+    if (!out) return CHX_OK;
+    std::vector<T> v;
+    int rc = fetch(v, d, (size_t)h->n_slots);
+    if (rc) return rc;
+    for (int e = 0; e < h->E; ++e) out[e] = v[h->user_to_slot[e]];
+    return CHX_OK;
+}
+template <class T>
+int set_env_field(chx_handle* h, const T* in, T* d)
+{
+    if (!in) return CHX_OK;
+    std::vector<T> v;
+    int rc = fetch(v, d, (size_t)h->n_slots);
+    if (rc) return rc;
+    for (int e = 0; e < h->E; ++e) v[h->user_to_slot[e]] = in[e];
+    return push(d, v);
+}
+
+}  // namespace
+
+#define RC(x)                  \
+    do {                       \
+        int _r = (x);          \
+        if (_r) return _r;     \
+    } while (0)
+
+extern "C" int chx_get_state(chx_handle* h, float* h_soc, float* h_erem, float* h_cap, float* h_rbar, float* h_p,
+                             uint8_t* h_trem, int32_t* h_tod, int32_t* h_day, uint32_t* h_gstep, uint32_t* h_key0,
+                             uint32_t* h_key1, float* h_ep_ret)
+{
+    if (!h) return fail(CHX_EINVAL, "null handle");
+    CUDA_TRY(cudaDeviceSynchronize());
+    const DevBatch& b = h->b;
+    RC(get_port_field(h, h_soc, b.soc));
+    RC(get_port_field(h, h_erem, b.erem));
+    RC(get_port_field(h, h_cap, b.cap));
+    RC(get_port_field(h, h_rbar, b.rbar));
+    RC(get_port_field(h, h_p, b.pw));
+    RC(get_port_field(h, h_trem, (const uint8_t*)b.trem));
+    RC(get_env_field(h, h_tod, (const int32_t*)b.tod));
+    RC(get_env_field(h, h_day, (const int32_t*)b.day));
+    RC(get_env_field(h, h_gstep, (const uint32_t*)b.gstep));
+    RC(get_env_field(h, h_key0, (const uint32_t*)b.key0));
+    RC(get_env_field(h, h_key1, (const uint32_t*)b.key1));
+    RC(get_env_field(h, h_ep_ret, (const float*)b.ep_ret));
+    return CHX_OK;
+}
+
+extern "C" int chx_set_state(chx_handle* h, const float* h_soc, const float* h_erem, const float* h_cap,
+                             const float* h_rbar, const float* h_p, const uint8_t* h_trem, const int32_t* h_tod,
+                             const int32_t* h_day, const uint32_t* h_gstep, const uint32_t* h_key0,
+                             const uint32_t* h_key1, const float* h_ep_ret)
+{
+    if (!h) return fail(CHX_EINVAL, "null handle");
+    if (h_tod)
+        for (int e = 0; e < h->E; ++e)
+            if (h_tod[e] < 0 || h_tod[e] >= h->params.ep_len) return fail(CHX_EINVAL, "step of day out of range");
+    if (h_day)
+        for (int e = 0; e < h->E; ++e)
+            if (h_day[e] < 0 || h_day[e] >= h->n_days) return fail(CHX_EINVAL, "day out of range");
+    CUDA_TRY(cudaDeviceSynchronize());
+    DevBatch& b = h->b;
+    RC(set_port_field(h, h_soc, b.soc));
+    RC(set_port_field(h, h_erem, b.erem));
+    RC(set_port_field(h, h_cap, b.cap));
+    RC(set_port_field(h, h_rbar, b.rbar));
+    RC(set_port_field(h, h_p, b.pw));
+    RC(set_port_field(h, h_trem, b.trem));
+    RC(set_env_field(h, h_tod, b.tod));
+    RC(set_env_field(h, h_day, b.day));
+    RC(set_env_field(h, h_gstep, b.gstep));
+    RC(set_env_field(h, h_key0, b.key0));
+    RC(set_env_field(h, h_key1, b.key1));
+    RC(set_env_field(h, h_ep_ret, b.ep_ret));
+    return CHX_OK;
+}
+
+extern "C" int chx_stats(chx_handle* h, uint32_t* h_arrived, uint32_t* h_rejected, float* h_missing_kwh,
+                         float* h_charged_kwh, uint32_t* h_episodes, float* h_last_return)
+{
+    if (!h) return fail(CHX_EINVAL, "null handle");
+    CUDA_TRY(cudaDeviceSynchronize());
+    const DevBatch& b = h->b;
+    RC(get_env_field(h, h_arrived, (const uint32_t*)b.st_arrived));
+    RC(get_env_field(h, h_rejected, (const uint32_t*)b.st_rejected));
+    RC(get_env_field(h, h_missing_kwh, (const float*)b.st_missing));
+    RC(get_env_field(h, h_charged_kwh, (const float*)b.st_charged));
+    RC(get_env_field(h, h_episodes, (const uint32_t*)b.n_episodes));
+    RC(get_env_field(h, h_last_return, (const float*)b.last_ret));
+    return CHX_OK;
+}
+
+namespace {
+constexpr uint64_t kCkptMagic = 0x43484158434B5031ull;   // "CHAXCKP1"
+struct CkptHeader {
+    uint64_t magic;
+    int64_t n_envs, n_ports;
+};
+size_t ckpt_size(const chx_handle* h)
+{
+    return sizeof(CkptHeader) + (size_t)h->P * (5 * 4 + 1) + (size_t)h->E * (6 * 4 + 6 * 4);
+}
+}  // namespace
+
+extern "C" int chx_save(chx_handle* h, void* h_buf, size_t* size)
+{
+    if (!h || !size) return fail(CHX_EINVAL, "null argument");
+    const size_t need = ckpt_size(h);
+    if (!h_buf) {
+        *size = need;
+        return CHX_OK;
+    }
+    if (*size < need) return fail(CHX_EINVAL, "checkpoint buffer too small");
+    const size_t P = h->P, E = h->E;
+    char* w = static_cast<char*>(h_buf);
+    CkptHeader hd{kCkptMagic, (int64_t)E, (int64_t)P};
+    std::memcpy(w, &hd, sizeof hd);
+    w += sizeof hd;
+    float* f = reinterpret_cast<float*>(w);
+    float *soc = f, *erem = f + P, *cap = f + 2 * P, *rbar = f + 3 * P, *pw = f + 4 * P;
+    uint8_t* trem = reinterpret_cast<uint8_t*>(f + 5 * P);
+    char* env = reinterpret_cast<char*>(trem + P);
+    int32_t* tod = reinterpret_cast<int32_t*>(env);
+    int32_t* day = tod + E;
+    uint32_t* gstep = reinterpret_cast<uint32_t*>(day + E);
+    uint32_t *key0 = gstep + E, *key1 = key0 + E;
+    float* ret = reinterpret_cast<float*>(key1 + E);
+    uint32_t* arrived = reinterpret_cast<uint32_t*>(ret + E);
+    uint32_t* rejected = arrived + E;
+    float* missing = reinterpret_cast<float*>(rejected + E);
+    float* charged = missing + E;
+    uint32_t* episodes = reinterpret_cast<uint32_t*>(charged + E);
+    float* last = reinterpret_cast<float*>(episodes + E);
+    RC(chx_get_state(h, soc, erem, cap, rbar, pw, trem, tod, day, gstep, key0, key1, ret));
+    RC(chx_stats(h, arrived, rejected, missing, charged, episodes, last));
+    *size = need;
+    return CHX_OK;
+}
+
+extern "C" int chx_load(chx_handle* h, const void* h_buf, size_t size)
+{
+    if (!h || !h_buf) return fail(CHX_EINVAL, "null argument");
+    if (size < ckpt_size(h)) return fail(CHX_EINVAL, "checkpoint too small");
+    CkptHeader hd;
+    std::memcpy(&hd, h_buf, sizeof hd);
+    if (hd.magic != kCkptMagic || hd.n_envs != h->E || hd.n_ports != h->P)
+        return fail(CHX_EINVAL, "checkpoint does not match this batch");
+    const size_t P = h->P, E = h->E;
+    const char* r = static_cast<const char*>(h_buf) + sizeof hd;
+    const float* f = reinterpret_cast<const float*>(r);
+    const uint8_t* trem = reinterpret_cast<const uint8_t*>(f + 5 * P);
+    const char* env = reinterpret_cast<const char*>(trem + P);
+    const int32_t* tod = reinterpret_cast<const int32_t*>(env);
+    const int32_t* day = tod + E;
+    const uint32_t* gstep = reinterpret_cast<const uint32_t*>(day + E);
+    const uint32_t *key0 = gstep + E, *key1 = key0 + E;
+    const float* ret = reinterpret_cast<const float*>(key1 + E);
+    const uint32_t* arrived = reinterpret_cast<const uint32_t*>(ret + E);
+    const uint32_t* rejected = arrived + E;
+    const float* missing = reinterpret_cast<const float*>(rejected + E);
+    const float* charged = missing + E;
+    const uint32_t* episodes = reinterpret_cast<const uint32_t*>(charged + E);
+    const float* last = reinterpret_cast<const float*>(episodes + E);
+    RC(chx_set_state(h, f, f + P, f + 2 * P, f + 3 * P, f + 4 * P, trem, tod, day, gstep, key0, key1, ret));
+    DevBatch& b = h->b;
+    RC(set_env_field(h, arrived, b.st_arrived));
+    RC(set_env_field(h, rejected, b.st_rejected));
+    RC(set_env_field(h, missing, b.st_missing));
+    RC(set_env_field(h, charged, b.st_charged));
+    RC(set_env_field(h, episodes, b.n_episodes));
+    RC(set_env_field(h, last, b.last_ret));
+    return CHX_OK;
+}
+
+extern "C" int chx_check(chx_handle* h, void* stream)
+{
+    if (!h) return fail(CHX_EINVAL, "null handle");
+    CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    uint32_t err = 0;
+    CUDA_TRY(cudaMemcpy(&err, h->b.err, sizeof err, cudaMemcpyDeviceToHost));
+    if (err) {
+        CUDA_TRY(cudaMemset(h->b.err, 0, sizeof(uint32_t)));
+        return fail(CHX_EFAULT, "a kernel saw an action level outside 0..n_levels-1 (clamped)");
+    }
+    return CHX_OK;
+}

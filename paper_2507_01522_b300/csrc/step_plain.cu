@@ -1,0 +1,163 @@
+// step_plain.cu -- the plain form of the step: one thread per station, one
+// launch per step, all state read from and written back to HBM.
+//
+// It is the baseline the fused kernel is measured against and a second,
+// structurally different CUDA implementation of the same transition
+// (sequential per-station sums instead of warp reductions).
+#include "chx_device.cuh"
+#include "chx_kernels.h"
+
+namespace chx {
+
+__global__ void __launch_bounds__(128) k_step_plain(DevBatch b, DevParams p, const int8_t* __restrict__ actions,
+                                                    long long lda, float* __restrict__ reward,
+                                                    uint8_t* __restrict__ done, const int* __restrict__ slot_list,
+                                                    int n_list)
+{
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (slot_list ? n_list : b.n_slots)) return;
+    const int s = slot_list ? slot_list[idx] : idx;
+    const int uid = b.user_id[s];
+    if (uid < 0) return;
+    const int c = class_of_slot(b, s);
+    const int C = 8 << c;
+    const long long pb = b.cls_port_base[c] + (long long)(s - b.cls_env_base[c]) * C;
+    const int n = b.n_ports[s];
+    const uint32_t g = b.gstep[s];
+    const int t = b.tod[s];
+    const uint32_t k0 = b.key0[s], k1 = b.key1[s];
+    const long long uoff = b.user_port_off[s];
+
+    // -- (i) apply actions: per-charger clip, then group sums (Eq. ArchConst)
+    float gscale[32];
+    float S = 0.f, Se = 0.f, s_raw = 0.f, s_grp = 0.f, se_grp = 0.f, over_max = 0.f;
+    for (int q = 0; q < n; ++q) {
+        const long long i = pb + q;
+        const uint32_t m = b.meta[i];
+        const bool dc = m & kMetaDC;
+        float P = 0.f;
+        if (b.trem[i] > 0) {
+            int lvl;
+            if (actions) {
+                lvl = actions[(uoff + q) * lda];
+                if (lvl < 0 || lvl >= p.n_levels) {
+                    atomicOr(b.err, kErrActionRange);
+                    lvl = min(max(lvl, 0), p.n_levels - 1);
+                }
+            } else {
+                const uint4 w = philox4x32_10(make_uint4((uint32_t)uid, g >> 3, (uint32_t)q, kPurposeAction), k0, k1);
+                lvl = random_level(w, g, p.n_levels);
+            }
+            P = clip_power(lvl, dc, b.soc[i], b.erem[i], b.cap[i], b.rbar[i], p);
+        }
+        S += P;
+        Se += P * (dc ? p.inv_eta1 : p.inv_eta0);
+        s_raw += P;
+        if (m & kMetaTail) {
+            const float gc = b.gcap[i];
+            const float sc = S > gc ? gc / S : 1.0f;
+            gscale[(m >> kMetaGroupShift) & 31] = sc;
+            over_max = fmaxf(over_max, (S - gc) * b.ginv_eta[i]);
+            s_grp += S * sc;
+            se_grp += Se * sc;
+            S = 0.f;
+            Se = 0.f;
+        }
+    }
+    // root node
+    const float grid_cap = b.grid_cap[s];
+    const float s_root = s_grp > grid_cap ? grid_cap / s_grp : 1.0f;
+    const float c_con = fmaxf(fmaxf(over_max, (s_raw - grid_cap) * b.grid_inv_eta[s]), 0.0f);
+
+    // -- (ii) charge, time advance, (iii) departures
+    float c_sat = 0.f;
+    int n_free = 0;
+    for (int q = 0; q < n; ++q) {
+        const long long i = pb + q;
+        const uint32_t m = b.meta[i];
+        const bool dc = m & kMetaDC;
+        int tr = b.trem[i];
+        float P = 0.f;
+        if (tr > 0) {
+            int lvl;
+            if (actions) {
+                lvl = min(max((int)actions[(uoff + q) * lda], 0), p.n_levels - 1);
+            } else {
+                const uint4 w = philox4x32_10(make_uint4((uint32_t)uid, g >> 3, (uint32_t)q, kPurposeAction), k0, k1);
+                lvl = random_level(w, g, p.n_levels);
+            }
+            float soc = b.soc[i], erem = b.erem[i];
+            const float cap = b.cap[i];
+            P = clip_power(lvl, dc, soc, erem, cap, b.rbar[i], p);
+            P = P * gscale[(m >> kMetaGroupShift) & 31] * s_root;
+            const float dE = P * p.dt;
+            soc = fminf(soc + dE / cap, 1.0f);
+            erem = fmaxf(erem - dE, 0.0f);
+            tr -= 1;
+            if (tr == 0) {
+                c_sat += erem;
+                b.soc[i] = 0.f; b.erem[i] = 0.f; b.cap[i] = 0.f; b.rbar[i] = 0.f;
+            } else {
+                b.soc[i] = soc; b.erem[i] = erem;
+            }
+            b.trem[i] = (uint8_t)tr;
+        }
+        b.pw[i] = P;
+        n_free += (tr == 0);
+    }
+    const float e_net = s_grp * s_root * p.dt;
+    const float e_grid = se_grp * s_root * p.dt;
+
+    // -- (iv) arrivals: Poisson count, first come first served
+    const int M = arrivals(b, p, (uint32_t)uid, g, t, b.arrival_class[s], k0, k1);
+    const int m_adm = min(M, n_free);
+    for (int q = 0, j = 0; q < n && j < m_adm; ++q) {
+        const long long i = pb + q;
+        if (b.trem[i] != 0) continue;
+        const Car car = draw_car((uint32_t)uid, g, (uint32_t)j, k0, k1, b.meta[i] & kMetaDC, p);
+        b.cap[i] = car.cap; b.soc[i] = car.soc; b.erem[i] = car.erem; b.rbar[i] = car.rbar;
+        b.trem[i] = (uint8_t)car.stay;
+        ++j;
+    }
+
+    // -- reward, Appendix A.3 (no discharge: E_grid,net = energy bought)
+    const float price = __ldg(b.price + (size_t)b.day[s] * (size_t)p.ep_len + (size_t)t);
+    const float profit = p.p_sell * e_net - price * e_grid - p.c_fixed;
+    const float r = profit - p.a_sat * c_sat - p.a_decl * (float)(M - m_adm) - p.a_con * c_con;
+
+    b.st_arrived[s] += (uint32_t)m_adm;
+    b.st_rejected[s] += (uint32_t)(M - m_adm);
+    b.st_missing[s] += c_sat;
+    b.st_charged[s] += e_net;
+    float ret = b.ep_ret[s] + r;
+    int t1 = t + 1;
+    uint8_t fin = 0;
+    if (t1 >= p.ep_len) {
+        fin = 1;
+        b.last_ret[s] = ret;
+        ret = 0.f;
+        b.n_episodes[s] += 1u;
+        for (int q = 0; q < C; ++q) {
+            const long long i = pb + q;
+            b.soc[i] = 0.f; b.erem[i] = 0.f; b.cap[i] = 0.f; b.rbar[i] = 0.f; b.pw[i] = 0.f; b.trem[i] = 0;
+        }
+        t1 = 0;
+        b.day[s] = draw_day((uint32_t)uid, g, 0u, k0, k1, p.n_days);
+    }
+    b.ep_ret[s] = ret;
+    b.tod[s] = t1;
+    b.gstep[s] = g + 1u;
+    if (reward) reward[uid] = r;
+    if (done) done[uid] = fin;
+}
+
+void launch_step_plain(const DevBatch& b, const DevParams& p, const int8_t* actions, long long lda, float* reward,
+                       uint8_t* done, const int* slot_list, int n_list, cudaStream_t st)
+{
+    const int n = slot_list ? n_list : b.n_slots;
+    if (n <= 0) return;
+    const int threads = 128;
+    k_step_plain<<<(n + threads - 1) / threads, threads, 0, st>>>(b, p, actions, lda, reward, done, slot_list, n_list);
+}
+
+}  // namespace chx

@@ -1,0 +1,408 @@
+"""Parity of the CUDA library with the CPU oracle, through the C interface.
+
+Events bit-exact, floats within the tolerances stated in tests/parity.py.
+Workloads are small enough for the oracle (seconds) but span several warp
+tiles of every size class, ragged station counts and charger counts that are
+not powers of two; the full-size workloads are checked on sampled stations.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import Oracle
+from paper_2507_01522_b300 import inputs as I
+
+from parity import (RETURN_RTOL, STEP_RTOL, TRAJ_RTOL, assert_events_equal, assert_floats_close,
+                    assert_reward_close, reward_scale, to_f32_state, widen)
+
+pytestmark = pytest.mark.gpu
+
+
+# ----------------------------------------------------------------------------
+# workloads
+# ----------------------------------------------------------------------------
+
+def odd_sizes(n_envs=150, seed=7):
+    """Stations of 1..128 chargers including every class edge (1, 8, 9, 16,
+    17, 32, 33, 64, 65, 128), groups of 4..16, mixed AC/DC."""
+    rng = np.random.default_rng(seed)
+    edges = [1, 5, 8, 9, 13, 16, 17, 31, 32, 33, 63, 64, 65, 100, 127, 128]
+    sizes = np.array([edges[i % len(edges)] for i in range(n_envs)], np.int32)
+    rng.shuffle(sizes)
+    p = I.EnvParams(p_max_kw=(11.0, 150.0))
+    classes = sorted(set(int(s) for s in sizes))
+    st = I.mixed_stations(rng, sizes, p.p_max_kw, class_sizes=classes)
+    exo = I.Exo(I.price_bank(seed=seed), I.arrival_rates(classes))
+    return I.Workload("odd", p, st, exo, seed)
+
+
+def stressed(n_envs=96, seed=11):
+    """Every reward term on: node efficiencies below 1, constraint penalty,
+    partial charging targets, fixed cost, distinct AC/DC efficiency, a short
+    episode and heavy traffic."""
+    w = odd_sizes(n_envs, seed)
+    p = w.params
+    p.alpha_con = 0.05
+    p.alpha_sat = 0.2
+    p.alpha_decl = 0.3
+    p.c_fixed = 0.01
+    p.soc_target = 0.85
+    p.eta_port = (0.95, 0.9)
+    p.ep_len = 37
+    p.stay_steps = (2, 20)
+    rng = np.random.default_rng(seed + 1)
+    st = w.stations
+    st.group_eta[:] = rng.uniform(0.8, 1.0, st.group_eta.shape).astype(np.float32)
+    st.grid_eta[:] = rng.uniform(0.85, 1.0, st.grid_eta.shape).astype(np.float32)
+    classes = sorted(set(int(s) for s in st.n_ports))
+    w.exo = I.Exo(I.price_bank(n_days=9, ep_len=37, seed=seed), I.arrival_rates(classes, ep_len=37, base=1.5))
+    return w
+
+
+WORKLOADS = {
+    "uniform16": lambda: I.small_uniform(),
+    "fixed203": lambda: I.fixed_station(n_envs=203),
+    "hetero64": lambda: I.heterogeneous(n_envs=64),
+    "odd150": lambda: odd_sizes(),
+    "stressed": lambda: stressed(),
+}
+
+
+def make(name):
+    import torch
+    from paper_2507_01522_b300.chargax import Batch
+    w = WORKLOADS[name]()
+    return w, Batch(w), Oracle(w), torch
+
+
+# ----------------------------------------------------------------------------
+# trajectories
+# ----------------------------------------------------------------------------
+
+def compare_traj(w, b, o, torch, steps, mode="plain", k=1, actions=None):
+    """Run both sides for `steps` steps and compare after every step (plain)
+    or every launch (fused)."""
+    E = b.E
+    params = w.params
+    returns_g, returns_o = np.zeros(E), np.zeros(E)
+    reward = torch.zeros(E, k, device="cuda")
+    done = torch.zeros(E, k, dtype=torch.uint8, device="cuda")
+    n_done = 0
+    for s0 in range(0, steps, k):
+        kk = min(k, steps - s0)
+        if mode == "plain":
+            a = None if actions is None else torch.from_numpy(np.ascontiguousarray(actions[:, s0])).cuda()
+            b.step(actions=a, reward=reward.view(-1), done=done.view(-1))
+        else:
+            a = None if actions is None else torch.from_numpy(np.ascontiguousarray(actions[:, s0:s0 + kk])).cuda()
+            b.step_n(kk, actions=a, reward=reward, done=done, lda=kk, ld_out=k)
+        torch.cuda.synchronize()
+        rg = reward.cpu().numpy()
+        dg = done.cpu().numpy()
+        for j in range(kk):
+            ro, do = o.step(None if actions is None else actions[:, s0 + j])
+            info = o.info()
+            assert_reward_close(rg[:, j], ro, reward_scale(info, params), TRAJ_RTOL, where=f"step {s0 + j}")
+            np.testing.assert_array_equal(dg[:, j], do, err_msg=f"done step {s0 + j}")
+            n_done += int(do.sum())
+        gs, os_ = b.get_state(), o.state()
+        assert_events_equal(gs, os_, where=f"after step {s0 + kk}")
+        assert_floats_close(gs, os_, TRAJ_RTOL, where=f"after step {s0 + kk}", cap_hi=params.cap_kwh[1])
+        stg, sto = b.stats(), o.stats()
+        np.testing.assert_array_equal(stg["arrived"], sto["arrived"].astype(np.uint32))
+        np.testing.assert_array_equal(stg["rejected"], sto["rejected"].astype(np.uint32))
+        np.testing.assert_array_equal(stg["n_episodes"], sto["n_episodes"])
+    stg, sto = b.stats(), o.stats()
+    fin = sto["n_episodes"] > 0
+    if fin.any():
+        d = np.abs(stg["last_ret"][fin] - sto["last_ret"][fin])
+        tol = RETURN_RTOL * np.maximum(np.abs(sto["last_ret"][fin]), 1.0)
+        assert np.all(d <= tol), (d.max(), tol[np.argmax(d - tol)])
+    np.testing.assert_allclose(stg["missing"], sto["missing"], rtol=1e-3, atol=1e-2)
+    np.testing.assert_allclose(stg["charged"], sto["charged"], rtol=1e-3, atol=1e-2)
+    return n_done
+
+
+@pytest.mark.parametrize("name,steps", [("uniform16", 300), ("fixed203", 60), ("hetero64", 60),
+                                        ("odd150", 80), ("stressed", 90)])
+def test_plain_random_actions(cuda_lib, name, steps):
+    w, b, o, torch = make(name)
+    n_done = compare_traj(w, b, o, torch, steps, mode="plain")
+    if name in ("uniform16", "stressed"):
+        assert n_done > 0                  # crossed episode ends
+
+
+@pytest.mark.parametrize("name,steps,k", [("uniform16", 300, 32), ("fixed203", 64, 16), ("hetero64", 64, 7),
+                                          ("odd150", 96, 24), ("stressed", 111, 37), ("odd150", 20, 1)])
+def test_fused_random_actions(cuda_lib, name, steps, k):
+    w, b, o, torch = make(name)
+    compare_traj(w, b, o, torch, steps, mode="fused", k=k)
+
+
+@pytest.mark.parametrize("mode", ["plain", "fused"])
+def test_given_actions(cuda_lib, mode):
+    w, b, o, torch = make("odd150")
+    rng = np.random.default_rng(5)
+    steps = 48
+    acts = I.random_actions(rng, w.stations.total_ports, steps=steps)
+    compare_traj(w, b, o, torch, steps, mode=mode, k=1 if mode == "plain" else 16, actions=acts)
+
+
+# ----------------------------------------------------------------------------
+# one step from a shared mid-episode state (1e-5)
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", ["odd150", "stressed", "fixed203"])
+@pytest.mark.parametrize("mode", ["plain", "fused"])
+def test_single_step_from_oracle_state(cuda_lib, name, mode):
+    w, b, o, torch = make(name)
+    rng = np.random.default_rng(3)
+    for _ in range(29):
+        o.step(None)
+    for trial in range(3):
+        s32 = to_f32_state(o.state())
+        o.set_state(widen(s32))
+        b.set_state(s32)
+        acts = I.random_actions(rng, w.stations.total_ports)
+        reward = torch.zeros(b.E, device="cuda")
+        done = torch.zeros(b.E, dtype=torch.uint8, device="cuda")
+        a = torch.from_numpy(acts).cuda()
+        if mode == "plain":
+            b.step(actions=a, reward=reward, done=done)
+        else:
+            b.step_n(1, actions=a, reward=reward, done=done, lda=1, ld_out=1)
+        ro, do = o.step(acts)
+        info = o.info()
+        gs, os_ = b.get_state(), o.state()
+        assert_events_equal(gs, os_, where=f"trial {trial}")
+        assert_floats_close(gs, os_, STEP_RTOL, where=f"trial {trial}", cap_hi=w.params.cap_kwh[1])
+        assert_reward_close(reward.cpu().numpy(), ro, reward_scale(info, w.params), STEP_RTOL, where=f"trial {trial}")
+        np.testing.assert_array_equal(done.cpu().numpy(), do)
+        for _ in range(7):
+            o.step(None)
+
+
+# ----------------------------------------------------------------------------
+# observation, reset, checkpoint, host API, launch paths
+# ----------------------------------------------------------------------------
+
+def test_observation(cuda_lib):
+    w, b, o, torch = make("odd150")
+    for _ in range(41):
+        o.step(None)
+    s32 = to_f32_state(o.state())
+    o.set_state(widen(s32))
+    b.set_state(s32)
+    obs = torch.zeros(b.obs_size, device="cuda")
+    b.observe(obs)
+    og = obs.cpu().numpy().astype(np.float64)
+    oo = o.observe()
+    np.testing.assert_allclose(og, oo, rtol=2e-6, atol=2e-6)
+
+
+def test_fused_obs_matches_observe(cuda_lib):
+    w, b, o, torch = make("odd150")
+    obs1 = torch.zeros(b.obs_size, device="cuda")
+    obs2 = torch.zeros(b.obs_size, device="cuda")
+    b.step_n(13, obs=obs1)
+    b.observe(obs2)
+    assert torch.equal(obs1, obs2)
+
+
+def test_reset_subset(cuda_lib):
+    w, b, o, torch = make("odd150")
+    for _ in range(20):
+        b.step()
+        o.step(None)
+    ids = np.array([0, 3, 17, 64, 149], np.int32)
+    b.reset(torch.from_numpy(ids).cuda(), seed=1234)
+    o.reset(ids, seed=1234)
+    assert_events_equal(b.get_state(), o.state(), "after reset")
+    compare_traj(w, b, o, torch, 30, mode="fused", k=10)
+
+
+def test_checkpoint_resume_bit_exact(cuda_lib):
+    w, b, o, torch = make("odd150")
+    for _ in range(15):
+        b.step()
+    blob = b.save()
+    r1 = torch.zeros(b.E, 40, device="cuda")
+    b.step_n(40, reward=r1)
+    s1 = b.get_state()
+    b.load(blob)
+    r2 = torch.zeros(b.E, 40, device="cuda")
+    b.step_n(40, reward=r2)
+    s2 = b.get_state()
+    assert torch.equal(r1, r2)
+    for k in s1:
+        np.testing.assert_array_equal(s1[k], s2[k])
+
+
+def test_rollout_graph_equals_chunks(cuda_lib):
+    import torch
+    from paper_2507_01522_b300.chargax import Batch
+    w = odd_sizes()
+    b1, b2 = Batch(w), Batch(w)
+    b1.set_launch(steps_per_launch=16, warps_per_block=4)
+    n = 50
+    r1 = torch.zeros(b1.E, n, device="cuda")
+    d1 = torch.zeros(b1.E, n, dtype=torch.uint8, device="cuda")
+    b1.rollout(n, reward=r1, done=d1)
+    r2 = torch.zeros(b2.E, n, device="cuda")
+    for k0 in range(0, n, 16):
+        kk = min(16, n - k0)
+        tmp = torch.zeros(b2.E, kk, device="cuda")
+        b2.step_n(kk, reward=tmp)
+        r2[:, k0:k0 + kk] = tmp
+    torch.cuda.synchronize()
+    assert torch.equal(r1, r2)
+    # a second replay of the captured graph continues the trajectory
+    b1.rollout(n, reward=r1, done=d1)
+    b2.step_n(n, reward=r2)
+    torch.cuda.synchronize()
+    s1, s2 = b1.get_state(), b2.get_state()
+    for k in ("trem", "tod", "gstep"):
+        np.testing.assert_array_equal(s1[k], s2[k])
+
+
+def test_autotune_keeps_state(cuda_lib):
+    w, b, o, torch = make("hetero64")
+    b.step_n(5)
+    before = b.get_state()
+    k, wpb = b.autotune(64)
+    assert k >= 1 and 1 <= wpb <= 8
+    after = b.get_state()
+    for key in before:
+        np.testing.assert_array_equal(before[key], after[key])
+
+
+def test_host_api_matches_device(cuda_lib):
+    import torch
+    from paper_2507_01522_b300.chargax import Batch
+    w = odd_sizes()
+    b1, b2 = Batch(w), Batch(w)
+    n = 20
+    hr = np.zeros(b1.E * n, np.float32)
+    hd = np.zeros(b1.E * n, np.uint8)
+    ho = np.zeros(b1.obs_size, np.float32)
+    b1.rollout_host(n, hr, hd, ho)
+    r = torch.zeros(b2.E, n, device="cuda")
+    d = torch.zeros(b2.E, n, dtype=torch.uint8, device="cuda")
+    ob = torch.zeros(b2.obs_size, device="cuda")
+    b2.rollout(n, reward=r, done=d, obs=ob)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(hr, r.cpu().numpy().ravel())
+    np.testing.assert_array_equal(hd, d.cpu().numpy().ravel())
+    np.testing.assert_array_equal(ho, ob.cpu().numpy())
+    # plain step with host buffers
+    acts = I.random_actions(np.random.default_rng(1), b1.P)
+    hr1 = np.zeros(b1.E, np.float32)
+    hd1 = np.zeros(b1.E, np.uint8)
+    b1.step_host(acts, hr1, hd1, ho)
+    r1 = torch.zeros(b2.E, device="cuda")
+    b2.step(actions=torch.from_numpy(acts).cuda(), reward=r1)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(hr1, r1.cpu().numpy())
+
+
+def test_action_out_of_range_is_flagged(cuda_lib):
+    from paper_2507_01522_b300.chargax import CHX_EFAULT, ChxError
+    w, b, o, torch = make("fixed203")
+    b.step()
+    b.step()
+    acts = torch.full((b.P,), 11, dtype=torch.int8, device="cuda")
+    b.step(actions=acts)
+    with pytest.raises(ChxError) as ei:
+        b.check()
+    assert ei.value.code == CHX_EFAULT
+    b.check()                               # flag cleared
+
+
+def test_invalid_configuration_rejected(cuda_lib):
+    from paper_2507_01522_b300.chargax import CHX_EINVAL, Batch, ChxError
+    w = I.small_uniform()
+    w.stations.group_size[0] = 15           # groups no longer cover the chargers
+    with pytest.raises(ChxError) as ei:
+        Batch(w)
+    assert ei.value.code == CHX_EINVAL
+
+
+# ----------------------------------------------------------------------------
+# full-size workloads, in the launch configuration the benchmark times
+# ----------------------------------------------------------------------------
+
+def sampled_oracle(w, ids):
+    sub = I.Workload(w.name, w.params, w.stations.subset(ids), w.exo, w.seed)
+    return Oracle(sub, streams=ids)
+
+
+def test_fullsize_heterogeneous_sampled(cuda_lib):
+    """65536 mixed stations in the benchmark's launch shape (autotuned fused
+    kernel, CUDA-graph rollout): two rollouts of 287 steps, so the second one
+    crosses an episode end; 192 sampled stations re-simulated by the oracle;
+    invariants checked on every station."""
+    import torch
+    from paper_2507_01522_b300.chargax import Batch
+    w = I.heterogeneous(n_envs=65536)
+    b = Batch(w)
+    T = w.params.ep_len
+    b.autotune(T)
+    n = T - 1
+    r = torch.zeros(b.E, n, device="cuda")
+    d = torch.zeros(b.E, n, dtype=torch.uint8, device="cuda")
+    rng = np.random.default_rng(0)
+    ids = np.sort(rng.choice(w.stations.n_envs, 192, replace=False)).astype(np.int64)
+    o = sampled_oracle(w, ids)
+    po = w.stations.port_off
+    sel = np.concatenate([np.arange(po[e], po[e + 1]) for e in ids])
+    for rep in range(2):
+        b.rollout(n, reward=r, done=d)
+        torch.cuda.synchronize()
+        gs = b.get_state()
+        rg, dg = r.cpu().numpy()[ids], d.cpu().numpy()[ids]
+        for j in range(n):
+            ro, do = o.step(None)
+            assert_reward_close(rg[:, j], ro, reward_scale(o.info(), w.params), TRAJ_RTOL, where=f"rep {rep} step {j}")
+            np.testing.assert_array_equal(dg[:, j], do)
+        sub = {k: (v[sel] if v.shape[0] == b.P else v[ids]) for k, v in gs.items()}
+        os_ = o.state()
+        assert_events_equal(sub, os_, f"sampled rep {rep}")
+        assert_floats_close(sub, os_, TRAJ_RTOL, f"sampled rep {rep}")
+        np.testing.assert_allclose(sub["ep_ret"], os_["ep_ret"], rtol=RETURN_RTOL, atol=1e-3)
+        # invariants on all stations
+        assert np.all((gs["soc"] >= 0) & (gs["soc"] <= 1))
+        assert np.all(gs["erem"] >= 0)
+        assert np.all(gs["trem"] <= w.params.stay_steps[1])
+        occ = np.add.reduceat((gs["trem"] > 0).astype(np.int64), po[:-1])
+        assert np.all(occ <= w.stations.n_ports)
+        pw = gs["p"].astype(np.float64)
+        assert np.all(np.add.reduceat(pw, po[:-1]) <= w.stations.grid_limit_kw * (1 + 1e-5) + 1e-4)
+    sg, so = b.stats(), o.stats()
+    np.testing.assert_array_equal(sg["n_episodes"][ids], so["n_episodes"])
+    np.testing.assert_allclose(sg["last_ret"][ids], so["last_ret"], rtol=RETURN_RTOL, atol=1e-3)
+    np.testing.assert_array_equal(sg["arrived"][ids], so["arrived"].astype(np.uint32))
+    np.testing.assert_array_equal(sg["rejected"][ids], so["rejected"].astype(np.uint32))
+
+
+def test_fullsize_fixed_station_plain_sampled(cuda_lib):
+    import torch
+    from paper_2507_01522_b300.chargax import Batch
+    w = I.fixed_station(n_envs=4096)
+    b = Batch(w)
+    r = torch.zeros(b.E, device="cuda")
+    for _ in range(100):
+        b.step(reward=r)
+    torch.cuda.synchronize()
+    ids = np.arange(0, 4096, 37)
+    o = sampled_oracle(w, ids)
+    for _ in range(99):
+        o.step(None)
+    ro, _ = o.step(None)
+    info = o.info()
+    gs = b.get_state()
+    po = w.stations.port_off
+    sel = np.concatenate([np.arange(po[e], po[e + 1]) for e in ids])
+    sub = {k: (v[sel] if v.shape[0] == b.P else v[ids]) for k, v in gs.items()}
+    assert_events_equal(sub, o.state(), "sampled")
+    assert_floats_close(sub, o.state(), TRAJ_RTOL, "sampled")
+    assert_reward_close(r.cpu().numpy()[ids], ro, reward_scale(info, w.params), TRAJ_RTOL)
