@@ -39,6 +39,7 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--shape", default="", help="K,W: fixed steps per launch and warps per block (skips the autotuner)")
     return ap.parse_args()
 
 
@@ -220,7 +221,11 @@ def run_b300(args):
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
-    K, W = b.autotune(T)
+    if args.shape:
+        K, W = (int(x) for x in args.shape.split(","))
+        b.set_launch(K, W)
+    else:
+        K, W = b.autotune(T)
     reward = torch.empty(E, T, device=dev)
     done = torch.empty(E, T, dtype=torch.uint8, device=dev)
     obs = torch.empty(b.obs_size, device=dev)

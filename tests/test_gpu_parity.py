@@ -13,7 +13,8 @@ from oracle import Oracle
 from paper_2507_01522_b300 import inputs as I
 
 from parity import (RETURN_RTOL, STEP_RTOL, TRAJ_RTOL, assert_events_equal, assert_floats_close,
-                    assert_reward_close, reward_scale, to_f32_state, widen)
+                    assert_reward_close, assert_traj_close, charger_pmax, reward_scale, station_step_scale,
+                    to_f32_state, widen)
 
 pytestmark = pytest.mark.gpu
 
@@ -102,12 +103,13 @@ def compare_traj(w, b, o, torch, steps, mode="plain", k=1, actions=None):
         for j in range(kk):
             ro, do = o.step(None if actions is None else actions[:, s0 + j])
             info = o.info()
-            assert_reward_close(rg[:, j], ro, reward_scale(info, params), TRAJ_RTOL, where=f"step {s0 + j}")
+            assert_reward_close(rg[:, j], ro, reward_scale(info, params) + station_step_scale(w, info), TRAJ_RTOL,
+                                where=f"step {s0 + j}")
             np.testing.assert_array_equal(dg[:, j], do, err_msg=f"done step {s0 + j}")
             n_done += int(do.sum())
         gs, os_ = b.get_state(), o.state()
         assert_events_equal(gs, os_, where=f"after step {s0 + kk}")
-        assert_floats_close(gs, os_, TRAJ_RTOL, where=f"after step {s0 + kk}", cap_hi=params.cap_kwh[1])
+        assert_traj_close(gs, os_, charger_pmax(w), TRAJ_RTOL, where=f"after step {s0 + kk}")
         stg, sto = b.stats(), o.stats()
         np.testing.assert_array_equal(stg["arrived"], sto["arrived"].astype(np.uint32))
         np.testing.assert_array_equal(stg["rejected"], sto["rejected"].astype(np.uint32))
@@ -333,7 +335,7 @@ def test_invalid_configuration_rejected(cuda_lib):
 
 def sampled_oracle(w, ids):
     sub = I.Workload(w.name, w.params, w.stations.subset(ids), w.exo, w.seed)
-    return Oracle(sub, streams=ids)
+    return Oracle(sub, streams=ids), sub
 
 
 def test_fullsize_heterogeneous_sampled(cuda_lib):
@@ -352,7 +354,7 @@ def test_fullsize_heterogeneous_sampled(cuda_lib):
     d = torch.zeros(b.E, n, dtype=torch.uint8, device="cuda")
     rng = np.random.default_rng(0)
     ids = np.sort(rng.choice(w.stations.n_envs, 192, replace=False)).astype(np.int64)
-    o = sampled_oracle(w, ids)
+    o, ws = sampled_oracle(w, ids)
     po = w.stations.port_off
     sel = np.concatenate([np.arange(po[e], po[e + 1]) for e in ids])
     for rep in range(2):
@@ -362,12 +364,14 @@ def test_fullsize_heterogeneous_sampled(cuda_lib):
         rg, dg = r.cpu().numpy()[ids], d.cpu().numpy()[ids]
         for j in range(n):
             ro, do = o.step(None)
-            assert_reward_close(rg[:, j], ro, reward_scale(o.info(), w.params), TRAJ_RTOL, where=f"rep {rep} step {j}")
+            inf = o.info()
+            assert_reward_close(rg[:, j], ro, reward_scale(inf, w.params) + station_step_scale(ws, inf), TRAJ_RTOL,
+                                where=f"rep {rep} step {j}")
             np.testing.assert_array_equal(dg[:, j], do)
         sub = {k: (v[sel] if v.shape[0] == b.P else v[ids]) for k, v in gs.items()}
         os_ = o.state()
         assert_events_equal(sub, os_, f"sampled rep {rep}")
-        assert_floats_close(sub, os_, TRAJ_RTOL, f"sampled rep {rep}")
+        assert_traj_close(sub, os_, charger_pmax(ws), TRAJ_RTOL, f"sampled rep {rep}")
         np.testing.assert_allclose(sub["ep_ret"], os_["ep_ret"], rtol=RETURN_RTOL, atol=1e-3)
         # invariants on all stations
         assert np.all((gs["soc"] >= 0) & (gs["soc"] <= 1))
@@ -394,7 +398,7 @@ def test_fullsize_fixed_station_plain_sampled(cuda_lib):
         b.step(reward=r)
     torch.cuda.synchronize()
     ids = np.arange(0, 4096, 37)
-    o = sampled_oracle(w, ids)
+    o, ws = sampled_oracle(w, ids)
     for _ in range(99):
         o.step(None)
     ro, _ = o.step(None)
@@ -404,5 +408,5 @@ def test_fullsize_fixed_station_plain_sampled(cuda_lib):
     sel = np.concatenate([np.arange(po[e], po[e + 1]) for e in ids])
     sub = {k: (v[sel] if v.shape[0] == b.P else v[ids]) for k, v in gs.items()}
     assert_events_equal(sub, o.state(), "sampled")
-    assert_floats_close(sub, o.state(), TRAJ_RTOL, "sampled")
-    assert_reward_close(r.cpu().numpy()[ids], ro, reward_scale(info, w.params), TRAJ_RTOL)
+    assert_traj_close(sub, o.state(), charger_pmax(ws), TRAJ_RTOL, "sampled")
+    assert_reward_close(r.cpu().numpy()[ids], ro, reward_scale(info, w.params) + station_step_scale(ws, info), TRAJ_RTOL)
