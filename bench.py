@@ -135,6 +135,23 @@ FUSED_STATE_BYTES_PER_ENV = 80.0
 LANES_PER_SM = 128
 
 
+def recorded_traffic(n_envs, K, W):
+    """DRAM bytes per fused launch from the committed ncu record, if the
+    kernel sources and the launch shape are those the counters were taken on."""
+    import hashlib
+    try:
+        rec = dict(l.split() for l in open(os.path.join(ROOT, "profiles", "k_step_fused_traffic.txt"))
+                   if l.strip() and not l.startswith("#"))
+        src = b"".join(open(os.path.join(ROOT, "paper_2507_01522_b300", "csrc", f), "rb").read()
+                       for f in ("step_fused.cu", "chx_device.cuh"))
+        if (hashlib.sha256(src).hexdigest()[:16] == rec["source_sha256_16"] and int(rec["n_envs"]) == n_envs
+                and int(rec["steps_per_launch"]) == K and int(rec["warps_per_block"]) == W):
+            return int(rec["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
 def cpu_baseline(w, n_sample_envs, steps):
     """Time the CPU oracle, as it stands (single thread), on the first
     ``n_sample_envs`` stations of the workload for ``steps`` steps."""
@@ -270,7 +287,7 @@ def run_b300(args):
     achieved = ops_launch / (launch_ms * 1e-3) / 1e12
     fused_bytes_launch = FUSED_STATE_BYTES_PER_PORT * P + FUSED_STATE_BYTES_PER_ENV * E + 5.0 * E * K
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s", "frac": achieved / alu_peak,
-                "traffic": None, "kernel": "k_step_fused", "launch_ms": launch_ms, "steps_per_launch": K,
+                "traffic": recorded_traffic(E, K, W), "algorithmic_bytes_per_launch": fused_bytes_launch, "kernel": "k_step_fused", "launch_ms": launch_ms, "steps_per_launch": K,
                 "warps_per_block": W, "ops_per_launch": ops_launch,
                 "peak_source": f"{sm_count} SMs x {LANES_PER_SM} lanes x {sm_mhz:.0f} MHz ({pk_kind} max clock)",
                 "hbm_gbs_algorithmic": fused_bytes_launch / (launch_ms * 1e-3) / 1e9,
