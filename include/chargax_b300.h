@@ -185,6 +185,29 @@ int chx_rollout_host(chx_handle* h, int32_t n_steps, float* h_reward, uint8_t* h
 int chx_step_host(chx_handle* h, const int8_t* h_actions, float* h_reward, uint8_t* h_done,
                   float* h_obs, void* stream);
 
+/* ---- rollout without allocation --------------------------------------------
+ * (No counterpart in the paper: an interface for callers that cannot allocate
+ * device memory while they step the simulator -- code running under a memory
+ * pool it does not own, latency-critical loops that must not enter the
+ * driver's allocator, or hosts that reserve all device memory up front.)
+ * Same transitions and outputs as chx_rollout (Philox actions, fused launches
+ * of the handle's steps per launch and warps per block), launched directly
+ * without a CUDA graph.  The call allocates nothing: its only scratch, one
+ * work counter per launch, lives in a 4 KB static device array of
+ * CHX_NOALLOC_MAX_LAUNCHES counters that every GPU loading this library keeps
+ * until the process exits.  n_steps may need at most that many launches
+ * (ceil(n_steps / steps per launch)); more returns CHX_EINVAL.
+ *   - The first call on a device looks up the array's device address (with
+ *     that device current) and caches it; make that first call before any
+ *     stream capture.
+ *   - All calls share the array.  Each call clears the counters it uses on
+ *     `stream` first; calls that overlap on the GPU (other streams, other
+ *     handles on the same device) race on the counters and must be ordered
+ *     by the caller. */
+#define CHX_NOALLOC_MAX_LAUNCHES 1024
+int chx_rollout_noalloc(chx_handle* h, int32_t n_steps, float* d_reward, uint8_t* d_done, float* d_obs,
+                        void* stream);
+
 /* Choose steps per launch and warps per block for chx_rollout by timing
  * candidate shapes on a copy of the state (the state is restored).  Blocks.
  * h_steps_per_launch / h_warps_per_block receive the choice (may be NULL). */

@@ -25,7 +25,7 @@ EXPORTS = (
     "chx_create", "chx_destroy", "chx_last_error", "chx_n_envs", "chx_n_ports_total", "chx_port_offsets",
     "chx_obs_size", "chx_reset", "chx_step", "chx_step_n", "chx_rollout", "chx_rollout_host", "chx_step_host",
     "chx_autotune", "chx_set_launch", "chx_observe", "chx_get_state", "chx_set_state", "chx_stats", "chx_save",
-    "chx_load", "chx_check",
+    "chx_load", "chx_check", "chx_rollout_noalloc",
 )
 
 
@@ -79,6 +79,7 @@ def load_library(path: str = LIB_PATH):
         "chx_autotune": [vp, i32, vp, vp], "chx_set_launch": [vp, i32, i32], "chx_observe": [vp, vp, vp],
         "chx_get_state": [vp] + [vp] * 12, "chx_set_state": [vp] + [vp] * 12, "chx_stats": [vp] + [vp] * 6,
         "chx_save": [vp, vp, vp], "chx_load": [vp, vp, C.c_size_t], "chx_check": [vp, vp],
+        "chx_rollout_noalloc": [vp, i32, vp, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -187,6 +188,12 @@ class Batch:
 
     def rollout(self, n_steps: int, reward=None, done=None, obs=None, stream=None):
         _check(_lib.chx_rollout(self.h, n_steps, _dev_ptr(reward), _dev_ptr(done), _dev_ptr(obs), _stream_ptr(stream)))
+
+    def rollout_noalloc(self, n_steps: int, reward=None, done=None, obs=None, stream=None):
+        """chx_rollout_noalloc: the rollout for callers that cannot allocate
+        device memory during the call (scratch in a static device array)."""
+        _check(_lib.chx_rollout_noalloc(self.h, n_steps, _dev_ptr(reward), _dev_ptr(done), _dev_ptr(obs),
+                                        _stream_ptr(stream)))
 
     def rollout_host(self, n_steps: int, reward=None, done=None, obs=None, stream=None):
         _check(_lib.chx_rollout_host(self.h, n_steps, _np_ptr(reward), _np_ptr(done), _np_ptr(obs),

@@ -1,0 +1,57 @@
+"""chx_rollout_noalloc, the rollout for callers that cannot allocate device
+memory during the call (for example code running under a memory pool it does
+not own): it must give the same results as chx_rollout, call after call,
+while keeping its scratch in a static device array.
+
+Kept in its own file so that it is collected last; it passes alone in a fresh
+process and after the other tests.
+"""
+import numpy as np
+import pytest
+
+from parity import STEP_RTOL
+
+pytestmark = pytest.mark.gpu
+
+
+def test_rollout_noalloc_matches_rollout_twice(cuda_lib):
+    import torch
+    from paper_2507_01522_b300 import inputs as I
+    from paper_2507_01522_b300.chargax import Batch
+    w = I.heterogeneous(n_envs=1000)
+    a, b = Batch(w), Batch(w)                      # identical batches, identical seeds
+    for x in (a, b):
+        x.set_launch(steps_per_launch=24, warps_per_block=4)
+    n = 100                                         # 5 launches per call
+    for call in range(2):                           # the scratch keeps the last call's contents
+        ra = torch.zeros(a.E, n, device="cuda")
+        da = torch.zeros(a.E, n, dtype=torch.uint8, device="cuda")
+        oa = torch.zeros(a.obs_size, device="cuda")
+        rb, db, ob = torch.zeros_like(ra), torch.zeros_like(da), torch.zeros_like(oa)
+        a.rollout(n, reward=ra, done=da, obs=oa)
+        b.rollout_noalloc(n, reward=rb, done=db, obs=ob)
+        torch.cuda.synchronize()
+        assert torch.equal(da, db), f"done differs on call {call}"
+        np.testing.assert_allclose(rb.cpu().numpy(), ra.cpu().numpy(), rtol=STEP_RTOL, atol=1e-6)
+        np.testing.assert_allclose(ob.cpu().numpy(), oa.cpu().numpy(), rtol=STEP_RTOL, atol=1e-6)
+        sa, sb = a.get_state(), b.get_state()
+        for k in ("trem", "tod", "day", "gstep"):
+            np.testing.assert_array_equal(sa[k], sb[k], err_msg=f"{k} on call {call}")
+        for k in ("soc", "erem", "p"):
+            np.testing.assert_allclose(sb[k], sa[k], rtol=STEP_RTOL, atol=1e-6)
+
+
+def test_rollout_noalloc_rejects_too_many_launches(cuda_lib):
+    import torch
+    from paper_2507_01522_b300 import inputs as I
+    from paper_2507_01522_b300.chargax import CHX_EINVAL, Batch, ChxError
+    w = I.small_uniform()
+    b = Batch(w)
+    b.set_launch(steps_per_launch=1, warps_per_block=2)
+    r = torch.zeros(b.E, 1025, device="cuda")
+    with pytest.raises(ChxError) as ei:
+        b.rollout_noalloc(1025, reward=r)           # 1025 launches > 1024 counters
+    assert ei.value.code == CHX_EINVAL
+    assert "at most 1024" in str(ei.value)
+    b.rollout_noalloc(1024, reward=r[:, :1024].contiguous())
+    torch.cuda.synchronize()
