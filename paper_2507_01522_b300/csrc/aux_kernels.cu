@@ -38,6 +38,38 @@ void launch_reset(const DevBatch& b, const DevParams& p, const int32_t* user_to_
     k_reset<<<n, 128, 0, st>>>(b, p, user_to_slot, env_ids, n, (uint32_t)seed, (uint32_t)(seed >> 32));
 }
 
+// Reset of listed station slots with one seed each (the serving pool, where a
+// station's id is its slot): same episode start as k_reset.
+__global__ void k_reset_slots(DevBatch b, DevParams p, const int32_t* __restrict__ slots,
+                              const unsigned long long* __restrict__ seeds, int n)
+{
+    const int j = blockIdx.x;
+    if (j >= n) return;
+    const int s = slots[j];
+    const int c = class_of_slot(b, s);
+    const int C = 8 << c;
+    const long long pb = b.cls_port_base[c] + (long long)(s - b.cls_env_base[c]) * C;
+    for (int q = threadIdx.x; q < C; q += blockDim.x) {
+        const long long i = pb + q;
+        b.soc[i] = 0.f; b.erem[i] = 0.f; b.cap[i] = 0.f; b.rbar[i] = 0.f; b.pw[i] = 0.f; b.trem[i] = 0;
+    }
+    if (threadIdx.x == 0) {
+        const uint32_t lo = (uint32_t)seeds[j], hi = (uint32_t)(seeds[j] >> 32);
+        b.key0[s] = lo;
+        b.key1[s] = hi;
+        b.gstep[s] = 0u;
+        b.tod[s] = 0;
+        b.ep_ret[s] = 0.f;
+        b.day[s] = draw_day((uint32_t)s, 0u, 1u, lo, hi, p.n_days);
+    }
+}
+
+void launch_reset_slots(const DevBatch& b, const DevParams& p, const int32_t* slots, const unsigned long long* seeds,
+                        int n, cudaStream_t st)
+{
+    if (n > 0) k_reset_slots<<<n, 128, 0, st>>>(b, p, slots, seeds, n);
+}
+
 // Observation: one warp per station slot; lanes stride over the chargers.
 __global__ void k_observe(DevBatch b, DevParams p, float* __restrict__ obs)
 {

@@ -23,6 +23,11 @@ struct FusedIO {
     int sched_tile_base[kNumClasses + 1];
     int total_tiles;
     int* counter;                          // work counter, zero at launch
+    // gather mode (NULL = every station of the batch): per class, a list of
+    // entries (station slot, action offset, output index, observation offset)
+    // padded with a padding slot to whole tiles; class c starts at gather_base[c]
+    const int4* gather;
+    int gather_base[kNumClasses];
 };
 
 void launch_step_plain(const DevBatch& b, const DevParams& p, const int8_t* actions, long long lda, float* reward,
@@ -35,5 +40,8 @@ int fused_max_blocks_per_sm(int threads);
 void launch_reset(const DevBatch& b, const DevParams& p, const int32_t* user_to_slot, const int32_t* env_ids, int n,
                   uint64_t seed, cudaStream_t st);
 void launch_observe(const DevBatch& b, const DevParams& p, float* obs, cudaStream_t st);
+// reset listed slots (station id = slot), one 64-bit seed per entry
+void launch_reset_slots(const DevBatch& b, const DevParams& p, const int32_t* slots, const unsigned long long* seeds,
+                        int n, cudaStream_t st);
 
 }  // namespace chx

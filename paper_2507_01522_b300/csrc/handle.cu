@@ -54,6 +54,10 @@ int dalloc(Buffers& bufs, T** p, size_t n)
     return CHX_OK;
 }
 
+}  // namespace
+
+namespace chx {
+
 int class_of_ports(int n)
 {
     int c = 0;
@@ -61,13 +65,9 @@ int class_of_ports(int n)
     return c;
 }
 
-int validate(const chx_stations* st, const chx_env_params* p, const chx_exo* x)
+int validate_params(const chx_env_params* p, const chx_exo* x)
 {
-    if (!st || !p || !x) return fail(CHX_EINVAL, "null configuration pointer");
-    if (st->n_envs < 1 || st->n_envs > (1 << 26)) return fail(CHX_EINVAL, "n_envs out of range");
-    if (!st->h_n_ports || !st->h_port_type || !st->h_n_groups || !st->h_group_size || !st->h_group_limit_kw ||
-        !st->h_grid_limit_kw || !st->h_arrival_class)
-        return fail(CHX_EINVAL, "missing station array");
+    if (!p || !x) return fail(CHX_EINVAL, "null configuration pointer");
     if (p->ep_len < 1 || p->ep_len > (1 << 20)) return fail(CHX_EINVAL, "ep_len out of range");
     if (p->n_levels < 2 || p->n_levels > 255) return fail(CHX_EINVAL, "n_levels must be in 2..255");
     if (!(p->dt_h > 0.f) || !std::isfinite(p->dt_h)) return fail(CHX_EINVAL, "dt_h must be > 0");
@@ -88,6 +88,16 @@ int validate(const chx_stations* st, const chx_env_params* p, const chx_exo* x)
         const float l = x->h_arrival_rate[i];
         if (!(l >= 0.f && l <= 64.f)) return fail(CHX_EINVAL, "arrival rates must be in [0, 64]");
     }
+    return CHX_OK;
+}
+
+int validate_stations(const chx_stations* st, const chx_exo* x, long long max_envs)
+{
+    if (!st || !x) return fail(CHX_EINVAL, "null configuration pointer");
+    if (st->n_envs < 1 || st->n_envs > max_envs) return fail(CHX_EINVAL, "n_envs out of range");
+    if (!st->h_n_ports || !st->h_port_type || !st->h_n_groups || !st->h_group_size || !st->h_group_limit_kw ||
+        !st->h_grid_limit_kw || !st->h_arrival_class)
+        return fail(CHX_EINVAL, "missing station array");
     long long go = 0, po = 0;
     for (int e = 0; e < st->n_envs; ++e) {
         const int n = st->h_n_ports[e], G = st->h_n_groups[e];
@@ -117,7 +127,15 @@ int validate(const chx_stations* st, const chx_env_params* p, const chx_exo* x)
         go += G;
         po += n;
     }
+    if (po >= (1LL << 31)) return fail(CHX_EINVAL, "more than 2^31 - 1 chargers in one batch");
     return CHX_OK;
+}
+
+int validate(const chx_stations* st, const chx_env_params* p, const chx_exo* x)
+{
+    int rc = validate_params(p, x);
+    if (rc) return rc;
+    return validate_stations(st, x, 1LL << 26);
 }
 
 DevParams make_params(const chx_env_params& q, int n_days)
@@ -159,7 +177,7 @@ DevParams make_params(const chx_env_params& q, int n_days)
     return p;
 }
 
-}  // namespace
+}  // namespace chx
 
 // ===========================================================================
 // lifetime

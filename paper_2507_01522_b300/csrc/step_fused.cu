@@ -149,9 +149,23 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
     const int lane = threadIdx.x & 31;
     const int ew = lane / LPE;            // station within the warp
     const int le = lane % LPE;            // lane within the station
-    const int env_local = tile * S::EPW + ew;
-    const int s = b.cls_env_base[CI] + env_local;
-    const long long pb = b.cls_port_base[CI] + (long long)env_local * C + le * PPL;
+    // the station this lane works on: the tile's own slots, or (gather mode)
+    // the slots a caller listed, with their own action/output/observation offsets
+    int s;
+    long long act_base, out_idx, obs_off;
+    if (io.gather) {
+        const int4 en = io.gather[io.gather_base[CI] + tile * S::EPW + ew];
+        s = en.x;
+        act_base = en.y;
+        out_idx = en.z;
+        obs_off = en.w;
+    } else {
+        s = b.cls_env_base[CI] + tile * S::EPW + ew;
+        act_base = b.user_port_off[s];
+        out_idx = b.user_id[s];
+        obs_off = 8LL * out_idx + 6LL * act_base;
+    }
+    const long long pb = b.cls_port_base[CI] + (long long)(s - b.cls_env_base[CI]) * C + le * PPL;
     const unsigned lt_mask = (1u << lane) - 1u;
     const unsigned env_mask = (LPE == 32) ? 0xFFFFFFFFu : (((1u << LPE) - 1u) << (ew * LPE));
 
@@ -162,7 +176,6 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
     const int cls_row = b.arrival_class[s];
     const float grid_cap = b.grid_cap[s], grid_inv_eta = b.grid_inv_eta[s];
     const uint32_t k0 = b.key0[s], k1 = b.key1[s];
-    const long long uoff = b.user_port_off[s];
     int t = b.tod[s], day = b.day[s];
     uint32_t g = b.gstep[s];
     float ret = b.ep_ret[s], last_ret = 0.f;
@@ -203,7 +216,7 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
                     aw[q] = philox4x32_10(make_uint4(uidu, g >> 3, (uint32_t)port, kPurposeAction), k0, k1);
                 lvl = random_level(aw[q], g, p.n_levels);
             } else if (trem[q] > 0) {
-                lvl = io.actions[(uoff + port) * io.lda + k];
+                lvl = io.actions[(act_base + port) * io.lda + k];
                 if (lvl < 0 || lvl >= p.n_levels) {
                     atomicOr(b.err, kErrActionRange);
                     lvl = min(max(lvl, 0), p.n_levels - 1);
@@ -330,18 +343,20 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
         }
         g += 1u;
         if (live && le == 0) {
-            if (io.reward) io.reward[(long long)uid * io.ld_out + k] = r;
-            if (io.done) io.done[(long long)uid * io.ld_out + k] = fin;
+            if (io.reward) io.reward[out_idx * io.ld_out + k] = r;
+            if (io.done) io.done[out_idx * io.ld_out + k] = fin;
         }
     }
 
     // ---- write back
-    st_vec(b.soc + pb, soc);
-    st_vec(b.erem + pb, erem);
-    st_vec(b.cap + pb, cap);
-    st_vec(b.rbar + pb, rbar);
-    st_vec(b.pw + pb, pw);
-    st_u8(b.trem + pb, trem);
+    if (live) {                            // padding stations never write
+        st_vec(b.soc + pb, soc);
+        st_vec(b.erem + pb, erem);
+        st_vec(b.cap + pb, cap);
+        st_vec(b.rbar + pb, rbar);
+        st_vec(b.pw + pb, pw);
+        st_u8(b.trem + pb, trem);
+    }
     if (le == 0 && live) {
         b.tod[s] = t;
         b.day[s] = day;
@@ -361,7 +376,7 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
         const int occ = (int)seg_sum<LPE>((float)occ_l);
         if (live) {
             const int n = b.n_ports[s];
-            float* ob = io.obs + 8LL * uid + 6LL * uoff;
+            float* ob = io.obs + obs_off;
             if (le == 0) obs_env(ob, t, day, occ, n, b, p);
 #pragma unroll
             for (int q = 0; q < PPL; ++q) {
