@@ -247,6 +247,99 @@ int chx_stats(chx_handle* h, uint32_t* h_arrived, uint32_t* h_rejected, float* h
 int chx_save(chx_handle* h, void* h_buf, size_t* size);
 int chx_load(chx_handle* h, const void* h_buf, size_t size);
 
+/* ---- serving loop ------------------------------------------------------------
+ * A pool of device-resident stations stepped by requests from many actors with
+ * continuous batching (the reset/step interface of the paper's Gym-style
+ * environment, App. "Practical Considerations", served to many clients).
+ * Stations are admitted into slots of their size class while the bytes they
+ * occupy stay within an HBM budget; a station's id is its slot and also its
+ * Philox stream id.  Requests wait in a queue; a scheduler thread packs every
+ * request whose stations are not in flight into the next tick (in arrival
+ * order, up to max_tick_envs stations) and keeps up to n_streams ticks on the
+ * device at once; a completion thread copies results back and completes
+ * tickets.  A request's results do not depend on what else shares its tick.
+ * Requests for one station are applied in submission order.  All server calls
+ * are thread-safe. */
+#define CHX_SRV_STEP 0
+#define CHX_SRV_RESET 1
+
+typedef struct chx_srv chx_srv;
+
+typedef struct chx_srv_cfg {
+    chx_env_params params;
+    chx_exo exo;                    /* host tables, copied at start; a station's
+                                       arrival class is its row                     */
+    int32_t class_capacity[5];      /* station slots of size class 8,16,32,64,128     */
+    double hbm_budget_bytes;        /* admission limit on the bytes admitted stations
+                                       occupy (33 B per charger slot + 128 B)        */
+    int32_t max_tick_envs;          /* most stations in one tick and in one request   */
+    int32_t n_streams;              /* ticks on the device at once, 1..8              */
+    int64_t max_tick_obs_floats;    /* observation floats one tick can return, 0 = none */
+} chx_srv_cfg;
+
+typedef struct chx_srv_req {
+    int32_t kind;                   /* CHX_SRV_STEP or CHX_SRV_RESET                  */
+    int32_t n_envs;                 /* 1..max_tick_envs, no station twice             */
+    const int32_t* h_env_ids;       /* station ids from chx_srv_admit (copied)        */
+    const int8_t* h_actions;        /* step: levels of the listed stations' chargers,
+                                       concatenated in list order (copied); NULL =
+                                       Philox levels as in chx_step                  */
+    float* h_reward;                /* step: [n_envs], written before completion      */
+    uint8_t* h_done;                /* step: [n_envs]                                 */
+    float* h_obs;                   /* step: observation after the step, 8 + 6 n floats
+                                       per listed station in list order, or NULL     */
+    uint64_t seed;                  /* reset: new Philox key of the listed stations   */
+} chx_srv_req;
+
+typedef struct chx_srv_stats_t {
+    int64_t n_ticks, n_requests, env_steps, env_resets;
+    int32_t resident;               /* admitted stations                              */
+    double used_bytes, budget_bytes;
+    double device_busy_ms, elapsed_ms;
+} chx_srv_stats_t;
+
+/* Start a server on the current device: allocate the pool and tick buffers,
+ * start the scheduler and completion threads.  CHX_EINVAL, CHX_ENOMEM. */
+int chx_srv_start(const chx_srv_cfg* cfg, chx_srv** out);
+/* Finish in-flight ticks, stop the threads, free everything. */
+int chx_srv_stop(chx_srv* s);
+/* Admit a batch of stations (all or none) and start their episodes with
+ * `seed`; their ids go to h_ids [n_envs].  CHX_ENOMEM if a class has no free
+ * slot or the HBM budget would be exceeded. */
+int chx_srv_admit(chx_srv* s, const chx_stations* st, uint64_t seed, int32_t* h_ids);
+/* Free the slots of stations with no queued or in-flight request (else
+ * CHX_EINVAL and nothing is evicted). */
+int chx_srv_evict(chx_srv* s, const int32_t* h_ids, int32_t n);
+/* Queue a request; *ticket identifies it.  The output buffers must stay valid
+ * until the ticket completes. */
+int chx_srv_submit(chx_srv* s, const chx_srv_req* r, uint64_t* ticket);
+/* Block until the ticket completes (CHX_ETIMEOUT after timeout_us); the
+ * ticket is then released.  latency_ns (may be NULL) = completion - submission.
+ * CHX_ECUDA if the device work carrying it failed. */
+int chx_srv_wait(chx_srv* s, uint64_t ticket, int64_t timeout_us, int64_t* latency_ns);
+/* Non-blocking: *h_done = 1 and the ticket is released if it has completed. */
+int chx_srv_test(chx_srv* s, uint64_t ticket, int32_t* h_done, int64_t* latency_ns);
+int chx_srv_stats(chx_srv* s, chx_srv_stats_t* out);
+
+/* Simulated actors for measurement: actor a owns the stations
+ * h_station_ids[a*envs_per_actor ...]; it submits a step of its stations
+ * (every reset_every-th request a reset instead, 0 = never), waits for it,
+ * thinks for an exponential time of mean mean_think_us and repeats, for
+ * warmup_s + duration_s seconds, driven by n_threads host threads.  Latency
+ * percentiles and throughput cover requests completed after the warm-up. */
+typedef struct chx_srv_sim_cfg {
+    int32_t n_actors, envs_per_actor, n_threads, reset_every;
+    double mean_think_us, warmup_s, duration_s;
+    uint64_t seed;
+} chx_srv_sim_cfg;
+typedef struct chx_srv_sim_result {
+    int64_t n_requests, env_steps;
+    double seconds, env_steps_per_s;
+    double p50_us, p90_us, p99_us, max_us, mean_us;
+    double mean_tick_envs, device_busy_frac;
+} chx_srv_sim_result;
+int chx_srv_simulate(chx_srv* s, const chx_srv_sim_cfg* c, const int32_t* h_station_ids, chx_srv_sim_result* res);
+
 /* Synchronise the handle's work on `stream` and report (then clear) the
  * device-side fault flag: CHX_EFAULT if a kernel saw bad input. */
 int chx_check(chx_handle* h, void* stream);

@@ -26,7 +26,11 @@ EXPORTS = (
     "chx_obs_size", "chx_reset", "chx_step", "chx_step_n", "chx_rollout", "chx_rollout_host", "chx_step_host",
     "chx_autotune", "chx_set_launch", "chx_observe", "chx_get_state", "chx_set_state", "chx_stats", "chx_save",
     "chx_load", "chx_check", "chx_rollout_noalloc",
+    "chx_srv_start", "chx_srv_stop", "chx_srv_admit", "chx_srv_evict", "chx_srv_submit", "chx_srv_wait",
+    "chx_srv_test", "chx_srv_stats", "chx_srv_simulate",
 )
+
+CHX_SRV_STEP, CHX_SRV_RESET = 0, 1
 
 
 class ChxError(RuntimeError):
@@ -58,6 +62,36 @@ class _Exo(C.Structure):
                 ("h_arrival_rate", C.c_void_p)]
 
 
+class _SrvCfg(C.Structure):
+    _fields_ = [("params", _Params), ("exo", _Exo), ("class_capacity", C.c_int32 * 5),
+                ("hbm_budget_bytes", C.c_double), ("max_tick_envs", C.c_int32), ("n_streams", C.c_int32),
+                ("max_tick_obs_floats", C.c_int64)]
+
+
+class _SrvReq(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("n_envs", C.c_int32), ("h_env_ids", C.c_void_p), ("h_actions", C.c_void_p),
+                ("h_reward", C.c_void_p), ("h_done", C.c_void_p), ("h_obs", C.c_void_p), ("seed", C.c_uint64)]
+
+
+class _SrvStats(C.Structure):
+    _fields_ = [("n_ticks", C.c_int64), ("n_requests", C.c_int64), ("env_steps", C.c_int64),
+                ("env_resets", C.c_int64), ("resident", C.c_int32), ("used_bytes", C.c_double),
+                ("budget_bytes", C.c_double), ("device_busy_ms", C.c_double), ("elapsed_ms", C.c_double)]
+
+
+class _SimCfg(C.Structure):
+    _fields_ = [("n_actors", C.c_int32), ("envs_per_actor", C.c_int32), ("n_threads", C.c_int32),
+                ("reset_every", C.c_int32), ("mean_think_us", C.c_double), ("warmup_s", C.c_double),
+                ("duration_s", C.c_double), ("seed", C.c_uint64)]
+
+
+class _SimRes(C.Structure):
+    _fields_ = [("n_requests", C.c_int64), ("env_steps", C.c_int64), ("seconds", C.c_double),
+                ("env_steps_per_s", C.c_double), ("p50_us", C.c_double), ("p90_us", C.c_double),
+                ("p99_us", C.c_double), ("max_us", C.c_double), ("mean_us", C.c_double),
+                ("mean_tick_envs", C.c_double), ("device_busy_frac", C.c_double)]
+
+
 _lib = None
 
 
@@ -80,6 +114,9 @@ def load_library(path: str = LIB_PATH):
         "chx_get_state": [vp] + [vp] * 12, "chx_set_state": [vp] + [vp] * 12, "chx_stats": [vp] + [vp] * 6,
         "chx_save": [vp, vp, vp], "chx_load": [vp, vp, C.c_size_t], "chx_check": [vp, vp],
         "chx_rollout_noalloc": [vp, i32, vp, vp, vp, vp],
+        "chx_srv_start": [vp, vp], "chx_srv_stop": [vp], "chx_srv_admit": [vp, vp, u64, vp],
+        "chx_srv_evict": [vp, vp, i32], "chx_srv_submit": [vp, vp, vp], "chx_srv_wait": [vp, u64, i64, vp],
+        "chx_srv_test": [vp, u64, vp, vp], "chx_srv_stats": [vp, vp], "chx_srv_simulate": [vp, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -245,3 +282,104 @@ class Batch:
     def load(self, blob: bytes):
         buf = np.frombuffer(blob, np.uint8).copy()
         _check(_lib.chx_load(self.h, _np_ptr(buf), len(blob)))
+
+
+def _stations_struct(st, keep):
+    arrs = [np.ascontiguousarray(a) for a in (
+        st.n_ports.astype(np.int32), st.port_type.astype(np.uint8), st.n_groups.astype(np.int32),
+        st.group_size.astype(np.int32), st.group_limit_kw.astype(np.float32), st.group_eta.astype(np.float32),
+        st.grid_limit_kw.astype(np.float32), st.grid_eta.astype(np.float32), st.arrival_class.astype(np.int32))]
+    keep.extend(arrs)
+    return _Stations(st.n_envs, *[_np_ptr(a) for a in arrs])
+
+
+class Server:
+    """The serving loop (chx_srv_*): a pool of device-resident stations stepped
+    by requests with continuous batching.  Host numpy buffers throughout."""
+
+    def __init__(self, params, exo, class_capacity, hbm_budget_bytes=150e9, max_tick_envs=65536, n_streams=2,
+                 max_tick_obs_floats=0):
+        L = load_library()
+        self._keep = [np.ascontiguousarray(exo.price, dtype=np.float32),
+                      np.ascontiguousarray(exo.arrival_rate, dtype=np.float32)]
+        cfg = _SrvCfg()
+        cfg.params = params_struct(params)
+        cfg.exo = _Exo(int(exo.price.shape[0]), _np_ptr(self._keep[0]), int(exo.arrival_rate.shape[0]),
+                       _np_ptr(self._keep[1]))
+        for c in range(5):
+            cfg.class_capacity[c] = int(class_capacity[c])
+        cfg.hbm_budget_bytes = float(hbm_budget_bytes)
+        cfg.max_tick_envs = int(max_tick_envs)
+        cfg.n_streams = int(n_streams)
+        cfg.max_tick_obs_floats = int(max_tick_obs_floats)
+        self._cfg = cfg
+        h = C.c_void_p()
+        _check(L.chx_srv_start(C.byref(cfg), C.byref(h)))
+        self.h = h
+        self.params = params
+        self._inflight = {}
+
+    def stop(self):
+        if getattr(self, "h", None):
+            _lib.chx_srv_stop(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.stop()
+        except Exception:
+            pass
+
+    def admit(self, stations, seed: int = 0) -> np.ndarray:
+        keep = []
+        s = _stations_struct(stations, keep)
+        ids = np.zeros(stations.n_envs, np.int32)
+        _check(_lib.chx_srv_admit(self.h, C.byref(s), C.c_uint64(seed), _np_ptr(ids)))
+        return ids
+
+    def evict(self, ids):
+        ids = np.ascontiguousarray(ids, dtype=np.int32)
+        _check(_lib.chx_srv_evict(self.h, _np_ptr(ids), len(ids)))
+
+    def submit(self, env_ids, kind=CHX_SRV_STEP, actions=None, reward=None, done=None, obs=None, seed: int = 0):
+        """Queue a request; the output arrays are kept alive here until the
+        ticket is seen complete by wait() or test()."""
+        ids = np.ascontiguousarray(env_ids, dtype=np.int32)
+        acts = None if actions is None else np.ascontiguousarray(actions, dtype=np.int8)
+        r = _SrvReq(kind, len(ids), _np_ptr(ids), _np_ptr(acts), _np_ptr(reward), _np_ptr(done), _np_ptr(obs),
+                    C.c_uint64(seed))
+        t = C.c_uint64()
+        _check(_lib.chx_srv_submit(self.h, C.byref(r), C.byref(t)))
+        self._inflight[t.value] = (ids, acts, reward, done, obs)
+        return t.value
+
+    def wait(self, ticket: int, timeout_us: int = 30_000_000) -> int:
+        lat = C.c_int64()
+        rc = _lib.chx_srv_wait(self.h, C.c_uint64(ticket), timeout_us, C.byref(lat))
+        if rc != CHX_ETIMEOUT:
+            self._inflight.pop(ticket, None)
+        _check(rc)
+        return lat.value
+
+    def test(self, ticket: int):
+        d = C.c_int32()
+        lat = C.c_int64()
+        rc = _lib.chx_srv_test(self.h, C.c_uint64(ticket), C.byref(d), C.byref(lat))
+        if d.value:
+            self._inflight.pop(ticket, None)
+        _check(rc)
+        return bool(d.value), lat.value
+
+    def stats(self) -> dict:
+        st = _SrvStats()
+        _check(_lib.chx_srv_stats(self.h, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in _SrvStats._fields_}
+
+    def simulate(self, station_ids, n_actors, envs_per_actor, mean_think_us, duration_s, warmup_s=0.5,
+                 n_threads=8, reset_every=0, seed=0) -> dict:
+        ids = np.ascontiguousarray(station_ids, dtype=np.int32)
+        assert len(ids) >= n_actors * envs_per_actor
+        c = _SimCfg(n_actors, envs_per_actor, n_threads, reset_every, mean_think_us, warmup_s, duration_s, seed)
+        r = _SimRes()
+        _check(_lib.chx_srv_simulate(self.h, C.byref(c), _np_ptr(ids), C.byref(r)))
+        return {k: getattr(r, k) for k, _ in _SimRes._fields_}
