@@ -1,0 +1,204 @@
+"""The serving loop (chx_srv_*): parity with the oracle through requests,
+results independent of what shares a tick ("alone vs in the mix"), per-station
+ordering, admission by HBM budget, errors, and the simulated actors."""
+import numpy as np
+import pytest
+
+from oracle import Oracle
+from paper_2507_01522_b300 import inputs as I
+
+from parity import TRAJ_RTOL, assert_reward_close, reward_scale, station_step_scale
+from test_gpu_parity import odd_sizes
+
+pytestmark = pytest.mark.gpu
+
+CAP = (64, 64, 64, 64, 64)
+
+
+def server_for(w, **kw):
+    from paper_2507_01522_b300.chargax import Server
+    kw.setdefault("max_tick_obs_floats", 8 * w.stations.n_envs + 6 * w.stations.total_ports)
+    return Server(w.params, w.exo, kw.pop("cap", CAP), **kw)
+
+
+def partition(rng, n, max_size=40):
+    perm = rng.permutation(n)
+    out, i = [], 0
+    while i < n:
+        k = int(rng.integers(1, max_size + 1))
+        out.append(perm[i:i + k])
+        i += k
+    return out
+
+
+def obs_of(w, o_obs, envs):
+    po = w.stations.port_off
+    return np.concatenate([o_obs[8 * e + 6 * po[e]: 8 * (e + 1) + 6 * po[e + 1]] for e in envs])
+
+
+def test_serving_matches_oracle():
+    from paper_2507_01522_b300.chargax import CHX_SRV_RESET
+    w = odd_sizes()
+    srv = server_for(w)
+    ids = srv.admit(w.stations, seed=5)
+    assert len(set(ids.tolist())) == w.stations.n_envs
+    o = Oracle(w, seed=5, streams=ids)
+    rng = np.random.default_rng(1)
+    po = w.stations.port_off
+    for rnd in range(40):
+        given = rnd % 3 == 2
+        acts = I.random_actions(rng, w.stations.total_ports) if given else None
+        if rnd == 25:                                   # a round of resets for a subset
+            sub = np.sort(rng.choice(w.stations.n_envs, 30, replace=False))
+            t = srv.submit(ids[sub], kind=CHX_SRV_RESET, seed=77)
+            srv.wait(t)
+            o.reset(sub, seed=77)
+        reqs = []
+        for part in partition(rng, w.stations.n_envs):
+            r = np.zeros(len(part), np.float32)
+            d = np.zeros(len(part), np.uint8)
+            n_ch = int(sum(po[e + 1] - po[e] for e in part))
+            ob = np.zeros(8 * len(part) + 6 * n_ch, np.float32)
+            a = None if acts is None else np.concatenate([acts[po[e]:po[e + 1]] for e in part])
+            reqs.append((part, r, d, ob, srv.submit(ids[part], actions=a, reward=r, done=d, obs=ob)))
+        for _, _, _, _, t in reqs:
+            srv.wait(t)
+        ro, do = o.step(acts)
+        info = o.info()
+        scale = reward_scale(info, w.params) + station_step_scale(w, info)
+        oo = o.observe()
+        for part, r, d, ob, _ in reqs:
+            assert_reward_close(r, ro[part], scale[part], TRAJ_RTOL, where=f"round {rnd}")
+            np.testing.assert_array_equal(d, do[part])
+            exp = obs_of(w, oo, part)
+            np.testing.assert_allclose(ob, exp, rtol=0, atol=2e-4, err_msg=f"obs round {rnd}")
+            # events: occupancy and remaining stay are exact
+            port_blocks = []
+            k = 0
+            for e in part:
+                n = po[e + 1] - po[e]
+                port_blocks.append(ob[k + 8: k + 8 + 6 * n].reshape(n, 6))
+                k += 8 + 6 * n
+            pb = np.concatenate(port_blocks)
+            trem_o = o.state()["trem"][np.concatenate([np.arange(po[e], po[e + 1]) for e in part])]
+            np.testing.assert_array_equal(np.rint(pb[:, 2] * w.params.stay_steps[1]).astype(int), trem_o)
+            np.testing.assert_array_equal(pb[:, 0], (trem_o > 0).astype(np.float32))
+    st = srv.stats()
+    assert st["env_steps"] == 40 * w.stations.n_envs
+    srv.stop()
+
+
+def run_rounds(srv, ids, w, rounds, mix, seed=3):
+    """Queue `rounds` rounds of steps (random partitions, some rounds with
+    given actions, one reset round).  mix=False: every request alone (submit,
+    wait).  mix=True: everything submitted at once, then waited."""
+    from paper_2507_01522_b300.chargax import CHX_SRV_RESET
+    rng = np.random.default_rng(seed)
+    po = w.stations.port_off
+    out, tickets = [], []
+    for rnd in range(rounds):
+        acts = I.random_actions(rng, w.stations.total_ports) if rnd % 2 else None
+        parts = partition(rng, w.stations.n_envs, 25)
+        for part in parts:
+            r = np.zeros(len(part), np.float32)
+            d = np.zeros(len(part), np.uint8)
+            n_ch = int(sum(po[e + 1] - po[e] for e in part))
+            ob = np.zeros(8 * len(part) + 6 * n_ch, np.float32)
+            a = None if acts is None else np.concatenate([acts[po[e]:po[e + 1]] for e in part])
+            t = srv.submit(ids[part], actions=a, reward=r, done=d, obs=ob)
+            out.append((r, d, ob))
+            tickets.append(t)
+            if not mix:
+                srv.wait(t)
+        if rnd == 4:
+            t = srv.submit(ids[parts[0]], kind=CHX_SRV_RESET, seed=9)
+            tickets.append(t)
+            if not mix:
+                srv.wait(t)
+    for t in tickets:
+        if mix:
+            srv.wait(t)
+    return out
+
+
+def test_serving_alone_equals_mix():
+    """Each request's reward, done flags and observation are the same when it
+    runs alone and when it shares ticks with others (here: bit-identical),
+    with several rounds for the same stations queued at once (so per-station
+    submission order must be kept)."""
+    w = odd_sizes()
+    a, b = server_for(w), server_for(w, n_streams=3)
+    ia, ib = a.admit(w.stations, seed=2), b.admit(w.stations, seed=2)
+    assert np.array_equal(ia, ib)
+    alone = run_rounds(a, ia, w, 12, mix=False)
+    mixed = run_rounds(b, ib, w, 12, mix=True)
+    assert len(alone) == len(mixed)
+    for (r1, d1, o1), (r2, d2, o2) in zip(alone, mixed):
+        assert np.array_equal(r1, r2)
+        assert np.array_equal(d1, d2)
+        assert np.array_equal(o1, o2)
+    sa, sb = a.stats(), b.stats()
+    assert sb["n_ticks"] < sb["n_requests"]          # requests really shared ticks
+    assert sa["n_ticks"] == sa["n_requests"]
+    a.stop()
+    b.stop()
+
+
+def test_serving_admission_budget_and_errors():
+    from paper_2507_01522_b300.chargax import CHX_EINVAL, CHX_ENOMEM, ChxError
+    w = I.fixed_station(n_envs=12)
+    one = 16 * 33.0 + 128.0
+    srv = server_for(w, cap=(0, 11, 0, 0, 0), hbm_budget_bytes=10 * one + 1)
+    ids = srv.admit(w.stations.subset(range(10)))
+    with pytest.raises(ChxError) as ei:                  # budget
+        srv.admit(w.stations.subset([10]))
+    assert ei.value.code == CHX_ENOMEM
+    srv.evict(ids[:2])
+    more = srv.admit(w.stations.subset([10, 11]))
+    assert srv.stats()["resident"] == 10
+    small = server_for(w, cap=(0, 2, 0, 0, 0))
+    with pytest.raises(ChxError) as ei:                  # class capacity (2 slots)
+        small.admit(w.stations.subset([0, 1, 2]))
+    assert ei.value.code == CHX_ENOMEM
+    assert small.stats()["resident"] == 0                # all or nothing
+    small.admit(w.stations.subset([0, 1]))
+    small.stop()
+    with pytest.raises(ChxError) as ei:                  # evicted id
+        srv.submit(ids[:1])
+    assert ei.value.code == CHX_EINVAL
+    with pytest.raises(ChxError) as ei:                  # duplicate station
+        srv.submit(np.array([more[0], more[0]]))
+    assert ei.value.code == CHX_EINVAL
+    bad = np.full(16, 11, np.int8)
+    with pytest.raises(ChxError) as ei:                  # action level out of range
+        srv.submit(more[:1], actions=bad)
+    assert ei.value.code == CHX_EINVAL
+    # a station with a queued request cannot be evicted
+    r = np.zeros(1, np.float32)
+    t = srv.submit(more[:1], reward=r)
+    try:
+        srv.evict(more[:1])
+        evicted = True
+    except ChxError as e:
+        evicted = False
+        assert e.code == CHX_EINVAL
+    srv.wait(t)
+    if evicted:                                          # it may have finished first
+        return
+    srv.evict(more[:1])
+    srv.stop()
+
+
+def test_serving_simulation_reports_latency():
+    w = I.serving_pool(n_envs=2048, seed=1)
+    cap = [int(np.sum((w.stations.n_ports > (4 << c)) & (w.stations.n_ports <= (8 << c)))) for c in range(5)]
+    cap[0] += int(np.sum(w.stations.n_ports <= 4))
+    srv = server_for(w, cap=cap, max_tick_obs_floats=0, max_tick_envs=4096)
+    ids = srv.admit(w.stations)
+    res = srv.simulate(ids, n_actors=64, envs_per_actor=32, mean_think_us=200.0, duration_s=0.5, warmup_s=0.2,
+                       n_threads=4, reset_every=10)
+    assert res["n_requests"] > 100
+    assert 0 < res["p50_us"] <= res["p99_us"] <= res["max_us"]
+    assert res["env_steps_per_s"] > 0
+    assert res["mean_tick_envs"] > 0
+    srv.stop()
