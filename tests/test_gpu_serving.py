@@ -163,9 +163,12 @@ def test_serving_admission_budget_and_errors():
     assert small.stats()["resident"] == 0                # all or nothing
     small.admit(w.stations.subset([0, 1]))
     small.stop()
-    with pytest.raises(ChxError) as ei:                  # evicted id
-        srv.submit(ids[:1])
-    assert ei.value.code == CHX_EINVAL
+    assert set(more.tolist()) == set(ids[:2].tolist())   # freed slots are reused
+    srv.evict(more[1:2])
+    for bad_id in (more[1:2], np.array([10 ** 6])):      # evicted / never admitted
+        with pytest.raises(ChxError) as ei:
+            srv.submit(bad_id)
+        assert ei.value.code == CHX_EINVAL
     with pytest.raises(ChxError) as ei:                  # duplicate station
         srv.submit(np.array([more[0], more[0]]))
     assert ei.value.code == CHX_EINVAL
