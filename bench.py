@@ -39,6 +39,11 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-envs", type=int, default=1 << 20, help="resident stations of the serving leg")
+    ap.add_argument("--serve-actors", type=int, default=4096)
+    ap.add_argument("--serve-think-us", type=float, default=2000.0, help="mean think time of a simulated actor")
+    ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--shape", default="", help="K,W: fixed steps per launch and warps per block (skips the autotuner)")
     return ap.parse_args()
 
@@ -356,12 +361,46 @@ def run_b300(args):
         line["gpu_launches"] += launches_per_step * args.steps
 
     line["clocks"] = ck.summary()
+    if not args.no_serve:
+        del b
+        torch.cuda.empty_cache()
+        line["serving"] = run_serving(args, rank)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         n = calibrate_sample(w, 12.0, T)
         line["cpu_baseline"] = cpu_baseline(w, n, T)
     if rank == 0:
         print(json.dumps(line), flush=True)
     barrier(ws)
+
+
+def run_serving(args, rank):
+    """Serving leg: a pool of resident stations (8-128 chargers, log-uniform),
+    closed-loop simulated actors each stepping its own stations, Philox
+    actions; latency from submission to completion."""
+    import numpy as np
+    from paper_2507_01522_b300 import chargax
+    from paper_2507_01522_b300 import inputs as I
+    w = I.serving_pool(args.serve_envs, seed=rank)
+    n = w.stations.n_ports
+    cap = [int(np.sum(n <= 8))] + [int(np.sum((n > (4 << c)) & (n <= (8 << c)))) for c in range(1, 5)]
+    t0 = time.perf_counter()
+    srv = chargax.Server(w.params, w.exo, cap, hbm_budget_bytes=150e9, max_tick_envs=65536, n_streams=2)
+    ids = srv.admit(w.stations, seed=2000 + rank)
+    t_admit = time.perf_counter() - t0
+    per = args.serve_envs // args.serve_actors
+    threads = max(2, min(16, (os.cpu_count() or 8) // 2))
+    res = srv.simulate(ids, n_actors=args.serve_actors, envs_per_actor=per, mean_think_us=args.serve_think_us,
+                       duration_s=args.serve_seconds, warmup_s=1.0, n_threads=threads, seed=rank)
+    st = srv.stats()
+    srv.stop()
+    return {"workload": w.name, "resident_stations": int(st["resident"]), "chargers": int(w.stations.total_ports),
+            "pool_bytes_admitted": st["used_bytes"], "hbm_budget_bytes": st["budget_bytes"],
+            "actors": args.serve_actors, "envs_per_request": per, "mean_think_us": args.serve_think_us,
+            "host_threads": threads, "admit_s": round(t_admit, 3),
+            "p50_us": res["p50_us"], "p90_us": res["p90_us"], "p99_us": res["p99_us"], "max_us": res["max_us"],
+            "env_steps_per_s": res["env_steps_per_s"], "requests": res["n_requests"],
+            "mean_tick_envs": res["mean_tick_envs"], "device_busy_frac": res["device_busy_frac"],
+            "seconds": res["seconds"]}
 
 
 def main():

@@ -153,22 +153,6 @@ def arrival_rates(port_counts, ep_len: int = STEPS_PER_DAY, base: float = 0.5) -
 # station layouts
 # ----------------------------------------------------------------------------
 
-def _random_groups(rng: np.random.Generator, n: int, lo: int = 4, hi: int = 16) -> List[int]:
-    """Sequential group sizes U{lo..hi}; a remainder below ``lo`` joins the
-    previous group (a station smaller than ``lo`` is one group)."""
-    sizes: List[int] = []
-    left = n
-    while left > 0:
-        s = int(rng.integers(lo, hi + 1))
-        s = min(s, left)
-        if s < lo and sizes:
-            sizes[-1] += s
-        else:
-            sizes.append(s)
-        left -= s
-    return sizes
-
-
 def _build(per_env: List[dict], class_of_n: Dict[int, int]) -> Stations:
     n_ports = np.array([d["n"] for d in per_env], dtype=np.int32)
     port_type = np.concatenate([np.asarray(d["types"], dtype=np.uint8) for d in per_env])
@@ -192,24 +176,42 @@ def uniform_stations(n_envs: int, n_ports: int, groups: List[int], group_limit_k
 
 def mixed_stations(rng: np.random.Generator, sizes: np.ndarray, p_max_kw, p_dc: float = 0.25,
                    grid_kw_per_port: float = 9.0, group_frac: float = 0.5,
-                   class_sizes: Optional[List[int]] = None) -> Stations:
+                   class_sizes: Optional[List[int]] = None, group_lo: int = 4, group_hi: int = 16) -> Stations:
     """Heterogeneous stations: per port DC with probability ``p_dc`` else AC;
-    sequential groups of 4..16 ports, each limited to ``group_frac`` of its
-    ports' summed maximum power; grid limit ``grid_kw_per_port`` x N."""
+    sequential groups of U{group_lo..group_hi} ports (the last one takes what
+    is left; a remainder below ``group_lo`` joins the previous group), each
+    limited to ``group_frac`` of its ports' summed maximum power; grid limit
+    ``grid_kw_per_port`` x N.  Vectorised over stations."""
+    sizes = np.asarray(sizes, dtype=np.int64)
+    E = len(sizes)
     if class_sizes is None:
         class_sizes = sorted(set(int(n) for n in sizes))
-    class_of_n = {n: i for i, n in enumerate(class_sizes)}
-    per_env = []
-    for n in sizes:
-        n = int(n)
-        types = (rng.random(n) < p_dc).astype(np.uint8)
-        groups = _random_groups(rng, n)
-        glim, o = [], 0
-        for g in groups:
-            glim.append(group_frac * float(sum(p_max_kw[int(x)] for x in types[o:o + g])))
-            o += g
-        per_env.append(dict(n=n, types=types, groups=groups, glim=glim, grid=grid_kw_per_port * n))
-    return _build(per_env, class_of_n)
+    class_of_n = np.full(max(class_sizes) + 1, -1, np.int64)
+    class_of_n[np.asarray(class_sizes)] = np.arange(len(class_sizes))
+    port_type = (rng.random(int(sizes.sum())) < p_dc).astype(np.uint8)
+    # candidate group sizes, their running sums, and the groups that fit
+    kmax = int(sizes.max()) // group_lo + 2
+    draws = rng.integers(group_lo, group_hi + 1, size=(E, kmax))
+    csum = np.cumsum(draws, axis=1)
+    full = csum < sizes[:, None]                       # groups completed before the end
+    k = full.sum(axis=1)                               # number of full groups
+    last = sizes - np.where(k > 0, csum[np.arange(E), np.maximum(k - 1, 0)], 0)
+    merge = (last < group_lo) & (k > 0)
+    n_groups = np.where(merge, k, k + 1)
+    cols = np.arange(kmax)[None, :]
+    g = np.where(cols < k[:, None], draws, 0)
+    g[np.arange(E), np.where(merge, k - 1, k)] += last   # the remainder: own group or merged
+    group_size = g[cols < n_groups[:, None]].astype(np.int32)
+    # group limits: fraction of the summed charger maxima of each group
+    pmax = np.asarray(p_max_kw, np.float64)[port_type]
+    g_start = np.concatenate([[0], np.cumsum(group_size)[:-1]])
+    glim = group_frac * np.add.reduceat(pmax, g_start) if len(g_start) else np.zeros(0)
+    return Stations(
+        n_ports=sizes.astype(np.int32), port_type=port_type, n_groups=n_groups.astype(np.int32),
+        group_size=group_size, group_limit_kw=glim.astype(np.float32),
+        group_eta=np.ones(len(group_size), np.float32),
+        grid_limit_kw=(grid_kw_per_port * sizes).astype(np.float32), grid_eta=np.ones(E, np.float32),
+        arrival_class=class_of_n[sizes].astype(np.int32))
 
 
 # ----------------------------------------------------------------------------
