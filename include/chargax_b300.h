@@ -311,7 +311,9 @@ int chx_srv_admit(chx_srv* s, const chx_stations* st, uint64_t seed, int32_t* h_
  * CHX_EINVAL and nothing is evicted). */
 int chx_srv_evict(chx_srv* s, const int32_t* h_ids, int32_t n);
 /* Queue a request; *ticket identifies it.  The output buffers must stay valid
- * until the ticket completes. */
+ * until the ticket completes.  At most 65536 tickets may be outstanding
+ * (submitted and not yet released by chx_srv_wait / chx_srv_test), else
+ * CHX_ENOMEM.  A ticket is waited on or tested by one thread at a time. */
 int chx_srv_submit(chx_srv* s, const chx_srv_req* r, uint64_t* ticket);
 /* Block until the ticket completes (CHX_ETIMEOUT after timeout_us); the
  * ticket is then released.  latency_ns (may be NULL) = completion - submission.

@@ -28,7 +28,6 @@
 #include <random>
 #include <string>
 #include <thread>
-#include <unordered_map>
 #include <vector>
 
 #include "../../include/chargax_b300.h"
@@ -51,10 +50,19 @@ inline int64_t now_ns()
     return std::chrono::duration_cast<std::chrono::nanoseconds>(Clock::now().time_since_epoch()).count();
 }
 
+constexpr uint64_t kMaxOutstanding = 1u << 16;   // request records (power of two)
+
 // bytes a station of class c occupies in the pool (state + statics)
 inline double slot_bytes(int c) { return (double)(8 << c) * 33.0 + 128.0; }
 
+constexpr int kFree = 0, kQueued = 1, kDone = 2;
+
+// A request record.  Records live in a fixed table indexed by ticket modulo
+// its size, so their addresses never change and a ticket's state can be read
+// without the server lock.
 struct Request {
+    std::atomic<int> state{kFree};
+    std::atomic<uint64_t> ticket{0};
     int32_t kind = 0;
     std::vector<int32_t> envs;
     std::vector<int8_t> actions;          // empty = Philox levels
@@ -65,7 +73,6 @@ struct Request {
     uint64_t seed = 0;
     int64_t obs_floats = 0;
     int64_t t_submit = 0, t_done = 0;
-    bool done = false;
     bool failed = false;
 };
 
@@ -81,8 +88,9 @@ struct Tick {
     int32_t *h_rslots = nullptr, *d_rslots = nullptr;
     unsigned long long *h_rseeds = nullptr, *d_rseeds = nullptr;
     int* d_counter = nullptr;
-    std::vector<uint64_t> tickets;
-    std::vector<int64_t> rew_off, obs_off;  // per ticket: where its outputs start in the tick buffers
+    std::vector<uint32_t> recs;             // request records in this tick
+    std::vector<int64_t> rew_off, obs_off;  // per record: where its outputs start in the tick buffers
+    std::vector<int4> per_cls[kNumClasses];
     bool busy = false;
     bool failed = false;
 };
@@ -100,6 +108,7 @@ struct chx_srv {
     int pad_slot[kNumClasses] = {};
     std::vector<int> free_slots[kNumClasses];
     std::vector<uint8_t> admitted;
+    std::vector<uint8_t> slot_cls;         // size class of each slot
     std::vector<int32_t> slot_nports;      // chargers of the station in each slot
     std::vector<int32_t> refs;             // queued or in-flight requests per station
     std::vector<uint8_t> in_flight;
@@ -111,8 +120,9 @@ struct chx_srv {
 
     std::mutex mu;
     std::condition_variable cv_sched, cv_done, cv_complete;
-    std::deque<uint64_t> pending;
-    std::unordered_map<uint64_t, Request> reqs;
+    std::deque<uint32_t> pending;          // queued request records, arrival order
+    std::vector<Request> table;
+    uint64_t req_mask = 0;
     uint64_t next_ticket = 1;
     uint64_t events = 0;                   // submissions + completions (wakes a blocked scheduler)
     std::vector<Tick> ticks;
@@ -177,6 +187,9 @@ int alloc_pool(chx_srv* s)
     std::vector<int32_t> minus1(NS, -1);
     SRV_TRY(cudaMemcpy(b.user_id, minus1.data(), NS * sizeof(int32_t), cudaMemcpyHostToDevice));
     s->admitted.assign(NS, 0);
+    s->slot_cls.assign(NS, 0);
+    for (int c = 0; c < kNumClasses; ++c)
+        for (int i = 0; i < b.cls_n_env[c]; ++i) s->slot_cls[b.cls_env_base[c] + i] = (uint8_t)c;
     s->slot_nports.assign(NS, 0);
     s->refs.assign(NS, 0);
     s->in_flight.assign(NS, 0);
@@ -227,20 +240,15 @@ void free_tick(Tick& t)
     t = Tick{};
 }
 
-inline int class_of_slot_host(const chx_srv* s, int slot)
-{
-    int c = 0;
-    for (int i = 1; i < kNumClasses; ++i)
-        if (slot >= s->b.cls_env_base[i]) c = i;
-    return c;
-}
+inline int class_of_slot_host(const chx_srv* s, int slot) { return s->slot_cls[slot]; }
 
 // Pack and launch one tick on ticks[ti] with the requests the scheduler chose.
 // Runs without the server lock (the requests and their stations are reserved).
 int launch_tick(chx_srv* s, int ti, const std::vector<Request*>& rq)
 {
     Tick& t = s->ticks[ti];
-    std::vector<int4> per_cls[kNumClasses];
+    auto& per_cls = t.per_cls;
+    for (auto& L : per_cls) L.clear();
     int n_reset = 0;
     int64_t act_used = 0, rew_used = 0, obs_used = 0;
     t.rew_off.assign(rq.size(), 0);
@@ -358,12 +366,12 @@ void scheduler(chx_srv* s)
             // its stations is in flight or claimed by an earlier waiting request
             const uint32_t gen = next_scan(s);
             rq.clear();
-            t.tickets.clear();
+            t.recs.clear();
             int envs = 0;
             int64_t act = 0, obs = 0;
             int with_actions = -1;         // a tick is all-Philox or all-given actions
             for (auto it = s->pending.begin(); it != s->pending.end();) {
-                Request& q = s->reqs[*it];
+                Request& q = s->table[*it];
                 bool blocked = false;
                 for (int32_t e : q.envs)
                     if (s->in_flight[e] || s->scan_mark[e] == gen) {
@@ -387,7 +395,7 @@ void scheduler(chx_srv* s)
                 act += (int64_t)q.actions.size();
                 obs += q.obs_floats;
                 rq.push_back(&q);
-                t.tickets.push_back(*it);
+                t.recs.push_back(*it);
                 it = s->pending.erase(it);
             }
             if (rq.empty()) {              // everything waits on in-flight stations
@@ -426,14 +434,10 @@ void completer(chx_srv* s)
             t.failed = true;
             ms = 0.f;
         }
-        // copy results to the requesters (their records do not move: the map
-        // keeps element addresses, and only completed tickets are erased)
-        for (size_t r = 0; r < t.tickets.size(); ++r) {
-            Request* q;
-            {
-                std::lock_guard<std::mutex> lk(s->mu);
-                q = &s->reqs[t.tickets[r]];
-            }
+        // copy results to the requesters without the lock (records stay put and
+        // are not released before they are marked done below)
+        for (size_t r = 0; r < t.recs.size(); ++r) {
+            Request* q = &s->table[t.recs[r]];
             if (q->kind != CHX_SRV_STEP || t.failed) continue;
             const size_t n = q->envs.size();
             if (q->h_reward) std::memcpy(q->h_reward, t.h_rew + t.rew_off[r], n * sizeof(float));
@@ -443,15 +447,15 @@ void completer(chx_srv* s)
         const int64_t tn = now_ns();
         {
             std::lock_guard<std::mutex> lk(s->mu);
-            for (uint64_t tk : t.tickets) {
-                Request& q = s->reqs[tk];
+            for (uint32_t ri : t.recs) {
+                Request& q = s->table[ri];
                 for (int32_t e : q.envs) {
                     s->in_flight[e] = 0;
                     s->refs[e] -= 1;
                 }
-                q.done = true;
                 q.failed = t.failed;
                 q.t_done = tn;
+                q.state.store(kDone, std::memory_order_release);
                 s->n_requests += 1;
                 if (q.kind == CHX_SRV_STEP)
                     s->n_env_steps += q.envs.size();
@@ -462,7 +466,7 @@ void completer(chx_srv* s)
             s->busy_ms += ms;
             s->events += 1;
             t.busy = false;
-            t.tickets.clear();
+            t.recs.clear();
         }
         s->cv_done.notify_all();
         s->cv_sched.notify_one();
@@ -526,6 +530,8 @@ extern "C" int chx_srv_start(const chx_srv_cfg* cfg, chx_srv** out)
     s->max_tick_envs = cfg->max_tick_envs;
     s->max_tick_act = (int64_t)cfg->max_tick_envs * CHX_MAX_PORTS;
     s->max_tick_obs = cfg->max_tick_obs_floats;
+    s->table = std::vector<Request>(kMaxOutstanding);
+    s->req_mask = kMaxOutstanding - 1;
     if (cudaGetDevice(&s->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess) {
         delete s;
@@ -726,16 +732,24 @@ extern "C" int chx_srv_submit(chx_srv* s, const chx_srv_req* r, uint64_t* ticket
     if (r->kind != CHX_SRV_STEP && r->kind != CHX_SRV_RESET) return fail(CHX_EINVAL, "unknown request kind");
     if (r->n_envs < 1 || r->n_envs > s->max_tick_envs || !r->h_env_ids)
         return fail(CHX_EINVAL, "n_envs must be in 1..max_tick_envs");
-    Request q;
+    std::unique_lock<std::mutex> lk(s->mu);
+    if (s->stopping) return fail(CHX_EINVAL, "server is stopping");
+    const uint64_t tk = s->next_ticket;
+    const uint32_t ri = (uint32_t)(tk & s->req_mask);
+    Request& q = s->table[ri];
+    if (q.state.load(std::memory_order_acquire) != kFree)
+        return fail(CHX_ENOMEM, "too many outstanding requests: release tickets with chx_srv_wait or chx_srv_test");
+    // the record is free: fill it under the lock, publish it last
     q.kind = r->kind;
     q.envs.assign(r->h_env_ids, r->h_env_ids + r->n_envs);
     q.h_reward = r->h_reward;
     q.h_done = r->h_done;
     q.h_obs = r->kind == CHX_SRV_STEP ? r->h_obs : nullptr;
     q.seed = r->seed;
+    q.failed = false;
+    q.obs_floats = 0;
+    q.actions.clear();
     q.act_off.assign(q.envs.size() + 1, 0);
-    std::unique_lock<std::mutex> lk(s->mu);
-    if (s->stopping) return fail(CHX_EINVAL, "server is stopping");
     const uint32_t gen = next_scan(s);
     for (size_t j = 0; j < q.envs.size(); ++j) {
         const int32_t e = q.envs[j];
@@ -755,9 +769,10 @@ extern "C" int chx_srv_submit(chx_srv* s, const chx_srv_req* r, uint64_t* ticket
     }
     for (int32_t e : q.envs) s->refs[e] += 1;
     q.t_submit = now_ns();
-    const uint64_t tk = s->next_ticket++;
-    s->reqs.emplace(tk, std::move(q));
-    s->pending.push_back(tk);
+    q.ticket.store(tk, std::memory_order_relaxed);
+    q.state.store(kQueued, std::memory_order_release);
+    s->next_ticket++;
+    s->pending.push_back(ri);
     s->events += 1;
     *ticket = tk;
     lk.unlock();
@@ -765,40 +780,41 @@ extern "C" int chx_srv_submit(chx_srv* s, const chx_srv_req* r, uint64_t* ticket
     return CHX_OK;
 }
 
+namespace {
+// release a completed record; returns its status
+int release(Request& q, int64_t* latency_ns)
+{
+    if (latency_ns) *latency_ns = q.t_done - q.t_submit;
+    const bool failed = q.failed;
+    q.state.store(kFree, std::memory_order_release);
+    return failed ? fail(CHX_ECUDA, "the tick carrying this request failed on the device") : CHX_OK;
+}
+}  // namespace
+
 extern "C" int chx_srv_wait(chx_srv* s, uint64_t ticket, int64_t timeout_us, int64_t* latency_ns)
 {
     if (!s) return fail(CHX_EINVAL, "null server");
-    std::unique_lock<std::mutex> lk(s->mu);
-    auto it = s->reqs.find(ticket);
-    if (it == s->reqs.end()) return fail(CHX_EINVAL, "unknown ticket");
-    const auto deadline = Clock::now() + std::chrono::microseconds(timeout_us < 0 ? 0 : timeout_us);
-    while (!it->second.done) {
-        if (s->cv_done.wait_until(lk, deadline) == std::cv_status::timeout) {
-            it = s->reqs.find(ticket);
-            if (!it->second.done) return fail(CHX_ETIMEOUT, "request not finished within the timeout");
-        }
-        it = s->reqs.find(ticket);
+    Request& q = s->table[ticket & s->req_mask];
+    if (q.ticket.load(std::memory_order_acquire) != ticket || q.state.load(std::memory_order_acquire) == kFree)
+        return fail(CHX_EINVAL, "unknown ticket");
+    if (q.state.load(std::memory_order_acquire) != kDone) {
+        std::unique_lock<std::mutex> lk(s->mu);
+        const auto deadline = Clock::now() + std::chrono::microseconds(timeout_us < 0 ? 0 : timeout_us);
+        if (!s->cv_done.wait_until(lk, deadline, [&] { return q.state.load(std::memory_order_acquire) == kDone; }))
+            return fail(CHX_ETIMEOUT, "request not finished within the timeout");
     }
-    if (latency_ns) *latency_ns = it->second.t_done - it->second.t_submit;
-    const bool failed = it->second.failed;
-    s->reqs.erase(it);
-    return failed ? fail(CHX_ECUDA, "the tick carrying this request failed on the device") : CHX_OK;
+    return release(q, latency_ns);
 }
 
 extern "C" int chx_srv_test(chx_srv* s, uint64_t ticket, int32_t* h_done, int64_t* latency_ns)
 {
     if (!s || !h_done) return fail(CHX_EINVAL, "null argument");
-    std::lock_guard<std::mutex> lk(s->mu);
-    auto it = s->reqs.find(ticket);
-    if (it == s->reqs.end()) return fail(CHX_EINVAL, "unknown ticket");
-    *h_done = it->second.done ? 1 : 0;
-    if (it->second.done) {
-        if (latency_ns) *latency_ns = it->second.t_done - it->second.t_submit;
-        const bool failed = it->second.failed;
-        s->reqs.erase(it);
-        if (failed) return fail(CHX_ECUDA, "the tick carrying this request failed on the device");
-    }
-    return CHX_OK;
+    Request& q = s->table[ticket & s->req_mask];
+    if (q.ticket.load(std::memory_order_acquire) != ticket) return fail(CHX_EINVAL, "unknown ticket");
+    const int st = q.state.load(std::memory_order_acquire);
+    if (st == kFree) return fail(CHX_EINVAL, "unknown ticket");
+    *h_done = st == kDone ? 1 : 0;
+    return st == kDone ? release(q, latency_ns) : CHX_OK;
 }
 
 extern "C" int chx_srv_stats(chx_srv* s, chx_srv_stats_t* out)
