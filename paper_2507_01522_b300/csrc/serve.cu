@@ -24,6 +24,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <memory>
 #include <mutex>
 #include <random>
 #include <string>
@@ -111,9 +112,14 @@ struct chx_srv {
     std::vector<uint8_t> slot_cls;         // size class of each slot
     std::vector<int32_t> slot_nports;      // chargers of the station in each slot
     std::vector<int32_t> refs;             // queued or in-flight requests per station
-    std::vector<uint8_t> in_flight;
-    std::vector<uint32_t> scan_mark;
+    // stations of ticks on the device; set only by the scheduler (which reads
+    // it without the lock: a stale 1 merely delays a request to the next scan)
+    // and cleared by the completer
+    std::unique_ptr<std::atomic<uint8_t>[]> in_flight;
+    std::vector<uint32_t> scan_mark;       // submit: duplicate check (under the lock)
     uint32_t scan_gen = 0;
+    std::vector<uint32_t> sched_mark;      // scheduler: stations claimed by waiting requests
+    uint32_t sched_gen = 0;
     double used_bytes = 0.0;
     int n_resident = 0;
     cudaStream_t admin = nullptr;
@@ -192,8 +198,9 @@ int alloc_pool(chx_srv* s)
         for (int i = 0; i < b.cls_n_env[c]; ++i) s->slot_cls[b.cls_env_base[c] + i] = (uint8_t)c;
     s->slot_nports.assign(NS, 0);
     s->refs.assign(NS, 0);
-    s->in_flight.assign(NS, 0);
+    s->in_flight.reset(new std::atomic<uint8_t>[NS]());
     s->scan_mark.assign(NS, 0);
+    s->sched_mark.assign(NS, 0);
     for (int c = 0; c < kNumClasses; ++c) {
         s->free_slots[c].clear();
         for (int i = s->cap[c] - 1; i >= 0; --i) s->free_slots[c].push_back(b.cls_env_base[c] + i);
@@ -343,9 +350,11 @@ void scheduler(chx_srv* s)
 {
     cudaSetDevice(s->device);
     std::vector<Request*> rq;
+    std::deque<uint32_t> work, rest;
     uint64_t seen = ~0ULL;                 // events counter when nothing could be scheduled
     for (;;) {
         int ti = -1;
+        uint64_t events_at_take = 0;
         {
             std::unique_lock<std::mutex> lk(s->mu);
             s->cv_sched.wait(lk, [&] {
@@ -361,51 +370,70 @@ void scheduler(chx_srv* s)
                     ti = (int)i;
                     break;
                 }
-            Tick& t = s->ticks[ti];
-            // pack pending requests in arrival order; a request waits if one of
-            // its stations is in flight or claimed by an earlier waiting request
-            const uint32_t gen = next_scan(s);
-            rq.clear();
-            t.recs.clear();
-            int envs = 0;
-            int64_t act = 0, obs = 0;
-            int with_actions = -1;         // a tick is all-Philox or all-given actions
-            for (auto it = s->pending.begin(); it != s->pending.end();) {
-                Request& q = s->table[*it];
-                bool blocked = false;
-                for (int32_t e : q.envs)
-                    if (s->in_flight[e] || s->scan_mark[e] == gen) {
-                        blocked = true;
-                        break;
-                    }
-                const int wa = q.kind == CHX_SRV_STEP ? (q.actions.empty() ? 0 : 1) : -1;
-                const bool fits = envs + (int)q.envs.size() <= s->max_tick_envs &&
-                                  act + (int64_t)q.actions.size() <= s->max_tick_act &&
-                                  obs + q.obs_floats <= s->max_tick_obs &&
-                                  (wa < 0 || with_actions < 0 || wa == with_actions);
-                if (blocked || !fits) {
-                    for (int32_t e : q.envs) s->scan_mark[e] = gen;
-                    ++it;
-                    if (!fits && envs >= s->max_tick_envs) break;
-                    continue;
+            s->ticks[ti].busy = true;
+            work.swap(s->pending);         // take the queue; submissions continue meanwhile
+            events_at_take = s->events;
+        }
+        // pack in arrival order outside the lock; a request waits if one of its
+        // stations is in flight or claimed by an earlier waiting request
+        Tick& t = s->ticks[ti];
+        if (++s->sched_gen == 0) {
+            std::fill(s->sched_mark.begin(), s->sched_mark.end(), 0u);
+            s->sched_gen = 1;
+        }
+        const uint32_t gen = s->sched_gen;
+        rq.clear();
+        t.recs.clear();
+        rest.clear();
+        int envs = 0;
+        int64_t act = 0, obs = 0;
+        int with_actions = -1;             // a tick is all-Philox or all-given actions
+        bool full = false;
+        for (uint32_t ri : work) {
+            Request& q = s->table[ri];
+            if (full) {
+                rest.push_back(ri);
+                continue;
+            }
+            bool blocked = false;
+            for (int32_t e : q.envs)
+                if (s->in_flight[e].load(std::memory_order_relaxed) || s->sched_mark[e] == gen) {
+                    blocked = true;
+                    break;
                 }
-                if (wa >= 0) with_actions = wa;
-                for (int32_t e : q.envs) s->in_flight[e] = 1;
-                envs += (int)q.envs.size();
-                act += (int64_t)q.actions.size();
-                obs += q.obs_floats;
-                rq.push_back(&q);
-                t.recs.push_back(*it);
-                it = s->pending.erase(it);
+            const int wa = q.kind == CHX_SRV_STEP ? (q.actions.empty() ? 0 : 1) : -1;
+            const bool fits = envs + (int)q.envs.size() <= s->max_tick_envs &&
+                              act + (int64_t)q.actions.size() <= s->max_tick_act &&
+                              obs + q.obs_floats <= s->max_tick_obs &&
+                              (wa < 0 || with_actions < 0 || wa == with_actions);
+            if (blocked || !fits) {
+                for (int32_t e : q.envs) s->sched_mark[e] = gen;
+                rest.push_back(ri);
+                full = !fits && envs >= s->max_tick_envs;
+                continue;
+            }
+            if (wa >= 0) with_actions = wa;
+            for (int32_t e : q.envs) s->in_flight[e].store(1, std::memory_order_relaxed);
+            envs += (int)q.envs.size();
+            act += (int64_t)q.actions.size();
+            obs += q.obs_floats;
+            rq.push_back(&q);
+            t.recs.push_back(ri);
+        }
+        work.clear();
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            if (!rest.empty()) {           // waiting requests stay ahead of newer ones
+                rest.insert(rest.end(), s->pending.begin(), s->pending.end());
+                s->pending.swap(rest);
             }
             if (rq.empty()) {              // everything waits on in-flight stations
-                seen = s->events;
+                t.busy = false;
+                seen = events_at_take;
                 continue;
             }
             seen = ~0ULL;
-            t.busy = true;
         }
-        Tick& t = s->ticks[ti];
         t.failed = launch_tick(s, ti, rq) != CHX_OK;
         {
             std::lock_guard<std::mutex> lk(s->mu);
@@ -450,7 +478,7 @@ void completer(chx_srv* s)
             for (uint32_t ri : t.recs) {
                 Request& q = s->table[ri];
                 for (int32_t e : q.envs) {
-                    s->in_flight[e] = 0;
+                    s->in_flight[e].store(0, std::memory_order_relaxed);
                     s->refs[e] -= 1;
                 }
                 q.failed = t.failed;
