@@ -296,6 +296,11 @@ typedef struct chx_srv_stats_t {
     int32_t resident;               /* admitted stations                              */
     double used_bytes, budget_bytes;
     double device_busy_ms, elapsed_ms;
+    /* host time spent (ms) in: submissions holding the server lock, the
+     * scheduler's packing scans, building and launching ticks, delivering
+     * results; number of packing scans */
+    double host_submit_ms, host_scan_ms, host_launch_ms, host_complete_ms;
+    int64_t n_scans;
 } chx_srv_stats_t;
 
 /* Start a server on the current device: allocate the pool and tick buffers,

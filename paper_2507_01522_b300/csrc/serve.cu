@@ -142,6 +142,7 @@ struct chx_srv {
     uint64_t n_ticks = 0, n_requests = 0, n_env_steps = 0, n_resets = 0;
     double busy_ms = 0.0;
     int64_t t_start = 0;
+    std::atomic<int64_t> ns_submit{0}, ns_scan{0}, ns_launch{0}, ns_complete{0}, n_scans{0};
     int fused_blocks = 0, threads = 256;
 };
 
@@ -376,6 +377,7 @@ void scheduler(chx_srv* s)
         }
         // pack in arrival order outside the lock; a request waits if one of its
         // stations is in flight or claimed by an earlier waiting request
+        const int64_t t_scan0 = now_ns();
         Tick& t = s->ticks[ti];
         if (++s->sched_gen == 0) {
             std::fill(s->sched_mark.begin(), s->sched_mark.end(), 0u);
@@ -421,6 +423,8 @@ void scheduler(chx_srv* s)
             t.recs.push_back(ri);
         }
         work.clear();
+        s->ns_scan += now_ns() - t_scan0;
+        s->n_scans += 1;
         {
             std::lock_guard<std::mutex> lk(s->mu);
             if (!rest.empty()) {           // waiting requests stay ahead of newer ones
@@ -434,7 +438,9 @@ void scheduler(chx_srv* s)
             }
             seen = ~0ULL;
         }
+        const int64_t t_l0 = now_ns();
         t.failed = launch_tick(s, ti, rq) != CHX_OK;
+        s->ns_launch += now_ns() - t_l0;
         {
             std::lock_guard<std::mutex> lk(s->mu);
             s->launched.push_back(ti);
@@ -462,6 +468,7 @@ void completer(chx_srv* s)
             t.failed = true;
             ms = 0.f;
         }
+        const int64_t t_c0 = now_ns();
         // copy results to the requesters without the lock (records stay put and
         // are not released before they are marked done below)
         for (size_t r = 0; r < t.recs.size(); ++r) {
@@ -496,6 +503,7 @@ void completer(chx_srv* s)
             t.busy = false;
             t.recs.clear();
         }
+        s->ns_complete += now_ns() - t_c0;
         s->cv_done.notify_all();
         s->cv_sched.notify_one();
     }
@@ -761,6 +769,7 @@ extern "C" int chx_srv_submit(chx_srv* s, const chx_srv_req* r, uint64_t* ticket
     if (r->n_envs < 1 || r->n_envs > s->max_tick_envs || !r->h_env_ids)
         return fail(CHX_EINVAL, "n_envs must be in 1..max_tick_envs");
     std::unique_lock<std::mutex> lk(s->mu);
+    const int64_t t_in = now_ns();
     if (s->stopping) return fail(CHX_EINVAL, "server is stopping");
     const uint64_t tk = s->next_ticket;
     const uint32_t ri = (uint32_t)(tk & s->req_mask);
@@ -803,6 +812,7 @@ extern "C" int chx_srv_submit(chx_srv* s, const chx_srv_req* r, uint64_t* ticket
     s->pending.push_back(ri);
     s->events += 1;
     *ticket = tk;
+    s->ns_submit += now_ns() - t_in;
     lk.unlock();
     s->cv_sched.notify_one();
     return CHX_OK;
@@ -858,6 +868,11 @@ extern "C" int chx_srv_stats(chx_srv* s, chx_srv_stats_t* out)
     out->budget_bytes = s->cfg.hbm_budget_bytes;
     out->device_busy_ms = s->busy_ms;
     out->elapsed_ms = (double)(now_ns() - s->t_start) * 1e-6;
+    out->host_submit_ms = s->ns_submit.load() * 1e-6;
+    out->host_scan_ms = s->ns_scan.load() * 1e-6;
+    out->host_launch_ms = s->ns_launch.load() * 1e-6;
+    out->host_complete_ms = s->ns_complete.load() * 1e-6;
+    out->n_scans = s->n_scans.load();
     return CHX_OK;
 }
 
