@@ -401,7 +401,7 @@ def run_serving(args, rank):
             "env_steps_per_s": res["env_steps_per_s"], "requests": res["n_requests"],
             "mean_tick_envs": res["mean_tick_envs"], "device_busy_frac": res["device_busy_frac"],
             "seconds": res["seconds"],
-            "host_ms": {k: round(st[k], 1) for k in ("host_submit_ms", "host_scan_ms", "host_launch_ms",
+            "host_ms": {k: round(st[k], 1) for k in ("host_submit_ms", "host_scan_ms", "host_pack_ms", "host_launch_ms",
                                                       "host_complete_ms", "elapsed_ms", "device_busy_ms")},
             "ticks": st["n_ticks"], "scans": st["n_scans"]}
 

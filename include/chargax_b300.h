@@ -297,9 +297,10 @@ typedef struct chx_srv_stats_t {
     double used_bytes, budget_bytes;
     double device_busy_ms, elapsed_ms;
     /* host time spent (ms) in: submissions holding the server lock, the
-     * scheduler's packing scans, building and launching ticks, delivering
-     * results; number of packing scans */
-    double host_submit_ms, host_scan_ms, host_launch_ms, host_complete_ms;
+     * scheduler's scans choosing requests, packing tick buffers, packing plus
+     * launching ticks (includes the packing), delivering results; number of
+     * scans */
+    double host_submit_ms, host_scan_ms, host_pack_ms, host_launch_ms, host_complete_ms;
     int64_t n_scans;
 } chx_srv_stats_t;
 

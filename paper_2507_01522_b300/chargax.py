@@ -77,7 +77,8 @@ class _SrvStats(C.Structure):
     _fields_ = [("n_ticks", C.c_int64), ("n_requests", C.c_int64), ("env_steps", C.c_int64),
                 ("env_resets", C.c_int64), ("resident", C.c_int32), ("used_bytes", C.c_double),
                 ("budget_bytes", C.c_double), ("device_busy_ms", C.c_double), ("elapsed_ms", C.c_double),
-                ("host_submit_ms", C.c_double), ("host_scan_ms", C.c_double), ("host_launch_ms", C.c_double),
+                ("host_submit_ms", C.c_double), ("host_scan_ms", C.c_double), ("host_pack_ms", C.c_double),
+                ("host_launch_ms", C.c_double),
                 ("host_complete_ms", C.c_double), ("n_scans", C.c_int64)]
 
 

@@ -91,7 +91,6 @@ struct Tick {
     int* d_counter = nullptr;
     std::vector<uint32_t> recs;             // request records in this tick
     std::vector<int64_t> rew_off, obs_off;  // per record: where its outputs start in the tick buffers
-    std::vector<int4> per_cls[kNumClasses];
     bool busy = false;
     bool failed = false;
 };
@@ -142,7 +141,7 @@ struct chx_srv {
     uint64_t n_ticks = 0, n_requests = 0, n_env_steps = 0, n_resets = 0;
     double busy_ms = 0.0;
     int64_t t_start = 0;
-    std::atomic<int64_t> ns_submit{0}, ns_scan{0}, ns_launch{0}, ns_complete{0}, n_scans{0};
+    std::atomic<int64_t> ns_submit{0}, ns_scan{0}, ns_pack{0}, ns_launch{0}, ns_complete{0}, n_scans{0};
     int fused_blocks = 0, threads = 256;
 };
 
@@ -255,8 +254,9 @@ inline int class_of_slot_host(const chx_srv* s, int slot) { return s->slot_cls[s
 int launch_tick(chx_srv* s, int ti, const std::vector<Request*>& rq)
 {
     Tick& t = s->ticks[ti];
-    auto& per_cls = t.per_cls;
-    for (auto& L : per_cls) L.clear();
+    const int64_t t_p0 = now_ns();
+    // pass 1: stations per class, output and observation offsets per request
+    int count[kNumClasses] = {};
     int n_reset = 0;
     int64_t act_used = 0, rew_used = 0, obs_used = 0;
     t.rew_off.assign(rq.size(), 0);
@@ -273,25 +273,51 @@ int launch_tick(chx_srv* s, int ti, const std::vector<Request*>& rq)
         }
         t.rew_off[r] = rew_used;
         t.obs_off[r] = obs_used;
+        for (int32_t e : q.envs) count[s->slot_cls[e]] += 1;
+        rew_used += (int64_t)q.envs.size();
+        if (q.h_obs) obs_used += q.obs_floats;
+    }
+    // schedule: largest class first, each class padded to whole tiles
+    FusedIO io{};
+    int cursor[kNumClasses] = {};
+    int n_entries = 0, tb = 0;
+    io.n_sched = 0;
+    for (int c = kNumClasses - 1; c >= 0; --c) {
+        if (count[c] == 0) continue;
+        const int C = 8 << c;
+        const int epw = C >= 32 ? 1 : 32 / C;
+        const int padded = (count[c] + epw - 1) / epw * epw;
+        io.gather_base[c] = n_entries;
+        cursor[c] = n_entries;
+        for (int i = count[c]; i < padded; ++i) t.h_entries[n_entries + i] = make_int4(s->pad_slot[c], 0, 0, 0);
+        n_entries += padded;
+        io.sched_cls[io.n_sched] = c;
+        io.sched_tile_base[io.n_sched] = tb;
+        io.n_sched++;
+        tb += padded / epw;
+    }
+    io.sched_tile_base[io.n_sched] = tb;
+    io.total_tiles = tb;
+    // pass 2: entries straight into the pinned buffer, actions concatenated
+    for (size_t r = 0; r < rq.size(); ++r) {
+        Request& q = *rq[r];
+        if (q.kind == CHX_SRV_RESET) continue;
         int64_t act_base = -1;
         if (!q.actions.empty()) {
             std::memcpy(t.h_act + act_used, q.actions.data(), q.actions.size());
             act_base = act_used;
             act_used += (int64_t)q.actions.size();
         }
-        int64_t obs_pos = obs_used;
+        int64_t obs_pos = t.obs_off[r];
+        const int out0 = (int)t.rew_off[r];
         for (size_t j = 0; j < q.envs.size(); ++j) {
             const int slot = q.envs[j];
-            const int c = class_of_slot_host(s, slot);
+            const int c = s->slot_cls[slot];
             const int ao = act_base >= 0 ? (int)(act_base + q.act_off[j]) : 0;
-            per_cls[c].push_back(make_int4(slot, ao, (int)(rew_used + (int64_t)j), (int)obs_pos));
+            t.h_entries[cursor[c]++] = make_int4(slot, ao, out0 + (int)j, (int)obs_pos);
             if (q.h_obs) obs_pos += 8 + 6 * (int64_t)(q.act_off[j + 1] - q.act_off[j]);
         }
-        rew_used += (int64_t)q.envs.size();
-        if (q.h_obs) obs_used = obs_pos;
     }
-    // schedule: largest class first, each class padded to whole tiles
-    FusedIO io{};
     io.k_steps = 1;
     // a tick is either all Philox actions or all given actions (the scheduler
     // never mixes them), so io.actions applies to every entry
@@ -303,24 +329,7 @@ int launch_tick(chx_srv* s, int ti, const std::vector<Request*>& rq)
     io.obs = obs_used > 0 ? t.d_obs : nullptr;
     io.counter = t.d_counter;
     io.gather = t.d_entries;
-    int n_entries = 0, tb = 0;
-    io.n_sched = 0;
-    for (int c = kNumClasses - 1; c >= 0; --c) {
-        auto& L = per_cls[c];
-        if (L.empty()) continue;
-        const int C = 8 << c;
-        const int epw = C >= 32 ? 1 : 32 / C;
-        while (L.size() % epw) L.push_back(make_int4(s->pad_slot[c], 0, 0, 0));
-        io.gather_base[c] = n_entries;
-        std::memcpy(t.h_entries + n_entries, L.data(), L.size() * sizeof(int4));
-        n_entries += (int)L.size();
-        io.sched_cls[io.n_sched] = c;
-        io.sched_tile_base[io.n_sched] = tb;
-        io.n_sched++;
-        tb += (int)L.size() / epw;
-    }
-    io.sched_tile_base[io.n_sched] = tb;
-    io.total_tiles = tb;
+    s->ns_pack += now_ns() - t_p0;
     cudaStream_t st = t.st;
     SRV_TRY(cudaEventRecord(t.ev_start, st));
     if (n_reset > 0) {
@@ -870,6 +879,7 @@ extern "C" int chx_srv_stats(chx_srv* s, chx_srv_stats_t* out)
     out->elapsed_ms = (double)(now_ns() - s->t_start) * 1e-6;
     out->host_submit_ms = s->ns_submit.load() * 1e-6;
     out->host_scan_ms = s->ns_scan.load() * 1e-6;
+    out->host_pack_ms = s->ns_pack.load() * 1e-6;
     out->host_launch_ms = s->ns_launch.load() * 1e-6;
     out->host_complete_ms = s->ns_complete.load() * 1e-6;
     out->n_scans = s->n_scans.load();
