@@ -42,7 +42,9 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-envs", type=int, default=1 << 20, help="resident stations of the serving leg")
     ap.add_argument("--serve-actors", type=int, default=4096)
-    ap.add_argument("--serve-think-us", type=float, default=2000.0, help="mean think time of a simulated actor")
+    ap.add_argument("--serve-think-us", type=float, default=0.0,
+                    help="mean think time of a simulated actor (0: chosen for --serve-load of peak throughput)")
+    ap.add_argument("--serve-load", type=float, default=0.7, help="offered load as a fraction of peak throughput")
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--shape", default="", help="K,W: fixed steps per launch and warps per block (skips the autotuner)")
     return ap.parse_args()
@@ -389,13 +391,24 @@ def run_serving(args, rank):
     t_admit = time.perf_counter() - t0
     per = args.serve_envs // args.serve_actors
     threads = max(2, min(16, (os.cpu_count() or 8) // 2))
-    res = srv.simulate(ids, n_actors=args.serve_actors, envs_per_actor=per, mean_think_us=args.serve_think_us,
-                       duration_s=args.serve_seconds, warmup_s=1.0, n_threads=threads, seed=rank)
+    # peak: every actor resubmits at once (no think time)
+    peak = srv.simulate(ids, n_actors=args.serve_actors, envs_per_actor=per, mean_think_us=0.0,
+                        duration_s=2.0, warmup_s=0.5, n_threads=threads, seed=rank)
+    x_peak = peak["n_requests"] / peak["seconds"]
+    # latency at a stated load: closed loop, think time Z with N / (Z + R) = load * peak
+    think = args.serve_think_us or args.serve_actors / (args.serve_load * x_peak) * 1e6
+    res = srv.simulate(ids, n_actors=args.serve_actors, envs_per_actor=per, mean_think_us=think,
+                       duration_s=args.serve_seconds, warmup_s=1.0, n_threads=threads, seed=rank + 1)
     st = srv.stats()
     srv.stop()
     return {"workload": w.name, "resident_stations": int(st["resident"]), "chargers": int(w.stations.total_ports),
             "pool_bytes_admitted": st["used_bytes"], "hbm_budget_bytes": st["budget_bytes"],
-            "actors": args.serve_actors, "envs_per_request": per, "mean_think_us": args.serve_think_us,
+            "actors": args.serve_actors, "envs_per_request": per, "mean_think_us": round(think, 1),
+            "offered_load": "think time for %.0f %% of peak request rate" % (100 * args.serve_load)
+            if not args.serve_think_us else "fixed think time",
+            "peak": {"env_steps_per_s": peak["env_steps_per_s"], "requests_per_s": x_peak,
+                     "p50_us": peak["p50_us"], "p99_us": peak["p99_us"],
+                     "device_busy_frac": peak["device_busy_frac"]},
             "host_threads": threads, "admit_s": round(t_admit, 3),
             "p50_us": res["p50_us"], "p90_us": res["p90_us"], "p99_us": res["p99_us"], "max_us": res["max_us"],
             "env_steps_per_s": res["env_steps_per_s"], "requests": res["n_requests"],

@@ -107,10 +107,15 @@ struct chx_srv {
     int cap[kNumClasses] = {};
     int pad_slot[kNumClasses] = {};
     std::vector<int> free_slots[kNumClasses];
-    std::vector<uint8_t> admitted;
-    std::vector<uint8_t> slot_cls;         // size class of each slot
-    std::vector<int32_t> slot_nports;      // chargers of the station in each slot
-    std::vector<int32_t> refs;             // queued or in-flight requests per station
+    // per slot, one 8-byte record so that a request touches one cache line
+    // per station: admitted flag, size class, charger count, queued or
+    // in-flight requests (the last three under the server lock)
+    struct SlotInfo {
+        uint8_t admitted, cls;
+        uint16_t nports;
+        int32_t refs;
+    };
+    std::vector<SlotInfo> slot;
     // stations of ticks on the device; set only by the scheduler (which reads
     // it without the lock: a stale 1 merely delays a request to the next scan)
     // and cleared by the completer
@@ -192,12 +197,9 @@ int alloc_pool(chx_srv* s)
 #undef PA
     std::vector<int32_t> minus1(NS, -1);
     SRV_TRY(cudaMemcpy(b.user_id, minus1.data(), NS * sizeof(int32_t), cudaMemcpyHostToDevice));
-    s->admitted.assign(NS, 0);
-    s->slot_cls.assign(NS, 0);
+    s->slot.assign(NS, chx_srv::SlotInfo{0, 0, 0, 0});
     for (int c = 0; c < kNumClasses; ++c)
-        for (int i = 0; i < b.cls_n_env[c]; ++i) s->slot_cls[b.cls_env_base[c] + i] = (uint8_t)c;
-    s->slot_nports.assign(NS, 0);
-    s->refs.assign(NS, 0);
+        for (int i = 0; i < b.cls_n_env[c]; ++i) s->slot[b.cls_env_base[c] + i].cls = (uint8_t)c;
     s->in_flight.reset(new std::atomic<uint8_t>[NS]());
     s->scan_mark.assign(NS, 0);
     s->sched_mark.assign(NS, 0);
@@ -247,7 +249,7 @@ void free_tick(Tick& t)
     t = Tick{};
 }
 
-inline int class_of_slot_host(const chx_srv* s, int slot) { return s->slot_cls[slot]; }
+inline int class_of_slot_host(const chx_srv* s, int slot) { return s->slot[slot].cls; }
 
 // Pack and launch one tick on ticks[ti] with the requests the scheduler chose.
 // Runs without the server lock (the requests and their stations are reserved).
@@ -273,7 +275,7 @@ int launch_tick(chx_srv* s, int ti, const std::vector<Request*>& rq)
         }
         t.rew_off[r] = rew_used;
         t.obs_off[r] = obs_used;
-        for (int32_t e : q.envs) count[s->slot_cls[e]] += 1;
+        for (int32_t e : q.envs) count[s->slot[e].cls] += 1;
         rew_used += (int64_t)q.envs.size();
         if (q.h_obs) obs_used += q.obs_floats;
     }
@@ -312,7 +314,7 @@ int launch_tick(chx_srv* s, int ti, const std::vector<Request*>& rq)
         const int out0 = (int)t.rew_off[r];
         for (size_t j = 0; j < q.envs.size(); ++j) {
             const int slot = q.envs[j];
-            const int c = s->slot_cls[slot];
+            const int c = s->slot[slot].cls;
             const int ao = act_base >= 0 ? (int)(act_base + q.act_off[j]) : 0;
             t.h_entries[cursor[c]++] = make_int4(slot, ao, out0 + (int)j, (int)obs_pos);
             if (q.h_obs) obs_pos += 8 + 6 * (int64_t)(q.act_off[j + 1] - q.act_off[j]);
@@ -495,7 +497,7 @@ void completer(chx_srv* s)
                 Request& q = s->table[ri];
                 for (int32_t e : q.envs) {
                     s->in_flight[e].store(0, std::memory_order_relaxed);
-                    s->refs[e] -= 1;
+                    s->slot[e].refs -= 1;
                 }
                 q.failed = t.failed;
                 q.t_done = tn;
@@ -709,8 +711,8 @@ extern "C" int chx_srv_admit(chx_srv* s, const chx_stations* st, uint64_t seed, 
                 ginv[poff[e] + q] = (float)(1.0 / eta);
             }
         }
-        s->admitted[slots[e]] = 1;
-        s->slot_nports[slots[e]] = n;
+        s->slot[slots[e]].admitted = 1;
+        s->slot[slots[e]].nports = (uint16_t)n;
         s->used_bytes += slot_bytes(c);
         s->n_resident += 1;
         po += n;
@@ -748,8 +750,8 @@ extern "C" int chx_srv_evict(chx_srv* s, const int32_t* h_ids, int32_t n)
     std::lock_guard<std::mutex> lk(s->mu);
     for (int j = 0; j < n; ++j) {
         const int e = h_ids[j];
-        if (e < 0 || e >= s->b.n_slots || !s->admitted[e]) return fail(CHX_EINVAL, "station id not admitted");
-        if (s->refs[e] > 0) return fail(CHX_EINVAL, "station has queued or in-flight requests");
+        if (e < 0 || e >= s->b.n_slots || !s->slot[e].admitted) return fail(CHX_EINVAL, "station id not admitted");
+        if (s->slot[e].refs > 0) return fail(CHX_EINVAL, "station has queued or in-flight requests");
     }
     DevBatch& b = s->b;
     const int32_t minus1 = -1;
@@ -762,8 +764,8 @@ extern "C" int chx_srv_evict(chx_srv* s, const int32_t* h_ids, int32_t n)
         SRV_TRY(cudaMemsetAsync(b.trem + pb, 0, C, s->admin));
         SRV_TRY(cudaMemcpyAsync(b.user_id + e, &minus1, 4, cudaMemcpyHostToDevice, s->admin));
         SRV_TRY(cudaStreamSynchronize(s->admin));
-        s->admitted[e] = 0;
-        s->slot_nports[e] = 0;
+        s->slot[e].admitted = 0;
+        s->slot[e].nports = 0;
         s->free_slots[c].push_back(e);
         s->used_bytes -= slot_bytes(c);
         s->n_resident -= 1;
@@ -777,6 +779,12 @@ extern "C" int chx_srv_submit(chx_srv* s, const chx_srv_req* r, uint64_t* ticket
     if (r->kind != CHX_SRV_STEP && r->kind != CHX_SRV_RESET) return fail(CHX_EINVAL, "unknown request kind");
     if (r->n_envs < 1 || r->n_envs > s->max_tick_envs || !r->h_env_ids)
         return fail(CHX_EINVAL, "n_envs must be in 1..max_tick_envs");
+    // copy the request's inputs before taking the lock
+    thread_local std::vector<int32_t> envs;
+    thread_local std::vector<int8_t> actions;
+    envs.assign(r->h_env_ids, r->h_env_ids + r->n_envs);
+    for (int32_t e : envs)
+        if (e < 0 || e >= s->b.n_slots) return fail(CHX_EINVAL, "station id out of range");
     std::unique_lock<std::mutex> lk(s->mu);
     const int64_t t_in = now_ns();
     if (s->stopping) return fail(CHX_EINVAL, "server is stopping");
@@ -785,35 +793,40 @@ extern "C" int chx_srv_submit(chx_srv* s, const chx_srv_req* r, uint64_t* ticket
     Request& q = s->table[ri];
     if (q.state.load(std::memory_order_acquire) != kFree)
         return fail(CHX_ENOMEM, "too many outstanding requests: release tickets with chx_srv_wait or chx_srv_test");
-    // the record is free: fill it under the lock, publish it last
+    // check the stations (admitted, listed once) and their charger offsets
+    const uint32_t gen = next_scan(s);
+    q.act_off.resize(envs.size() + 1);
+    q.act_off[0] = 0;
+    for (size_t j = 0; j < envs.size(); ++j) {
+        const int32_t e = envs[j];
+        const chx_srv::SlotInfo& si = s->slot[e];
+        if (!si.admitted) return fail(CHX_EINVAL, "station id not admitted");
+        if (s->scan_mark[e] == gen) return fail(CHX_EINVAL, "station listed twice in one request");
+        s->scan_mark[e] = gen;
+        q.act_off[j + 1] = q.act_off[j] + si.nports;
+    }
+    int64_t obs_floats = 0;
+    actions.clear();
+    if (r->kind == CHX_SRV_STEP) {
+        if (r->h_actions) {
+            actions.assign(r->h_actions, r->h_actions + q.act_off.back());
+            for (int8_t a : actions)
+                if (a < 0 || a >= s->params.n_levels) return fail(CHX_EINVAL, "action level out of range");
+        }
+        if (r->h_obs) obs_floats = 8LL * (int64_t)envs.size() + 6LL * q.act_off.back();
+        if (obs_floats > s->max_tick_obs) return fail(CHX_EINVAL, "observation larger than max_tick_obs_floats");
+    }
+    // the record is free: fill it, publish it last
     q.kind = r->kind;
-    q.envs.assign(r->h_env_ids, r->h_env_ids + r->n_envs);
+    q.envs.swap(envs);
+    q.actions.swap(actions);
     q.h_reward = r->h_reward;
     q.h_done = r->h_done;
     q.h_obs = r->kind == CHX_SRV_STEP ? r->h_obs : nullptr;
     q.seed = r->seed;
     q.failed = false;
-    q.obs_floats = 0;
-    q.actions.clear();
-    q.act_off.assign(q.envs.size() + 1, 0);
-    const uint32_t gen = next_scan(s);
-    for (size_t j = 0; j < q.envs.size(); ++j) {
-        const int32_t e = q.envs[j];
-        if (e < 0 || e >= s->b.n_slots || !s->admitted[e]) return fail(CHX_EINVAL, "station id not admitted");
-        if (s->scan_mark[e] == gen) return fail(CHX_EINVAL, "station listed twice in one request");
-        s->scan_mark[e] = gen;
-        q.act_off[j + 1] = q.act_off[j] + s->slot_nports[e];
-    }
-    if (q.kind == CHX_SRV_STEP) {
-        if (r->h_actions) {
-            q.actions.assign(r->h_actions, r->h_actions + q.act_off.back());
-            for (int8_t a : q.actions)
-                if (a < 0 || a >= s->params.n_levels) return fail(CHX_EINVAL, "action level out of range");
-        }
-        if (q.h_obs) q.obs_floats = 8LL * (int64_t)q.envs.size() + 6LL * q.act_off.back();
-        if (q.obs_floats > s->max_tick_obs) return fail(CHX_EINVAL, "observation larger than max_tick_obs_floats");
-    }
-    for (int32_t e : q.envs) s->refs[e] += 1;
+    q.obs_floats = obs_floats;
+    for (int32_t e : q.envs) s->slot[e].refs += 1;
     q.t_submit = now_ns();
     q.ticket.store(tk, std::memory_order_relaxed);
     q.state.store(kQueued, std::memory_order_release);
@@ -972,7 +985,7 @@ extern "C" int chx_srv_simulate(chx_srv* s, const chx_srv_sim_cfg* c, const int3
                     idle = false;
                 }
             }
-            if (idle) std::this_thread::yield();
+            if (idle) std::this_thread::sleep_for(std::chrono::microseconds(20));
         }
         for (auto& x : actors)            // drain
             if (x.busy) chx_srv_wait(s, x.ticket, 30000000, nullptr);
