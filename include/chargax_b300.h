@@ -192,10 +192,10 @@ int chx_step_host(chx_handle* h, const int8_t* h_actions, float* h_reward, uint8
  * driver's allocator, or hosts that reserve all device memory up front.)
  * Same transitions and outputs as chx_rollout (Philox actions, fused launches
  * of the handle's steps per launch and warps per block), launched directly
- * without a CUDA graph.  The call allocates nothing: its only scratch, one
- * work counter per launch, lives in a 4 KB static device array of
- * CHX_NOALLOC_MAX_LAUNCHES counters that every GPU loading this library keeps
- * until the process exits.  n_steps may need at most that many launches
+ * without a CUDA graph.  The call allocates nothing: its only scratch, the
+ * work counters of each launch (two per launch), lives in an 8 KB static
+ * device array that every GPU loading this library keeps until the process
+ * exits.  n_steps may need at most that many launches
  * (ceil(n_steps / steps per launch)); more returns CHX_EINVAL.
  *   - The first call on a device looks up the array's device address (with
  *     that device current) and caches it; make that first call before any

@@ -18,6 +18,7 @@ namespace chx {
 constexpr int kWarp = 32;
 constexpr int kNumClasses = 5;             // 8, 16, 32, 64, 128
 constexpr int kPoissonMax = 127;
+constexpr int kCdfLen = 128;               // CDF entries per (row, step): F_0..F_126, then +inf
 constexpr uint32_t kPurposeArrival = 0u, kPurposeCar = 1u, kPurposeAction = 2u, kPurposeDay = 3u;
 
 // per-charger static bits
@@ -55,7 +56,8 @@ struct DevBatch {
     uint32_t *st_arrived, *st_rejected;
     float *st_missing, *st_charged;
     // exogenous tables
-    const float *price, *lam, *exp_neg_lam;
+    const float* price;                    // [days][T] buy price
+    const float* cdf;                      // [rows][T][kCdfLen] Poisson CDF of the arrival count
     // classes (index 0..4 = size 8..128)
     int cls_n_env[kNumClasses];            // padded station count
     int cls_env_base[kNumClasses];
@@ -101,21 +103,18 @@ __device__ __forceinline__ int random_level(uint4 words, uint32_t g, int n_level
 }
 
 // ---------------------------------------------------------------------------
-// Poisson count by inverse transform.  The count is an integer chosen by
-// floating point, so this exact sequence of correctly rounded FP32 operations
-// (explicit _rn intrinsics: no contraction into FMA) is the definition;
-// exp(-lambda) comes precomputed from the host in double, rounded once.
+// Poisson count by inverse transform: the smallest k with u < F_k, at most
+// 127.  The count is an integer chosen by floating point, so F is defined by
+// one exact sequence of correctly rounded FP32 operations (exp(-lambda) in
+// double rounded once, p_k = (p_{k-1} * lambda) / k, F_k = F_{k-1} + p_k),
+// evaluated on the host into a table per (arrival row, step of day) whose
+// entry 127 is +inf; the kernel compares u against it.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int poisson_count(float lam, float e0, uint32_t w)
+__device__ __forceinline__ int poisson_count(const float* __restrict__ F, uint32_t w)
 {
     const float u = __fmul_rn(__uint2float_rn(w >> 8), 0x1p-24f);
-    float pk = e0, cdf = e0;
     int k = 0;
-    while (u >= cdf && k < kPoissonMax) {
-        k += 1;
-        pk = __fdiv_rn(__fmul_rn(pk, lam), __int2float_rn(k));
-        cdf = __fadd_rn(cdf, pk);
-    }
+    while (u >= __ldg(F + k)) ++k;
     return k;
 }
 
@@ -165,8 +164,8 @@ __device__ __forceinline__ int arrivals(const DevBatch& b, const DevParams& p, u
                                         uint32_t k0, uint32_t k1)
 {
     const uint4 w = philox4x32_10(make_uint4(uid, g, 0u, kPurposeArrival), k0, k1);
-    const size_t ix = (size_t)cls_row * (size_t)p.ep_len + (size_t)t;
-    return poisson_count(__ldg(b.lam + ix), __ldg(b.exp_neg_lam + ix), w.x);
+    const size_t row = ((size_t)cls_row * (size_t)p.ep_len + (size_t)t) * kCdfLen;
+    return poisson_count(b.cdf + row, w.x);
 }
 
 // observation features of a station (8 floats) and of one charger (6 floats)

@@ -67,6 +67,8 @@ int class_of_ports(int n);
 int validate_params(const chx_env_params* p, const chx_exo* x);
 int validate_stations(const chx_stations* st, const chx_exo* x, long long max_envs);
 DevParams make_params(const chx_env_params& q, int n_days);
+// Poisson CDF table of the arrival counts for n_rows_steps means (see poisson_count)
+void build_poisson_cdf(const float* lam, size_t n_rows_steps, std::vector<float>& F);
 int build_handle(const chx_stations* st, const chx_env_params* prm, const chx_exo* exo, uint64_t seed,
                  int min_pad_envs_per_class, chx_handle** out);
 int enqueue_fused(chx_handle* h, int k_steps, const int8_t* actions, long long lda, float* reward, uint8_t* done,

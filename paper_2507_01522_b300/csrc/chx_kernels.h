@@ -32,9 +32,15 @@ struct FusedIO {
 
 void launch_step_plain(const DevBatch& b, const DevParams& p, const int8_t* actions, long long lda, float* reward,
                        uint8_t* done, const int* slot_list, int n_list, cudaStream_t st);
-void launch_step_fused(const DevBatch& b, const DevParams& p, const FusedIO& io, int blocks, int threads,
+// The fused step over io's schedule: the 128-charger class (if any) by one
+// persistent kernel, the other classes by a second one, each grid sized to
+// the resident blocks on sm_count SMs.  io.counter must point to
+// kFusedCounters zeroed ints (one work counter per kernel).
+constexpr int kFusedCounters = 2;
+void launch_step_fused(const DevBatch& b, const DevParams& p, const FusedIO& io, int threads, int sm_count,
                        cudaStream_t st);
-int fused_max_blocks_per_sm(int threads);
+// both fused kernels can be resident with blocks of `threads` threads
+bool fused_block_size_ok(int threads);
 
 // reset the stations whose batch ids are listed (NULL = all)
 void launch_reset(const DevBatch& b, const DevParams& p, const int32_t* user_to_slot, const int32_t* env_ids, int n,

@@ -138,6 +138,25 @@ int validate(const chx_stations* st, const chx_env_params* p, const chx_exo* x)
     return validate_stations(st, x, 1LL << 26);
 }
 
+void build_poisson_cdf(const float* lam, size_t n_rows_steps, std::vector<float>& F)
+{
+    F.assign(n_rows_steps * kCdfLen, 0.f);
+    for (size_t i = 0; i < n_rows_steps; ++i) {
+        float* f = F.data() + i * kCdfLen;
+        const float l = lam[i];
+        float pk = (float)std::exp(-(double)l);
+        float cdf = pk;
+        f[0] = cdf;
+        for (int k = 1; k < kPoissonMax; ++k) {
+            const float num = pk * l;           // separate statements: no contraction
+            pk = num / (float)k;
+            cdf = cdf + pk;
+            f[k] = cdf;
+        }
+        f[kPoissonMax] = INFINITY;
+    }
+}
+
 DevParams make_params(const chx_env_params& q, int n_days)
 {
     DevParams p{};
@@ -298,17 +317,15 @@ int build_handle(const chx_stations* st, const chx_env_params* prm, const chx_ex
     ALLOC(b.st_arrived, NS) ALLOC(b.st_rejected, NS) ALLOC(b.st_missing, NS) ALLOC(b.st_charged, NS)
     ALLOC(h->d_user_to_slot, E) ALLOC(h->d_counter, 64) ALLOC(b.err, 1)
     const size_t nprice = (size_t)exo->n_days * prm->ep_len, nlam = (size_t)exo->n_arrival_classes * prm->ep_len;
-    float *price = nullptr, *lam = nullptr, *elam = nullptr;
-    ALLOC(price, nprice) ALLOC(lam, nlam) ALLOC(elam, nlam)
+    float *price = nullptr, *cdf = nullptr;
+    ALLOC(price, nprice) ALLOC(cdf, nlam * kCdfLen)
 #undef ALLOC
     b.price = price;
-    b.lam = lam;
-    b.exp_neg_lam = elam;
-    std::vector<float> e0(nlam);
-    for (size_t i = 0; i < nlam; ++i) e0[i] = (float)std::exp(-(double)exo->h_arrival_rate[i]);
+    b.cdf = cdf;
+    std::vector<float> F;
+    build_poisson_cdf(exo->h_arrival_rate, nlam, F);
     CUDA_TRY(cudaMemcpy(price, exo->h_price, nprice * sizeof(float), cudaMemcpyHostToDevice));
-    CUDA_TRY(cudaMemcpy(lam, exo->h_arrival_rate, nlam * sizeof(float), cudaMemcpyHostToDevice));
-    CUDA_TRY(cudaMemcpy(elam, e0.data(), nlam * sizeof(float), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(cdf, F.data(), F.size() * sizeof(float), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(b.meta, meta.data(), PS * sizeof(uint32_t), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(b.gcap, gcap.data(), PS * sizeof(float), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(b.ginv_eta, ginv.data(), PS * sizeof(float), cudaMemcpyHostToDevice));
@@ -449,12 +466,9 @@ int enqueue_fused(chx_handle* h, int k_steps, const int8_t* actions, long long l
     io.ld_out = ld_out;
     io.obs = obs;
     const int threads = warps * 32;
-    const int per_sm = fused_max_blocks_per_sm(threads);
-    if (per_sm <= 0) return fail(CHX_ECUDA, "fused kernel cannot be resident with this block size");
-    const int tiles_blocks = (io.total_tiles + warps - 1) / warps;
-    const int blocks = std::max(1, std::min(per_sm * h->sm_count, tiles_blocks));
-    CUDA_TRY(cudaMemsetAsync(h->d_counter, 0, sizeof(int), st));
-    launch_step_fused(h->b, h->dp, io, blocks, threads, st);
+    if (!fused_block_size_ok(threads)) return fail(CHX_ECUDA, "fused kernel cannot be resident with this block size");
+    CUDA_TRY(cudaMemsetAsync(h->d_counter, 0, kFusedCounters * sizeof(int), st));
+    launch_step_fused(h->b, h->dp, io, threads, h->sm_count, st);
     CUDA_TRY(cudaGetLastError());
     return CHX_OK;
 }
@@ -664,13 +678,13 @@ extern "C" int chx_autotune(chx_handle* h, int32_t n_steps, int32_t* h_steps_per
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const int ks[] = {4, 8, 16, 32, 48, 72, 96, 144, 288};
+    const int ks[] = {8, 16, 32, 72, 144, 288};
     const int ws[] = {2, 4, 8};
     float best = 1e30f;
     int best_k = h->steps_per_launch, best_w = h->warps_per_block;
     const int old_k = h->steps_per_launch, old_w = h->warps_per_block;
     for (int w : ws) {
-        if (fused_max_blocks_per_sm(w * 32) <= 0) continue;
+        if (!fused_block_size_ok(w * 32)) continue;
         for (int k : ks) {
             if (k > n_steps && k != ks[0]) continue;
             h->steps_per_launch = k;

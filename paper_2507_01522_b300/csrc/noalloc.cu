@@ -20,9 +20,9 @@ namespace {
 
 constexpr int kMaxDevices = 64;
 
-// One zero-initialised work counter per launch of a call.  Every GPU that
-// loads this library holds this array until the process exits.
-static __device__ __align__(256) int g_noalloc_counters[CHX_NOALLOC_MAX_LAUNCHES];
+// The work counters of every launch of a call (kFusedCounters per launch).
+// Every GPU that loads this library holds this array until the process exits.
+static __device__ __align__(256) int g_noalloc_counters[CHX_NOALLOC_MAX_LAUNCHES * chx::kFusedCounters];
 
 std::mutex g_setup_mutex;
 int* g_counters_addr[kMaxDevices] = {};
@@ -68,12 +68,11 @@ extern "C" int chx_rollout_noalloc(chx_handle* h, int32_t n_steps, float* d_rewa
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     // the previous call left its counters non-zero: clear the ones this call uses
-    cudaError_t e = cudaMemsetAsync(counters, 0, (size_t)launches * sizeof(int), st);
+    cudaError_t e = cudaMemsetAsync(counters, 0, (size_t)launches * chx::kFusedCounters * sizeof(int), st);
     if (e != cudaSuccess) return chx::cuda_fail(e, "cudaMemsetAsync");
-    const int warps = h->warps_per_block;
-    const int threads = warps * 32;
-    const int per_sm = chx::fused_max_blocks_per_sm(threads);
-    if (per_sm <= 0) return chx::fail(CHX_ECUDA, "fused kernel cannot be resident with this block size");
+    const int threads = h->warps_per_block * 32;
+    if (!chx::fused_block_size_ok(threads))
+        return chx::fail(CHX_ECUDA, "fused kernel cannot be resident with this block size");
     for (long long i = 0; i < launches; ++i) {
         const int k0 = (int)(i * K);
         const int k = n_steps - k0 < K ? n_steps - k0 : K;
@@ -85,12 +84,8 @@ extern "C" int chx_rollout_noalloc(chx_handle* h, int32_t n_steps, float* d_rewa
         io.done = d_done ? d_done + k0 : nullptr;
         io.ld_out = n_steps;
         io.obs = (i == launches - 1) ? d_obs : nullptr;
-        io.counter = counters + i;
-        const int tiles_blocks = (io.total_tiles + warps - 1) / warps;
-        int blocks = per_sm * h->sm_count;
-        if (tiles_blocks < blocks) blocks = tiles_blocks;
-        if (blocks < 1) blocks = 1;
-        chx::launch_step_fused(h->b, h->dp, io, blocks, threads, st);
+        io.counter = counters + i * chx::kFusedCounters;
+        chx::launch_step_fused(h->b, h->dp, io, threads, h->sm_count, st);
         e = cudaGetLastError();
         if (e != cudaSuccess) return chx::cuda_fail(e, "k_step_fused launch");
     }

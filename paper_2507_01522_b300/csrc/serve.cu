@@ -147,7 +147,7 @@ struct chx_srv {
     double busy_ms = 0.0;
     int64_t t_start = 0;
     std::atomic<int64_t> ns_submit{0}, ns_scan{0}, ns_pack{0}, ns_launch{0}, ns_complete{0}, n_scans{0};
-    int fused_blocks = 0, threads = 256;
+    int threads = 256;
 };
 
 namespace {
@@ -232,7 +232,7 @@ int alloc_tick(chx_srv* s, Tick& t)
     SRV_TRY(cudaMalloc(&t.d_obs, no * sizeof(float)));
     SRV_TRY(cudaMalloc(&t.d_rslots, ne * sizeof(int32_t)));
     SRV_TRY(cudaMalloc(&t.d_rseeds, ne * sizeof(unsigned long long)));
-    SRV_TRY(cudaMalloc(&t.d_counter, sizeof(int)));
+    SRV_TRY(cudaMalloc(&t.d_counter, kFusedCounters * sizeof(int)));
     return CHX_OK;
 }
 
@@ -344,10 +344,8 @@ int launch_tick(chx_srv* s, int ti, const std::vector<Request*>& rq)
     if (tb > 0) {
         SRV_TRY(cudaMemcpyAsync(t.d_entries, t.h_entries, n_entries * sizeof(int4), cudaMemcpyHostToDevice, st));
         if (act_used > 0) SRV_TRY(cudaMemcpyAsync(t.d_act, t.h_act, act_used, cudaMemcpyHostToDevice, st));
-        SRV_TRY(cudaMemsetAsync(t.d_counter, 0, sizeof(int), st));
-        const int warps = s->threads / 32;
-        const int blocks = std::max(1, std::min(s->fused_blocks, (tb + warps - 1) / warps));
-        launch_step_fused(s->b, s->dp, io, blocks, s->threads, st);
+        SRV_TRY(cudaMemsetAsync(t.d_counter, 0, kFusedCounters * sizeof(int), st));
+        launch_step_fused(s->b, s->dp, io, s->threads, s->sm_count, st);
         SRV_TRY(cudaGetLastError());
         SRV_TRY(cudaMemcpyAsync(t.h_rew, t.d_rew, rew_used * sizeof(float), cudaMemcpyDeviceToHost, st));
         SRV_TRY(cudaMemcpyAsync(t.h_done, t.d_done, rew_used, cudaMemcpyDeviceToHost, st));
@@ -591,35 +589,28 @@ extern "C" int chx_srv_start(const chx_srv_cfg* cfg, chx_srv** out)
     }
     const size_t nprice = (size_t)cfg->exo.n_days * cfg->params.ep_len;
     const size_t nlam = (size_t)cfg->exo.n_arrival_classes * cfg->params.ep_len;
-    float *price = nullptr, *lam = nullptr, *elam = nullptr;
-    if (cudaMalloc(&price, nprice * 4) != cudaSuccess || cudaMalloc(&lam, nlam * 4) != cudaSuccess ||
-        cudaMalloc(&elam, nlam * 4) != cudaSuccess) {
+    float *price = nullptr, *cdf = nullptr;
+    if (cudaMalloc(&price, nprice * 4) != cudaSuccess || cudaMalloc(&cdf, nlam * kCdfLen * 4) != cudaSuccess) {
         cudaFree(price);
-        cudaFree(lam);
         chx_srv_stop(s);
         return fail(CHX_ENOMEM, "exogenous table allocation failed");
     }
     s->bufs.push_back(price);
-    s->bufs.push_back(lam);
-    s->bufs.push_back(elam);
-    std::vector<float> e0(nlam);
-    for (size_t i = 0; i < nlam; ++i) e0[i] = (float)std::exp(-(double)cfg->exo.h_arrival_rate[i]);
+    s->bufs.push_back(cdf);
+    std::vector<float> F;
+    build_poisson_cdf(cfg->exo.h_arrival_rate, nlam, F);
     if (cudaMemcpy(price, cfg->exo.h_price, nprice * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(lam, cfg->exo.h_arrival_rate, nlam * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(elam, e0.data(), nlam * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaMemcpy(cdf, F.data(), F.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
         chx_srv_stop(s);
         return fail(CHX_ECUDA, "exogenous table upload failed");
     }
     s->b.price = price;
-    s->b.lam = lam;
-    s->b.exp_neg_lam = elam;
+    s->b.cdf = cdf;
     s->threads = 256;
-    const int per_sm = fused_max_blocks_per_sm(s->threads);
-    if (per_sm <= 0) {
+    if (!fused_block_size_ok(s->threads)) {
         chx_srv_stop(s);
         return fail(CHX_ECUDA, "fused kernel cannot be resident");
     }
-    s->fused_blocks = per_sm * s->sm_count;
     s->ticks.resize(cfg->n_streams);
     for (auto& t : s->ticks)
         if ((rc = alloc_tick(s, t))) {

@@ -13,6 +13,8 @@
 // station totals use an xor butterfly inside the station's aligned lane
 // segment.  Both depend only on a charger's position inside its station, so a
 // station's result does not depend on which tile or lane offset it runs in.
+#include <algorithm>
+
 #include "chx_device.cuh"
 #include "chx_kernels.h"
 
@@ -139,9 +141,21 @@ __device__ __forceinline__ void seg_scan(float (&v)[PPL], const uint32_t (&meta)
     }
 }
 
+// Per-warp shared memory: group scales and limits by group slot, the running
+// statistics of the warp's stations, and the Philox action words of its
+// chargers (kept here instead of registers).
+struct WarpSmem {
+    float scale[32];
+    float gcap[32];
+    float ginv[32];
+    float st_f[4][4];                      // per station: missing kWh, charged kWh, last return
+    uint32_t st_u[4][4];                   // per station: admitted, rejected, episodes, episode ended
+    uint4 aw[32 * 4];                      // action words of charger slot lane*PPL + q
+};
+
 template <int C>
-__device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, const FusedIO& io, int cls, int tile,
-                                         float* sw)
+__device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, const FusedIO& io, int tile,
+                                         WarpSmem* ws)
 {
     using S = Shape<C>;
     constexpr int PPL = S::PPL, LPE = S::LPE;
@@ -151,19 +165,17 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
     const int le = lane % LPE;            // lane within the station
     // the station this lane works on: the tile's own slots, or (gather mode)
     // the slots a caller listed, with their own action/output/observation offsets
-    int s;
-    long long act_base, out_idx, obs_off;
+    int s, act_base, out_idx, obs_w = 0;
     if (io.gather) {
         const int4 en = io.gather[io.gather_base[CI] + tile * S::EPW + ew];
         s = en.x;
         act_base = en.y;
         out_idx = en.z;
-        obs_off = en.w;
+        obs_w = en.w;
     } else {
         s = b.cls_env_base[CI] + tile * S::EPW + ew;
         act_base = b.user_port_off[s];
         out_idx = b.user_id[s];
-        obs_off = 8LL * out_idx + 6LL * act_base;
     }
     const long long pb = b.cls_port_base[CI] + (long long)(s - b.cls_env_base[CI]) * C + le * PPL;
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -174,20 +186,16 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
     const bool live = uid >= 0;
     const uint32_t uidu = (uint32_t)(live ? uid : 0);
     const int cls_row = b.arrival_class[s];
-    const float grid_cap = b.grid_cap[s], grid_inv_eta = b.grid_inv_eta[s];
+    const float grid_cap = b.grid_cap[s];
     const uint32_t k0 = b.key0[s], k1 = b.key1[s];
     int t = b.tod[s], day = b.day[s];
     uint32_t g = b.gstep[s];
-    float ret = b.ep_ret[s], last_ret = 0.f;
-    uint32_t n_ep = 0, arrived = 0, rejected = 0;
-    float missing = 0.f, charged = 0.f;
-    bool had_end = false;
+    float ret = b.ep_ret[s];
 
     // per-charger state
     float soc[PPL], erem[PPL], cap[PPL], rbar[PPL], pw[PPL];
     int trem[PPL];
     uint32_t meta[PPL];
-    float gcap[PPL], ginv[PPL];
     ld_vec(b.soc + pb, soc);
     ld_vec(b.erem + pb, erem);
     ld_vec(b.cap + pb, cap);
@@ -195,13 +203,26 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
     ld_vec(b.pw + pb, pw);
     ld_u8(b.trem + pb, trem);
     ld_vec_u32(b.meta + pb, meta);
-    ld_vec(b.gcap + pb, gcap);
-    ld_vec(b.ginv_eta + pb, ginv);
-    int gslot[PPL];
+    {
+        float gc[PPL], gi[PPL];
+        ld_vec(b.gcap + pb, gc);
+        ld_vec(b.ginv_eta + pb, gi);
 #pragma unroll
-    for (int q = 0; q < PPL; ++q) gslot[q] = ew * LPE + (int)((meta[q] >> kMetaGroupShift) & 31u);
-
-    uint4 aw[PPL];                        // Philox words of the current 8-step action block
+        for (int q = 0; q < PPL; ++q)
+            if (meta[q] & kMetaTail) {
+                const int gs = ew * LPE + (int)((meta[q] >> kMetaGroupShift) & 31u);
+                ws->gcap[gs] = gc[q];
+                ws->ginv[gs] = gi[q];
+            }
+    }
+    if (le == 0) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            ws->st_f[ew][i] = 0.f;
+            ws->st_u[ew][i] = 0u;
+        }
+    }
+    __syncwarp();
     const bool random_actions = io.actions == nullptr;
 
     for (int k = 0; k < io.k_steps; ++k) {
@@ -212,11 +233,14 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
             const int port = le * PPL + q;
             int lvl = 0;
             if (random_actions) {
+                uint4* w = &ws->aw[lane * PPL + q];
                 if (k == 0 || (g & 7u) == 0u)
-                    aw[q] = philox4x32_10(make_uint4(uidu, g >> 3, (uint32_t)port, kPurposeAction), k0, k1);
-                lvl = random_level(aw[q], g, p.n_levels);
+                    *w = philox4x32_10(make_uint4(uidu, g >> 3, (uint32_t)port, kPurposeAction), k0, k1);
+                const uint32_t word = reinterpret_cast<const uint32_t*>(w)[(g >> 1) & 3u];
+                const uint32_t half = (g & 1u) ? (word >> 16) : (word & 0xFFFFu);
+                lvl = (int)((half * (uint32_t)p.n_levels) >> 16);
             } else if (trem[q] > 0) {
-                lvl = io.actions[(act_base + port) * io.lda + k];
+                lvl = io.actions[((long long)act_base + port) * io.lda + k];
                 if (lvl < 0 || lvl >= p.n_levels) {
                     atomicOr(b.err, kErrActionRange);
                     lvl = min(max(lvl, 0), p.n_levels - 1);
@@ -235,9 +259,11 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
 #pragma unroll
         for (int q = 0; q < PPL; ++q) {
             if (meta[q] & kMetaTail) {
-                const float sc = Sg[q] > gcap[q] ? gcap[q] / Sg[q] : 1.0f;
-                sw[gslot[q]] = sc;
-                over = fmaxf(over, (Sg[q] - gcap[q]) * ginv[q]);
+                const int gs = ew * LPE + (int)((meta[q] >> kMetaGroupShift) & 31u);
+                const float gc = ws->gcap[gs];
+                const float sc = Sg[q] > gc ? __fdividef(gc, Sg[q]) : 1.0f;
+                ws->scale[gs] = sc;
+                if (p.a_con != 0.f) over = fmaxf(over, (Sg[q] - gc) * ws->ginv[gs]);
             }
         }
         __syncwarp();
@@ -245,7 +271,7 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
 #pragma unroll
         for (int q = 0; q < PPL; ++q) {
             raw += P[q];
-            P[q] *= sw[gslot[q]];
+            P[q] *= ws->scale[ew * LPE + (int)((meta[q] >> kMetaGroupShift) & 31u)];
             sp += P[q];
             se += P[q] * ((meta[q] & kMetaDC) ? p.inv_eta1 : p.inv_eta0);
         }
@@ -256,27 +282,26 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
         if (p.a_con != 0.f) {
             raw = seg_sum<LPE>(raw);
             over = seg_max<LPE>(over);
-            c_con = fmaxf(fmaxf(over, (raw - grid_cap) * grid_inv_eta), 0.f);
+            c_con = fmaxf(fmaxf(over, (raw - grid_cap) * b.grid_inv_eta[s]), 0.f);
         }
-        const float s_root = sp > grid_cap ? grid_cap / sp : 1.0f;
+        const float s_root = sp > grid_cap ? __fdividef(grid_cap, sp) : 1.0f;
 
         // ---- (ii) charge, time advance, (iii) departures
-        bool leave[PPL];
         bool any_leave = false;
+        uint32_t leave = 0;
 #pragma unroll
         for (int q = 0; q < PPL; ++q) {
             const float Pq = P[q] * s_root;
             pw[q] = Pq;
-            leave[q] = false;
             if (trem[q] > 0) {
                 const float dE = Pq * p.dt;
-                soc[q] = fminf(soc[q] + dE / cap[q], 1.0f);
+                soc[q] = fminf(soc[q] + __fdividef(dE, cap[q]), 1.0f);
                 erem[q] = fmaxf(erem[q] - dE, 0.0f);
                 trem[q] -= 1;
-                leave[q] = trem[q] == 0;
-                any_leave = any_leave || leave[q];
+                if (trem[q] == 0) leave |= 1u << q;
             }
         }
+        any_leave = leave != 0;
         const float e_net = sp * s_root * p.dt;
         const float e_grid = se * s_root * p.dt;
         float c_sat = 0.f;
@@ -284,7 +309,7 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
             float v = 0.f;
 #pragma unroll
             for (int q = 0; q < PPL; ++q) {
-                if (leave[q]) {
+                if (leave & (1u << q)) {
                     v += erem[q];
                     soc[q] = 0.f; erem[q] = 0.f; cap[q] = 0.f; rbar[q] = 0.f;
                 }
@@ -294,12 +319,13 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
 
         // ---- (iv) arrivals: Poisson count, first come first served
         const int M = arrivals(b, p, uidu, g, t, cls_row, k0, k1);
-        bool fr[PPL];
         int n_free = 0, before = 0;
+        uint32_t fr = 0;
 #pragma unroll
         for (int q = 0; q < PPL; ++q) {
-            fr[q] = (meta[q] & kMetaValid) && trem[q] == 0;
-            const unsigned bq = __ballot_sync(0xFFFFFFFFu, fr[q]) & env_mask;
+            const bool f = (meta[q] & kMetaValid) && trem[q] == 0;
+            fr |= (f ? 1u : 0u) << q;
+            const unsigned bq = __ballot_sync(0xFFFFFFFFu, f) & env_mask;
             n_free += __popc(bq);
             before += __popc(bq & lt_mask);
         }
@@ -308,12 +334,13 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
             int rank = before;
 #pragma unroll
             for (int q = 0; q < PPL; ++q) {
-                if (fr[q] && rank < m_adm) {
+                const bool f = fr & (1u << q);
+                if (f && rank < m_adm) {
                     const Car car = draw_car(uidu, g, (uint32_t)rank, k0, k1, meta[q] & kMetaDC, p);
                     cap[q] = car.cap; soc[q] = car.soc; erem[q] = car.erem; rbar[q] = car.rbar;
                     trem[q] = car.stay;
                 }
-                rank += fr[q] ? 1 : 0;
+                rank += f ? 1 : 0;
             }
         }
 
@@ -321,19 +348,26 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
         const float price = __ldg(b.price + (size_t)day * (size_t)p.ep_len + (size_t)t);
         const float profit = p.p_sell * e_net - price * e_grid - p.c_fixed;
         const float r = profit - p.a_sat * c_sat - p.a_decl * (float)(M - m_adm) - p.a_con * c_con;
-        arrived += (uint32_t)m_adm;
-        rejected += (uint32_t)(M - m_adm);
-        missing += c_sat;
-        charged += e_net;
         ret += r;
         t += 1;
-        uint8_t fin = 0;
-        if (t >= p.ep_len) {               // episode end: record and start a new one
-            fin = 1;
-            last_ret = ret;
-            had_end = true;
+        const bool fin = t >= p.ep_len;
+        if (le == 0) {                     // station statistics, one lane per station
+            ws->st_u[ew][0] += (uint32_t)m_adm;
+            ws->st_u[ew][1] += (uint32_t)(M - m_adm);
+            ws->st_f[ew][0] += c_sat;
+            ws->st_f[ew][1] += e_net;
+            if (fin) {
+                ws->st_f[ew][2] = ret;
+                ws->st_u[ew][2] += 1u;
+                ws->st_u[ew][3] = 1u;
+            }
+            if (live) {
+                if (io.reward) io.reward[(long long)out_idx * io.ld_out + k] = r;
+                if (io.done) io.done[(long long)out_idx * io.ld_out + k] = fin ? 1 : 0;
+            }
+        }
+        if (fin) {                         // episode end: start a new one
             ret = 0.f;
-            n_ep += 1u;
 #pragma unroll
             for (int q = 0; q < PPL; ++q) {
                 soc[q] = 0.f; erem[q] = 0.f; cap[q] = 0.f; rbar[q] = 0.f; pw[q] = 0.f; trem[q] = 0;
@@ -342,10 +376,6 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
             day = draw_day(uidu, g, 0u, k0, k1, p.n_days);
         }
         g += 1u;
-        if (live && le == 0) {
-            if (io.reward) io.reward[out_idx * io.ld_out + k] = r;
-            if (io.done) io.done[out_idx * io.ld_out + k] = fin;
-        }
     }
 
     // ---- write back
@@ -357,17 +387,18 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
         st_vec(b.pw + pb, pw);
         st_u8(b.trem + pb, trem);
     }
+    __syncwarp();
     if (le == 0 && live) {
         b.tod[s] = t;
         b.day[s] = day;
         b.gstep[s] = g;
         b.ep_ret[s] = ret;
-        if (had_end) b.last_ret[s] = last_ret;
-        b.n_episodes[s] += n_ep;
-        b.st_arrived[s] += arrived;
-        b.st_rejected[s] += rejected;
-        b.st_missing[s] += missing;
-        b.st_charged[s] += charged;
+        if (ws->st_u[ew][3]) b.last_ret[s] = ws->st_f[ew][2];
+        b.n_episodes[s] += ws->st_u[ew][2];
+        b.st_arrived[s] += ws->st_u[ew][0];
+        b.st_rejected[s] += ws->st_u[ew][1];
+        b.st_missing[s] += ws->st_f[ew][0];
+        b.st_charged[s] += ws->st_f[ew][1];
     }
     if (io.obs) {                          // uniform across the warp
         int occ_l = 0;
@@ -376,7 +407,7 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
         const int occ = (int)seg_sum<LPE>((float)occ_l);
         if (live) {
             const int n = b.n_ports[s];
-            float* ob = io.obs + obs_off;
+            float* ob = io.obs + (io.gather ? (long long)obs_w : 8LL * uid + 6LL * act_base);
             if (le == 0) obs_env(ob, t, day, occ, n, b, p);
 #pragma unroll
             for (int q = 0; q < PPL; ++q) {
@@ -386,14 +417,22 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
             }
         }
     }
+    __syncwarp();
 }
 
-__global__ void __launch_bounds__(256, 2) k_step_fused(DevBatch b, DevParams p, FusedIO io)
+// Persistent work loop over a schedule of classes in [CLO, CHI]: one
+// instantiation for the 128-charger class (4 chargers per lane, more
+// registers), one for the others, so the smaller classes keep more warps
+// resident.
+template <int CLO, int CHI, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_step_fused(DevBatch b, DevParams p, FusedIO io)
 {
-    extern __shared__ float smem[];
-    float* sw = smem + (threadIdx.x >> 5) * 32;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    WarpSmem* ws = reinterpret_cast<WarpSmem*>(smem_raw) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
-    sw[lane] = 1.0f;                       // group scales; padding chargers read a defined value
+    ws->scale[lane] = 1.0f;                // padding chargers read a defined value
+    ws->gcap[lane] = 0.f;
+    ws->ginv[lane] = 1.f;
     __syncwarp();
     for (;;) {
         int tile_id = 0;
@@ -408,29 +447,73 @@ __global__ void __launch_bounds__(256, 2) k_step_fused(DevBatch b, DevParams p, 
                 tile = tile_id - io.sched_tile_base[i];
             }
         }
-        switch (cls) {
-            case 0: run_tile<8>(b, p, io, cls, tile, sw); break;
-            case 1: run_tile<16>(b, p, io, cls, tile, sw); break;
-            case 2: run_tile<32>(b, p, io, cls, tile, sw); break;
-            case 3: run_tile<64>(b, p, io, cls, tile, sw); break;
-            default: run_tile<128>(b, p, io, cls, tile, sw); break;
-        }
+        if (CLO <= 0 && 0 <= CHI && cls == 0) run_tile<8>(b, p, io, tile, ws);
+        if (CLO <= 1 && 1 <= CHI && cls == 1) run_tile<16>(b, p, io, tile, ws);
+        if (CLO <= 2 && 2 <= CHI && cls == 2) run_tile<32>(b, p, io, tile, ws);
+        if (CLO <= 3 && 3 <= CHI && cls == 3) run_tile<64>(b, p, io, tile, ws);
+        if (CLO <= 4 && 4 <= CHI && cls == 4) run_tile<128>(b, p, io, tile, ws);
     }
 }
 
-int fused_max_blocks_per_sm(int threads)
+namespace {
+
+auto* const kSmallKernel = &k_step_fused<0, 3, 3>;
+auto* const kLargeKernel = &k_step_fused<4, 4, 2>;
+
+// the part of a schedule whose classes lie in [clo, chi], tiles renumbered
+FusedIO sub_schedule(const FusedIO& io, int clo, int chi, int* counter)
+{
+    FusedIO o = io;
+    o.n_sched = 0;
+    int tb = 0;
+    for (int i = 0; i < io.n_sched; ++i) {
+        const int c = io.sched_cls[i];
+        if (c < clo || c > chi) continue;
+        o.sched_cls[o.n_sched] = c;
+        o.sched_tile_base[o.n_sched] = tb;
+        o.n_sched++;
+        tb += io.sched_tile_base[i + 1] - io.sched_tile_base[i];
+    }
+    o.sched_tile_base[o.n_sched] = tb;
+    o.total_tiles = tb;
+    o.counter = counter;
+    return o;
+}
+
+int blocks_per_sm(const void* kernel, int threads)
 {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_fused, threads, (threads / 32) * 32 * sizeof(float)) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, (threads / 32) * sizeof(WarpSmem)) !=
         cudaSuccess)
         return 0;
     return n;
 }
 
-void launch_step_fused(const DevBatch& b, const DevParams& p, const FusedIO& io, int blocks, int threads,
+}  // namespace
+
+bool fused_block_size_ok(int threads)
+{
+    return threads >= 32 && threads <= 256 && threads % 32 == 0 &&
+           blocks_per_sm((const void*)kSmallKernel, threads) > 0 && blocks_per_sm((const void*)kLargeKernel, threads) > 0;
+}
+
+void launch_step_fused(const DevBatch& b, const DevParams& p, const FusedIO& io, int threads, int sm_count,
                        cudaStream_t st)
 {
-    k_step_fused<<<blocks, threads, (threads / 32) * 32 * sizeof(float), st>>>(b, p, io);
+    const int warps = threads / 32;
+    const size_t smem = (size_t)warps * sizeof(WarpSmem);
+    const FusedIO big = sub_schedule(io, 4, 4, io.counter);
+    const FusedIO small = sub_schedule(io, 0, 3, io.counter + 1);
+    if (big.total_tiles > 0) {             // the heavy class first
+        const int per_sm = blocks_per_sm((const void*)kLargeKernel, threads);
+        const int blocks = std::max(1, std::min(per_sm * sm_count, (big.total_tiles + warps - 1) / warps));
+        kLargeKernel<<<blocks, threads, smem, st>>>(b, p, big);
+    }
+    if (small.total_tiles > 0) {
+        const int per_sm = blocks_per_sm((const void*)kSmallKernel, threads);
+        const int blocks = std::max(1, std::min(per_sm * sm_count, (small.total_tiles + warps - 1) / warps));
+        kSmallKernel<<<blocks, threads, smem, st>>>(b, p, small);
+    }
 }
 
 }  // namespace chx

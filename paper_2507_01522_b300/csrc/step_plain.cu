@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(128) k_step_plain(DevBatch b, DevParams p, con
         s_raw += P;
         if (m & kMetaTail) {
             const float gc = b.gcap[i];
-            const float sc = S > gc ? gc / S : 1.0f;
+            const float sc = S > gc ? __fdividef(gc, S) : 1.0f;
             gscale[(m >> kMetaGroupShift) & 31] = sc;
             over_max = fmaxf(over_max, (S - gc) * b.ginv_eta[i]);
             s_grp += S * sc;
@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(128) k_step_plain(DevBatch b, DevParams p, con
     }
     // root node
     const float grid_cap = b.grid_cap[s];
-    const float s_root = s_grp > grid_cap ? grid_cap / s_grp : 1.0f;
+    const float s_root = s_grp > grid_cap ? __fdividef(grid_cap, s_grp) : 1.0f;
     const float c_con = fmaxf(fmaxf(over_max, (s_raw - grid_cap) * b.grid_inv_eta[s]), 0.0f);
 
     // -- (ii) charge, time advance, (iii) departures
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(128) k_step_plain(DevBatch b, DevParams p, con
             P = clip_power(lvl, dc, soc, erem, cap, b.rbar[i], p);
             P = P * gscale[(m >> kMetaGroupShift) & 31] * s_root;
             const float dE = P * p.dt;
-            soc = fminf(soc + dE / cap, 1.0f);
+            soc = fminf(soc + __fdividef(dE, cap), 1.0f);
             erem = fmaxf(erem - dE, 0.0f);
             tr -= 1;
             if (tr == 0) {
