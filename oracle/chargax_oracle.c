@@ -412,10 +412,12 @@ void orc_step(orc *o, const int8_t *actions, int64_t lda, double *reward, uint8_
          * free ports (first come first served); the rest are rejected.  Car j
          * parks at the j-th free port in port order and draws its car and
          * user profile. */
+        /* one Philox call of counter (e, g/4, 0, ARRIVAL) serves 4 steps:
+         * step g uses word g mod 4 */
         uint32_t w[4];
-        draw(o, e, g, 0u, ORC_PURPOSE_ARRIVAL, w);
+        draw(o, e, g >> 2, 0u, ORC_PURPOSE_ARRIVAL, w);
         float lam = o->lam[(size_t)o->arrival_class[e] * (size_t)p->ep_len + (size_t)t];
-        int32_t M = orc_poisson(lam, w[0]);
+        int32_t M = orc_poisson(lam, w[g & 3u]);
         int32_t n_free = 0;
         for (int64_t i = p0; i < p1; ++i) n_free += (o->trem[i] == 0);
         int32_t m = M < n_free ? M : n_free;
