@@ -160,12 +160,23 @@ __device__ __forceinline__ int draw_day(uint32_t uid, uint32_t c1, uint32_t c2, 
     return (int)range_of(w.x, (uint32_t)n_days);
 }
 
+// Philox words of a station's arrival draws: one call serves steps 4j..4j+3
+__device__ __forceinline__ uint4 arrival_words(uint32_t uid, uint32_t g, uint32_t k0, uint32_t k1)
+{
+    return philox4x32_10(make_uint4(uid, g >> 2, 0u, kPurposeArrival), k0, k1);
+}
+
+// arrival count of step g from its Philox word
+__device__ __forceinline__ int arrival_count(const DevBatch& b, const DevParams& p, uint32_t word, int t, int cls_row)
+{
+    const size_t row = ((size_t)cls_row * (size_t)p.ep_len + (size_t)t) * kCdfLen;
+    return poisson_count(b.cdf + row, word);
+}
+
 __device__ __forceinline__ int arrivals(const DevBatch& b, const DevParams& p, uint32_t uid, uint32_t g, int t, int cls_row,
                                         uint32_t k0, uint32_t k1)
 {
-    const uint4 w = philox4x32_10(make_uint4(uid, g, 0u, kPurposeArrival), k0, k1);
-    const size_t row = ((size_t)cls_row * (size_t)p.ep_len + (size_t)t) * kCdfLen;
-    return poisson_count(b.cdf + row, w.x);
+    return arrival_count(b, p, word_of(arrival_words(uid, g, k0, k1), g & 3u), t, cls_row);
 }
 
 // observation features of a station (8 floats) and of one charger (6 floats)

@@ -150,7 +150,8 @@ struct WarpSmem {
     float ginv[32];
     float st_f[4][4];                      // per station: missing kWh, charged kWh, last return
     uint32_t st_u[4][4];                   // per station: admitted, rejected, episodes, episode ended
-    uint4 aw[32 * 4];                      // action words of charger slot lane*PPL + q
+    uint32_t arr[4][4];                    // per station: Philox words of its 4-step arrival block
+    uint32_t aw[4][32 * 4];                // action words: word w of charger slot q*32 + lane
 };
 
 template <int C>
@@ -233,10 +234,15 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
             const int port = le * PPL + q;
             int lvl = 0;
             if (random_actions) {
-                uint4* w = &ws->aw[lane * PPL + q];
-                if (k == 0 || (g & 7u) == 0u)
-                    *w = philox4x32_10(make_uint4(uidu, g >> 3, (uint32_t)port, kPurposeAction), k0, k1);
-                const uint32_t word = reinterpret_cast<const uint32_t*>(w)[(g >> 1) & 3u];
+                const int j = q * 32 + lane;
+                if (k == 0 || (g & 7u) == 0u) {
+                    const uint4 w = philox4x32_10(make_uint4(uidu, g >> 3, (uint32_t)port, kPurposeAction), k0, k1);
+                    ws->aw[0][j] = w.x;
+                    ws->aw[1][j] = w.y;
+                    ws->aw[2][j] = w.z;
+                    ws->aw[3][j] = w.w;
+                }
+                const uint32_t word = ws->aw[(g >> 1) & 3u][j];
                 const uint32_t half = (g & 1u) ? (word >> 16) : (word & 0xFFFFu);
                 lvl = (int)((half * (uint32_t)p.n_levels) >> 16);
             } else if (trem[q] > 0) {
@@ -318,7 +324,17 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
         }
 
         // ---- (iv) arrivals: Poisson count, first come first served
-        const int M = arrivals(b, p, uidu, g, t, cls_row, k0, k1);
+        if (k == 0 || (g & 3u) == 0u) {    // a new 4-step block of arrival words
+            const uint4 w = arrival_words(uidu, g, k0, k1);
+            if (le == 0) {
+                ws->arr[ew][0] = w.x;
+                ws->arr[ew][1] = w.y;
+                ws->arr[ew][2] = w.z;
+                ws->arr[ew][3] = w.w;
+            }
+        }
+        __syncwarp();
+        const int M = arrival_count(b, p, ws->arr[ew][g & 3u], t, cls_row);
         int n_free = 0, before = 0;
         uint32_t fr = 0;
 #pragma unroll
