@@ -150,7 +150,7 @@ struct WarpSmem {
     float ginv[32];
     float st_f[4][4];                      // per station: missing kWh, charged kWh, last return
     uint32_t st_u[4][4];                   // per station: admitted, rejected, episodes, episode ended
-    uint32_t arr[4][4];                    // per station: Philox words of its 4-step arrival block
+    uint32_t arrw[4][32];                  // arrival words: word w of block (blk0 + x - station's first lane) at [w][x]
     uint32_t aw[4][32 * 4];                // action words: word w of charger slot q*32 + lane
 };
 
@@ -225,6 +225,10 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
     }
     __syncwarp();
     const bool random_actions = io.actions == nullptr;
+    // Arrival words are prefetched lane-parallel: lane le of a station holds the
+    // Philox block (blk0 + le), i.e. the words of steps 4*(blk0+le)..+3, so one
+    // pass covers 4*LPE steps.
+    uint32_t blk0 = 0;
 
     for (int k = 0; k < io.k_steps; ++k) {
         // ---- (i) apply actions: per-charger clip
@@ -324,17 +328,17 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
         }
 
         // ---- (iv) arrivals: Poisson count, first come first served
-        if (k == 0 || (g & 3u) == 0u) {    // a new 4-step block of arrival words
-            const uint4 w = arrival_words(uidu, g, k0, k1);
-            if (le == 0) {
-                ws->arr[ew][0] = w.x;
-                ws->arr[ew][1] = w.y;
-                ws->arr[ew][2] = w.z;
-                ws->arr[ew][3] = w.w;
-            }
+        const uint32_t blk = g >> 2;
+        if (k == 0 || blk - blk0 >= (uint32_t)LPE) {   // first step, or past the prefetched blocks
+            blk0 = blk;
+            const uint4 w = arrival_words(uidu, (blk + (uint32_t)le) << 2, k0, k1);
+            ws->arrw[0][lane] = w.x;
+            ws->arrw[1][lane] = w.y;
+            ws->arrw[2][lane] = w.z;
+            ws->arrw[3][lane] = w.w;
         }
         __syncwarp();
-        const int M = arrival_count(b, p, ws->arr[ew][g & 3u], t, cls_row);
+        const int M = arrival_count(b, p, ws->arrw[g & 3u][ew * LPE + (int)(blk - blk0)], t, cls_row);
         int n_free = 0, before = 0;
         uint32_t fr = 0;
 #pragma unroll
