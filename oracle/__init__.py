@@ -59,8 +59,8 @@ def lib():
         L.orc_reset.argtypes = [vp, vp, i32, u64]
         L.orc_step.argtypes = [vp, vp, i64, vp, vp]
         L.orc_observe.argtypes = [vp, vp]
-        L.orc_get_state.argtypes = [vp] + [vp] * 12
-        L.orc_set_state.argtypes = [vp] + [vp] * 12
+        L.orc_get_state.argtypes = [vp] + [vp] * 13
+        L.orc_set_state.argtypes = [vp] + [vp] * 13
         L.orc_get_info.argtypes = [vp] + [vp] * 9
         L.orc_get_stats.argtypes = [vp] + [vp] * 6
         L.orc_get_power.argtypes = [vp, vp]
@@ -167,14 +167,15 @@ class Oracle:
         P, E = self.P, self.E
         s = dict(soc=np.zeros(P), erem=np.zeros(P), cap=np.zeros(P), rbar=np.zeros(P), p=np.zeros(P),
                  trem=np.zeros(P, np.int32), tod=np.zeros(E, np.int32), day=np.zeros(E, np.int32),
-                 gstep=np.zeros(E, np.uint32), key0=np.zeros(E, np.uint32), key1=np.zeros(E, np.uint32),
+                 gstep=np.zeros(E, np.uint32), ncar=np.zeros(E, np.uint32), key0=np.zeros(E, np.uint32),
+                 key1=np.zeros(E, np.uint32),
                  ep_ret=np.zeros(E))
         lib().orc_get_state(self.h, *[_ptr(s[k]) for k in STATE_KEYS])
         return s
 
     def set_state(self, s: dict):
         conv = dict(soc=np.float64, erem=np.float64, cap=np.float64, rbar=np.float64, p=np.float64,
-                    trem=np.int32, tod=np.int32, day=np.int32, gstep=np.uint32, key0=np.uint32,
+                    trem=np.int32, tod=np.int32, day=np.int32, gstep=np.uint32, ncar=np.uint32, key0=np.uint32,
                     key1=np.uint32, ep_ret=np.float64)
         arrs = [np.ascontiguousarray(s[k], dtype=conv[k]) for k in STATE_KEYS]
         lib().orc_set_state(self.h, *[_ptr(a) for a in arrs])
@@ -205,4 +206,4 @@ class Oracle:
         return int(lib().orc_random_action(self.h, env, gstep, port))
 
 
-STATE_KEYS = ("soc", "erem", "cap", "rbar", "p", "trem", "tod", "day", "gstep", "key0", "key1", "ep_ret")
+STATE_KEYS = ("soc", "erem", "cap", "rbar", "p", "trem", "tod", "day", "gstep", "ncar", "key0", "key1", "ep_ret")

@@ -67,6 +67,7 @@ typedef struct orc {
     /* per-env state */
     int32_t *tod, *day;
     uint32_t *gstep, *key0, *key1;
+    uint32_t *ncar;                        /* cars admitted since the last reset    */
     uint32_t *stream;                      /* Philox stream id (default: index) */
     double *ep_ret, *last_ret;
     uint32_t *n_episodes;
@@ -177,6 +178,7 @@ void orc_reset(orc *o, const int32_t *env_ids, int32_t n, uint64_t seed)
         o->key0[e] = (uint32_t)seed;
         o->key1[e] = (uint32_t)(seed >> 32);
         o->gstep[e] = 0;
+        o->ncar[e] = 0;
         o->ep_ret[e] = 0.0;
         start_episode(o, e, 0u, 1u);
     }
@@ -247,6 +249,7 @@ orc *orc_create(const orc_params *prm, int32_t E,
     o->tod = (int32_t *)xcalloc((size_t)E, sizeof(int32_t));
     o->day = (int32_t *)xcalloc((size_t)E, sizeof(int32_t));
     o->gstep = (uint32_t *)xcalloc((size_t)E, sizeof(uint32_t));
+    o->ncar = (uint32_t *)xcalloc((size_t)E, sizeof(uint32_t));
     o->key0 = (uint32_t *)xcalloc((size_t)E, sizeof(uint32_t));
     o->key1 = (uint32_t *)xcalloc((size_t)E, sizeof(uint32_t));
     o->stream = (uint32_t *)xcalloc((size_t)E, sizeof(uint32_t));
@@ -277,7 +280,7 @@ void orc_destroy(orc *o)
     void *ptrs[] = {o->port_off, o->group_off, o->n_ports, o->n_groups, o->arrival_class, o->grid_limit,
                     o->grid_eta, o->port_type, o->port_group, o->group_size, o->group_limit, o->group_eta,
                     o->price, o->lam, o->soc, o->erem, o->cap, o->rbar, o->pw, o->scratch_p, o->scratch_leave, o->trem, o->tod,
-                    o->day, o->gstep, o->key0, o->key1, o->stream, o->ep_ret, o->last_ret, o->n_episodes,
+                    o->day, o->gstep, o->ncar, o->key0, o->key1, o->stream, o->ep_ret, o->last_ret, o->n_episodes,
                     o->st_arrived, o->st_rejected, o->st_missing, o->st_charged, o->inf_M, o->inf_admitted,
                     o->inf_departed, o->inf_csat, o->inf_ccon, o->inf_enet, o->inf_egrid, o->inf_price,
                     o->inf_req_sum};
@@ -410,8 +413,9 @@ void orc_step(orc *o, const int8_t *actions, int64_t lda, double *reward, uint8_
 
         /* (iv) Arrival of new Cars: M ~ Poisson(lambda(t)), clipped by the
          * free ports (first come first served); the rest are rejected.  Car j
-         * parks at the j-th free port in port order and draws its car and
-         * user profile. */
+         * of this step parks at the j-th free port in port order; its car and
+         * user profile are the Philox words of the station's car number
+         * (cars admitted since the last reset + j). */
         /* one Philox call of counter (e, g/4, 0, ARRIVAL) serves 4 steps:
          * step g uses word g mod 4 */
         uint32_t w[4];
@@ -426,7 +430,7 @@ void orc_step(orc *o, const int8_t *actions, int64_t lda, double *reward, uint8_
         for (int64_t i = p0; i < p1 && j < m; ++i) {
             if (o->trem[i] != 0) continue;
             uint32_t c[4];
-            draw(o, e, g, (uint32_t)j, ORC_PURPOSE_CAR, c);
+            draw(o, e, o->ncar[e] + (uint32_t)j, 0u, ORC_PURPOSE_CAR, c);
             int ty = o->port_type[i];
             double C = p->cap_kwh[0] + (p->cap_kwh[1] - p->cap_kwh[0]) * to_unit(c[0]);
             double soc0 = p->soc0[0] + (p->soc0[1] - p->soc0[0]) * to_unit(c[1]);
@@ -452,6 +456,7 @@ void orc_step(orc *o, const int8_t *actions, int64_t lda, double *reward, uint8_
         else profit = p->p_sell * e_net - price * e_grid_net - p->c_fixed;   /* p_sell,grid = p_buy */
         double r = profit - p->alpha_sat * c_sat - p->alpha_decl * (double)c_decl - p->alpha_con * c_con;
 
+        o->ncar[e] += (uint32_t)m;
         o->inf_M[e] = M; o->inf_admitted[e] = m; o->inf_departed[e] = departed;
         o->inf_csat[e] = c_sat; o->inf_ccon[e] = c_con; o->inf_enet[e] = e_net;
         o->inf_egrid[e] = e_grid; o->inf_price[e] = price; o->inf_req_sum[e] = req_sum;
@@ -509,9 +514,10 @@ void orc_observe(const orc *o, double *obs)
 }
 
 /* State access in batch order: per port soc, erem, cap, rbar, p, trem; per
- * env step-of-day, day, global step, key words, running episode return. */
+ * env step-of-day, day, global step, car count, key words, running episode
+ * return. */
 void orc_get_state(const orc *o, double *soc, double *erem, double *cap, double *rbar, double *pw,
-                   int32_t *trem, int32_t *tod, int32_t *day, uint32_t *gstep, uint32_t *key0,
+                   int32_t *trem, int32_t *tod, int32_t *day, uint32_t *gstep, uint32_t *ncar, uint32_t *key0,
                    uint32_t *key1, double *ep_ret)
 {
     size_t P = (size_t)o->P, E = (size_t)o->E;
@@ -520,12 +526,14 @@ void orc_get_state(const orc *o, double *soc, double *erem, double *cap, double 
     memcpy(pw, o->pw, P * sizeof(double)); memcpy(trem, o->trem, P * sizeof(int32_t));
     memcpy(tod, o->tod, E * sizeof(int32_t)); memcpy(day, o->day, E * sizeof(int32_t));
     memcpy(gstep, o->gstep, E * sizeof(uint32_t)); memcpy(key0, o->key0, E * sizeof(uint32_t));
+    memcpy(ncar, o->ncar, E * sizeof(uint32_t));
     memcpy(key1, o->key1, E * sizeof(uint32_t)); memcpy(ep_ret, o->ep_ret, E * sizeof(double));
 }
 
 void orc_set_state(orc *o, const double *soc, const double *erem, const double *cap, const double *rbar,
                    const double *pw, const int32_t *trem, const int32_t *tod, const int32_t *day,
-                   const uint32_t *gstep, const uint32_t *key0, const uint32_t *key1, const double *ep_ret)
+                   const uint32_t *gstep, const uint32_t *ncar, const uint32_t *key0, const uint32_t *key1,
+                   const double *ep_ret)
 {
     size_t P = (size_t)o->P, E = (size_t)o->E;
     memcpy(o->soc, soc, P * sizeof(double)); memcpy(o->erem, erem, P * sizeof(double));
@@ -533,6 +541,7 @@ void orc_set_state(orc *o, const double *soc, const double *erem, const double *
     memcpy(o->pw, pw, P * sizeof(double)); memcpy(o->trem, trem, P * sizeof(int32_t));
     memcpy(o->tod, tod, E * sizeof(int32_t)); memcpy(o->day, day, E * sizeof(int32_t));
     memcpy(o->gstep, gstep, E * sizeof(uint32_t)); memcpy(o->key0, key0, E * sizeof(uint32_t));
+    memcpy(o->ncar, ncar, E * sizeof(uint32_t));
     memcpy(o->key1, key1, E * sizeof(uint32_t)); memcpy(o->ep_ret, ep_ret, E * sizeof(double));
 }
 

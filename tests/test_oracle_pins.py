@@ -558,7 +558,10 @@ def test_reset_subset_and_determinism():
         ra, _ = a.step(None)
         rb, _ = b.step(None)
         assert np.array_equal(ra, rb)
+    # the car count is the number of cars admitted since the last reset
+    np.testing.assert_array_equal(a.state()["ncar"], a.stats()["arrived"].astype(np.uint32))
     a.reset([1, 4], seed=99)
     sa = a.state()
+    assert sa["ncar"][1] == 0 and sa["ncar"][4] == 0 and sa["ncar"][0] == a.stats()["arrived"][0]
     assert sa["gstep"][1] == 0 and sa["gstep"][4] == 0 and sa["gstep"][0] == 30
     assert np.all(sa["trem"][16:32] == 0) and sa["key0"][1] == 99
