@@ -227,15 +227,16 @@ int chx_observe(chx_handle* h, float* d_obs, void* stream);
  * Host arrays in batch order (all blocking).  Per charger [P]: SoC, remaining
  * demand kWh, capacity kWh, car maximum rate kW, last applied power kW,
  * remaining stay (0 = empty).  Per env [E]: step of day, day, global step,
+ * cars admitted since the last reset (indexes the cars' Philox draws),
  * Philox key words, running episode return.  NULL skips a field on get and
  * keeps it on set. */
 int chx_get_state(chx_handle* h, float* h_soc, float* h_erem, float* h_cap, float* h_rbar, float* h_p,
-                  uint8_t* h_trem, int32_t* h_tod, int32_t* h_day, uint32_t* h_gstep, uint32_t* h_key0,
-                  uint32_t* h_key1, float* h_ep_ret);
+                  uint8_t* h_trem, int32_t* h_tod, int32_t* h_day, uint32_t* h_gstep, uint32_t* h_ncar,
+                  uint32_t* h_key0, uint32_t* h_key1, float* h_ep_ret);
 int chx_set_state(chx_handle* h, const float* h_soc, const float* h_erem, const float* h_cap,
                   const float* h_rbar, const float* h_p, const uint8_t* h_trem, const int32_t* h_tod,
-                  const int32_t* h_day, const uint32_t* h_gstep, const uint32_t* h_key0,
-                  const uint32_t* h_key1, const float* h_ep_ret);
+                  const int32_t* h_day, const uint32_t* h_gstep, const uint32_t* h_ncar,
+                  const uint32_t* h_key0, const uint32_t* h_key1, const float* h_ep_ret);
 
 /* Per-env running statistics [E]: cars admitted, cars rejected, kWh missing
  * at departure, kWh charged, finished episodes, return of the last episode. */

@@ -114,7 +114,7 @@ def load_library(path: str = LIB_PATH):
         "chx_step_n": [vp, i32, vp, i64, vp, vp, i64, vp, vp], "chx_rollout": [vp, i32, vp, vp, vp, vp],
         "chx_rollout_host": [vp, i32, vp, vp, vp, vp], "chx_step_host": [vp, vp, vp, vp, vp, vp],
         "chx_autotune": [vp, i32, vp, vp], "chx_set_launch": [vp, i32, i32], "chx_observe": [vp, vp, vp],
-        "chx_get_state": [vp] + [vp] * 12, "chx_set_state": [vp] + [vp] * 12, "chx_stats": [vp] + [vp] * 6,
+        "chx_get_state": [vp] + [vp] * 13, "chx_set_state": [vp] + [vp] * 13, "chx_stats": [vp] + [vp] * 6,
         "chx_save": [vp, vp, vp], "chx_load": [vp, vp, C.c_size_t], "chx_check": [vp, vp],
         "chx_rollout_noalloc": [vp, i32, vp, vp, vp, vp],
         "chx_srv_start": [vp, vp], "chx_srv_stop": [vp], "chx_srv_admit": [vp, vp, u64, vp],
@@ -170,7 +170,7 @@ def params_struct(p: "_inputs.EnvParams") -> _Params:
 
 STATE_FIELDS = (("soc", np.float32, "P"), ("erem", np.float32, "P"), ("cap", np.float32, "P"),
                 ("rbar", np.float32, "P"), ("p", np.float32, "P"), ("trem", np.uint8, "P"),
-                ("tod", np.int32, "E"), ("day", np.int32, "E"), ("gstep", np.uint32, "E"),
+                ("tod", np.int32, "E"), ("day", np.int32, "E"), ("gstep", np.uint32, "E"), ("ncar", np.uint32, "E"),
                 ("key0", np.uint32, "E"), ("key1", np.uint32, "E"), ("ep_ret", np.float32, "E"))
 
 

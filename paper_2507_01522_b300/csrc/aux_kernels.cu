@@ -25,6 +25,7 @@ __global__ void k_reset(DevBatch b, DevParams p, const int32_t* __restrict__ use
         b.key0[s] = seed_lo;
         b.key1[s] = seed_hi;
         b.gstep[s] = 0u;
+        b.ncar[s] = 0u;
         b.tod[s] = 0;
         b.ep_ret[s] = 0.f;
         b.day[s] = draw_day((uint32_t)uid, 0u, 1u, seed_lo, seed_hi, p.n_days);
@@ -58,6 +59,7 @@ __global__ void k_reset_slots(DevBatch b, DevParams p, const int32_t* __restrict
         b.key0[s] = lo;
         b.key1[s] = hi;
         b.gstep[s] = 0u;
+        b.ncar[s] = 0u;
         b.tod[s] = 0;
         b.ep_ret[s] = 0.f;
         b.day[s] = draw_day((uint32_t)s, 0u, 1u, lo, hi, p.n_days);

@@ -51,6 +51,7 @@ struct DevBatch {
     float *grid_cap, *grid_inv_eta;        // eta_0 * I_0 of the root, 1/eta_0
     int32_t *tod, *day;
     uint32_t *gstep, *key0, *key1;
+    uint32_t* ncar;                        // cars admitted since the last reset
     float *ep_ret, *last_ret;
     uint32_t* n_episodes;
     uint32_t *st_arrived, *st_rejected;
@@ -140,11 +141,15 @@ __device__ __forceinline__ float clip_power(int level, bool dc, float soc, float
 
 struct Car { float cap, soc, erem, rbar; int stay; };
 
-// car and user profile of the j-th arriving car (one Philox call)
-__device__ __forceinline__ Car draw_car(uint32_t uid, uint32_t g, uint32_t j, uint32_t k0, uint32_t k1, bool dc,
-                                        const DevParams& p)
+// Philox words of the station's n-th car since its last reset
+__device__ __forceinline__ uint4 car_words(uint32_t uid, uint32_t n, uint32_t k0, uint32_t k1)
 {
-    const uint4 w = philox4x32_10(make_uint4(uid, g, j, kPurposeCar), k0, k1);
+    return philox4x32_10(make_uint4(uid, n, 0u, kPurposeCar), k0, k1);
+}
+
+// car and user profile from its Philox words, at a charger of type dc
+__device__ __forceinline__ Car car_from_words(uint4 w, bool dc, const DevParams& p)
+{
     Car c;
     c.cap = p.cap_lo + p.cap_span * unit_of(w.x);
     c.soc = p.soc_lo + p.soc_span * unit_of(w.y);

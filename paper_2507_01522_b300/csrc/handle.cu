@@ -312,7 +312,7 @@ int build_handle(const chx_stations* st, const chx_env_params* prm, const chx_ex
     ALLOC(b.soc, PS) ALLOC(b.erem, PS) ALLOC(b.cap, PS) ALLOC(b.rbar, PS) ALLOC(b.pw, PS)
     ALLOC(b.trem, PS) ALLOC(b.meta, PS) ALLOC(b.gcap, PS) ALLOC(b.ginv_eta, PS)
     ALLOC(b.user_id, NS) ALLOC(b.user_port_off, NS) ALLOC(b.n_ports, NS) ALLOC(b.arrival_class, NS)
-    ALLOC(b.grid_cap, NS) ALLOC(b.grid_inv_eta, NS) ALLOC(b.tod, NS) ALLOC(b.day, NS) ALLOC(b.gstep, NS)
+    ALLOC(b.grid_cap, NS) ALLOC(b.grid_inv_eta, NS) ALLOC(b.tod, NS) ALLOC(b.day, NS) ALLOC(b.gstep, NS) ALLOC(b.ncar, NS)
     ALLOC(b.key0, NS) ALLOC(b.key1, NS) ALLOC(b.ep_ret, NS) ALLOC(b.last_ret, NS) ALLOC(b.n_episodes, NS)
     ALLOC(b.st_arrived, NS) ALLOC(b.st_rejected, NS) ALLOC(b.st_missing, NS) ALLOC(b.st_charged, NS)
     ALLOC(h->d_user_to_slot, E) ALLOC(h->d_counter, 64) ALLOC(b.err, 1)
@@ -636,7 +636,7 @@ int snapshot_take(chx_handle* h, Snapshot& s)
     const DevBatch& b = h->b;
     const size_t PS = h->n_port_slots, NS = h->n_slots;
     s.items = {{b.soc, PS * 4}, {b.erem, PS * 4}, {b.cap, PS * 4}, {b.rbar, PS * 4}, {b.pw, PS * 4},
-               {b.trem, PS}, {b.tod, NS * 4}, {b.day, NS * 4}, {b.gstep, NS * 4}, {b.key0, NS * 4},
+               {b.trem, PS}, {b.tod, NS * 4}, {b.day, NS * 4}, {b.gstep, NS * 4}, {b.ncar, NS * 4}, {b.key0, NS * 4},
                {b.key1, NS * 4}, {b.ep_ret, NS * 4}, {b.last_ret, NS * 4}, {b.n_episodes, NS * 4},
                {b.st_arrived, NS * 4}, {b.st_rejected, NS * 4}, {b.st_missing, NS * 4}, {b.st_charged, NS * 4}};
     for (auto& it : s.items) {
@@ -809,7 +809,8 @@ int set_env_field(chx_handle* h, const T* in, T* d)
     } while (0)
 
 extern "C" int chx_get_state(chx_handle* h, float* h_soc, float* h_erem, float* h_cap, float* h_rbar, float* h_p,
-                             uint8_t* h_trem, int32_t* h_tod, int32_t* h_day, uint32_t* h_gstep, uint32_t* h_key0,
+                             uint8_t* h_trem, int32_t* h_tod, int32_t* h_day, uint32_t* h_gstep, uint32_t* h_ncar,
+                             uint32_t* h_key0,
                              uint32_t* h_key1, float* h_ep_ret)
 {
     if (!h) return fail(CHX_EINVAL, "null handle");
@@ -824,6 +825,7 @@ extern "C" int chx_get_state(chx_handle* h, float* h_soc, float* h_erem, float* 
     RC(get_env_field(h, h_tod, (const int32_t*)b.tod));
     RC(get_env_field(h, h_day, (const int32_t*)b.day));
     RC(get_env_field(h, h_gstep, (const uint32_t*)b.gstep));
+    RC(get_env_field(h, h_ncar, (const uint32_t*)b.ncar));
     RC(get_env_field(h, h_key0, (const uint32_t*)b.key0));
     RC(get_env_field(h, h_key1, (const uint32_t*)b.key1));
     RC(get_env_field(h, h_ep_ret, (const float*)b.ep_ret));
@@ -832,7 +834,8 @@ extern "C" int chx_get_state(chx_handle* h, float* h_soc, float* h_erem, float* 
 
 extern "C" int chx_set_state(chx_handle* h, const float* h_soc, const float* h_erem, const float* h_cap,
                              const float* h_rbar, const float* h_p, const uint8_t* h_trem, const int32_t* h_tod,
-                             const int32_t* h_day, const uint32_t* h_gstep, const uint32_t* h_key0,
+                             const int32_t* h_day, const uint32_t* h_gstep, const uint32_t* h_ncar,
+                             const uint32_t* h_key0,
                              const uint32_t* h_key1, const float* h_ep_ret)
 {
     if (!h) return fail(CHX_EINVAL, "null handle");
@@ -853,6 +856,7 @@ extern "C" int chx_set_state(chx_handle* h, const float* h_soc, const float* h_e
     RC(set_env_field(h, h_tod, b.tod));
     RC(set_env_field(h, h_day, b.day));
     RC(set_env_field(h, h_gstep, b.gstep));
+    RC(set_env_field(h, h_ncar, b.ncar));
     RC(set_env_field(h, h_key0, b.key0));
     RC(set_env_field(h, h_key1, b.key1));
     RC(set_env_field(h, h_ep_ret, b.ep_ret));
@@ -875,14 +879,14 @@ extern "C" int chx_stats(chx_handle* h, uint32_t* h_arrived, uint32_t* h_rejecte
 }
 
 namespace {
-constexpr uint64_t kCkptMagic = 0x43484158434B5031ull;   // "CHAXCKP1"
+constexpr uint64_t kCkptMagic = 0x43484158434B5032ull;   // "CHAXCKP2"
 struct CkptHeader {
     uint64_t magic;
     int64_t n_envs, n_ports;
 };
 size_t ckpt_size(const chx_handle* h)
 {
-    return sizeof(CkptHeader) + (size_t)h->P * (5 * 4 + 1) + (size_t)h->E * (6 * 4 + 6 * 4);
+    return sizeof(CkptHeader) + (size_t)h->P * (5 * 4 + 1) + (size_t)h->E * (7 * 4 + 6 * 4);
 }
 }  // namespace
 
@@ -907,7 +911,8 @@ extern "C" int chx_save(chx_handle* h, void* h_buf, size_t* size)
     int32_t* tod = reinterpret_cast<int32_t*>(env);
     int32_t* day = tod + E;
     uint32_t* gstep = reinterpret_cast<uint32_t*>(day + E);
-    uint32_t *key0 = gstep + E, *key1 = key0 + E;
+    uint32_t* ncar = gstep + E;
+    uint32_t *key0 = ncar + E, *key1 = key0 + E;
     float* ret = reinterpret_cast<float*>(key1 + E);
     uint32_t* arrived = reinterpret_cast<uint32_t*>(ret + E);
     uint32_t* rejected = arrived + E;
@@ -915,7 +920,7 @@ extern "C" int chx_save(chx_handle* h, void* h_buf, size_t* size)
     float* charged = missing + E;
     uint32_t* episodes = reinterpret_cast<uint32_t*>(charged + E);
     float* last = reinterpret_cast<float*>(episodes + E);
-    RC(chx_get_state(h, soc, erem, cap, rbar, pw, trem, tod, day, gstep, key0, key1, ret));
+    RC(chx_get_state(h, soc, erem, cap, rbar, pw, trem, tod, day, gstep, ncar, key0, key1, ret));
     RC(chx_stats(h, arrived, rejected, missing, charged, episodes, last));
     *size = need;
     return CHX_OK;
@@ -937,7 +942,8 @@ extern "C" int chx_load(chx_handle* h, const void* h_buf, size_t size)
     const int32_t* tod = reinterpret_cast<const int32_t*>(env);
     const int32_t* day = tod + E;
     const uint32_t* gstep = reinterpret_cast<const uint32_t*>(day + E);
-    const uint32_t *key0 = gstep + E, *key1 = key0 + E;
+    const uint32_t* ncar = gstep + E;
+    const uint32_t *key0 = ncar + E, *key1 = key0 + E;
     const float* ret = reinterpret_cast<const float*>(key1 + E);
     const uint32_t* arrived = reinterpret_cast<const uint32_t*>(ret + E);
     const uint32_t* rejected = arrived + E;
@@ -945,7 +951,7 @@ extern "C" int chx_load(chx_handle* h, const void* h_buf, size_t size)
     const float* charged = missing + E;
     const uint32_t* episodes = reinterpret_cast<const uint32_t*>(charged + E);
     const float* last = reinterpret_cast<const float*>(episodes + E);
-    RC(chx_set_state(h, f, f + P, f + 2 * P, f + 3 * P, f + 4 * P, trem, tod, day, gstep, key0, key1, ret));
+    RC(chx_set_state(h, f, f + P, f + 2 * P, f + 3 * P, f + 4 * P, trem, tod, day, gstep, ncar, key0, key1, ret));
     DevBatch& b = h->b;
     RC(set_env_field(h, arrived, b.st_arrived));
     RC(set_env_field(h, rejected, b.st_rejected));

@@ -192,7 +192,7 @@ int alloc_pool(chx_srv* s)
     PA(b.soc, PS) PA(b.erem, PS) PA(b.cap, PS) PA(b.rbar, PS) PA(b.pw, PS) PA(b.trem, PS) PA(b.meta, PS)
     PA(b.gcap, PS) PA(b.ginv_eta, PS) PA(b.user_id, NS) PA(b.user_port_off, NS) PA(b.n_ports, NS)
     PA(b.arrival_class, NS) PA(b.grid_cap, NS) PA(b.grid_inv_eta, NS) PA(b.tod, NS) PA(b.day, NS) PA(b.gstep, NS)
-    PA(b.key0, NS) PA(b.key1, NS) PA(b.ep_ret, NS) PA(b.last_ret, NS) PA(b.n_episodes, NS) PA(b.st_arrived, NS)
+    PA(b.key0, NS) PA(b.key1, NS) PA(b.ncar, NS) PA(b.ep_ret, NS) PA(b.last_ret, NS) PA(b.n_episodes, NS) PA(b.st_arrived, NS)
     PA(b.st_rejected, NS) PA(b.st_missing, NS) PA(b.st_charged, NS) PA(b.err, 1)
 #undef PA
     std::vector<int32_t> minus1(NS, -1);

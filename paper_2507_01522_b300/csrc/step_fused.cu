@@ -152,6 +152,7 @@ struct WarpSmem {
     uint32_t st_u[4][4];                   // per station: admitted, rejected, episodes, episode ended
     uint32_t arrw[4][32];                  // arrival words: word w of block (blk0 + x - station's first lane) at [w][x]
     uint32_t aw[4][32 * 4];                // action words: word w of charger slot q*32 + lane
+    uint32_t carw[4][128];                 // pre-drawn car words: station ew's i-th buffered car at ew*C + i
 };
 
 template <int C>
@@ -192,6 +193,9 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
     int t = b.tod[s], day = b.day[s];
     uint32_t g = b.gstep[s];
     float ret = b.ep_ret[s];
+    // cars: the station's next C car profiles are drawn in one lane-parallel
+    // pass into shared memory and handed out as cars arrive
+    uint32_t ncar = b.ncar[s], cend = ncar;
 
     // per-charger state
     float soc[PPL], erem[PPL], cap[PPL], rbar[PPL], pw[PPL];
@@ -351,17 +355,34 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
         }
         const int m_adm = min(M, n_free);
         if (__any_sync(0xFFFFFFFFu, m_adm > 0)) {
+            if (ncar + (uint32_t)m_adm > cend) {   // buffer exhausted: draw cars ncar .. ncar+C-1
+#pragma unroll
+                for (int q = 0; q < PPL; ++q) {
+                    const int i = q * LPE + le;
+                    const uint4 w = car_words(uidu, ncar + (uint32_t)i, k0, k1);
+                    ws->carw[0][ew * C + i] = w.x;
+                    ws->carw[1][ew * C + i] = w.y;
+                    ws->carw[2][ew * C + i] = w.z;
+                    ws->carw[3][ew * C + i] = w.w;
+                }
+                cend = ncar + (uint32_t)C;
+            }
+            __syncwarp();
+            const int x0 = ew * C + (int)(ncar - (cend - (uint32_t)C));   // buffer slot of car ncar
             int rank = before;
 #pragma unroll
             for (int q = 0; q < PPL; ++q) {
                 const bool f = fr & (1u << q);
                 if (f && rank < m_adm) {
-                    const Car car = draw_car(uidu, g, (uint32_t)rank, k0, k1, meta[q] & kMetaDC, p);
+                    const int x = x0 + rank;
+                    const uint4 w = make_uint4(ws->carw[0][x], ws->carw[1][x], ws->carw[2][x], ws->carw[3][x]);
+                    const Car car = car_from_words(w, meta[q] & kMetaDC, p);
                     cap[q] = car.cap; soc[q] = car.soc; erem[q] = car.erem; rbar[q] = car.rbar;
                     trem[q] = car.stay;
                 }
                 rank += f ? 1 : 0;
             }
+            ncar += (uint32_t)m_adm;
         }
 
         // ---- reward, Appendix A.3
@@ -412,6 +433,7 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
         b.tod[s] = t;
         b.day[s] = day;
         b.gstep[s] = g;
+        b.ncar[s] = ncar;
         b.ep_ret[s] = ret;
         if (ws->st_u[ew][3]) b.last_ret[s] = ws->st_f[ew][2];
         b.n_episodes[s] += ws->st_u[ew][2];
@@ -477,7 +499,7 @@ __global__ void __launch_bounds__(256, MINB) k_step_fused(DevBatch b, DevParams 
 
 namespace {
 
-auto* const kSmallKernel = &k_step_fused<0, 3, 3>;
+auto* const kSmallKernel = &k_step_fused<0, 3, 4>;
 auto* const kLargeKernel = &k_step_fused<4, 4, 2>;
 
 // the part of a schedule whose classes lie in [clo, chi], tiles renumbered

@@ -111,10 +111,11 @@ __global__ void __launch_bounds__(128) k_step_plain(DevBatch b, DevParams p, con
     // -- (iv) arrivals: Poisson count, first come first served
     const int M = arrivals(b, p, (uint32_t)uid, g, t, b.arrival_class[s], k0, k1);
     const int m_adm = min(M, n_free);
+    const uint32_t ncar = b.ncar[s];
     for (int q = 0, j = 0; q < n && j < m_adm; ++q) {
         const long long i = pb + q;
         if (b.trem[i] != 0) continue;
-        const Car car = draw_car((uint32_t)uid, g, (uint32_t)j, k0, k1, b.meta[i] & kMetaDC, p);
+        const Car car = car_from_words(car_words((uint32_t)uid, ncar + (uint32_t)j, k0, k1), b.meta[i] & kMetaDC, p);
         b.cap[i] = car.cap; b.soc[i] = car.soc; b.erem[i] = car.erem; b.rbar[i] = car.rbar;
         b.trem[i] = (uint8_t)car.stay;
         ++j;
@@ -125,6 +126,7 @@ __global__ void __launch_bounds__(128) k_step_plain(DevBatch b, DevParams p, con
     const float profit = p.p_sell * e_net - price * e_grid - p.c_fixed;
     const float r = profit - p.a_sat * c_sat - p.a_decl * (float)(M - m_adm) - p.a_con * c_con;
 
+    b.ncar[s] = ncar + (uint32_t)m_adm;
     b.st_arrived[s] += (uint32_t)m_adm;
     b.st_rejected[s] += (uint32_t)(M - m_adm);
     b.st_missing[s] += c_sat;

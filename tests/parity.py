@@ -38,7 +38,7 @@ def reward_scale(info, params):
 
 def assert_events_equal(gs: dict, os_: dict, where: str = ""):
     np.testing.assert_array_equal(gs["trem"].astype(np.int32), os_["trem"], err_msg=f"trem {where}")
-    for k in ("tod", "day", "gstep", "key0", "key1"):
+    for k in ("tod", "day", "gstep", "ncar", "key0", "key1"):
         np.testing.assert_array_equal(gs[k].astype(np.int64), os_[k].astype(np.int64), err_msg=f"{k} {where}")
 
 
