@@ -105,27 +105,41 @@ __device__ __forceinline__ float seg_max(float v)
     return v;
 }
 
-// Inclusive segmented scan of v over the chargers of the warp in charger
-// order (lane-major, PPL per lane); a set head bit starts a new segment.
+// Distance, in lanes, from this lane back to the lane holding the head of the
+// group that this lane's last charger belongs to (0 if that head is in this
+// lane).  Groups are static, so this is computed once per tile: a prefix
+// maximum of "this lane holds a head" over the station's lanes.
 template <int PPL, int LPE>
-__device__ __forceinline__ void seg_scan(float (&v)[PPL], const uint32_t (&meta)[PPL], int le)
+__device__ __forceinline__ int head_distance(const uint32_t (&meta)[PPL], int le)
 {
-    bool any_head = meta[0] & kMetaHead;
+    bool any_head = false;
 #pragma unroll
-    for (int q = 1; q < PPL; ++q) {
-        if (!(meta[q] & kMetaHead)) v[q] += v[q - 1];
-        any_head = any_head || (meta[q] & kMetaHead);
+    for (int q = 0; q < PPL; ++q) any_head = any_head || (meta[q] & kMetaHead);
+    int hl = any_head ? le : 0;            // lane 0 of a station always holds a head
+#pragma unroll
+    for (int d = 1; d < LPE; d <<= 1) {
+        const int o = __shfl_up_sync(0xFFFFFFFFu, hl, d);
+        if (le >= d) hl = max(hl, o);
     }
+    return le - hl;
+}
+
+// Inclusive segmented scan of v over the chargers of the warp in charger
+// order (lane-major, PPL per lane); a head bit starts a new group.  The lane
+// aggregates are scanned with the static head distance dh: in the round of
+// offset d a lane adds the partial of lane - d only while d <= dh, which keeps
+// every sum inside its group (and its station).
+template <int PPL, int LPE>
+__device__ __forceinline__ void seg_scan(float (&v)[PPL], const uint32_t (&meta)[PPL], int le, int dh)
+{
+#pragma unroll
+    for (int q = 1; q < PPL; ++q)
+        if (!(meta[q] & kMetaHead)) v[q] += v[q - 1];
     float x = v[PPL - 1];
-    int f = any_head ? 1 : 0;
 #pragma unroll
     for (int d = 1; d < LPE; d <<= 1) {
         const float xu = __shfl_up_sync(0xFFFFFFFFu, x, d);
-        const int fu = __shfl_up_sync(0xFFFFFFFFu, f, d);
-        if (le >= d) {
-            if (!f) x += xu;
-            f |= fu;
-        }
+        if (d <= dh) x += xu;
     }
     if constexpr (PPL == 1) {
         v[0] = x;
@@ -139,6 +153,28 @@ __device__ __forceinline__ void seg_scan(float (&v)[PPL], const uint32_t (&meta)
             if (!seen) v[q] += carry;
         }
     }
+}
+
+// Poisson count (see poisson_count) searched by the station's lanes in
+// parallel: lane le tests CDF entry base + le; the entries <= u form a prefix
+// because the CDF is nondecreasing, so their number is the count.
+template <int LPE>
+__device__ __forceinline__ int poisson_count_warp(const float* __restrict__ F, uint32_t w, int le, unsigned env_mask)
+{
+    const float u = __fmul_rn(__uint2float_rn(w >> 8), 0x1p-24f);
+    int M = 0;
+    bool more = true;
+#pragma unroll 1
+    for (int base = 0; base < kCdfLen; base += LPE) {
+        const bool ok = more && u >= __ldg(F + base + le);
+        const int cnt = __popc(__ballot_sync(0xFFFFFFFFu, ok) & env_mask);
+        if (more) {
+            M = base + cnt;
+            more = cnt == LPE;
+        }
+        if (!__any_sync(0xFFFFFFFFu, more)) break;
+    }
+    return M;
 }
 
 // Per-warp shared memory: group scales and limits by group slot, the running
@@ -229,6 +265,7 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
     }
     __syncwarp();
     const bool random_actions = io.actions == nullptr;
+    const int dh = head_distance<PPL, LPE>(meta, le);
     // Arrival words are prefetched lane-parallel: lane le of a station holds the
     // Philox block (blk0 + le), i.e. the words of steps 4*(blk0+le)..+3, so one
     // pass covers 4*LPE steps.
@@ -268,7 +305,7 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
         float Sg[PPL];
 #pragma unroll
         for (int q = 0; q < PPL; ++q) Sg[q] = P[q];
-        seg_scan<PPL, LPE>(Sg, meta, le);
+        seg_scan<PPL, LPE>(Sg, meta, le, dh);
         float over = 0.f;
 #pragma unroll
         for (int q = 0; q < PPL; ++q) {
@@ -342,7 +379,8 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
             ws->arrw[3][lane] = w.w;
         }
         __syncwarp();
-        const int M = arrival_count(b, p, ws->arrw[g & 3u][ew * LPE + (int)(blk - blk0)], t, cls_row);
+        const int M = poisson_count_warp<LPE>(b.cdf + ((size_t)cls_row * (size_t)p.ep_len + (size_t)t) * kCdfLen,
+                                              ws->arrw[g & 3u][ew * LPE + (int)(blk - blk0)], le, env_mask);
         int n_free = 0, before = 0;
         uint32_t fr = 0;
 #pragma unroll
