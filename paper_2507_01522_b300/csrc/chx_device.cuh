@@ -25,6 +25,14 @@ constexpr uint32_t kPurposeArrival = 0u, kPurposeCar = 1u, kPurposeAction = 2u, 
 constexpr uint32_t kMetaDC = 1u, kMetaValid = 2u, kMetaHead = 4u, kMetaTail = 8u;
 constexpr int kMetaGroupShift = 4;         // 5 bits: group slot within the warp tile (0..31)
 
+// Warp tile shape of size class c (C = 8 << c chargers): chargers per lane,
+// lanes per station and stations per warp.  Small stations take 2 chargers
+// per lane so that a warp carries more of them and per-station work is
+// shared by more chargers.
+__host__ __device__ constexpr int tile_ppl(int c) { return c >= 4 ? 4 : 2; }
+__host__ __device__ constexpr int tile_lpe(int c) { return (8 << c) / tile_ppl(c); }
+__host__ __device__ constexpr int tile_epw(int c) { return 32 / tile_lpe(c); }
+
 // device error bits
 constexpr uint32_t kErrActionRange = 1u;
 

@@ -236,7 +236,7 @@ int build_handle(const chx_stations* st, const chx_env_params* prm, const chx_ex
     long long port_base = 0;
     for (int c = 0; c < kNumClasses; ++c) {
         const int C = 8 << c;
-        const int epw = C >= 32 ? 1 : 32 / C;
+        const int epw = tile_epw(c);
         int padded = (count[c] + epw - 1) / epw * epw;
         if (padded < min_pad_envs_per_class && count[c] > 0) padded = min_pad_envs_per_class;
         h->cls_n_env[c] = padded;
@@ -350,7 +350,7 @@ int build_handle(const chx_stations* st, const chx_env_params* prm, const chx_ex
     for (int c = kNumClasses - 1; c >= 0; --c) {
         if (h->cls_n_env[c] == 0) continue;
         const int C = 8 << c;
-        const int epw = C >= 32 ? 1 : 32 / C;
+        const int epw = tile_epw(c);
         h->sched.sched_cls[h->sched.n_sched] = c;
         h->sched.sched_tile_base[h->sched.n_sched] = tb;
         h->sched.n_sched++;

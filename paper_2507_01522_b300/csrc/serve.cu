@@ -287,7 +287,7 @@ int launch_tick(chx_srv* s, int ti, const std::vector<Request*>& rq)
     for (int c = kNumClasses - 1; c >= 0; --c) {
         if (count[c] == 0) continue;
         const int C = 8 << c;
-        const int epw = C >= 32 ? 1 : 32 / C;
+        const int epw = tile_epw(c);
         const int padded = (count[c] + epw - 1) / epw * epw;
         io.gather_base[c] = n_entries;
         cursor[c] = n_entries;

@@ -22,9 +22,10 @@ namespace chx {
 
 template <int C>
 struct Shape {
-    static constexpr int PPL = C > 32 ? C / 32 : 1;   // chargers per lane
-    static constexpr int LPE = C > 32 ? 32 : C;       // lanes per station
-    static constexpr int EPW = 32 / LPE;              // stations per warp
+    static constexpr int CI = C == 8 ? 0 : (C == 16 ? 1 : (C == 32 ? 2 : (C == 64 ? 3 : 4)));
+    static constexpr int PPL = tile_ppl(CI);         // chargers per lane
+    static constexpr int LPE = tile_lpe(CI);         // lanes per station
+    static constexpr int EPW = tile_epw(CI);         // stations per warp
 };
 
 template <int N>
@@ -181,11 +182,11 @@ __device__ __forceinline__ int poisson_count_warp(const float* __restrict__ F, u
 // statistics of the warp's stations, and the Philox action words of its
 // chargers (kept here instead of registers).
 struct WarpSmem {
-    float scale[32];
-    float gcap[32];
-    float ginv[32];
-    float st_f[4][4];                      // per station: missing kWh, charged kWh, last return
-    uint32_t st_u[4][4];                   // per station: admitted, rejected, episodes, episode ended
+    float scale[64];                       // group slots: station ew's group g at ew * min(C, 32) + g
+    float gcap[64];
+    float ginv[64];
+    float st_f[8][4];                      // per station: missing kWh, charged kWh, last return
+    uint32_t st_u[8][4];                   // per station: admitted, rejected, episodes, episode ended
     uint32_t arrw[4][32];                  // arrival words: word w of block (blk0 + x - station's first lane) at [w][x]
     uint32_t aw[4][32 * 4];                // action words: word w of charger slot q*32 + lane
     uint32_t carw[4][128];                 // pre-drawn car words: station ew's i-th buffered car at ew*C + i
@@ -197,6 +198,7 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
 {
     using S = Shape<C>;
     constexpr int PPL = S::PPL, LPE = S::LPE;
+    constexpr int GPS = C < 32 ? C : 32;   // group slots per station (at most 32 groups)
     constexpr int CI = C == 8 ? 0 : (C == 16 ? 1 : (C == 32 ? 2 : (C == 64 ? 3 : 4)));
     const int lane = threadIdx.x & 31;
     const int ew = lane / LPE;            // station within the warp
@@ -251,7 +253,7 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
 #pragma unroll
         for (int q = 0; q < PPL; ++q)
             if (meta[q] & kMetaTail) {
-                const int gs = ew * LPE + (int)((meta[q] >> kMetaGroupShift) & 31u);
+                const int gs = ew * GPS + (int)((meta[q] >> kMetaGroupShift) & 31u);
                 ws->gcap[gs] = gc[q];
                 ws->ginv[gs] = gi[q];
             }
@@ -310,7 +312,7 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
 #pragma unroll
         for (int q = 0; q < PPL; ++q) {
             if (meta[q] & kMetaTail) {
-                const int gs = ew * LPE + (int)((meta[q] >> kMetaGroupShift) & 31u);
+                const int gs = ew * GPS + (int)((meta[q] >> kMetaGroupShift) & 31u);
                 const float gc = ws->gcap[gs];
                 const float sc = Sg[q] > gc ? __fdividef(gc, Sg[q]) : 1.0f;
                 ws->scale[gs] = sc;
@@ -322,7 +324,7 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
 #pragma unroll
         for (int q = 0; q < PPL; ++q) {
             raw += P[q];
-            P[q] *= ws->scale[ew * LPE + (int)((meta[q] >> kMetaGroupShift) & 31u)];
+            P[q] *= ws->scale[ew * GPS + (int)((meta[q] >> kMetaGroupShift) & 31u)];
             sp += P[q];
             se += P[q] * ((meta[q] & kMetaDC) ? p.inv_eta1 : p.inv_eta0);
         }
@@ -510,9 +512,11 @@ __global__ void __launch_bounds__(256, MINB) k_step_fused(DevBatch b, DevParams 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WarpSmem* ws = reinterpret_cast<WarpSmem*>(smem_raw) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
-    ws->scale[lane] = 1.0f;                // padding chargers read a defined value
-    ws->gcap[lane] = 0.f;
-    ws->ginv[lane] = 1.f;
+    for (int i = lane; i < 64; i += 32) {   // padding chargers read defined values
+        ws->scale[i] = 1.0f;
+        ws->gcap[i] = 0.f;
+        ws->ginv[i] = 1.f;
+    }
     __syncwarp();
     for (;;) {
         int tile_id = 0;
@@ -537,7 +541,7 @@ __global__ void __launch_bounds__(256, MINB) k_step_fused(DevBatch b, DevParams 
 
 namespace {
 
-auto* const kSmallKernel = &k_step_fused<0, 3, 4>;
+auto* const kSmallKernel = &k_step_fused<0, 3, 3>;
 auto* const kLargeKernel = &k_step_fused<4, 4, 2>;
 
 // the part of a schedule whose classes lie in [clo, chi], tiles renumbered
@@ -560,8 +564,19 @@ FusedIO sub_schedule(const FusedIO& io, int clo, int chi, int* counter)
     return o;
 }
 
+// allow each kernel the dynamic shared memory of 8 warps (above the 48 KB default)
+bool raise_smem_limit()
+{
+    static const bool ok = cudaFuncSetAttribute((const void*)kSmallKernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                8 * (int)sizeof(WarpSmem)) == cudaSuccess &&
+                           cudaFuncSetAttribute((const void*)kLargeKernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                8 * (int)sizeof(WarpSmem)) == cudaSuccess;
+    return ok;
+}
+
 int blocks_per_sm(const void* kernel, int threads)
 {
+    if (!raise_smem_limit()) return 0;
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, (threads / 32) * sizeof(WarpSmem)) !=
         cudaSuccess)
