@@ -97,15 +97,19 @@ class Clocks:
                 "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
 
 
-def dist_init():
+def dist_init(backend: str = "nccl"):
+    """Rank, world size and local rank from the torchrun environment; one
+    process per GPU (nccl) or per CPU worker (gloo, used by the tests)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws == 1:
         return 0, 1, 0
     import torch
     import torch.distributed as dist
     rank, local = int(os.environ["RANK"]), int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dist.init_process_group("nccl")
+    if backend == "nccl":
+        torch.cuda.set_device(local)
+    if not dist.is_initialized():
+        dist.init_process_group(backend)
     return rank, ws, local
 
 
@@ -115,14 +119,32 @@ def barrier(ws):
         dist.barrier()
 
 
-def max_over_ranks(x, ws):
+def _reduce(x, ws, op):
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=op)
     return float(t.item())
+
+
+def max_over_ranks(x, ws):
+    import torch.distributed as dist
+    return _reduce(x, ws, dist.ReduceOp.MAX) if ws > 1 else x
+
+
+def whole_job_rate(units_local, seconds_local, ws):
+    """Whole-job throughput: units summed over ranks / the slowest rank's time."""
+    import torch.distributed as dist
+    units = _reduce(float(units_local), ws, dist.ReduceOp.SUM) if ws > 1 else float(units_local)
+    return units / max_over_ranks(seconds_local, ws)
+
+
+def rank_seed(rank):
+    """Philox key of a rank's batch: ranks simulate different stations."""
+    return 1000 + rank
 
 
 def peaks():
@@ -240,7 +262,7 @@ def run_b300(args):
     dev = torch.device("cuda", local)
     w = I.heterogeneous(n_envs=args.n_envs, seed=0)
     T = w.params.ep_len
-    b = chargax.Batch(w, seed=1000 + rank)
+    b = chargax.Batch(w, seed=rank_seed(rank))
     E, P = b.E, b.P
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -281,8 +303,7 @@ def run_b300(args):
     b.check()
     total_s = max_over_ranks(sum(ms) / 1e3, ws)
     ms_step = 1e3 * total_s / args.steps
-    env_steps = E * T * args.steps * ws
-    value = env_steps / total_s
+    value = whole_job_rate(E * T * args.steps, sum(ms) / 1e3, ws)
 
     # roofline of the fused kernel (ALU-bound: state stays in registers)
     pk, pk_kind = peaks()
@@ -312,7 +333,7 @@ def run_b300(args):
 
     # plain form, same protocol: one launch per step, replayed as a graph
     if not args.no_plain:
-        bp = chargax.Batch(w, seed=1000 + rank)
+        bp = chargax.Batch(w, seed=rank_seed(rank))
         rp = torch.empty(T, E, device=dev)
         dp = torch.empty(T, E, dtype=torch.uint8, device=dev)
         bp.step(reward=rp[0], done=dp[0])

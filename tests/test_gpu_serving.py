@@ -205,3 +205,29 @@ def test_serving_simulation_reports_latency():
     assert res["env_steps_per_s"] > 0
     assert res["mean_tick_envs"] > 0
     srv.stop()
+
+
+def test_serving_wait_timeout():
+    """A wait that runs out of time returns CHX_ETIMEOUT and leaves the ticket
+    valid; a later wait collects it."""
+    from paper_2507_01522_b300.chargax import CHX_ETIMEOUT, ChxError
+    w = I.serving_pool(n_envs=4096, seed=3)
+    n = w.stations.n_ports
+    cap = [int(np.sum(n <= 8))] + [int(np.sum((n > (4 << c)) & (n <= (8 << c)))) for c in range(1, 5)]
+    srv = server_for(w, cap=cap, max_tick_obs_floats=0, max_tick_envs=4096)
+    ids = srv.admit(w.stations)
+    seen = False
+    for _ in range(5):
+        r = np.zeros(len(ids), np.float32)
+        t = srv.submit(ids, reward=r)
+        try:
+            srv.wait(t, timeout_us=0)
+        except ChxError as e:
+            assert e.code == CHX_ETIMEOUT
+            seen = True
+        else:
+            continue                                     # finished before the zero-time wait
+        lat = srv.wait(t)
+        assert lat > 0 and np.all(np.isfinite(r))
+    assert seen
+    srv.stop()
