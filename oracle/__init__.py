@@ -70,6 +70,7 @@ def lib():
         L.orc_poisson.argtypes = [C.c_float, C.c_uint32]
         L.orc_taper.restype = C.c_double
         L.orc_taper.argtypes = [C.c_double, C.c_double, C.c_double]
+        L.orc_policy_uniforms.argtypes = [vp, i32, vp]
         L.orc_random_action.restype = i32
         L.orc_random_action.argtypes = [vp, i32, C.c_uint32, i32]
         _lib = L
@@ -204,6 +205,13 @@ class Oracle:
 
     def random_action(self, env: int, gstep: int, port: int) -> int:
         return int(lib().orc_random_action(self.h, env, gstep, port))
+
+    def policy_uniforms(self, n_ports: int) -> np.ndarray:
+        """[E, n_ports] uniforms of the policy's next action samples (every
+        env must have n_ports chargers)."""
+        u = np.zeros((self.E, n_ports))
+        lib().orc_policy_uniforms(self.h, n_ports, _ptr(u))
+        return u
 
 
 STATE_KEYS = ("soc", "erem", "cap", "rbar", "p", "trem", "tod", "day", "gstep", "ncar", "key0", "key1", "ep_ret")

@@ -33,6 +33,7 @@
 #define ORC_PURPOSE_CAR 1u
 #define ORC_PURPOSE_ACTION 2u
 #define ORC_PURPOSE_DAY 3u
+#define ORC_PURPOSE_POLICY 4u
 
 typedef struct orc_params {
     int32_t ep_len;        /* steps per episode (24 h / dt)                     */
@@ -300,6 +301,23 @@ int32_t orc_random_action(const orc *o, int32_t e, uint32_t g, int32_t q)
     uint32_t word = w[(g >> 1) & 3u];
     uint32_t half = (g & 1u) ? (word >> 16) : (word & 0xFFFFu);
     return (int32_t)((half * (uint32_t)o->p.n_levels) >> 16);
+}
+
+/* Uniforms of the policy's action samples for the next step (the PPO actor
+ * of Sec. 5 samples one level per charger): u[e][q] for charger q of env e
+ * is word q mod 4 of the Philox block (e, g, q / 4, POLICY), g = the env's
+ * global step, mapped to [0, 1) by its top 24 bits.  All envs must have
+ * n_ports chargers.  Pinned by the Philox known-answer tests and by the
+ * policy pins (closed-form samples, frequencies). */
+void orc_policy_uniforms(const orc *o, int32_t n_ports, double *u)
+{
+    for (int32_t e = 0; e < o->E; ++e)
+        for (int32_t q = 0; q < n_ports; q += 4) {
+            uint32_t w[4];
+            draw(o, e, o->gstep[e], (uint32_t)(q >> 2), ORC_PURPOSE_POLICY, w);
+            for (int32_t j = 0; j < 4 && q + j < n_ports; ++j)
+                u[(int64_t)e * n_ports + q + j] = to_unit(w[j]);
+        }
 }
 
 /* ------------------------------------------------------------------------ */

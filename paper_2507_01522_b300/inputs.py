@@ -280,3 +280,50 @@ def random_actions(rng: np.random.Generator, n_ports_total: int, n_levels: int =
     """Uniform action levels 0..n_levels-1 as int8, shape [P] or [P, steps]."""
     shape = (n_ports_total,) if steps is None else (n_ports_total, steps)
     return rng.integers(0, n_levels, size=shape, dtype=np.int64).astype(np.int8)
+
+
+# ----------------------------------------------------------------------------
+# policy weights (the agent's actor network, random initialisation)
+# ----------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class PolicyWeights:
+    """A 3-layer actor obs [D] -> H -> H -> N * L logits.  Float32 arrays
+    whose values are BF16 numbers (low 16 bits of each float zero)."""
+    w1: np.ndarray               # [H, D]
+    b1: np.ndarray               # [H]
+    w2: np.ndarray               # [H, H]
+    b2: np.ndarray               # [H]
+    w3: np.ndarray               # [N * L, H]; row c * L + j = level j of charger c
+    b3: np.ndarray               # [N * L]
+
+
+def _orthogonal(rng: np.random.Generator, rows: int, cols: int, gain: float) -> np.ndarray:
+    a = rng.standard_normal((max(rows, cols), min(rows, cols)))
+    q, r = np.linalg.qr(a)
+    q = q * np.sign(np.diag(r))
+    q = q if rows >= cols else q.T
+    return gain * q[:rows, :cols]
+
+
+def _bf16_values(x: np.ndarray) -> np.ndarray:
+    """float32 copy with the low 16 bits cleared, i.e. exact BF16 values."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32) & np.uint32(0xFFFF0000)
+    return u.view(np.float32)
+
+
+def policy_weights(obs_dim: int, n_ports: int, n_levels: int = 11, hidden: int = 256, seed: int = 0,
+                   head_gain: float = 0.01, bias_scale: float = 0.0) -> PolicyWeights:
+    """Random initialisation as PPO actors are commonly initialised:
+    orthogonal matrices, gain sqrt(2) for the hidden layers and `head_gain`
+    for the logits layer, zero biases; `bias_scale` > 0 draws biases from
+    U(-bias_scale, bias_scale) instead (tests use it to exercise the bias
+    path and to make the distributions far from uniform)."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0x9011C7]))
+    n_out = n_ports * n_levels
+    mats = [_orthogonal(rng, hidden, obs_dim, math.sqrt(2.0)), _orthogonal(rng, hidden, hidden, math.sqrt(2.0)),
+            _orthogonal(rng, n_out, hidden, head_gain)]
+    biases = [rng.uniform(-bias_scale, bias_scale, n) if bias_scale > 0 else np.zeros(n) for n in (hidden, hidden, n_out)]
+    w1, w2, w3 = (_bf16_values(m) for m in mats)
+    b1, b2, b3 = (np.asarray(b, np.float32) for b in biases)
+    return PolicyWeights(w1, b1, w2, b2, w3, b3)
