@@ -248,6 +248,48 @@ int chx_stats(chx_handle* h, uint32_t* h_arrived, uint32_t* h_rejected, float* h
 int chx_save(chx_handle* h, void* h_buf, size_t* size);
 int chx_load(chx_handle* h, const void* h_buf, size_t size);
 
+/* ---- on-device policy and policy rollout -------------------------------------
+ * The agent of the paper's experiments (Sec. 5 and Table "PPO hyper-
+ * parameters": a PPO actor over the Gym-style observation) as a 3-layer MLP
+ * run on the tensor cores:
+ *   h1 = relu(W1 bf16(obs) + b1), h2 = relu(W2 bf16(h1) + b2),
+ *   logits = W3 bf16(h2) + b3,
+ * BF16 operands (bf16() = round to nearest even), FP32 accumulation.  Each
+ * charger's level is sampled from the softmax of its n_levels logits by
+ * inverse transform: with u = (w >> 8) * 2^-24 from Philox word w at counter
+ * (env, global step of the env, charger / 4, 4), word charger % 4, under the
+ * env's key, the level is the number of j < n_levels - 1 whose cumulative
+ * sum e_0 + .. + e_j is <= u * sum(e), e_j = exp(l_j - max l).
+ *
+ * chx_policy_load: host weights, BF16 bit patterns, row-major:
+ *   h_w1 [hidden][D], h_w2 [hidden][hidden], h_w3 [N * n_levels][hidden]
+ *   (row c * n_levels + j = level j of charger c), biases FP32 h_b1 [hidden],
+ *   h_b2 [hidden], h_b3 [N * n_levels].  D = 8 + 6 N, the observation size of
+ *   one env.  Requirements (else CHX_EINVAL): hidden = 256; every station of
+ *   the batch has the same charger count N, 1 <= N <= 32; 2 <= n_levels <= 12.
+ *   The weights are copied to the device (the call synchronises the device
+ *   first); loading again with the same N updates them in place, so captured
+ *   rollouts stay valid.
+ * chx_policy_act: actions for every env from observations d_obs [E][D] FP32
+ *   (the layout of chx_observe) into d_actions [E][N] int8; d_logits (NULL
+ *   or [E][N][n_levels] FP32) receives the logits.  Uses each env's current
+ *   global step and key; changes no env state.
+ * chx_policy_rollout: n_steps steps of "act, then step" from the current
+ *   state, written to caller buffers (device):
+ *   d_obs [n_steps][E][D]      observation the step's action was chosen from
+ *   d_actions [n_steps][E][N]  sampled levels
+ *   d_reward [n_steps][E], d_done [n_steps][E] (each NULL to skip)
+ *   d_logits NULL or [n_steps][E][N][n_levels].
+ *   The launches are captured into a CUDA graph on the first call with a
+ *   given (n_steps, buffers, launch shape) and replayed afterwards.
+ * A tensor-core wait that runs out of time (it should not) makes chx_check
+ * return CHX_ETIMEOUT; the results of that call are then invalid. */
+int chx_policy_load(chx_handle* h, int32_t hidden, const uint16_t* h_w1, const float* h_b1,
+                    const uint16_t* h_w2, const float* h_b2, const uint16_t* h_w3, const float* h_b3);
+int chx_policy_act(chx_handle* h, const float* d_obs, int8_t* d_actions, float* d_logits, void* stream);
+int chx_policy_rollout(chx_handle* h, int32_t n_steps, float* d_obs, int8_t* d_actions, float* d_reward,
+                       uint8_t* d_done, float* d_logits, void* stream);
+
 /* ---- serving loop ------------------------------------------------------------
  * A pool of device-resident stations stepped by requests from many actors with
  * continuous batching (the reset/step interface of the paper's Gym-style
@@ -350,7 +392,8 @@ typedef struct chx_srv_sim_result {
 int chx_srv_simulate(chx_srv* s, const chx_srv_sim_cfg* c, const int32_t* h_station_ids, chx_srv_sim_result* res);
 
 /* Synchronise the handle's work on `stream` and report (then clear) the
- * device-side fault flag: CHX_EFAULT if a kernel saw bad input. */
+ * device-side fault flags: CHX_ETIMEOUT if a policy kernel's wait ran out,
+ * else CHX_EFAULT if a kernel saw bad input. */
 int chx_check(chx_handle* h, void* stream);
 
 #ifdef __cplusplus

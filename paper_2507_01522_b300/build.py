@@ -15,8 +15,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libchargax_b300.so")
 BUILD = os.path.join(ROOT, "_build")
-SOURCES = ["handle.cu", "step_plain.cu", "step_fused.cu", "aux_kernels.cu", "noalloc.cu", "serve.cu"]
-HEADERS = ["chx_device.cuh", "chx_kernels.h", "chx_handle.h"]
+SOURCES = ["handle.cu", "step_plain.cu", "step_fused.cu", "aux_kernels.cu", "noalloc.cu", "serve.cu", "policy.cu",
+           "policy_api.cu"]
+HEADERS = ["chx_device.cuh", "chx_kernels.h", "chx_handle.h", "chx_tc.cuh"]
 
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

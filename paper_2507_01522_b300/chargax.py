@@ -25,7 +25,7 @@ EXPORTS = (
     "chx_create", "chx_destroy", "chx_last_error", "chx_n_envs", "chx_n_ports_total", "chx_port_offsets",
     "chx_obs_size", "chx_reset", "chx_step", "chx_step_n", "chx_rollout", "chx_rollout_host", "chx_step_host",
     "chx_autotune", "chx_set_launch", "chx_observe", "chx_get_state", "chx_set_state", "chx_stats", "chx_save",
-    "chx_load", "chx_check", "chx_rollout_noalloc",
+    "chx_load", "chx_check", "chx_rollout_noalloc", "chx_policy_load", "chx_policy_act", "chx_policy_rollout",
     "chx_srv_start", "chx_srv_stop", "chx_srv_admit", "chx_srv_evict", "chx_srv_submit", "chx_srv_wait",
     "chx_srv_test", "chx_srv_stats", "chx_srv_simulate",
 )
@@ -117,6 +117,8 @@ def load_library(path: str = LIB_PATH):
         "chx_get_state": [vp] + [vp] * 13, "chx_set_state": [vp] + [vp] * 13, "chx_stats": [vp] + [vp] * 6,
         "chx_save": [vp, vp, vp], "chx_load": [vp, vp, C.c_size_t], "chx_check": [vp, vp],
         "chx_rollout_noalloc": [vp, i32, vp, vp, vp, vp],
+        "chx_policy_load": [vp, i32, vp, vp, vp, vp, vp, vp], "chx_policy_act": [vp, vp, vp, vp, vp],
+        "chx_policy_rollout": [vp, i32, vp, vp, vp, vp, vp, vp],
         "chx_srv_start": [vp, vp], "chx_srv_stop": [vp], "chx_srv_admit": [vp, vp, u64, vp],
         "chx_srv_evict": [vp, vp, i32], "chx_srv_submit": [vp, vp, vp], "chx_srv_wait": [vp, u64, i64, vp],
         "chx_srv_test": [vp, u64, vp, vp], "chx_srv_stats": [vp, vp], "chx_srv_simulate": [vp, vp, vp, vp],
@@ -285,6 +287,30 @@ class Batch:
     def load(self, blob: bytes):
         buf = np.frombuffer(blob, np.uint8).copy()
         _check(_lib.chx_load(self.h, _np_ptr(buf), len(blob)))
+
+    # ---- on-device policy -----------------------------------------------
+    def policy_load(self, w1, b1, w2, b2, w3, b3):
+        """chx_policy_load.  Weights are float arrays whose values are BF16
+        numbers (their top 16 bits are passed); shapes [H][D], [H][H],
+        [N * n_levels][H]; biases float32."""
+        def bits(w):
+            w = np.ascontiguousarray(w, dtype=np.float32)
+            u = w.view(np.uint32)
+            if np.any(u & 0xFFFF):
+                raise ValueError("policy weights must be BF16 values")
+            return np.ascontiguousarray((u >> 16).astype(np.uint16))
+        ws = [bits(w1), bits(w2), bits(w3)]
+        bs = [np.ascontiguousarray(b, dtype=np.float32) for b in (b1, b2, b3)]
+        self._policy_keep = ws + bs
+        _check(_lib.chx_policy_load(self.h, int(np.shape(w1)[0]), _np_ptr(ws[0]), _np_ptr(bs[0]), _np_ptr(ws[1]),
+                                    _np_ptr(bs[1]), _np_ptr(ws[2]), _np_ptr(bs[2])))
+
+    def policy_act(self, obs, actions, logits=None, stream=None):
+        _check(_lib.chx_policy_act(self.h, _dev_ptr(obs), _dev_ptr(actions), _dev_ptr(logits), _stream_ptr(stream)))
+
+    def policy_rollout(self, n_steps: int, obs, actions, reward=None, done=None, logits=None, stream=None):
+        _check(_lib.chx_policy_rollout(self.h, n_steps, _dev_ptr(obs), _dev_ptr(actions), _dev_ptr(reward),
+                                       _dev_ptr(done), _dev_ptr(logits), _stream_ptr(stream)))
 
 
 def _stations_struct(st, keep):

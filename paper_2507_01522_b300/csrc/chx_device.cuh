@@ -20,6 +20,7 @@ constexpr int kNumClasses = 5;             // 8, 16, 32, 64, 128
 constexpr int kPoissonMax = 127;
 constexpr int kCdfLen = 128;               // CDF entries per (row, step): F_0..F_126, then +inf
 constexpr uint32_t kPurposeArrival = 0u, kPurposeCar = 1u, kPurposeAction = 2u, kPurposeDay = 3u;
+constexpr uint32_t kPurposePolicy = 4u;   // policy sample: (env, step, charger / 4, 4), word charger % 4
 
 // per-charger static bits
 constexpr uint32_t kMetaDC = 1u, kMetaValid = 2u, kMetaHead = 4u, kMetaTail = 8u;
@@ -35,6 +36,7 @@ __host__ __device__ constexpr int tile_epw(int c) { return 32 / tile_lpe(c); }
 
 // device error bits
 constexpr uint32_t kErrActionRange = 1u;
+constexpr uint32_t kErrPolicyWait = 2u;     // a tensor-core wait of the policy kernel timed out
 
 struct DevParams {
     int ep_len, n_levels, n_days;

@@ -26,6 +26,36 @@ struct GraphKey {
     }
 };
 
+// the rollout with the on-device policy: graph cache key
+struct PolicyGraphKey {
+    int n_steps = 0;
+    float* obs = nullptr;
+    int8_t* actions = nullptr;
+    float* reward = nullptr;
+    uint8_t* done = nullptr;
+    float* logits = nullptr;
+    int w = 0;
+    bool valid = false;
+    bool operator==(const PolicyGraphKey& o) const
+    {
+        return valid && o.valid && n_steps == o.n_steps && obs == o.obs && actions == o.actions &&
+               reward == o.reward && done == o.done && logits == o.logits && w == o.w;
+    }
+};
+
+// weights and geometry of the loaded policy (see PolicyArgs)
+struct PolicyState {
+    bool loaded = false;
+    int obs_dim = 0, n_ports = 0, n_levels = 0, n_out_pad = 0, rows = 0;
+    int ch1 = 0, ks1_last = 0, parts3 = 0, n3_last = 0;
+    uint16_t* d_w = nullptr;               // [rows][256] BF16 bits
+    float* d_bias = nullptr;               // [512 + n_out_pad]
+    CUtensorMap map{};                     // over-aligned type; the handle is allocated with new
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    PolicyGraphKey key{};
+};
+
 int fail(int code, const std::string& msg);
 int cuda_fail(cudaError_t e, const char* what);
 
@@ -60,6 +90,7 @@ struct chx_handle {
     chx::GraphKey graph_key{};
     void* staging[8] = {};
     size_t staging_bytes[8] = {};
+    chx::PolicyState policy;
 };
 
 namespace chx {
@@ -74,4 +105,5 @@ int build_handle(const chx_stations* st, const chx_env_params* prm, const chx_ex
 int enqueue_fused(chx_handle* h, int k_steps, const int8_t* actions, long long lda, float* reward, uint8_t* done,
                   long long ld_out, float* obs, int warps, cudaStream_t st);
 void free_graph(chx_handle* h);
+void free_policy(chx_handle* h);
 }  // namespace chx

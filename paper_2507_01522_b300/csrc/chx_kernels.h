@@ -1,6 +1,7 @@
 // chx_kernels.h -- host-side launchers of the device kernels.
 #pragma once
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "chx_device.cuh"
@@ -49,5 +50,33 @@ void launch_observe(const DevBatch& b, const DevParams& p, float* obs, cudaStrea
 // reset listed slots (station id = slot), one 64-bit seed per entry
 void launch_reset_slots(const DevBatch& b, const DevParams& p, const int32_t* slots, const unsigned long long* seeds,
                         int n, cudaStream_t st);
+
+
+// ---- policy (3-layer BF16 MLP on the tensor cores + fused sampling) ------
+constexpr int kPolicyHidden = 256;
+constexpr int kPolicyMaxPorts = 32;
+constexpr int kPolicyGroup = 12;           // logit columns per charger (levels padded)
+constexpr int kPolicyMaxOut = kPolicyMaxPorts * kPolicyGroup;
+
+// Weights: one BF16 matrix [512 + n_out_pad][256], row-major, streamed by a
+// TMA map with 64 x 128 boxes and 128-byte swizzle.  Rows 0-255 = W1 (columns
+// >= obs_dim zero), 256-511 = W2, 512 + 12 c + j = row c * n_levels + j of W3
+// (j < n_levels; other rows zero).  bias = b1 | b2 | b3 in the same row order.
+struct PolicyArgs {
+    const float* obs;                      // [E][obs_dim] FP32
+    int E, obs_dim, n_ports, n_levels;
+    int ch1, ks1_last;                     // layer-1 K chunks of 64, K = 16 steps in the last one
+    int parts3, n3_last;                   // layer-3 N parts of 128, N of the last part
+    int n_out_pad;                         // 12 * n_ports rounded up to 16
+    const float* bias;
+    const int32_t* user_to_slot;
+    const uint32_t *gstep, *key0, *key1;   // per station slot
+    float* logits;                         // NULL or [E][n_ports][n_levels]
+    int8_t* actions;                       // [E][n_ports]
+    uint32_t* err;
+};
+int policy_smem_bytes();
+cudaError_t policy_prepare();              // once per process, before capture
+cudaError_t launch_policy(const CUtensorMap& wmap, const PolicyArgs& a, int sm_count, cudaStream_t st);
 
 }  // namespace chx

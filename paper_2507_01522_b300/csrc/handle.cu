@@ -393,6 +393,7 @@ extern "C" int chx_destroy(chx_handle* h)
 {
     if (!h) return CHX_OK;
     free_graph(h);
+    free_policy(h);
     for (void* p : h->bufs) cudaFree(p);
     for (void* p : h->staging) cudaFree(p);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -970,6 +971,7 @@ extern "C" int chx_check(chx_handle* h, void* stream)
     CUDA_TRY(cudaMemcpy(&err, h->b.err, sizeof err, cudaMemcpyDeviceToHost));
     if (err) {
         CUDA_TRY(cudaMemset(h->b.err, 0, sizeof(uint32_t)));
+        if (err & kErrPolicyWait) return fail(CHX_ETIMEOUT, "a tensor-core wait of the policy kernel ran out of time");
         return fail(CHX_EFAULT, "a kernel saw an action level outside 0..n_levels-1 (clamped)");
     }
     return CHX_OK;
