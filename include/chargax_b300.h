@@ -277,18 +277,26 @@ int chx_load(chx_handle* h, const void* h_buf, size_t size);
  * chx_policy_rollout: n_steps steps of "act, then step" from the current
  *   state, written to caller buffers (device):
  *   d_obs [n_steps][E][D]      observation the step's action was chosen from
+ *                              (may be NULL in the fused form)
  *   d_actions [n_steps][E][N]  sampled levels
  *   d_reward [n_steps][E], d_done [n_steps][E] (each NULL to skip)
  *   d_logits NULL or [n_steps][E][N][n_levels].
- *   The launches are captured into a CUDA graph on the first call with a
- *   given (n_steps, buffers, launch shape) and replayed afterwards.
+ *   form CHX_ROLLOUT_FUSED: one kernel launch; each CTA keeps 128 envs on
+ *   its SM for all n_steps (state in tensor memory, weights streamed from
+ *   L2), needs N * n_levels <= 352 (else CHX_EINVAL).  CHX_ROLLOUT_SPLIT:
+ *   per step one policy launch and one environment-step launch, captured
+ *   into a CUDA graph on the first call with the same (n_steps, buffers,
+ *   launch shape) and replayed afterwards.  Both forms compute the same
+ *   function (FP32 sums may round differently) and leave the same state.
  * A tensor-core wait that runs out of time (it should not) makes chx_check
  * return CHX_ETIMEOUT; the results of that call are then invalid. */
+#define CHX_ROLLOUT_FUSED 0
+#define CHX_ROLLOUT_SPLIT 1
 int chx_policy_load(chx_handle* h, int32_t hidden, const uint16_t* h_w1, const float* h_b1,
                     const uint16_t* h_w2, const float* h_b2, const uint16_t* h_w3, const float* h_b3);
 int chx_policy_act(chx_handle* h, const float* d_obs, int8_t* d_actions, float* d_logits, void* stream);
 int chx_policy_rollout(chx_handle* h, int32_t n_steps, float* d_obs, int8_t* d_actions, float* d_reward,
-                       uint8_t* d_done, float* d_logits, void* stream);
+                       uint8_t* d_done, float* d_logits, int32_t form, void* stream);
 
 /* ---- serving loop ------------------------------------------------------------
  * A pool of device-resident stations stepped by requests from many actors with

@@ -31,6 +31,7 @@ EXPORTS = (
 )
 
 CHX_SRV_STEP, CHX_SRV_RESET = 0, 1
+CHX_ROLLOUT_FUSED, CHX_ROLLOUT_SPLIT = 0, 1
 
 
 class ChxError(RuntimeError):
@@ -118,7 +119,7 @@ def load_library(path: str = LIB_PATH):
         "chx_save": [vp, vp, vp], "chx_load": [vp, vp, C.c_size_t], "chx_check": [vp, vp],
         "chx_rollout_noalloc": [vp, i32, vp, vp, vp, vp],
         "chx_policy_load": [vp, i32, vp, vp, vp, vp, vp, vp], "chx_policy_act": [vp, vp, vp, vp, vp],
-        "chx_policy_rollout": [vp, i32, vp, vp, vp, vp, vp, vp],
+        "chx_policy_rollout": [vp, i32, vp, vp, vp, vp, vp, i32, vp],
         "chx_srv_start": [vp, vp], "chx_srv_stop": [vp], "chx_srv_admit": [vp, vp, u64, vp],
         "chx_srv_evict": [vp, vp, i32], "chx_srv_submit": [vp, vp, vp], "chx_srv_wait": [vp, u64, i64, vp],
         "chx_srv_test": [vp, u64, vp, vp], "chx_srv_stats": [vp, vp], "chx_srv_simulate": [vp, vp, vp, vp],
@@ -308,9 +309,12 @@ class Batch:
     def policy_act(self, obs, actions, logits=None, stream=None):
         _check(_lib.chx_policy_act(self.h, _dev_ptr(obs), _dev_ptr(actions), _dev_ptr(logits), _stream_ptr(stream)))
 
-    def policy_rollout(self, n_steps: int, obs, actions, reward=None, done=None, logits=None, stream=None):
+    def policy_rollout(self, n_steps: int, obs, actions, reward=None, done=None, logits=None, form=None,
+                       stream=None):
+        """chx_policy_rollout; form CHX_ROLLOUT_FUSED (default) or CHX_ROLLOUT_SPLIT."""
+        form = CHX_ROLLOUT_FUSED if form is None else form
         _check(_lib.chx_policy_rollout(self.h, n_steps, _dev_ptr(obs), _dev_ptr(actions), _dev_ptr(reward),
-                                       _dev_ptr(done), _dev_ptr(logits), _stream_ptr(stream)))
+                                       _dev_ptr(done), _dev_ptr(logits), form, _stream_ptr(stream)))
 
 
 def _stations_struct(st, keep):

@@ -55,28 +55,45 @@ void launch_reset_slots(const DevBatch& b, const DevParams& p, const int32_t* sl
 // ---- policy (3-layer BF16 MLP on the tensor cores + fused sampling) ------
 constexpr int kPolicyHidden = 256;
 constexpr int kPolicyMaxPorts = 32;
-constexpr int kPolicyGroup = 12;           // logit columns per charger (levels padded)
-constexpr int kPolicyMaxOut = kPolicyMaxPorts * kPolicyGroup;
+constexpr int kPolicyGroup = 12;           // most action levels the sampler handles
 
 // Weights: one BF16 matrix [512 + n_out_pad][256], row-major, streamed by a
 // TMA map with 64 x 128 boxes and 128-byte swizzle.  Rows 0-255 = W1 (columns
-// >= obs_dim zero), 256-511 = W2, 512 + 12 c + j = row c * n_levels + j of W3
-// (j < n_levels; other rows zero).  bias = b1 | b2 | b3 in the same row order.
+// >= obs_dim zero), 256-511 = W2, 512 + c * L + j = level j of charger c
+// (W3; rows up to n_out_pad zero).  bias = b1 | b2 | b3 in the same order.
 struct PolicyArgs {
-    const float* obs;                      // [E][obs_dim] FP32
+    const float* obs;                      // [E][obs_dim] FP32 (k_policy)
     int E, obs_dim, n_ports, n_levels;
     int ch1, ks1_last;                     // layer-1 K chunks of 64, K = 16 steps in the last one
     int parts3, n3_last;                   // layer-3 N parts of 128, N of the last part
-    int n_out_pad;                         // 12 * n_ports rounded up to 16
+    int n_out_pad;                         // n_ports * n_levels rounded up to 16
     const float* bias;
     const int32_t* user_to_slot;
     const uint32_t *gstep, *key0, *key1;   // per station slot
-    float* logits;                         // NULL or [E][n_ports][n_levels]
-    int8_t* actions;                       // [E][n_ports]
+    float* logits;                         // NULL or [(T)][E][n_ports][n_levels]
+    int8_t* actions;                       // [(T)][E][n_ports]
     uint32_t* err;
 };
+
+// The fused rollout: T x (MLP pass, sample, environment step) per 128-env
+// tile, all stations of one size class (class size C >= n_ports).
+struct RolloutArgs {
+    PolicyArgs pol;
+    DevBatch b;
+    DevParams p;
+    int T;
+    float* obs_out;                        // NULL or [T][E][obs_dim]
+    float* reward;                         // NULL or [T][E]
+    uint8_t* done;                         // NULL or [T][E]
+    long long port_base;                   // charger slot of the class's first station
+    int env_base;                          // station slot of the class's first station
+    int C;                                 // charger slots per station
+};
+
 int policy_smem_bytes();
 cudaError_t policy_prepare();              // once per process, before capture
 cudaError_t launch_policy(const CUtensorMap& wmap, const PolicyArgs& a, int sm_count, cudaStream_t st);
+bool rollout_fits(int n_out_pad);          // logits leave TMEM room for the env state
+cudaError_t launch_rollout(const CUtensorMap& wmap, const RolloutArgs& r, cudaStream_t st);
 
 }  // namespace chx

@@ -1,25 +1,36 @@
-// policy.cu -- the on-device policy of a rollout: a 3-layer MLP
+// policy.cu -- the on-device policy: a 3-layer MLP
 // obs (D = 8 + 6N) -> 256 -> 256 -> N x L logits (ReLU between layers; the
-// PPO actor of the paper's Table "PPO hyper-parameters" with its random
-// initialisation), BF16 operands, FP32 accumulation, on the 5th-generation
-// tensor cores, with the categorical sample of every charger's action level
-// fused into the last layer's epilogue.
+// actor of the PPO agent of the paper's Sec. 5, randomly initialised), BF16
+// operands, FP32 accumulation, on the 5th-generation tensor cores, with the
+// categorical sample of every charger's action level fused into the last
+// layer's epilogue.  Two kernels share it:
 //
-// One CTA per 128-env tile (persistent over tiles when there are more tiles
-// than SMs).  Roles:
+//   k_policy   actions of every env from given observations (one MLP pass
+//              per 128-env tile);
+//   k_rollout  the fused rollout: one CTA owns 128 envs for all T steps and
+//              alternates "observe -> MLP -> sample -> environment step"
+//              without leaving the SM.  The env state lives in TMEM next to
+//              the accumulators (lane = env, see kCol*); the environment step
+//              runs one thread per env.
+//
+// Roles (both kernels, 10 warps):
 //   warp 0, lane 0   TMA producer: streams the weights, one 128-row x 64-col
-//                    BF16 box (16 KB) per stage, through a kStages ring;
+//                    BF16 box (16 KB) per stage, through a ring of stages;
 //   warp 1           owns the TMEM allocation (512 columns); lane 0 issues
-//                    every tcgen05.mma (M = 128, N = 128 per part, K = 16);
-//   warps 2..9       load the tile's observations (FP32 -> BF16, swizzled),
-//                    run the epilogues (bias, ReLU, BF16 into the next
-//                    layer's A operand) and the sampling.
-// Epilogue warp w reads TMEM lanes 32 (w % 4) .. +31 (one env per thread);
-// warps 2-5 take columns 0-127 of a layer (part 0), warps 6-9 columns
-// 128-255 (part 1), so each half starts as soon as its part's MMAs finish,
-// and the next layer's MMAs over K = 0..127 start as soon as half 0 is
-// written.  Every wait is bounded (kWaitCycles); a timeout sets
-// kErrPolicyWait and unwinds without hanging.
+//                    every tcgen05.mma (M = 128, N <= 128 per part, K = 16);
+//   warps 2..9       "workers": write the layer-1 operand, run the epilogues
+//                    (bias, ReLU, BF16 into the next layer's operand) and the
+//                    sampling.  Worker warp w reads TMEM lanes 32 (w % 4) ..
+//                    +31 (one env per thread); warps 2-5 take accumulator
+//                    columns 0-127, warps 6-9 columns 128-255 (chargers 0-15
+//                    and 16-31 in the sampling).  In k_rollout warps 2-5 also
+//                    own the env rows of their lane quadrant.
+//
+// One operand buffer A (128 x 256 BF16, swizzled) holds the observations,
+// then h1, then h2: an epilogue writes A only after every MMA of its layer
+// has finished.  Every wait is bounded (kWaitCycles); a timeout sets
+// kErrPolicyWait and a shared flag that makes every role skip its remaining
+// waits and asynchronous work, so the kernel always ends.
 #include <cuda.h>
 
 #include "chx_kernels.h"
@@ -33,102 +44,140 @@ using namespace tc;
 
 constexpr int kM = 128;                    // envs per tile (MMA M, TMEM lanes)
 constexpr int kChunkBytes = kM * 128;      // 128 rows x 64 BF16
-constexpr int kActBytes = 4 * kChunkBytes; // 128 x 256 BF16 activation tile
-constexpr int kStages = 5;
+constexpr int kActBytes = 4 * kChunkBytes; // 128 x 256 BF16 operand
 constexpr int kStageBytes = 128 * 128;     // 128 weight rows x 64 BF16
-constexpr int kEpiWarps = 8;
-constexpr int kThreads = (2 + kEpiWarps) * 32;
-constexpr int kSmemBytes = 1024 + 2 * kActBytes + kStages * kStageBytes;
+constexpr int kWorkerWarps = 8;
+constexpr int kWorkers = kWorkerWarps * 32;
+constexpr int kThreads = (2 + kWorkerWarps) * 32;
 constexpr uint32_t kTmemCols = 512;
-constexpr int kGroup = kPolicyGroup;
+constexpr int kPolStages = 9;              // weight ring of k_policy
+constexpr int kRollStages = 6;             // weight ring of k_rollout
+constexpr int kMaxStages = kPolStages;
+constexpr int kBarWorkers = 1;             // named barrier of the worker warps
 
-struct Bars {
-    uint64_t full[kStages], empty[kStages];
-    uint64_t accb[2];                      // layer 1/2 part p accumulated
-    uint64_t acc3;                         // layer 3 accumulated
-    uint64_t xrdy;                         // observations of the tile in act0
-    uint64_t hrdy[2];                      // half h of the next layer's input written
-    uint64_t fin;                          // every MMA of this CTA done
+// k_rollout: TMEM columns of the env state, 32 per field (charger c at +c)
+constexpr int kColSoc = 352, kColErem = 384, kColCap = 416, kColRbar = 448;
+constexpr int kColPack = 480;              // remaining stay | meta << 8
+constexpr int kColPw = 0;                  // last applied power, parked in accumulator columns between MLP passes
+constexpr int kMaxObs = 8 + 6 * kPolicyMaxPorts;
+
+struct Sync {
+    uint64_t full[kMaxStages], empty[kMaxStages];
+    uint64_t acc;                          // a layer is accumulated (3 completions per pass)
+    uint64_t xrdy;                         // layer-1 operand written (kWorkers arrivals)
+    uint64_t hrdy;                         // h1 / h2 written (kWorkers arrivals, 2 per pass)
+    uint64_t fin;                          // every MMA of the CTA finished
     uint32_t tmem;
+    int bad;                               // a wait timed out: skip everything
 };
 
-__device__ __forceinline__ void raise(uint32_t* err) { atomicOr(err, kErrPolicyWait); }
+__device__ __forceinline__ bool is_bad(const Sync& S) { return *reinterpret_cast<const volatile int*>(&S.bad) != 0; }
 
-// ---- TMA producer -------------------------------------------------------
-__device__ void produce(const CUtensorMap* wmap, const PolicyArgs& a, unsigned char* ring, Bars& B, int n_tiles)
+// bounded wait; on timeout raise the error and the shared flag; returns
+// immediately (false) once the flag is set
+__device__ __forceinline__ bool wait_sync(uint64_t* bar, uint32_t parity, Sync& S, uint32_t* err)
+{
+    if (mbar_try(bar, parity)) return true;
+    const long long t0 = clock64();
+    for (;;) {
+        if (mbar_try(bar, parity)) return true;
+        if (is_bad(S)) return false;
+        if (clock64() - t0 > kWaitCycles) {
+            *reinterpret_cast<volatile int*>(&S.bad) = 1;
+            atomicOr(err, kErrPolicyWait);
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void init_sync(Sync& S, int n_stages)
+{
+    for (int s = 0; s < n_stages; ++s) {
+        mbar_init(&S.full[s], 1);
+        mbar_init(&S.empty[s], 1);
+    }
+    mbar_init(&S.acc, 1);
+    mbar_init(&S.fin, 1);
+    mbar_init(&S.xrdy, kWorkers);
+    mbar_init(&S.hrdy, kWorkers);
+    S.bad = 0;
+    mbar_fence_init();
+}
+
+// ---- TMA producer: n_passes MLP passes worth of weight stages ------------
+template <int NS>
+__device__ void produce(const CUtensorMap* wmap, const PolicyArgs& a, unsigned char* ring, Sync& S, int n_passes)
 {
     uint32_t s = 0;
-    bool ok = true;
-    for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x)
-        for (int L = 0; L < 3 && ok; ++L) {
+    int last[NS];
+#pragma unroll
+    for (int j = 0; j < NS; ++j) last[j] = -1;
+    for (int it = 0; it < n_passes; ++it)
+        for (int L = 0; L < 3; ++L) {
             const int parts = L < 2 ? 2 : a.parts3;
             const int chunks = L == 0 ? a.ch1 : 4;
-            for (int p = 0; p < parts && ok; ++p)
+            for (int p = 0; p < parts; ++p)
                 for (int k = 0; k < chunks; ++k, ++s) {
-                    const uint32_t slot = s % kStages;
-                    if (s >= (uint32_t)kStages && !mbar_wait(&B.empty[slot], ((s / kStages) - 1) & 1)) {
-                        raise(a.err);
-                        ok = false;
-                        break;
-                    }
-                    mbar_arrive_expect_tx(&B.full[slot], kStageBytes);
-                    tma_load_2d(ring + slot * kStageBytes, wmap, k * 64, L * 256 + p * 128, &B.full[slot]);
+                    const uint32_t slot = s % NS;
+                    if (s >= (uint32_t)NS) wait_sync(&S.empty[slot], ((s / NS) - 1) & 1, S, a.err);
+                    if (is_bad(S)) continue;
+                    mbar_arrive_expect_tx(&S.full[slot], kStageBytes);
+                    tma_load_2d(ring + slot * kStageBytes, wmap, k * 64, L * 256 + p * 128, &S.full[slot]);
+#pragma unroll
+                    for (int j = 0; j < NS; ++j)
+                        if (j == (int)slot) last[j] = (int)s;
                 }
         }
     // nothing may still be landing in shared memory when the CTA exits
-    for (uint32_t j = s > (uint32_t)kStages ? s - kStages : 0; j < s; ++j)
-        if (!mbar_wait(&B.full[j % kStages], (j / kStages) & 1)) raise(a.err);
+#pragma unroll
+    for (int j = 0; j < NS; ++j)
+        if (last[j] >= 0 && !mbar_wait(&S.full[j], ((uint32_t)last[j] / NS) & 1)) atomicOr(a.err, kErrPolicyWait);
 }
 
-// ---- MMA issuer ---------------------------------------------------------
-__device__ void issue(const PolicyArgs& a, unsigned char* act0, unsigned char* act1, unsigned char* ring, Bars& B,
-                      uint32_t tmem, int n_tiles)
+// ---- MMA issuer ------------------------------------------------------------
+template <int NS>
+__device__ void issue(const PolicyArgs& a, unsigned char* A, unsigned char* ring, Sync& S, uint32_t tmem,
+                      int n_passes)
 {
     uint32_t s = 0;
-    bool ok = true;
     const uint32_t id128 = idesc_bf16_f32(kM, 128);
-    int i = 0;
-    for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++i) {
-        if (!mbar_wait(&B.xrdy, i & 1)) { ok = false; break; }
+    const uint32_t id3 = idesc_bf16_f32(kM, a.n3_last);
+    for (int it = 0; it < n_passes; ++it) {
+        wait_sync(&S.xrdy, it & 1, S, a.err);
         fence_after();
-        for (int L = 0; L < 3 && ok; ++L) {
-            unsigned char* A = (L == 1) ? act1 : act0;
+        for (int L = 0; L < 3; ++L) {
+            if (L > 0) {
+                wait_sync(&S.hrdy, (2 * it + L - 1) & 1, S, a.err);
+                fence_after();
+            }
             const int parts = L < 2 ? 2 : a.parts3;
             const int chunks = L == 0 ? a.ch1 : 4;
-            for (int p = 0; p < parts && ok; ++p) {
-                const int n = (L == 2 && p == parts - 1) ? a.n3_last : 128;
-                const uint32_t id = n == 128 ? id128 : idesc_bf16_f32(kM, n);
+            for (int p = 0; p < parts; ++p) {
+                const uint32_t id = (L == 2 && p == parts - 1) ? id3 : id128;
                 for (int k = 0; k < chunks; ++k, ++s) {
-                    // layers 2 and 3 read the previous epilogue's halves
-                    if (L > 0 && p == 0 && (k == 0 || k == 2)) {
-                        if (!mbar_wait(&B.hrdy[k >> 1], (2 * i + L - 1) & 1)) { ok = false; break; }
-                        fence_after();
-                    }
-                    const uint32_t slot = s % kStages;
-                    if (!mbar_wait(&B.full[slot], (s / kStages) & 1)) { ok = false; break; }
+                    const uint32_t slot = s % NS;
+                    wait_sync(&S.full[slot], (s / NS) & 1, S, a.err);
                     fence_after();
+                    if (is_bad(S)) continue;
                     const int nks = (L == 0 && k == chunks - 1) ? a.ks1_last : 4;
                     unsigned char* bst = ring + slot * kStageBytes;
                     for (int j = 0; j < nks; ++j)
                         mma_bf16(tmem + (uint32_t)(p * 128), sdesc_sw128(A + k * kChunkBytes + j * 32),
                                  sdesc_sw128(bst + j * 32), id, (k | j) != 0);
-                    mma_commit(&B.empty[slot]);
+                    mma_commit(&S.empty[slot]);
                 }
-                if (L < 2) mma_commit(&B.accb[p]);
             }
+            if (!is_bad(S)) mma_commit(&S.acc);
         }
-        if (ok) mma_commit(&B.acc3);
     }
-    if (!ok) raise(a.err);
-    mma_commit(&B.fin);
-    if (!mbar_wait(&B.fin, 0)) raise(a.err);
+    mma_commit(&S.fin);
+    if (!mbar_wait(&S.fin, 0)) atomicOr(a.err, kErrPolicyWait);
 }
 
-// ---- epilogue of layers 1 and 2: bias, ReLU, BF16, swizzled store -------
-__device__ __forceinline__ void hidden_epilogue(uint32_t taddr, const float* bias, unsigned char* dst, int row,
+// ---- epilogue of layers 1 and 2: bias, ReLU, BF16 into A --------------------
+__device__ __forceinline__ void hidden_epilogue(uint32_t taddr, const float* __restrict__ bias, uint32_t abase, int row,
                                                 int col0)
 {
-    const uint32_t dbase = smem_addr(dst);
 #pragma unroll 1
     for (int blk = 0; blk < 4; ++blk) {
         const int c = col0 + 32 * blk;
@@ -138,12 +187,13 @@ __device__ __forceinline__ void hidden_epilogue(uint32_t taddr, const float* bia
         uint32_t q[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-            const float x0 = fmaxf(__uint_as_float(v[2 * j]) + bias[c + 2 * j], 0.f);
-            const float x1 = fmaxf(__uint_as_float(v[2 * j + 1]) + bias[c + 2 * j + 1], 0.f);
+            const float2 bb = __ldg(reinterpret_cast<const float2*>(bias + c + 2 * j));
+            const float x0 = fmaxf(__uint_as_float(v[2 * j]) + bb.x, 0.f);
+            const float x1 = fmaxf(__uint_as_float(v[2 * j + 1]) + bb.y, 0.f);
             q[j] = pack_bf16x2(x0, x1);
         }
         const int unit0 = (c & 63) >> 3;
-        const uint32_t rbase = dbase + (uint32_t)((c >> 6) * kChunkBytes + row * 128);
+        const uint32_t rbase = abase + (uint32_t)((c >> 6) * kChunkBytes + row * 128);
 #pragma unroll
         for (int u = 0; u < 4; ++u)
             st_shared_v4(rbase + ((uint32_t)((unit0 + u) ^ (row & 7)) << 4), q[4 * u], q[4 * u + 1], q[4 * u + 2],
@@ -151,171 +201,191 @@ __device__ __forceinline__ void hidden_epilogue(uint32_t taddr, const float* bia
     }
 }
 
-// ---- sampling of the action levels of chargers c0..c0+3 of one env ------
-// Inverse transform of the softmax: level = #{j < L-1 : e_0 + .. + e_j <= u S}
-// with e_j = exp(l_j - max l), S = sum e_j, u from the policy Philox word.
-__device__ __forceinline__ uint32_t sample4(const uint32_t (&v)[48], const float* b3, int c0, int n_ports,
+// ---- sampling ----------------------------------------------------------------
+// Inverse transform of the softmax of charger c's logits l_0..l_{L-1}:
+// level = #{j < L-1 : e_0 + .. + e_j <= u S}, e_j = exp(l_j - max l),
+// S = sum e_j, u from word c % 4 of the policy Philox block (env, step, c / 4).
+template <int LT>
+__device__ __forceinline__ uint32_t sample4(const uint32_t (&v)[48], const float* __restrict__ b3, int c0, int n_ports,
                                            int n_levels, uint4 words, float* logits_out)
 {
+    const int L = LT ? LT : n_levels;
     uint32_t packed = 0;
 #pragma unroll
     for (int ci = 0; ci < 4; ++ci) {
         const int c = c0 + ci;
         if (c >= n_ports) break;
-        float l[kGroup];
+        float l[kPolicyGroup];
         float m = -INFINITY;
 #pragma unroll
-        for (int j = 0; j < kGroup; ++j) {
-            l[j] = __uint_as_float(v[kGroup * ci + j]) + b3[kGroup * c + j];
-            if (j < n_levels) m = fmaxf(m, l[j]);
+        for (int j = 0; j < kPolicyGroup; ++j) {
+            l[j] = j < L ? __uint_as_float(v[L * ci + j]) + __ldg(b3 + L * c + j) : 0.f;
+            if (j < L) m = fmaxf(m, l[j]);
         }
-        float e[kGroup], S = 0.f;
+        float e[kPolicyGroup], S = 0.f;
 #pragma unroll
-        for (int j = 0; j < kGroup; ++j) {
-            e[j] = j < n_levels ? __expf(l[j] - m) : 0.f;
+        for (int j = 0; j < kPolicyGroup; ++j) {
+            e[j] = j < L ? __expf(l[j] - m) : 0.f;
             S += e[j];
         }
         const float T = unit_of(word_of(words, (uint32_t)ci)) * S;
         float cum = 0.f;
         int level = 0;
 #pragma unroll
-        for (int j = 0; j < kGroup - 1; ++j) {
+        for (int j = 0; j < kPolicyGroup - 1; ++j) {
             cum += e[j];
-            level += (j < n_levels - 1 && cum <= T) ? 1 : 0;
+            level += (j < L - 1 && cum <= T) ? 1 : 0;
         }
         packed |= (uint32_t)level << (8 * ci);
         if (logits_out)
-            for (int j = 0; j < n_levels; ++j) logits_out[(long long)ci * n_levels + j] = l[j];
+#pragma unroll
+            for (int j = 0; j < kPolicyGroup; ++j)
+                if (j < L) logits_out[(long long)ci * L + j] = l[j];
     }
     return packed;
 }
 
-__device__ void epilogue(const PolicyArgs& a, unsigned char* act0, unsigned char* act1, Bars& B, const float* bias_s,
-                         uint32_t tmem, int n_tiles)
+// Levels of chargers 16h .. 16h+15 of the env in TMEM lane `tl`, four per
+// block; returns them packed 4 per word.
+template <int LT>
+__device__ __forceinline__ void sample_row(const PolicyArgs& a, uint32_t tl, int h, long long env, bool live,
+                                           uint32_t g, uint32_t k0, uint32_t k1, float* logits_env,
+                                           uint32_t (&packed)[4])
 {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ew = warp - 2;                 // 0..7
-    const int q = warp & 3;                  // TMEM lane quadrant
-    const int h = ew >> 2;                   // column half
-    const int row = 32 * q + lane;
-    const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);
-    const uint32_t a0 = smem_addr(act0);
-    const int D = a.obs_dim;
-    const int pairs = ((D + 15) & ~15) >> 1; // K padded to the MMA's 16
-    int i = 0;
-    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++i) {
-        // (1) observations -> BF16 A operand of layer 1 (rows ew, ew + 8, ...)
-        for (int r = ew; r < kM; r += kEpiWarps) {
-            const long long e = (long long)tile * kM + r;
-            const float* src = a.obs + e * D;
-            for (int pr = lane; pr < pairs; pr += 32) {
-                const int k = 2 * pr;
-                float2 x = make_float2(0.f, 0.f);
-                if (e < a.E && k < D) x = *reinterpret_cast<const float2*>(src + k);
-                st_shared_u32(a0 + sw128_offset(r, k, kChunkBytes), pack_bf16x2(x.x, x.y));
-            }
-        }
-        fence_proxy_async();
-        fence_before();
-        mbar_arrive(&B.xrdy);
-
-        // per-env sampling inputs, fetched early
-        const long long env = (long long)tile * kM + row;
-        const bool live = env < a.E;
-        uint32_t g = 0, k0 = 0, k1 = 0;
-        if (live) {
-            const int slot = a.user_to_slot[env];
-            g = a.gstep[slot];
-            k0 = a.key0[slot];
-            k1 = a.key1[slot];
-        }
-
-        // (2) layers 1 and 2: this half's 128 columns
-        bool ok = true;
-        for (int L = 0; L < 2; ++L) {
-            if (!mbar_wait(&B.accb[h], (2 * i + L) & 1)) { ok = false; break; }
-            fence_after();
-            hidden_epilogue(tl + (uint32_t)(128 * h), bias_s + 256 * L, L == 0 ? act1 : act0, row, 128 * h);
-            fence_proxy_async();
-            fence_before();
-            mbar_arrive(&B.hrdy[h]);
-        }
-        if (ok && !mbar_wait(&B.acc3, i & 1)) ok = false;
-        if (!ok) {
-            raise(a.err);
-            return;
-        }
-        fence_after();
-
-        // (3) layer 3: chargers 16h .. 16h + 15 of this env, four at a time
-        const float* b3 = bias_s + 512;
-        uint32_t packed[4] = {0, 0, 0, 0};
+    const int L = LT ? LT : a.n_levels;
+    const float* b3 = a.bias + 2 * kPolicyHidden;
 #pragma unroll 1
-        for (int blk = 0; blk < 4; ++blk) {
-            const int c0 = 16 * h + 4 * blk;
-            if (c0 >= a.n_ports) break;
-            uint32_t v[48];
-            tmem_ld32(tl + (uint32_t)(kGroup * c0), *reinterpret_cast<uint32_t(*)[32]>(v));
-            tmem_ld16(tl + (uint32_t)(kGroup * c0 + 32), v + 32);
-            tmem_wait_ld();
-            if (!live) continue;
-            const uint4 words = philox4x32_10(make_uint4((uint32_t)env, g, (uint32_t)(c0 >> 2), kPurposePolicy), k0, k1);
-            float* lo = a.logits ? a.logits + (env * a.n_ports + c0) * a.n_levels : nullptr;
-            packed[blk] = sample4(v, b3, c0, a.n_ports, a.n_levels, words, lo);
-        }
-        fence_before();
-        if (live) {
-            int8_t* dst = a.actions + env * a.n_ports;
-            if (a.n_ports == 32) {
-                *reinterpret_cast<uint4*>(dst + 16 * h) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
-            } else {
-                for (int c = 16 * h; c < 16 * h + 16 && c < a.n_ports; ++c)
-                    dst[c] = (int8_t)((packed[(c - 16 * h) >> 2] >> (8 * (c & 3))) & 0xFF);
-            }
+    for (int blk = 0; blk < 4; ++blk) {
+        packed[blk] = 0;
+        const int c0 = 16 * h + 4 * blk;
+        if (c0 >= a.n_ports) break;                    // uniform across the warp
+        uint32_t v[48];
+        tmem_ld32(tl + (uint32_t)(L * c0), *reinterpret_cast<uint32_t(*)[32]>(v));
+        tmem_ld16(tl + (uint32_t)(L * c0 + 32), v + 32);
+        tmem_wait_ld();
+        if (!live) continue;
+        const uint4 words = philox4x32_10(make_uint4((uint32_t)env, g, (uint32_t)(c0 >> 2), kPurposePolicy), k0, k1);
+        packed[blk] = sample4<LT>(v, b3, c0, a.n_ports, a.n_levels, words,
+                                  logits_env ? logits_env + (long long)c0 * L : nullptr);
+    }
+}
+
+__device__ __forceinline__ void store_levels(int8_t* dst, int h, int n_ports, const uint32_t (&packed)[4])
+{
+    if (n_ports == 32) {
+        *reinterpret_cast<uint4*>(dst + 16 * h) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int c = 16 * h + j;
+            if (c < n_ports) dst[c] = (int8_t)((packed[j >> 2] >> (8 * (j & 3))) & 0xFFu);
         }
     }
 }
 
+// ---- common prologue / epilogue of both kernels ------------------------------
+__device__ __forceinline__ unsigned char* aligned_smem(unsigned char* raw)
+{
+    return reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~static_cast<uintptr_t>(1023));
+}
+
+__device__ __forceinline__ void worker_arrive(uint64_t* bar)
+{
+    fence_proxy_async();
+    fence_before();
+    mbar_arrive(bar);
+}
+
+// =============================================================================
+// k_policy: actions of every env from observations
+// =============================================================================
+template <int LT>
 __global__ void __launch_bounds__(kThreads, 1) k_policy(const __grid_constant__ CUtensorMap wmap, const PolicyArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
-                                                           ~static_cast<uintptr_t>(1023));
-    unsigned char* act0 = base;
-    unsigned char* act1 = base + kActBytes;
-    unsigned char* ring = base + 2 * kActBytes;
-    __shared__ Bars B;
-    __shared__ float bias_s[512 + kPolicyMaxOut];
-    const int warp = threadIdx.x >> 5;
-    for (int j = threadIdx.x; j < 512 + a.n_out_pad; j += blockDim.x) bias_s[j] = a.bias[j];
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) {
-            mbar_init(&B.full[s], 1);
-            mbar_init(&B.empty[s], 1);
-        }
-        mbar_init(&B.accb[0], 1);
-        mbar_init(&B.accb[1], 1);
-        mbar_init(&B.acc3, 1);
-        mbar_init(&B.fin, 1);
-        mbar_init(&B.xrdy, kEpiWarps * 32);
-        mbar_init(&B.hrdy[0], kEpiWarps * 16);
-        mbar_init(&B.hrdy[1], kEpiWarps * 16);
-        mbar_fence_init();
-    }
-    if (warp == 1) tmem_alloc(&B.tmem, kTmemCols);
+    unsigned char* A = aligned_smem(smem_raw);
+    unsigned char* ring = A + kActBytes;
+    __shared__ Sync S;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) init_sync(S, kPolStages);
+    if (warp == 1) tmem_alloc(&S.tmem, kTmemCols);
     fence_before();
     __syncthreads();
     fence_after();
-    const uint32_t tmem = B.tmem;
+    const uint32_t tmem = S.tmem;
     const int n_tiles = (a.E + kM - 1) / kM;
+    const int my_tiles = blockIdx.x < n_tiles ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     if (warp == 0) {
-        if ((threadIdx.x & 31) == 0) produce(&wmap, a, ring, B, n_tiles);
+        if (lane == 0) produce<kPolStages>(&wmap, a, ring, S, my_tiles);
         __syncwarp();
     } else if (warp == 1) {
-        if ((threadIdx.x & 31) == 0) issue(a, act0, act1, ring, B, tmem, n_tiles);
+        if (lane == 0) issue<kPolStages>(a, A, ring, S, tmem, my_tiles);
         __syncwarp();
     } else {
-        epilogue(a, act0, act1, B, bias_s, tmem, n_tiles);
+        const int ew = warp - 2, q = warp & 3, h = ew >> 2;
+        const int row = 32 * q + lane;
+        const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);
+        const uint32_t abase = smem_addr(A);
+        const int D = a.obs_dim;
+        const int pairs = ((D + 15) & ~15) >> 1;     // K padded to the MMA's 16
+        for (int i = 0; i < my_tiles; ++i) {
+            const int tile = (int)blockIdx.x + i * (int)gridDim.x;
+            // (1) observations -> BF16 operand (rows ew, ew + 8, ...); kRowBatch
+            // rows x 4 column pairs per lane are loaded before any is stored
+            constexpr int kRowBatch = 4;
+            for (int r0 = ew; r0 < kM; r0 += kWorkerWarps * kRowBatch) {
+                float2 x[kRowBatch][4];
+#pragma unroll
+                for (int j = 0; j < kRowBatch; ++j) {
+                    const int r = r0 + j * kWorkerWarps;
+                    const long long e = (long long)tile * kM + r;
+                    const float* src = a.obs + e * D;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int k = 2 * (lane + 32 * u);
+                        x[j][u] = make_float2(0.f, 0.f);
+                        if (r < kM && e < a.E && k < D) x[j][u] = __ldg(reinterpret_cast<const float2*>(src + k));
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < kRowBatch; ++j) {
+                    const int r = r0 + j * kWorkerWarps;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int pr = lane + 32 * u;
+                        if (r < kM && pr < pairs)
+                            st_shared_u32(abase + sw128_offset(r, 2 * pr, kChunkBytes),
+                                          pack_bf16x2(x[j][u].x, x[j][u].y));
+                    }
+                }
+            }
+            worker_arrive(&S.xrdy);
+
+            const long long env = (long long)tile * kM + row;
+            const bool live = env < a.E;
+            uint32_t g = 0, k0 = 0, k1 = 0;
+            if (live) {
+                const int slot = a.user_to_slot[env];
+                g = a.gstep[slot];
+                k0 = a.key0[slot];
+                k1 = a.key1[slot];
+            }
+            // (2) hidden layers
+            for (int L = 0; L < 2; ++L) {
+                wait_sync(&S.acc, (3 * i + L) & 1, S, a.err);
+                fence_after();
+                hidden_epilogue(tl + (uint32_t)(128 * h), a.bias + kPolicyHidden * L, abase, row, 128 * h);
+                worker_arrive(&S.hrdy);
+            }
+            // (3) logits -> levels
+            wait_sync(&S.acc, (3 * i + 2) & 1, S, a.err);
+            fence_after();
+            uint32_t packed[4];
+            sample_row<LT>(a, tl, h, env, live, g, k0, k1,
+                           (a.logits && live) ? a.logits + env * a.n_ports * a.n_levels : nullptr, packed);
+            fence_before();
+            if (live) store_levels(a.actions + env * a.n_ports, h, a.n_ports, packed);
+        }
     }
     fence_before();
     __syncthreads();
@@ -325,13 +395,465 @@ __global__ void __launch_bounds__(kThreads, 1) k_policy(const __grid_constant__ 
     }
 }
 
+// =============================================================================
+// k_rollout: observe -> MLP -> sample -> environment step, T times
+// =============================================================================
+
+// per-env state held by the owner thread (warps 2-5, one env per thread)
+struct Owner {
+    long long e;
+    bool live;
+    int slot, t, day, cls_row, occ;
+    long long pb;
+    uint32_t uid, k0, k1, g, ncar, ablk;
+    uint4 aw;
+    float grid_cap, grid_inv_eta, ret, price;
+    uint32_t st_arr, st_rej, st_eps;
+    float st_miss, st_chg, last_ret;
+    bool ended;
+};
+
+struct RollSmem {
+    float gcap[32 * kM];                   // group slot x row: eta_H * I_H of the group of a tail charger
+    float gscale[32 * kM];                 // group slot x row: this step's scale of the group
+    float stage[4][8 * kMaxObs];           // observation rows on their way to HBM (per owner warp)
+    uint32_t act[kM * kPolicyMaxPorts / 4]; // sampled levels, row-major [row][charger] bytes
+    uint32_t gstep[kM], key0[kM], key1[kM];
+};
+
+__device__ __forceinline__ uint32_t taddr_of(uint32_t tl, int col) { return tl + (uint32_t)col; }
+
+__device__ __forceinline__ void owner_load(Owner& o, const RolloutArgs& R, int tile, int row, uint32_t tl, RollSmem& rs)
+{
+    const DevBatch& b = R.b;
+    o.e = (long long)tile * kM + row;
+    o.live = o.e < R.pol.E;
+    o.slot = 0; o.pb = 0; o.uid = 0; o.k0 = o.k1 = o.g = o.ncar = 0;
+    o.t = 0; o.day = 0; o.cls_row = 0; o.occ = 0;
+    o.grid_cap = 1.f; o.grid_inv_eta = 1.f; o.ret = 0.f; o.price = 0.f;
+    o.st_arr = o.st_rej = o.st_eps = 0; o.st_miss = o.st_chg = 0.f; o.last_ret = 0.f; o.ended = false;
+    o.ablk = 0xFFFFFFFFu;
+    o.aw = make_uint4(0, 0, 0, 0);
+    if (o.live) {
+        o.slot = R.pol.user_to_slot[o.e];
+        o.pb = R.port_base + (long long)(o.slot - R.env_base) * R.C;
+        o.uid = (uint32_t)b.user_id[o.slot];
+        o.k0 = b.key0[o.slot];
+        o.k1 = b.key1[o.slot];
+        o.g = b.gstep[o.slot];
+        o.ncar = b.ncar[o.slot];
+        o.t = b.tod[o.slot];
+        o.day = b.day[o.slot];
+        o.cls_row = b.arrival_class[o.slot];
+        o.grid_cap = b.grid_cap[o.slot];
+        o.grid_inv_eta = b.grid_inv_eta[o.slot];
+        o.ret = b.ep_ret[o.slot];
+        o.price = __ldg(b.price + (size_t)o.day * (size_t)R.p.ep_len + (size_t)o.t);
+    }
+#pragma unroll 1
+    for (int k = 0; k < 4; ++k) {
+        uint32_t vs[8], ve[8], vc[8], vr[8], vp[8], vw[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int c = 8 * k + i;
+            vs[i] = ve[i] = vc[i] = vr[i] = vp[i] = vw[i] = 0u;
+            if (o.live && c < R.C) {
+                const long long x = o.pb + c;
+                vs[i] = __float_as_uint(b.soc[x]);
+                ve[i] = __float_as_uint(b.erem[x]);
+                vc[i] = __float_as_uint(b.cap[x]);
+                vr[i] = __float_as_uint(b.rbar[x]);
+                vw[i] = __float_as_uint(b.pw[x]);
+                const uint32_t meta = b.meta[x];
+                vp[i] = (uint32_t)b.trem[x] | (meta << 8);
+                o.occ += b.trem[x] > 0 ? 1 : 0;
+                if (meta & kMetaTail) rs.gcap[((meta >> kMetaGroupShift) & 31u) * kM + row] = b.gcap[x];
+            }
+        }
+        tmem_st8(taddr_of(tl, kColSoc + 8 * k), vs);
+        tmem_st8(taddr_of(tl, kColErem + 8 * k), ve);
+        tmem_st8(taddr_of(tl, kColCap + 8 * k), vc);
+        tmem_st8(taddr_of(tl, kColRbar + 8 * k), vr);
+        tmem_st8(taddr_of(tl, kColPack + 8 * k), vp);
+        tmem_st8(taddr_of(tl, kColPw + 8 * k), vw);
+    }
+    tmem_wait_st();
+    rs.gstep[row] = o.g;
+    rs.key0[row] = o.k0;
+    rs.key1[row] = o.k1;
+}
+
+// One environment step of the owner's env with the sampled levels of this
+// step (Appendix A.2 then A.3, the same operations as the fused step kernel).
+__device__ __forceinline__ void owner_step(Owner& o, const RolloutArgs& R, int it, int row, uint32_t tl, RollSmem& rs)
+{
+    const DevParams& p = R.p;
+    const DevBatch& b = R.b;
+    // arrival count of this step (Philox word, Poisson CDF row)
+    const uint32_t blk = o.g >> 2;
+    if (blk != o.ablk) {
+        o.aw = arrival_words(o.uid, o.g, o.k0, o.k1);
+        o.ablk = blk;
+    }
+    const float* F = b.cdf + ((size_t)o.cls_row * (size_t)p.ep_len + (size_t)o.t) * kCdfLen;
+    const float4 f0 = __ldg(reinterpret_cast<const float4*>(F));
+    const float4 f1 = __ldg(reinterpret_cast<const float4*>(F + 4));
+    uint32_t lv[kPolicyMaxPorts / 4];
+#pragma unroll
+    for (int j = 0; j < kPolicyMaxPorts / 4; ++j) lv[j] = rs.act[row * (kPolicyMaxPorts / 4) + j];
+
+    // (i) per-charger clip; group sums at each group's tail charger
+    float P[32];
+    float gacc = 0.f, raw = 0.f, over = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        uint32_t vs[8], ve[8], vc[8], vr[8], vp[8];
+        tmem_ld8(taddr_of(tl, kColSoc + 8 * k), vs);
+        tmem_ld8(taddr_of(tl, kColErem + 8 * k), ve);
+        tmem_ld8(taddr_of(tl, kColCap + 8 * k), vc);
+        tmem_ld8(taddr_of(tl, kColRbar + 8 * k), vr);
+        tmem_ld8(taddr_of(tl, kColPack + 8 * k), vp);
+        tmem_wait_ld();
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int c = 8 * k + i;
+            const int trem = (int)(vp[i] & 0xFFu);
+            const uint32_t meta = vp[i] >> 8;
+            const int lvl = (int)((lv[c >> 2] >> (8 * (c & 3))) & 0xFFu);
+            const bool dc = meta & kMetaDC;
+            P[c] = trem > 0 ? clip_power(lvl, dc, __uint_as_float(vs[i]), __uint_as_float(ve[i]),
+                                         __uint_as_float(vc[i]), __uint_as_float(vr[i]), p)
+                            : 0.f;
+            raw += P[c];
+            gacc += P[c];
+            if (meta & kMetaTail) {
+                const int gs = (int)((meta >> kMetaGroupShift) & 31u);
+                const float gc = rs.gcap[gs * kM + row];
+                rs.gscale[gs * kM + row] = gacc > gc ? __fdividef(gc, gacc) : 1.0f;
+                if (p.a_con != 0.f) over = fmaxf(over, (gacc - gc) * __ldg(b.ginv_eta + o.pb + c));
+                gacc = 0.f;
+            }
+        }
+    }
+    // architecture constraint: each charger scaled by its group, then the root
+    float sp = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        uint32_t vp[8];
+        tmem_ld8(taddr_of(tl, kColPack + 8 * k), vp);
+        tmem_wait_ld();
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int c = 8 * k + i;
+            const uint32_t meta = vp[i] >> 8;
+            if (meta & kMetaValid) P[c] *= rs.gscale[((meta >> kMetaGroupShift) & 31u) * kM + row];
+            sp += P[c];
+        }
+    }
+    const float s_root = sp > o.grid_cap ? __fdividef(o.grid_cap, sp) : 1.0f;
+    const float c_con = p.a_con != 0.f ? fmaxf(fmaxf(over, (raw - o.grid_cap) * o.grid_inv_eta), 0.f) : 0.f;
+
+    // Poisson count: the smallest k with u < F_k (F nondecreasing, F_127 = inf)
+    const uint32_t word = word_of(o.aw, o.g & 3u);
+    const float u = __fmul_rn(__uint2float_rn(word >> 8), 0x1p-24f);
+    int M = (u >= f0.x) + (u >= f0.y) + (u >= f0.z) + (u >= f0.w) + (u >= f1.x) + (u >= f1.y) + (u >= f1.z) +
+            (u >= f1.w);
+    if (M == 8)
+        while (u >= __ldg(F + M)) ++M;
+
+    // (ii) charge, (iii) departures, (iv) arrivals first come first served,
+    // and the episode end; state written back to TMEM
+    const bool fin = o.t + 1 >= p.ep_len;
+    float se = 0.f, c_sat = 0.f;
+    int adm = 0, occ = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        uint32_t vs[8], ve[8], vc[8], vr[8], vp[8], vw[8];
+        tmem_ld8(taddr_of(tl, kColSoc + 8 * k), vs);
+        tmem_ld8(taddr_of(tl, kColErem + 8 * k), ve);
+        tmem_ld8(taddr_of(tl, kColCap + 8 * k), vc);
+        tmem_ld8(taddr_of(tl, kColRbar + 8 * k), vr);
+        tmem_ld8(taddr_of(tl, kColPack + 8 * k), vp);
+        tmem_wait_ld();
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int c = 8 * k + i;
+            int trem = (int)(vp[i] & 0xFFu);
+            const uint32_t meta = vp[i] >> 8;
+            const bool dc = meta & kMetaDC;
+            float soc = __uint_as_float(vs[i]), erem = __uint_as_float(ve[i]);
+            float cap = __uint_as_float(vc[i]), rbar = __uint_as_float(vr[i]);
+            const float Pq = P[c] * s_root;
+            se += P[c] * (dc ? p.inv_eta1 : p.inv_eta0);
+            float pw = Pq;
+            if (trem > 0) {
+                const float dE = Pq * p.dt;
+                soc = fminf(soc + __fdividef(dE, cap), 1.0f);
+                erem = fmaxf(erem - dE, 0.0f);
+                trem -= 1;
+                if (trem == 0) {
+                    c_sat += erem;
+                    soc = 0.f; erem = 0.f; cap = 0.f; rbar = 0.f;
+                }
+            }
+            if ((meta & kMetaValid) && trem == 0 && adm < M) {
+                const Car car = car_from_words(car_words(o.uid, o.ncar + (uint32_t)adm, o.k0, o.k1), dc, p);
+                cap = car.cap; soc = car.soc; erem = car.erem; rbar = car.rbar;
+                trem = car.stay;
+                ++adm;
+            }
+            if (fin) {
+                soc = 0.f; erem = 0.f; cap = 0.f; rbar = 0.f; pw = 0.f;
+                trem = 0;
+            }
+            occ += trem > 0 ? 1 : 0;
+            vs[i] = __float_as_uint(soc);
+            ve[i] = __float_as_uint(erem);
+            vc[i] = __float_as_uint(cap);
+            vr[i] = __float_as_uint(rbar);
+            vp[i] = (uint32_t)trem | (meta << 8);
+            vw[i] = __float_as_uint(pw);
+        }
+        tmem_st8(taddr_of(tl, kColSoc + 8 * k), vs);
+        tmem_st8(taddr_of(tl, kColErem + 8 * k), ve);
+        tmem_st8(taddr_of(tl, kColCap + 8 * k), vc);
+        tmem_st8(taddr_of(tl, kColRbar + 8 * k), vr);
+        tmem_st8(taddr_of(tl, kColPack + 8 * k), vp);
+        tmem_st8(taddr_of(tl, kColPw + 8 * k), vw);
+    }
+    tmem_wait_st();
+
+    // reward, Appendix A.3
+    const float e_net = sp * s_root * p.dt;
+    const float e_grid = se * s_root * p.dt;
+    o.ncar += (uint32_t)adm;
+    const float profit = p.p_sell * e_net - o.price * e_grid - p.c_fixed;
+    const float r = profit - p.a_sat * c_sat - p.a_decl * (float)(M - adm) - p.a_con * c_con;
+    o.ret += r;
+    o.t += 1;
+    o.st_arr += (uint32_t)adm;
+    o.st_rej += (uint32_t)(M - adm);
+    o.st_miss += c_sat;
+    o.st_chg += e_net;
+    if (fin) {
+        o.last_ret = o.ret;
+        o.ended = true;
+        o.st_eps += 1u;
+        o.ret = 0.f;
+        o.t = 0;
+        o.day = draw_day(o.uid, o.g, 0u, o.k0, o.k1, p.n_days);
+    }
+    o.g += 1u;
+    o.occ = occ;
+    if (o.live) {
+        const long long out = (long long)it * R.pol.E + o.e;
+        if (R.reward) R.reward[out] = r;
+        if (R.done) R.done[out] = fin ? 1 : 0;
+        o.price = __ldg(b.price + (size_t)o.day * (size_t)p.ep_len + (size_t)o.t);
+    }
+    rs.gstep[row] = o.g;
+}
+
+// Observation of the owner warp's 32 envs (rows 32q .. 32q+31) after the
+// step: FP32 rows to HBM through the warp's staging buffer (8 rows per
+// round, written out coalesced), BF16 into the layer-1 operand.
+__device__ __forceinline__ void owner_observe(const Owner& o, const RolloutArgs& R, int it, int q, int lane, uint32_t tl, uint32_t abase,
+                              float* stage)
+{
+    const DevParams& p = R.p;
+    const int D = R.pol.obs_dim, N = R.pol.n_ports;
+    const int D16 = (D + 15) & ~15;
+    const int row = 32 * q + lane;
+#pragma unroll 1
+    for (int j = 0; j < 4; ++j) {
+        const bool active = (lane >> 3) == j;
+        float* orow = stage + (lane & 7) * D;
+#pragma unroll 1
+        for (int k = 0; k < 4; ++k) {
+            uint32_t vs[8], ve[8], vr[8], vp[8], vw[8];
+            tmem_ld8(taddr_of(tl, kColSoc + 8 * k), vs);
+            tmem_ld8(taddr_of(tl, kColErem + 8 * k), ve);
+            tmem_ld8(taddr_of(tl, kColRbar + 8 * k), vr);
+            tmem_ld8(taddr_of(tl, kColPack + 8 * k), vp);
+            tmem_ld8(taddr_of(tl, kColPw + 8 * k), vw);
+            tmem_wait_ld();
+            if (active) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int c = 8 * k + i;
+                    if (c < N) {
+                        if (o.live)
+                            obs_port(orow + 8 + 6 * c, (int)(vp[i] & 0xFFu), __uint_as_float(vs[i]),
+                                     __uint_as_float(ve[i]), __uint_as_float(vr[i]), __uint_as_float(vw[i]),
+                                     (vp[i] >> 8) & kMetaDC, p);
+                        else
+                            for (int f = 0; f < 6; ++f) orow[8 + 6 * c + f] = 0.f;
+                    }
+                }
+            }
+        }
+        if (active) {
+            if (o.live) obs_env(orow, o.t, o.day, o.occ, N, R.b, p);
+            else
+                for (int f = 0; f < 8; ++f) orow[f] = 0.f;
+            for (int k = 0; k < D16; k += 2) {
+                const float x0 = k < D ? orow[k] : 0.f, x1 = k + 1 < D ? orow[k + 1] : 0.f;
+                st_shared_u32(abase + sw128_offset(row, k, kChunkBytes), pack_bf16x2(x0, x1));
+            }
+        }
+        __syncwarp();
+        if (R.obs_out) {
+            const long long e0 = o.e - lane + 8 * j;               // first env of this round
+            const long long n_rows = min(8LL, max(0LL, (long long)R.pol.E - e0));
+            float* dst = R.obs_out + ((long long)it * R.pol.E + e0) * D;
+            const int n = (int)(n_rows * D);
+            if ((D & 3) == 0) {
+                for (int x = 4 * lane; x < n; x += 128)
+                    *reinterpret_cast<float4*>(dst + x) = *reinterpret_cast<const float4*>(stage + x);
+            } else {
+                for (int x = 2 * lane; x < n; x += 64)
+                    *reinterpret_cast<float2*>(dst + x) = *reinterpret_cast<const float2*>(stage + x);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+__device__ __forceinline__ void owner_store(const Owner& o, const RolloutArgs& R, uint32_t tl)
+{
+    const DevBatch& b = R.b;
+#pragma unroll 1
+    for (int k = 0; k < 4; ++k) {
+        uint32_t vs[8], ve[8], vc[8], vr[8], vp[8], vw[8];
+        tmem_ld8(taddr_of(tl, kColSoc + 8 * k), vs);
+        tmem_ld8(taddr_of(tl, kColErem + 8 * k), ve);
+        tmem_ld8(taddr_of(tl, kColCap + 8 * k), vc);
+        tmem_ld8(taddr_of(tl, kColRbar + 8 * k), vr);
+        tmem_ld8(taddr_of(tl, kColPack + 8 * k), vp);
+        tmem_ld8(taddr_of(tl, kColPw + 8 * k), vw);
+        tmem_wait_ld();
+        if (!o.live) continue;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int c = 8 * k + i;
+            if (c < R.C) {
+                const long long x = o.pb + c;
+                b.soc[x] = __uint_as_float(vs[i]);
+                b.erem[x] = __uint_as_float(ve[i]);
+                b.cap[x] = __uint_as_float(vc[i]);
+                b.rbar[x] = __uint_as_float(vr[i]);
+                b.pw[x] = __uint_as_float(vw[i]);
+                b.trem[x] = (uint8_t)(vp[i] & 0xFFu);
+            }
+        }
+    }
+    if (!o.live) return;
+    const int s = o.slot;
+    b.tod[s] = o.t;
+    b.day[s] = o.day;
+    b.gstep[s] = o.g;
+    b.ncar[s] = o.ncar;
+    b.ep_ret[s] = o.ret;
+    if (o.ended) b.last_ret[s] = o.last_ret;
+    b.n_episodes[s] += o.st_eps;
+    b.st_arrived[s] += o.st_arr;
+    b.st_rejected[s] += o.st_rej;
+    b.st_missing[s] += o.st_miss;
+    b.st_charged[s] += o.st_chg;
+}
+
+template <int LT>
+__global__ void __launch_bounds__(kThreads, 1) k_rollout(const __grid_constant__ CUtensorMap wmap, const RolloutArgs R)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* A = aligned_smem(smem_raw);
+    unsigned char* ring = A + kActBytes;
+    RollSmem& rs = *reinterpret_cast<RollSmem*>(ring + kRollStages * kStageBytes);
+    __shared__ Sync S;
+    const PolicyArgs& a = R.pol;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) init_sync(S, kRollStages);
+    if (warp == 1) tmem_alloc(&S.tmem, kTmemCols);
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = S.tmem;
+    const int tile = blockIdx.x;
+    if (warp == 0) {
+        if (lane == 0) produce<kRollStages>(&wmap, a, ring, S, R.T);
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) issue<kRollStages>(a, A, ring, S, tmem, R.T);
+        __syncwarp();
+    } else {
+        const int ew = warp - 2, q = warp & 3, h = ew >> 2;
+        const bool owner = ew < 4;
+        const int row = 32 * q + lane;
+        const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);
+        const uint32_t abase = smem_addr(A);
+        const long long env = (long long)tile * kM + row;
+        const bool live = env < a.E;
+        Owner o;
+        if (owner) {
+            owner_load(o, R, tile, row, tl, rs);
+            fence_before();
+            owner_observe(o, R, 0, q, lane, tl, abase, rs.stage[ew]);
+        }
+        for (int it = 0; it < R.T; ++it) {
+            named_sync(kBarWorkers, kWorkers);
+            worker_arrive(&S.xrdy);
+            for (int L = 0; L < 2; ++L) {
+                wait_sync(&S.acc, (3 * it + L) & 1, S, a.err);
+                fence_after();
+                hidden_epilogue(tl + (uint32_t)(128 * h), a.bias + kPolicyHidden * L, abase, row, 128 * h);
+                worker_arrive(&S.hrdy);
+            }
+            wait_sync(&S.acc, (3 * it + 2) & 1, S, a.err);
+            fence_after();
+            uint32_t packed[4];
+            sample_row<LT>(a, tl, h, env, live, rs.gstep[row], rs.key0[row], rs.key1[row],
+                           (a.logits && live) ? a.logits + ((long long)it * a.E + env) * a.n_ports * a.n_levels
+                                              : nullptr,
+                           packed);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) rs.act[row * (kPolicyMaxPorts / 4) + 4 * h + j] = packed[j];
+            if (live) store_levels(a.actions + ((long long)it * a.E + env) * a.n_ports, h, a.n_ports, packed);
+            fence_before();
+            named_sync(kBarWorkers, kWorkers);
+            if (owner) {
+                fence_after();
+                owner_step(o, R, it, row, tl, rs);
+                if (it + 1 < R.T) owner_observe(o, R, it + 1, q, lane, tl, abase, rs.stage[ew]);
+                fence_before();
+            }
+        }
+        if (owner) owner_store(o, R, tl);
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        fence_after();
+        tmem_dealloc(tmem, kTmemCols);
+    }
+}
+
+constexpr int kPolicySmem = 1024 + kActBytes + kPolStages * kStageBytes;
+constexpr int kRolloutSmem = 1024 + kActBytes + kRollStages * kStageBytes + (int)sizeof(RollSmem);
+static_assert(kPolicySmem <= 227 * 1024 - 256, "k_policy shared memory");
+static_assert(kRolloutSmem <= 227 * 1024 - 256, "k_rollout shared memory");
+
 }  // namespace
 
-int policy_smem_bytes() { return kSmemBytes; }
+int policy_smem_bytes() { return kPolicySmem; }
 
 cudaError_t policy_prepare()
 {
-    return cudaFuncSetAttribute(k_policy, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_policy<11>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPolicySmem))) return e;
+    if ((e = cudaFuncSetAttribute(k_policy<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPolicySmem))) return e;
+    if ((e = cudaFuncSetAttribute(k_rollout<11>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRolloutSmem)))
+        return e;
+    return cudaFuncSetAttribute(k_rollout<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRolloutSmem);
 }
 
 cudaError_t launch_policy(const CUtensorMap& wmap, const PolicyArgs& a, int sm_count, cudaStream_t st)
@@ -339,7 +861,23 @@ cudaError_t launch_policy(const CUtensorMap& wmap, const PolicyArgs& a, int sm_c
     const int n_tiles = (a.E + kM - 1) / kM;
     const int grid = n_tiles < sm_count ? n_tiles : sm_count;
     if (grid <= 0) return cudaSuccess;
-    k_policy<<<grid, kThreads, kSmemBytes, st>>>(wmap, a);
+    if (a.n_levels == 11)
+        k_policy<11><<<grid, kThreads, kPolicySmem, st>>>(wmap, a);
+    else
+        k_policy<0><<<grid, kThreads, kPolicySmem, st>>>(wmap, a);
+    return cudaGetLastError();
+}
+
+bool rollout_fits(int n_out_pad) { return n_out_pad <= kColSoc; }
+
+cudaError_t launch_rollout(const CUtensorMap& wmap, const RolloutArgs& r, cudaStream_t st)
+{
+    const int n_tiles = (r.pol.E + kM - 1) / kM;
+    if (n_tiles <= 0 || r.T <= 0) return cudaSuccess;
+    if (r.pol.n_levels == 11)
+        k_rollout<11><<<n_tiles, kThreads, kRolloutSmem, st>>>(wmap, r);
+    else
+        k_rollout<0><<<n_tiles, kThreads, kRolloutSmem, st>>>(wmap, r);
     return cudaGetLastError();
 }
 

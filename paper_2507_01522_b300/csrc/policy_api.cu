@@ -1,6 +1,6 @@
 // policy_api.cu -- C entry points of the on-device policy and of the rollout
-// that alternates it with the environment step (all launches of a rollout
-// captured once into a CUDA graph).
+// that alternates it with the environment step: fused (one kernel) or split
+// (two launches per step, captured once into a CUDA graph).
 #include <cuda.h>
 
 #include <algorithm>
@@ -154,7 +154,7 @@ extern "C" int chx_policy_load(chx_handle* h, int32_t hidden, const uint16_t* h_
     if (!enc) return fail(CHX_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
 
     const int N = (int)n, D = 8 + 6 * N, H = chx::kPolicyHidden;
-    const int n_out_pad = (chx::kPolicyGroup * N + 15) & ~15;
+    const int n_out_pad = (L * N + 15) & ~15;
     const int rows = 2 * H + n_out_pad;
     std::vector<uint16_t> W((size_t)rows * H, 0);
     std::vector<float> bias((size_t)2 * H + n_out_pad, 0.f);
@@ -164,12 +164,10 @@ extern "C" int chx_policy_load(chx_handle* h, int32_t hidden, const uint16_t* h_
         bias[r] = h_b1[r];
         bias[H + r] = h_b2[r];
     }
-    for (int c = 0; c < N; ++c)
-        for (int j = 0; j < L; ++j) {
-            const int row = 2 * H + chx::kPolicyGroup * c + j;
-            std::memcpy(&W[(size_t)row * H], h_w3 + (size_t)(c * L + j) * H, (size_t)H * sizeof(uint16_t));
-            bias[row] = h_b3[c * L + j];
-        }
+    for (int j = 0; j < N * L; ++j) {
+        std::memcpy(&W[(size_t)(2 * H + j) * H], h_w3 + (size_t)j * H, (size_t)H * sizeof(uint16_t));
+        bias[2 * H + j] = h_b3[j];
+    }
 
     chx::PolicyState& P = h->policy;
     CUDA_TRY(cudaDeviceSynchronize());       // no rollout may be reading the old weights
@@ -213,11 +211,33 @@ extern "C" int chx_policy_act(chx_handle* h, const float* d_obs, int8_t* d_actio
 }
 
 extern "C" int chx_policy_rollout(chx_handle* h, int32_t n_steps, float* d_obs, int8_t* d_actions, float* d_reward,
-                                  uint8_t* d_done, float* d_logits, void* stream)
+                                  uint8_t* d_done, float* d_logits, int32_t form, void* stream)
 {
-    if (!h || !d_obs || !d_actions) return fail(CHX_EINVAL, "null argument");
+    if (!h || !d_actions) return fail(CHX_EINVAL, "null argument");
     if (!h->policy.loaded) return fail(CHX_EINVAL, "no policy loaded");
     if (n_steps < 1) return fail(CHX_EINVAL, "n_steps must be >= 1");
+    if (form != CHX_ROLLOUT_FUSED && form != CHX_ROLLOUT_SPLIT) return fail(CHX_EINVAL, "unknown rollout form");
+    const chx::PolicyState& P = h->policy;
+    if (form == CHX_ROLLOUT_FUSED) {
+        if (!chx::rollout_fits(P.n_out_pad))
+            return fail(CHX_EINVAL, "the fused rollout needs n_ports * n_levels <= 352 (use CHX_ROLLOUT_SPLIT)");
+        int cls = 0;
+        while ((8 << cls) < P.n_ports) ++cls;
+        chx::RolloutArgs r{};
+        r.pol = policy_args(h, nullptr, d_actions, d_logits);
+        r.b = h->b;
+        r.p = h->dp;
+        r.T = n_steps;
+        r.obs_out = d_obs;
+        r.reward = d_reward;
+        r.done = d_done;
+        r.port_base = h->cls_port_base[cls];
+        r.env_base = h->cls_env_base[cls];
+        r.C = 8 << cls;
+        CUDA_TRY(chx::launch_rollout(P.map, r, (cudaStream_t)stream));
+        return CHX_OK;
+    }
+    if (!d_obs) return fail(CHX_EINVAL, "the split rollout needs the observation buffer");
     const chx::PolicyGraphKey want{n_steps, d_obs, d_actions, d_reward, d_done, d_logits, h->warps_per_block, true};
     if (!(h->policy.key == want)) {
         const int rc = build_policy_graph(h, want);

@@ -123,7 +123,7 @@ def test_policy_act_without_logits_and_ppo_init(cuda_lib):
                  margin_tol=MARGIN + 2 * bound.max(), where="ppo init")
 
 
-def run_policy_rollout(w, b, pw, N, T, with_logits=True):
+def run_policy_rollout(w, b, pw, N, T, with_logits=True, form=0):
     import torch
     E, D, L = b.E, 8 + 6 * N, w.params.n_levels
     obs = torch.zeros(T, E, D, device="cuda")
@@ -131,65 +131,131 @@ def run_policy_rollout(w, b, pw, N, T, with_logits=True):
     rew = torch.zeros(T, E, device="cuda")
     done = torch.zeros(T, E, dtype=torch.uint8, device="cuda")
     logits = torch.zeros(T, E, N * L, device="cuda") if with_logits else None
-    b.policy_rollout(T, obs, acts, rew, done, logits)
+    b.policy_rollout(T, obs, acts, rew, done, logits, form=form)
     b.check()
     return obs, acts, rew, done, logits
 
 
-def test_policy_rollout_matches_oracle(cuda_lib):
+def replay_in_oracle(w, b, o, pw, N, T, obs, acts, rew, done, logits, where=""):
+    """Step the oracle with the kernel's actions and compare everything the
+    rollout wrote; returns the number of episode ends."""
+    L = w.params.n_levels
+    n_done = 0
+    for t in range(T):
+        oo = o.observe().reshape(b.E, -1)
+        np.testing.assert_allclose(obs[t], oo, rtol=0, atol=OBS_ATOL, err_msg=f"obs step {t} {where}")
+        check_logits(logits[t], obs[t], pw, where=f"step {t} {where}")
+        check_levels(acts[t], logits[t], o.policy_uniforms(N), L, where=f"step {t} {where}")
+        ro, do = o.step(acts[t].reshape(-1))
+        info = o.info()
+        assert_reward_close(rew[t], ro, reward_scale(info, w.params) + station_step_scale(w, info), TRAJ_RTOL,
+                            where=f"step {t} {where}")
+        np.testing.assert_array_equal(done[t], do, err_msg=f"done step {t} {where}")
+        n_done += int(do.sum())
+    gs, os_ = b.get_state(), o.state()
+    assert_events_equal(gs, os_, where=f"after rollout {where}")
+    assert_traj_close(gs, os_, charger_pmax(w), TRAJ_RTOL, where=f"after rollout {where}")
+    stg, sto = b.stats(), o.stats()
+    np.testing.assert_array_equal(stg["arrived"], sto["arrived"].astype(np.uint32))
+    np.testing.assert_array_equal(stg["rejected"], sto["rejected"].astype(np.uint32))
+    np.testing.assert_array_equal(stg["n_episodes"], sto["n_episodes"])
+    return n_done
+
+
+def stressed_uniform(n_envs, n_ports, seed):
+    """Uniform charger count, but per-station random group layouts (4..9
+    chargers), 30 % DC ports, efficiencies below 1, tight group and grid
+    limits, every reward term on, a 16-step episode and heavy traffic."""
+    rng = np.random.default_rng(seed)
+    p = I.EnvParams(p_max_kw=(22.0, 150.0))
+    p.alpha_con, p.alpha_sat, p.alpha_decl, p.c_fixed = 0.05, 0.2, 0.3, 0.01
+    p.soc_target, p.eta_port, p.ep_len, p.stay_steps = 0.85, (0.95, 0.9), 16, (2, 20)
+    st = I.mixed_stations(rng, np.full(n_envs, n_ports), p.p_max_kw, p_dc=0.3, grid_kw_per_port=6.0,
+                          group_frac=0.35, class_sizes=[n_ports], group_lo=4, group_hi=9)
+    st.group_eta[:] = rng.uniform(0.8, 1.0, st.group_eta.shape).astype(np.float32)
+    st.grid_eta[:] = rng.uniform(0.85, 1.0, st.grid_eta.shape).astype(np.float32)
+    exo = I.Exo(I.price_bank(n_days=9, ep_len=16, seed=seed), I.arrival_rates([n_ports], ep_len=16, base=2.5))
+    return I.Workload(f"stressed-{n_envs}x{n_ports}", p, st, exo, seed)
+
+
+@pytest.mark.parametrize("form", [0, 1], ids=["fused", "split"])
+def test_policy_rollout_matches_oracle(cuda_lib, form):
     w = uniform_workload(200, 32, seed=9)
     w.params.ep_len = 16                                   # cross an episode end
     w.exo = I.Exo(I.price_bank(n_days=5, ep_len=16, seed=9), I.arrival_rates([32], ep_len=16, base=2.0))
     b, pw, N = batch_with_policy(w, seed=9, head_gain=1.0, bias_scale=0.5)
     o = Oracle(w)
     T, L = 24, w.params.n_levels
-    obs, acts, rew, done, logits = (x.cpu().numpy() for x in run_policy_rollout(w, b, pw, N, T))
-    pm = charger_pmax(w)
-    n_done = 0
-    for t in range(T):
-        oo = o.observe().reshape(b.E, -1)
-        np.testing.assert_allclose(obs[t], oo, rtol=0, atol=OBS_ATOL, err_msg=f"obs step {t}")
-        check_logits(logits[t], obs[t], pw, where=f"step {t}")
-        check_levels(acts[t], logits[t], o.policy_uniforms(N), L, where=f"step {t}")
-        ro, do = o.step(acts[t].reshape(-1))
-        info = o.info()
-        assert_reward_close(rew[t], ro, reward_scale(info, w.params) + station_step_scale(w, info), TRAJ_RTOL,
-                            where=f"step {t}")
-        np.testing.assert_array_equal(done[t], do, err_msg=f"done step {t}")
-        n_done += int(do.sum())
+    out = [x.cpu().numpy() for x in run_policy_rollout(w, b, pw, N, T, form=form)]
+    n_done = replay_in_oracle(w, b, o, pw, N, T, *out)
     assert n_done == b.E                                   # every env ended its 16-step episode once
-    gs, os_ = b.get_state(), o.state()
-    assert_events_equal(gs, os_, where="after rollout")
-    assert_traj_close(gs, os_, pm, TRAJ_RTOL, where="after rollout")
-    assert len(np.unique(acts)) == L                       # a spread of levels was sampled
+    assert len(np.unique(out[1])) == L                     # a spread of levels was sampled
 
 
-def test_policy_rollout_replay_is_deterministic(cuda_lib):
-    """Same start state -> bit-identical rollout buffers; the second call
-    replays the captured graph; loading new weights with the same shape keeps
-    the graph valid and changes the actions."""
+@pytest.mark.parametrize("N,E", [(20, 300), (8, 130), (32, 129)])
+def test_fused_rollout_stressed(cuda_lib, N, E):
+    """Padding charger slots (N = 20 in the 32 class), a small class (N = 8),
+    ragged tiles, per-station group layouts, every reward term; two
+    rollouts back to back (the second starts from the first one's state)."""
+    w = stressed_uniform(E, N, seed=N)
+    b, pw, _ = batch_with_policy(w, seed=N, head_gain=1.0, bias_scale=0.5)
+    o = Oracle(w)
+    for rep in range(2):
+        T = 21 if rep == 0 else 13
+        out = [x.cpu().numpy() for x in run_policy_rollout(w, b, pw, N, T, form=0)]
+        n_done = replay_in_oracle(w, b, o, pw, N, T, *out, where=f"rollout {rep}")
+        assert n_done > 0
+
+
+@pytest.mark.parametrize("form", [0, 1], ids=["fused", "split"])
+def test_policy_rollout_replay_is_deterministic(cuda_lib, form):
+    """Same start state -> bit-identical rollout buffers (the split form
+    replays its captured graph on the second call); loading new weights with
+    the same shape keeps a captured graph valid and changes the actions."""
     import torch
     w = uniform_workload(150, 32, seed=4)
     b, pw, N = batch_with_policy(w, seed=4, head_gain=1.0, bias_scale=0.5)
     blob = b.save()
     T = 12
-    first = [x.clone() for x in run_policy_rollout(w, b, pw, N, T, with_logits=False)[:4]]
-    b.load(blob)
+    first = [x.clone() for x in run_policy_rollout(w, b, pw, N, T, with_logits=False, form=form)[:4]]
+    end_state = b.get_state()
     E, D = b.E, 8 + 6 * N
     bufs = (torch.zeros(T, E, D, device="cuda"), torch.zeros(T, E, N, dtype=torch.int8, device="cuda"),
             torch.zeros(T, E, device="cuda"), torch.zeros(T, E, dtype=torch.uint8, device="cuda"))
     for _ in range(2):
         b.load(blob)
-        b.policy_rollout(T, *bufs)
+        b.policy_rollout(T, *bufs, form=form)
         b.check()
         for x, y in zip(first, bufs):
             assert torch.equal(x, y)
+        again = b.get_state()
+        for k in end_state:
+            np.testing.assert_array_equal(end_state[k], again[k])
     pw2 = I.policy_weights(D, N, seed=5, head_gain=1.0, bias_scale=0.5)
     b.policy_load(pw2.w1, pw2.b1, pw2.w2, pw2.b2, pw2.w3, pw2.b3)
     b.load(blob)
-    b.policy_rollout(T, *bufs)
+    b.policy_rollout(T, *bufs, form=form)
     b.check()
     assert not torch.equal(first[1], bufs[1])
+
+
+def test_fused_and_split_rollouts_agree(cuda_lib):
+    """Same start state: identical events while the levels agree; the
+    sampled levels differ only where the two FP32 computations straddle a
+    sampling boundary (rare), so compare the first steps before divergence."""
+    import torch
+    w = uniform_workload(256, 32, seed=12)
+    b, pw, N = batch_with_policy(w, seed=12, head_gain=1.0, bias_scale=0.5)
+    blob = b.save()
+    T = 8
+    fa = [x.cpu().numpy() for x in run_policy_rollout(w, b, pw, N, T, form=0)]
+    b.load(blob)
+    sa = [x.cpu().numpy() for x in run_policy_rollout(w, b, pw, N, T, form=1)]
+    same_env = np.all(fa[1].reshape(T, b.E, -1) == sa[1].reshape(T, b.E, -1), axis=(0, 2))
+    assert same_env.mean() > 0.9
+    for t in range(T):
+        np.testing.assert_allclose(fa[0][t][same_env], sa[0][t][same_env], rtol=0, atol=OBS_ATOL)
+        np.testing.assert_array_equal(fa[3][t][same_env], sa[3][t][same_env])
 
 
 def test_policy_rejects_unsupported_batches(cuda_lib):
@@ -210,6 +276,17 @@ def test_policy_rejects_unsupported_batches(cuda_lib):
     with pytest.raises(ChxError) as ei:                     # no policy loaded
         b.policy_act(torch.zeros(10, 206, device="cuda"), torch.zeros(10, 33, dtype=torch.int8, device="cuda"))
     assert ei.value.code == CHX_EINVAL
+    w = uniform_workload(10, 32)                            # 32 x 12 logits: split form only
+    w.params.n_levels = 12
+    b, pw, N = batch_with_policy(w)
+    acts = torch.zeros(2, 10, 32, dtype=torch.int8, device="cuda")
+    obs = torch.zeros(2, 10, 200, device="cuda")
+    with pytest.raises(ChxError) as ei:
+        b.policy_rollout(2, obs, acts, form=0)
+    assert ei.value.code == CHX_EINVAL
+    b.policy_rollout(2, obs, acts, form=1)
+    b.check()
+    assert int(acts.max()) <= 11
 
 
 def test_policy_rollout_fullsize_sampled(cuda_lib):
@@ -222,7 +299,7 @@ def test_policy_rollout_fullsize_sampled(cuda_lib):
     b, pw, N = batch_with_policy(w, seed=0)
     o = Oracle(w)
     T, L = 128, w.params.n_levels
-    obs, acts, rew, done, _ = run_policy_rollout(w, b, pw, N, T, with_logits=False)
+    obs, acts, rew, done, _ = run_policy_rollout(w, b, pw, N, T, with_logits=False, form=0)
     obs, acts, rew, done = (x.cpu().numpy() for x in (obs, acts, rew, done))
     rng = np.random.default_rng(0)
     sample = np.sort(rng.choice(b.E, 256, replace=False))
