@@ -54,6 +54,7 @@ constexpr int kPolStages = 9;              // weight ring of k_policy
 constexpr int kRollStages = 6;             // weight ring of k_rollout
 constexpr int kMaxStages = kPolStages;
 constexpr int kBarWorkers = 1;             // named barrier of the worker warps
+constexpr int kBarOwners = 2;              // named barrier of the owner warps (k_rollout)
 
 // k_rollout: TMEM columns of the env state, 32 per field (charger c at +c)
 constexpr int kColSoc = 352, kColErem = 384, kColCap = 416, kColRbar = 448;
@@ -75,17 +76,24 @@ __device__ __forceinline__ bool is_bad(const Sync& S) { return *reinterpret_cast
 
 // bounded wait; on timeout raise the error and the shared flag; returns
 // immediately (false) once the flag is set
+// (after a short spin the waiting thread sleeps with exponential backoff,
+// so that long waits leave the issue slots to the warps doing the work)
 __device__ __forceinline__ bool wait_sync(uint64_t* bar, uint32_t parity, Sync& S, uint32_t* err)
 {
     if (mbar_try(bar, parity)) return true;
     const long long t0 = clock64();
-    for (;;) {
+    unsigned ns = 0;
+    for (int i = 0;; ++i) {
         if (mbar_try(bar, parity)) return true;
         if (is_bad(S)) return false;
         if (clock64() - t0 > kWaitCycles) {
             *reinterpret_cast<volatile int*>(&S.bad) = 1;
             atomicOr(err, kErrPolicyWait);
             return false;
+        }
+        if (i >= 8) {
+            ns = ns ? (ns < 256u ? 2u * ns : 256u) : 32u;
+            __nanosleep(ns);
         }
     }
 }
@@ -413,15 +421,26 @@ struct Owner {
     bool ended;
 };
 
+// Observation staging: one 8-charger chunk (plus the 8 station features in
+// chunk 0) of each of an owner warp's 32 rows; row stride kStageRow floats.
+constexpr int kStageRow = 8 + 48 + 4;   // 16-byte aligned rows
 struct RollSmem {
     float gcap[32 * kM];                   // group slot x row: eta_H * I_H of the group of a tail charger
-    float gscale[32 * kM];                 // group slot x row: this step's scale of the group
-    float stage[4][8 * kMaxObs];           // observation rows on their way to HBM (per owner warp)
+    union {                                // the step's group scales, then the observation staging
+        float gscale[32 * kM];             // group slot x row
+        float stage[4][32 * kStageRow];    // per owner warp
+    } u;
     uint32_t act[kM * kPolicyMaxPorts / 4]; // sampled levels, row-major [row][charger] bytes
     uint32_t gstep[kM], key0[kM], key1[kM];
 };
 
 __device__ __forceinline__ uint32_t taddr_of(uint32_t tl, int col) { return tl + (uint32_t)col; }
+
+// car words for the rare step with more than kPreCars arrivals (kept out of line)
+__device__ __noinline__ uint4 car_words_late(uint32_t uid, uint32_t n, uint32_t k0, uint32_t k1)
+{
+    return car_words(uid, n, k0, k1);
+}
 
 __device__ __forceinline__ void owner_load(Owner& o, const RolloutArgs& R, int tile, int row, uint32_t tl, RollSmem& rs)
 {
@@ -529,7 +548,7 @@ __device__ __forceinline__ void owner_step(Owner& o, const RolloutArgs& R, int i
             if (meta & kMetaTail) {
                 const int gs = (int)((meta >> kMetaGroupShift) & 31u);
                 const float gc = rs.gcap[gs * kM + row];
-                rs.gscale[gs * kM + row] = gacc > gc ? __fdividef(gc, gacc) : 1.0f;
+                rs.u.gscale[gs * kM + row] = gacc > gc ? __fdividef(gc, gacc) : 1.0f;
                 if (p.a_con != 0.f) over = fmaxf(over, (gacc - gc) * __ldg(b.ginv_eta + o.pb + c));
                 gacc = 0.f;
             }
@@ -546,7 +565,7 @@ __device__ __forceinline__ void owner_step(Owner& o, const RolloutArgs& R, int i
         for (int i = 0; i < 8; ++i) {
             const int c = 8 * k + i;
             const uint32_t meta = vp[i] >> 8;
-            if (meta & kMetaValid) P[c] *= rs.gscale[((meta >> kMetaGroupShift) & 31u) * kM + row];
+            if (meta & kMetaValid) P[c] *= rs.u.gscale[((meta >> kMetaGroupShift) & 31u) * kM + row];
             sp += P[c];
         }
     }
@@ -560,6 +579,14 @@ __device__ __forceinline__ void owner_step(Owner& o, const RolloutArgs& R, int i
             (u >= f1.w);
     if (M == 8)
         while (u >= __ldg(F + M)) ++M;
+
+    // words of the first cars that may arrive (at most M are admitted); more
+    // than kPreCars arrivals in one step are drawn where they are placed
+    constexpr int kPreCars = 4;
+    uint4 cw[kPreCars];
+#pragma unroll
+    for (int j = 0; j < kPreCars; ++j)
+        cw[j] = j < M ? car_words(o.uid, o.ncar + (uint32_t)j, o.k0, o.k1) : make_uint4(0, 0, 0, 0);
 
     // (ii) charge, (iii) departures, (iv) arrivals first come first served,
     // and the episode end; state written back to TMEM
@@ -597,7 +624,12 @@ __device__ __forceinline__ void owner_step(Owner& o, const RolloutArgs& R, int i
                 }
             }
             if ((meta & kMetaValid) && trem == 0 && adm < M) {
-                const Car car = car_from_words(car_words(o.uid, o.ncar + (uint32_t)adm, o.k0, o.k1), dc, p);
+                const uint4 w = adm == 0 ? cw[0]
+                              : adm == 1 ? cw[1]
+                              : adm == 2 ? cw[2]
+                              : adm == 3 ? cw[3]
+                                         : car_words_late(o.uid, o.ncar + (uint32_t)adm, o.k0, o.k1);
+                const Car car = car_from_words(w, dc, p);
                 cap = car.cap; soc = car.soc; erem = car.erem; rbar = car.rbar;
                 trem = car.stay;
                 ++adm;
@@ -655,64 +687,78 @@ __device__ __forceinline__ void owner_step(Owner& o, const RolloutArgs& R, int i
 }
 
 // Observation of the owner warp's 32 envs (rows 32q .. 32q+31) after the
-// step: FP32 rows to HBM through the warp's staging buffer (8 rows per
-// round, written out coalesced), BF16 into the layer-1 operand.
-__device__ __forceinline__ void owner_observe(const Owner& o, const RolloutArgs& R, int it, int q, int lane, uint32_t tl, uint32_t abase,
-                              float* stage)
+// step, one 8-charger chunk at a time with every lane on its own row: the
+// chunk's features go to the layer-1 operand as BF16 and, as FP32, to the
+// warp's staging buffer, which the warp then writes to HBM row by row
+// (each row's chunk is a contiguous, 16-byte aligned run).
+__device__ __forceinline__ void owner_observe(const Owner& o, const RolloutArgs& R, int it, int q, int lane, uint32_t tl,
+                                              uint32_t abase, float* stage)
 {
     const DevParams& p = R.p;
     const int D = R.pol.obs_dim, N = R.pol.n_ports;
-    const int D16 = (D + 15) & ~15;
     const int row = 32 * q + lane;
+    float* srow = stage + lane * kStageRow;
+    const long long e0 = o.e - lane;                        // env of the warp's first row
+    const int n_rows = (int)min(32LL, max(0LL, (long long)R.pol.E - e0));
+    const int n_chunks = (N + 7) >> 3;
 #pragma unroll 1
-    for (int j = 0; j < 4; ++j) {
-        const bool active = (lane >> 3) == j;
-        float* orow = stage + (lane & 7) * D;
-#pragma unroll 1
-        for (int k = 0; k < 4; ++k) {
-            uint32_t vs[8], ve[8], vr[8], vp[8], vw[8];
-            tmem_ld8(taddr_of(tl, kColSoc + 8 * k), vs);
-            tmem_ld8(taddr_of(tl, kColErem + 8 * k), ve);
-            tmem_ld8(taddr_of(tl, kColRbar + 8 * k), vr);
-            tmem_ld8(taddr_of(tl, kColPack + 8 * k), vp);
-            tmem_ld8(taddr_of(tl, kColPw + 8 * k), vw);
-            tmem_wait_ld();
-            if (active) {
+    for (int k = 0; k < n_chunks; ++k) {
+        uint32_t vs[8], ve[8], vr[8], vp[8], vw[8];
+        tmem_ld8(taddr_of(tl, kColSoc + 8 * k), vs);
+        tmem_ld8(taddr_of(tl, kColErem + 8 * k), ve);
+        tmem_ld8(taddr_of(tl, kColRbar + 8 * k), vr);
+        tmem_ld8(taddr_of(tl, kColPack + 8 * k), vp);
+        tmem_ld8(taddr_of(tl, kColPw + 8 * k), vw);
+        tmem_wait_ld();
+        // features [f0, f1) of the row: the station's 8 in chunk 0, then 6 per charger
+        const int f0 = k == 0 ? 0 : 8 + 48 * k;
+        const int f1 = min(8 + 48 * (k + 1), D);
+        float* base = srow - f0;                            // feature f of the row at base[f]
+        if (k == 0) {
+            if (o.live) obs_env(base, o.t, o.day, o.occ, N, R.b, p);
+            else
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const int c = 8 * k + i;
-                    if (c < N) {
-                        if (o.live)
-                            obs_port(orow + 8 + 6 * c, (int)(vp[i] & 0xFFu), __uint_as_float(vs[i]),
-                                     __uint_as_float(ve[i]), __uint_as_float(vr[i]), __uint_as_float(vw[i]),
-                                     (vp[i] >> 8) & kMetaDC, p);
-                        else
-                            for (int f = 0; f < 6; ++f) orow[8 + 6 * c + f] = 0.f;
-                    }
+                for (int f = 0; f < 8; ++f) base[f] = 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int c = 8 * k + i;
+            if (c < N) {
+                float* f = base + 8 + 6 * c;
+                if (o.live) {
+                    obs_port(f, (int)(vp[i] & 0xFFu), __uint_as_float(vs[i]), __uint_as_float(ve[i]),
+                             __uint_as_float(vr[i]), __uint_as_float(vw[i]), (vp[i] >> 8) & kMetaDC, p);
+                } else {
+#pragma unroll
+                    for (int x = 0; x < 6; ++x) f[x] = 0.f;
                 }
             }
         }
-        if (active) {
-            if (o.live) obs_env(orow, o.t, o.day, o.occ, N, R.b, p);
-            else
-                for (int f = 0; f < 8; ++f) orow[f] = 0.f;
-            for (int k = 0; k < D16; k += 2) {
-                const float x0 = k < D ? orow[k] : 0.f, x1 = k + 1 < D ? orow[k + 1] : 0.f;
-                st_shared_u32(abase + sw128_offset(row, k, kChunkBytes), pack_bf16x2(x0, x1));
-            }
+        // BF16 copy into the operand (pairs; the K padding up to 16 is zero)
+        const int f1p = k == n_chunks - 1 ? ((D + 15) & ~15) : f1;
+#pragma unroll 4
+        for (int f = f0; f < f1p; f += 2) {
+            const float x0 = f < D ? base[f] : 0.f, x1 = f + 1 < D ? base[f + 1] : 0.f;
+            st_shared_u32(abase + sw128_offset(row, f, kChunkBytes), pack_bf16x2(x0, x1));
         }
         __syncwarp();
-        if (R.obs_out) {
-            const long long e0 = o.e - lane + 8 * j;               // first env of this round
-            const long long n_rows = min(8LL, max(0LL, (long long)R.pol.E - e0));
-            float* dst = R.obs_out + ((long long)it * R.pol.E + e0) * D;
-            const int n = (int)(n_rows * D);
+        if (R.obs_out) {                                     // rows of the chunk -> HBM
+            const int len = f1 - f0;                         // a multiple of 2 (4 when D % 4 == 0)
+            float* dst0 = R.obs_out + ((long long)it * R.pol.E + e0) * D + f0;
             if ((D & 3) == 0) {
-                for (int x = 4 * lane; x < n; x += 128)
-                    *reinterpret_cast<float4*>(dst + x) = *reinterpret_cast<const float4*>(stage + x);
+                const int per = len >> 2;
+                for (int x = lane; x < n_rows * per; x += 32) {
+                    const int r = x / per, v = x - r * per;
+                    *reinterpret_cast<float4*>(dst0 + (long long)r * D + 4 * v) =
+                        *reinterpret_cast<const float4*>(stage + r * kStageRow + 4 * v);
+                }
             } else {
-                for (int x = 2 * lane; x < n; x += 64)
-                    *reinterpret_cast<float2*>(dst + x) = *reinterpret_cast<const float2*>(stage + x);
+                const int per = len >> 1;
+                for (int x = lane; x < n_rows * per; x += 32) {
+                    const int r = x / per, v = x - r * per;
+                    *reinterpret_cast<float2*>(dst0 + (long long)r * D + 2 * v) =
+                        *reinterpret_cast<const float2*>(stage + r * kStageRow + 2 * v);
+                }
             }
         }
         __syncwarp();
@@ -797,7 +843,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rollout(const __grid_constant__
         if (owner) {
             owner_load(o, R, tile, row, tl, rs);
             fence_before();
-            owner_observe(o, R, 0, q, lane, tl, abase, rs.stage[ew]);
+            owner_observe(o, R, 0, q, lane, tl, abase, rs.u.stage[ew]);
         }
         for (int it = 0; it < R.T; ++it) {
             named_sync(kBarWorkers, kWorkers);
@@ -823,7 +869,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_rollout(const __grid_constant__
             if (owner) {
                 fence_after();
                 owner_step(o, R, it, row, tl, rs);
-                if (it + 1 < R.T) owner_observe(o, R, it + 1, q, lane, tl, abase, rs.stage[ew]);
+                named_sync(kBarOwners, 128);           // group scales done: the staging may overwrite them
+                if (it + 1 < R.T) owner_observe(o, R, it + 1, q, lane, tl, abase, rs.u.stage[ew]);
                 fence_before();
             }
         }
