@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-policy", action="store_true", help="skip the on-device policy rollout leg")
+    ap.add_argument("--policy-steps", type=int, default=128, help="rollout buffer length of the policy leg")
     ap.add_argument("--serve-envs", type=int, default=1 << 20, help="resident stations of the serving leg")
     ap.add_argument("--serve-actors", type=int, default=4096)
     ap.add_argument("--serve-think-us", type=float, default=0.0,
@@ -162,6 +164,19 @@ FUSED_OPS_PER_ENV_STEP = 130.0       # arrival Philox + Poisson + reward of one 
 FUSED_STATE_BYTES_PER_PORT = 54.0    # per launch: state in (21) + out (21) + statics (12)
 FUSED_STATE_BYTES_PER_ENV = 80.0
 LANES_PER_SM = 128
+POLICY_HIDDEN = 256
+
+
+def policy_flops_per_env_step(D, N, L, H=POLICY_HIDDEN):
+    """Multiply-adds x 2 of one MLP pass for one env (the algorithmic
+    D -> H -> H -> N*L network; padding is not counted)."""
+    return 2.0 * (D * H + H * H + H * N * L)
+
+
+def policy_bytes_per_env_step(D, N):
+    """HBM bytes the rollout must write per env-step: observation (FP32),
+    levels (int8), reward (FP32), done (u8)."""
+    return 4.0 * D + N + 4.0 + 1.0
 
 
 def recorded_traffic(n_envs, K, W):
@@ -384,6 +399,11 @@ def run_b300(args):
         line["gpu_launches"] += launches_per_step * args.steps
 
     line["clocks"] = ck.summary()
+    if not args.no_policy:
+        del reward, done, obs
+        pol = run_policy_rollout(args, rank, ws, dev, timed, pk)
+        line["policy_rollout"] = pol
+        line["gpu_launches"] += pol["gpu_launches"]
     if not args.no_serve:
         del b
         torch.cuda.empty_cache()
@@ -394,6 +414,62 @@ def run_b300(args):
     if rank == 0:
         print(json.dumps(line), flush=True)
     barrier(ws)
+
+
+def run_policy_rollout(args, rank, ws, dev, timed, pk):
+    """On-device policy rollout: 16384 stations x 32 chargers, a buffer of
+    args.policy_steps steps (observation FP32, levels int8, reward FP32,
+    done), actions sampled from a randomly initialised BF16 MLP
+    200 -> 256 -> 256 -> 32 x 11 on the tensor cores.  Both forms: fused
+    (one kernel per rollout) and split (policy and step launches per step)."""
+    import torch
+    from paper_2507_01522_b300 import chargax
+    from paper_2507_01522_b300 import inputs as I
+    w = I.rollout_stations(seed=0)
+    T = args.policy_steps
+    b = chargax.Batch(w, seed=rank_seed(rank))
+    E = b.E
+    N = int(w.stations.n_ports[0])
+    L = w.params.n_levels
+    D = 8 + 6 * N
+    pw = I.policy_weights(D, N, n_levels=L, seed=rank)
+    b.policy_load(pw.w1, pw.b1, pw.w2, pw.b2, pw.w3, pw.b3)
+    obs = torch.empty(T, E, D, device=dev)
+    acts = torch.empty(T, E, N, dtype=torch.int8, device=dev)
+    rew = torch.empty(T, E, device=dev)
+    done = torch.empty(T, E, dtype=torch.uint8, device=dev)
+    out = {"workload": w.name, "n_envs": E, "chargers_per_station": N, "rollout_steps": T,
+           "policy": f"BF16 MLP {D}-{POLICY_HIDDEN}-{POLICY_HIDDEN}-{N}x{L}, FP32 accumulation, PPO initialisation",
+           "unit": "env-steps/s", "buffers": "obs f32 [T][E][D], levels int8 [T][E][N], reward f32, done u8"}
+    launches = 0
+    for form, name in ((chargax.CHX_ROLLOUT_FUSED, "fused"), (chargax.CHX_ROLLOUT_SPLIT, "split")):
+        fn = lambda: b.policy_rollout(T, obs, acts, rew, done, form=form)
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        barrier(ws)
+        ms = timed(fn, args.steps)
+        b.check()
+        tot = max_over_ranks(sum(ms) / 1e3, ws)
+        ms_roll = 1e3 * tot / args.steps
+        flops = policy_flops_per_env_step(D, N, L) * E * T
+        tf = flops / (ms_roll * 1e-3) / 1e12
+        by = policy_bytes_per_env_step(D, N) * E * T
+        gbs = by / (ms_roll * 1e-3) / 1e9
+        n_launch = 1 if name == "fused" else 2 * T + 1
+        launches += n_launch * args.steps
+        out[name] = {"value": E * T * args.steps * ws / tot, "ms_per_rollout": ms_roll, "launches_per_rollout": n_launch,
+                     "roofline": {"bound": "tensor", "achieved": tf, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
+                                  "frac": tf / pk["bf16_tflops"], "traffic": None,
+                                  "kernel": "k_rollout" if name == "fused" else "k_policy + k_step_fused",
+                                  "flops_per_rollout": flops,
+                                  "hbm_output_gbs": gbs, "hbm_output_frac": gbs / pk["hbm_gbs"]}}
+    out["value"] = out["fused"]["value"]
+    out["fused_over_split"] = out["fused"]["value"] / out["split"]["value"]
+    out["gpu_launches"] = launches
+    del b
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_serving(args, rank):

@@ -50,7 +50,8 @@ struct PolicyState {
     int ch1 = 0, ks1_last = 0, parts3 = 0, n3_last = 0;
     uint16_t* d_w = nullptr;               // [rows][256] BF16 bits
     float* d_bias = nullptr;               // [512 + n_out_pad]
-    CUtensorMap map{};                     // over-aligned type; the handle is allocated with new
+    WMaps maps{};                          // k_policy (over-aligned; the handle is allocated with new)
+    WMaps maps_roll{};                     // k_rollout (boxes split across the cluster)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     PolicyGraphKey key{};

@@ -57,15 +57,21 @@ constexpr int kPolicyHidden = 256;
 constexpr int kPolicyMaxPorts = 32;
 constexpr int kPolicyGroup = 12;           // most action levels the sampler handles
 
-// Weights: one BF16 matrix [512 + n_out_pad][256], row-major, streamed by a
-// TMA map with 64 x 128 boxes and 128-byte swizzle.  Rows 0-255 = W1 (columns
-// >= obs_dim zero), 256-511 = W2, 512 + c * L + j = level j of charger c
-// (W3; rows up to n_out_pad zero).  bias = b1 | b2 | b3 in the same order.
+// Weights: one BF16 matrix [512 + n_out_pad][256], row-major, streamed by
+// TMA with 128-byte swizzle.  Rows 0-255 = W1 (columns >= obs_dim zero),
+// 256-511 = W2, 512 + c * L + j = level j of charger c (W3; rows up to
+// n_out_pad zero).  bias = b1 | b2 | b3 in the same order.  Two maps over
+// it: boxes of 64 columns x (policy_stage_rows() / CS) rows, and x (n3_last
+// / CS) rows for the last part of layer 3; CS = 1 for k_policy and
+// rollout_cluster() for the fused rollout.
+struct WMaps {
+    CUtensorMap main, tail;
+};
 struct PolicyArgs {
     const float* obs;                      // [E][obs_dim] FP32 (k_policy)
     int E, obs_dim, n_ports, n_levels;
     int ch1, ks1_last;                     // layer-1 K chunks of 64, K = 16 steps in the last one
-    int parts3, n3_last;                   // layer-3 N parts of 128, N of the last part
+    int parts3, n3_last;                   // layer-3 N parts of policy_stage_rows(), N of the last part
     int n_out_pad;                         // n_ports * n_levels rounded up to 16
     const float* bias;
     const int32_t* user_to_slot;
@@ -92,8 +98,10 @@ struct RolloutArgs {
 
 int policy_smem_bytes();
 cudaError_t policy_prepare();              // once per process, before capture
-cudaError_t launch_policy(const CUtensorMap& wmap, const PolicyArgs& a, int sm_count, cudaStream_t st);
+int policy_stage_rows();                   // weight rows (MMA N) of a full layer part
+cudaError_t launch_policy(const WMaps& wm, const PolicyArgs& a, int sm_count, cudaStream_t st);
 bool rollout_fits(int n_out_pad);          // logits leave TMEM room for the env state
-cudaError_t launch_rollout(const CUtensorMap& wmap, const RolloutArgs& r, cudaStream_t st);
+int rollout_cluster();                     // CTAs sharing the weight stages (TMA multicast)
+cudaError_t launch_rollout(const WMaps& wm, const RolloutArgs& r, cudaStream_t st);
 
 }  // namespace chx

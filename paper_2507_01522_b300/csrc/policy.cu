@@ -45,16 +45,17 @@ using namespace tc;
 constexpr int kM = 128;                    // envs per tile (MMA M, TMEM lanes)
 constexpr int kChunkBytes = kM * 128;      // 128 rows x 64 BF16
 constexpr int kActBytes = 4 * kChunkBytes; // 128 x 256 BF16 operand
-constexpr int kStageBytes = 128 * 128;     // 128 weight rows x 64 BF16
+constexpr int kStageRows = 256;            // weight rows (MMA N) per stage
+constexpr int kStageBytes = kStageRows * 128; // 256 weight rows x 64 BF16
 constexpr int kWorkerWarps = 8;
 constexpr int kWorkers = kWorkerWarps * 32;
 constexpr int kThreads = (2 + kWorkerWarps) * 32;
 constexpr uint32_t kTmemCols = 512;
-constexpr int kPolStages = 9;              // weight ring of k_policy
-constexpr int kRollStages = 6;             // weight ring of k_rollout
+constexpr int kPolStages = 4;              // weight ring of k_policy
+constexpr int kRollStages = 3;             // weight ring of k_rollout
+constexpr int kRollCluster = 2;            // k_rollout CTAs sharing each weight stage (TMA multicast)
 constexpr int kMaxStages = kPolStages;
 constexpr int kBarWorkers = 1;             // named barrier of the worker warps
-constexpr int kBarOwners = 2;              // named barrier of the owner warps (k_rollout)
 
 // k_rollout: TMEM columns of the env state, 32 per field (charger c at +c)
 constexpr int kColSoc = 352, kColErem = 384, kColCap = 416, kColRbar = 448;
@@ -76,8 +77,11 @@ __device__ __forceinline__ bool is_bad(const Sync& S) { return *reinterpret_cast
 
 // bounded wait; on timeout raise the error and the shared flag; returns
 // immediately (false) once the flag is set
-// (after a short spin the waiting thread sleeps with exponential backoff,
-// so that long waits leave the issue slots to the warps doing the work)
+// (kSleep: after a short spin the waiting thread sleeps with exponential
+// backoff, so that long waits leave the issue slots to the warps doing the
+// work; the single producer and MMA threads spin, their waits are on the
+// critical path)
+template <bool kSleep = true>
 __device__ __forceinline__ bool wait_sync(uint64_t* bar, uint32_t parity, Sync& S, uint32_t* err)
 {
     if (mbar_try(bar, parity)) return true;
@@ -91,18 +95,18 @@ __device__ __forceinline__ bool wait_sync(uint64_t* bar, uint32_t parity, Sync& 
             atomicOr(err, kErrPolicyWait);
             return false;
         }
-        if (i >= 8) {
+        if (kSleep && i >= 8) {
             ns = ns ? (ns < 256u ? 2u * ns : 256u) : 32u;
             __nanosleep(ns);
         }
     }
 }
 
-__device__ __forceinline__ void init_sync(Sync& S, int n_stages)
+__device__ __forceinline__ void init_sync(Sync& S, int n_stages, int cluster)
 {
     for (int s = 0; s < n_stages; ++s) {
         mbar_init(&S.full[s], 1);
-        mbar_init(&S.empty[s], 1);
+        mbar_init(&S.empty[s], cluster);       // one MMA commit from every CTA sharing the stage
     }
     mbar_init(&S.acc, 1);
     mbar_init(&S.fin, 1);
@@ -113,28 +117,48 @@ __device__ __forceinline__ void init_sync(Sync& S, int n_stages)
 }
 
 // ---- TMA producer: n_passes MLP passes worth of weight stages ------------
-template <int NS>
-__device__ void produce(const CUtensorMap* wmap, const PolicyArgs& a, unsigned char* ring, Sync& S, int n_passes)
+// A stage is one 64-column K chunk of one layer part: 256 weight rows (the
+// MMA's N), or n3_last rows for the last part of layer 3.
+// CS > 1: the CTAs of a cluster of CS share every stage; each loads rows
+// [rank * rows / CS, +rows / CS) of it into all of them (the maps' boxes are
+// that tall), and a slot is refilled once every CTA's MMAs have read it.
+__device__ __forceinline__ int part_rows(const PolicyArgs& a, int L, int p)
 {
+    return (L == 2 && p == a.parts3 - 1) ? a.n3_last : kStageRows;
+}
+
+template <int NS, int CS>
+__device__ void produce(const WMaps* wm, const PolicyArgs& a, unsigned char* ring, Sync& S, int n_passes)
+{
+    const uint32_t rank = CS > 1 ? cluster_rank() : 0u;
     uint32_t s = 0;
     int last[NS];
 #pragma unroll
     for (int j = 0; j < NS; ++j) last[j] = -1;
     for (int it = 0; it < n_passes; ++it)
         for (int L = 0; L < 3; ++L) {
-            const int parts = L < 2 ? 2 : a.parts3;
+            const int parts = L < 2 ? 1 : a.parts3;
             const int chunks = L == 0 ? a.ch1 : 4;
-            for (int p = 0; p < parts; ++p)
+            for (int p = 0; p < parts; ++p) {
+                const int rows = part_rows(a, L, p);
+                const int piece = rows / CS;
+                const CUtensorMap* map = rows == kStageRows ? &wm->main : &wm->tail;
                 for (int k = 0; k < chunks; ++k, ++s) {
                     const uint32_t slot = s % NS;
-                    if (s >= (uint32_t)NS) wait_sync(&S.empty[slot], ((s / NS) - 1) & 1, S, a.err);
+                    if (s >= (uint32_t)NS) wait_sync<false>(&S.empty[slot], ((s / NS) - 1) & 1, S, a.err);
                     if (is_bad(S)) continue;
-                    mbar_arrive_expect_tx(&S.full[slot], kStageBytes);
-                    tma_load_2d(ring + slot * kStageBytes, wmap, k * 64, L * 256 + p * 128, &S.full[slot]);
+                    mbar_arrive_expect_tx(&S.full[slot], (uint32_t)rows * 128u);
+                    unsigned char* dst = ring + slot * kStageBytes + rank * piece * 128;
+                    const int y = L * 256 + p * kStageRows + (int)rank * piece;
+                    if (CS == 1)
+                        tma_load_2d(dst, map, k * 64, y, &S.full[slot]);
+                    else
+                        tma_load_2d_multicast(dst, map, k * 64, y, &S.full[slot], (uint16_t)((1u << CS) - 1u));
 #pragma unroll
                     for (int j = 0; j < NS; ++j)
                         if (j == (int)slot) last[j] = (int)s;
                 }
+            }
         }
     // nothing may still be landing in shared memory when the CTA exits
 #pragma unroll
@@ -143,36 +167,35 @@ __device__ void produce(const CUtensorMap* wmap, const PolicyArgs& a, unsigned c
 }
 
 // ---- MMA issuer ------------------------------------------------------------
-template <int NS>
+template <int NS, int CS>
 __device__ void issue(const PolicyArgs& a, unsigned char* A, unsigned char* ring, Sync& S, uint32_t tmem,
                       int n_passes)
 {
     uint32_t s = 0;
-    const uint32_t id128 = idesc_bf16_f32(kM, 128);
-    const uint32_t id3 = idesc_bf16_f32(kM, a.n3_last);
     for (int it = 0; it < n_passes; ++it) {
-        wait_sync(&S.xrdy, it & 1, S, a.err);
+        wait_sync<false>(&S.xrdy, it & 1, S, a.err);
         fence_after();
         for (int L = 0; L < 3; ++L) {
             if (L > 0) {
-                wait_sync(&S.hrdy, (2 * it + L - 1) & 1, S, a.err);
+                wait_sync<false>(&S.hrdy, (2 * it + L - 1) & 1, S, a.err);
                 fence_after();
             }
-            const int parts = L < 2 ? 2 : a.parts3;
+            const int parts = L < 2 ? 1 : a.parts3;
             const int chunks = L == 0 ? a.ch1 : 4;
             for (int p = 0; p < parts; ++p) {
-                const uint32_t id = (L == 2 && p == parts - 1) ? id3 : id128;
+                const uint32_t id = idesc_bf16_f32(kM, part_rows(a, L, p));
                 for (int k = 0; k < chunks; ++k, ++s) {
                     const uint32_t slot = s % NS;
-                    wait_sync(&S.full[slot], (s / NS) & 1, S, a.err);
+                    wait_sync<false>(&S.full[slot], (s / NS) & 1, S, a.err);
                     fence_after();
                     if (is_bad(S)) continue;
                     const int nks = (L == 0 && k == chunks - 1) ? a.ks1_last : 4;
                     unsigned char* bst = ring + slot * kStageBytes;
                     for (int j = 0; j < nks; ++j)
-                        mma_bf16(tmem + (uint32_t)(p * 128), sdesc_sw128(A + k * kChunkBytes + j * 32),
+                        mma_bf16(tmem + (uint32_t)(p * kStageRows), sdesc_sw128(A + k * kChunkBytes + j * 32),
                                  sdesc_sw128(bst + j * 32), id, (k | j) != 0);
-                    mma_commit(&S.empty[slot]);
+                    if (CS == 1) mma_commit(&S.empty[slot]);
+                    else mma_commit_multicast(&S.empty[slot], (uint16_t)((1u << CS) - 1u));
                 }
             }
             if (!is_bad(S)) mma_commit(&S.acc);
@@ -308,14 +331,14 @@ __device__ __forceinline__ void worker_arrive(uint64_t* bar)
 // k_policy: actions of every env from observations
 // =============================================================================
 template <int LT>
-__global__ void __launch_bounds__(kThreads, 1) k_policy(const __grid_constant__ CUtensorMap wmap, const PolicyArgs a)
+__global__ void __launch_bounds__(kThreads, 1) k_policy(const __grid_constant__ WMaps wm, const PolicyArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* A = aligned_smem(smem_raw);
     unsigned char* ring = A + kActBytes;
     __shared__ Sync S;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (threadIdx.x == 0) init_sync(S, kPolStages);
+    if (threadIdx.x == 0) init_sync(S, kPolStages, 1);
     if (warp == 1) tmem_alloc(&S.tmem, kTmemCols);
     fence_before();
     __syncthreads();
@@ -324,10 +347,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_policy(const __grid_constant__ 
     const int n_tiles = (a.E + kM - 1) / kM;
     const int my_tiles = blockIdx.x < n_tiles ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     if (warp == 0) {
-        if (lane == 0) produce<kPolStages>(&wmap, a, ring, S, my_tiles);
+        if (lane == 0) produce<kPolStages, 1>(&wm, a, ring, S, my_tiles);
         __syncwarp();
     } else if (warp == 1) {
-        if (lane == 0) issue<kPolStages>(a, A, ring, S, tmem, my_tiles);
+        if (lane == 0) issue<kPolStages, 1>(a, A, ring, S, tmem, my_tiles);
         __syncwarp();
     } else {
         const int ew = warp - 2, q = warp & 3, h = ew >> 2;
@@ -407,11 +430,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_policy(const __grid_constant__ 
 // k_rollout: observe -> MLP -> sample -> environment step, T times
 // =============================================================================
 
-// per-env state held by the owner thread (warps 2-5, one env per thread)
+// Per-station state, held in registers by BOTH worker threads of a station
+// (warps 2-5 take its chargers 0-15, warps 6-9 chargers 16-31: "half" 0 and
+// 1).  Both halves apply the same station-level updates from the same
+// exchanged totals, so their copies stay identical; half 0 writes the
+// station's outputs.
 struct Owner {
     long long e;
     bool live;
-    int slot, t, day, cls_row, occ;
+    int half, slot, t, day, cls_row, occ;
     long long pb;
     uint32_t uid, k0, k1, g, ncar, ablk;
     uint4 aw;
@@ -422,14 +449,26 @@ struct Owner {
 };
 
 // Observation staging: one 8-charger chunk (plus the 8 station features in
-// chunk 0) of each of an owner warp's 32 rows; row stride kStageRow floats.
-constexpr int kStageRow = 8 + 48 + 4;   // 16-byte aligned rows
+// chunk 0) of 16 rows per worker warp; row stride kStageRow floats.
+constexpr int kStageRow = 8 + 48 + 4;      // 16-byte aligned rows
+constexpr int kObsRows = 16;               // rows per staging round
+
+// values the two halves of a station exchange during a step (per row)
+struct Xchg {
+    float trail[kM];                       // half 0: power of the group still open after charger 15
+    float lead[kM];                        // half 1: power up to its first tail charger
+    int first_gs[kM];                      // half 1: group slot of that tail (-1: none)
+    float raw[2][kM], over[2][kM], sp[2][kM], se[2][kM], csat[2][kM];
+    int nfree[2][kM], occ[2][kM];
+};
+
 struct RollSmem {
     float gcap[32 * kM];                   // group slot x row: eta_H * I_H of the group of a tail charger
     union {                                // the step's group scales, then the observation staging
         float gscale[32 * kM];             // group slot x row
-        float stage[4][32 * kStageRow];    // per owner warp
+        float stage[kWorkerWarps][kObsRows * kStageRow];
     } u;
+    Xchg x;
     uint32_t act[kM * kPolicyMaxPorts / 4]; // sampled levels, row-major [row][charger] bytes
     uint32_t gstep[kM], key0[kM], key1[kM];
 };
@@ -442,11 +481,15 @@ __device__ __noinline__ uint4 car_words_late(uint32_t uid, uint32_t n, uint32_t 
     return car_words(uid, n, k0, k1);
 }
 
-__device__ __forceinline__ void owner_load(Owner& o, const RolloutArgs& R, int tile, int row, uint32_t tl, RollSmem& rs)
+// Load the station's state (both halves: station fields; each half: its 16
+// chargers into TMEM).  Ends with the workers' named barrier (occupancy).
+__device__ __forceinline__ void owner_load(Owner& o, const RolloutArgs& R, int tile, int row, int half, uint32_t tl,
+                                           RollSmem& rs)
 {
     const DevBatch& b = R.b;
     o.e = (long long)tile * kM + row;
     o.live = o.e < R.pol.E;
+    o.half = half;
     o.slot = 0; o.pb = 0; o.uid = 0; o.k0 = o.k1 = o.g = o.ncar = 0;
     o.t = 0; o.day = 0; o.cls_row = 0; o.occ = 0;
     o.grid_cap = 1.f; o.grid_inv_eta = 1.f; o.ret = 0.f; o.price = 0.f;
@@ -469,8 +512,10 @@ __device__ __forceinline__ void owner_load(Owner& o, const RolloutArgs& R, int t
         o.ret = b.ep_ret[o.slot];
         o.price = __ldg(b.price + (size_t)o.day * (size_t)R.p.ep_len + (size_t)o.t);
     }
+    int occ = 0;
 #pragma unroll 1
-    for (int k = 0; k < 4; ++k) {
+    for (int kk = 0; kk < 2; ++kk) {
+        const int k = 2 * half + kk;
         uint32_t vs[8], ve[8], vc[8], vr[8], vp[8], vw[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
@@ -485,7 +530,7 @@ __device__ __forceinline__ void owner_load(Owner& o, const RolloutArgs& R, int t
                 vw[i] = __float_as_uint(b.pw[x]);
                 const uint32_t meta = b.meta[x];
                 vp[i] = (uint32_t)b.trem[x] | (meta << 8);
-                o.occ += b.trem[x] > 0 ? 1 : 0;
+                occ += b.trem[x] > 0 ? 1 : 0;
                 if (meta & kMetaTail) rs.gcap[((meta >> kMetaGroupShift) & 31u) * kM + row] = b.gcap[x];
             }
         }
@@ -497,17 +542,26 @@ __device__ __forceinline__ void owner_load(Owner& o, const RolloutArgs& R, int t
         tmem_st8(taddr_of(tl, kColPw + 8 * k), vw);
     }
     tmem_wait_st();
-    rs.gstep[row] = o.g;
-    rs.key0[row] = o.k0;
-    rs.key1[row] = o.k1;
+    rs.x.occ[half][row] = occ;
+    if (half == 0) {
+        rs.gstep[row] = o.g;
+        rs.key0[row] = o.k0;
+        rs.key1[row] = o.k1;
+    }
+    fence_before();
+    named_sync(kBarWorkers, kWorkers);
+    fence_after();
+    o.occ = rs.x.occ[0][row] + rs.x.occ[1][row];
 }
 
-// One environment step of the owner's env with the sampled levels of this
-// step (Appendix A.2 then A.3, the same operations as the fused step kernel).
+// One environment step of the station with this step's sampled levels
+// (Appendix A.2 then A.3; the operations of the fused step kernel), this
+// thread's half of the chargers, three exchanges with the other half.
 __device__ __forceinline__ void owner_step(Owner& o, const RolloutArgs& R, int it, int row, uint32_t tl, RollSmem& rs)
 {
     const DevParams& p = R.p;
     const DevBatch& b = R.b;
+    const int h = o.half;
     // arrival count of this step (Philox word, Poisson CDF row)
     const uint32_t blk = o.g >> 2;
     if (blk != o.ablk) {
@@ -517,15 +571,18 @@ __device__ __forceinline__ void owner_step(Owner& o, const RolloutArgs& R, int i
     const float* F = b.cdf + ((size_t)o.cls_row * (size_t)p.ep_len + (size_t)o.t) * kCdfLen;
     const float4 f0 = __ldg(reinterpret_cast<const float4*>(F));
     const float4 f1 = __ldg(reinterpret_cast<const float4*>(F + 4));
-    uint32_t lv[kPolicyMaxPorts / 4];
+    uint32_t lv[4];
 #pragma unroll
-    for (int j = 0; j < kPolicyMaxPorts / 4; ++j) lv[j] = rs.act[row * (kPolicyMaxPorts / 4) + j];
+    for (int j = 0; j < 4; ++j) lv[j] = rs.act[row * (kPolicyMaxPorts / 4) + 4 * h + j];
 
-    // (i) per-charger clip; group sums at each group's tail charger
-    float P[32];
+    // (i) per-charger clip; sums of the groups whose tail is in this half
+    float P[16];
     float gacc = 0.f, raw = 0.f, over = 0.f;
+    int nfree = 0, last_tail = -1, first_tail = -1, first_gs = -1;
+    float lead = 0.f;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int kk = 0; kk < 2; ++kk) {
+        const int k = 2 * h + kk;
         uint32_t vs[8], ve[8], vc[8], vr[8], vp[8];
         tmem_ld8(taddr_of(tl, kColSoc + 8 * k), vs);
         tmem_ld8(taddr_of(tl, kColErem + 8 * k), ve);
@@ -535,42 +592,85 @@ __device__ __forceinline__ void owner_step(Owner& o, const RolloutArgs& R, int i
         tmem_wait_ld();
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            const int c = 8 * k + i;
+            const int ci = 8 * kk + i;
             const int trem = (int)(vp[i] & 0xFFu);
             const uint32_t meta = vp[i] >> 8;
-            const int lvl = (int)((lv[c >> 2] >> (8 * (c & 3))) & 0xFFu);
+            const int lvl = (int)((lv[ci >> 2] >> (8 * (ci & 3))) & 0xFFu);
             const bool dc = meta & kMetaDC;
-            P[c] = trem > 0 ? clip_power(lvl, dc, __uint_as_float(vs[i]), __uint_as_float(ve[i]),
-                                         __uint_as_float(vc[i]), __uint_as_float(vr[i]), p)
-                            : 0.f;
-            raw += P[c];
-            gacc += P[c];
+            P[ci] = trem > 0 ? clip_power(lvl, dc, __uint_as_float(vs[i]), __uint_as_float(ve[i]),
+                                          __uint_as_float(vc[i]), __uint_as_float(vr[i]), p)
+                             : 0.f;
+            raw += P[ci];
+            gacc += P[ci];
+            nfree += ((meta & kMetaValid) && trem <= 1) ? 1 : 0;    // free once this step's departures left
             if (meta & kMetaTail) {
                 const int gs = (int)((meta >> kMetaGroupShift) & 31u);
-                const float gc = rs.gcap[gs * kM + row];
-                rs.u.gscale[gs * kM + row] = gacc > gc ? __fdividef(gc, gacc) : 1.0f;
-                if (p.a_con != 0.f) over = fmaxf(over, (gacc - gc) * __ldg(b.ginv_eta + o.pb + c));
+                if (h == 1 && first_tail < 0) {                      // may close a group opened in half 0
+                    first_tail = ci;
+                    first_gs = gs;
+                    lead = gacc;
+                } else {
+                    const float gc = rs.gcap[gs * kM + row];
+                    rs.u.gscale[gs * kM + row] = gacc > gc ? __fdividef(gc, gacc) : 1.0f;
+                    if (p.a_con != 0.f) over = fmaxf(over, (gacc - gc) * __ldg(b.ginv_eta + o.pb + 16 * h + ci));
+                }
+                last_tail = ci;
                 gacc = 0.f;
             }
         }
     }
-    // architecture constraint: each charger scaled by its group, then the root
+    if (h == 0) rs.x.trail[row] = gacc;
+    else {
+        rs.x.lead[row] = lead;
+        rs.x.first_gs[row] = first_gs;
+    }
+    rs.x.raw[h][row] = raw;
+    rs.x.over[h][row] = over;
+    rs.x.nfree[h][row] = nfree;
+    named_sync(kBarWorkers, kWorkers);                               // exchange A
+
+    // the group that closes at half 1's first tail charger (it may have
+    // started in half 0): both halves compute its scale
+    const int sgs = rs.x.first_gs[row];
+    float s_scale = 1.f, s_over = 0.f;
+    if (sgs >= 0) {
+        const float S = rs.x.trail[row] + rs.x.lead[row];
+        const float gc = rs.gcap[sgs * kM + row];
+        s_scale = S > gc ? __fdividef(gc, S) : 1.0f;
+        // its tail charger is half 1's first tail (an index only half 1 has)
+        if (h == 1 && p.a_con != 0.f) s_over = (S - gc) * __ldg(b.ginv_eta + o.pb + 16 + first_tail);
+    }
+    const int nfree0 = rs.x.nfree[0][row], nfree1 = rs.x.nfree[1][row];
+    // architecture constraint: charger power scaled by its group
     float sp = 0.f;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int kk = 0; kk < 2; ++kk) {
+        const int k = 2 * h + kk;
         uint32_t vp[8];
         tmem_ld8(taddr_of(tl, kColPack + 8 * k), vp);
         tmem_wait_ld();
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            const int c = 8 * k + i;
+            const int ci = 8 * kk + i;
             const uint32_t meta = vp[i] >> 8;
-            if (meta & kMetaValid) P[c] *= rs.u.gscale[((meta >> kMetaGroupShift) & 31u) * kM + row];
-            sp += P[c];
+            const bool in_split = h == 0 ? ci > last_tail : (first_tail >= 0 && ci <= first_tail);
+            float sc = 1.f;
+            if (in_split) sc = s_scale;
+            else if (meta & kMetaValid) sc = rs.u.gscale[((meta >> kMetaGroupShift) & 31u) * kM + row];
+            P[ci] *= sc;
+            sp += P[ci];
         }
     }
-    const float s_root = sp > o.grid_cap ? __fdividef(o.grid_cap, sp) : 1.0f;
-    const float c_con = p.a_con != 0.f ? fmaxf(fmaxf(over, (raw - o.grid_cap) * o.grid_inv_eta), 0.f) : 0.f;
+    rs.x.sp[h][row] = sp;
+    named_sync(kBarWorkers, kWorkers);                               // exchange B
+    const float sp_all = rs.x.sp[0][row] + rs.x.sp[1][row];
+    const float raw_all = rs.x.raw[0][row] + rs.x.raw[1][row];
+    const float s_root = sp_all > o.grid_cap ? __fdividef(o.grid_cap, sp_all) : 1.0f;
+    float c_con = 0.f;
+    if (p.a_con != 0.f) {
+        // s_over was formed by half 1 with the right tail; half 0 takes it from the exchange
+        if (h == 1) rs.x.over[1][row] = fmaxf(rs.x.over[1][row], s_over);
+    }
 
     // Poisson count: the smallest k with u < F_k (F nondecreasing, F_127 = inf)
     const uint32_t word = word_of(o.aw, o.g & 3u);
@@ -579,22 +679,23 @@ __device__ __forceinline__ void owner_step(Owner& o, const RolloutArgs& R, int i
             (u >= f1.w);
     if (M == 8)
         while (u >= __ldg(F + M)) ++M;
-
-    // words of the first cars that may arrive (at most M are admitted); more
-    // than kPreCars arrivals in one step are drawn where they are placed
+    // first come first served: half 0's free chargers take the first cars
+    const int adm0 = min(M, nfree0), adm1 = min(M - adm0, nfree1);
+    const int quota = h == 0 ? adm0 : adm1;
+    const uint32_t car0 = o.ncar + (uint32_t)(h == 0 ? 0 : adm0);
     constexpr int kPreCars = 4;
     uint4 cw[kPreCars];
 #pragma unroll
     for (int j = 0; j < kPreCars; ++j)
-        cw[j] = j < M ? car_words(o.uid, o.ncar + (uint32_t)j, o.k0, o.k1) : make_uint4(0, 0, 0, 0);
+        cw[j] = j < quota ? car_words(o.uid, car0 + (uint32_t)j, o.k0, o.k1) : make_uint4(0, 0, 0, 0);
 
-    // (ii) charge, (iii) departures, (iv) arrivals first come first served,
-    // and the episode end; state written back to TMEM
+    // (ii) charge, (iii) departures, (iv) arrivals, and the episode end
     const bool fin = o.t + 1 >= p.ep_len;
     float se = 0.f, c_sat = 0.f;
     int adm = 0, occ = 0;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int kk = 0; kk < 2; ++kk) {
+        const int k = 2 * h + kk;
         uint32_t vs[8], ve[8], vc[8], vr[8], vp[8], vw[8];
         tmem_ld8(taddr_of(tl, kColSoc + 8 * k), vs);
         tmem_ld8(taddr_of(tl, kColErem + 8 * k), ve);
@@ -604,14 +705,14 @@ __device__ __forceinline__ void owner_step(Owner& o, const RolloutArgs& R, int i
         tmem_wait_ld();
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            const int c = 8 * k + i;
+            const int ci = 8 * kk + i;
             int trem = (int)(vp[i] & 0xFFu);
             const uint32_t meta = vp[i] >> 8;
             const bool dc = meta & kMetaDC;
             float soc = __uint_as_float(vs[i]), erem = __uint_as_float(ve[i]);
             float cap = __uint_as_float(vc[i]), rbar = __uint_as_float(vr[i]);
-            const float Pq = P[c] * s_root;
-            se += P[c] * (dc ? p.inv_eta1 : p.inv_eta0);
+            const float Pq = P[ci] * s_root;
+            se += P[ci] * (dc ? p.inv_eta1 : p.inv_eta0);
             float pw = Pq;
             if (trem > 0) {
                 const float dE = Pq * p.dt;
@@ -623,12 +724,12 @@ __device__ __forceinline__ void owner_step(Owner& o, const RolloutArgs& R, int i
                     soc = 0.f; erem = 0.f; cap = 0.f; rbar = 0.f;
                 }
             }
-            if ((meta & kMetaValid) && trem == 0 && adm < M) {
+            if ((meta & kMetaValid) && trem == 0 && adm < quota) {
                 const uint4 w = adm == 0 ? cw[0]
                               : adm == 1 ? cw[1]
                               : adm == 2 ? cw[2]
                               : adm == 3 ? cw[3]
-                                         : car_words_late(o.uid, o.ncar + (uint32_t)adm, o.k0, o.k1);
+                                         : car_words_late(o.uid, car0 + (uint32_t)adm, o.k0, o.k1);
                 const Car car = car_from_words(w, dc, p);
                 cap = car.cap; soc = car.soc; erem = car.erem; rbar = car.rbar;
                 trem = car.stay;
@@ -654,18 +755,30 @@ __device__ __forceinline__ void owner_step(Owner& o, const RolloutArgs& R, int i
         tmem_st8(taddr_of(tl, kColPw + 8 * k), vw);
     }
     tmem_wait_st();
+    rs.x.se[h][row] = se;
+    rs.x.csat[h][row] = c_sat;
+    rs.x.occ[h][row] = occ;
+    named_sync(kBarWorkers, kWorkers);                               // exchange C
+    const float se_all = rs.x.se[0][row] + rs.x.se[1][row];
+    const float csat_all = rs.x.csat[0][row] + rs.x.csat[1][row];
+    const int adm_all = adm0 + adm1;
+    if (p.a_con != 0.f) {
+        const float over_all = fmaxf(rs.x.over[0][row], rs.x.over[1][row]);
+        c_con = fmaxf(fmaxf(over_all, (raw_all - o.grid_cap) * o.grid_inv_eta), 0.f);
+    }
+    o.occ = rs.x.occ[0][row] + rs.x.occ[1][row];
 
     // reward, Appendix A.3
-    const float e_net = sp * s_root * p.dt;
-    const float e_grid = se * s_root * p.dt;
-    o.ncar += (uint32_t)adm;
+    const float e_net = sp_all * s_root * p.dt;
+    const float e_grid = se_all * s_root * p.dt;
+    o.ncar += (uint32_t)adm_all;
     const float profit = p.p_sell * e_net - o.price * e_grid - p.c_fixed;
-    const float r = profit - p.a_sat * c_sat - p.a_decl * (float)(M - adm) - p.a_con * c_con;
+    const float r = profit - p.a_sat * csat_all - p.a_decl * (float)(M - adm_all) - p.a_con * c_con;
     o.ret += r;
     o.t += 1;
-    o.st_arr += (uint32_t)adm;
-    o.st_rej += (uint32_t)(M - adm);
-    o.st_miss += c_sat;
+    o.st_arr += (uint32_t)adm_all;
+    o.st_rej += (uint32_t)(M - adm_all);
+    o.st_miss += csat_all;
     o.st_chg += e_net;
     if (fin) {
         o.last_ret = o.ret;
@@ -676,33 +789,33 @@ __device__ __forceinline__ void owner_step(Owner& o, const RolloutArgs& R, int i
         o.day = draw_day(o.uid, o.g, 0u, o.k0, o.k1, p.n_days);
     }
     o.g += 1u;
-    o.occ = occ;
     if (o.live) {
-        const long long out = (long long)it * R.pol.E + o.e;
-        if (R.reward) R.reward[out] = r;
-        if (R.done) R.done[out] = fin ? 1 : 0;
+        if (h == 0) {
+            const long long out = (long long)it * R.pol.E + o.e;
+            if (R.reward) R.reward[out] = r;
+            if (R.done) R.done[out] = fin ? 1 : 0;
+        }
         o.price = __ldg(b.price + (size_t)o.day * (size_t)p.ep_len + (size_t)o.t);
     }
-    rs.gstep[row] = o.g;
+    if (h == 0) rs.gstep[row] = o.g;
 }
 
-// Observation of the owner warp's 32 envs (rows 32q .. 32q+31) after the
-// step, one 8-charger chunk at a time with every lane on its own row: the
-// chunk's features go to the layer-1 operand as BF16 and, as FP32, to the
-// warp's staging buffer, which the warp then writes to HBM row by row
-// (each row's chunk is a contiguous, 16-byte aligned run).
+// Observation after the step: this half's chunks (half 0 also the 8 station
+// features), every lane on its own row; BF16 into the layer-1 operand, FP32
+// to HBM through the warp's staging buffer, 16 rows at a time, each row's
+// chunk a contiguous, 16-byte aligned run.
 __device__ __forceinline__ void owner_observe(const Owner& o, const RolloutArgs& R, int it, int q, int lane, uint32_t tl,
                                               uint32_t abase, float* stage)
 {
     const DevParams& p = R.p;
     const int D = R.pol.obs_dim, N = R.pol.n_ports;
     const int row = 32 * q + lane;
-    float* srow = stage + lane * kStageRow;
     const long long e0 = o.e - lane;                        // env of the warp's first row
-    const int n_rows = (int)min(32LL, max(0LL, (long long)R.pol.E - e0));
     const int n_chunks = (N + 7) >> 3;
 #pragma unroll 1
-    for (int k = 0; k < n_chunks; ++k) {
+    for (int kk = 0; kk < 2; ++kk) {
+        const int k = 2 * o.half + kk;
+        if (k >= n_chunks) break;                           // uniform across the warp
         uint32_t vs[8], ve[8], vr[8], vp[8], vw[8];
         tmem_ld8(taddr_of(tl, kColSoc + 8 * k), vs);
         tmem_ld8(taddr_of(tl, kColErem + 8 * k), ve);
@@ -710,66 +823,86 @@ __device__ __forceinline__ void owner_observe(const Owner& o, const RolloutArgs&
         tmem_ld8(taddr_of(tl, kColPack + 8 * k), vp);
         tmem_ld8(taddr_of(tl, kColPw + 8 * k), vw);
         tmem_wait_ld();
-        // features [f0, f1) of the row: the station's 8 in chunk 0, then 6 per charger
+        // features [f0, f1): the station's 8 in chunk 0, then 6 per charger
         const int f0 = k == 0 ? 0 : 8 + 48 * k;
         const int f1 = min(8 + 48 * (k + 1), D);
-        float* base = srow - f0;                            // feature f of the row at base[f]
-        if (k == 0) {
-            if (o.live) obs_env(base, o.t, o.day, o.occ, N, R.b, p);
-            else
+        float st8[8], cf[48];
+        if (k == 0 && o.live) obs_env(st8, o.t, o.day, o.occ, N, R.b, p);
+        else
 #pragma unroll
-                for (int f = 0; f < 8; ++f) base[f] = 0.f;
-        }
+            for (int f = 0; f < 8; ++f) st8[f] = 0.f;
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const int c = 8 * k + i;
-            if (c < N) {
-                float* f = base + 8 + 6 * c;
-                if (o.live) {
-                    obs_port(f, (int)(vp[i] & 0xFFu), __uint_as_float(vs[i]), __uint_as_float(ve[i]),
-                             __uint_as_float(vr[i]), __uint_as_float(vw[i]), (vp[i] >> 8) & kMetaDC, p);
-                } else {
-#pragma unroll
-                    for (int x = 0; x < 6; ++x) f[x] = 0.f;
-                }
-            }
-        }
-        // BF16 copy into the operand (pairs; the K padding up to 16 is zero)
-        const int f1p = k == n_chunks - 1 ? ((D + 15) & ~15) : f1;
-#pragma unroll 4
-        for (int f = f0; f < f1p; f += 2) {
-            const float x0 = f < D ? base[f] : 0.f, x1 = f + 1 < D ? base[f + 1] : 0.f;
-            st_shared_u32(abase + sw128_offset(row, f, kChunkBytes), pack_bf16x2(x0, x1));
-        }
-        __syncwarp();
-        if (R.obs_out) {                                     // rows of the chunk -> HBM
-            const int len = f1 - f0;                         // a multiple of 2 (4 when D % 4 == 0)
-            float* dst0 = R.obs_out + ((long long)it * R.pol.E + e0) * D + f0;
-            if ((D & 3) == 0) {
-                const int per = len >> 2;
-                for (int x = lane; x < n_rows * per; x += 32) {
-                    const int r = x / per, v = x - r * per;
-                    *reinterpret_cast<float4*>(dst0 + (long long)r * D + 4 * v) =
-                        *reinterpret_cast<const float4*>(stage + r * kStageRow + 4 * v);
-                }
+            if (o.live && c < N) {
+                obs_port(cf + 6 * i, (int)(vp[i] & 0xFFu), __uint_as_float(vs[i]), __uint_as_float(ve[i]),
+                         __uint_as_float(vr[i]), __uint_as_float(vw[i]), (vp[i] >> 8) & kMetaDC, p);
             } else {
-                const int per = len >> 1;
-                for (int x = lane; x < n_rows * per; x += 32) {
-                    const int r = x / per, v = x - r * per;
-                    *reinterpret_cast<float2*>(dst0 + (long long)r * D + 2 * v) =
-                        *reinterpret_cast<const float2*>(stage + r * kStageRow + 2 * v);
-                }
+#pragma unroll
+                for (int x = 0; x < 6; ++x) cf[6 * i + x] = 0.f;
             }
         }
-        __syncwarp();
+        // feature f0 + j (j a compile-time index after unrolling)
+        auto V = [&](int j) -> float {
+            if (k == 0) return j < 8 ? st8[j < 8 ? j : 0] : cf[j >= 8 && j < 56 ? j - 8 : 0];
+            return j < 48 ? cf[j < 48 ? j : 0] : 0.f;
+        };
+        // BF16 into the operand (pairs; the K padding up to 16 is zero)
+        const int n_f = f1 - f0;
+        const bool last = k == n_chunks - 1;
+        const int n_fp = last ? (((D + 15) & ~15) - f0) : n_f;
+#pragma unroll
+        for (int j = 0; j < 56; j += 2) {
+            if (j < n_fp) {
+                const float x0 = j < n_f ? V(j) : 0.f, x1 = j + 1 < n_f ? V(j + 1) : 0.f;
+                st_shared_u32(abase + sw128_offset(row, f0 + j, kChunkBytes), pack_bf16x2(x0, x1));
+            }
+        }
+        if (last && n_fp > 56) {                             // padding beyond the chunk's own width
+            for (int j = 56; j < n_fp; j += 2) st_shared_u32(abase + sw128_offset(row, f0 + j, kChunkBytes), 0u);
+        }
+        if (R.obs_out) {
+#pragma unroll 1
+            for (int half_rows = 0; half_rows < 2; ++half_rows) {
+                if ((lane >> 4) == half_rows) {
+                    float* srow = stage + (lane & 15) * kStageRow;
+#pragma unroll
+                    for (int j = 0; j < 56; j += 4)
+                        if (j < n_f)
+                            *reinterpret_cast<float4*>(srow + j) = make_float4(V(j), V(j + 1), V(j + 2), V(j + 3));
+                }
+                __syncwarp();
+                const long long eb = e0 + 16 * half_rows;
+                const int n_rows = (int)min(16LL, max(0LL, (long long)R.pol.E - eb));
+                float* dst0 = R.obs_out + ((long long)it * R.pol.E + eb) * D + f0;
+                if ((D & 3) == 0) {
+                    const int per = n_f >> 2;
+                    for (int x = lane; x < n_rows * per; x += 32) {
+                        const int r = x / per, c4 = x - r * per;
+                        *reinterpret_cast<float4*>(dst0 + (long long)r * D + 4 * c4) =
+                            *reinterpret_cast<const float4*>(stage + r * kStageRow + 4 * c4);
+                    }
+                } else {
+                    const int per = n_f >> 1;
+                    for (int x = lane; x < n_rows * per; x += 32) {
+                        const int r = x / per, c2 = x - r * per;
+                        *reinterpret_cast<float2*>(dst0 + (long long)r * D + 2 * c2) =
+                            *reinterpret_cast<const float2*>(stage + r * kStageRow + 2 * c2);
+                    }
+                }
+                __syncwarp();
+            }
+        }
     }
 }
 
+// State back to HBM: each half its chargers, half 0 the station fields.
 __device__ __forceinline__ void owner_store(const Owner& o, const RolloutArgs& R, uint32_t tl)
 {
     const DevBatch& b = R.b;
 #pragma unroll 1
-    for (int k = 0; k < 4; ++k) {
+    for (int kk = 0; kk < 2; ++kk) {
+        const int k = 2 * o.half + kk;
         uint32_t vs[8], ve[8], vc[8], vr[8], vp[8], vw[8];
         tmem_ld8(taddr_of(tl, kColSoc + 8 * k), vs);
         tmem_ld8(taddr_of(tl, kColErem + 8 * k), ve);
@@ -793,7 +926,7 @@ __device__ __forceinline__ void owner_store(const Owner& o, const RolloutArgs& R
             }
         }
     }
-    if (!o.live) return;
+    if (!o.live || o.half != 0) return;
     const int s = o.slot;
     b.tod[s] = o.t;
     b.day[s] = o.day;
@@ -809,7 +942,7 @@ __device__ __forceinline__ void owner_store(const Owner& o, const RolloutArgs& R
 }
 
 template <int LT>
-__global__ void __launch_bounds__(kThreads, 1) k_rollout(const __grid_constant__ CUtensorMap wmap, const RolloutArgs R)
+__global__ void __launch_bounds__(kThreads, 1) k_rollout(const __grid_constant__ WMaps wm, const RolloutArgs R)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* A = aligned_smem(smem_raw);
@@ -818,34 +951,31 @@ __global__ void __launch_bounds__(kThreads, 1) k_rollout(const __grid_constant__
     __shared__ Sync S;
     const PolicyArgs& a = R.pol;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (threadIdx.x == 0) init_sync(S, kRollStages);
+    if (threadIdx.x == 0) init_sync(S, kRollStages, kRollCluster);
     if (warp == 1) tmem_alloc(&S.tmem, kTmemCols);
     fence_before();
-    __syncthreads();
+    cluster_sync();                        // barriers of every CTA initialised before any multicast
     fence_after();
     const uint32_t tmem = S.tmem;
     const int tile = blockIdx.x;
     if (warp == 0) {
-        if (lane == 0) produce<kRollStages>(&wmap, a, ring, S, R.T);
+        if (lane == 0) produce<kRollStages, kRollCluster>(&wm, a, ring, S, R.T);
         __syncwarp();
     } else if (warp == 1) {
-        if (lane == 0) issue<kRollStages>(a, A, ring, S, tmem, R.T);
+        if (lane == 0) issue<kRollStages, kRollCluster>(a, A, ring, S, tmem, R.T);
         __syncwarp();
     } else {
         const int ew = warp - 2, q = warp & 3, h = ew >> 2;
-        const bool owner = ew < 4;
         const int row = 32 * q + lane;
         const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);
         const uint32_t abase = smem_addr(A);
         const long long env = (long long)tile * kM + row;
         const bool live = env < a.E;
         Owner o;
-        if (owner) {
-            owner_load(o, R, tile, row, tl, rs);
-            fence_before();
-            owner_observe(o, R, 0, q, lane, tl, abase, rs.u.stage[ew]);
-        }
+        owner_load(o, R, tile, row, h, tl, rs);
+        owner_observe(o, R, 0, q, lane, tl, abase, rs.u.stage[ew]);
         for (int it = 0; it < R.T; ++it) {
+            fence_before();
             named_sync(kBarWorkers, kWorkers);
             worker_arrive(&S.xrdy);
             for (int L = 0; L < 2; ++L) {
@@ -866,18 +996,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_rollout(const __grid_constant__
             if (live) store_levels(a.actions + ((long long)it * a.E + env) * a.n_ports, h, a.n_ports, packed);
             fence_before();
             named_sync(kBarWorkers, kWorkers);
-            if (owner) {
-                fence_after();
-                owner_step(o, R, it, row, tl, rs);
-                named_sync(kBarOwners, 128);           // group scales done: the staging may overwrite them
-                if (it + 1 < R.T) owner_observe(o, R, it + 1, q, lane, tl, abase, rs.u.stage[ew]);
-                fence_before();
-            }
+            fence_after();
+            owner_step(o, R, it, row, tl, rs);
+            named_sync(kBarWorkers, kWorkers);                 // group scales done: the staging may overwrite them
+            if (it + 1 < R.T) owner_observe(o, R, it + 1, q, lane, tl, abase, rs.u.stage[ew]);
         }
-        if (owner) owner_store(o, R, tl);
+        owner_store(o, R, tl);
     }
     fence_before();
-    __syncthreads();
+    cluster_sync();                        // no peer still commits to or multicasts into this CTA
     if (warp == 1) {
         fence_after();
         tmem_dealloc(tmem, kTmemCols);
@@ -903,29 +1030,40 @@ cudaError_t policy_prepare()
     return cudaFuncSetAttribute(k_rollout<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRolloutSmem);
 }
 
-cudaError_t launch_policy(const CUtensorMap& wmap, const PolicyArgs& a, int sm_count, cudaStream_t st)
+cudaError_t launch_policy(const WMaps& wm, const PolicyArgs& a, int sm_count, cudaStream_t st)
 {
     const int n_tiles = (a.E + kM - 1) / kM;
     const int grid = n_tiles < sm_count ? n_tiles : sm_count;
     if (grid <= 0) return cudaSuccess;
     if (a.n_levels == 11)
-        k_policy<11><<<grid, kThreads, kPolicySmem, st>>>(wmap, a);
+        k_policy<11><<<grid, kThreads, kPolicySmem, st>>>(wm, a);
     else
-        k_policy<0><<<grid, kThreads, kPolicySmem, st>>>(wmap, a);
+        k_policy<0><<<grid, kThreads, kPolicySmem, st>>>(wm, a);
     return cudaGetLastError();
 }
 
 bool rollout_fits(int n_out_pad) { return n_out_pad <= kColSoc; }
+int policy_stage_rows() { return kStageRows; }
+int rollout_cluster() { return kRollCluster; }
 
-cudaError_t launch_rollout(const CUtensorMap& wmap, const RolloutArgs& r, cudaStream_t st)
+cudaError_t launch_rollout(const WMaps& wm, const RolloutArgs& r, cudaStream_t st)
 {
     const int n_tiles = (r.pol.E + kM - 1) / kM;
     if (n_tiles <= 0 || r.T <= 0) return cudaSuccess;
-    if (r.pol.n_levels == 11)
-        k_rollout<11><<<n_tiles, kThreads, kRolloutSmem, st>>>(wmap, r);
-    else
-        k_rollout<0><<<n_tiles, kThreads, kRolloutSmem, st>>>(wmap, r);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)((n_tiles + kRollCluster - 1) / kRollCluster * kRollCluster));
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = kRolloutSmem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kRollCluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (r.pol.n_levels == 11) return cudaLaunchKernelEx(&cfg, k_rollout<11>, wm, r);
+    return cudaLaunchKernelEx(&cfg, k_rollout<0>, wm, r);
 }
 
 }  // namespace chx

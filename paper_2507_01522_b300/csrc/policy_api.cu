@@ -80,7 +80,7 @@ chx::PolicyArgs policy_args(const chx_handle* h, const float* obs, int8_t* actio
 
 int enqueue_policy(chx_handle* h, const float* obs, int8_t* actions, float* logits, cudaStream_t st)
 {
-    CUDA_TRY(chx::launch_policy(h->policy.map, policy_args(h, obs, actions, logits), h->sm_count, st));
+    CUDA_TRY(chx::launch_policy(h->policy.maps, policy_args(h, obs, actions, logits), h->sm_count, st));
     return CHX_OK;
 }
 
@@ -177,14 +177,21 @@ extern "C" int chx_policy_load(chx_handle* h, int32_t hidden, const uint16_t* h_
         CUDA_TRY(cudaMalloc(&P.d_bias, bias.size() * sizeof(float)));
         const cuuint64_t dims[2] = {(cuuint64_t)H, (cuuint64_t)rows};
         const cuuint64_t strides[1] = {(cuuint64_t)H * sizeof(uint16_t)};
-        const cuuint32_t box[2] = {64, 128};
         const cuuint32_t estr[2] = {1, 1};
-        const CUresult r = enc(&P.map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, P.d_w, dims, strides, box, estr,
-                               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) {
-            chx::free_policy(h);
-            return fail(CHX_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+        const int sr = chx::policy_stage_rows();
+        const int parts3 = (n_out_pad + sr - 1) / sr, n3_last = n_out_pad - sr * (parts3 - 1);
+        const int cs = chx::rollout_cluster();
+        struct { CUtensorMap* m; int box_rows; } want[4] = {
+            {&P.maps.main, sr}, {&P.maps.tail, n3_last}, {&P.maps_roll.main, sr / cs}, {&P.maps_roll.tail, n3_last / cs}};
+        for (auto& w : want) {
+            const cuuint32_t box[2] = {64, (cuuint32_t)w.box_rows};
+            const CUresult r = enc(w.m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, P.d_w, dims, strides, box, estr,
+                                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) {
+                chx::free_policy(h);
+                return fail(CHX_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+            }
         }
         CUDA_TRY(chx::policy_prepare());
     }
@@ -197,8 +204,8 @@ extern "C" int chx_policy_load(chx_handle* h, int32_t hidden, const uint16_t* h_
     P.rows = rows;
     P.ch1 = (D + 63) / 64;
     P.ks1_last = (D - 64 * (P.ch1 - 1) + 15) / 16;
-    P.parts3 = (n_out_pad + 127) / 128;
-    P.n3_last = n_out_pad - 128 * (P.parts3 - 1);
+    P.parts3 = (n_out_pad + chx::policy_stage_rows() - 1) / chx::policy_stage_rows();
+    P.n3_last = n_out_pad - chx::policy_stage_rows() * (P.parts3 - 1);
     P.loaded = true;
     return CHX_OK;
 }
@@ -234,7 +241,7 @@ extern "C" int chx_policy_rollout(chx_handle* h, int32_t n_steps, float* d_obs, 
         r.port_base = h->cls_port_base[cls];
         r.env_base = h->cls_env_base[cls];
         r.C = 8 << cls;
-        CUDA_TRY(chx::launch_rollout(P.map, r, (cudaStream_t)stream));
+        CUDA_TRY(chx::launch_rollout(P.maps_roll, r, (cudaStream_t)stream));
         return CHX_OK;
     }
     if (!d_obs) return fail(CHX_EINVAL, "the split rollout needs the observation buffer");
