@@ -48,6 +48,7 @@ struct DevParams {
     uint32_t stay_span;
     float rb_lo0, rb_span0, rb_lo1, rb_span1;
     float obs_inv_stay, obs_inv_cap, obs_inv_days, obs_inv_len;
+    float inv_pmax0, inv_pmax1;            // 1 / maximum power (FP32, correctly rounded), per type
 };
 
 struct DevBatch {
@@ -212,7 +213,7 @@ __device__ __forceinline__ void obs_env(float* o, int t, int day, int occ, int n
 __device__ __forceinline__ void obs_port(float* o, int trem, float soc, float erem, float rbar, float pw, bool dc,
                                          const DevParams& p)
 {
-    const float inv_pmax = 1.0f / (dc ? p.pmax1 : p.pmax0);
+    const float inv_pmax = dc ? p.inv_pmax1 : p.inv_pmax0;
     const bool on = trem > 0;
     o[0] = on ? 1.0f : 0.0f;
     o[1] = soc;

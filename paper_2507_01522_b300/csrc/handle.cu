@@ -189,6 +189,8 @@ DevParams make_params(const chx_env_params& q, int n_days)
     p.rb_span0 = q.rbar_kw[0][1] - q.rbar_kw[0][0];
     p.rb_lo1 = q.rbar_kw[1][0];
     p.rb_span1 = q.rbar_kw[1][1] - q.rbar_kw[1][0];
+    p.inv_pmax0 = 1.0f / q.p_max_kw[0];      // FP32 division: the value the kernels computed before
+    p.inv_pmax1 = 1.0f / q.p_max_kw[1];
     p.obs_inv_stay = (float)(1.0 / (double)q.stay_steps[1]);
     p.obs_inv_cap = (float)(1.0 / (double)q.cap_kwh[1]);
     p.obs_inv_days = (float)(1.0 / (double)n_days);

@@ -191,9 +191,9 @@ __device__ void issue(const PolicyArgs& a, unsigned char* A, unsigned char* ring
                     if (is_bad(S)) continue;
                     const int nks = (L == 0 && k == chunks - 1) ? a.ks1_last : 4;
                     unsigned char* bst = ring + slot * kStageBytes;
-                    for (int j = 0; j < nks; ++j)
+                    for (int j = 0; j < nks; ++j)          // onto the bias the workers placed in TMEM
                         mma_bf16(tmem + (uint32_t)(p * kStageRows), sdesc_sw128(A + k * kChunkBytes + j * 32),
-                                 sdesc_sw128(bst + j * 32), id, (k | j) != 0);
+                                 sdesc_sw128(bst + j * 32), id, true);
                     if (CS == 1) mma_commit(&S.empty[slot]);
                     else mma_commit_multicast(&S.empty[slot], (uint16_t)((1u << CS) - 1u));
                 }
@@ -205,9 +205,42 @@ __device__ void issue(const PolicyArgs& a, unsigned char* A, unsigned char* ring
     if (!mbar_wait(&S.fin, 0)) atomicOr(a.err, kErrPolicyWait);
 }
 
-// ---- epilogue of layers 1 and 2: bias, ReLU, BF16 into A --------------------
-__device__ __forceinline__ void hidden_epilogue(uint32_t taddr, const float* __restrict__ bias, uint32_t abase, int row,
-                                                int col0)
+// ---- bias rows into TMEM: every accumulator of a layer starts at its bias --
+// 32 columns [c0, c0 + 32) of the warp's 32 lanes := bias[c0 .. c0 + 31]
+__device__ __forceinline__ void bias_to_tmem(uint32_t taddr, const float* bias)
+{
+    uint32_t v[32];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const float4 b = reinterpret_cast<const float4*>(bias)[j];
+        v[4 * j] = __float_as_uint(b.x);
+        v[4 * j + 1] = __float_as_uint(b.y);
+        v[4 * j + 2] = __float_as_uint(b.z);
+        v[4 * j + 3] = __float_as_uint(b.w);
+    }
+    tmem_st32(taddr, v);
+}
+
+// Bias of layer L (0, 1: 256 columns; 2: n_out_pad columns) into the
+// accumulator columns this worker warp may write: half h takes hidden
+// columns 128h .. 128h+127 and, for layer 3, 48 of columns 256 .. 351 as
+// well (columns it does not read in the layer-2 epilogue).
+__device__ __forceinline__ void layer_bias(const PolicyArgs& a, const float* bias_s, uint32_t tl, int L, int h)
+{
+    const float* b = bias_s + kPolicyHidden * L;
+    const int n = L < 2 ? kPolicyHidden : a.n_out_pad;
+#pragma unroll 1
+    for (int c = 128 * h; c < 128 * h + 128; c += 32)
+        if (c < n) bias_to_tmem(tl + (uint32_t)c, b + c);
+    if (L == 2)
+#pragma unroll 1
+        for (int c = 256 + 64 * h; c < 256 + 64 * h + 64; c += 32)
+            if (c < n) bias_to_tmem(tl + (uint32_t)c, b + c);
+    tmem_wait_st();
+}
+
+// ---- epilogue of layers 1 and 2: ReLU, BF16 into A ------------------------
+__device__ __forceinline__ void hidden_epilogue(uint32_t taddr, uint32_t abase, int row, int col0)
 {
 #pragma unroll 1
     for (int blk = 0; blk < 4; ++blk) {
@@ -217,12 +250,8 @@ __device__ __forceinline__ void hidden_epilogue(uint32_t taddr, const float* __r
         tmem_wait_ld();
         uint32_t q[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const float2 bb = __ldg(reinterpret_cast<const float2*>(bias + c + 2 * j));
-            const float x0 = fmaxf(__uint_as_float(v[2 * j]) + bb.x, 0.f);
-            const float x1 = fmaxf(__uint_as_float(v[2 * j + 1]) + bb.y, 0.f);
-            q[j] = pack_bf16x2(x0, x1);
-        }
+        for (int j = 0; j < 16; ++j)
+            q[j] = pack_bf16x2(fmaxf(__uint_as_float(v[2 * j]), 0.f), fmaxf(__uint_as_float(v[2 * j + 1]), 0.f));
         const int unit0 = (c & 63) >> 3;
         const uint32_t rbase = abase + (uint32_t)((c >> 6) * kChunkBytes + row * 128);
 #pragma unroll
@@ -237,8 +266,8 @@ __device__ __forceinline__ void hidden_epilogue(uint32_t taddr, const float* __r
 // level = #{j < L-1 : e_0 + .. + e_j <= u S}, e_j = exp(l_j - max l),
 // S = sum e_j, u from word c % 4 of the policy Philox block (env, step, c / 4).
 template <int LT>
-__device__ __forceinline__ uint32_t sample4(const uint32_t (&v)[48], const float* __restrict__ b3, int c0, int n_ports,
-                                           int n_levels, uint4 words, float* logits_out)
+__device__ __forceinline__ uint32_t sample4(const uint32_t (&v)[48], int c0, int n_ports, int n_levels, uint4 words,
+                                           float* logits_out)
 {
     const int L = LT ? LT : n_levels;
     uint32_t packed = 0;
@@ -250,7 +279,7 @@ __device__ __forceinline__ uint32_t sample4(const uint32_t (&v)[48], const float
         float m = -INFINITY;
 #pragma unroll
         for (int j = 0; j < kPolicyGroup; ++j) {
-            l[j] = j < L ? __uint_as_float(v[L * ci + j]) + __ldg(b3 + L * c + j) : 0.f;
+            l[j] = j < L ? __uint_as_float(v[L * ci + j]) : 0.f;
             if (j < L) m = fmaxf(m, l[j]);
         }
         float e[kPolicyGroup], S = 0.f;
@@ -284,7 +313,10 @@ __device__ __forceinline__ void sample_row(const PolicyArgs& a, uint32_t tl, int
                                            uint32_t (&packed)[4])
 {
     const int L = LT ? LT : a.n_levels;
-    const float* b3 = a.bias + 2 * kPolicyHidden;
+    uint4 words[4];                                    // the four Philox blocks of chargers 16h .. 16h+15
+#pragma unroll
+    for (int blk = 0; blk < 4; ++blk)
+        words[blk] = philox4x32_10(make_uint4((uint32_t)env, g, (uint32_t)(4 * h + blk), kPurposePolicy), k0, k1);
 #pragma unroll 1
     for (int blk = 0; blk < 4; ++blk) {
         packed[blk] = 0;
@@ -295,8 +327,8 @@ __device__ __forceinline__ void sample_row(const PolicyArgs& a, uint32_t tl, int
         tmem_ld16(tl + (uint32_t)(L * c0 + 32), v + 32);
         tmem_wait_ld();
         if (!live) continue;
-        const uint4 words = philox4x32_10(make_uint4((uint32_t)env, g, (uint32_t)(c0 >> 2), kPurposePolicy), k0, k1);
-        packed[blk] = sample4<LT>(v, b3, c0, a.n_ports, a.n_levels, words,
+        const uint4 w = blk == 0 ? words[0] : blk == 1 ? words[1] : blk == 2 ? words[2] : words[3];
+        packed[blk] = sample4<LT>(v, c0, a.n_ports, a.n_levels, w,
                                   logits_env ? logits_env + (long long)c0 * L : nullptr);
     }
 }
@@ -337,7 +369,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_policy(const __grid_constant__ 
     unsigned char* A = aligned_smem(smem_raw);
     unsigned char* ring = A + kActBytes;
     __shared__ Sync S;
+    __shared__ __align__(16) float bias_s[2 * kPolicyHidden + kPolicyMaxPorts * kPolicyGroup];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int j = threadIdx.x; j < 2 * kPolicyHidden + a.n_out_pad; j += blockDim.x) bias_s[j] = a.bias[j];
     if (threadIdx.x == 0) init_sync(S, kPolStages, 1);
     if (warp == 1) tmem_alloc(&S.tmem, kTmemCols);
     fence_before();
@@ -390,6 +424,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_policy(const __grid_constant__ 
                     }
                 }
             }
+            named_sync(kBarWorkers, kWorkers);       // the previous tile's sampling has left TMEM
+            layer_bias(a, bias_s, tl, 0, h);
             worker_arrive(&S.xrdy);
 
             const long long env = (long long)tile * kM + row;
@@ -405,7 +441,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_policy(const __grid_constant__ 
             for (int L = 0; L < 2; ++L) {
                 wait_sync(&S.acc, (3 * i + L) & 1, S, a.err);
                 fence_after();
-                hidden_epilogue(tl + (uint32_t)(128 * h), a.bias + kPolicyHidden * L, abase, row, 128 * h);
+                hidden_epilogue(tl + (uint32_t)(128 * h), abase, row, 128 * h);
+                layer_bias(a, bias_s, tl, L + 1, h);
                 worker_arrive(&S.hrdy);
             }
             // (3) logits -> levels
@@ -875,20 +912,20 @@ __device__ __forceinline__ void owner_observe(const Owner& o, const RolloutArgs&
                 const long long eb = e0 + 16 * half_rows;
                 const int n_rows = (int)min(16LL, max(0LL, (long long)R.pol.E - eb));
                 float* dst0 = R.obs_out + ((long long)it * R.pol.E + eb) * D + f0;
+                // two rows per pass, 16 lanes per row (a row's run is at most 14 float4)
+                const int cl = lane & 15;
                 if ((D & 3) == 0) {
-                    const int per = n_f >> 2;
-                    for (int x = lane; x < n_rows * per; x += 32) {
-                        const int r = x / per, c4 = x - r * per;
-                        *reinterpret_cast<float4*>(dst0 + (long long)r * D + 4 * c4) =
-                            *reinterpret_cast<const float4*>(stage + r * kStageRow + 4 * c4);
-                    }
+                    if (4 * cl < n_f)
+#pragma unroll 4
+                        for (int r = lane >> 4; r < n_rows; r += 2)
+                            *reinterpret_cast<float4*>(dst0 + (long long)r * D + 4 * cl) =
+                                *reinterpret_cast<const float4*>(stage + r * kStageRow + 4 * cl);
                 } else {
-                    const int per = n_f >> 1;
-                    for (int x = lane; x < n_rows * per; x += 32) {
-                        const int r = x / per, c2 = x - r * per;
-                        *reinterpret_cast<float2*>(dst0 + (long long)r * D + 2 * c2) =
-                            *reinterpret_cast<const float2*>(stage + r * kStageRow + 2 * c2);
-                    }
+#pragma unroll 4
+                    for (int r = lane >> 4; r < n_rows; r += 2)
+                        for (int c2 = cl; 2 * c2 < n_f; c2 += 16)
+                            *reinterpret_cast<float2*>(dst0 + (long long)r * D + 2 * c2) =
+                                *reinterpret_cast<const float2*>(stage + r * kStageRow + 2 * c2);
                 }
                 __syncwarp();
             }
@@ -949,8 +986,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_rollout(const __grid_constant__
     unsigned char* ring = A + kActBytes;
     RollSmem& rs = *reinterpret_cast<RollSmem*>(ring + kRollStages * kStageBytes);
     __shared__ Sync S;
+    __shared__ __align__(16) float bias_s[2 * kPolicyHidden + kPolicyMaxPorts * kPolicyGroup];
     const PolicyArgs& a = R.pol;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int j = threadIdx.x; j < 2 * kPolicyHidden + a.n_out_pad; j += blockDim.x) bias_s[j] = a.bias[j];
     if (threadIdx.x == 0) init_sync(S, kRollStages, kRollCluster);
     if (warp == 1) tmem_alloc(&S.tmem, kTmemCols);
     fence_before();
@@ -976,12 +1015,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_rollout(const __grid_constant__
         owner_observe(o, R, 0, q, lane, tl, abase, rs.u.stage[ew]);
         for (int it = 0; it < R.T; ++it) {
             fence_before();
-            named_sync(kBarWorkers, kWorkers);
+            named_sync(kBarWorkers, kWorkers);     // every observation (and its parked power) written
+            fence_after();
+            layer_bias(a, bias_s, tl, 0, h);
             worker_arrive(&S.xrdy);
             for (int L = 0; L < 2; ++L) {
                 wait_sync(&S.acc, (3 * it + L) & 1, S, a.err);
                 fence_after();
-                hidden_epilogue(tl + (uint32_t)(128 * h), a.bias + kPolicyHidden * L, abase, row, 128 * h);
+                hidden_epilogue(tl + (uint32_t)(128 * h), abase, row, 128 * h);
+                layer_bias(a, bias_s, tl, L + 1, h);
                 worker_arrive(&S.hrdy);
             }
             wait_sync(&S.acc, (3 * it + 2) & 1, S, a.err);
@@ -1014,7 +1056,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_rollout(const __grid_constant__
 constexpr int kPolicySmem = 1024 + kActBytes + kPolStages * kStageBytes;
 constexpr int kRolloutSmem = 1024 + kActBytes + kRollStages * kStageBytes + (int)sizeof(RollSmem);
 static_assert(kPolicySmem <= 227 * 1024 - 256, "k_policy shared memory");
-static_assert(kRolloutSmem <= 227 * 1024 - 256, "k_rollout shared memory");
+static_assert(kRolloutSmem + (2 * kPolicyHidden + kPolicyMaxPorts * kPolicyGroup) * 4 <= 227 * 1024 - 256,
+              "k_rollout shared memory");
 
 }  // namespace
 
