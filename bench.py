@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-policy", action="store_true", help="skip the on-device policy rollout leg")
     ap.add_argument("--policy-steps", type=int, default=128, help="rollout buffer length of the policy leg")
+    ap.add_argument("--policy-only", action="store_true",
+                    help="time only the policy rollout leg and print its JSON object (profiling aid)")
     ap.add_argument("--serve-envs", type=int, default=1 << 20, help="resident stations of the serving leg")
     ap.add_argument("--serve-actors", type=int, default=4096)
     ap.add_argument("--serve-think-us", type=float, default=0.0,
@@ -179,21 +181,45 @@ def policy_bytes_per_env_step(D, N):
     return 4.0 * D + N + 4.0 + 1.0
 
 
-def recorded_traffic(n_envs, K, W):
-    """DRAM bytes per fused launch from the committed ncu record, if the
-    kernel sources and the launch shape are those the counters were taken on."""
+def _recorded(name, sources, **want):
+    """A per-launch DRAM byte count from a committed ncu record (profiles/
+    <name>), if the kernel sources and the launch parameters are those the
+    counters were taken on; else None."""
     import hashlib
     try:
-        rec = dict(l.split() for l in open(os.path.join(ROOT, "profiles", "k_step_fused_traffic.txt"))
+        rec = dict(l.split() for l in open(os.path.join(ROOT, "profiles", name))
                    if l.strip() and not l.startswith("#"))
-        src = b"".join(open(os.path.join(ROOT, "paper_2507_01522_b300", "csrc", f), "rb").read()
-                       for f in ("step_fused.cu", "chx_device.cuh"))
-        if (hashlib.sha256(src).hexdigest()[:16] == rec["source_sha256_16"] and int(rec["n_envs"]) == n_envs
-                and int(rec["steps_per_launch"]) == K and int(rec["warps_per_block"]) == W):
-            return int(rec["dram_bytes_per_launch"])
+        src = b"".join(open(os.path.join(ROOT, "paper_2507_01522_b300", "csrc", f), "rb").read() for f in sources)
+        if hashlib.sha256(src).hexdigest()[:16] != rec["source_sha256_16"]:
+            return None
+        if any(int(rec[k]) != int(v) for k, v in want.items()):
+            return None
+        return int(rec["dram_bytes_per_launch"])
     except Exception:
-        pass
-    return None
+        return None
+
+
+def recorded_traffic(n_envs, K, W):
+    """DRAM bytes per fused step launch (k_step_fused record)."""
+    return _recorded("k_step_fused_traffic.txt", ("step_fused.cu", "chx_device.cuh"), n_envs=n_envs,
+                     steps_per_launch=K, warps_per_block=W)
+
+
+ROLLOUT_SOURCES = ("policy.cu", "chx_tc.cuh", "chx_device.cuh", "chx_kernels.h")
+
+
+def recorded_rollout_traffic(n_envs, T):
+    """DRAM bytes per fused rollout launch (k_rollout record, scaled from the
+    captured rollout length: every step writes the same buffers)."""
+    try:
+        rec = dict(l.split() for l in open(os.path.join(ROOT, "profiles", "k_rollout_traffic.txt"))
+                   if l.strip() and not l.startswith("#"))
+        per = _recorded("k_rollout_traffic.txt", ROLLOUT_SOURCES, n_envs=n_envs)
+        if per is None:
+            return None
+        return int(per * T / int(rec["rollout_steps"]))
+    except Exception:
+        return None
 
 
 def cpu_baseline(w, n_sample_envs, steps):
@@ -460,7 +486,8 @@ def run_policy_rollout(args, rank, ws, dev, timed, pk):
         launches += n_launch * args.steps
         out[name] = {"value": E * T * args.steps * ws / tot, "ms_per_rollout": ms_roll, "launches_per_rollout": n_launch,
                      "roofline": {"bound": "tensor", "achieved": tf, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
-                                  "frac": tf / pk["bf16_tflops"], "traffic": None,
+                                  "frac": tf / pk["bf16_tflops"],
+                                  "traffic": recorded_rollout_traffic(E, T) if name == "fused" else None,
                                   "kernel": "k_rollout" if name == "fused" else "k_policy + k_step_fused",
                                   "flops_per_rollout": flops,
                                   "hbm_output_gbs": gbs, "hbm_output_frac": gbs / pk["hbm_gbs"]}}
@@ -516,10 +543,39 @@ def run_serving(args, rank):
             "ticks": st["n_ticks"], "scans": st["n_scans"]}
 
 
+def run_policy_only(args):
+    import torch
+    rank, ws, local = dist_init()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def timed(fn, n):
+        times = []
+        for _ in range(n):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            times.append((e0, e1))
+        torch.cuda.synchronize()
+        return [a.elapsed_time(c) for a, c in times]
+
+    pk, _ = peaks()
+    out = run_policy_rollout(args, rank, ws, dev, timed, pk)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.policy_only:
+        run_policy_only(args)
     else:
         run_b300(args)
 
