@@ -78,6 +78,23 @@ typedef struct chx_env_params {
     float soc0[2];           /* arrival SoC ~ U(lo, hi)                       */
     int32_t stay_steps[2];   /* stay ~ U{lo..hi} steps, 1 <= lo <= hi <= 255  */
     float rbar_kw[2][2];     /* car maximum rate ~ U(lo, hi) per charger type */
+    /* Vehicle-to-grid mode (App. A.1 "Endogenous state space", A.2 "Apply
+     * Actions", A.3): v2g = 1 makes the action levels signed -- level k in
+     * 0..n_levels-1 (n_levels odd) requests (k - h)/h of the charger maximum,
+     * h = (n_levels-1)/2, negative = discharge along the charging curve
+     * flipped at SoC = 0.5 -- and adds one station battery per station
+     * (capacity, maximum rate, taper point, SoC at each episode start) with
+     * its own action level after the chargers', at the root of the station's
+     * tree.  Energy sold back to the grid earns sell_grid_ratio x the buy
+     * price; discharged energy (cars and battery) costs alpha_degrad per
+     * kWh.  v2g = 0 ignores the remaining fields. */
+    int32_t v2g;
+    float sell_grid_ratio;
+    float alpha_degrad;
+    float batt_cap_kwh;
+    float batt_rate_kw;
+    float batt_tau;
+    float batt_soc0;
 } chx_env_params;
 
 /* A batch of stations, CSR.  Groups of a station are contiguous charger

@@ -42,6 +42,9 @@ class _Params(C.Structure):
         ("cap_kwh", C.c_double * 2), ("soc0", C.c_double * 2),
         ("stay_steps", C.c_int32 * 2),
         ("rbar_kw", (C.c_double * 2) * 2),
+        ("v2g", C.c_int32), ("sell_grid_ratio", C.c_double), ("alpha_degrad", C.c_double),
+        ("batt_cap_kwh", C.c_double), ("batt_rate_kw", C.c_double), ("batt_tau", C.c_double),
+        ("batt_soc0", C.c_double),
     ]
 
 
@@ -71,6 +74,11 @@ def lib():
         L.orc_taper.restype = C.c_double
         L.orc_taper.argtypes = [C.c_double, C.c_double, C.c_double]
         L.orc_policy_uniforms.argtypes = [vp, i32, vp]
+        L.orc_obs_env_features.restype = i32
+        L.orc_obs_env_features.argtypes = [vp]
+        L.orc_get_battery.argtypes = [vp, vp, vp]
+        L.orc_set_battery.argtypes = [vp, vp, vp]
+        L.orc_get_info_v2g.argtypes = [vp, vp, vp, vp, vp]
         L.orc_random_action.restype = i32
         L.orc_random_action.argtypes = [vp, i32, C.c_uint32, i32]
         _lib = L
@@ -109,6 +117,9 @@ def params_struct(p) -> _Params:
         s.cap_kwh[k] = p.cap_kwh[k]; s.soc0[k] = p.soc0[k]; s.stay_steps[k] = int(p.stay_steps[k])
     for k in range(2):
         s.rbar_kw[0][k] = p.rbar_ac_kw[k]; s.rbar_kw[1][k] = p.rbar_dc_kw[k]
+    s.v2g = int(p.v2g); s.sell_grid_ratio = p.sell_grid_ratio; s.alpha_degrad = p.alpha_degrad
+    s.batt_cap_kwh = p.batt_cap_kwh; s.batt_rate_kw = p.batt_rate_kw; s.batt_tau = p.batt_tau
+    s.batt_soc0 = p.batt_soc0
     return s
 
 
@@ -159,10 +170,29 @@ class Oracle:
         lib().orc_step(self.h, _ptr(a), lda, _ptr(r), _ptr(d))
         return r, d
 
+    @property
+    def obs_env_features(self) -> int:
+        return int(lib().orc_obs_env_features(self.h))
+
     def observe(self) -> np.ndarray:
-        o = np.zeros(8 * self.E + 6 * self.P, np.float64)
+        o = np.zeros(self.obs_env_features * self.E + 6 * self.P, np.float64)
         lib().orc_observe(self.h, _ptr(o))
         return o
+
+    def battery(self) -> dict:
+        d = dict(soc=np.zeros(self.E), p=np.zeros(self.E))
+        lib().orc_get_battery(self.h, _ptr(d["soc"]), _ptr(d["p"]))
+        return d
+
+    def set_battery(self, soc, p):
+        a = np.ascontiguousarray(soc, dtype=np.float64)
+        b = np.ascontiguousarray(p, dtype=np.float64)
+        lib().orc_set_battery(self.h, _ptr(a), _ptr(b))
+
+    def info_v2g(self) -> dict:
+        d = dict(e_to=np.zeros(self.E), e_b=np.zeros(self.E), degrad=np.zeros(self.E), e_grid_net=np.zeros(self.E))
+        lib().orc_get_info_v2g(self.h, *[_ptr(d[k]) for k in ("e_to", "e_b", "degrad", "e_grid_net")])
+        return d
 
     def state(self) -> dict:
         P, E = self.P, self.E

@@ -50,6 +50,12 @@ typedef struct orc_params {
     double soc0[2];        /* U(lo, hi) arrival SoC                             */
     int32_t stay_steps[2]; /* inclusive integer range of the stay, in steps     */
     double rbar_kw[2][2];  /* [type][lo, hi] car maximum rate per charger type  */
+    /* vehicle-to-grid mode: signed levels, station battery, sell-back price,
+     * degradation penalty (see orc_step) */
+    int32_t v2g;
+    double sell_grid_ratio;
+    double alpha_degrad;
+    double batt_cap_kwh, batt_rate_kw, batt_tau, batt_soc0;
 } orc_params;
 
 typedef struct orc {
@@ -72,11 +78,14 @@ typedef struct orc {
     uint32_t *stream;                      /* Philox stream id (default: index) */
     double *ep_ret, *last_ret;
     uint32_t *n_episodes;
+    /* station battery (V2G mode): SoC and last applied power */
+    double *bsoc, *bp;
     /* per-env running statistics */
     double *st_arrived, *st_rejected, *st_missing, *st_charged;
     /* per-env record of the last step (for invariant tests) */
     int32_t *inf_M, *inf_admitted, *inf_departed;
     double *inf_csat, *inf_ccon, *inf_enet, *inf_egrid, *inf_price, *inf_req_sum;
+    double *inf_eto, *inf_eb, *inf_degrad, *inf_egrid_net;   /* V2G terms of the last step */
     double *scratch_p;                     /* per-port power within one step    */
     uint8_t *scratch_leave;                /* port's stay ended in this step    */
 } orc;
@@ -165,6 +174,8 @@ static void clear_port(orc *o, int64_t i)
 static void start_episode(orc *o, int32_t e, uint32_t c1, uint32_t c2)
 {
     for (int64_t i = o->port_off[e]; i < o->port_off[e + 1]; ++i) { clear_port(o, i); o->pw[i] = 0.0; }
+    o->bsoc[e] = o->p.v2g ? o->p.batt_soc0 : 0.0;
+    o->bp[e] = 0.0;
     o->tod[e] = 0;
     uint32_t w[4];
     draw(o, e, c1, c2, ORC_PURPOSE_DAY, w);
@@ -271,6 +282,12 @@ orc *orc_create(const orc_params *prm, int32_t E,
     o->inf_egrid = (double *)xcalloc((size_t)E, sizeof(double));
     o->inf_price = (double *)xcalloc((size_t)E, sizeof(double));
     o->inf_req_sum = (double *)xcalloc((size_t)E, sizeof(double));
+    o->inf_eto = (double *)xcalloc((size_t)E, sizeof(double));
+    o->inf_eb = (double *)xcalloc((size_t)E, sizeof(double));
+    o->inf_degrad = (double *)xcalloc((size_t)E, sizeof(double));
+    o->inf_egrid_net = (double *)xcalloc((size_t)E, sizeof(double));
+    o->bsoc = (double *)xcalloc((size_t)E, sizeof(double));
+    o->bp = (double *)xcalloc((size_t)E, sizeof(double));
     orc_reset(o, NULL, 0, seed);
     return o;
 }
@@ -284,7 +301,7 @@ void orc_destroy(orc *o)
                     o->day, o->gstep, o->ncar, o->key0, o->key1, o->stream, o->ep_ret, o->last_ret, o->n_episodes,
                     o->st_arrived, o->st_rejected, o->st_missing, o->st_charged, o->inf_M, o->inf_admitted,
                     o->inf_departed, o->inf_csat, o->inf_ccon, o->inf_enet, o->inf_egrid, o->inf_price,
-                    o->inf_req_sum};
+                    o->inf_req_sum, o->inf_eto, o->inf_eb, o->inf_degrad, o->inf_egrid_net, o->bsoc, o->bp};
     for (size_t k = 0; k < sizeof(ptrs) / sizeof(ptrs[0]); ++k) free(ptrs[k]);
     free(o);
 }
@@ -324,11 +341,48 @@ void orc_policy_uniforms(const orc *o, int32_t n_ports, double *u)
 /* One transition of every env, Appendix A.2 then A.3.                      */
 /* actions: int8 level per port in batch port order with stride `lda`, or   */
 /* NULL for Philox-drawn uniform levels.  reward[E] and done[E] are outputs.*/
+/* In V2G mode (p.v2g) each env has one more action, its battery's level,   */
+/* after its ports: port i of env e at (i + e) * lda, the battery of env e  */
+/* at (port_off[e+1] + e) * lda; a drawn battery level uses local port      */
+/* index n_ports.                                                           */
 /* ------------------------------------------------------------------------ */
+
+/* signed V2G request of level k: (k - h)/h of the maximum, h = (L-1)/2 */
+static double v2g_request(const orc *o, int32_t k, double pmax)
+{
+    const int32_t h = (o->p.n_levels - 1) / 2;
+    return (double)(k - h) / (double)h * pmax;
+}
+
+/* V2G clip (A.2 "Apply Actions", negative branch): charge as in the
+ * charge-only mode; discharge limited by the request, the car's discharging
+ * rate (the charging curve flipped at SoC = 0.5: r_hat(1 - SoC)), the port
+ * maximum and SoC >= 0.  Pinned by the closed-form discharge trajectory and
+ * by the reduction to the charge-only mode. */
+static double v2g_clip(double preq, double soc, double erem, double cap, double rbar, double tau, double pmax,
+                       double dt)
+{
+    if (preq >= 0.0) {
+        double P = preq, rhat = orc_taper(soc, rbar, tau);
+        double soc_cap = (1.0 - soc) * cap / dt, dem_cap = erem / dt;
+        if (rhat < P) P = rhat;
+        if (pmax < P) P = pmax;
+        if (soc_cap < P) P = soc_cap;
+        if (dem_cap < P) P = dem_cap;
+        return P < 0.0 ? 0.0 : P;
+    }
+    double D = -preq, rdis = orc_taper(1.0 - soc, rbar, tau), soc_cap = soc * cap / dt;
+    if (rdis < D) D = rdis;
+    if (pmax < D) D = pmax;
+    if (soc_cap < D) D = soc_cap;
+    return D < 0.0 ? 0.0 : -D;
+}
+
 void orc_step(orc *o, const int8_t *actions, int64_t lda, double *reward, uint8_t *done)
 {
     const orc_params *p = &o->p;
     const double dt = p->dt_h;
+    const int v2g = p->v2g != 0;
     for (int32_t e = 0; e < o->E; ++e) {
         const int64_t p0 = o->port_off[e], p1 = o->port_off[e + 1];
         const uint32_t g = o->gstep[e];
@@ -337,27 +391,42 @@ void orc_step(orc *o, const int8_t *actions, int64_t lda, double *reward, uint8_
         /* (i) Apply Actions: requested level clipped by the port capacity and
          * by the car's current maximum rate r_hat(SoC); the two extra caps
          * keep SoC <= 1 and the remaining demand >= 0 (SoC in [0,1] and
-         * Delta E_remain >= 0 are the state domains of the "State summary"). */
+         * Delta E_remain >= 0 are the state domains of the "State summary").
+         * V2G: signed levels (v2g_clip) and the station battery, a leaf of
+         * the root with its own level, rate curve and SoC in [0, 1]. */
         double req_sum = 0.0;
         for (int64_t i = p0; i < p1; ++i) {
             double P = 0.0;
             if (o->trem[i] > 0) {
-                int32_t k = actions ? (int32_t)actions[i * lda] : orc_random_action(o, e, g, (int32_t)(i - p0));
+                int32_t k = actions ? (int32_t)actions[(i + (v2g ? e : 0)) * lda]
+                                    : orc_random_action(o, e, g, (int32_t)(i - p0));
                 int ty = o->port_type[i];
                 double pmax = p->p_max_kw[ty];
-                double preq = (double)k / (double)(p->n_levels - 1) * pmax;
-                double rhat = orc_taper(o->soc[i], o->rbar[i], p->tau);
-                double soc_cap = (1.0 - o->soc[i]) * o->cap[i] / dt;
-                double dem_cap = o->erem[i] / dt;
-                P = preq;
-                if (rhat < P) P = rhat;
-                if (pmax < P) P = pmax;
-                if (soc_cap < P) P = soc_cap;
-                if (dem_cap < P) P = dem_cap;
-                if (P < 0.0) P = 0.0;
+                if (v2g) {
+                    P = v2g_clip(v2g_request(o, k, pmax), o->soc[i], o->erem[i], o->cap[i], o->rbar[i], p->tau,
+                                 pmax, dt);
+                } else {
+                    double preq = (double)k / (double)(p->n_levels - 1) * pmax;
+                    double rhat = orc_taper(o->soc[i], o->rbar[i], p->tau);
+                    double soc_cap = (1.0 - o->soc[i]) * o->cap[i] / dt;
+                    double dem_cap = o->erem[i] / dt;
+                    P = preq;
+                    if (rhat < P) P = rhat;
+                    if (pmax < P) P = pmax;
+                    if (soc_cap < P) P = soc_cap;
+                    if (dem_cap < P) P = dem_cap;
+                    if (P < 0.0) P = 0.0;
+                }
             }
             o->scratch_p[i] = P;
             req_sum += P;
+        }
+        double Pb = 0.0;
+        if (v2g) {
+            int32_t kb = actions ? (int32_t)actions[(p1 + e) * lda] : orc_random_action(o, e, g, o->n_ports[e]);
+            /* the battery never leaves: its remaining demand never binds */
+            Pb = v2g_clip(v2g_request(o, kb, p->batt_rate_kw), o->bsoc[e], 1e300, p->batt_cap_kwh, p->batt_rate_kw,
+                          p->batt_tau, p->batt_rate_kw, dt);
         }
 
         /* Architecture constraint, Eq. (ArchConst): for every subtree H,
@@ -365,46 +434,63 @@ void orc_step(orc *o, const int8_t *actions, int64_t lda, double *reward, uint8_
          * resolved by proportional rescaling of the leaves, bottom-up: the
          * group nodes first, then the root (grid connection).  The
          * constraint-violation penalty (Appendix A.3) is measured on the
-         * requested (pre-rescale) power. */
+         * requested (pre-rescale) power.  V2G: the limit binds the net flow
+         * in either direction (|sum| / eta_H <= I_H), and the battery is a
+         * leaf of the root. */
         double c_con = 0.0;
         for (int64_t gi = o->group_off[e]; gi < o->group_off[e + 1]; ++gi) {
             double s = 0.0;
             for (int64_t i = p0; i < p1; ++i)
                 if (o->port_group[i] == gi) s += o->scratch_p[i];
-            double over = s / o->group_eta[gi] - o->group_limit[gi];
+            double mag = v2g ? fabs(s) : s;
+            double over = mag / o->group_eta[gi] - o->group_limit[gi];
             if (over > c_con) c_con = over;
             if (over > 0.0) {
-                double scale = o->group_eta[gi] * o->group_limit[gi] / s;
+                double scale = o->group_eta[gi] * o->group_limit[gi] / mag;
                 for (int64_t i = p0; i < p1; ++i)
                     if (o->port_group[i] == gi) o->scratch_p[i] *= scale;
             }
         }
         {
-            double root_over = req_sum / o->grid_eta[e] - o->grid_limit[e];
+            double req_root = req_sum + Pb;
+            double root_over = (v2g ? fabs(req_root) : req_root) / o->grid_eta[e] - o->grid_limit[e];
             if (root_over > c_con) c_con = root_over;
-            double s = 0.0;
+            double s = Pb;
             for (int64_t i = p0; i < p1; ++i) s += o->scratch_p[i];
-            if (s / o->grid_eta[e] > o->grid_limit[e]) {
-                double scale = o->grid_eta[e] * o->grid_limit[e] / s;
+            double mag = v2g ? fabs(s) : s;
+            if (mag / o->grid_eta[e] > o->grid_limit[e]) {
+                double scale = o->grid_eta[e] * o->grid_limit[e] / mag;
                 for (int64_t i = p0; i < p1; ++i) o->scratch_p[i] *= scale;
+                Pb *= scale;
             }
         }
 
         /* (ii) Charge Stationed Cars at constant power over dt; energy bought
-         * from the grid includes the port efficiency (Appendix A.3). */
-        double e_net = 0.0, e_grid = 0.0;
+         * from the grid includes the port efficiency (Appendix A.3).  V2G:
+         * energy pushed into the grid by discharging cars loses the port
+         * efficiency on the way (Eq. Profit1), the battery's energy counts at
+         * face value, and SoC stays in [0, 1]. */
+        double e_net = 0.0, e_grid = 0.0, e_to = 0.0;
         for (int64_t i = p0; i < p1; ++i) {
             double P = o->scratch_p[i];
             o->pw[i] = P;
             if (o->trem[i] > 0) {
                 double dE = P * dt;
                 double s = o->soc[i] + dE / o->cap[i];
-                o->soc[i] = s > 1.0 ? 1.0 : s;
+                o->soc[i] = s > 1.0 ? 1.0 : (s < 0.0 ? 0.0 : s);
                 double r = o->erem[i] - dE;
                 o->erem[i] = r < 0.0 ? 0.0 : r;
                 e_net += dE;
-                e_grid += dE / p->eta_port[o->port_type[i]];
+                if (dE >= 0.0) e_grid += dE / p->eta_port[o->port_type[i]];
+                else e_to += dE * p->eta_port[o->port_type[i]];
             }
+        }
+        double e_b = 0.0;
+        if (v2g) {
+            e_b = Pb * dt;
+            double s = o->bsoc[e] + e_b / p->batt_cap_kwh;
+            o->bsoc[e] = s > 1.0 ? 1.0 : (s < 0.0 ? 0.0 : s);
+            o->bp[e] = Pb;
         }
 
         /* time moves on: every stationed car has one step less to stay */
@@ -464,20 +550,28 @@ void orc_step(orc *o, const int8_t *actions, int64_t lda, double *reward, uint8_
             j += 1;
         }
 
-        /* Reward (Appendix A.3): profit with the two-case grid price (no
-         * discharge and no station battery here, so Delta E_grid,net is the
-         * energy bought), minus the weighted penalties. */
+        /* Reward (Appendix A.3): profit with the two-case grid price, minus
+         * the weighted penalties.  Delta E_grid,net = energy bought for the
+         * cars + energy pushed into the grid by discharging cars (<= 0) +
+         * the battery's energy; when it is <= 0 the station sells to the
+         * grid at p_sell,grid (= sell_grid_ratio x the buy price in V2G
+         * mode; without V2G the case cannot occur and p_sell,grid = p_buy).
+         * Battery degradation: discharged energy of the battery and of the
+         * cars (c_degrad,battery + c_degrad,cars). */
         double price = o->price[(size_t)o->day[e] * (size_t)p->ep_len + (size_t)t];
-        double e_grid_net = e_grid;
+        double e_grid_net = e_grid + e_to + e_b;
         double profit;
         if (e_grid_net > 0.0) profit = p->p_sell * e_net - price * e_grid_net - p->c_fixed;
-        else profit = p->p_sell * e_net - price * e_grid_net - p->c_fixed;   /* p_sell,grid = p_buy */
+        else profit = p->p_sell * e_net - (v2g ? p->sell_grid_ratio : 1.0) * price * e_grid_net - p->c_fixed;
+        double c_degrad = (e_b < 0.0 ? -e_b : 0.0) - e_to;
         double r = profit - p->alpha_sat * c_sat - p->alpha_decl * (double)c_decl - p->alpha_con * c_con;
+        if (v2g) r -= p->alpha_degrad * c_degrad;
 
         o->ncar[e] += (uint32_t)m;
         o->inf_M[e] = M; o->inf_admitted[e] = m; o->inf_departed[e] = departed;
         o->inf_csat[e] = c_sat; o->inf_ccon[e] = c_con; o->inf_enet[e] = e_net;
         o->inf_egrid[e] = e_grid; o->inf_price[e] = price; o->inf_req_sum[e] = req_sum;
+        o->inf_eto[e] = e_to; o->inf_eb[e] = e_b; o->inf_degrad[e] = c_degrad; o->inf_egrid_net[e] = e_grid_net;
         o->st_arrived[e] += m; o->st_rejected[e] += c_decl;
         o->st_missing[e] += c_sat; o->st_charged[e] += e_net;
 
@@ -486,7 +580,7 @@ void orc_step(orc *o, const int8_t *actions, int64_t lda, double *reward, uint8_
         o->tod[e] = t + 1;
         o->gstep[e] = g + 1u;
         done[e] = 0;
-        /* episode end: record the return and start a new episode at once */
+        /* episode end: record the return and start a new one at once */
         if (o->tod[e] >= p->ep_len) {
             done[e] = 1;
             o->last_ret[e] = o->ep_ret[e];
@@ -499,13 +593,18 @@ void orc_step(orc *o, const int8_t *actions, int64_t lda, double *reward, uint8_
 
 /* Observation (the state of Appendix "State summary" plus time of day, the
  * episode's day and a weekday flag, as the agent sees them).  Layout per env
- * at float offset 8*e + 6*port_off[e]: 8 env features, then 6 per port. */
+ * at float offset F*e + 6*port_off[e]: F env features, then 6 per port;
+ * F = 8, or 10 in V2G mode (+ battery SoC, battery power / its rate, the
+ * battery state s_battery of A.1). */
+int32_t orc_obs_env_features(const orc *o) { return o->p.v2g ? 10 : 8; }
+
 void orc_observe(const orc *o, double *obs)
 {
     const orc_params *p = &o->p;
     const double two_pi = 6.283185307179586476925;
+    const int64_t F = orc_obs_env_features(o);
     for (int32_t e = 0; e < o->E; ++e) {
-        double *ob = obs + 8 * (int64_t)e + 6 * o->port_off[e];
+        double *ob = obs + F * (int64_t)e + 6 * o->port_off[e];
         int32_t t = o->tod[e], n = o->n_ports[e], occ = 0;
         for (int64_t i = o->port_off[e]; i < o->port_off[e + 1]; ++i) occ += o->trem[i] > 0;
         ob[0] = sin(two_pi * t / p->ep_len);
@@ -516,9 +615,13 @@ void orc_observe(const orc *o, double *obs)
         ob[5] = (double)o->day[e] / o->n_days;
         ob[6] = (double)t / p->ep_len;
         ob[7] = (o->day[e] % 7) < 5 ? 1.0 : 0.0;
+        if (p->v2g) {
+            ob[8] = o->bsoc[e];
+            ob[9] = p->batt_rate_kw > 0.0 ? o->bp[e] / p->batt_rate_kw : 0.0;
+        }
         for (int32_t q = 0; q < n; ++q) {
             int64_t i = o->port_off[e] + q;
-            double *op = ob + 8 + 6 * q;
+            double *op = ob + F + 6 * q;
             double pmax = p->p_max_kw[o->port_type[i]];
             int on = o->trem[i] > 0;
             op[0] = on ? 1.0 : 0.0;
@@ -593,6 +696,28 @@ void orc_set_streams(orc *o, const uint32_t *ids, uint64_t seed)
 {
     memcpy(o->stream, ids, (size_t)o->E * sizeof(uint32_t));
     orc_reset(o, NULL, 0, seed);
+}
+
+/* Station battery state per env (V2G mode): SoC and last applied power. */
+void orc_get_battery(const orc *o, double *soc, double *pw)
+{
+    memcpy(soc, o->bsoc, (size_t)o->E * sizeof(double));
+    memcpy(pw, o->bp, (size_t)o->E * sizeof(double));
+}
+void orc_set_battery(orc *o, const double *soc, const double *pw)
+{
+    memcpy(o->bsoc, soc, (size_t)o->E * sizeof(double));
+    memcpy(o->bp, pw, (size_t)o->E * sizeof(double));
+}
+
+/* V2G terms of the last step per env: energy pushed into the grid by cars
+ * (<= 0, after port losses), battery energy, degradation cost basis, and
+ * Delta E_grid,net. */
+void orc_get_info_v2g(const orc *o, double *e_to, double *e_b, double *degrad, double *e_grid_net)
+{
+    size_t E = (size_t)o->E;
+    memcpy(e_to, o->inf_eto, E * sizeof(double)); memcpy(e_b, o->inf_eb, E * sizeof(double));
+    memcpy(degrad, o->inf_degrad, E * sizeof(double)); memcpy(e_grid_net, o->inf_egrid_net, E * sizeof(double));
 }
 
 /* the per-step power of each port (after rescaling) of the last step */

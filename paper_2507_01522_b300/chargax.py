@@ -47,6 +47,9 @@ class _Params(C.Structure):
         ("alpha_sat", C.c_float), ("alpha_decl", C.c_float), ("alpha_con", C.c_float), ("soc_target", C.c_float),
         ("p_max_kw", C.c_float * 2), ("eta_port", C.c_float * 2), ("cap_kwh", C.c_float * 2),
         ("soc0", C.c_float * 2), ("stay_steps", C.c_int32 * 2), ("rbar_kw", (C.c_float * 2) * 2),
+        ("v2g", C.c_int32), ("sell_grid_ratio", C.c_float), ("alpha_degrad", C.c_float),
+        ("batt_cap_kwh", C.c_float), ("batt_rate_kw", C.c_float), ("batt_tau", C.c_float),
+        ("batt_soc0", C.c_float),
     ]
 
 
@@ -168,6 +171,9 @@ def params_struct(p: "_inputs.EnvParams") -> _Params:
         s.p_max_kw[k] = p.p_max_kw[k]; s.eta_port[k] = p.eta_port[k]; s.cap_kwh[k] = p.cap_kwh[k]
         s.soc0[k] = p.soc0[k]; s.stay_steps[k] = int(p.stay_steps[k])
         s.rbar_kw[0][k] = p.rbar_ac_kw[k]; s.rbar_kw[1][k] = p.rbar_dc_kw[k]
+    s.v2g = int(p.v2g); s.sell_grid_ratio = p.sell_grid_ratio; s.alpha_degrad = p.alpha_degrad
+    s.batt_cap_kwh = p.batt_cap_kwh; s.batt_rate_kw = p.batt_rate_kw; s.batt_tau = p.batt_tau
+    s.batt_soc0 = p.batt_soc0
     return s
 
 

@@ -56,6 +56,14 @@ class EnvParams:
     stay_steps: tuple = (12, 96)         # inclusive integer range (1 h .. 8 h)
     rbar_ac_kw: tuple = (7.0, 22.0)
     rbar_dc_kw: tuple = (50.0, 150.0)
+    # vehicle-to-grid mode (signed levels, station battery); off by default
+    v2g: int = 0
+    sell_grid_ratio: float = 0.8         # feed-in price = ratio x buy price
+    alpha_degrad: float = 0.02           # EUR per discharged kWh
+    batt_cap_kwh: float = 200.0
+    batt_rate_kw: float = 60.0
+    batt_tau: float = 0.8
+    batt_soc0: float = 0.5
 
 
 @dataclasses.dataclass
