@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-policy", action="store_true", help="skip the on-device policy rollout leg")
+    ap.add_argument("--no-v2g", action="store_true", help="skip the vehicle-to-grid leg")
     ap.add_argument("--policy-steps", type=int, default=128, help="rollout buffer length of the policy leg")
     ap.add_argument("--policy-only", action="store_true",
                     help="time only the policy rollout leg and print its JSON object (profiling aid)")
@@ -425,6 +426,9 @@ def run_b300(args):
         line["gpu_launches"] += launches_per_step * args.steps
 
     line["clocks"] = ck.summary()
+    if not args.no_v2g:
+        line["v2g"] = run_v2g(args, rank, ws, dev, timed, w, line["value"])
+        line["gpu_launches"] += line["v2g"]["gpu_launches"]
     if not args.no_policy:
         del reward, done, obs
         pol = run_policy_rollout(args, rank, ws, dev, timed, pk)
@@ -440,6 +444,39 @@ def run_b300(args):
     if rank == 0:
         print(json.dumps(line), flush=True)
     barrier(ws)
+
+
+def run_v2g(args, rank, ws, dev, timed, w, charge_only_value):
+    """The same batch in vehicle-to-grid mode (signed levels, discharge
+    taper, station battery, feed-in price, degradation), fused form, same
+    timing protocol as the headline leg."""
+    import torch
+    from paper_2507_01522_b300 import chargax
+    from paper_2507_01522_b300 import inputs as I
+
+    wv = I.v2g_variant(w)
+    T = wv.params.ep_len
+    b = chargax.Batch(wv, seed=rank_seed(rank))
+    K, W = b.autotune(T)
+    reward = torch.empty(b.E, T, device=dev)
+    done = torch.empty(b.E, T, dtype=torch.uint8, device=dev)
+    obs = torch.empty(b.obs_size, device=dev)
+    fn = lambda: b.rollout(T, reward=reward, done=done, obs=obs)
+    for _ in range(args.warmup):
+        fn()
+    torch.cuda.synchronize()
+    barrier(ws)
+    ms = timed(fn, args.steps)
+    b.check()
+    total = max_over_ranks(sum(ms) / 1e3, ws)
+    value = b.E * T * args.steps * ws / total
+    out = {"value": value, "unit": "env-steps/s", "ms_per_step": 1e3 * total / args.steps, "workload": wv.name,
+           "n_levels": wv.params.n_levels, "steps_per_launch": K, "warps_per_block": W,
+           "actions": f"Philox uniform {wv.params.n_levels} signed levels per charger and battery, in-kernel",
+           "v2g_over_charge_only": value / charge_only_value,
+           "gpu_launches": math.ceil(T / K) * args.steps}
+    del b
+    return out
 
 
 def run_policy_rollout(args, rank, ws, dev, timed, pk):

@@ -141,7 +141,8 @@ int chx_n_envs(const chx_handle* h, int32_t* out);
 int chx_n_ports_total(const chx_handle* h, int64_t* out);
 /* h_offsets[n_envs+1]: charger offsets in batch order. */
 int chx_port_offsets(const chx_handle* h, int64_t* h_offsets);
-/* Floats of one observation of the whole batch: 8 per env + 6 per charger. */
+/* Floats of one observation of the whole batch: 8 per env (10 in V2G mode)
+ * + 6 per charger. */
 int chx_obs_size(const chx_handle* h, int64_t* out);
 
 /* ---- reset, Appendix "Practical Considerations" ---------------------------
@@ -158,7 +159,11 @@ int chx_reset(chx_handle* h, const int32_t* d_env_ids, int32_t n, uint64_t seed,
  *              (port_off[e]+q)*lda; NULL = uniform levels drawn in the kernel
  *              with Philox (counter: env, step/8, charger, 2; 16-bit half of a
  *              word).  Levels outside 0..n_levels-1 are clamped and flag
- *              CHX_EFAULT at the next chx_check.
+ *              CHX_EFAULT at the next chx_check.  V2G mode: every env has
+ *              n_ports + 1 actions, its chargers' then its battery's, so
+ *              charger q of env e is element (port_off[e]+e+q)*lda and the
+ *              battery element (port_off[e+1]+e)*lda; a drawn battery level
+ *              uses charger index n_ports in the Philox counter.
  *   d_reward:  device float [n_envs]; d_done: device uint8 [n_envs] (1 when
  *              the episode ended in this step; the env is already reset).
  * Either output may be NULL. */
@@ -235,7 +240,9 @@ int chx_set_launch(chx_handle* h, int32_t steps_per_launch, int32_t warps_per_bl
 /* ---- observation -----------------------------------------------------------
  * d_obs: device float [chx_obs_size].  Env e's block starts at float
  * 8*e + 6*port_off[e]: [sin, cos of time of day, buy price now, p_sell,
- * occupied fraction, day/n_days, step/ep_len, weekday flag], then per charger
+ * occupied fraction, day/n_days, step/ep_len, weekday flag] (V2G mode: then
+ * battery SoC and battery power / batt_rate_kw; the station block is 10
+ * floats and starts at 10*e + 6*port_off[e]), then per charger
  * [occupied, SoC, remaining stay/stay_hi, r_hat/P_max, last power/P_max,
  * remaining demand/cap_hi]. */
 int chx_observe(chx_handle* h, float* d_obs, void* stream);
@@ -254,6 +261,12 @@ int chx_set_state(chx_handle* h, const float* h_soc, const float* h_erem, const 
                   const float* h_rbar, const float* h_p, const uint8_t* h_trem, const int32_t* h_tod,
                   const int32_t* h_day, const uint32_t* h_gstep, const uint32_t* h_ncar,
                   const uint32_t* h_key0, const uint32_t* h_key1, const float* h_ep_ret);
+
+/* Station battery per env [E] (V2G mode; zeros otherwise): SoC and last
+ * applied power kW.  chx_set_battery: CHX_EINVAL for a SoC outside [0,1];
+ * NULL keeps a field.  Blocking. */
+int chx_get_battery(chx_handle* h, float* h_soc, float* h_p);
+int chx_set_battery(chx_handle* h, const float* h_soc, const float* h_p);
 
 /* Per-env running statistics [E]: cars admitted, cars rejected, kWh missing
  * at departure, kWh charged, finished episodes, return of the last episode. */

@@ -26,6 +26,7 @@ EXPORTS = (
     "chx_obs_size", "chx_reset", "chx_step", "chx_step_n", "chx_rollout", "chx_rollout_host", "chx_step_host",
     "chx_autotune", "chx_set_launch", "chx_observe", "chx_get_state", "chx_set_state", "chx_stats", "chx_save",
     "chx_load", "chx_check", "chx_rollout_noalloc", "chx_policy_load", "chx_policy_act", "chx_policy_rollout",
+    "chx_get_battery", "chx_set_battery",
     "chx_srv_start", "chx_srv_stop", "chx_srv_admit", "chx_srv_evict", "chx_srv_submit", "chx_srv_wait",
     "chx_srv_test", "chx_srv_stats", "chx_srv_simulate",
 )
@@ -123,6 +124,7 @@ def load_library(path: str = LIB_PATH):
         "chx_rollout_noalloc": [vp, i32, vp, vp, vp, vp],
         "chx_policy_load": [vp, i32, vp, vp, vp, vp, vp, vp], "chx_policy_act": [vp, vp, vp, vp, vp],
         "chx_policy_rollout": [vp, i32, vp, vp, vp, vp, vp, i32, vp],
+        "chx_get_battery": [vp, vp, vp], "chx_set_battery": [vp, vp, vp],
         "chx_srv_start": [vp, vp], "chx_srv_stop": [vp], "chx_srv_admit": [vp, vp, u64, vp],
         "chx_srv_evict": [vp, vp, i32], "chx_srv_submit": [vp, vp, vp], "chx_srv_wait": [vp, u64, i64, vp],
         "chx_srv_test": [vp, u64, vp, vp], "chx_srv_stats": [vp, vp], "chx_srv_simulate": [vp, vp, vp, vp],
@@ -275,6 +277,22 @@ class Batch:
     def set_state(self, s: dict):
         arrs = [None if s.get(n) is None else np.ascontiguousarray(s[n], dtype=dt) for n, dt, _ in STATE_FIELDS]
         _check(_lib.chx_set_state(self.h, *[_np_ptr(a) for a in arrs]))
+
+    def battery(self) -> dict:
+        d = dict(soc=np.zeros(self.E, np.float32), p=np.zeros(self.E, np.float32))
+        _check(_lib.chx_get_battery(self.h, _np_ptr(d["soc"]), _np_ptr(d["p"])))
+        return d
+
+    def set_battery(self, soc=None, p=None):
+        a = None if soc is None else np.ascontiguousarray(soc, dtype=np.float32)
+        b = None if p is None else np.ascontiguousarray(p, dtype=np.float32)
+        _check(_lib.chx_set_battery(self.h, _np_ptr(a), _np_ptr(b)))
+
+    @property
+    def n_actions(self) -> int:
+        """Actions per step: one per charger, plus one battery level per
+        station in V2G mode."""
+        return self.P + (self.E if self.workload.params.v2g else 0)
 
     def stats(self) -> dict:
         E = self.E

@@ -28,6 +28,10 @@ __global__ void k_reset(DevBatch b, DevParams p, const int32_t* __restrict__ use
         b.ncar[s] = 0u;
         b.tod[s] = 0;
         b.ep_ret[s] = 0.f;
+        if (p.v2g) {  // the battery arrays exist only in V2G mode
+            b.bsoc[s] = p.batt_soc0;
+            b.bp[s] = 0.f;
+        }
         b.day[s] = draw_day((uint32_t)uid, 0u, 1u, seed_lo, seed_hi, p.n_days);
     }
 }
@@ -62,6 +66,10 @@ __global__ void k_reset_slots(DevBatch b, DevParams p, const int32_t* __restrict
         b.ncar[s] = 0u;
         b.tod[s] = 0;
         b.ep_ret[s] = 0.f;
+        if (p.v2g) {  // the battery arrays exist only in V2G mode
+            b.bsoc[s] = p.batt_soc0;
+            b.bp[s] = 0.f;
+        }
         b.day[s] = draw_day((uint32_t)s, 0u, 1u, lo, hi, p.n_days);
     }
 }
@@ -84,17 +92,18 @@ __global__ void k_observe(DevBatch b, DevParams p, float* __restrict__ obs)
     const int C = 8 << c;
     const long long pb = b.cls_port_base[c] + (long long)(s - b.cls_env_base[c]) * C;
     const int n = b.n_ports[s];
-    float* ob = obs + 8LL * uid + 6LL * b.user_port_off[s];
+    float* ob = obs + (long long)p.obs_env * uid + 6LL * b.user_port_off[s];
     int occ = 0;
     for (int q = lane; q < n; q += 32) {
         const long long i = pb + q;
         const int tr = b.trem[i];
         occ += tr > 0;
-        obs_port(ob + 8 + 6 * q, tr, b.soc[i], b.erem[i], b.rbar[i], b.pw[i], b.meta[i] & kMetaDC, p);
+        obs_port(ob + p.obs_env + 6 * q, tr, b.soc[i], b.erem[i], b.rbar[i], b.pw[i], b.meta[i] & kMetaDC, p);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) occ += __shfl_xor_sync(0xFFFFFFFFu, occ, o);
-    if (lane == 0) obs_env(ob, b.tod[s], b.day[s], occ, n, b, p);
+    if (lane == 0)
+        obs_env(ob, b.tod[s], b.day[s], occ, n, p.v2g ? b.bsoc[s] : 0.f, p.v2g ? b.bp[s] : 0.f, b, p);
 }
 
 void launch_observe(const DevBatch& b, const DevParams& p, float* obs, cudaStream_t st)

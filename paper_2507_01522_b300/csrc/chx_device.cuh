@@ -49,6 +49,12 @@ struct DevParams {
     float rb_lo0, rb_span0, rb_lo1, rb_span1;
     float obs_inv_stay, obs_inv_cap, obs_inv_days, obs_inv_len;
     float inv_pmax0, inv_pmax1;            // 1 / maximum power (FP32, correctly rounded), per type
+    // vehicle-to-grid mode (signed levels, station battery)
+    int v2g, half;                         // half = (n_levels - 1) / 2: level k requests (k - half) * lvl
+    float eta0, eta1;                      // charger efficiency per type (discharge losses)
+    float batt_cap, inv_batt_cap, batt_rate, batt_lvl, batt_tau, batt_inv_1m_tau, batt_soc0;
+    float sell_grid_ratio, a_degrad, obs_inv_batt_rate;
+    int obs_env;                           // station features of an observation: 8, or 10 in V2G mode
 };
 
 struct DevBatch {
@@ -64,6 +70,7 @@ struct DevBatch {
     uint32_t *gstep, *key0, *key1;
     uint32_t* ncar;                        // cars admitted since the last reset
     float *ep_ret, *last_ret;
+    float *bsoc, *bp;                      // station battery (V2G mode): SoC, last applied power
     uint32_t* n_episodes;
     uint32_t *st_arrived, *st_rejected;
     float *st_missing, *st_charged;
@@ -150,6 +157,40 @@ __device__ __forceinline__ float clip_power(int level, bool dc, float soc, float
     return fmaxf(P, 0.0f);
 }
 
+// V2G clip (A.2 "Apply Actions", both branches): level k requests
+// (k - half) * lvl; charging as clip_power, discharging limited by the
+// request, the car's discharging rate (the charging curve flipped at
+// SoC = 0.5: r_hat(1 - SoC)), the charger maximum and SoC >= 0
+__device__ __forceinline__ float clip_power_v2g(int level, bool dc, float soc, float erem, float cap, float rbar,
+                                                const DevParams& p)
+{
+    const float pmax = dc ? p.pmax1 : p.pmax0;
+    const float preq = (float)(level - p.half) * (dc ? p.lvl1 : p.lvl0);
+    if (preq >= 0.f) {
+        const float rhat = taper(soc, rbar, p);
+        const float soc_cap = (1.0f - soc) * cap * p.inv_dt;
+        const float dem_cap = erem * p.inv_dt;
+        return fmaxf(fminf(fminf(preq, rhat), fminf(fminf(pmax, soc_cap), dem_cap)), 0.0f);
+    }
+    // r_hat(1 - SoC) written without forming 1 - (1 - SoC) (cancellation in FP32)
+    const float rdis = 1.0f - soc <= p.tau ? rbar : soc * rbar * p.inv_1m_tau;
+    const float soc_cap = soc * cap * p.inv_dt;
+    return -fmaxf(fminf(fminf(-preq, rdis), fminf(pmax, soc_cap)), 0.0f);
+}
+
+// the station battery's power (V2G): the same two branches with its own
+// rate curve and SoC in [0, 1]; it never leaves, so no demand cap
+__device__ __forceinline__ float clip_battery(int level, float bsoc, const DevParams& p)
+{
+    const float preq = (float)(level - p.half) * p.batt_lvl;
+    if (preq >= 0.f) {
+        const float rhat = bsoc <= p.batt_tau ? p.batt_rate : (1.0f - bsoc) * p.batt_rate * p.batt_inv_1m_tau;
+        return fmaxf(fminf(fminf(preq, rhat), (1.0f - bsoc) * p.batt_cap * p.inv_dt), 0.0f);
+    }
+    const float rdis = 1.0f - bsoc <= p.batt_tau ? p.batt_rate : bsoc * p.batt_rate * p.batt_inv_1m_tau;
+    return -fmaxf(fminf(fminf(-preq, rdis), bsoc * p.batt_cap * p.inv_dt), 0.0f);
+}
+
 struct Car { float cap, soc, erem, rbar; int stay; };
 
 // Philox words of the station's n-th car since its last reset
@@ -195,8 +236,10 @@ __device__ __forceinline__ int arrivals(const DevBatch& b, const DevParams& p, u
     return arrival_count(b, p, word_of(arrival_words(uid, g, k0, k1), g & 3u), t, cls_row);
 }
 
-// observation features of a station (8 floats) and of one charger (6 floats)
-__device__ __forceinline__ void obs_env(float* o, int t, int day, int occ, int n, const DevBatch& b, const DevParams& p)
+// observation features of a station (p.obs_env floats: 8, + battery SoC and
+// power / rate in V2G mode) and of one charger (6 floats)
+__device__ __forceinline__ void obs_env(float* o, int t, int day, int occ, int n, float bsoc, float bpw,
+                                        const DevBatch& b, const DevParams& p)
 {
     float s, c;
     sincospif(2.0f * (float)t * p.obs_inv_len, &s, &c);
@@ -208,6 +251,10 @@ __device__ __forceinline__ void obs_env(float* o, int t, int day, int occ, int n
     o[5] = (float)day * p.obs_inv_days;
     o[6] = (float)t * p.obs_inv_len;
     o[7] = (day % 7) < 5 ? 1.0f : 0.0f;
+    if (p.v2g) {
+        o[8] = bsoc;
+        o[9] = bpw * p.obs_inv_batt_rate;
+    }
 }
 
 __device__ __forceinline__ void obs_port(float* o, int trem, float soc, float erem, float rbar, float pw, bool dc,

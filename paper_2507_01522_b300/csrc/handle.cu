@@ -81,6 +81,18 @@ int validate_params(const chx_env_params* p, const chx_exo* x)
         if (!(p->eta_port[t] > 0.f && p->eta_port[t] <= 1.f)) return fail(CHX_EINVAL, "eta_port must be in (0,1]");
         if (p->rbar_kw[t][0] < 0.f || p->rbar_kw[t][1] < p->rbar_kw[t][0]) return fail(CHX_EINVAL, "rbar range invalid");
     }
+    if (p->v2g != 0 && p->v2g != 1) return fail(CHX_EINVAL, "v2g must be 0 or 1");
+    if (p->v2g) {
+        if (p->n_levels < 3 || (p->n_levels & 1) == 0)
+            return fail(CHX_EINVAL, "V2G mode needs an odd n_levels >= 3 (levels symmetric around idle)");
+        if (!(p->batt_cap_kwh > 0.f) || !std::isfinite(p->batt_cap_kwh)) return fail(CHX_EINVAL, "batt_cap_kwh must be > 0");
+        if (!(p->batt_rate_kw >= 0.f) || !std::isfinite(p->batt_rate_kw)) return fail(CHX_EINVAL, "batt_rate_kw must be >= 0");
+        if (!(p->batt_tau > 0.f && p->batt_tau < 1.f)) return fail(CHX_EINVAL, "batt_tau must be in (0,1)");
+        if (!(p->batt_soc0 >= 0.f && p->batt_soc0 <= 1.f)) return fail(CHX_EINVAL, "batt_soc0 must be in [0,1]");
+        if (!(p->sell_grid_ratio >= 0.f) || !std::isfinite(p->sell_grid_ratio))
+            return fail(CHX_EINVAL, "sell_grid_ratio must be >= 0");
+        if (!std::isfinite(p->alpha_degrad)) return fail(CHX_EINVAL, "alpha_degrad must be finite");
+    }
     if (x->n_days < 1 || !x->h_price) return fail(CHX_EINVAL, "price bank missing");
     if (x->n_arrival_classes < 1 || !x->h_arrival_rate) return fail(CHX_EINVAL, "arrival table missing");
     const size_t nl = (size_t)x->n_arrival_classes * (size_t)p->ep_len;
@@ -175,8 +187,26 @@ DevParams make_params(const chx_env_params& q, int n_days)
     p.soc_target = q.soc_target;
     p.pmax0 = q.p_max_kw[0];
     p.pmax1 = q.p_max_kw[1];
-    p.lvl0 = (float)((double)q.p_max_kw[0] / (double)(q.n_levels - 1));
-    p.lvl1 = (float)((double)q.p_max_kw[1] / (double)(q.n_levels - 1));
+    p.v2g = q.v2g ? 1 : 0;
+    p.half = p.v2g ? (q.n_levels - 1) / 2 : 0;
+    const double per_level = p.v2g ? (double)p.half : (double)(q.n_levels - 1);
+    p.lvl0 = (float)((double)q.p_max_kw[0] / per_level);
+    p.lvl1 = (float)((double)q.p_max_kw[1] / per_level);
+    p.eta0 = q.eta_port[0];
+    p.eta1 = q.eta_port[1];
+    if (p.v2g) {
+        p.batt_cap = q.batt_cap_kwh;
+        p.inv_batt_cap = (float)(1.0 / (double)q.batt_cap_kwh);
+        p.batt_rate = q.batt_rate_kw;
+        p.batt_lvl = (float)((double)q.batt_rate_kw / (double)p.half);
+        p.batt_tau = q.batt_tau;
+        p.batt_inv_1m_tau = (float)(1.0 / (1.0 - (double)q.batt_tau));
+        p.batt_soc0 = q.batt_soc0;
+        p.sell_grid_ratio = q.sell_grid_ratio;
+        p.a_degrad = q.alpha_degrad;
+        p.obs_inv_batt_rate = q.batt_rate_kw > 0.f ? (float)(1.0 / (double)q.batt_rate_kw) : 0.f;
+    }
+    p.obs_env = p.v2g ? 10 : 8;
     p.inv_eta0 = (float)(1.0 / (double)q.eta_port[0]);
     p.inv_eta1 = (float)(1.0 / (double)q.eta_port[1]);
     p.cap_lo = q.cap_kwh[0];
@@ -316,6 +346,7 @@ int build_handle(const chx_stations* st, const chx_env_params* prm, const chx_ex
     ALLOC(b.user_id, NS) ALLOC(b.user_port_off, NS) ALLOC(b.n_ports, NS) ALLOC(b.arrival_class, NS)
     ALLOC(b.grid_cap, NS) ALLOC(b.grid_inv_eta, NS) ALLOC(b.tod, NS) ALLOC(b.day, NS) ALLOC(b.gstep, NS) ALLOC(b.ncar, NS)
     ALLOC(b.key0, NS) ALLOC(b.key1, NS) ALLOC(b.ep_ret, NS) ALLOC(b.last_ret, NS) ALLOC(b.n_episodes, NS)
+    ALLOC(b.bsoc, NS) ALLOC(b.bp, NS)
     ALLOC(b.st_arrived, NS) ALLOC(b.st_rejected, NS) ALLOC(b.st_missing, NS) ALLOC(b.st_charged, NS)
     ALLOC(h->d_user_to_slot, E) ALLOC(h->d_counter, 64) ALLOC(b.err, 1)
     const size_t nprice = (size_t)exo->n_days * prm->ep_len, nlam = (size_t)exo->n_arrival_classes * prm->ep_len;
@@ -427,7 +458,7 @@ extern "C" int chx_port_offsets(const chx_handle* h, int64_t* h_offsets)
 extern "C" int chx_obs_size(const chx_handle* h, int64_t* out)
 {
     if (!h || !out) return fail(CHX_EINVAL, "null argument");
-    *out = 8LL * h->E + 6LL * h->P;
+    *out = (long long)h->dp.obs_env * h->E + 6LL * h->P;
     return CHX_OK;
 }
 
@@ -574,7 +605,7 @@ extern "C" int chx_rollout_host(chx_handle* h, int32_t n_steps, float* h_reward,
     if (!h) return fail(CHX_EINVAL, "null handle");
     if (n_steps < 1) return fail(CHX_EINVAL, "n_steps must be >= 1");
     const size_t ne = (size_t)h->E * (size_t)n_steps;
-    const size_t nobs = 8 * (size_t)h->E + 6 * (size_t)h->P;
+    const size_t nobs = (size_t)h->dp.obs_env * (size_t)h->E + 6 * (size_t)h->P;
     float* dr = h_reward ? (float*)staging(h, 0, ne * sizeof(float)) : nullptr;
     uint8_t* dd = h_done ? (uint8_t*)staging(h, 1, ne) : nullptr;
     float* dob = h_obs ? (float*)staging(h, 2, nobs * sizeof(float)) : nullptr;
@@ -594,14 +625,15 @@ extern "C" int chx_step_host(chx_handle* h, const int8_t* h_actions, float* h_re
 {
     if (!h) return fail(CHX_EINVAL, "null handle");
     cudaStream_t st = (cudaStream_t)stream;
-    const size_t nobs = 8 * (size_t)h->E + 6 * (size_t)h->P;
-    int8_t* da = h_actions ? (int8_t*)staging(h, 3, (size_t)h->P) : nullptr;
+    const size_t nobs = (size_t)h->dp.obs_env * (size_t)h->E + 6 * (size_t)h->P;
+    const size_t nact = (size_t)h->P + (h->dp.v2g ? (size_t)h->E : 0);
+    int8_t* da = h_actions ? (int8_t*)staging(h, 3, nact) : nullptr;
     float* dr = h_reward ? (float*)staging(h, 4, (size_t)h->E * sizeof(float)) : nullptr;
     uint8_t* dd = h_done ? (uint8_t*)staging(h, 5, (size_t)h->E) : nullptr;
     float* dob = h_obs ? (float*)staging(h, 2, nobs * sizeof(float)) : nullptr;
     if ((h_actions && !da) || (h_reward && !dr) || (h_done && !dd) || (h_obs && !dob))
         return fail(CHX_ENOMEM, "staging allocation failed");
-    if (h_actions) CUDA_TRY(cudaMemcpyAsync(da, h_actions, (size_t)h->P, cudaMemcpyHostToDevice, st));
+    if (h_actions) CUDA_TRY(cudaMemcpyAsync(da, h_actions, nact, cudaMemcpyHostToDevice, st));
     launch_step_plain(h->b, h->dp, da, 1, dr, dd, nullptr, 0, st);
     CUDA_TRY(cudaGetLastError());
     if (h_obs) {
@@ -641,7 +673,8 @@ int snapshot_take(chx_handle* h, Snapshot& s)
     s.items = {{b.soc, PS * 4}, {b.erem, PS * 4}, {b.cap, PS * 4}, {b.rbar, PS * 4}, {b.pw, PS * 4},
                {b.trem, PS}, {b.tod, NS * 4}, {b.day, NS * 4}, {b.gstep, NS * 4}, {b.ncar, NS * 4}, {b.key0, NS * 4},
                {b.key1, NS * 4}, {b.ep_ret, NS * 4}, {b.last_ret, NS * 4}, {b.n_episodes, NS * 4},
-               {b.st_arrived, NS * 4}, {b.st_rejected, NS * 4}, {b.st_missing, NS * 4}, {b.st_charged, NS * 4}};
+               {b.st_arrived, NS * 4}, {b.st_rejected, NS * 4}, {b.st_missing, NS * 4}, {b.st_charged, NS * 4},
+               {b.bsoc, NS * 4}, {b.bp, NS * 4}};
     for (auto& it : s.items) {
         void* c = nullptr;
         if (cudaMalloc(&c, it.second) != cudaSuccess) return fail(CHX_ENOMEM, "snapshot allocation failed");
@@ -881,15 +914,36 @@ extern "C" int chx_stats(chx_handle* h, uint32_t* h_arrived, uint32_t* h_rejecte
     return CHX_OK;
 }
 
+extern "C" int chx_get_battery(chx_handle* h, float* h_soc, float* h_p)
+{
+    if (!h) return fail(CHX_EINVAL, "null handle");
+    CUDA_TRY(cudaDeviceSynchronize());
+    RC(get_env_field(h, h_soc, (const float*)h->b.bsoc));
+    RC(get_env_field(h, h_p, (const float*)h->b.bp));
+    return CHX_OK;
+}
+
+extern "C" int chx_set_battery(chx_handle* h, const float* h_soc, const float* h_p)
+{
+    if (!h) return fail(CHX_EINVAL, "null handle");
+    if (h_soc)
+        for (int e = 0; e < h->E; ++e)
+            if (!(h_soc[e] >= 0.f && h_soc[e] <= 1.f)) return fail(CHX_EINVAL, "battery SoC out of [0,1]");
+    CUDA_TRY(cudaDeviceSynchronize());
+    RC(set_env_field(h, h_soc, h->b.bsoc));
+    RC(set_env_field(h, h_p, h->b.bp));
+    return CHX_OK;
+}
+
 namespace {
-constexpr uint64_t kCkptMagic = 0x43484158434B5032ull;   // "CHAXCKP2"
+constexpr uint64_t kCkptMagic = 0x43484158434B5033ull;   // "CHAXCKP3"
 struct CkptHeader {
     uint64_t magic;
     int64_t n_envs, n_ports;
 };
 size_t ckpt_size(const chx_handle* h)
 {
-    return sizeof(CkptHeader) + (size_t)h->P * (5 * 4 + 1) + (size_t)h->E * (7 * 4 + 6 * 4);
+    return sizeof(CkptHeader) + (size_t)h->P * (5 * 4 + 1) + (size_t)h->E * (7 * 4 + 6 * 4 + 2 * 4);
 }
 }  // namespace
 
@@ -923,8 +977,10 @@ extern "C" int chx_save(chx_handle* h, void* h_buf, size_t* size)
     float* charged = missing + E;
     uint32_t* episodes = reinterpret_cast<uint32_t*>(charged + E);
     float* last = reinterpret_cast<float*>(episodes + E);
+    float *bsoc = last + E, *bpw = bsoc + E;
     RC(chx_get_state(h, soc, erem, cap, rbar, pw, trem, tod, day, gstep, ncar, key0, key1, ret));
     RC(chx_stats(h, arrived, rejected, missing, charged, episodes, last));
+    RC(chx_get_battery(h, bsoc, bpw));
     *size = need;
     return CHX_OK;
 }
@@ -954,7 +1010,10 @@ extern "C" int chx_load(chx_handle* h, const void* h_buf, size_t size)
     const float* charged = missing + E;
     const uint32_t* episodes = reinterpret_cast<const uint32_t*>(charged + E);
     const float* last = reinterpret_cast<const float*>(episodes + E);
+    const float *bsoc = last + E, *bpw = bsoc + E;
     RC(chx_set_state(h, f, f + P, f + 2 * P, f + 3 * P, f + 4 * P, trem, tod, day, gstep, ncar, key0, key1, ret));
+    RC(set_env_field(h, bsoc, h->b.bsoc));
+    RC(set_env_field(h, bpw, h->b.bp));
     DevBatch& b = h->b;
     RC(set_env_field(h, arrived, b.st_arrived));
     RC(set_env_field(h, rejected, b.st_rejected));

@@ -864,7 +864,7 @@ __device__ __forceinline__ void owner_observe(const Owner& o, const RolloutArgs&
         const int f0 = k == 0 ? 0 : 8 + 48 * k;
         const int f1 = min(8 + 48 * (k + 1), D);
         float st8[8], cf[48];
-        if (k == 0 && o.live) obs_env(st8, o.t, o.day, o.occ, N, R.b, p);
+        if (k == 0 && o.live) obs_env(st8, o.t, o.day, o.occ, N, 0.f, 0.f, R.b, p);   // charge-only mode
         else
 #pragma unroll
             for (int f = 0; f < 8; ++f) st8[f] = 0.f;

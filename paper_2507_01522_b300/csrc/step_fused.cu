@@ -192,7 +192,11 @@ struct WarpSmem {
     uint32_t carw[4][128];                 // pre-drawn car words: station ew's i-th buffered car at ew*C + i
 };
 
-template <int C>
+// V2G: signed levels, the station battery at the root (state in the
+// station's lanes, its level after the chargers' or drawn at charger index
+// n), signed limits, discharge energy after the port loss, two-case profit,
+// degradation penalty; observation with the battery features.
+template <int C, bool V2G>
 __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, const FusedIO& io, int tile,
                                          WarpSmem* ws)
 {
@@ -216,6 +220,7 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
         s = b.cls_env_base[CI] + tile * S::EPW + ew;
         act_base = b.user_port_off[s];
         out_idx = b.user_id[s];
+        if (V2G) act_base += out_idx;     // one more action (the battery's) per station before this one
     }
     const long long pb = b.cls_port_base[CI] + (long long)(s - b.cls_env_base[CI]) * C + le * PPL;
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -231,6 +236,13 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
     int t = b.tod[s], day = b.day[s];
     uint32_t g = b.gstep[s];
     float ret = b.ep_ret[s];
+    // station battery (V2G): the same values in all the station's lanes
+    float bsoc = 0.f, bpw = 0.f;
+    uint4 bwords = make_uint4(0, 0, 0, 0);
+    if (V2G) {
+        bsoc = b.bsoc[s];
+        bpw = b.bp[s];
+    }
     // cars: the station's next C car profiles are drawn in one lane-parallel
     // pass into shared memory and handed out as cars arrive
     uint32_t ncar = b.ncar[s], cend = ncar;
@@ -300,7 +312,28 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
                 }
             }
             const bool dc = meta[q] & kMetaDC;
-            P[q] = trem[q] > 0 ? clip_power(lvl, dc, soc[q], erem[q], cap[q], rbar[q], p) : 0.f;
+            if (V2G)
+                P[q] = trem[q] > 0 ? clip_power_v2g(lvl, dc, soc[q], erem[q], cap[q], rbar[q], p) : 0.f;
+            else
+                P[q] = trem[q] > 0 ? clip_power(lvl, dc, soc[q], erem[q], cap[q], rbar[q], p) : 0.f;
+        }
+        // the battery's request (V2G; computed alike in every lane of the station)
+        float Pb = 0.f;
+        if (V2G) {
+            const int n_st = b.n_ports[s];
+            int lvl;
+            if (random_actions) {
+                if (k == 0 || (g & 7u) == 0u)
+                    bwords = philox4x32_10(make_uint4(uidu, g >> 3, (uint32_t)n_st, kPurposeAction), k0, k1);
+                lvl = random_level(bwords, g, p.n_levels);
+            } else {
+                lvl = io.actions[((long long)act_base + n_st) * io.lda + k];
+                if (lvl < 0 || lvl >= p.n_levels) {
+                    atomicOr(b.err, kErrActionRange);
+                    lvl = min(max(lvl, 0), p.n_levels - 1);
+                }
+            }
+            Pb = clip_battery(lvl, bsoc, p);
         }
 
         // ---- architecture constraint: group nodes (segmented scan), then root
@@ -314,30 +347,41 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
             if (meta[q] & kMetaTail) {
                 const int gs = ew * GPS + (int)((meta[q] >> kMetaGroupShift) & 31u);
                 const float gc = ws->gcap[gs];
-                const float sc = Sg[q] > gc ? __fdividef(gc, Sg[q]) : 1.0f;
+                const float mag = V2G ? fabsf(Sg[q]) : Sg[q];
+                const float sc = mag > gc ? __fdividef(gc, mag) : 1.0f;
                 ws->scale[gs] = sc;
-                if (p.a_con != 0.f) over = fmaxf(over, (Sg[q] - gc) * ws->ginv[gs]);
+                if (p.a_con != 0.f) over = fmaxf(over, (mag - gc) * ws->ginv[gs]);
             }
         }
         __syncwarp();
-        float raw = 0.f, sp = 0.f, se = 0.f;
+        float raw = 0.f, sp = 0.f, se = 0.f, sn = 0.f;
 #pragma unroll
         for (int q = 0; q < PPL; ++q) {
             raw += P[q];
             P[q] *= ws->scale[ew * GPS + (int)((meta[q] >> kMetaGroupShift) & 31u)];
             sp += P[q];
-            se += P[q] * ((meta[q] & kMetaDC) ? p.inv_eta1 : p.inv_eta0);
+            const bool dcq = meta[q] & kMetaDC;
+            if (V2G) {
+                if (P[q] >= 0.f) se += P[q] * (dcq ? p.inv_eta1 : p.inv_eta0);
+                else sn += P[q] * (dcq ? p.eta1 : p.eta0);
+            } else {
+                se += P[q] * (dcq ? p.inv_eta1 : p.inv_eta0);
+            }
         }
         __syncwarp();
         sp = seg_sum<LPE>(sp);
         se = seg_sum<LPE>(se);
+        if (V2G) sn = seg_sum<LPE>(sn);
         float c_con = 0.f;
         if (p.a_con != 0.f) {
             raw = seg_sum<LPE>(raw);
             over = seg_max<LPE>(over);
-            c_con = fmaxf(fmaxf(over, (raw - grid_cap) * b.grid_inv_eta[s]), 0.f);
+            const float raw_root = V2G ? fabsf(raw + Pb) : raw;
+            c_con = fmaxf(fmaxf(over, (raw_root - grid_cap) * b.grid_inv_eta[s]), 0.f);
         }
-        const float s_root = sp > grid_cap ? __fdividef(grid_cap, sp) : 1.0f;
+        const float s_tot = V2G ? sp + Pb : sp;
+        const float mag_root = V2G ? fabsf(s_tot) : s_tot;
+        const float s_root = mag_root > grid_cap ? __fdividef(grid_cap, mag_root) : 1.0f;
 
         // ---- (ii) charge, time advance, (iii) departures
         bool any_leave = false;
@@ -349,6 +393,7 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
             if (trem[q] > 0) {
                 const float dE = Pq * p.dt;
                 soc[q] = fminf(soc[q] + __fdividef(dE, cap[q]), 1.0f);
+                if (V2G) soc[q] = fmaxf(soc[q], 0.0f);
                 erem[q] = fmaxf(erem[q] - dE, 0.0f);
                 trem[q] -= 1;
                 if (trem[q] == 0) leave |= 1u << q;
@@ -357,6 +402,13 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
         any_leave = leave != 0;
         const float e_net = sp * s_root * p.dt;
         const float e_grid = se * s_root * p.dt;
+        float e_to = 0.f, e_b = 0.f;
+        if (V2G) {
+            e_to = sn * s_root * p.dt;
+            bpw = Pb * s_root;
+            e_b = bpw * p.dt;
+            bsoc = fminf(fmaxf(bsoc + e_b * p.inv_batt_cap, 0.0f), 1.0f);
+        }
         float c_sat = 0.f;
         if (__any_sync(0xFFFFFFFFu, any_leave)) {
             float v = 0.f;
@@ -427,8 +479,17 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
 
         // ---- reward, Appendix A.3
         const float price = __ldg(b.price + (size_t)day * (size_t)p.ep_len + (size_t)t);
-        const float profit = p.p_sell * e_net - price * e_grid - p.c_fixed;
-        const float r = profit - p.a_sat * c_sat - p.a_decl * (float)(M - m_adm) - p.a_con * c_con;
+        float r;
+        if (V2G) {
+            const float e_gn = e_grid + e_to + e_b;
+            const float pg = e_gn > 0.f ? price : p.sell_grid_ratio * price;
+            const float degrad = fmaxf(-e_b, 0.0f) - e_to;
+            r = p.p_sell * e_net - pg * e_gn - p.c_fixed - p.a_sat * c_sat - p.a_decl * (float)(M - m_adm) -
+                p.a_con * c_con - p.a_degrad * degrad;
+        } else {
+            const float profit = p.p_sell * e_net - price * e_grid - p.c_fixed;
+            r = profit - p.a_sat * c_sat - p.a_decl * (float)(M - m_adm) - p.a_con * c_con;
+        }
         ret += r;
         t += 1;
         const bool fin = t >= p.ep_len;
@@ -455,6 +516,10 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
             }
             t = 0;
             day = draw_day(uidu, g, 0u, k0, k1, p.n_days);
+            if (V2G) {
+                bsoc = p.batt_soc0;
+                bpw = 0.f;
+            }
         }
         g += 1u;
     }
@@ -481,6 +546,10 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
         b.st_rejected[s] += ws->st_u[ew][1];
         b.st_missing[s] += ws->st_f[ew][0];
         b.st_charged[s] += ws->st_f[ew][1];
+        if (V2G) {
+            b.bsoc[s] = bsoc;
+            b.bp[s] = bpw;
+        }
     }
     if (io.obs) {                          // uniform across the warp
         int occ_l = 0;
@@ -489,13 +558,15 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
         const int occ = (int)seg_sum<LPE>((float)occ_l);
         if (live) {
             const int n = b.n_ports[s];
-            float* ob = io.obs + (io.gather ? (long long)obs_w : 8LL * uid + 6LL * act_base);
-            if (le == 0) obs_env(ob, t, day, occ, n, b, p);
+            float* ob = io.obs + (io.gather ? (long long)obs_w
+                                            : (long long)p.obs_env * uid + 6LL * b.user_port_off[s]);
+            if (le == 0) obs_env(ob, t, day, occ, n, bsoc, bpw, b, p);
 #pragma unroll
             for (int q = 0; q < PPL; ++q) {
                 const int port = le * PPL + q;
                 if (port < n)
-                    obs_port(ob + 8 + 6 * port, trem[q], soc[q], erem[q], rbar[q], pw[q], meta[q] & kMetaDC, p);
+                    obs_port(ob + p.obs_env + 6 * port, trem[q], soc[q], erem[q], rbar[q], pw[q], meta[q] & kMetaDC,
+                             p);
             }
         }
     }
@@ -506,7 +577,7 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
 // instantiation for the 128-charger class (4 chargers per lane, more
 // registers), one for the others, so the smaller classes keep more warps
 // resident.
-template <int CLO, int CHI, int MINB>
+template <int CLO, int CHI, int MINB, bool V2G>
 __global__ void __launch_bounds__(256, MINB) k_step_fused(DevBatch b, DevParams p, FusedIO io)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -531,18 +602,21 @@ __global__ void __launch_bounds__(256, MINB) k_step_fused(DevBatch b, DevParams 
                 tile = tile_id - io.sched_tile_base[i];
             }
         }
-        if (CLO <= 0 && 0 <= CHI && cls == 0) run_tile<8>(b, p, io, tile, ws);
-        if (CLO <= 1 && 1 <= CHI && cls == 1) run_tile<16>(b, p, io, tile, ws);
-        if (CLO <= 2 && 2 <= CHI && cls == 2) run_tile<32>(b, p, io, tile, ws);
-        if (CLO <= 3 && 3 <= CHI && cls == 3) run_tile<64>(b, p, io, tile, ws);
-        if (CLO <= 4 && 4 <= CHI && cls == 4) run_tile<128>(b, p, io, tile, ws);
+        if (CLO <= 0 && 0 <= CHI && cls == 0) run_tile<8, V2G>(b, p, io, tile, ws);
+        if (CLO <= 1 && 1 <= CHI && cls == 1) run_tile<16, V2G>(b, p, io, tile, ws);
+        if (CLO <= 2 && 2 <= CHI && cls == 2) run_tile<32, V2G>(b, p, io, tile, ws);
+        if (CLO <= 3 && 3 <= CHI && cls == 3) run_tile<64, V2G>(b, p, io, tile, ws);
+        if (CLO <= 4 && 4 <= CHI && cls == 4) run_tile<128, V2G>(b, p, io, tile, ws);
     }
 }
 
 namespace {
 
-auto* const kSmallKernel = &k_step_fused<0, 3, 3>;
-auto* const kLargeKernel = &k_step_fused<4, 4, 2>;
+// [v2g]: the charge-only and the vehicle-to-grid instantiations
+void (*const kSmallKernel[2])(DevBatch, DevParams, FusedIO) = {&k_step_fused<0, 3, 3, false>,
+                                                                &k_step_fused<0, 3, 3, true>};
+void (*const kLargeKernel[2])(DevBatch, DevParams, FusedIO) = {&k_step_fused<4, 4, 2, false>,
+                                                                &k_step_fused<4, 4, 2, true>};
 
 // the part of a schedule whose classes lie in [clo, chi], tiles renumbered
 FusedIO sub_schedule(const FusedIO& io, int clo, int chi, int* counter)
@@ -567,10 +641,15 @@ FusedIO sub_schedule(const FusedIO& io, int clo, int chi, int* counter)
 // allow each kernel the dynamic shared memory of 8 warps (above the 48 KB default)
 bool raise_smem_limit()
 {
-    static const bool ok = cudaFuncSetAttribute((const void*)kSmallKernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                8 * (int)sizeof(WarpSmem)) == cudaSuccess &&
-                           cudaFuncSetAttribute((const void*)kLargeKernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                8 * (int)sizeof(WarpSmem)) == cudaSuccess;
+    static const bool ok = [] {
+        for (int v = 0; v < 2; ++v)
+            if (cudaFuncSetAttribute((const void*)kSmallKernel[v], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     8 * (int)sizeof(WarpSmem)) != cudaSuccess ||
+                cudaFuncSetAttribute((const void*)kLargeKernel[v], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     8 * (int)sizeof(WarpSmem)) != cudaSuccess)
+                return false;
+        return true;
+    }();
     return ok;
 }
 
@@ -588,8 +667,12 @@ int blocks_per_sm(const void* kernel, int threads)
 
 bool fused_block_size_ok(int threads)
 {
-    return threads >= 32 && threads <= 256 && threads % 32 == 0 &&
-           blocks_per_sm((const void*)kSmallKernel, threads) > 0 && blocks_per_sm((const void*)kLargeKernel, threads) > 0;
+    if (threads < 32 || threads > 256 || threads % 32 != 0) return false;
+    for (int v = 0; v < 2; ++v)
+        if (blocks_per_sm((const void*)kSmallKernel[v], threads) <= 0 ||
+            blocks_per_sm((const void*)kLargeKernel[v], threads) <= 0)
+            return false;
+    return true;
 }
 
 void launch_step_fused(const DevBatch& b, const DevParams& p, const FusedIO& io, int threads, int sm_count,
@@ -599,15 +682,16 @@ void launch_step_fused(const DevBatch& b, const DevParams& p, const FusedIO& io,
     const size_t smem = (size_t)warps * sizeof(WarpSmem);
     const FusedIO big = sub_schedule(io, 4, 4, io.counter);
     const FusedIO small = sub_schedule(io, 0, 3, io.counter + 1);
+    const int v = p.v2g ? 1 : 0;
     if (big.total_tiles > 0) {             // the heavy class first
-        const int per_sm = blocks_per_sm((const void*)kLargeKernel, threads);
+        const int per_sm = blocks_per_sm((const void*)kLargeKernel[v], threads);
         const int blocks = std::max(1, std::min(per_sm * sm_count, (big.total_tiles + warps - 1) / warps));
-        kLargeKernel<<<blocks, threads, smem, st>>>(b, p, big);
+        kLargeKernel[v]<<<blocks, threads, smem, st>>>(b, p, big);
     }
     if (small.total_tiles > 0) {
-        const int per_sm = blocks_per_sm((const void*)kSmallKernel, threads);
+        const int per_sm = blocks_per_sm((const void*)kSmallKernel[v], threads);
         const int blocks = std::max(1, std::min(per_sm * sm_count, (small.total_tiles + warps - 1) / warps));
-        kSmallKernel<<<blocks, threads, smem, st>>>(b, p, small);
+        kSmallKernel[v]<<<blocks, threads, smem, st>>>(b, p, small);
     }
 }
 

@@ -9,14 +9,15 @@
 
 namespace chx {
 
-__global__ void __launch_bounds__(128) k_step_plain(DevBatch b, DevParams p, const int8_t* __restrict__ actions,
-                                                    long long lda, float* __restrict__ reward,
-                                                    uint8_t* __restrict__ done, const int* __restrict__ slot_list,
-                                                    int n_list)
+// One station's step.  V2G: signed levels (clip_power_v2g), the station
+// battery at the root (its level after the chargers' in the action array, or
+// drawn at charger index n), signed limits (|sum| <= eta * I), discharge
+// energy after the port loss, two-case profit and degradation penalty.
+template <bool V2G>
+__device__ __forceinline__ void step_station(const DevBatch& b, const DevParams& p, const int8_t* __restrict__ actions,
+                                             long long lda, float* __restrict__ reward, uint8_t* __restrict__ done,
+                                             int s)
 {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (slot_list ? n_list : b.n_slots)) return;
-    const int s = slot_list ? slot_list[idx] : idx;
     const int uid = b.user_id[s];
     if (uid < 0) return;
     const int c = class_of_slot(b, s);
@@ -26,48 +27,68 @@ __global__ void __launch_bounds__(128) k_step_plain(DevBatch b, DevParams p, con
     const uint32_t g = b.gstep[s];
     const int t = b.tod[s];
     const uint32_t k0 = b.key0[s], k1 = b.key1[s];
-    const long long uoff = b.user_port_off[s];
+    const long long aoff = b.user_port_off[s] + (V2G ? uid : 0);   // the station's first action
+
+    auto level_of = [&](int q) -> int {                 // action level of charger q (q = n: battery)
+        int lvl;
+        if (actions) {
+            lvl = actions[(aoff + q) * lda];
+            if (lvl < 0 || lvl >= p.n_levels) {
+                atomicOr(b.err, kErrActionRange);
+                lvl = min(max(lvl, 0), p.n_levels - 1);
+            }
+        } else {
+            const uint4 w = philox4x32_10(make_uint4((uint32_t)uid, g >> 3, (uint32_t)q, kPurposeAction), k0, k1);
+            lvl = random_level(w, g, p.n_levels);
+        }
+        return lvl;
+    };
+    auto clip = [&](int lvl, bool dc, float soc, float erem, float cap, float rbar) -> float {
+        return V2G ? clip_power_v2g(lvl, dc, soc, erem, cap, rbar, p) : clip_power(lvl, dc, soc, erem, cap, rbar, p);
+    };
 
     // -- (i) apply actions: per-charger clip, then group sums (Eq. ArchConst)
     float gscale[32];
-    float S = 0.f, Se = 0.f, s_raw = 0.f, s_grp = 0.f, se_grp = 0.f, over_max = 0.f;
+    float S = 0.f, Se = 0.f, Sn = 0.f, s_raw = 0.f, s_grp = 0.f, se_grp = 0.f, sn_grp = 0.f, over_max = 0.f;
     for (int q = 0; q < n; ++q) {
         const long long i = pb + q;
         const uint32_t m = b.meta[i];
         const bool dc = m & kMetaDC;
         float P = 0.f;
-        if (b.trem[i] > 0) {
-            int lvl;
-            if (actions) {
-                lvl = actions[(uoff + q) * lda];
-                if (lvl < 0 || lvl >= p.n_levels) {
-                    atomicOr(b.err, kErrActionRange);
-                    lvl = min(max(lvl, 0), p.n_levels - 1);
-                }
-            } else {
-                const uint4 w = philox4x32_10(make_uint4((uint32_t)uid, g >> 3, (uint32_t)q, kPurposeAction), k0, k1);
-                lvl = random_level(w, g, p.n_levels);
-            }
-            P = clip_power(lvl, dc, b.soc[i], b.erem[i], b.cap[i], b.rbar[i], p);
-        }
+        if (b.trem[i] > 0) P = clip(level_of(q), dc, b.soc[i], b.erem[i], b.cap[i], b.rbar[i]);
         S += P;
-        Se += P * (dc ? p.inv_eta1 : p.inv_eta0);
+        if (V2G) {
+            if (P >= 0.f) Se += P * (dc ? p.inv_eta1 : p.inv_eta0);
+            else Sn += P * (dc ? p.eta1 : p.eta0);
+        } else {
+            Se += P * (dc ? p.inv_eta1 : p.inv_eta0);
+        }
         s_raw += P;
         if (m & kMetaTail) {
             const float gc = b.gcap[i];
-            const float sc = S > gc ? __fdividef(gc, S) : 1.0f;
+            const float mag = V2G ? fabsf(S) : S;
+            const float sc = mag > gc ? __fdividef(gc, mag) : 1.0f;
             gscale[(m >> kMetaGroupShift) & 31] = sc;
-            over_max = fmaxf(over_max, (S - gc) * b.ginv_eta[i]);
+            over_max = fmaxf(over_max, (mag - gc) * b.ginv_eta[i]);
             s_grp += S * sc;
             se_grp += Se * sc;
+            sn_grp += Sn * sc;
             S = 0.f;
             Se = 0.f;
+            Sn = 0.f;
         }
     }
-    // root node
+    // station battery (a leaf of the root), then the root node
+    float Pb = 0.f, bsoc = 0.f;
+    if (V2G) {
+        bsoc = b.bsoc[s];
+        Pb = clip_battery(level_of(n), bsoc, p);
+    }
     const float grid_cap = b.grid_cap[s];
-    const float s_root = s_grp > grid_cap ? __fdividef(grid_cap, s_grp) : 1.0f;
-    const float c_con = fmaxf(fmaxf(over_max, (s_raw - grid_cap) * b.grid_inv_eta[s]), 0.0f);
+    const float s_tot = s_grp + Pb, mag = V2G ? fabsf(s_tot) : s_tot;
+    const float s_root = mag > grid_cap ? __fdividef(grid_cap, mag) : 1.0f;
+    const float raw = V2G ? fabsf(s_raw + Pb) : s_raw;
+    const float c_con = fmaxf(fmaxf(over_max, (raw - grid_cap) * b.grid_inv_eta[s]), 0.0f);
 
     // -- (ii) charge, time advance, (iii) departures
     float c_sat = 0.f;
@@ -79,19 +100,13 @@ __global__ void __launch_bounds__(128) k_step_plain(DevBatch b, DevParams p, con
         int tr = b.trem[i];
         float P = 0.f;
         if (tr > 0) {
-            int lvl;
-            if (actions) {
-                lvl = min(max((int)actions[(uoff + q) * lda], 0), p.n_levels - 1);
-            } else {
-                const uint4 w = philox4x32_10(make_uint4((uint32_t)uid, g >> 3, (uint32_t)q, kPurposeAction), k0, k1);
-                lvl = random_level(w, g, p.n_levels);
-            }
             float soc = b.soc[i], erem = b.erem[i];
             const float cap = b.cap[i];
-            P = clip_power(lvl, dc, soc, erem, cap, b.rbar[i], p);
+            P = clip(level_of(q), dc, soc, erem, cap, b.rbar[i]);
             P = P * gscale[(m >> kMetaGroupShift) & 31] * s_root;
             const float dE = P * p.dt;
             soc = fminf(soc + __fdividef(dE, cap), 1.0f);
+            if (V2G) soc = fmaxf(soc, 0.0f);
             erem = fmaxf(erem - dE, 0.0f);
             tr -= 1;
             if (tr == 0) {
@@ -107,6 +122,14 @@ __global__ void __launch_bounds__(128) k_step_plain(DevBatch b, DevParams p, con
     }
     const float e_net = s_grp * s_root * p.dt;
     const float e_grid = se_grp * s_root * p.dt;
+    float e_to = 0.f, e_b = 0.f;
+    if (V2G) {
+        e_to = sn_grp * s_root * p.dt;
+        const float pb_applied = Pb * s_root;
+        e_b = pb_applied * p.dt;
+        b.bsoc[s] = fminf(fmaxf(bsoc + e_b * p.inv_batt_cap, 0.0f), 1.0f);
+        b.bp[s] = pb_applied;
+    }
 
     // -- (iv) arrivals: Poisson count, first come first served
     const int M = arrivals(b, p, (uint32_t)uid, g, t, b.arrival_class[s], k0, k1);
@@ -121,10 +144,19 @@ __global__ void __launch_bounds__(128) k_step_plain(DevBatch b, DevParams p, con
         ++j;
     }
 
-    // -- reward, Appendix A.3 (no discharge: E_grid,net = energy bought)
+    // -- reward, Appendix A.3: E_grid,net = bought + pushed into the grid + battery
     const float price = __ldg(b.price + (size_t)b.day[s] * (size_t)p.ep_len + (size_t)t);
-    const float profit = p.p_sell * e_net - price * e_grid - p.c_fixed;
-    const float r = profit - p.a_sat * c_sat - p.a_decl * (float)(M - m_adm) - p.a_con * c_con;
+    float r;
+    if (V2G) {
+        const float e_gn = e_grid + e_to + e_b;
+        const float pg = e_gn > 0.f ? price : p.sell_grid_ratio * price;
+        const float degrad = fmaxf(-e_b, 0.0f) - e_to;
+        r = p.p_sell * e_net - pg * e_gn - p.c_fixed - p.a_sat * c_sat - p.a_decl * (float)(M - m_adm) -
+            p.a_con * c_con - p.a_degrad * degrad;
+    } else {
+        const float profit = p.p_sell * e_net - price * e_grid - p.c_fixed;
+        r = profit - p.a_sat * c_sat - p.a_decl * (float)(M - m_adm) - p.a_con * c_con;
+    }
 
     b.ncar[s] = ncar + (uint32_t)m_adm;
     b.st_arrived[s] += (uint32_t)m_adm;
@@ -143,6 +175,10 @@ __global__ void __launch_bounds__(128) k_step_plain(DevBatch b, DevParams p, con
             const long long i = pb + q;
             b.soc[i] = 0.f; b.erem[i] = 0.f; b.cap[i] = 0.f; b.rbar[i] = 0.f; b.pw[i] = 0.f; b.trem[i] = 0;
         }
+        if (V2G) {
+            b.bsoc[s] = p.batt_soc0;
+            b.bp[s] = 0.f;
+        }
         t1 = 0;
         b.day[s] = draw_day((uint32_t)uid, g, 0u, k0, k1, p.n_days);
     }
@@ -153,13 +189,29 @@ __global__ void __launch_bounds__(128) k_step_plain(DevBatch b, DevParams p, con
     if (done) done[uid] = fin;
 }
 
+template <bool V2G>
+__global__ void __launch_bounds__(128) k_step_plain(DevBatch b, DevParams p, const int8_t* __restrict__ actions,
+                                                    long long lda, float* __restrict__ reward,
+                                                    uint8_t* __restrict__ done, const int* __restrict__ slot_list,
+                                                    int n_list)
+{
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (slot_list ? n_list : b.n_slots)) return;
+    step_station<V2G>(b, p, actions, lda, reward, done, slot_list ? slot_list[idx] : idx);
+}
+
 void launch_step_plain(const DevBatch& b, const DevParams& p, const int8_t* actions, long long lda, float* reward,
                        uint8_t* done, const int* slot_list, int n_list, cudaStream_t st)
 {
     const int n = slot_list ? n_list : b.n_slots;
     if (n <= 0) return;
     const int threads = 128;
-    k_step_plain<<<(n + threads - 1) / threads, threads, 0, st>>>(b, p, actions, lda, reward, done, slot_list, n_list);
+    if (p.v2g)
+        k_step_plain<true><<<(n + threads - 1) / threads, threads, 0, st>>>(b, p, actions, lda, reward, done, slot_list,
+                                                                              n_list);
+    else
+        k_step_plain<false><<<(n + threads - 1) / threads, threads, 0, st>>>(b, p, actions, lda, reward, done,
+                                                                               slot_list, n_list);
 }
 
 }  // namespace chx

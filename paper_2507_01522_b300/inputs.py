@@ -258,6 +258,15 @@ def heterogeneous(n_envs: int = 65536, seed: int = 0, classes=(8, 16, 32, 64)) -
     return Workload(f"hetero-{n_envs}-8/16/32/64", p, st, exo, seed)
 
 
+def v2g_variant(w: Workload, n_levels: int = 21, batt_cap_kwh: float = 150.0, batt_rate_kw: float = 60.0) -> Workload:
+    """The same stations in vehicle-to-grid mode: 21 signed levels (-100 %
+    .. +100 % in 10 % steps), a 150 kWh / 60 kW station battery starting
+    half full, feed-in at 0.8 x the buy price, 0.02 EUR per discharged kWh."""
+    p = EnvParams(**{**w.params.__dict__, "v2g": 1, "n_levels": n_levels, "batt_cap_kwh": batt_cap_kwh,
+                     "batt_rate_kw": batt_rate_kw})
+    return Workload(w.name + "-v2g", p, w.stations, w.exo, w.seed)
+
+
 def rollout_stations(n_envs: int = 16384, seed: int = 0) -> Workload:
     """16384 stations x 32 AC chargers (22 kW) in groups of 8 at 80 kW, grid
     9 kW x 32."""
