@@ -17,7 +17,7 @@ from test_gpu_parity import odd_sizes, stressed
 pytestmark = pytest.mark.gpu
 
 V2G = dict(v2g=1, n_levels=21, sell_grid_ratio=0.8, alpha_degrad=0.02, batt_cap_kwh=150.0, batt_rate_kw=60.0,
-           batt_tau=0.8, batt_soc0=0.5)
+           batt_tau=0.7, batt_soc0=0.5)
 
 
 def v2g(w):

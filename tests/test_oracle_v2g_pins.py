@@ -107,11 +107,13 @@ def test_single_car_discharge_closed_form(eta):
     np.testing.assert_allclose(rews, expect_r, rtol=1e-12, atol=1e-12)
 
 
-def test_battery_closed_form_and_two_case_profit():
+@pytest.mark.parametrize("tau", [0.8, 0.65])
+def test_battery_closed_form_and_two_case_profit(tau):
     """No cars: the battery charges at its full rate from the grid (buy
     price), then discharges (sell-back price, degradation cost); its SoC
-    follows the bulk/taper closed forms in both directions."""
-    price, ratio, Cb, rate, tau = float(np.float32(0.3)), 0.7, 200.0, 60.0, 0.8
+    follows the bulk/taper closed forms in both directions, with the
+    battery's own taper knee (0.65 differs from the cars' 0.8)."""
+    price, ratio, Cb, rate = float(np.float32(0.3)), 0.7, 200.0, 60.0
     w = hand_workload(n_ports=2, price=price, alpha_sat=0.0, alpha_decl=0.0, c_fixed=0.01, sell_grid_ratio=ratio,
                       alpha_degrad=0.05, batt_cap_kwh=Cb, batt_rate_kw=rate, batt_tau=tau, batt_soc0=0.5, **V2G)
     o = Oracle(w)
