@@ -45,6 +45,7 @@ class _Params(C.Structure):
         ("v2g", C.c_int32), ("sell_grid_ratio", C.c_double), ("alpha_degrad", C.c_double),
         ("batt_cap_kwh", C.c_double), ("batt_rate_kw", C.c_double), ("batt_tau", C.c_double),
         ("batt_soc0", C.c_double),
+        ("action_delta", C.c_int32), ("p_max_dis_kw", C.c_double * 2),
     ]
 
 
@@ -120,6 +121,10 @@ def params_struct(p) -> _Params:
     s.v2g = int(p.v2g); s.sell_grid_ratio = p.sell_grid_ratio; s.alpha_degrad = p.alpha_degrad
     s.batt_cap_kwh = p.batt_cap_kwh; s.batt_rate_kw = p.batt_rate_kw; s.batt_tau = p.batt_tau
     s.batt_soc0 = p.batt_soc0
+    s.action_delta = int(p.action_delta)
+    pd = p.p_max_kw if p.p_max_dis_kw is None else p.p_max_dis_kw
+    for k in range(2):
+        s.p_max_dis_kw[k] = pd[k]
     return s
 
 

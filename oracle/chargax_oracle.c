@@ -56,6 +56,10 @@ typedef struct orc_params {
     double sell_grid_ratio;
     double alpha_degrad;
     double batt_cap_kwh, batt_rate_kw, batt_tau, batt_soc0;
+    /* Delta-current action form (A.2 "Apply Actions"): the level is an
+     * increment of the charger's (battery's) last applied power */
+    int32_t action_delta;
+    double p_max_dis_kw[2]; /* discharge maximum I_max<- per charger type (V2G) */
 } orc_params;
 
 typedef struct orc {
@@ -347,20 +351,26 @@ void orc_policy_uniforms(const orc *o, int32_t n_ports, double *u)
 /* index n_ports.                                                           */
 /* ------------------------------------------------------------------------ */
 
-/* signed V2G request of level k: (k - h)/h of the maximum, h = (L-1)/2 */
-static double v2g_request(const orc *o, int32_t k, double pmax)
+/* Requested power of level k (A.2 "Apply Actions"; discretisation of
+ * "Practical Considerations").  Absolute form: k/(L-1) of the maximum, or
+ * in V2G mode the signed (k - h)/h of it, h = (L-1)/2.  Delta-current form:
+ * the last applied power plus the signed increment (k - h)/h of the
+ * maximum, I_drawn(t - dt) + a(t). */
+static double request(const orc *o, int32_t k, double pmax, double last)
 {
-    const int32_t h = (o->p.n_levels - 1) / 2;
-    return (double)(k - h) / (double)h * pmax;
+    const int32_t L = o->p.n_levels, h = (L - 1) / 2;
+    if (o->p.action_delta) return last + (double)(k - h) / (double)h * pmax;
+    if (o->p.v2g) return (double)(k - h) / (double)h * pmax;
+    return (double)k / (double)(L - 1) * pmax;
 }
 
-/* V2G clip (A.2 "Apply Actions", negative branch): charge as in the
+/* V2G clip (A.2 "Apply Actions", both branches): charge as in the
  * charge-only mode; discharge limited by the request, the car's discharging
- * rate (the charging curve flipped at SoC = 0.5: r_hat(1 - SoC)), the port
- * maximum and SoC >= 0.  Pinned by the closed-form discharge trajectory and
- * by the reduction to the charge-only mode. */
+ * rate (the charging curve flipped at SoC = 0.5: r_hat(1 - SoC)), the port's
+ * discharge maximum I_max<- and SoC >= 0.  Pinned by the closed-form
+ * discharge trajectory and by the reduction to the charge-only mode. */
 static double v2g_clip(double preq, double soc, double erem, double cap, double rbar, double tau, double pmax,
-                       double dt)
+                       double pmax_dis, double dt)
 {
     if (preq >= 0.0) {
         double P = preq, rhat = orc_taper(soc, rbar, tau);
@@ -373,7 +383,7 @@ static double v2g_clip(double preq, double soc, double erem, double cap, double 
     }
     double D = -preq, rdis = orc_taper(1.0 - soc, rbar, tau), soc_cap = soc * cap / dt;
     if (rdis < D) D = rdis;
-    if (pmax < D) D = pmax;
+    if (pmax_dis < D) D = pmax_dis;
     if (soc_cap < D) D = soc_cap;
     return D < 0.0 ? 0.0 : -D;
 }
@@ -402,11 +412,11 @@ void orc_step(orc *o, const int8_t *actions, int64_t lda, double *reward, uint8_
                                     : orc_random_action(o, e, g, (int32_t)(i - p0));
                 int ty = o->port_type[i];
                 double pmax = p->p_max_kw[ty];
+                double preq = request(o, k, pmax, o->pw[i]);
                 if (v2g) {
-                    P = v2g_clip(v2g_request(o, k, pmax), o->soc[i], o->erem[i], o->cap[i], o->rbar[i], p->tau,
-                                 pmax, dt);
+                    P = v2g_clip(preq, o->soc[i], o->erem[i], o->cap[i], o->rbar[i], p->tau, pmax,
+                                 p->p_max_dis_kw[ty], dt);
                 } else {
-                    double preq = (double)k / (double)(p->n_levels - 1) * pmax;
                     double rhat = orc_taper(o->soc[i], o->rbar[i], p->tau);
                     double soc_cap = (1.0 - o->soc[i]) * o->cap[i] / dt;
                     double dem_cap = o->erem[i] / dt;
@@ -425,8 +435,8 @@ void orc_step(orc *o, const int8_t *actions, int64_t lda, double *reward, uint8_
         if (v2g) {
             int32_t kb = actions ? (int32_t)actions[(p1 + e) * lda] : orc_random_action(o, e, g, o->n_ports[e]);
             /* the battery never leaves: its remaining demand never binds */
-            Pb = v2g_clip(v2g_request(o, kb, p->batt_rate_kw), o->bsoc[e], 1e300, p->batt_cap_kwh, p->batt_rate_kw,
-                          p->batt_tau, p->batt_rate_kw, dt);
+            Pb = v2g_clip(request(o, kb, p->batt_rate_kw, o->bp[e]), o->bsoc[e], 1e300, p->batt_cap_kwh,
+                          p->batt_rate_kw, p->batt_tau, p->batt_rate_kw, p->batt_rate_kw, dt);
         }
 
         /* Architecture constraint, Eq. (ArchConst): for every subtree H,
@@ -511,6 +521,10 @@ void orc_step(orc *o, const int8_t *actions, int64_t lda, double *reward, uint8_
             if (o->scratch_leave[i]) {
                 c_sat += o->erem[i] > 0.0 ? o->erem[i] : 0.0;
                 clear_port(o, i);
+                /* Delta form: the charger of a departed car drops to 0, the
+                 * base of the next car's first increment (an arriving car's
+                 * port state starts at I_drawn = 0) */
+                if (p->action_delta) o->pw[i] = 0.0;
                 departed += 1;
             }
         }

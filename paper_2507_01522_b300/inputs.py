@@ -64,6 +64,11 @@ class EnvParams:
     batt_rate_kw: float = 60.0
     batt_tau: float = 0.8
     batt_soc0: float = 0.5
+    # discharge maximum per charger type (I_max<-); None = the charging maximum
+    p_max_dis_kw: tuple | None = None
+    # action form: 0 = absolute levels, 1 = increments of the last applied
+    # power (Delta-current form of A.2 "Apply Actions"; n_levels odd)
+    action_delta: int = 0
 
 
 @dataclasses.dataclass
