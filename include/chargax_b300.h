@@ -95,6 +95,18 @@ typedef struct chx_env_params {
     float batt_rate_kw;
     float batt_tau;
     float batt_soc0;
+    /* Action form (A.2 "Apply Actions"): action_delta = 0 takes the level as
+     * an absolute request (above); action_delta = 1 takes it as an increment
+     * of the charger's last applied power, the Delta-current form: level k
+     * (n_levels odd, h = (n_levels-1)/2) requests last + (k - h)/h x the
+     * charger maximum, clipped as above (at 0 from below without V2G).  In
+     * this form a departing car's charger drops to 0 power, so the next car
+     * starts from 0.  The battery's level is an increment of its last power
+     * alike. */
+    int32_t action_delta;
+    /* Discharge maximum I_max<- per charger type, > 0 (V2G mode; the
+     * discharge branch of the clip caps at it instead of p_max_kw). */
+    float p_max_dis_kw[2];
 } chx_env_params;
 
 /* A batch of stations, CSR.  Groups of a station are contiguous charger

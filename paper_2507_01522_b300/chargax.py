@@ -51,6 +51,7 @@ class _Params(C.Structure):
         ("v2g", C.c_int32), ("sell_grid_ratio", C.c_float), ("alpha_degrad", C.c_float),
         ("batt_cap_kwh", C.c_float), ("batt_rate_kw", C.c_float), ("batt_tau", C.c_float),
         ("batt_soc0", C.c_float),
+        ("action_delta", C.c_int32), ("p_max_dis_kw", C.c_float * 2),
     ]
 
 
@@ -176,6 +177,10 @@ def params_struct(p: "_inputs.EnvParams") -> _Params:
     s.v2g = int(p.v2g); s.sell_grid_ratio = p.sell_grid_ratio; s.alpha_degrad = p.alpha_degrad
     s.batt_cap_kwh = p.batt_cap_kwh; s.batt_rate_kw = p.batt_rate_kw; s.batt_tau = p.batt_tau
     s.batt_soc0 = p.batt_soc0
+    s.action_delta = int(p.action_delta)
+    pd = p.p_max_kw if p.p_max_dis_kw is None else p.p_max_dis_kw
+    for k in range(2):
+        s.p_max_dis_kw[k] = pd[k]
     return s
 
 

@@ -50,7 +50,10 @@ struct DevParams {
     float obs_inv_stay, obs_inv_cap, obs_inv_days, obs_inv_len;
     float inv_pmax0, inv_pmax1;            // 1 / maximum power (FP32, correctly rounded), per type
     // vehicle-to-grid mode (signed levels, station battery)
-    int v2g, half;                         // half = (n_levels - 1) / 2: level k requests (k - half) * lvl
+    int v2g, half;                         // level k requests (k - half) * lvl: half = (n_levels - 1) / 2 in
+                                           // V2G mode or the Delta form, else 0
+    int delta;                             // Delta-current form: requests add to the last applied power
+    float pdis0, pdis1;                    // discharge maximum I_max<- per type (V2G)
     float eta0, eta1;                      // charger efficiency per type (discharge losses)
     float batt_cap, inv_batt_cap, batt_rate, batt_lvl, batt_tau, batt_inv_1m_tau, batt_soc0;
     float sell_grid_ratio, a_degrad, obs_inv_batt_rate;
@@ -143,13 +146,30 @@ __device__ __forceinline__ float taper(float soc, float rbar, const DevParams& p
     return soc <= p.tau ? rbar : (1.0f - soc) * rbar * p.inv_1m_tau;
 }
 
+// requested power of action level k (A.2 "Apply Actions", discretised):
+// (k - half) * step, half = 0 for absolute charge-only levels; in the
+// Delta-current form the increment adds to the last applied power
+__device__ __forceinline__ float request(int level, float step, float last, const DevParams& p)
+{
+    const float a = (float)(level - p.half) * step;
+    return p.delta ? last + a : a;
+}
+
+// the same with the form fixed at compile time (SIGNED: V2G or Delta form)
+template <bool SIGNED, bool DELTA>
+__device__ __forceinline__ float request_t(int level, float step, float last, const DevParams& p)
+{
+    const float a = (float)(SIGNED ? level - p.half : level) * step;
+    return DELTA ? last + a : a;
+}
+
 // per-charger clip of Appendix A.2 "Apply Actions" (power form): requested
-// level, car rate r_hat, charger maximum, SoC <= 1 and demand >= 0 caps
-__device__ __forceinline__ float clip_power(int level, bool dc, float soc, float erem, float cap, float rbar,
+// power, car rate r_hat, charger maximum, SoC <= 1 and demand >= 0 caps,
+// and 0 from below
+__device__ __forceinline__ float clip_power(float preq, bool dc, float soc, float erem, float cap, float rbar,
                                             const DevParams& p)
 {
     const float pmax = dc ? p.pmax1 : p.pmax0;
-    const float preq = (float)level * (dc ? p.lvl1 : p.lvl0);
     const float rhat = taper(soc, rbar, p);
     const float soc_cap = (1.0f - soc) * cap * p.inv_dt;
     const float dem_cap = erem * p.inv_dt;
@@ -157,16 +177,15 @@ __device__ __forceinline__ float clip_power(int level, bool dc, float soc, float
     return fmaxf(P, 0.0f);
 }
 
-// V2G clip (A.2 "Apply Actions", both branches): level k requests
-// (k - half) * lvl; charging as clip_power, discharging limited by the
-// request, the car's discharging rate (the charging curve flipped at
-// SoC = 0.5: r_hat(1 - SoC)), the charger maximum and SoC >= 0
-__device__ __forceinline__ float clip_power_v2g(int level, bool dc, float soc, float erem, float cap, float rbar,
+// V2G clip (A.2 "Apply Actions", both branches) of a signed request:
+// charging as clip_power, discharging limited by the request, the car's
+// discharging rate (the charging curve flipped at SoC = 0.5: r_hat(1 - SoC)),
+// the charger's discharge maximum I_max<- and SoC >= 0
+__device__ __forceinline__ float clip_power_v2g(float preq, bool dc, float soc, float erem, float cap, float rbar,
                                                 const DevParams& p)
 {
-    const float pmax = dc ? p.pmax1 : p.pmax0;
-    const float preq = (float)(level - p.half) * (dc ? p.lvl1 : p.lvl0);
     if (preq >= 0.f) {
+        const float pmax = dc ? p.pmax1 : p.pmax0;
         const float rhat = taper(soc, rbar, p);
         const float soc_cap = (1.0f - soc) * cap * p.inv_dt;
         const float dem_cap = erem * p.inv_dt;
@@ -175,14 +194,13 @@ __device__ __forceinline__ float clip_power_v2g(int level, bool dc, float soc, f
     // r_hat(1 - SoC) written without forming 1 - (1 - SoC) (cancellation in FP32)
     const float rdis = 1.0f - soc <= p.tau ? rbar : soc * rbar * p.inv_1m_tau;
     const float soc_cap = soc * cap * p.inv_dt;
-    return -fmaxf(fminf(fminf(-preq, rdis), fminf(pmax, soc_cap)), 0.0f);
+    return -fmaxf(fminf(fminf(-preq, rdis), fminf(dc ? p.pdis1 : p.pdis0, soc_cap)), 0.0f);
 }
 
 // the station battery's power (V2G): the same two branches with its own
 // rate curve and SoC in [0, 1]; it never leaves, so no demand cap
-__device__ __forceinline__ float clip_battery(int level, float bsoc, const DevParams& p)
+__device__ __forceinline__ float clip_battery(float preq, float bsoc, const DevParams& p)
 {
-    const float preq = (float)(level - p.half) * p.batt_lvl;
     if (preq >= 0.f) {
         const float rhat = bsoc <= p.batt_tau ? p.batt_rate : (1.0f - bsoc) * p.batt_rate * p.batt_inv_1m_tau;
         return fmaxf(fminf(fminf(preq, rhat), (1.0f - bsoc) * p.batt_cap * p.inv_dt), 0.0f);

@@ -92,7 +92,13 @@ int validate_params(const chx_env_params* p, const chx_exo* x)
         if (!(p->sell_grid_ratio >= 0.f) || !std::isfinite(p->sell_grid_ratio))
             return fail(CHX_EINVAL, "sell_grid_ratio must be >= 0");
         if (!std::isfinite(p->alpha_degrad)) return fail(CHX_EINVAL, "alpha_degrad must be finite");
+        for (int t = 0; t < 2; ++t)
+            if (!(p->p_max_dis_kw[t] > 0.f) || !std::isfinite(p->p_max_dis_kw[t]))
+                return fail(CHX_EINVAL, "p_max_dis_kw must be > 0");
     }
+    if (p->action_delta != 0 && p->action_delta != 1) return fail(CHX_EINVAL, "action_delta must be 0 or 1");
+    if (p->action_delta && (p->n_levels < 3 || (p->n_levels & 1) == 0))
+        return fail(CHX_EINVAL, "the Delta action form needs an odd n_levels >= 3 (increments symmetric around 0)");
     if (x->n_days < 1 || !x->h_price) return fail(CHX_EINVAL, "price bank missing");
     if (x->n_arrival_classes < 1 || !x->h_arrival_rate) return fail(CHX_EINVAL, "arrival table missing");
     const size_t nl = (size_t)x->n_arrival_classes * (size_t)p->ep_len;
@@ -188,8 +194,11 @@ DevParams make_params(const chx_env_params& q, int n_days)
     p.pmax0 = q.p_max_kw[0];
     p.pmax1 = q.p_max_kw[1];
     p.v2g = q.v2g ? 1 : 0;
-    p.half = p.v2g ? (q.n_levels - 1) / 2 : 0;
-    const double per_level = p.v2g ? (double)p.half : (double)(q.n_levels - 1);
+    p.delta = q.action_delta ? 1 : 0;
+    p.half = (p.v2g || p.delta) ? (q.n_levels - 1) / 2 : 0;
+    const double per_level = p.half ? (double)p.half : (double)(q.n_levels - 1);
+    p.pdis0 = p.v2g ? q.p_max_dis_kw[0] : q.p_max_kw[0];
+    p.pdis1 = p.v2g ? q.p_max_dis_kw[1] : q.p_max_kw[1];
     p.lvl0 = (float)((double)q.p_max_kw[0] / per_level);
     p.lvl1 = (float)((double)q.p_max_kw[1] / per_level);
     p.eta0 = q.eta_port[0];

@@ -634,7 +634,7 @@ __device__ __forceinline__ void owner_step(Owner& o, const RolloutArgs& R, int i
             const uint32_t meta = vp[i] >> 8;
             const int lvl = (int)((lv[ci >> 2] >> (8 * (ci & 3))) & 0xFFu);
             const bool dc = meta & kMetaDC;
-            P[ci] = trem > 0 ? clip_power(lvl, dc, __uint_as_float(vs[i]), __uint_as_float(ve[i]),
+            P[ci] = trem > 0 ? clip_power((float)lvl * (dc ? p.lvl1 : p.lvl0), dc, __uint_as_float(vs[i]), __uint_as_float(ve[i]),
                                           __uint_as_float(vc[i]), __uint_as_float(vr[i]), p)
                              : 0.f;
             raw += P[ci];

@@ -196,7 +196,7 @@ struct WarpSmem {
 // station's lanes, its level after the chargers' or drawn at charger index
 // n), signed limits, discharge energy after the port loss, two-case profit,
 // degradation penalty; observation with the battery features.
-template <int C, bool V2G>
+template <int C, bool V2G, bool DELTA>
 __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, const FusedIO& io, int tile,
                                          WarpSmem* ws)
 {
@@ -312,10 +312,11 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
                 }
             }
             const bool dc = meta[q] & kMetaDC;
+            const float preq = request_t<V2G || DELTA, DELTA>(lvl, dc ? p.lvl1 : p.lvl0, pw[q], p);
             if (V2G)
-                P[q] = trem[q] > 0 ? clip_power_v2g(lvl, dc, soc[q], erem[q], cap[q], rbar[q], p) : 0.f;
+                P[q] = trem[q] > 0 ? clip_power_v2g(preq, dc, soc[q], erem[q], cap[q], rbar[q], p) : 0.f;
             else
-                P[q] = trem[q] > 0 ? clip_power(lvl, dc, soc[q], erem[q], cap[q], rbar[q], p) : 0.f;
+                P[q] = trem[q] > 0 ? clip_power(preq, dc, soc[q], erem[q], cap[q], rbar[q], p) : 0.f;
         }
         // the battery's request (V2G; computed alike in every lane of the station)
         float Pb = 0.f;
@@ -333,7 +334,7 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
                     lvl = min(max(lvl, 0), p.n_levels - 1);
                 }
             }
-            Pb = clip_battery(lvl, bsoc, p);
+            Pb = clip_battery(request_t<true, DELTA>(lvl, p.batt_lvl, bpw, p), bsoc, p);
         }
 
         // ---- architecture constraint: group nodes (segmented scan), then root
@@ -417,6 +418,7 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
                 if (leave & (1u << q)) {
                     v += erem[q];
                     soc[q] = 0.f; erem[q] = 0.f; cap[q] = 0.f; rbar[q] = 0.f;
+                    if (DELTA) pw[q] = 0.f;        // Delta form: the next car starts from 0
                 }
             }
             c_sat = seg_sum<LPE>(v);
@@ -577,7 +579,7 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
 // instantiation for the 128-charger class (4 chargers per lane, more
 // registers), one for the others, so the smaller classes keep more warps
 // resident.
-template <int CLO, int CHI, int MINB, bool V2G>
+template <int CLO, int CHI, int MINB, bool V2G, bool DELTA>
 __global__ void __launch_bounds__(256, MINB) k_step_fused(DevBatch b, DevParams p, FusedIO io)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -602,21 +604,24 @@ __global__ void __launch_bounds__(256, MINB) k_step_fused(DevBatch b, DevParams 
                 tile = tile_id - io.sched_tile_base[i];
             }
         }
-        if (CLO <= 0 && 0 <= CHI && cls == 0) run_tile<8, V2G>(b, p, io, tile, ws);
-        if (CLO <= 1 && 1 <= CHI && cls == 1) run_tile<16, V2G>(b, p, io, tile, ws);
-        if (CLO <= 2 && 2 <= CHI && cls == 2) run_tile<32, V2G>(b, p, io, tile, ws);
-        if (CLO <= 3 && 3 <= CHI && cls == 3) run_tile<64, V2G>(b, p, io, tile, ws);
-        if (CLO <= 4 && 4 <= CHI && cls == 4) run_tile<128, V2G>(b, p, io, tile, ws);
+        if (CLO <= 0 && 0 <= CHI && cls == 0) run_tile<8, V2G, DELTA>(b, p, io, tile, ws);
+        if (CLO <= 1 && 1 <= CHI && cls == 1) run_tile<16, V2G, DELTA>(b, p, io, tile, ws);
+        if (CLO <= 2 && 2 <= CHI && cls == 2) run_tile<32, V2G, DELTA>(b, p, io, tile, ws);
+        if (CLO <= 3 && 3 <= CHI && cls == 3) run_tile<64, V2G, DELTA>(b, p, io, tile, ws);
+        if (CLO <= 4 && 4 <= CHI && cls == 4) run_tile<128, V2G, DELTA>(b, p, io, tile, ws);
     }
 }
 
 namespace {
 
-// [v2g]: the charge-only and the vehicle-to-grid instantiations
-void (*const kSmallKernel[2])(DevBatch, DevParams, FusedIO) = {&k_step_fused<0, 3, 3, false>,
-                                                                &k_step_fused<0, 3, 3, true>};
-void (*const kLargeKernel[2])(DevBatch, DevParams, FusedIO) = {&k_step_fused<4, 4, 2, false>,
-                                                                &k_step_fused<4, 4, 2, true>};
+// [v2g | delta << 1]: charge-only / vehicle-to-grid, absolute / Delta-current levels
+constexpr int kForms = 4;
+void (*const kSmallKernel[kForms])(DevBatch, DevParams, FusedIO) = {
+    &k_step_fused<0, 3, 3, false, false>, &k_step_fused<0, 3, 3, true, false>,
+    &k_step_fused<0, 3, 3, false, true>, &k_step_fused<0, 3, 3, true, true>};
+void (*const kLargeKernel[kForms])(DevBatch, DevParams, FusedIO) = {
+    &k_step_fused<4, 4, 2, false, false>, &k_step_fused<4, 4, 2, true, false>,
+    &k_step_fused<4, 4, 2, false, true>, &k_step_fused<4, 4, 2, true, true>};
 
 // the part of a schedule whose classes lie in [clo, chi], tiles renumbered
 FusedIO sub_schedule(const FusedIO& io, int clo, int chi, int* counter)
@@ -642,7 +647,7 @@ FusedIO sub_schedule(const FusedIO& io, int clo, int chi, int* counter)
 bool raise_smem_limit()
 {
     static const bool ok = [] {
-        for (int v = 0; v < 2; ++v)
+        for (int v = 0; v < kForms; ++v)
             if (cudaFuncSetAttribute((const void*)kSmallKernel[v], cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      8 * (int)sizeof(WarpSmem)) != cudaSuccess ||
                 cudaFuncSetAttribute((const void*)kLargeKernel[v], cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -668,7 +673,7 @@ int blocks_per_sm(const void* kernel, int threads)
 bool fused_block_size_ok(int threads)
 {
     if (threads < 32 || threads > 256 || threads % 32 != 0) return false;
-    for (int v = 0; v < 2; ++v)
+    for (int v = 0; v < kForms; ++v)
         if (blocks_per_sm((const void*)kSmallKernel[v], threads) <= 0 ||
             blocks_per_sm((const void*)kLargeKernel[v], threads) <= 0)
             return false;
@@ -682,7 +687,7 @@ void launch_step_fused(const DevBatch& b, const DevParams& p, const FusedIO& io,
     const size_t smem = (size_t)warps * sizeof(WarpSmem);
     const FusedIO big = sub_schedule(io, 4, 4, io.counter);
     const FusedIO small = sub_schedule(io, 0, 3, io.counter + 1);
-    const int v = p.v2g ? 1 : 0;
+    const int v = (p.v2g ? 1 : 0) | (p.delta ? 2 : 0);
     if (big.total_tiles > 0) {             // the heavy class first
         const int per_sm = blocks_per_sm((const void*)kLargeKernel[v], threads);
         const int blocks = std::max(1, std::min(per_sm * sm_count, (big.total_tiles + warps - 1) / warps));

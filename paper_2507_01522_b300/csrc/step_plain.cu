@@ -43,8 +43,9 @@ __device__ __forceinline__ void step_station(const DevBatch& b, const DevParams&
         }
         return lvl;
     };
-    auto clip = [&](int lvl, bool dc, float soc, float erem, float cap, float rbar) -> float {
-        return V2G ? clip_power_v2g(lvl, dc, soc, erem, cap, rbar, p) : clip_power(lvl, dc, soc, erem, cap, rbar, p);
+    auto clip = [&](int lvl, bool dc, float soc, float erem, float cap, float rbar, float last) -> float {
+        const float preq = request(lvl, dc ? p.lvl1 : p.lvl0, last, p);
+        return V2G ? clip_power_v2g(preq, dc, soc, erem, cap, rbar, p) : clip_power(preq, dc, soc, erem, cap, rbar, p);
     };
 
     // -- (i) apply actions: per-charger clip, then group sums (Eq. ArchConst)
@@ -55,7 +56,7 @@ __device__ __forceinline__ void step_station(const DevBatch& b, const DevParams&
         const uint32_t m = b.meta[i];
         const bool dc = m & kMetaDC;
         float P = 0.f;
-        if (b.trem[i] > 0) P = clip(level_of(q), dc, b.soc[i], b.erem[i], b.cap[i], b.rbar[i]);
+        if (b.trem[i] > 0) P = clip(level_of(q), dc, b.soc[i], b.erem[i], b.cap[i], b.rbar[i], b.pw[i]);
         S += P;
         if (V2G) {
             if (P >= 0.f) Se += P * (dc ? p.inv_eta1 : p.inv_eta0);
@@ -82,7 +83,7 @@ __device__ __forceinline__ void step_station(const DevBatch& b, const DevParams&
     float Pb = 0.f, bsoc = 0.f;
     if (V2G) {
         bsoc = b.bsoc[s];
-        Pb = clip_battery(level_of(n), bsoc, p);
+        Pb = clip_battery(request(level_of(n), p.batt_lvl, b.bp[s], p), bsoc, p);
     }
     const float grid_cap = b.grid_cap[s];
     const float s_tot = s_grp + Pb, mag = V2G ? fabsf(s_tot) : s_tot;
@@ -102,7 +103,7 @@ __device__ __forceinline__ void step_station(const DevBatch& b, const DevParams&
         if (tr > 0) {
             float soc = b.soc[i], erem = b.erem[i];
             const float cap = b.cap[i];
-            P = clip(level_of(q), dc, soc, erem, cap, b.rbar[i]);
+            P = clip(level_of(q), dc, soc, erem, cap, b.rbar[i], b.pw[i]);
             P = P * gscale[(m >> kMetaGroupShift) & 31] * s_root;
             const float dE = P * p.dt;
             soc = fminf(soc + __fdividef(dE, cap), 1.0f);
@@ -117,7 +118,8 @@ __device__ __forceinline__ void step_station(const DevBatch& b, const DevParams&
             }
             b.trem[i] = (uint8_t)tr;
         }
-        b.pw[i] = P;
+        // Delta form: a departed car's charger drops to 0, the next car's base
+        b.pw[i] = (p.delta && tr == 0) ? 0.f : P;
         n_free += (tr == 0);
     }
     const float e_net = s_grp * s_root * p.dt;

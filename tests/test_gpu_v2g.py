@@ -17,7 +17,7 @@ from test_gpu_parity import odd_sizes, stressed
 pytestmark = pytest.mark.gpu
 
 V2G = dict(v2g=1, n_levels=21, sell_grid_ratio=0.8, alpha_degrad=0.02, batt_cap_kwh=150.0, batt_rate_kw=60.0,
-           batt_tau=0.7, batt_soc0=0.5)
+           batt_tau=0.7, batt_soc0=0.5, p_max_dis_kw=(9.0, 100.0))
 
 
 def v2g(w):
@@ -120,10 +120,15 @@ def test_v2g_given_actions_discharge(cuda_lib, mode):
 @pytest.mark.parametrize("mode", ["plain", "fused"])
 def test_v2g_single_step_from_oracle_state(cuda_lib, mode):
     w, b, o, torch = make("stressed")
-    rng = np.random.default_rng(9)
+    check_single_steps(w, b, o, torch, mode, np.random.default_rng(9), lambda rng: v2g_actions(rng, b, 1)[:, 0])
+
+
+def check_single_steps(w, b, o, torch, mode, rng, draw, trials=3):
+    """From the oracle's state rounded to FP32 (shared by both sides), one
+    step with the levels draw(rng): events exact, floats within STEP_RTOL."""
     for _ in range(21):
         o.step(None)
-    for trial in range(3):
+    for trial in range(trials):
         s32 = to_f32_state(o.state())
         bo = o.battery()
         bs, bpw = bo["soc"].astype(np.float32), bo["p"].astype(np.float32)
@@ -131,7 +136,7 @@ def test_v2g_single_step_from_oracle_state(cuda_lib, mode):
         o.set_battery(bs.astype(np.float64), bpw.astype(np.float64))
         b.set_state(s32)
         b.set_battery(bs, bpw)
-        acts = v2g_actions(rng, b, 1)[:, 0]
+        acts = draw(rng)
         reward = torch.zeros(b.E, device="cuda")
         done = torch.zeros(b.E, dtype=torch.uint8, device="cuda")
         a = torch.from_numpy(acts).cuda()
