@@ -46,6 +46,8 @@ class _Params(C.Structure):
         ("batt_cap_kwh", C.c_double), ("batt_rate_kw", C.c_double), ("batt_tau", C.c_double),
         ("batt_soc0", C.c_double),
         ("action_delta", C.c_int32), ("p_max_dis_kw", C.c_double * 2),
+        ("cs_share_256", C.c_int32), ("alpha_sat1", C.c_double), ("beta_early", C.c_double),
+        ("eps_kwh", C.c_double),
     ]
 
 
@@ -80,6 +82,11 @@ def lib():
         L.orc_get_battery.argtypes = [vp, vp, vp]
         L.orc_set_battery.argtypes = [vp, vp, vp]
         L.orc_get_info_v2g.argtypes = [vp, vp, vp, vp, vp]
+        L.orc_obs_port_features.restype = i32
+        L.orc_obs_port_features.argtypes = [vp]
+        L.orc_get_due.argtypes = [vp, vp]
+        L.orc_set_due.argtypes = [vp, vp]
+        L.orc_get_info_cs.argtypes = [vp, vp, vp]
         L.orc_random_action.restype = i32
         L.orc_random_action.argtypes = [vp, i32, C.c_uint32, i32]
         _lib = L
@@ -125,6 +132,8 @@ def params_struct(p) -> _Params:
     pd = p.p_max_kw if p.p_max_dis_kw is None else p.p_max_dis_kw
     for k in range(2):
         s.p_max_dis_kw[k] = pd[k]
+    s.cs_share_256 = int(p.cs_share_256); s.alpha_sat1 = p.alpha_sat1; s.beta_early = p.beta_early
+    s.eps_kwh = p.eps_kwh
     return s
 
 
@@ -179,8 +188,12 @@ class Oracle:
     def obs_env_features(self) -> int:
         return int(lib().orc_obs_env_features(self.h))
 
+    @property
+    def obs_port_features(self) -> int:
+        return int(lib().orc_obs_port_features(self.h))
+
     def observe(self) -> np.ndarray:
-        o = np.zeros(self.obs_env_features * self.E + 6 * self.P, np.float64)
+        o = np.zeros(self.obs_env_features * self.E + self.obs_port_features * self.P, np.float64)
         lib().orc_observe(self.h, _ptr(o))
         return o
 
@@ -193,6 +206,21 @@ class Oracle:
         a = np.ascontiguousarray(soc, dtype=np.float64)
         b = np.ascontiguousarray(p, dtype=np.float64)
         lib().orc_set_battery(self.h, _ptr(a), _ptr(b))
+
+    def due(self) -> np.ndarray:
+        """Delta t_remain of charge-sensitive cars per port (0 elsewhere)."""
+        d = np.zeros(self.P, np.int32)
+        lib().orc_get_due(self.h, _ptr(d))
+        return d
+
+    def set_due(self, due):
+        a = np.ascontiguousarray(due, dtype=np.int32)
+        lib().orc_set_due(self.h, _ptr(a))
+
+    def info_cs(self) -> dict:
+        d = dict(csat1=np.zeros(self.E), margin=np.zeros(self.E))
+        lib().orc_get_info_cs(self.h, _ptr(d["csat1"]), _ptr(d["margin"]))
+        return d
 
     def info_v2g(self) -> dict:
         d = dict(e_to=np.zeros(self.E), e_b=np.zeros(self.E), degrad=np.zeros(self.E), e_grid_net=np.zeros(self.E))

@@ -34,6 +34,7 @@
 #define ORC_PURPOSE_ACTION 2u
 #define ORC_PURPOSE_DAY 3u
 #define ORC_PURPOSE_POLICY 4u
+#define ORC_TREM_CS 255       /* trem of a port holding a charge-sensitive car */
 
 typedef struct orc_params {
     int32_t ep_len;        /* steps per episode (24 h / dt)                     */
@@ -60,6 +61,12 @@ typedef struct orc_params {
      * increment of the charger's (battery's) last applied power */
     int32_t action_delta;
     double p_max_dis_kw[2]; /* discharge maximum I_max<- per charger type (V2G) */
+    /* charge-sensitive users (u = 1, A.1 User Profiles): a car's user is
+     * charge-sensitive iff the low byte of its first profile word is below
+     * cs_share_256; such a user leaves once Delta E_remain <= eps_kwh and
+     * costs alpha_sat1 * c_Sat,1 with early-leave weight beta_early */
+    int32_t cs_share_256;
+    double alpha_sat1, beta_early, eps_kwh;
 } orc_params;
 
 typedef struct orc {
@@ -74,7 +81,11 @@ typedef struct orc {
     float *price, *lam;                    /* [D][T], [C][T] as given           */
     /* per-port state (car-state + port state, Appendix A.1) */
     double *soc, *erem, *cap, *rbar, *pw;
-    int32_t *trem;                         /* remaining steps, 0 = empty port   */
+    int32_t *trem;                         /* remaining steps, 0 = empty port;
+                                              ORC_TREM_CS: a charge-sensitive car */
+    int32_t *due;                          /* Delta t_remain of a charge-sensitive
+                                              car (steps to its desired departure,
+                                              negative once overdue)              */
     /* per-env state */
     int32_t *tod, *day;
     uint32_t *gstep, *key0, *key1;
@@ -90,6 +101,9 @@ typedef struct orc {
     int32_t *inf_M, *inf_admitted, *inf_departed;
     double *inf_csat, *inf_ccon, *inf_enet, *inf_egrid, *inf_price, *inf_req_sum;
     double *inf_eto, *inf_eb, *inf_degrad, *inf_egrid_net;   /* V2G terms of the last step */
+    double *inf_csat1;                     /* c_Sat,1 of the last step                        */
+    double *inf_cs_margin;                 /* min |Delta E_remain - eps| over charge-sensitive
+                                              cars tested for departure in the last step      */
     double *scratch_p;                     /* per-port power within one step    */
     uint8_t *scratch_leave;                /* port's stay ended in this step    */
 } orc;
@@ -170,7 +184,7 @@ double orc_taper(double soc, double rbar, double tau)
 
 static void clear_port(orc *o, int64_t i)
 {
-    o->soc[i] = 0.0; o->erem[i] = 0.0; o->cap[i] = 0.0; o->rbar[i] = 0.0; o->trem[i] = 0;
+    o->soc[i] = 0.0; o->erem[i] = 0.0; o->cap[i] = 0.0; o->rbar[i] = 0.0; o->trem[i] = 0; o->due[i] = 0;
 }
 
 /* Episode start (Appendix "Practical Considerations", exploring starts): an
@@ -262,6 +276,7 @@ orc *orc_create(const orc_params *prm, int32_t E,
     o->scratch_p = (double *)xcalloc((size_t)P, sizeof(double));
     o->scratch_leave = (uint8_t *)xcalloc((size_t)P, 1);
     o->trem = (int32_t *)xcalloc((size_t)P, sizeof(int32_t));
+    o->due = (int32_t *)xcalloc((size_t)P, sizeof(int32_t));
     o->tod = (int32_t *)xcalloc((size_t)E, sizeof(int32_t));
     o->day = (int32_t *)xcalloc((size_t)E, sizeof(int32_t));
     o->gstep = (uint32_t *)xcalloc((size_t)E, sizeof(uint32_t));
@@ -292,6 +307,8 @@ orc *orc_create(const orc_params *prm, int32_t E,
     o->inf_egrid_net = (double *)xcalloc((size_t)E, sizeof(double));
     o->bsoc = (double *)xcalloc((size_t)E, sizeof(double));
     o->bp = (double *)xcalloc((size_t)E, sizeof(double));
+    o->inf_csat1 = (double *)xcalloc((size_t)E, sizeof(double));
+    o->inf_cs_margin = (double *)xcalloc((size_t)E, sizeof(double));
     orc_reset(o, NULL, 0, seed);
     return o;
 }
@@ -305,7 +322,8 @@ void orc_destroy(orc *o)
                     o->day, o->gstep, o->ncar, o->key0, o->key1, o->stream, o->ep_ret, o->last_ret, o->n_episodes,
                     o->st_arrived, o->st_rejected, o->st_missing, o->st_charged, o->inf_M, o->inf_admitted,
                     o->inf_departed, o->inf_csat, o->inf_ccon, o->inf_enet, o->inf_egrid, o->inf_price,
-                    o->inf_req_sum, o->inf_eto, o->inf_eb, o->inf_degrad, o->inf_egrid_net, o->bsoc, o->bp};
+                    o->inf_req_sum, o->inf_eto, o->inf_eb, o->inf_degrad, o->inf_egrid_net, o->bsoc, o->bp, o->due,
+                    o->inf_csat1, o->inf_cs_margin};
     for (size_t k = 0; k < sizeof(ptrs) / sizeof(ptrs[0]); ++k) free(ptrs[k]);
     free(o);
 }
@@ -503,10 +521,19 @@ void orc_step(orc *o, const int8_t *actions, int64_t lda, double *reward, uint8_
             o->bp[e] = Pb;
         }
 
-        /* time moves on: every stationed car has one step less to stay */
+        /* time moves on: every stationed car has one step less to stay; a
+         * time-sensitive user (u = 0) leaves when none is left, a
+         * charge-sensitive one (u = 1) once its demand is met, read as
+         * Delta E_remain <= eps_kwh (its Delta t_remain may turn negative) */
+        double cs_margin = 1e300;
         for (int64_t i = p0; i < p1; ++i) {
             o->scratch_leave[i] = 0;
-            if (o->trem[i] > 0) {
+            if (o->trem[i] == ORC_TREM_CS) {
+                o->due[i] -= 1;
+                o->scratch_leave[i] = (o->erem[i] <= p->eps_kwh);
+                double m = fabs(o->erem[i] - p->eps_kwh);
+                if (m < cs_margin) cs_margin = m;
+            } else if (o->trem[i] > 0) {
                 o->trem[i] -= 1;
                 o->scratch_leave[i] = (o->trem[i] == 0);
             }
@@ -515,11 +542,17 @@ void orc_step(orc *o, const int8_t *actions, int64_t lda, double *reward, uint8_
         /* (iii) Departure of Cars: time-sensitive users (u = 0) leave when no
          * time remains; the satisfaction penalty c_Sat,0 adds their missing
          * energy. */
-        double c_sat = 0.0;
+        double c_sat = 0.0, c_sat1 = 0.0;
         int32_t departed = 0;
         for (int64_t i = p0; i < p1; ++i) {
             if (o->scratch_leave[i]) {
-                c_sat += o->erem[i] > 0.0 ? o->erem[i] : 0.0;
+                if (o->trem[i] == ORC_TREM_CS) {
+                    /* c_Sat,1 (A.3): steps overdue, minus beta x steps early */
+                    int32_t d = o->due[i];
+                    c_sat1 += (d < 0 ? (double)-d : 0.0) - p->beta_early * (d > 0 ? (double)d : 0.0);
+                } else {
+                    c_sat += o->erem[i] > 0.0 ? o->erem[i] : 0.0;
+                }
                 clear_port(o, i);
                 /* Delta form: the charger of a departed car drops to 0, the
                  * base of the next car's first increment (an arriving car's
@@ -560,7 +593,14 @@ void orc_step(orc *o, const int8_t *actions, int64_t lda, double *reward, uint8_
             o->soc[i] = soc0;
             o->erem[i] = (want > 0.0 ? want : 0.0) * C;
             o->rbar[i] = rb;
-            o->trem[i] = stay;
+            /* user preference u (A.1 User Profiles): the low byte of the
+             * first word, unused by the capacity's 24 bits */
+            if ((int32_t)(c[0] & 0xFFu) < p->cs_share_256) {
+                o->trem[i] = ORC_TREM_CS;
+                o->due[i] = stay;
+            } else {
+                o->trem[i] = stay;
+            }
             j += 1;
         }
 
@@ -580,12 +620,14 @@ void orc_step(orc *o, const int8_t *actions, int64_t lda, double *reward, uint8_
         double c_degrad = (e_b < 0.0 ? -e_b : 0.0) - e_to;
         double r = profit - p->alpha_sat * c_sat - p->alpha_decl * (double)c_decl - p->alpha_con * c_con;
         if (v2g) r -= p->alpha_degrad * c_degrad;
+        r -= p->alpha_sat1 * c_sat1;
 
         o->ncar[e] += (uint32_t)m;
         o->inf_M[e] = M; o->inf_admitted[e] = m; o->inf_departed[e] = departed;
         o->inf_csat[e] = c_sat; o->inf_ccon[e] = c_con; o->inf_enet[e] = e_net;
         o->inf_egrid[e] = e_grid; o->inf_price[e] = price; o->inf_req_sum[e] = req_sum;
         o->inf_eto[e] = e_to; o->inf_eb[e] = e_b; o->inf_degrad[e] = c_degrad; o->inf_egrid_net[e] = e_grid_net;
+        o->inf_csat1[e] = c_sat1; o->inf_cs_margin[e] = cs_margin;
         o->st_arrived[e] += m; o->st_rejected[e] += c_decl;
         o->st_missing[e] += c_sat; o->st_charged[e] += e_net;
 
@@ -607,18 +649,20 @@ void orc_step(orc *o, const int8_t *actions, int64_t lda, double *reward, uint8_
 
 /* Observation (the state of Appendix "State summary" plus time of day, the
  * episode's day and a weekday flag, as the agent sees them).  Layout per env
- * at float offset F*e + 6*port_off[e]: F env features, then 6 per port;
+ * at float offset F*e + Q*port_off[e]: F env features, then Q per port;
  * F = 8, or 10 in V2G mode (+ battery SoC, battery power / its rate, the
- * battery state s_battery of A.1). */
+ * battery state s_battery of A.1); Q = 6, or 7 with charge-sensitive users
+ * (+ the user preference u; their stay feature is Delta t_remain). */
 int32_t orc_obs_env_features(const orc *o) { return o->p.v2g ? 10 : 8; }
+int32_t orc_obs_port_features(const orc *o) { return o->p.cs_share_256 > 0 ? 7 : 6; }
 
 void orc_observe(const orc *o, double *obs)
 {
     const orc_params *p = &o->p;
     const double two_pi = 6.283185307179586476925;
-    const int64_t F = orc_obs_env_features(o);
+    const int64_t F = orc_obs_env_features(o), Q = orc_obs_port_features(o);
     for (int32_t e = 0; e < o->E; ++e) {
-        double *ob = obs + F * (int64_t)e + 6 * o->port_off[e];
+        double *ob = obs + F * (int64_t)e + Q * o->port_off[e];
         int32_t t = o->tod[e], n = o->n_ports[e], occ = 0;
         for (int64_t i = o->port_off[e]; i < o->port_off[e + 1]; ++i) occ += o->trem[i] > 0;
         ob[0] = sin(two_pi * t / p->ep_len);
@@ -635,15 +679,16 @@ void orc_observe(const orc *o, double *obs)
         }
         for (int32_t q = 0; q < n; ++q) {
             int64_t i = o->port_off[e] + q;
-            double *op = ob + F + 6 * q;
+            double *op = ob + F + Q * q;
             double pmax = p->p_max_kw[o->port_type[i]];
-            int on = o->trem[i] > 0;
+            int on = o->trem[i] > 0, cs = o->trem[i] == ORC_TREM_CS;
             op[0] = on ? 1.0 : 0.0;
             op[1] = o->soc[i];
-            op[2] = (double)o->trem[i] / p->stay_steps[1];
+            op[2] = (double)(cs ? o->due[i] : o->trem[i]) / p->stay_steps[1];
             op[3] = on ? orc_taper(o->soc[i], o->rbar[i], p->tau) / pmax : 0.0;
             op[4] = o->pw[i] / pmax;
             op[5] = o->erem[i] / p->cap_kwh[1];
+            if (Q == 7) op[6] = cs ? 1.0 : 0.0;
         }
     }
 }
@@ -722,6 +767,19 @@ void orc_set_battery(orc *o, const double *soc, const double *pw)
 {
     memcpy(o->bsoc, soc, (size_t)o->E * sizeof(double));
     memcpy(o->bp, pw, (size_t)o->E * sizeof(double));
+}
+
+/* Delta t_remain of charge-sensitive cars per port (0 elsewhere). */
+void orc_get_due(const orc *o, int32_t *due) { memcpy(due, o->due, (size_t)o->P * sizeof(int32_t)); }
+void orc_set_due(orc *o, const int32_t *due) { memcpy(o->due, due, (size_t)o->P * sizeof(int32_t)); }
+
+/* c_Sat,1 of the last step per env, and the smallest distance of a tested
+ * charge-sensitive car's remaining demand from the departure threshold
+ * (1e300 when none was tested). */
+void orc_get_info_cs(const orc *o, double *csat1, double *margin)
+{
+    memcpy(csat1, o->inf_csat1, (size_t)o->E * sizeof(double));
+    memcpy(margin, o->inf_cs_margin, (size_t)o->E * sizeof(double));
 }
 
 /* V2G terms of the last step per env: energy pushed into the grid by cars

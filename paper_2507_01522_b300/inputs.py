@@ -69,6 +69,13 @@ class EnvParams:
     # action form: 0 = absolute levels, 1 = increments of the last applied
     # power (Delta-current form of A.2 "Apply Actions"; n_levels odd)
     action_delta: int = 0
+    # charge-sensitive users (u = 1): share in 256ths, weight of c_Sat,1 per
+    # step overdue, beta (weight of steps early), departure threshold on the
+    # remaining demand
+    cs_share_256: int = 0
+    alpha_sat1: float = 0.05
+    beta_early: float = 0.5
+    eps_kwh: float = 1e-4
 
 
 @dataclasses.dataclass
