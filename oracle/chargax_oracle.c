@@ -63,10 +63,12 @@ typedef struct orc_params {
     double p_max_dis_kw[2]; /* discharge maximum I_max<- per charger type (V2G) */
     /* charge-sensitive users (u = 1, A.1 User Profiles): a car's user is
      * charge-sensitive iff the low byte of its first profile word is below
-     * cs_share_256; such a user leaves once Delta E_remain <= eps_kwh and
-     * costs alpha_sat1 * c_Sat,1 with early-leave weight beta_early */
+     * cs_share_256; such a user leaves once its Delta E_remain is 0, read
+     * as: this step's charge covered it up to the relative slack eps_rel
+     * (remaining after <= eps_rel x remaining before); it costs
+     * alpha_sat1 * c_Sat,1 with early-leave weight beta_early */
     int32_t cs_share_256;
-    double alpha_sat1, beta_early, eps_kwh;
+    double alpha_sat1, beta_early, eps_rel;
 } orc_params;
 
 typedef struct orc {
@@ -102,9 +104,11 @@ typedef struct orc {
     double *inf_csat, *inf_ccon, *inf_enet, *inf_egrid, *inf_price, *inf_req_sum;
     double *inf_eto, *inf_eb, *inf_degrad, *inf_egrid_net;   /* V2G terms of the last step */
     double *inf_csat1;                     /* c_Sat,1 of the last step                        */
-    double *inf_cs_margin;                 /* min |Delta E_remain - eps| over charge-sensitive
-                                              cars tested for departure in the last step      */
+    double *inf_cs_margin;                 /* min over charge-sensitive cars tested in the last
+                                              step of |after/before - eps_rel| / eps_rel, their
+                                              distance from the departure decision            */
     double *scratch_p;                     /* per-port power within one step    */
+    double *scratch_e0;                    /* per-port remaining demand before the charge */
     uint8_t *scratch_leave;                /* port's stay ended in this step    */
 } orc;
 
@@ -274,6 +278,7 @@ orc *orc_create(const orc_params *prm, int32_t E,
     o->rbar = (double *)xcalloc((size_t)P, sizeof(double));
     o->pw = (double *)xcalloc((size_t)P, sizeof(double));
     o->scratch_p = (double *)xcalloc((size_t)P, sizeof(double));
+    o->scratch_e0 = (double *)xcalloc((size_t)P, sizeof(double));
     o->scratch_leave = (uint8_t *)xcalloc((size_t)P, 1);
     o->trem = (int32_t *)xcalloc((size_t)P, sizeof(int32_t));
     o->due = (int32_t *)xcalloc((size_t)P, sizeof(int32_t));
@@ -323,7 +328,7 @@ void orc_destroy(orc *o)
                     o->st_arrived, o->st_rejected, o->st_missing, o->st_charged, o->inf_M, o->inf_admitted,
                     o->inf_departed, o->inf_csat, o->inf_ccon, o->inf_enet, o->inf_egrid, o->inf_price,
                     o->inf_req_sum, o->inf_eto, o->inf_eb, o->inf_degrad, o->inf_egrid_net, o->bsoc, o->bp, o->due,
-                    o->inf_csat1, o->inf_cs_margin};
+                    o->inf_csat1, o->inf_cs_margin, o->scratch_e0};
     for (size_t k = 0; k < sizeof(ptrs) / sizeof(ptrs[0]); ++k) free(ptrs[k]);
     free(o);
 }
@@ -506,6 +511,7 @@ void orc_step(orc *o, const int8_t *actions, int64_t lda, double *reward, uint8_
                 double dE = P * dt;
                 double s = o->soc[i] + dE / o->cap[i];
                 o->soc[i] = s > 1.0 ? 1.0 : (s < 0.0 ? 0.0 : s);
+                o->scratch_e0[i] = o->erem[i];
                 double r = o->erem[i] - dE;
                 o->erem[i] = r < 0.0 ? 0.0 : r;
                 e_net += dE;
@@ -523,16 +529,21 @@ void orc_step(orc *o, const int8_t *actions, int64_t lda, double *reward, uint8_
 
         /* time moves on: every stationed car has one step less to stay; a
          * time-sensitive user (u = 0) leaves when none is left, a
-         * charge-sensitive one (u = 1) once its demand is met, read as
-         * Delta E_remain <= eps_kwh (its Delta t_remain may turn negative) */
+         * charge-sensitive one (u = 1) once its demand is met: Delta
+         * E_remain = 0, read as this step's charge having covered the
+         * remaining demand up to the relative slack eps_rel (its Delta
+         * t_remain may turn negative meanwhile) */
         double cs_margin = 1e300;
         for (int64_t i = p0; i < p1; ++i) {
             o->scratch_leave[i] = 0;
             if (o->trem[i] == ORC_TREM_CS) {
+                double e0 = o->scratch_e0[i], e1 = o->erem[i];
                 o->due[i] -= 1;
-                o->scratch_leave[i] = (o->erem[i] <= p->eps_kwh);
-                double m = fabs(o->erem[i] - p->eps_kwh);
-                if (m < cs_margin) cs_margin = m;
+                o->scratch_leave[i] = (e1 <= p->eps_rel * e0);
+                if (e0 > 0.0) {
+                    double m = fabs(e1 / e0 - p->eps_rel) / p->eps_rel;
+                    if (m < cs_margin) cs_margin = m;
+                }
             } else if (o->trem[i] > 0) {
                 o->trem[i] -= 1;
                 o->scratch_leave[i] = (o->trem[i] == 0);
@@ -773,9 +784,10 @@ void orc_set_battery(orc *o, const double *soc, const double *pw)
 void orc_get_due(const orc *o, int32_t *due) { memcpy(due, o->due, (size_t)o->P * sizeof(int32_t)); }
 void orc_set_due(orc *o, const int32_t *due) { memcpy(o->due, due, (size_t)o->P * sizeof(int32_t)); }
 
-/* c_Sat,1 of the last step per env, and the smallest distance of a tested
- * charge-sensitive car's remaining demand from the departure threshold
- * (1e300 when none was tested). */
+/* c_Sat,1 of the last step per env, and the smallest relative distance
+ * |after/before - eps_rel| / eps_rel of a tested charge-sensitive car's
+ * remaining demand from the departure decision (1e300 when none was
+ * tested). */
 void orc_get_info_cs(const orc *o, double *csat1, double *margin)
 {
     memcpy(csat1, o->inf_csat1, (size_t)o->E * sizeof(double));

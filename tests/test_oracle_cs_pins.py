@@ -61,21 +61,29 @@ def test_departure_when_charged_and_csat1(due, early):
     rts, occ = run_levels(o, 10, due)
     assert int(occ[due - 1][0]) == 0 and all(int(x[0]) > 0 for x in occ[:due - 1])
 
-def test_remaining_demand_threshold():
-    """Two cars at 0.0096 kW (8e-4 kWh per step): 1e-3 kWh leaves 2e-4 after
-    one step (above 1e-4: stays, then the demand cap empties it), 8.5e-4
-    leaves 5e-5 (at most 1e-4: leaves at once)."""
-    w = hand_workload(n_ports=2, cs_share_256=256, alpha_sat=0.0, alpha_decl=0.0)
+@pytest.mark.parametrize("short,leaves", [(5e-6, True), (3e-5, False)])
+def test_demand_met_up_to_the_relative_slack(short, leaves):
+    """Two charge-sensitive cars with 1 kWh left each in one group: both ask
+    for their whole remainder (12 kW), the group limit is 24 kW x (1 - short),
+    so each keeps short x 1 kWh.  Within the slack eps_rel = 1e-5 of its
+    remainder the demand counts as met and the car leaves; 3e-5 stays, and
+    the next step (unclipped) covers the rest exactly."""
+    w = hand_workload(n_ports=2, cs_share_256=256, group_limit=24.0 * (1 - short), alpha_sat=0.0, alpha_decl=0.0)
     o = Oracle(w)
-    park_cs(o, 0, 50, soc=0.5, cap=50.0, rbar=0.0096, erem=1e-3)
-    park_cs(o, 1, 50, soc=0.5, cap=50.0, rbar=0.0096, erem=8.5e-4)
+    for q in (0, 1):
+        park_cs(o, q, 50, soc=0.5, cap=50.0, rbar=50.0, erem=1.0)
     o.step(np.array([10, 10], np.int8))
     s = o.state()
-    assert list(s["trem"]) == [CS, 0]
-    np.testing.assert_allclose(s["erem"][0], 2e-4, rtol=1e-9)
-    np.testing.assert_allclose(o.info_cs()["margin"][0], 5e-5, rtol=1e-6)
-    o.step(np.array([10, 10], np.int8))
-    assert list(o.state()["trem"]) == [0, 0]
+    # the limit is stored in FP32: the shortfall is short within 1e-2
+    np.testing.assert_allclose(o.info_cs()["margin"][0], abs(short / 1e-5 - 1.0), rtol=1e-2)
+    if leaves:
+        assert list(s["trem"]) == [0, 0]
+    else:
+        assert list(s["trem"]) == [CS, CS]
+        np.testing.assert_allclose(s["erem"], short, rtol=1e-2)
+        o.step(np.array([10, 10], np.int8))
+        assert list(o.state()["trem"]) == [0, 0]
+
 
 def test_uncharged_car_stays_to_episode_end():
     """Level 0 never charges: the charge-sensitive car stays past its due
@@ -152,8 +160,8 @@ def test_observation_port_features():
 
 def test_cs_invariants_along_random_trajectories():
     """Half charge-sensitive users, every penalty on: each step a
-    charge-sensitive car either stays with remaining demand above the
-    threshold and Delta t_remain one lower, or leaves with its demand met;
+    charge-sensitive car either stays, its remaining demand above the slack
+    of what it had and Delta t_remain one lower, or leaves with its demand met;
     time-sensitive cars keep their stay rule; SoC and demand domains hold."""
     w = I.heterogeneous(n_envs=32, seed=7)
     p = w.params
@@ -172,7 +180,7 @@ def test_cs_invariants_along_random_trajectories():
         cs0 = s0["trem"] == CS
         stay = cs0 & (s1["trem"] == CS) & (s1["cap"] == s0["cap"])
         assert np.all(d1[stay] == d0[stay] - 1)
-        assert np.all(s1["erem"][stay] > p.eps_kwh)
+        assert np.all(s1["erem"][stay] > p.eps_rel * s0["erem"][stay])
         left = cs0 & ((s1["trem"] != CS) | (s1["cap"] != s0["cap"]))
         seen_cs_leave += int(left.sum())
         assert np.all((s1["soc"] >= 0) & (s1["soc"] <= 1)) and np.all(s1["erem"] >= 0)
@@ -216,15 +224,16 @@ def test_user_draw_from_the_pinned_generator():
 
 
 def test_charge_sensitive_departure_carries_no_csat0():
-    """A charge-sensitive car leaving with 5e-5 kWh still due adds nothing to
-    c_Sat,0 (that term is the time-sensitive users'): the reward does not
-    move with alpha_sat."""
+    """A charge-sensitive car leaving with 5e-6 kWh still due (within the
+    slack) adds nothing to c_Sat,0, the time-sensitive users' term: the
+    reward does not move with alpha_sat."""
     out = []
     for a in (0.0, 1.0):
-        w = hand_workload(n_ports=1, cs_share_256=256, alpha_sat=a, alpha_decl=0.0)
+        w = hand_workload(n_ports=2, cs_share_256=256, group_limit=24.0 * (1 - 5e-6), alpha_sat=a, alpha_decl=0.0)
         o = Oracle(w)
-        park_cs(o, 0, 50, soc=0.5, cap=50.0, rbar=0.0096, erem=8.5e-4)
-        r, _ = o.step(np.array([10], np.int8))
-        assert o.state()["trem"][0] == 0
+        for q in (0, 1):
+            park_cs(o, q, 50, soc=0.5, cap=50.0, rbar=50.0, erem=1.0)
+        r, _ = o.step(np.array([10, 10], np.int8))
+        assert list(o.state()["trem"]) == [0, 0]
         out.append(r[0])
     assert out[0] == out[1]
