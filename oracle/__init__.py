@@ -47,7 +47,7 @@ class _Params(C.Structure):
         ("batt_soc0", C.c_double),
         ("action_delta", C.c_int32), ("p_max_dis_kw", C.c_double * 2),
         ("cs_share_256", C.c_int32), ("alpha_sat1", C.c_double), ("beta_early", C.c_double),
-        ("eps_rel", C.c_double),
+        ("eps_cap", C.c_double),
     ]
 
 
@@ -133,7 +133,7 @@ def params_struct(p) -> _Params:
     for k in range(2):
         s.p_max_dis_kw[k] = pd[k]
     s.cs_share_256 = int(p.cs_share_256); s.alpha_sat1 = p.alpha_sat1; s.beta_early = p.beta_early
-    s.eps_rel = p.eps_rel
+    s.eps_cap = p.eps_cap
     return s
 
 

@@ -64,11 +64,11 @@ typedef struct orc_params {
     /* charge-sensitive users (u = 1, A.1 User Profiles): a car's user is
      * charge-sensitive iff the low byte of its first profile word is below
      * cs_share_256; such a user leaves once its Delta E_remain is 0, read
-     * as: this step's charge covered it up to the relative slack eps_rel
-     * (remaining after <= eps_rel x remaining before); it costs
-     * alpha_sat1 * c_Sat,1 with early-leave weight beta_early */
+     * as at most eps_cap of its car's capacity (the target SoC reached
+     * within eps_cap); it costs alpha_sat1 * c_Sat,1 with early-leave
+     * weight beta_early */
     int32_t cs_share_256;
-    double alpha_sat1, beta_early, eps_rel;
+    double alpha_sat1, beta_early, eps_cap;
 } orc_params;
 
 typedef struct orc {
@@ -105,10 +105,9 @@ typedef struct orc {
     double *inf_eto, *inf_eb, *inf_degrad, *inf_egrid_net;   /* V2G terms of the last step */
     double *inf_csat1;                     /* c_Sat,1 of the last step                        */
     double *inf_cs_margin;                 /* min over charge-sensitive cars tested in the last
-                                              step of |after/before - eps_rel| / eps_rel, their
-                                              distance from the departure decision            */
+                                              step of |Delta E_remain - eps_cap C| / (eps_cap C),
+                                              their distance from the departure decision      */
     double *scratch_p;                     /* per-port power within one step    */
-    double *scratch_e0;                    /* per-port remaining demand before the charge */
     uint8_t *scratch_leave;                /* port's stay ended in this step    */
 } orc;
 
@@ -278,7 +277,6 @@ orc *orc_create(const orc_params *prm, int32_t E,
     o->rbar = (double *)xcalloc((size_t)P, sizeof(double));
     o->pw = (double *)xcalloc((size_t)P, sizeof(double));
     o->scratch_p = (double *)xcalloc((size_t)P, sizeof(double));
-    o->scratch_e0 = (double *)xcalloc((size_t)P, sizeof(double));
     o->scratch_leave = (uint8_t *)xcalloc((size_t)P, 1);
     o->trem = (int32_t *)xcalloc((size_t)P, sizeof(int32_t));
     o->due = (int32_t *)xcalloc((size_t)P, sizeof(int32_t));
@@ -328,7 +326,7 @@ void orc_destroy(orc *o)
                     o->st_arrived, o->st_rejected, o->st_missing, o->st_charged, o->inf_M, o->inf_admitted,
                     o->inf_departed, o->inf_csat, o->inf_ccon, o->inf_enet, o->inf_egrid, o->inf_price,
                     o->inf_req_sum, o->inf_eto, o->inf_eb, o->inf_degrad, o->inf_egrid_net, o->bsoc, o->bp, o->due,
-                    o->inf_csat1, o->inf_cs_margin, o->scratch_e0};
+                    o->inf_csat1, o->inf_cs_margin};
     for (size_t k = 0; k < sizeof(ptrs) / sizeof(ptrs[0]); ++k) free(ptrs[k]);
     free(o);
 }
@@ -511,7 +509,6 @@ void orc_step(orc *o, const int8_t *actions, int64_t lda, double *reward, uint8_
                 double dE = P * dt;
                 double s = o->soc[i] + dE / o->cap[i];
                 o->soc[i] = s > 1.0 ? 1.0 : (s < 0.0 ? 0.0 : s);
-                o->scratch_e0[i] = o->erem[i];
                 double r = o->erem[i] - dE;
                 o->erem[i] = r < 0.0 ? 0.0 : r;
                 e_net += dE;
@@ -530,18 +527,17 @@ void orc_step(orc *o, const int8_t *actions, int64_t lda, double *reward, uint8_
         /* time moves on: every stationed car has one step less to stay; a
          * time-sensitive user (u = 0) leaves when none is left, a
          * charge-sensitive one (u = 1) once its demand is met: Delta
-         * E_remain = 0, read as this step's charge having covered the
-         * remaining demand up to the relative slack eps_rel (its Delta
-         * t_remain may turn negative meanwhile) */
+         * E_remain = 0, read as at most eps_cap of the car's capacity (its
+         * Delta t_remain may turn negative meanwhile) */
         double cs_margin = 1e300;
         for (int64_t i = p0; i < p1; ++i) {
             o->scratch_leave[i] = 0;
             if (o->trem[i] == ORC_TREM_CS) {
-                double e0 = o->scratch_e0[i], e1 = o->erem[i];
+                double thr = p->eps_cap * o->cap[i];
                 o->due[i] -= 1;
-                o->scratch_leave[i] = (e1 <= p->eps_rel * e0);
-                if (e0 > 0.0) {
-                    double m = fabs(e1 / e0 - p->eps_rel) / p->eps_rel;
+                o->scratch_leave[i] = (o->erem[i] <= thr);
+                if (thr > 0.0) {
+                    double m = fabs(o->erem[i] - thr) / thr;
                     if (m < cs_margin) cs_margin = m;
                 }
             } else if (o->trem[i] > 0) {
@@ -785,9 +781,8 @@ void orc_get_due(const orc *o, int32_t *due) { memcpy(due, o->due, (size_t)o->P 
 void orc_set_due(orc *o, const int32_t *due) { memcpy(o->due, due, (size_t)o->P * sizeof(int32_t)); }
 
 /* c_Sat,1 of the last step per env, and the smallest relative distance
- * |after/before - eps_rel| / eps_rel of a tested charge-sensitive car's
- * remaining demand from the departure decision (1e300 when none was
- * tested). */
+ * |Delta E_remain - eps_cap C| / (eps_cap C) of a tested charge-sensitive
+ * car from the departure threshold (1e300 when none was tested). */
 void orc_get_info_cs(const orc *o, double *csat1, double *margin)
 {
     memcpy(csat1, o->inf_csat1, (size_t)o->E * sizeof(double));

@@ -70,12 +70,12 @@ class EnvParams:
     # power (Delta-current form of A.2 "Apply Actions"; n_levels odd)
     action_delta: int = 0
     # charge-sensitive users (u = 1): share in 256ths, weight of c_Sat,1 per
-    # step overdue, beta (weight of steps early), relative slack of "demand
-    # met" (remaining after the step <= eps_rel x remaining before it)
+    # step overdue, beta (weight of steps early), "demand met" threshold as a
+    # fraction of the car's capacity
     cs_share_256: int = 0
     alpha_sat1: float = 0.05
     beta_early: float = 0.5
-    eps_rel: float = 1e-5
+    eps_cap: float = 1e-3
 
 
 @dataclasses.dataclass

@@ -61,28 +61,42 @@ def test_departure_when_charged_and_csat1(due, early):
     rts, occ = run_levels(o, 10, due)
     assert int(occ[due - 1][0]) == 0 and all(int(x[0]) > 0 for x in occ[:due - 1])
 
-@pytest.mark.parametrize("short,leaves", [(5e-6, True), (3e-5, False)])
-def test_demand_met_up_to_the_relative_slack(short, leaves):
-    """Two charge-sensitive cars with 1 kWh left each in one group: both ask
-    for their whole remainder (12 kW), the group limit is 24 kW x (1 - short),
-    so each keeps short x 1 kWh.  Within the slack eps_rel = 1e-5 of its
-    remainder the demand counts as met and the car leaves; 3e-5 stays, and
-    the next step (unclipped) covers the rest exactly."""
-    w = hand_workload(n_ports=2, cs_share_256=256, group_limit=24.0 * (1 - short), alpha_sat=0.0, alpha_decl=0.0)
+def test_demand_met_threshold():
+    """Capacity 50 kWh: the demand counts as met at 1e-3 x 50 = 0.05 kWh.
+    At 0.06 kW (0.005 kWh per step) a car with 0.0512 kWh left ends at
+    0.0462 and leaves; one with 0.0562 ends at 0.0512, stays, and leaves a
+    step later."""
+    w = hand_workload(n_ports=2, cs_share_256=256, alpha_sat=0.0, alpha_decl=0.0)
+    o = Oracle(w)
+    park_cs(o, 0, 50, soc=0.5, cap=50.0, rbar=0.06, erem=0.0512)
+    park_cs(o, 1, 50, soc=0.5, cap=50.0, rbar=0.06, erem=0.0562)
+    o.step(np.array([10, 10], np.int8))
+    s = o.state()
+    assert list(s["trem"]) == [0, CS]
+    np.testing.assert_allclose(s["erem"][1], 0.0512, rtol=1e-12)
+    np.testing.assert_allclose(o.info_cs()["margin"][0], 0.0012 / 0.05, rtol=1e-9)
+    o.step(np.array([10, 10], np.int8))
+    assert list(o.state()["trem"]) == [0, 0]
+
+
+def test_threshold_reached_under_a_group_limit():
+    """Two charge-sensitive cars with 1 kWh left (capacity 50 kWh) in a
+    2.304 kW group: the proportional rescale gives each 1.152 kW, 0.096 kWh
+    per step, so 1 - 0.096 k remains; at k = 10 that is 0.04 kWh, below
+    1e-3 x 50, and both leave a step before the demand cap would finish
+    them."""
+    w = hand_workload(n_ports=2, cs_share_256=256, group_limit=2.304, alpha_sat=0.0, alpha_decl=0.0)
     o = Oracle(w)
     for q in (0, 1):
         park_cs(o, q, 50, soc=0.5, cap=50.0, rbar=50.0, erem=1.0)
-    o.step(np.array([10, 10], np.int8))
-    s = o.state()
-    # the limit is stored in FP32: the shortfall is short within 1e-2
-    np.testing.assert_allclose(o.info_cs()["margin"][0], abs(short / 1e-5 - 1.0), rtol=1e-2)
-    if leaves:
-        assert list(s["trem"]) == [0, 0]
-    else:
-        assert list(s["trem"]) == [CS, CS]
-        np.testing.assert_allclose(s["erem"], short, rtol=1e-2)
+    glim = float(np.float32(2.304))                       # limits are stored in FP32
+    for k in range(1, 10):
         o.step(np.array([10, 10], np.int8))
-        assert list(o.state()["trem"]) == [0, 0]
+        s = o.state()
+        assert list(s["trem"]) == [CS, CS]
+        np.testing.assert_allclose(s["erem"], 1.0 - k * glim / 24.0, rtol=1e-12)
+    o.step(np.array([10, 10], np.int8))
+    assert list(o.state()["trem"]) == [0, 0]
 
 
 def test_uncharged_car_stays_to_episode_end():
@@ -160,8 +174,8 @@ def test_observation_port_features():
 
 def test_cs_invariants_along_random_trajectories():
     """Half charge-sensitive users, every penalty on: each step a
-    charge-sensitive car either stays, its remaining demand above the slack
-    of what it had and Delta t_remain one lower, or leaves with its demand met;
+    charge-sensitive car either stays, its remaining demand above the
+    threshold and Delta t_remain one lower, or leaves with its demand met;
     time-sensitive cars keep their stay rule; SoC and demand domains hold."""
     w = I.heterogeneous(n_envs=32, seed=7)
     p = w.params
@@ -180,7 +194,7 @@ def test_cs_invariants_along_random_trajectories():
         cs0 = s0["trem"] == CS
         stay = cs0 & (s1["trem"] == CS) & (s1["cap"] == s0["cap"])
         assert np.all(d1[stay] == d0[stay] - 1)
-        assert np.all(s1["erem"][stay] > p.eps_rel * s0["erem"][stay])
+        assert np.all(s1["erem"][stay] > p.eps_cap * s1["cap"][stay])
         left = cs0 & ((s1["trem"] != CS) | (s1["cap"] != s0["cap"]))
         seen_cs_leave += int(left.sum())
         assert np.all((s1["soc"] >= 0) & (s1["soc"] <= 1)) and np.all(s1["erem"] >= 0)
@@ -224,16 +238,15 @@ def test_user_draw_from_the_pinned_generator():
 
 
 def test_charge_sensitive_departure_carries_no_csat0():
-    """A charge-sensitive car leaving with 5e-6 kWh still due (within the
-    slack) adds nothing to c_Sat,0, the time-sensitive users' term: the
+    """A charge-sensitive car leaving with 0.0462 kWh still due (below its
+    threshold) adds nothing to c_Sat,0, the time-sensitive users' term: the
     reward does not move with alpha_sat."""
     out = []
     for a in (0.0, 1.0):
-        w = hand_workload(n_ports=2, cs_share_256=256, group_limit=24.0 * (1 - 5e-6), alpha_sat=a, alpha_decl=0.0)
+        w = hand_workload(n_ports=1, cs_share_256=256, alpha_sat=a, alpha_decl=0.0)
         o = Oracle(w)
-        for q in (0, 1):
-            park_cs(o, q, 50, soc=0.5, cap=50.0, rbar=50.0, erem=1.0)
-        r, _ = o.step(np.array([10, 10], np.int8))
-        assert list(o.state()["trem"]) == [0, 0]
+        park_cs(o, 0, 50, soc=0.5, cap=50.0, rbar=0.06, erem=0.0512)
+        r, _ = o.step(np.array([10], np.int8))
+        assert o.state()["trem"][0] == 0
         out.append(r[0])
     assert out[0] == out[1]
