@@ -107,7 +107,24 @@ typedef struct chx_env_params {
     /* Discharge maximum I_max<- per charger type, > 0 (V2G mode; the
      * discharge branch of the clip caps at it instead of p_max_kw). */
     float p_max_dis_kw[2];
+    /* Charge-sensitive users (A.1 User Profiles, u = 1; A.2 "Departure of
+     * Cars"; A.3 c_Sat,1): an arriving car's user is charge-sensitive iff
+     * the low byte of the first word of its profile draw is below
+     * cs_share_256 (0 = none, 256 = all).  Such a car occupies its charger
+     * with trem = CHX_TREM_CS and counts its steps to the desired departure
+     * (Delta t_remain, negative once overdue) in a separate per-charger
+     * array (chx_get_due); it leaves once its demand is met, i.e. at most
+     * eps_cap x its car's capacity remains (the target SoC reached within
+     * eps_cap), costing alpha_sat1 x (steps overdue - beta_early x steps
+     * early).  cs_share_256 > 0 needs stay_steps[1] <= 254, and adds a 7th
+     * per-charger observation feature (u).  0 ignores the other fields. */
+    int32_t cs_share_256;
+    float alpha_sat1;
+    float beta_early;
+    float eps_cap;
 } chx_env_params;
+
+#define CHX_TREM_CS 255     /* trem of a charger holding a charge-sensitive car */
 
 /* A batch of stations, CSR.  Groups of a station are contiguous charger
  * ranges listed in charger order.  All pointers are host pointers, read only
@@ -279,6 +296,15 @@ int chx_set_state(chx_handle* h, const float* h_soc, const float* h_erem, const 
  * NULL keeps a field.  Blocking. */
 int chx_get_battery(chx_handle* h, float* h_soc, float* h_p);
 int chx_set_battery(chx_handle* h, const float* h_soc, const float* h_p);
+
+/* Delta t_remain of charge-sensitive cars (A.1 User Profiles, u = 1): per
+ * charger in batch order (the order of chx_get_state), int16 steps to the
+ * desired departure, negative once overdue; meaningful where trem is
+ * CHX_TREM_CS, 0 elsewhere.  Host arrays of [total chargers]; NULL skips.
+ * Both synchronise the device.  Without charge-sensitive users the values
+ * are unused. */
+int chx_get_due(chx_handle* h, int16_t* h_due);
+int chx_set_due(chx_handle* h, const int16_t* h_due);
 
 /* Per-env running statistics [E]: cars admitted, cars rejected, kWh missing
  * at departure, kWh charged, finished episodes, return of the last episode. */

@@ -26,7 +26,7 @@ EXPORTS = (
     "chx_obs_size", "chx_reset", "chx_step", "chx_step_n", "chx_rollout", "chx_rollout_host", "chx_step_host",
     "chx_autotune", "chx_set_launch", "chx_observe", "chx_get_state", "chx_set_state", "chx_stats", "chx_save",
     "chx_load", "chx_check", "chx_rollout_noalloc", "chx_policy_load", "chx_policy_act", "chx_policy_rollout",
-    "chx_get_battery", "chx_set_battery",
+    "chx_get_battery", "chx_set_battery", "chx_get_due", "chx_set_due",
     "chx_srv_start", "chx_srv_stop", "chx_srv_admit", "chx_srv_evict", "chx_srv_submit", "chx_srv_wait",
     "chx_srv_test", "chx_srv_stats", "chx_srv_simulate",
 )
@@ -52,6 +52,7 @@ class _Params(C.Structure):
         ("batt_cap_kwh", C.c_float), ("batt_rate_kw", C.c_float), ("batt_tau", C.c_float),
         ("batt_soc0", C.c_float),
         ("action_delta", C.c_int32), ("p_max_dis_kw", C.c_float * 2),
+        ("cs_share_256", C.c_int32), ("alpha_sat1", C.c_float), ("beta_early", C.c_float), ("eps_cap", C.c_float),
     ]
 
 
@@ -126,6 +127,7 @@ def load_library(path: str = LIB_PATH):
         "chx_policy_load": [vp, i32, vp, vp, vp, vp, vp, vp], "chx_policy_act": [vp, vp, vp, vp, vp],
         "chx_policy_rollout": [vp, i32, vp, vp, vp, vp, vp, i32, vp],
         "chx_get_battery": [vp, vp, vp], "chx_set_battery": [vp, vp, vp],
+        "chx_get_due": [vp, vp], "chx_set_due": [vp, vp],
         "chx_srv_start": [vp, vp], "chx_srv_stop": [vp], "chx_srv_admit": [vp, vp, u64, vp],
         "chx_srv_evict": [vp, vp, i32], "chx_srv_submit": [vp, vp, vp], "chx_srv_wait": [vp, u64, i64, vp],
         "chx_srv_test": [vp, u64, vp, vp], "chx_srv_stats": [vp, vp], "chx_srv_simulate": [vp, vp, vp, vp],
@@ -181,6 +183,8 @@ def params_struct(p: "_inputs.EnvParams") -> _Params:
     pd = p.p_max_kw if p.p_max_dis_kw is None else p.p_max_dis_kw
     for k in range(2):
         s.p_max_dis_kw[k] = pd[k]
+    s.cs_share_256 = int(p.cs_share_256); s.alpha_sat1 = p.alpha_sat1; s.beta_early = p.beta_early
+    s.eps_cap = p.eps_cap
     return s
 
 
@@ -292,6 +296,16 @@ class Batch:
         a = None if soc is None else np.ascontiguousarray(soc, dtype=np.float32)
         b = None if p is None else np.ascontiguousarray(p, dtype=np.float32)
         _check(_lib.chx_set_battery(self.h, _np_ptr(a), _np_ptr(b)))
+
+    def due(self) -> np.ndarray:
+        """Delta t_remain of charge-sensitive cars per charger (batch order)."""
+        d = np.zeros(self.P, np.int16)
+        _check(_lib.chx_get_due(self.h, _np_ptr(d)))
+        return d
+
+    def set_due(self, due):
+        a = np.ascontiguousarray(due, dtype=np.int16)
+        _check(_lib.chx_set_due(self.h, _np_ptr(a)))
 
     @property
     def n_actions(self) -> int:

@@ -20,6 +20,7 @@ __global__ void k_reset(DevBatch b, DevParams p, const int32_t* __restrict__ use
     for (int q = threadIdx.x; q < C; q += blockDim.x) {
         const long long i = pb + q;
         b.soc[i] = 0.f; b.erem[i] = 0.f; b.cap[i] = 0.f; b.rbar[i] = 0.f; b.pw[i] = 0.f; b.trem[i] = 0;
+        if (p.cs_share) b.due[i] = 0;      // the array exists only with charge-sensitive users
     }
     if (threadIdx.x == 0) {
         b.key0[s] = seed_lo;
@@ -57,6 +58,7 @@ __global__ void k_reset_slots(DevBatch b, DevParams p, const int32_t* __restrict
     for (int q = threadIdx.x; q < C; q += blockDim.x) {
         const long long i = pb + q;
         b.soc[i] = 0.f; b.erem[i] = 0.f; b.cap[i] = 0.f; b.rbar[i] = 0.f; b.pw[i] = 0.f; b.trem[i] = 0;
+        if (p.cs_share) b.due[i] = 0;      // the array exists only with charge-sensitive users
     }
     if (threadIdx.x == 0) {
         const uint32_t lo = (uint32_t)seeds[j], hi = (uint32_t)(seeds[j] >> 32);
@@ -92,13 +94,14 @@ __global__ void k_observe(DevBatch b, DevParams p, float* __restrict__ obs)
     const int C = 8 << c;
     const long long pb = b.cls_port_base[c] + (long long)(s - b.cls_env_base[c]) * C;
     const int n = b.n_ports[s];
-    float* ob = obs + (long long)p.obs_env * uid + 6LL * b.user_port_off[s];
+    float* ob = obs + (long long)p.obs_env * uid + (long long)p.obs_port * b.user_port_off[s];
     int occ = 0;
     for (int q = lane; q < n; q += 32) {
         const long long i = pb + q;
         const int tr = b.trem[i];
         occ += tr > 0;
-        obs_port(ob + p.obs_env + 6 * q, tr, b.soc[i], b.erem[i], b.rbar[i], b.pw[i], b.meta[i] & kMetaDC, p);
+        obs_port(ob + p.obs_env + p.obs_port * q, tr, p.cs_share ? (int)b.due[i] : 0, b.soc[i], b.erem[i], b.rbar[i],
+                 b.pw[i], b.meta[i] & kMetaDC, p);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) occ += __shfl_xor_sync(0xFFFFFFFFu, occ, o);

@@ -34,6 +34,8 @@ __host__ __device__ constexpr int tile_ppl(int c) { return c >= 4 ? 4 : 2; }
 __host__ __device__ constexpr int tile_lpe(int c) { return (8 << c) / tile_ppl(c); }
 __host__ __device__ constexpr int tile_epw(int c) { return 32 / tile_lpe(c); }
 
+constexpr int kTremCS = 255;               // trem of a charger holding a charge-sensitive car
+
 // device error bits
 constexpr uint32_t kErrActionRange = 1u;
 constexpr uint32_t kErrPolicyWait = 2u;     // a tensor-core wait of the policy kernel timed out
@@ -54,6 +56,10 @@ struct DevParams {
                                            // V2G mode or the Delta form, else 0
     int delta;                             // Delta-current form: requests add to the last applied power
     float pdis0, pdis1;                    // discharge maximum I_max<- per type (V2G)
+    // charge-sensitive users: u = 1 iff (first profile word & 0xFF) < cs_share
+    int cs_share;                          // 0 = none (the mode is off)
+    float a_sat1, beta, eps;               // weight of c_Sat,1, early-leave weight, "demand met" share of capacity
+    int obs_port;                          // per-charger observation features: 6, or 7 with u
     float eta0, eta1;                      // charger efficiency per type (discharge losses)
     float batt_cap, inv_batt_cap, batt_rate, batt_lvl, batt_tau, batt_inv_1m_tau, batt_soc0;
     float sell_grid_ratio, a_degrad, obs_inv_batt_rate;
@@ -63,7 +69,8 @@ struct DevParams {
 struct DevBatch {
     // per charger slot
     float *soc, *erem, *cap, *rbar, *pw;
-    uint8_t* trem;                         // remaining stay in steps, 0 = empty
+    uint8_t* trem;                         // remaining stay in steps, 0 = empty, kTremCS = charge-sensitive car
+    int16_t* due;                          // Delta t_remain of a charge-sensitive car (cs_share > 0 only)
     uint32_t* meta;                        // kMeta* bits | group slot << 4
     float *gcap, *ginv_eta;                // eta_H * I_H of the charger's group, 1/eta_H
     // per station slot
@@ -209,7 +216,7 @@ __device__ __forceinline__ float clip_battery(float preq, float bsoc, const DevP
     return -fmaxf(fminf(fminf(-preq, rdis), bsoc * p.batt_cap * p.inv_dt), 0.0f);
 }
 
-struct Car { float cap, soc, erem, rbar; int stay; };
+struct Car { float cap, soc, erem, rbar; int stay; bool cs; };
 
 // Philox words of the station's n-th car since its last reset
 __device__ __forceinline__ uint4 car_words(uint32_t uid, uint32_t n, uint32_t k0, uint32_t k1)
@@ -226,6 +233,7 @@ __device__ __forceinline__ Car car_from_words(uint4 w, bool dc, const DevParams&
     c.stay = p.stay_lo + (int)range_of(w.z, p.stay_span);
     c.rbar = dc ? p.rb_lo1 + p.rb_span1 * unit_of(w.w) : p.rb_lo0 + p.rb_span0 * unit_of(w.w);
     c.erem = fmaxf(p.soc_target - c.soc, 0.0f) * c.cap;
+    c.cs = (int)(w.x & 0xFFu) < p.cs_share;   // user preference: the low byte the capacity leaves unused
     return c;
 }
 
@@ -275,17 +283,23 @@ __device__ __forceinline__ void obs_env(float* o, int t, int day, int occ, int n
     }
 }
 
-__device__ __forceinline__ void obs_port(float* o, int trem, float soc, float erem, float rbar, float pw, bool dc,
-                                         const DevParams& p)
+// per-charger features (p.obs_port of them): occupied, SoC, stay / max stay
+// (a charge-sensitive car's Delta t_remain), r_hat / P_max, last power /
+// P_max, remaining demand / max capacity, and with charge-sensitive users u
+// (CS = false: a caller that never runs with charge-sensitive users)
+template <bool CS = true>
+__device__ __forceinline__ void obs_port(float* o, int trem, int due, float soc, float erem, float rbar, float pw,
+                                         bool dc, const DevParams& p)
 {
     const float inv_pmax = dc ? p.inv_pmax1 : p.inv_pmax0;
-    const bool on = trem > 0;
+    const bool on = trem > 0, cs = CS && trem == kTremCS && p.cs_share > 0;
     o[0] = on ? 1.0f : 0.0f;
     o[1] = soc;
-    o[2] = (float)trem * p.obs_inv_stay;
+    o[2] = (float)(cs ? due : trem) * p.obs_inv_stay;
     o[3] = on ? taper(soc, rbar, p) * inv_pmax : 0.0f;
     o[4] = pw * inv_pmax;
     o[5] = erem * p.obs_inv_cap;
+    if (CS && p.obs_port == 7) o[6] = cs ? 1.0f : 0.0f;
 }
 
 // class of a station slot (classes are consecutive in slot space)

@@ -96,6 +96,14 @@ int validate_params(const chx_env_params* p, const chx_exo* x)
             if (!(p->p_max_dis_kw[t] > 0.f) || !std::isfinite(p->p_max_dis_kw[t]))
                 return fail(CHX_EINVAL, "p_max_dis_kw must be > 0");
     }
+    if (p->cs_share_256 < 0 || p->cs_share_256 > 256) return fail(CHX_EINVAL, "cs_share_256 must be in 0..256");
+    if (p->cs_share_256 > 0) {
+        if (p->stay_steps[1] > 254)
+            return fail(CHX_EINVAL, "with charge-sensitive users stays must be <= 254 steps (255 marks such a car)");
+        if (!(p->eps_cap >= 0.f && p->eps_cap < 1.f)) return fail(CHX_EINVAL, "eps_cap must be in [0,1)");
+        if (!std::isfinite(p->alpha_sat1) || !std::isfinite(p->beta_early))
+            return fail(CHX_EINVAL, "alpha_sat1 and beta_early must be finite");
+    }
     if (p->action_delta != 0 && p->action_delta != 1) return fail(CHX_EINVAL, "action_delta must be 0 or 1");
     if (p->action_delta && (p->n_levels < 3 || (p->n_levels & 1) == 0))
         return fail(CHX_EINVAL, "the Delta action form needs an odd n_levels >= 3 (increments symmetric around 0)");
@@ -216,6 +224,11 @@ DevParams make_params(const chx_env_params& q, int n_days)
         p.obs_inv_batt_rate = q.batt_rate_kw > 0.f ? (float)(1.0 / (double)q.batt_rate_kw) : 0.f;
     }
     p.obs_env = p.v2g ? 10 : 8;
+    p.cs_share = q.cs_share_256;
+    p.a_sat1 = q.alpha_sat1;
+    p.beta = q.beta_early;
+    p.eps = q.eps_cap;
+    p.obs_port = q.cs_share_256 > 0 ? 7 : 6;
     p.inv_eta0 = (float)(1.0 / (double)q.eta_port[0]);
     p.inv_eta1 = (float)(1.0 / (double)q.eta_port[1]);
     p.cap_lo = q.cap_kwh[0];
@@ -355,7 +368,7 @@ int build_handle(const chx_stations* st, const chx_env_params* prm, const chx_ex
     ALLOC(b.user_id, NS) ALLOC(b.user_port_off, NS) ALLOC(b.n_ports, NS) ALLOC(b.arrival_class, NS)
     ALLOC(b.grid_cap, NS) ALLOC(b.grid_inv_eta, NS) ALLOC(b.tod, NS) ALLOC(b.day, NS) ALLOC(b.gstep, NS) ALLOC(b.ncar, NS)
     ALLOC(b.key0, NS) ALLOC(b.key1, NS) ALLOC(b.ep_ret, NS) ALLOC(b.last_ret, NS) ALLOC(b.n_episodes, NS)
-    ALLOC(b.bsoc, NS) ALLOC(b.bp, NS)
+    ALLOC(b.bsoc, NS) ALLOC(b.bp, NS) ALLOC(b.due, PS)
     ALLOC(b.st_arrived, NS) ALLOC(b.st_rejected, NS) ALLOC(b.st_missing, NS) ALLOC(b.st_charged, NS)
     ALLOC(h->d_user_to_slot, E) ALLOC(h->d_counter, 64) ALLOC(b.err, 1)
     const size_t nprice = (size_t)exo->n_days * prm->ep_len, nlam = (size_t)exo->n_arrival_classes * prm->ep_len;
@@ -467,7 +480,7 @@ extern "C" int chx_port_offsets(const chx_handle* h, int64_t* h_offsets)
 extern "C" int chx_obs_size(const chx_handle* h, int64_t* out)
 {
     if (!h || !out) return fail(CHX_EINVAL, "null argument");
-    *out = (long long)h->dp.obs_env * h->E + 6LL * h->P;
+    *out = (long long)h->dp.obs_env * h->E + (long long)h->dp.obs_port * h->P;
     return CHX_OK;
 }
 
@@ -614,7 +627,7 @@ extern "C" int chx_rollout_host(chx_handle* h, int32_t n_steps, float* h_reward,
     if (!h) return fail(CHX_EINVAL, "null handle");
     if (n_steps < 1) return fail(CHX_EINVAL, "n_steps must be >= 1");
     const size_t ne = (size_t)h->E * (size_t)n_steps;
-    const size_t nobs = (size_t)h->dp.obs_env * (size_t)h->E + 6 * (size_t)h->P;
+    const size_t nobs = (size_t)h->dp.obs_env * (size_t)h->E + (size_t)h->dp.obs_port * (size_t)h->P;
     float* dr = h_reward ? (float*)staging(h, 0, ne * sizeof(float)) : nullptr;
     uint8_t* dd = h_done ? (uint8_t*)staging(h, 1, ne) : nullptr;
     float* dob = h_obs ? (float*)staging(h, 2, nobs * sizeof(float)) : nullptr;
@@ -634,7 +647,7 @@ extern "C" int chx_step_host(chx_handle* h, const int8_t* h_actions, float* h_re
 {
     if (!h) return fail(CHX_EINVAL, "null handle");
     cudaStream_t st = (cudaStream_t)stream;
-    const size_t nobs = (size_t)h->dp.obs_env * (size_t)h->E + 6 * (size_t)h->P;
+    const size_t nobs = (size_t)h->dp.obs_env * (size_t)h->E + (size_t)h->dp.obs_port * (size_t)h->P;
     const size_t nact = (size_t)h->P + (h->dp.v2g ? (size_t)h->E : 0);
     int8_t* da = h_actions ? (int8_t*)staging(h, 3, nact) : nullptr;
     float* dr = h_reward ? (float*)staging(h, 4, (size_t)h->E * sizeof(float)) : nullptr;
@@ -683,7 +696,7 @@ int snapshot_take(chx_handle* h, Snapshot& s)
                {b.trem, PS}, {b.tod, NS * 4}, {b.day, NS * 4}, {b.gstep, NS * 4}, {b.ncar, NS * 4}, {b.key0, NS * 4},
                {b.key1, NS * 4}, {b.ep_ret, NS * 4}, {b.last_ret, NS * 4}, {b.n_episodes, NS * 4},
                {b.st_arrived, NS * 4}, {b.st_rejected, NS * 4}, {b.st_missing, NS * 4}, {b.st_charged, NS * 4},
-               {b.bsoc, NS * 4}, {b.bp, NS * 4}};
+               {b.bsoc, NS * 4}, {b.bp, NS * 4}, {b.due, PS * 2}};
     for (auto& it : s.items) {
         void* c = nullptr;
         if (cudaMalloc(&c, it.second) != cudaSuccess) return fail(CHX_ENOMEM, "snapshot allocation failed");
@@ -944,15 +957,31 @@ extern "C" int chx_set_battery(chx_handle* h, const float* h_soc, const float* h
     return CHX_OK;
 }
 
+extern "C" int chx_get_due(chx_handle* h, int16_t* h_due)
+{
+    if (!h) return fail(CHX_EINVAL, "null handle");
+    CUDA_TRY(cudaDeviceSynchronize());
+    RC(get_port_field(h, h_due, (const int16_t*)h->b.due));
+    return CHX_OK;
+}
+
+extern "C" int chx_set_due(chx_handle* h, const int16_t* h_due)
+{
+    if (!h) return fail(CHX_EINVAL, "null handle");
+    CUDA_TRY(cudaDeviceSynchronize());
+    RC(set_port_field(h, h_due, h->b.due));
+    return CHX_OK;
+}
+
 namespace {
-constexpr uint64_t kCkptMagic = 0x43484158434B5033ull;   // "CHAXCKP3"
+constexpr uint64_t kCkptMagic = 0x43484158434B5034ull;   // "CHAXCKP4"
 struct CkptHeader {
     uint64_t magic;
     int64_t n_envs, n_ports;
 };
 size_t ckpt_size(const chx_handle* h)
 {
-    return sizeof(CkptHeader) + (size_t)h->P * (5 * 4 + 1) + (size_t)h->E * (7 * 4 + 6 * 4 + 2 * 4);
+    return sizeof(CkptHeader) + (size_t)h->P * (5 * 4 + 1) + (size_t)h->E * (7 * 4 + 6 * 4 + 2 * 4) + (size_t)h->P * 2;
 }
 }  // namespace
 
@@ -987,9 +1016,11 @@ extern "C" int chx_save(chx_handle* h, void* h_buf, size_t* size)
     uint32_t* episodes = reinterpret_cast<uint32_t*>(charged + E);
     float* last = reinterpret_cast<float*>(episodes + E);
     float *bsoc = last + E, *bpw = bsoc + E;
+    int16_t* due = reinterpret_cast<int16_t*>(bpw + E);
     RC(chx_get_state(h, soc, erem, cap, rbar, pw, trem, tod, day, gstep, ncar, key0, key1, ret));
     RC(chx_stats(h, arrived, rejected, missing, charged, episodes, last));
     RC(chx_get_battery(h, bsoc, bpw));
+    RC(chx_get_due(h, due));
     *size = need;
     return CHX_OK;
 }
@@ -1020,9 +1051,11 @@ extern "C" int chx_load(chx_handle* h, const void* h_buf, size_t size)
     const uint32_t* episodes = reinterpret_cast<const uint32_t*>(charged + E);
     const float* last = reinterpret_cast<const float*>(episodes + E);
     const float *bsoc = last + E, *bpw = bsoc + E;
+    const int16_t* due = reinterpret_cast<const int16_t*>(bpw + E);
     RC(chx_set_state(h, f, f + P, f + 2 * P, f + 3 * P, f + 4 * P, trem, tod, day, gstep, ncar, key0, key1, ret));
     RC(set_env_field(h, bsoc, h->b.bsoc));
     RC(set_env_field(h, bpw, h->b.bp));
+    RC(set_port_field(h, due, h->b.due));
     DevBatch& b = h->b;
     RC(set_env_field(h, arrived, b.st_arrived));
     RC(set_env_field(h, rejected, b.st_rejected));

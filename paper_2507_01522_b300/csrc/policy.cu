@@ -872,7 +872,7 @@ __device__ __forceinline__ void owner_observe(const Owner& o, const RolloutArgs&
         for (int i = 0; i < 8; ++i) {
             const int c = 8 * k + i;
             if (o.live && c < N) {
-                obs_port(cf + 6 * i, (int)(vp[i] & 0xFFu), __uint_as_float(vs[i]), __uint_as_float(ve[i]),
+                obs_port<false>(cf + 6 * i, (int)(vp[i] & 0xFFu), 0, __uint_as_float(vs[i]), __uint_as_float(ve[i]),
                          __uint_as_float(vr[i]), __uint_as_float(vw[i]), (vp[i] >> 8) & kMetaDC, p);
             } else {
 #pragma unroll

@@ -559,6 +559,7 @@ extern "C" int chx_srv_start(const chx_srv_cfg* cfg, chx_srv** out)
     *out = nullptr;
     if (cfg->params.v2g) return fail(CHX_EINVAL, "the serving loop runs the charge-only mode (v2g = 0)");
     if (cfg->params.action_delta) return fail(CHX_EINVAL, "the serving loop takes absolute levels (action_delta = 0)");
+    if (cfg->params.cs_share_256) return fail(CHX_EINVAL, "the serving loop runs time-sensitive users only (cs_share_256 = 0)");
     int rc = validate_params(&cfg->params, &cfg->exo);
     if (rc) return rc;
     if (cfg->max_tick_envs < 1 || cfg->max_tick_envs > (1 << 20)) return fail(CHX_EINVAL, "max_tick_envs out of range");

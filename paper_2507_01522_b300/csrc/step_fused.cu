@@ -79,6 +79,32 @@ __device__ __forceinline__ void ld_u8(const uint8_t* src, int (&d)[N])
     }
 }
 template <int N>
+__device__ __forceinline__ void ld_i16(const int16_t* src, int (&d)[N])
+{
+    if constexpr (N == 1) {
+        d[0] = src[0];
+    } else if constexpr (N == 2) {
+        const uint32_t v = *reinterpret_cast<const uint32_t*>(src);
+        d[0] = (int16_t)(v & 0xFFFFu); d[1] = (int16_t)(v >> 16);
+    } else {
+        const uint2 v = *reinterpret_cast<const uint2*>(src);
+        d[0] = (int16_t)(v.x & 0xFFFFu); d[1] = (int16_t)(v.x >> 16);
+        d[2] = (int16_t)(v.y & 0xFFFFu); d[3] = (int16_t)(v.y >> 16);
+    }
+}
+template <int N>
+__device__ __forceinline__ void st_i16(int16_t* dst, const int (&d)[N])
+{
+    if constexpr (N == 1) {
+        dst[0] = (int16_t)d[0];
+    } else if constexpr (N == 2) {
+        *reinterpret_cast<uint32_t*>(dst) = (uint32_t)(d[0] & 0xFFFF) | ((uint32_t)d[1] << 16);
+    } else {
+        *reinterpret_cast<uint2*>(dst) = make_uint2((uint32_t)(d[0] & 0xFFFF) | ((uint32_t)d[1] << 16),
+                                                    (uint32_t)(d[2] & 0xFFFF) | ((uint32_t)d[3] << 16));
+    }
+}
+template <int N>
 __device__ __forceinline__ void st_u8(uint8_t* dst, const int (&d)[N])
 {
     if constexpr (N == 1) {
@@ -196,7 +222,7 @@ struct WarpSmem {
 // station's lanes, its level after the chargers' or drawn at charger index
 // n), signed limits, discharge energy after the port loss, two-case profit,
 // degradation penalty; observation with the battery features.
-template <int C, bool V2G, bool DELTA>
+template <int C, bool V2G, bool EXT>
 __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, const FusedIO& io, int tile,
                                          WarpSmem* ws)
 {
@@ -257,6 +283,12 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
     ld_vec(b.rbar + pb, rbar);
     ld_vec(b.pw + pb, pw);
     ld_u8(b.trem + pb, trem);
+    // charge-sensitive users (EXT instances): Delta t_remain per charger
+    const bool cs_on = EXT && p.cs_share > 0;
+    int due[PPL];
+#pragma unroll
+    for (int q = 0; q < PPL; ++q) due[q] = 0;
+    if (cs_on) ld_i16(b.due + pb, due);
     ld_vec_u32(b.meta + pb, meta);
     {
         float gc[PPL], gi[PPL];
@@ -312,7 +344,8 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
                 }
             }
             const bool dc = meta[q] & kMetaDC;
-            const float preq = request_t<V2G || DELTA, DELTA>(lvl, dc ? p.lvl1 : p.lvl0, pw[q], p);
+            const float preq = EXT ? request(lvl, dc ? p.lvl1 : p.lvl0, pw[q], p)
+                                   : request_t<V2G, false>(lvl, dc ? p.lvl1 : p.lvl0, pw[q], p);
             if (V2G)
                 P[q] = trem[q] > 0 ? clip_power_v2g(preq, dc, soc[q], erem[q], cap[q], rbar[q], p) : 0.f;
             else
@@ -334,7 +367,8 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
                     lvl = min(max(lvl, 0), p.n_levels - 1);
                 }
             }
-            Pb = clip_battery(request_t<true, DELTA>(lvl, p.batt_lvl, bpw, p), bsoc, p);
+            Pb = clip_battery(EXT ? request(lvl, p.batt_lvl, bpw, p) : request_t<true, false>(lvl, p.batt_lvl, bpw, p),
+                              bsoc, p);
         }
 
         // ---- architecture constraint: group nodes (segmented scan), then root
@@ -386,7 +420,7 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
 
         // ---- (ii) charge, time advance, (iii) departures
         bool any_leave = false;
-        uint32_t leave = 0;
+        uint32_t leave = 0, leave_cs = 0;
 #pragma unroll
         for (int q = 0; q < PPL; ++q) {
             const float Pq = P[q] * s_root;
@@ -396,10 +430,16 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
                 soc[q] = fminf(soc[q] + __fdividef(dE, cap[q]), 1.0f);
                 if (V2G) soc[q] = fmaxf(soc[q], 0.0f);
                 erem[q] = fmaxf(erem[q] - dE, 0.0f);
-                trem[q] -= 1;
-                if (trem[q] == 0) leave |= 1u << q;
+                if (cs_on && trem[q] == kTremCS) {   // charge-sensitive: leaves once charged
+                    due[q] -= 1;
+                    if (erem[q] <= p.eps * cap[q]) leave_cs |= 1u << q;
+                } else {
+                    trem[q] -= 1;
+                    if (trem[q] == 0) leave |= 1u << q;
+                }
             }
         }
+        leave |= leave_cs;
         any_leave = leave != 0;
         const float e_net = sp * s_root * p.dt;
         const float e_grid = se * s_root * p.dt;
@@ -410,18 +450,26 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
             e_b = bpw * p.dt;
             bsoc = fminf(fmaxf(bsoc + e_b * p.inv_batt_cap, 0.0f), 1.0f);
         }
-        float c_sat = 0.f;
+        float c_sat = 0.f, c_sat1 = 0.f;
         if (__any_sync(0xFFFFFFFFu, any_leave)) {
-            float v = 0.f;
+            float v = 0.f, v1 = 0.f;
 #pragma unroll
             for (int q = 0; q < PPL; ++q) {
                 if (leave & (1u << q)) {
-                    v += erem[q];
+                    if (EXT && (leave_cs & (1u << q))) {
+                        // c_Sat,1: steps overdue minus beta x steps early
+                        v1 += (float)max(-due[q], 0) - p.beta * (float)max(due[q], 0);
+                        trem[q] = 0;
+                        due[q] = 0;
+                    } else {
+                        v += erem[q];
+                    }
                     soc[q] = 0.f; erem[q] = 0.f; cap[q] = 0.f; rbar[q] = 0.f;
-                    if (DELTA) pw[q] = 0.f;        // Delta form: the next car starts from 0
+                    if (EXT && p.delta) pw[q] = 0.f;   // Delta form: the next car starts from 0
                 }
             }
             c_sat = seg_sum<LPE>(v);
+            if (cs_on) c_sat1 = seg_sum<LPE>(v1);
         }
 
         // ---- (iv) arrivals: Poisson count, first come first served
@@ -472,7 +520,12 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
                     const uint4 w = make_uint4(ws->carw[0][x], ws->carw[1][x], ws->carw[2][x], ws->carw[3][x]);
                     const Car car = car_from_words(w, meta[q] & kMetaDC, p);
                     cap[q] = car.cap; soc[q] = car.soc; erem[q] = car.erem; rbar[q] = car.rbar;
-                    trem[q] = car.stay;
+                    if (EXT && car.cs) {   // charge-sensitive user: stays until charged
+                        trem[q] = kTremCS;
+                        due[q] = car.stay;
+                    } else {
+                        trem[q] = car.stay;
+                    }
                 }
                 rank += f ? 1 : 0;
             }
@@ -492,6 +545,7 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
             const float profit = p.p_sell * e_net - price * e_grid - p.c_fixed;
             r = profit - p.a_sat * c_sat - p.a_decl * (float)(M - m_adm) - p.a_con * c_con;
         }
+        if (EXT) r -= p.a_sat1 * c_sat1;
         ret += r;
         t += 1;
         const bool fin = t >= p.ep_len;
@@ -515,6 +569,7 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
 #pragma unroll
             for (int q = 0; q < PPL; ++q) {
                 soc[q] = 0.f; erem[q] = 0.f; cap[q] = 0.f; rbar[q] = 0.f; pw[q] = 0.f; trem[q] = 0;
+                due[q] = 0;
             }
             t = 0;
             day = draw_day(uidu, g, 0u, k0, k1, p.n_days);
@@ -534,6 +589,7 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
         st_vec(b.rbar + pb, rbar);
         st_vec(b.pw + pb, pw);
         st_u8(b.trem + pb, trem);
+        if (cs_on) st_i16(b.due + pb, due);
     }
     __syncwarp();
     if (le == 0 && live) {
@@ -560,15 +616,16 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
         const int occ = (int)seg_sum<LPE>((float)occ_l);
         if (live) {
             const int n = b.n_ports[s];
+            const int QP = EXT ? p.obs_port : 6;   // features per charger
             float* ob = io.obs + (io.gather ? (long long)obs_w
-                                            : (long long)p.obs_env * uid + 6LL * b.user_port_off[s]);
+                                            : (long long)p.obs_env * uid + (long long)QP * b.user_port_off[s]);
             if (le == 0) obs_env(ob, t, day, occ, n, bsoc, bpw, b, p);
 #pragma unroll
             for (int q = 0; q < PPL; ++q) {
                 const int port = le * PPL + q;
                 if (port < n)
-                    obs_port(ob + p.obs_env + 6 * port, trem[q], soc[q], erem[q], rbar[q], pw[q], meta[q] & kMetaDC,
-                             p);
+                    obs_port<EXT>(ob + p.obs_env + QP * port, trem[q], due[q], soc[q], erem[q], rbar[q], pw[q],
+                             meta[q] & kMetaDC, p);
             }
         }
     }
@@ -579,7 +636,7 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
 // instantiation for the 128-charger class (4 chargers per lane, more
 // registers), one for the others, so the smaller classes keep more warps
 // resident.
-template <int CLO, int CHI, int MINB, bool V2G, bool DELTA>
+template <int CLO, int CHI, int MINB, bool V2G, bool EXT>
 __global__ void __launch_bounds__(256, MINB) k_step_fused(DevBatch b, DevParams p, FusedIO io)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -604,17 +661,18 @@ __global__ void __launch_bounds__(256, MINB) k_step_fused(DevBatch b, DevParams 
                 tile = tile_id - io.sched_tile_base[i];
             }
         }
-        if (CLO <= 0 && 0 <= CHI && cls == 0) run_tile<8, V2G, DELTA>(b, p, io, tile, ws);
-        if (CLO <= 1 && 1 <= CHI && cls == 1) run_tile<16, V2G, DELTA>(b, p, io, tile, ws);
-        if (CLO <= 2 && 2 <= CHI && cls == 2) run_tile<32, V2G, DELTA>(b, p, io, tile, ws);
-        if (CLO <= 3 && 3 <= CHI && cls == 3) run_tile<64, V2G, DELTA>(b, p, io, tile, ws);
-        if (CLO <= 4 && 4 <= CHI && cls == 4) run_tile<128, V2G, DELTA>(b, p, io, tile, ws);
+        if (CLO <= 0 && 0 <= CHI && cls == 0) run_tile<8, V2G, EXT>(b, p, io, tile, ws);
+        if (CLO <= 1 && 1 <= CHI && cls == 1) run_tile<16, V2G, EXT>(b, p, io, tile, ws);
+        if (CLO <= 2 && 2 <= CHI && cls == 2) run_tile<32, V2G, EXT>(b, p, io, tile, ws);
+        if (CLO <= 3 && 3 <= CHI && cls == 3) run_tile<64, V2G, EXT>(b, p, io, tile, ws);
+        if (CLO <= 4 && 4 <= CHI && cls == 4) run_tile<128, V2G, EXT>(b, p, io, tile, ws);
     }
 }
 
 namespace {
 
-// [v2g | delta << 1]: charge-only / vehicle-to-grid, absolute / Delta-current levels
+// [v2g | ext << 1]: charge-only / vehicle-to-grid; ext instances add, switched
+// at run time, the Delta-current form and charge-sensitive users
 constexpr int kForms = 4;
 void (*const kSmallKernel[kForms])(DevBatch, DevParams, FusedIO) = {
     &k_step_fused<0, 3, 3, false, false>, &k_step_fused<0, 3, 3, true, false>,
@@ -687,7 +745,7 @@ void launch_step_fused(const DevBatch& b, const DevParams& p, const FusedIO& io,
     const size_t smem = (size_t)warps * sizeof(WarpSmem);
     const FusedIO big = sub_schedule(io, 4, 4, io.counter);
     const FusedIO small = sub_schedule(io, 0, 3, io.counter + 1);
-    const int v = (p.v2g ? 1 : 0) | (p.delta ? 2 : 0);
+    const int v = (p.v2g ? 1 : 0) | ((p.delta || p.cs_share) ? 2 : 0);
     if (big.total_tiles > 0) {             // the heavy class first
         const int per_sm = blocks_per_sm((const void*)kLargeKernel[v], threads);
         const int blocks = std::max(1, std::min(per_sm * sm_count, (big.total_tiles + warps - 1) / warps));

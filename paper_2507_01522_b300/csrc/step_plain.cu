@@ -92,7 +92,7 @@ __device__ __forceinline__ void step_station(const DevBatch& b, const DevParams&
     const float c_con = fmaxf(fmaxf(over_max, (raw - grid_cap) * b.grid_inv_eta[s]), 0.0f);
 
     // -- (ii) charge, time advance, (iii) departures
-    float c_sat = 0.f;
+    float c_sat = 0.f, c_sat1 = 0.f;
     int n_free = 0;
     for (int q = 0; q < n; ++q) {
         const long long i = pb + q;
@@ -109,9 +109,25 @@ __device__ __forceinline__ void step_station(const DevBatch& b, const DevParams&
             soc = fminf(soc + __fdividef(dE, cap), 1.0f);
             if (V2G) soc = fmaxf(soc, 0.0f);
             erem = fmaxf(erem - dE, 0.0f);
-            tr -= 1;
-            if (tr == 0) {
-                c_sat += erem;
+            bool leave;
+            if (p.cs_share && tr == kTremCS) {
+                // charge-sensitive: one step nearer the desired departure;
+                // leaves once the demand is met (c_Sat,1: overdue - beta early)
+                const int d = (int)b.due[i] - 1;
+                leave = erem <= p.eps * cap;     // demand met: target SoC within eps
+                if (leave) {
+                    c_sat1 += (float)max(-d, 0) - p.beta * (float)max(d, 0);
+                    tr = 0;
+                    b.due[i] = 0;
+                } else {
+                    b.due[i] = (int16_t)d;
+                }
+            } else {
+                tr -= 1;
+                leave = tr == 0;
+                if (leave) c_sat += erem;
+            }
+            if (leave) {
                 b.soc[i] = 0.f; b.erem[i] = 0.f; b.cap[i] = 0.f; b.rbar[i] = 0.f;
             } else {
                 b.soc[i] = soc; b.erem[i] = erem;
@@ -142,7 +158,12 @@ __device__ __forceinline__ void step_station(const DevBatch& b, const DevParams&
         if (b.trem[i] != 0) continue;
         const Car car = car_from_words(car_words((uint32_t)uid, ncar + (uint32_t)j, k0, k1), b.meta[i] & kMetaDC, p);
         b.cap[i] = car.cap; b.soc[i] = car.soc; b.erem[i] = car.erem; b.rbar[i] = car.rbar;
-        b.trem[i] = (uint8_t)car.stay;
+        if (car.cs) {                      // charge-sensitive user: stays until charged
+            b.trem[i] = (uint8_t)kTremCS;
+            b.due[i] = (int16_t)car.stay;
+        } else {
+            b.trem[i] = (uint8_t)car.stay;
+        }
         ++j;
     }
 
@@ -159,6 +180,7 @@ __device__ __forceinline__ void step_station(const DevBatch& b, const DevParams&
         const float profit = p.p_sell * e_net - price * e_grid - p.c_fixed;
         r = profit - p.a_sat * c_sat - p.a_decl * (float)(M - m_adm) - p.a_con * c_con;
     }
+    if (p.cs_share) r -= p.a_sat1 * c_sat1;
 
     b.ncar[s] = ncar + (uint32_t)m_adm;
     b.st_arrived[s] += (uint32_t)m_adm;
@@ -176,6 +198,7 @@ __device__ __forceinline__ void step_station(const DevBatch& b, const DevParams&
         for (int q = 0; q < C; ++q) {
             const long long i = pb + q;
             b.soc[i] = 0.f; b.erem[i] = 0.f; b.cap[i] = 0.f; b.rbar[i] = 0.f; b.pw[i] = 0.f; b.trem[i] = 0;
+            if (p.cs_share) b.due[i] = 0;
         }
         if (V2G) {
             b.bsoc[s] = p.batt_soc0;

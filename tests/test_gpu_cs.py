@@ -1,0 +1,256 @@
+"""Parity of charge-sensitive users (u = 1: leave once charged, c_Sat,1) with
+the oracle, through the C interface, plain and fused kernels, alone and with
+the V2G mode and the Delta-current form.
+
+The departure of a charge-sensitive car is a decision on a float: its
+demand counts as met once at most eps_cap = 1e-3 of its capacity remains.
+The kernel's remaining demand (FP32, a running sum) differs from the
+oracle's by at most TRAJ_RTOL x capacity, which the trajectory comparison
+asserts, a tenth of that threshold; so the two sides can only decide
+differently for a car the oracle finds within that distance of the
+threshold.  The tests take the oracle's decision first: in a launch where
+the oracle saw a tested car within TIE_MARGIN = 0.2 of the threshold
+(twice the asserted error), that station's rewards are not compared, and
+if the two sides' states then differ it is re-synchronised, the oracle
+taking over the kernel's state of the station, before the comparison goes
+on; every other station is compared as everywhere else (events and Delta
+t_remain exact, floats within the tolerances of tests/parity.py), and
+re-synchronised stations must stay few."""
+import numpy as np
+import pytest
+
+from oracle import Oracle
+from paper_2507_01522_b300 import inputs as I
+
+from parity import (RETURN_RTOL, STEP_RTOL, TRAJ_RTOL, assert_events_equal, assert_floats_close,
+                    assert_reward_close, assert_traj_close, charger_pmax, reward_scale, station_step_scale,
+                    to_f32_state, widen)
+from test_gpu_parity import odd_sizes, stressed
+from test_gpu_v2g import V2G, v2g_scale
+
+pytestmark = pytest.mark.gpu
+
+TIE_MARGIN = 0.2
+CS = dict(cs_share_256=128, alpha_sat1=0.05, beta_early=0.5, eps_cap=1e-3, soc_target=0.8)
+BASE = {"odd150": odd_sizes, "stressed": stressed, "hetero64": lambda: I.heterogeneous(n_envs=64),
+        "hetero512": lambda: I.heterogeneous(n_envs=512, seed=2)}
+ENV_KEYS = ("tod", "day", "gstep", "ncar", "key0", "key1", "ep_ret")
+
+
+def make(name, v2g=False, delta=False, **extra):
+    import torch
+    from paper_2507_01522_b300.chargax import Batch
+    w = BASE[name]()
+    kw = dict(CS)
+    if v2g:
+        kw.update(V2G)
+    if delta:
+        kw.update(action_delta=1, n_levels=21)
+    kw.update(extra)
+    w.params = I.EnvParams(**{**w.params.__dict__, **kw})
+    return w, Batch(w), Oracle(w), torch
+
+
+def restrict(s, env_keep, port_keep):
+    return {k: (v[env_keep] if k in ENV_KEYS else v[port_keep]) for k, v in s.items()}
+
+
+def resync(o, b, w, envs):
+    """The oracle takes over the kernel's state of stations envs."""
+    po = w.stations.port_off
+    ports = np.concatenate([np.arange(po[e], po[e + 1]) for e in envs])
+    gs, os_ = b.get_state(), o.state()
+    for k, v in os_.items():
+        idx = envs if k in ENV_KEYS else ports
+        v[idx] = gs[k][idx]
+    o.set_state(os_)
+    d = o.due()
+    d[ports] = b.due()[ports]
+    o.set_due(d)
+    bo, bg = o.battery(), b.battery()
+    o.set_battery(np.where(np.isin(np.arange(b.E), envs), bg["soc"], bo["soc"]),
+                  np.where(np.isin(np.arange(b.E), envs), bg["p"], bo["p"]))
+
+
+def compare_cs(w, b, o, torch, steps, mode="plain", k=1, actions=None, max_resync_frac=0.1):
+    E = b.E
+    po = w.stations.port_off
+    port_env = np.repeat(np.arange(E), np.diff(po))
+    clean = np.ones(E, bool)                 # never re-synchronised
+    reward = torch.zeros(E, k, device="cuda")
+    done = torch.zeros(E, k, dtype=torch.uint8, device="cuda")
+    cs_seen = 0
+    for s0 in range(0, steps, k):
+        kk = min(k, steps - s0)
+        if mode == "plain":
+            a = None if actions is None else torch.from_numpy(np.ascontiguousarray(actions[:, s0])).cuda()
+            b.step(actions=a, reward=reward.view(-1), done=done.view(-1))
+        else:
+            a = None if actions is None else torch.from_numpy(np.ascontiguousarray(actions[:, s0:s0 + kk])).cuda()
+            b.step_n(kk, actions=a, reward=reward, done=done, lda=kk, ld_out=k)
+        torch.cuda.synchronize()
+        rg, dg = reward.cpu().numpy(), done.cpu().numpy()
+        near = np.zeros(E, bool)
+        for j in range(kk):
+            ro, do = o.step(None if actions is None else actions[:, s0 + j])
+            near |= o.info_cs()["margin"] < TIE_MARGIN
+            ok = ~near
+            info = o.info()
+            sc = (v2g_scale(w, info, o.info_v2g()) if w.params.v2g else
+                  reward_scale(info, w.params) + station_step_scale(w, info))
+            sc = sc + w.params.alpha_sat1 * (np.abs(o.info_cs()["csat1"]) + 1.0)
+            assert_reward_close(rg[ok, j], ro[ok], sc[ok], TRAJ_RTOL, where=f"step {s0 + j}")
+            np.testing.assert_array_equal(dg[ok, j], do[ok], err_msg=f"done step {s0 + j}")
+        gs, os_ = b.get_state(), o.state()
+        ok = ~near
+        keep_p = ok[port_env]
+        g, r = restrict(gs, ok, keep_p), restrict(os_, ok, keep_p)
+        assert_events_equal(g, r, where=f"after step {s0 + kk}")
+        np.testing.assert_array_equal(b.due()[keep_p].astype(np.int32), o.due()[keep_p], err_msg=f"due {s0 + kk}")
+        assert_traj_close(g, r, charger_pmax(w)[keep_p], TRAJ_RTOL, where=f"after step {s0 + kk}")
+        cs_seen += int((os_["trem"][keep_p] == 255).sum())
+        if near.any():                       # near-ties: re-synchronise the stations whose events differ
+            differ = np.array([not np.array_equal(gs["trem"][po[e]:po[e + 1]].astype(np.int32),
+                                                  os_["trem"][po[e]:po[e + 1]]) for e in range(E)]) & near
+            if differ.any():
+                resync(o, b, w, np.flatnonzero(differ))
+                clean &= ~differ
+    assert cs_seen > 0, "no charge-sensitive car was compared"
+    assert (~clean).mean() <= max_resync_frac, f"{(~clean).sum()} of {E} stations re-synchronised"
+    stg, sto = b.stats(), o.stats()
+    np.testing.assert_array_equal(stg["arrived"][clean], sto["arrived"][clean].astype(np.uint32))
+    fin = (sto["n_episodes"] > 0) & clean
+    if fin.any():
+        d = np.abs(stg["last_ret"][fin] - sto["last_ret"][fin])
+        assert np.all(d <= RETURN_RTOL * np.maximum(np.abs(sto["last_ret"][fin]), 1.0))
+    return clean
+
+
+@pytest.mark.parametrize("name", ["odd150", "stressed", "hetero64"])
+@pytest.mark.parametrize("mode,k", [("plain", 1), ("fused", 24)])
+def test_cs_random_levels(cuda_lib, name, mode, k):
+    w, b, o, torch = make(name)
+    compare_cs(w, b, o, torch, 96, mode=mode, k=k)
+
+
+@pytest.mark.parametrize("mode,k", [("plain", 1), ("fused", 32)])
+def test_cs_full_target_tail(cuda_lib, mode, k):
+    """Target SoC 1: cars reach the threshold in the taper's geometric tail
+    (and the SoC cap coincides with the demand cap)."""
+    w, b, o, torch = make("hetero64", soc_target=1.0)
+    compare_cs(w, b, o, torch, 128, mode=mode, k=k)
+
+
+@pytest.mark.parametrize("v2g,delta", [(True, False), (False, True), (True, True)])
+@pytest.mark.parametrize("mode,k", [("plain", 1), ("fused", 16)])
+def test_cs_with_v2g_and_delta(cuda_lib, v2g, delta, mode, k):
+    w, b, o, torch = make("stressed", v2g=v2g, delta=delta)
+    compare_cs(w, b, o, torch, 64, mode=mode, k=k)
+
+
+def test_cs_every_class_fused_long(cuda_lib):
+    """512 mixed stations, two episodes of 288 steps in 96-step launches
+    (near-ties about 1.3e-4 per station-step here)."""
+    w, b, o, torch = make("hetero512")
+    compare_cs(w, b, o, torch, 2 * 288, mode="fused", k=96)
+
+
+@pytest.mark.parametrize("mode", ["plain", "fused"])
+def test_cs_single_step_from_oracle_state(cuda_lib, mode):
+    """From the oracle's state rounded to FP32 (charge-sensitive cars and
+    their Delta t_remain included), one step: events and Delta t_remain
+    exact, floats within STEP_RTOL."""
+    w, b, o, torch = make("stressed")
+    rng = np.random.default_rng(21)
+    for _ in range(30):
+        o.step(None)
+    for trial in range(3):
+        s32 = to_f32_state(o.state())
+        o.set_state(widen(s32))
+        b.set_state(s32)
+        b.set_due(o.due().astype(np.int16))
+        acts = rng.integers(0, w.params.n_levels, b.n_actions).astype(np.int8)
+        reward = torch.zeros(b.E, device="cuda")
+        a = torch.from_numpy(acts).cuda()
+        if mode == "plain":
+            b.step(actions=a, reward=reward)
+        else:
+            b.step_n(1, actions=a, reward=reward, lda=1, ld_out=1)
+        ro, _ = o.step(acts)
+        live = o.info_cs()["margin"] >= TIE_MARGIN
+        assert live.mean() > 0.9
+        gs, os_ = b.get_state(), o.state()
+        po = w.stations.port_off
+        keep_p = live[np.repeat(np.arange(b.E), np.diff(po))]
+        g, r = restrict(gs, live, keep_p), restrict(os_, live, keep_p)
+        assert_events_equal(g, r, where=f"trial {trial}")
+        np.testing.assert_array_equal(b.due()[keep_p].astype(np.int32), o.due()[keep_p])
+        assert_floats_close(g, r, STEP_RTOL, where=f"trial {trial}", cap_hi=w.params.cap_kwh[1])
+        sc = reward_scale(o.info(), w.params) + w.params.alpha_sat1 * (np.abs(o.info_cs()["csat1"]) + 1.0)
+        assert_reward_close(reward.cpu().numpy()[live], ro[live], sc[live], STEP_RTOL, where=f"trial {trial}")
+        for _ in range(4):
+            o.step(None)
+
+
+def test_cs_observation(cuda_lib):
+    w, b, o, torch = make("odd150")
+    for _ in range(40):
+        o.step(None)
+    s32 = to_f32_state(o.state())
+    o.set_state(widen(s32))
+    b.set_state(s32)
+    b.set_due(o.due().astype(np.int16))
+    assert b.obs_size == 8 * b.E + 7 * b.P
+    obs = torch.zeros(b.obs_size, device="cuda")
+    b.observe(obs)
+    ref = o.observe()
+    np.testing.assert_allclose(obs.cpu().numpy().astype(np.float64), ref, rtol=2e-6, atol=2e-6)
+    assert (ref[8:] < 0).any() or (o.due() > 0).any()
+    obs2 = torch.zeros(b.obs_size, device="cuda")
+    b.step_n(9, obs=obs2)
+    b.observe(obs)
+    assert torch.equal(obs, obs2)
+
+
+def test_cs_checkpoint_and_autotune_keep_due(cuda_lib):
+    w, b, o, torch = make("odd150")
+    for _ in range(25):
+        b.step()
+    assert (b.get_state()["trem"] == 255).any()
+    before, due0 = b.get_state(), b.due()
+    b.autotune(40)
+    for key, v in b.get_state().items():
+        np.testing.assert_array_equal(before[key], v)
+    np.testing.assert_array_equal(due0, b.due())
+    blob = b.save()
+    r1 = torch.zeros(b.E, 30, device="cuda")
+    b.step_n(30, reward=r1)
+    s1, d1 = b.get_state(), b.due()
+    b.load(blob)
+    r2 = torch.zeros(b.E, 30, device="cuda")
+    b.step_n(30, reward=r2)
+    assert torch.equal(r1, r2)
+    np.testing.assert_array_equal(d1, b.due())
+    for key, v in s1.items():
+        np.testing.assert_array_equal(v, b.get_state()[key])
+
+
+def test_cs_rejections(cuda_lib):
+    from paper_2507_01522_b300.chargax import CHX_EINVAL, Batch, ChxError
+    w = I.small_uniform()
+    w.params.cs_share_256 = 64
+    w.params.stay_steps = (12, 255)                         # 255 marks a charge-sensitive car
+    with pytest.raises(ChxError) as ei:
+        Batch(w)
+    assert ei.value.code == CHX_EINVAL
+    w.params.stay_steps = (12, 96)
+    w.params.cs_share_256 = 257
+    with pytest.raises(ChxError) as ei:
+        Batch(w)
+    assert ei.value.code == CHX_EINVAL
+    w.params.cs_share_256 = 64
+    b = Batch(w)
+    pw = I.policy_weights(8 + 6 * 16, 16)
+    with pytest.raises(ChxError) as ei:
+        b.policy_load(pw.w1, pw.b1, pw.w2, pw.b2, pw.w3, pw.b3)
+    assert ei.value.code == CHX_EINVAL
