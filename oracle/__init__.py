@@ -87,6 +87,7 @@ def lib():
         L.orc_get_due.argtypes = [vp, vp]
         L.orc_set_due.argtypes = [vp, vp]
         L.orc_get_info_cs.argtypes = [vp, vp, vp]
+        L.orc_set_tree.argtypes = [vp, vp, vp, vp, vp, vp]
         L.orc_random_action.restype = i32
         L.orc_random_action.argtypes = [vp, i32, C.c_uint32, i32]
         _lib = L
@@ -158,6 +159,12 @@ class Oracle:
         self.h = lib().orc_create(C.byref(self._p), self.E, *[_ptr(a) for a in k[:9]],
                                   int(exo.price.shape[0]), _ptr(k[9]), int(exo.arrival_rate.shape[0]),
                                   _ptr(k[10]), C.c_uint64(seed))
+        st = w.stations
+        if st.n_upper is not None:
+            self._tree = [np.ascontiguousarray(a, dtype=dt) for a, dt in (
+                (st.n_upper, np.int32), (st.group_parent, np.int32), (st.upper_parent, np.int32),
+                (st.upper_limit_kw, np.float32), (st.upper_eta, np.float32))]
+            lib().orc_set_tree(self.h, *[_ptr(a) for a in self._tree])
         if streams is not None:
             ids = np.ascontiguousarray(streams, dtype=np.uint32)
             assert ids.shape == (self.E,)

@@ -80,6 +80,11 @@ typedef struct orc {
     uint8_t *port_type;
     int32_t *port_group;                   /* global group index of each port   */
     double *group_limit, *group_eta, *grid_limit, *grid_eta;
+    /* deeper architecture trees (Fig. charge-tree c): nodes above the
+     * groups; parents are global indices, -1 = the root */
+    int64_t U, *upper_off;
+    int32_t *group_parent, *upper_parent;
+    double *upper_limit, *upper_eta;
     float *price, *lam;                    /* [D][T], [C][T] as given           */
     /* per-port state (car-state + port state, Appendix A.1) */
     double *soc, *erem, *cap, *rbar, *pw;
@@ -108,6 +113,8 @@ typedef struct orc {
                                               step of |Delta E_remain - eps_cap C| / (eps_cap C),
                                               their distance from the departure decision      */
     double *scratch_p;                     /* per-port power within one step    */
+    double *scratch_req;                   /* per-port requested power (pre-rescale) */
+    uint8_t *scratch_in;                   /* per-port leaf mask of one node         */
     uint8_t *scratch_leave;                /* port's stay ended in this step    */
 } orc;
 
@@ -277,6 +284,11 @@ orc *orc_create(const orc_params *prm, int32_t E,
     o->rbar = (double *)xcalloc((size_t)P, sizeof(double));
     o->pw = (double *)xcalloc((size_t)P, sizeof(double));
     o->scratch_p = (double *)xcalloc((size_t)P, sizeof(double));
+    o->scratch_req = (double *)xcalloc((size_t)P, sizeof(double));
+    o->scratch_in = (uint8_t *)xcalloc((size_t)P + 1, 1);
+    o->upper_off = (int64_t *)xcalloc((size_t)E + 1, sizeof(int64_t));
+    o->group_parent = (int32_t *)xcalloc((size_t)G, sizeof(int32_t));
+    for (int64_t g = 0; g < G; ++g) o->group_parent[g] = -1;
     o->scratch_leave = (uint8_t *)xcalloc((size_t)P, 1);
     o->trem = (int32_t *)xcalloc((size_t)P, sizeof(int32_t));
     o->due = (int32_t *)xcalloc((size_t)P, sizeof(int32_t));
@@ -326,7 +338,8 @@ void orc_destroy(orc *o)
                     o->st_arrived, o->st_rejected, o->st_missing, o->st_charged, o->inf_M, o->inf_admitted,
                     o->inf_departed, o->inf_csat, o->inf_ccon, o->inf_enet, o->inf_egrid, o->inf_price,
                     o->inf_req_sum, o->inf_eto, o->inf_eb, o->inf_degrad, o->inf_egrid_net, o->bsoc, o->bp, o->due,
-                    o->inf_csat1, o->inf_cs_margin};
+                    o->inf_csat1, o->inf_cs_margin,
+                    o->scratch_req, o->scratch_in, o->upper_off, o->group_parent, o->upper_parent, o->upper_limit, o->upper_eta};
     for (size_t k = 0; k < sizeof(ptrs) / sizeof(ptrs[0]); ++k) free(ptrs[k]);
     free(o);
 }
@@ -360,6 +373,73 @@ void orc_policy_uniforms(const orc *o, int32_t n_ports, double *u)
             for (int32_t j = 0; j < 4 && q + j < n_ports; ++j)
                 u[(int64_t)e * n_ports + q + j] = to_unit(w[j]);
         }
+}
+
+/* Deeper trees (Fig. charge-tree c): n_upper[e] nodes above the groups of
+ * env e, listed per env; group_parent[g] and upper_parent[u] are indices
+ * into the env's own upper nodes, -1 = the root; each upper node has a
+ * limit I_H (kW) and efficiency eta_H.  Without a call every group hangs
+ * from the root. */
+void orc_set_tree(orc *o, const int32_t *n_upper, const int32_t *group_parent, const int32_t *upper_parent,
+                  const float *upper_limit, const float *upper_eta)
+{
+    for (int32_t e = 0; e < o->E; ++e) o->upper_off[e + 1] = o->upper_off[e] + n_upper[e];
+    o->U = o->upper_off[o->E];
+    free(o->upper_parent); free(o->upper_limit); free(o->upper_eta);
+    o->upper_parent = (int32_t *)xcalloc((size_t)o->U + 1, sizeof(int32_t));
+    o->upper_limit = (double *)xcalloc((size_t)o->U + 1, sizeof(double));
+    o->upper_eta = (double *)xcalloc((size_t)o->U + 1, sizeof(double));
+    for (int32_t e = 0; e < o->E; ++e) {
+        int64_t u0 = o->upper_off[e];
+        for (int64_t g = o->group_off[e]; g < o->group_off[e + 1]; ++g)
+            o->group_parent[g] = group_parent[g] < 0 ? -1 : (int32_t)(u0 + group_parent[g]);
+        for (int64_t u = u0; u < o->upper_off[e + 1]; ++u) {
+            o->upper_parent[u] = upper_parent[u] < 0 ? -1 : (int32_t)(u0 + upper_parent[u]);
+            o->upper_limit[u] = upper_limit[u];
+            o->upper_eta[u] = upper_eta[u];
+        }
+    }
+}
+
+/* depth below the root of an upper node (a child of the root has depth 1) */
+static int32_t upper_depth(const orc *o, int32_t u)
+{
+    int32_t d = 0;
+    for (int32_t a = u; a >= 0; a = o->upper_parent[a]) d += 1;
+    return d;
+}
+
+static int32_t group_depth(const orc *o, int64_t g)
+{
+    int32_t a = o->group_parent[g];
+    return 1 + (a < 0 ? 0 : upper_depth(o, a));
+}
+
+/* is port i a leaf of upper node u (u an ancestor of the port's group)? */
+static int port_under_upper(const orc *o, int64_t i, int32_t u)
+{
+    for (int32_t a = o->group_parent[o->port_group[i]]; a >= 0; a = o->upper_parent[a])
+        if (a == u) return 1;
+    return 0;
+}
+
+/* One node H of Eq. (ArchConst) over the ports marked in `in`: the penalty
+ * on the requested power, then the proportional rescale of the leaves if
+ * (1/eta_H) |sum| > I_H. */
+static void apply_node(orc *o, int64_t p0, int64_t p1, const uint8_t *in, double limit, double eta, int v2g,
+                       double *c_con)
+{
+    double s = 0.0, sreq = 0.0;
+    for (int64_t i = p0; i < p1; ++i)
+        if (in[i]) { s += o->scratch_p[i]; sreq += o->scratch_req[i]; }
+    double over_req = (v2g ? fabs(sreq) : sreq) / eta - limit;
+    if (over_req > *c_con) *c_con = over_req;
+    double mag = v2g ? fabs(s) : s;
+    if (mag / eta > limit) {
+        double scale = eta * limit / mag;
+        for (int64_t i = p0; i < p1; ++i)
+            if (in[i]) o->scratch_p[i] *= scale;
+    }
 }
 
 /* ------------------------------------------------------------------------ */
@@ -463,23 +543,32 @@ void orc_step(orc *o, const int8_t *actions, int64_t lda, double *reward, uint8_
         /* Architecture constraint, Eq. (ArchConst): for every subtree H,
          * (1/eta_H) * sum of its leaves' power <= I_H.  Violations are
          * resolved by proportional rescaling of the leaves, bottom-up: the
-         * group nodes first, then the root (grid connection).  The
+         * nodes in order of decreasing depth (every node after all nodes
+         * below it), the root (grid connection) last.  The
          * constraint-violation penalty (Appendix A.3) is measured on the
          * requested (pre-rescale) power.  V2G: the limit binds the net flow
          * in either direction (|sum| / eta_H <= I_H), and the battery is a
          * leaf of the root. */
         double c_con = 0.0;
-        for (int64_t gi = o->group_off[e]; gi < o->group_off[e + 1]; ++gi) {
-            double s = 0.0;
-            for (int64_t i = p0; i < p1; ++i)
-                if (o->port_group[i] == gi) s += o->scratch_p[i];
-            double mag = v2g ? fabs(s) : s;
-            double over = mag / o->group_eta[gi] - o->group_limit[gi];
-            if (over > c_con) c_con = over;
-            if (over > 0.0) {
-                double scale = o->group_eta[gi] * o->group_limit[gi] / mag;
-                for (int64_t i = p0; i < p1; ++i)
-                    if (o->port_group[i] == gi) o->scratch_p[i] *= scale;
+        for (int64_t i = p0; i < p1; ++i) o->scratch_req[i] = o->scratch_p[i];
+        {
+            int32_t max_d = 1;
+            for (int64_t gi = o->group_off[e]; gi < o->group_off[e + 1]; ++gi) {
+                int32_t d = group_depth(o, gi);
+                if (d > max_d) max_d = d;
+            }
+            uint8_t *in = o->scratch_in;
+            for (int32_t d = max_d; d >= 1; --d) {
+                for (int64_t gi = o->group_off[e]; gi < o->group_off[e + 1]; ++gi) {
+                    if (group_depth(o, gi) != d) continue;
+                    for (int64_t i = p0; i < p1; ++i) in[i] = o->port_group[i] == gi;
+                    apply_node(o, p0, p1, in, o->group_limit[gi], o->group_eta[gi], v2g, &c_con);
+                }
+                for (int64_t u = o->upper_off[e]; u < o->upper_off[e + 1]; ++u) {
+                    if (upper_depth(o, (int32_t)u) != d) continue;
+                    for (int64_t i = p0; i < p1; ++i) in[i] = (uint8_t)port_under_upper(o, i, (int32_t)u);
+                    apply_node(o, p0, p1, in, o->upper_limit[u], o->upper_eta[u], v2g, &c_con);
+                }
             }
         }
         {

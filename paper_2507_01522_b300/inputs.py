@@ -85,6 +85,11 @@ class Stations:
     Ports of station e are ``port_off[e] .. port_off[e+1]-1``; its groups are
     contiguous port ranges listed in order (``group_size`` sums to the port
     count), each group node with a power limit (kW) and efficiency.
+
+    Deeper trees (optional): ``n_upper[e]`` nodes above station e's groups,
+    listed per station; ``group_parent`` [G] and ``upper_parent`` [U] index
+    the station's own upper nodes, -1 = the root; every node's chargers must
+    form one contiguous range (chargers in depth-first order).
     """
     n_ports: np.ndarray          # int32 [E]
     port_type: np.ndarray        # uint8 [P]
@@ -95,6 +100,11 @@ class Stations:
     grid_limit_kw: np.ndarray    # float32 [E]
     grid_eta: np.ndarray         # float32 [E]
     arrival_class: np.ndarray    # int32 [E]
+    n_upper: Optional[np.ndarray] = None          # int32 [E]
+    group_parent: Optional[np.ndarray] = None     # int32 [G]
+    upper_parent: Optional[np.ndarray] = None     # int32 [U]
+    upper_limit_kw: Optional[np.ndarray] = None   # float32 [U]
+    upper_eta: Optional[np.ndarray] = None        # float32 [U]
 
     @property
     def n_envs(self) -> int:
@@ -113,6 +123,13 @@ class Stations:
         return off
 
     @property
+    def upper_off(self) -> np.ndarray:
+        off = np.zeros(self.n_envs + 1, dtype=np.int64)
+        if self.n_upper is not None:
+            np.cumsum(self.n_upper, out=off[1:])
+        return off
+
+    @property
     def total_ports(self) -> int:
         return int(self.n_ports.sum())
 
@@ -123,12 +140,20 @@ class Stations:
         pt = np.concatenate([self.port_type[po[e]:po[e + 1]] for e in env_ids]) if len(env_ids) else np.zeros(0, np.uint8)
         gsl = [slice(go[e], go[e + 1]) for e in env_ids]
         cat = lambda a, dt: (np.concatenate([a[s] for s in gsl]) if len(env_ids) else np.zeros(0, dt))
+        tree = {}
+        if self.n_upper is not None:
+            uo = self.upper_off
+            usl = [slice(uo[e], uo[e + 1]) for e in env_ids]
+            ucat = lambda a, dt: (np.concatenate([a[s] for s in usl]) if len(env_ids) else np.zeros(0, dt))
+            tree = dict(n_upper=self.n_upper[env_ids].copy(), group_parent=cat(self.group_parent, np.int32),
+                        upper_parent=ucat(self.upper_parent, np.int32),
+                        upper_limit_kw=ucat(self.upper_limit_kw, np.float32), upper_eta=ucat(self.upper_eta, np.float32))
         return Stations(
             n_ports=self.n_ports[env_ids].copy(), port_type=pt.astype(np.uint8),
             n_groups=self.n_groups[env_ids].copy(), group_size=cat(self.group_size, np.int32),
             group_limit_kw=cat(self.group_limit_kw, np.float32), group_eta=cat(self.group_eta, np.float32),
             grid_limit_kw=self.grid_limit_kw[env_ids].copy(), grid_eta=self.grid_eta[env_ids].copy(),
-            arrival_class=self.arrival_class[env_ids].copy())
+            arrival_class=self.arrival_class[env_ids].copy(), **tree)
 
 
 @dataclasses.dataclass
@@ -268,6 +293,73 @@ def heterogeneous(n_envs: int = 65536, seed: int = 0, classes=(8, 16, 32, 64)) -
     st = mixed_stations(rng, sizes, p.p_max_kw, class_sizes=list(classes))
     exo = Exo(price_bank(seed=seed), arrival_rates(list(classes)))
     return Workload(f"hetero-{n_envs}-8/16/32/64", p, st, exo, seed)
+
+
+def tree_stations(rng: np.random.Generator, n_envs: int, p_max_kw=(22.0, 150.0), eta: float = 0.98) -> Stations:
+    """Stations with the deeper architecture of Fig. charge-tree c: the root
+    (grid) feeds one splitter per charger type, each type splitter feeds
+    1..3 sub-splitters, each sub-splitter 1..3 groups of 2..6 chargers; a
+    third of the stations skip the sub-splitters of the DC branch (its
+    groups hang from the type splitter: a tree of uneven depth).  Limits
+    take 0.75 / 0.6 / 0.5 / 0.4 of the summed charger maxima at the group /
+    sub-splitter / type splitter / grid; node efficiencies ``eta``."""
+    pm = np.asarray(p_max_kw, np.float64)
+    n_ports, port_type, n_groups, group_size, glim, geta = [], [], [], [], [], []
+    n_upper, group_parent, upper_parent, ulim, ueta, grid = [], [], [], [], [], []
+    for e in range(n_envs):
+        nodes = []                                        # (parent, limit) of this station's upper nodes
+        n, ng, total = 0, 0, 0.0
+        shallow_dc = rng.random() < 1 / 3
+        for ty in (AC, DC):
+            t_idx = len(nodes)
+            nodes.append([-1, 0.0])
+            t_sum = 0.0
+            subs = [None] if (ty == DC and shallow_dc) else [len(nodes) + i for i in range(int(rng.integers(1, 4)))]
+            for sidx in subs:
+                if sidx is not None:
+                    nodes.append([t_idx, 0.0])
+                s_sum = 0.0
+                for _ in range(int(rng.integers(1, 4))):
+                    k = int(rng.integers(2, 7))
+                    port_type.extend([ty] * k)
+                    group_size.append(k)
+                    glim.append(0.75 * k * pm[ty])
+                    geta.append(eta)
+                    group_parent.append(t_idx if sidx is None else sidx)
+                    s_sum += k * pm[ty]
+                    n += k
+                    ng += 1
+                if sidx is not None:
+                    nodes[sidx][1] = 0.6 * s_sum
+                t_sum += s_sum
+            nodes[t_idx][1] = 0.5 * t_sum
+            total += t_sum
+        n_ports.append(n)
+        n_groups.append(ng)
+        n_upper.append(len(nodes))
+        for par, lim in nodes:
+            upper_parent.append(par)
+            ulim.append(lim)
+            ueta.append(eta)
+        grid.append(0.4 * total)
+    return Stations(
+        n_ports=np.array(n_ports, np.int32), port_type=np.array(port_type, np.uint8),
+        n_groups=np.array(n_groups, np.int32), group_size=np.array(group_size, np.int32),
+        group_limit_kw=np.array(glim, np.float32), group_eta=np.array(geta, np.float32),
+        grid_limit_kw=np.array(grid, np.float32), grid_eta=np.full(n_envs, eta, np.float32),
+        arrival_class=np.zeros(n_envs, np.int32), n_upper=np.array(n_upper, np.int32),
+        group_parent=np.array(group_parent, np.int32), upper_parent=np.array(upper_parent, np.int32),
+        upper_limit_kw=np.array(ulim, np.float32), upper_eta=np.array(ueta, np.float32))
+
+
+def tree_workload(n_envs: int = 256, seed: int = 0) -> Workload:
+    """Stations of ``tree_stations`` (3..63 chargers), arrivals of a
+    32-charger station."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0x7E]))
+    p = EnvParams(p_max_kw=(22.0, 150.0))
+    st = tree_stations(rng, n_envs, p.p_max_kw)
+    exo = Exo(price_bank(seed=seed), arrival_rates([32]))
+    return Workload(f"tree-{n_envs}", p, st, exo, seed)
 
 
 def v2g_variant(w: Workload, n_levels: int = 21, batt_cap_kwh: float = 150.0, batt_rate_kw: float = 60.0) -> Workload:
