@@ -53,6 +53,7 @@ extern "C" {
 #define CHX_EFAULT (-5)   /* a kernel flagged bad input (e.g. action level out of range) */
 
 #define CHX_MAX_PORTS 128   /* chargers per station                          */
+#define CHX_MAX_UPPER_DEPTH 3   /* levels of tree nodes above the groups     */
 #define CHX_MAX_GROUPS 32   /* group nodes per station                       */
 #define CHX_MAX_STAY 255    /* longest stay in steps                         */
 
@@ -140,6 +141,20 @@ typedef struct chx_stations {
     const float* h_grid_limit_kw;    /* [n_envs] root limit, > 0              */
     const float* h_grid_eta;         /* [n_envs] or NULL = 1                  */
     const int32_t* h_arrival_class;  /* [n_envs] row of the arrival table     */
+    /* Deeper trees (Fig. charge-tree c), optional; NULL h_n_upper: every
+     * group hangs from the root.  Station e has h_n_upper[e] nodes above its
+     * groups (listed per station, in station order); parents are
+     * station-local upper-node indices, -1 = the root.  Eq. (ArchConst)
+     * holds at every node, (1/eta_H) sum <= I_H, enforced bottom-up by
+     * proportional rescaling (deeper nodes first).  Every upper node has at
+     * least one group below it, the groups below a node are consecutive,
+     * and upper nodes lie at most CHX_MAX_UPPER_DEPTH levels deep
+     * (CHX_EINVAL otherwise). */
+    const int32_t* h_n_upper;        /* [n_envs] 0..CHX_MAX_GROUPS            */
+    const int32_t* h_group_parent;   /* [sum n_groups] parent of each group   */
+    const int32_t* h_upper_parent;   /* [sum n_upper] parent of each node     */
+    const float* h_upper_limit_kw;   /* [sum n_upper] I_H > 0                 */
+    const float* h_upper_eta;        /* [sum n_upper] in (0,1], or NULL = 1   */
 } chx_stations;
 
 /* Exogenous tables (host pointers, copied to the device by chx_create). */

@@ -61,6 +61,8 @@ class _Stations(C.Structure):
         ("n_envs", C.c_int32), ("h_n_ports", C.c_void_p), ("h_port_type", C.c_void_p), ("h_n_groups", C.c_void_p),
         ("h_group_size", C.c_void_p), ("h_group_limit_kw", C.c_void_p), ("h_group_eta", C.c_void_p),
         ("h_grid_limit_kw", C.c_void_p), ("h_grid_eta", C.c_void_p), ("h_arrival_class", C.c_void_p),
+        ("h_n_upper", C.c_void_p), ("h_group_parent", C.c_void_p), ("h_upper_parent", C.c_void_p),
+        ("h_upper_limit_kw", C.c_void_p), ("h_upper_eta", C.c_void_p),
     ]
 
 
@@ -208,6 +210,12 @@ class Batch:
             exo.price.astype(np.float32), exo.arrival_rate.astype(np.float32))]
         k = self._keep
         s = _Stations(st.n_envs, *[_np_ptr(a) for a in k[:9]])
+        if st.n_upper is not None:
+            self._tree = [np.ascontiguousarray(a, dtype=dt) for a, dt in (
+                (st.n_upper, np.int32), (st.group_parent, np.int32), (st.upper_parent, np.int32),
+                (st.upper_limit_kw, np.float32), (st.upper_eta, np.float32))]
+            (s.h_n_upper, s.h_group_parent, s.h_upper_parent, s.h_upper_limit_kw,
+             s.h_upper_eta) = [_np_ptr(a) for a in self._tree]
         x = _Exo(int(exo.price.shape[0]), _np_ptr(k[9]), int(exo.arrival_rate.shape[0]), _np_ptr(k[10]))
         self._p = params_struct(workload.params)
         h = C.c_void_p()

@@ -35,6 +35,7 @@ __host__ __device__ constexpr int tile_lpe(int c) { return (8 << c) / tile_ppl(c
 __host__ __device__ constexpr int tile_epw(int c) { return 32 / tile_lpe(c); }
 
 constexpr int kTremCS = 255;               // trem of a charger holding a charge-sensitive car
+constexpr int kMaxUpperDepth = 3;          // levels of tree nodes above the groups
 
 // device error bits
 constexpr uint32_t kErrActionRange = 1u;
@@ -60,6 +61,7 @@ struct DevParams {
     int cs_share;                          // 0 = none (the mode is off)
     float a_sat1, beta, eps;               // weight of c_Sat,1, early-leave weight, "demand met" share of capacity
     int obs_port;                          // per-charger observation features: 6, or 7 with u
+    int tree_levels;                       // levels of tree nodes above the groups (0 = none)
     float eta0, eta1;                      // charger efficiency per type (discharge losses)
     float batt_cap, inv_batt_cap, batt_rate, batt_lvl, batt_tau, batt_inv_1m_tau, batt_soc0;
     float sell_grid_ratio, a_degrad, obs_inv_batt_rate;
@@ -71,6 +73,12 @@ struct DevBatch {
     float *soc, *erem, *cap, *rbar, *pw;
     uint8_t* trem;                         // remaining stay in steps, 0 = empty, kTremCS = charge-sensitive car
     int16_t* due;                          // Delta t_remain of a charge-sensitive car (cs_share > 0 only)
+    // deeper trees (tree_levels > 0 only): level j (deepest first) of charger
+    // i has head (bit 0), tail (bit 1) and node slot (bits 2-6) in byte j of
+    // meta2[i]; its node's eta * I and 1 / eta at ucap / uinv[j * port_slots + i]
+    uint32_t* meta2;
+    float *ucap, *uinv;
+    long long port_slots;
     uint32_t* meta;                        // kMeta* bits | group slot << 4
     float *gcap, *ginv_eta;                // eta_H * I_H of the charger's group, 1/eta_H
     // per station slot

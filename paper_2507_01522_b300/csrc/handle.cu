@@ -1,6 +1,7 @@
 // handle.cu -- the C interface (include/chargax_b300.h): batch creation and
 // layout, launches, CUDA-graph rollouts, autotuning, state access.
 #include <algorithm>
+#include <cfloat>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -117,6 +118,72 @@ int validate_params(const chx_env_params* p, const chx_exo* x)
     return CHX_OK;
 }
 
+static_assert(kMaxUpperDepth == CHX_MAX_UPPER_DEPTH, "tree depth limits differ");
+
+// Depth below the root of every upper node of one station (a child of the
+// root has depth 1); -1 if some chain does not reach the root within
+// CHX_MAX_UPPER_DEPTH steps (too deep, or a cycle).
+int upper_depths(const int32_t* parent, int n_up, std::vector<int>& depth)
+{
+    depth.assign(n_up, 0);
+    int dmax = 0;
+    for (int u = 0; u < n_up; ++u) {
+        int d = 0, a = u;
+        while (a >= 0 && d <= CHX_MAX_UPPER_DEPTH) {
+            a = parent[a];
+            ++d;
+        }
+        if (a >= 0 || d > CHX_MAX_UPPER_DEPTH) return -1;
+        depth[u] = d;
+        dmax = std::max(dmax, d);
+    }
+    return dmax;
+}
+
+int validate_tree(const chx_stations* st)
+{
+    if (!st->h_group_parent || !st->h_upper_parent || !st->h_upper_limit_kw)
+        return fail(CHX_EINVAL, "deeper tree: missing group_parent, upper_parent or upper_limit_kw");
+    long long go = 0, uo = 0;
+    std::vector<int> depth;
+    for (int e = 0; e < st->n_envs; ++e) {
+        const int G = st->h_n_groups[e], U = st->h_n_upper[e];
+        const std::string where = "station " + std::to_string(e) + ": ";
+        if (U < 0 || U > CHX_MAX_GROUPS) return fail(CHX_EINVAL, where + "n_upper out of 0..32");
+        for (int k = 0; k < G; ++k) {
+            const int a = st->h_group_parent[go + k];
+            if (a < -1 || a >= U) return fail(CHX_EINVAL, where + "group parent out of range");
+        }
+        for (int u = 0; u < U; ++u) {
+            const int a = st->h_upper_parent[uo + u];
+            if (a < -1 || a >= U) return fail(CHX_EINVAL, where + "upper parent out of range");
+            if (!(st->h_upper_limit_kw[uo + u] > 0.f)) return fail(CHX_EINVAL, where + "upper limit must be > 0");
+            if (st->h_upper_eta && !(st->h_upper_eta[uo + u] > 0.f && st->h_upper_eta[uo + u] <= 1.f))
+                return fail(CHX_EINVAL, where + "upper eta must be in (0,1]");
+        }
+        if (upper_depths(st->h_upper_parent + uo, U, depth) < 0)
+            return fail(CHX_EINVAL, where + "upper nodes deeper than CHX_MAX_UPPER_DEPTH levels, or a cycle");
+        // every node's groups: non-empty and consecutive
+        for (int u = 0; u < U; ++u) {
+            int lo = G, hi = -1, cnt = 0;
+            for (int k = 0; k < G; ++k) {
+                int a = st->h_group_parent[go + k];
+                while (a >= 0 && a != u) a = st->h_upper_parent[uo + a];
+                if (a == u) {
+                    lo = std::min(lo, k);
+                    hi = std::max(hi, k);
+                    ++cnt;
+                }
+            }
+            if (cnt == 0) return fail(CHX_EINVAL, where + "an upper node has no group below it");
+            if (hi - lo + 1 != cnt) return fail(CHX_EINVAL, where + "the groups below an upper node are not consecutive");
+        }
+        go += G;
+        uo += U;
+    }
+    return CHX_OK;
+}
+
 int validate_stations(const chx_stations* st, const chx_exo* x, long long max_envs)
 {
     if (!st || !x) return fail(CHX_EINVAL, "null configuration pointer");
@@ -154,6 +221,7 @@ int validate_stations(const chx_stations* st, const chx_exo* x, long long max_en
         po += n;
     }
     if (po >= (1LL << 31)) return fail(CHX_EINVAL, "more than 2^31 - 1 chargers in one batch");
+    if (st->h_n_upper) return validate_tree(st);
     return CHX_OK;
 }
 
@@ -358,6 +426,63 @@ int build_handle(const chx_stations* st, const chx_env_params* prm, const chx_ex
         }
     }
 
+    // ---- deeper trees: per level (deepest first) a partition of each
+    // station's chargers into its upper nodes at that depth and
+    // pass-through runs (branches that are shallower); per charger and level
+    // head / tail / slot bits and the node's eta * I and 1 / eta
+    int tree_levels = 0;
+    std::vector<uint32_t> meta2;
+    std::vector<float> ucap, uinv;
+    if (st->h_n_upper) {
+        std::vector<int> depth;
+        long long uo = 0;
+        std::vector<long long> upper_off(E + 1, 0);
+        for (int e = 0; e < E; ++e) {
+            upper_off[e + 1] = upper_off[e] + st->h_n_upper[e];
+            tree_levels = std::max(tree_levels, upper_depths(st->h_upper_parent + upper_off[e], st->h_n_upper[e], depth));
+        }
+        meta2.assign(PS, 0u);
+        ucap.assign((size_t)tree_levels * PS, 0.f);
+        uinv.assign((size_t)tree_levels * PS, 0.f);
+        for (int e = 0; e < E; ++e) {
+            const int G = st->h_n_groups[e], U = st->h_n_upper[e];
+            uo = upper_off[e];
+            upper_depths(st->h_upper_parent + uo, U, depth);
+            const long long pb = h->slot_port_base[h->user_to_slot[e]];
+            for (int j = 0; j < tree_levels; ++j) {
+                const int lev = tree_levels - j;          // depth of the nodes of level j
+                int q = 0, slot = -1, prev = -2;
+                for (int k = 0; k < G; ++k) {
+                    int a = st->h_group_parent[group_off[e] + k];
+                    while (a >= 0 && depth[a] > lev) a = st->h_upper_parent[uo + a];
+                    const int anc = (a >= 0 && depth[a] == lev) ? a : -1;   // -1: pass-through
+                    if (anc != prev || (anc < 0 && prev >= 0)) ++slot;
+                    const int gs = st->h_group_size[group_off[e] + k];
+                    double eta = 1.0, lim = 0.0;
+                    if (anc >= 0) {
+                        eta = st->h_upper_eta ? st->h_upper_eta[uo + anc] : 1.0;
+                        lim = st->h_upper_limit_kw[uo + anc];
+                    }
+                    for (int r = 0; r < gs; ++r, ++q) {
+                        const long long i = pb + q;
+                        uint32_t bits = (uint32_t)slot << 2;
+                        if (anc != prev && r == 0) bits |= 1u;   // head
+                        meta2[i] |= bits << (8 * j);
+                        ucap[(size_t)j * PS + i] = anc >= 0 ? (float)(eta * lim) : FLT_MAX;
+                        uinv[(size_t)j * PS + i] = (float)(1.0 / eta);
+                    }
+                    prev = anc;
+                }
+                // tails: the last charger of each segment
+                for (int r = 0; r < q; ++r) {
+                    const long long i = pb + r;
+                    const bool last = r == q - 1 || ((meta2[i + 1] >> (8 * j)) & 1u);
+                    if (last) meta2[i] |= 2u << (8 * j);
+                }
+            }
+        }
+    }
+
     // ---- device arrays
     DevBatch& b = h->b;
     Buffers& B = h->bufs;
@@ -369,6 +494,9 @@ int build_handle(const chx_stations* st, const chx_env_params* prm, const chx_ex
     ALLOC(b.grid_cap, NS) ALLOC(b.grid_inv_eta, NS) ALLOC(b.tod, NS) ALLOC(b.day, NS) ALLOC(b.gstep, NS) ALLOC(b.ncar, NS)
     ALLOC(b.key0, NS) ALLOC(b.key1, NS) ALLOC(b.ep_ret, NS) ALLOC(b.last_ret, NS) ALLOC(b.n_episodes, NS)
     ALLOC(b.bsoc, NS) ALLOC(b.bp, NS) ALLOC(b.due, PS)
+    if (tree_levels > 0) {
+        ALLOC(b.meta2, PS) ALLOC(b.ucap, (size_t)tree_levels * PS) ALLOC(b.uinv, (size_t)tree_levels * PS)
+    }
     ALLOC(b.st_arrived, NS) ALLOC(b.st_rejected, NS) ALLOC(b.st_missing, NS) ALLOC(b.st_charged, NS)
     ALLOC(h->d_user_to_slot, E) ALLOC(h->d_counter, 64) ALLOC(b.err, 1)
     const size_t nprice = (size_t)exo->n_days * prm->ep_len, nlam = (size_t)exo->n_arrival_classes * prm->ep_len;
@@ -382,6 +510,11 @@ int build_handle(const chx_stations* st, const chx_env_params* prm, const chx_ex
     CUDA_TRY(cudaMemcpy(price, exo->h_price, nprice * sizeof(float), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(cdf, F.data(), F.size() * sizeof(float), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(b.meta, meta.data(), PS * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    if (tree_levels > 0) {
+        CUDA_TRY(cudaMemcpy(b.meta2, meta2.data(), PS * sizeof(uint32_t), cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(b.ucap, ucap.data(), ucap.size() * sizeof(float), cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(b.uinv, uinv.data(), uinv.size() * sizeof(float), cudaMemcpyHostToDevice));
+    }
     CUDA_TRY(cudaMemcpy(b.gcap, gcap.data(), PS * sizeof(float), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(b.ginv_eta, ginv.data(), PS * sizeof(float), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(b.user_id, s_uid.data(), NS * sizeof(int32_t), cudaMemcpyHostToDevice));
@@ -397,7 +530,9 @@ int build_handle(const chx_stations* st, const chx_env_params* prm, const chx_ex
         b.cls_port_base[c] = h->cls_port_base[c];
     }
     b.n_slots = NS;
+    b.port_slots = PS;
     h->dp = make_params(*prm, exo->n_days);
+    h->dp.tree_levels = tree_levels;
 
     // fused schedule: largest class first
     h->sched.n_sched = 0;

@@ -146,6 +146,7 @@ extern "C" int chx_policy_load(chx_handle* h, int32_t hidden, const uint16_t* h_
     if (h->dp.v2g) return fail(CHX_EINVAL, "the on-device policy runs the charge-only mode (v2g = 0)");
     if (h->dp.delta) return fail(CHX_EINVAL, "the on-device policy samples absolute levels (action_delta = 0)");
     if (h->dp.cs_share) return fail(CHX_EINVAL, "the on-device policy runs time-sensitive users only (cs_share_256 = 0)");
+    if (h->dp.tree_levels) return fail(CHX_EINVAL, "the on-device policy takes two-level trees (no upper nodes)");
     const long long n = h->user_port_off[1] - h->user_port_off[0];
     for (int e = 1; e < h->E; ++e)
         if (h->user_port_off[e + 1] - h->user_port_off[e] != n)

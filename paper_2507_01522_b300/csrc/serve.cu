@@ -653,6 +653,7 @@ extern "C" int chx_srv_stop(chx_srv* s)
 extern "C" int chx_srv_admit(chx_srv* s, const chx_stations* st, uint64_t seed, int32_t* h_ids)
 {
     if (!s || !st || !h_ids) return fail(CHX_EINVAL, "null argument");
+    if (st->h_n_upper) return fail(CHX_EINVAL, "the serving loop takes two-level trees (h_n_upper = NULL)");
     int rc = validate_stations(st, &s->cfg.exo, 1LL << 24);
     if (rc) return rc;
     std::lock_guard<std::mutex> lk(s->mu);

@@ -14,6 +14,8 @@
 // segment.  Both depend only on a charger's position inside its station, so a
 // station's result does not depend on which tile or lane offset it runs in.
 #include <algorithm>
+#include <cfloat>
+#include <type_traits>
 
 #include "chx_device.cuh"
 #include "chx_kernels.h"
@@ -218,13 +220,28 @@ struct WarpSmem {
     uint32_t carw[4][128];                 // pre-drawn car words: station ew's i-th buffered car at ew*C + i
 };
 
+// extended instances: also the nodes above the groups, per level, at the
+// group slots' indexing (station ew's node slot k at ew * min(C, 32) + k)
+struct WarpSmemExt : WarpSmem {
+    float ucap[kMaxUpperDepth][64];
+    float uinv[kMaxUpperDepth][64];
+    float uscale[kMaxUpperDepth][64];
+};
+
+// level j's byte of meta2 in the layout of the group bits of meta
+__device__ __forceinline__ uint32_t level_meta(uint32_t m2, int j)
+{
+    const uint32_t b8 = (m2 >> (8 * j)) & 0xFFu;
+    return ((b8 & 1u) ? kMetaHead : 0u) | ((b8 & 2u) ? kMetaTail : 0u) | (((b8 >> 2) & 31u) << kMetaGroupShift);
+}
+
 // V2G: signed levels, the station battery at the root (state in the
 // station's lanes, its level after the chargers' or drawn at charger index
 // n), signed limits, discharge energy after the port loss, two-case profit,
 // degradation penalty; observation with the battery features.
-template <int C, bool V2G, bool EXT>
+template <int C, bool V2G, bool EXT, class SM>
 __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, const FusedIO& io, int tile,
-                                         WarpSmem* ws)
+                                         SM* ws)
 {
     using S = Shape<C>;
     constexpr int PPL = S::PPL, LPE = S::LPE;
@@ -309,6 +326,33 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
             ws->st_u[ew][i] = 0u;
         }
     }
+    // deeper trees (extended instances): per level the chargers' node bits,
+    // its head distance, and the nodes' limits at their tails
+    const int TL = EXT ? p.tree_levels : 0;
+    uint32_t m2[PPL];
+    int dhu[kMaxUpperDepth] = {0, 0, 0};
+#pragma unroll
+    for (int q = 0; q < PPL; ++q) m2[q] = 0u;
+    if constexpr (EXT) {
+        if (TL > 0) {
+            ld_vec_u32(b.meta2 + pb, m2);
+#pragma unroll
+            for (int j = 0; j < kMaxUpperDepth; ++j) {
+                if (j >= TL) break;
+                uint32_t lm[PPL];
+#pragma unroll
+                for (int q = 0; q < PPL; ++q) {
+                    lm[q] = level_meta(m2[q], j);
+                    if (lm[q] & kMetaTail) {
+                        const int us = ew * GPS + (int)((lm[q] >> kMetaGroupShift) & 31u);
+                        ws->ucap[j][us] = b.ucap[(long long)j * b.port_slots + pb + q];
+                        ws->uinv[j][us] = b.uinv[(long long)j * b.port_slots + pb + q];
+                    }
+                }
+                dhu[j] = head_distance<PPL, LPE>(lm, le);
+            }
+        }
+    }
     __syncwarp();
     const bool random_actions = io.actions == nullptr;
     const int dh = head_distance<PPL, LPE>(meta, le);
@@ -390,6 +434,9 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
         }
         __syncwarp();
         float raw = 0.f, sp = 0.f, se = 0.f, sn = 0.f;
+        float Preq[PPL];                   // requested power (the upper nodes' penalty)
+#pragma unroll
+        for (int q = 0; q < PPL; ++q) Preq[q] = P[q];
 #pragma unroll
         for (int q = 0; q < PPL; ++q) {
             raw += P[q];
@@ -401,6 +448,56 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
                 else sn += P[q] * (dcq ? p.eta1 : p.eta0);
             } else {
                 se += P[q] * (dcq ? p.inv_eta1 : p.inv_eta0);
+            }
+        }
+        if constexpr (EXT) {
+            if (TL > 0) {
+                // the upper levels, deepest first: each node rescales its
+                // chargers' power, then the station sums are taken again
+#pragma unroll
+                for (int j = 0; j < kMaxUpperDepth; ++j) {
+                    if (j >= TL) break;
+                    uint32_t lm[PPL];
+                    float Su[PPL], Sr[PPL];
+#pragma unroll
+                    for (int q = 0; q < PPL; ++q) {
+                        lm[q] = level_meta(m2[q], j);
+                        Su[q] = P[q];
+                        Sr[q] = Preq[q];
+                    }
+                    seg_scan<PPL, LPE>(Su, lm, le, dhu[j]);
+                    if (p.a_con != 0.f) seg_scan<PPL, LPE>(Sr, lm, le, dhu[j]);
+#pragma unroll
+                    for (int q = 0; q < PPL; ++q) {
+                        if (lm[q] & kMetaTail) {
+                            const int us = ew * GPS + (int)((lm[q] >> kMetaGroupShift) & 31u);
+                            const float cu = ws->ucap[j][us];
+                            const float mag = V2G ? fabsf(Su[q]) : Su[q];
+                            ws->uscale[j][us] = mag > cu ? __fdividef(cu, mag) : 1.0f;
+                            if (p.a_con != 0.f)
+                                over = fmaxf(over, ((V2G ? fabsf(Sr[q]) : Sr[q]) - cu) * ws->uinv[j][us]);
+                        }
+                    }
+                    __syncwarp();
+#pragma unroll
+                    for (int q = 0; q < PPL; ++q)
+                        P[q] *= ws->uscale[j][ew * GPS + (int)((lm[q] >> kMetaGroupShift) & 31u)];
+                    __syncwarp();
+                }
+                sp = 0.f;
+                se = 0.f;
+                sn = 0.f;
+#pragma unroll
+                for (int q = 0; q < PPL; ++q) {
+                    sp += P[q];
+                    const bool dcq = meta[q] & kMetaDC;
+                    if (V2G) {
+                        if (P[q] >= 0.f) se += P[q] * (dcq ? p.inv_eta1 : p.inv_eta0);
+                        else sn += P[q] * (dcq ? p.eta1 : p.eta0);
+                    } else {
+                        se += P[q] * (dcq ? p.inv_eta1 : p.inv_eta0);
+                    }
+                }
             }
         }
         __syncwarp();
@@ -640,12 +737,20 @@ template <int CLO, int CHI, int MINB, bool V2G, bool EXT>
 __global__ void __launch_bounds__(256, MINB) k_step_fused(DevBatch b, DevParams p, FusedIO io)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    WarpSmem* ws = reinterpret_cast<WarpSmem*>(smem_raw) + (threadIdx.x >> 5);
+    using SM = std::conditional_t<EXT, WarpSmemExt, WarpSmem>;
+    SM* ws = reinterpret_cast<SM*>(smem_raw) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     for (int i = lane; i < 64; i += 32) {   // padding chargers read defined values
         ws->scale[i] = 1.0f;
         ws->gcap[i] = 0.f;
         ws->ginv[i] = 1.f;
+        if constexpr (EXT) {
+            for (int j = 0; j < kMaxUpperDepth; ++j) {
+                ws->uscale[j][i] = 1.0f;
+                ws->ucap[j][i] = FLT_MAX;
+                ws->uinv[j][i] = 1.f;
+            }
+        }
     }
     __syncwarp();
     for (;;) {
@@ -672,8 +777,9 @@ __global__ void __launch_bounds__(256, MINB) k_step_fused(DevBatch b, DevParams 
 namespace {
 
 // [v2g | ext << 1]: charge-only / vehicle-to-grid; ext instances add, switched
-// at run time, the Delta-current form and charge-sensitive users
+// at run time, the Delta-current form, charge-sensitive users and deeper trees
 constexpr int kForms = 4;
+constexpr size_t smem_per_warp(int v) { return (v & 2) ? sizeof(WarpSmemExt) : sizeof(WarpSmem); }
 void (*const kSmallKernel[kForms])(DevBatch, DevParams, FusedIO) = {
     &k_step_fused<0, 3, 3, false, false>, &k_step_fused<0, 3, 3, true, false>,
     &k_step_fused<0, 3, 3, false, true>, &k_step_fused<0, 3, 3, true, true>};
@@ -707,20 +813,20 @@ bool raise_smem_limit()
     static const bool ok = [] {
         for (int v = 0; v < kForms; ++v)
             if (cudaFuncSetAttribute((const void*)kSmallKernel[v], cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     8 * (int)sizeof(WarpSmem)) != cudaSuccess ||
+                                     8 * (int)smem_per_warp(v)) != cudaSuccess ||
                 cudaFuncSetAttribute((const void*)kLargeKernel[v], cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     8 * (int)sizeof(WarpSmem)) != cudaSuccess)
+                                     8 * (int)smem_per_warp(v)) != cudaSuccess)
                 return false;
         return true;
     }();
     return ok;
 }
 
-int blocks_per_sm(const void* kernel, int threads)
+int blocks_per_sm(const void* kernel, int v, int threads)
 {
     if (!raise_smem_limit()) return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, (threads / 32) * sizeof(WarpSmem)) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, (threads / 32) * smem_per_warp(v)) !=
         cudaSuccess)
         return 0;
     return n;
@@ -732,8 +838,8 @@ bool fused_block_size_ok(int threads)
 {
     if (threads < 32 || threads > 256 || threads % 32 != 0) return false;
     for (int v = 0; v < kForms; ++v)
-        if (blocks_per_sm((const void*)kSmallKernel[v], threads) <= 0 ||
-            blocks_per_sm((const void*)kLargeKernel[v], threads) <= 0)
+        if (blocks_per_sm((const void*)kSmallKernel[v], v, threads) <= 0 ||
+            blocks_per_sm((const void*)kLargeKernel[v], v, threads) <= 0)
             return false;
     return true;
 }
@@ -742,17 +848,17 @@ void launch_step_fused(const DevBatch& b, const DevParams& p, const FusedIO& io,
                        cudaStream_t st)
 {
     const int warps = threads / 32;
-    const size_t smem = (size_t)warps * sizeof(WarpSmem);
+    const int v = (p.v2g ? 1 : 0) | ((p.delta || p.cs_share || p.tree_levels) ? 2 : 0);
+    const size_t smem = (size_t)warps * smem_per_warp(v);
     const FusedIO big = sub_schedule(io, 4, 4, io.counter);
     const FusedIO small = sub_schedule(io, 0, 3, io.counter + 1);
-    const int v = (p.v2g ? 1 : 0) | ((p.delta || p.cs_share) ? 2 : 0);
     if (big.total_tiles > 0) {             // the heavy class first
-        const int per_sm = blocks_per_sm((const void*)kLargeKernel[v], threads);
+        const int per_sm = blocks_per_sm((const void*)kLargeKernel[v], v, threads);
         const int blocks = std::max(1, std::min(per_sm * sm_count, (big.total_tiles + warps - 1) / warps));
         kLargeKernel[v]<<<blocks, threads, smem, st>>>(b, p, big);
     }
     if (small.total_tiles > 0) {
-        const int per_sm = blocks_per_sm((const void*)kSmallKernel[v], threads);
+        const int per_sm = blocks_per_sm((const void*)kSmallKernel[v], v, threads);
         const int blocks = std::max(1, std::min(per_sm * sm_count, (small.total_tiles + warps - 1) / warps));
         kSmallKernel[v]<<<blocks, threads, smem, st>>>(b, p, small);
     }

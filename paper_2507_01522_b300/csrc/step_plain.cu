@@ -79,6 +79,59 @@ __device__ __forceinline__ void step_station(const DevBatch& b, const DevParams&
             Sn = 0.f;
         }
     }
+    // deeper trees: the nodes above the groups, level by level (deepest
+    // first), each node rescaling its chargers' (already group-rescaled)
+    // power; then the root sums over the fully rescaled powers
+    float uscale[kMaxUpperDepth][32];
+    const int TL = p.tree_levels;
+    auto upper_mult = [&](long long i, int levels) -> float {
+        float f = 1.f;
+        for (int j = 0; j < levels; ++j) f *= uscale[j][(b.meta2[i] >> (8 * j + 2)) & 31u];
+        return f;
+    };
+    if (TL > 0) {
+        for (int j = 0; j < TL; ++j) {
+            float Su = 0.f, Sr = 0.f;
+            for (int q = 0; q < n; ++q) {
+                const long long i = pb + q;
+                const uint32_t m = b.meta[i], m2 = b.meta2[i] >> (8 * j);
+                float Pr = 0.f;
+                if (b.trem[i] > 0)
+                    Pr = clip(level_of(q), m & kMetaDC, b.soc[i], b.erem[i], b.cap[i], b.rbar[i], b.pw[i]);
+                if (m2 & 1u) {
+                    Su = 0.f;
+                    Sr = 0.f;
+                }
+                Su += Pr * gscale[(m >> kMetaGroupShift) & 31] * upper_mult(i, j);
+                Sr += Pr;
+                if (m2 & 2u) {
+                    const float cap_u = b.ucap[(long long)j * b.port_slots + i];
+                    const float mag = V2G ? fabsf(Su) : Su;
+                    uscale[j][(m2 >> 2) & 31u] = mag > cap_u ? __fdividef(cap_u, mag) : 1.0f;
+                    over_max = fmaxf(over_max, ((V2G ? fabsf(Sr) : Sr) - cap_u) * b.uinv[(long long)j * b.port_slots + i]);
+                }
+            }
+        }
+        s_grp = 0.f;
+        se_grp = 0.f;
+        sn_grp = 0.f;
+        for (int q = 0; q < n; ++q) {
+            const long long i = pb + q;
+            if (b.trem[i] == 0) continue;
+            const uint32_t m = b.meta[i];
+            const bool dc = m & kMetaDC;
+            const float P = clip(level_of(q), dc, b.soc[i], b.erem[i], b.cap[i], b.rbar[i], b.pw[i]) *
+                            gscale[(m >> kMetaGroupShift) & 31] * upper_mult(i, TL);
+            s_grp += P;
+            if (V2G) {
+                if (P >= 0.f) se_grp += P * (dc ? p.inv_eta1 : p.inv_eta0);
+                else sn_grp += P * (dc ? p.eta1 : p.eta0);
+            } else {
+                se_grp += P * (dc ? p.inv_eta1 : p.inv_eta0);
+            }
+        }
+    }
+
     // station battery (a leaf of the root), then the root node
     float Pb = 0.f, bsoc = 0.f;
     if (V2G) {
@@ -104,7 +157,9 @@ __device__ __forceinline__ void step_station(const DevBatch& b, const DevParams&
             float soc = b.soc[i], erem = b.erem[i];
             const float cap = b.cap[i];
             P = clip(level_of(q), dc, soc, erem, cap, b.rbar[i], b.pw[i]);
-            P = P * gscale[(m >> kMetaGroupShift) & 31] * s_root;
+            P = P * gscale[(m >> kMetaGroupShift) & 31];
+            if (TL > 0) P *= upper_mult(i, TL);
+            P *= s_root;
             const float dE = P * p.dt;
             soc = fminf(soc + __fdividef(dE, cap), 1.0f);
             if (V2G) soc = fmaxf(soc, 0.0f);

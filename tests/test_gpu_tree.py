@@ -1,0 +1,115 @@
+"""Parity of deeper architecture trees (Fig. charge-tree c: nodes above the
+groups, Eq. ArchConst at every node, proportional rescale deepest first)
+with the oracle, through the C interface: plain and fused kernels, charge-
+only and V2G, with charge-sensitive users and the Delta form, every penalty
+on; events exact, floats within the tolerances of tests/parity.py."""
+import numpy as np
+import pytest
+
+from oracle import Oracle
+from paper_2507_01522_b300 import inputs as I
+
+from parity import STEP_RTOL, assert_events_equal, assert_floats_close, assert_reward_close, reward_scale, to_f32_state, widen
+from test_gpu_parity import compare_traj
+from test_gpu_v2g import V2G, compare_traj as compare_traj_v2g
+from test_gpu_cs import CS, compare_cs
+
+pytestmark = pytest.mark.gpu
+
+
+def make(n_envs=96, seed=4, **extra):
+    import torch
+    from paper_2507_01522_b300.chargax import Batch
+    w = I.tree_workload(n_envs, seed=seed)
+    kw = dict(alpha_con=0.05, alpha_sat=0.1, alpha_decl=0.2, c_fixed=0.01)
+    kw.update(extra)
+    w.params = I.EnvParams(**{**w.params.__dict__, **kw})
+    return w, Batch(w), Oracle(w), torch
+
+
+@pytest.mark.parametrize("mode,k", [("plain", 1), ("fused", 24)])
+def test_tree_random_levels(cuda_lib, mode, k):
+    w, b, o, torch = make()
+    compare_traj(w, b, o, torch, 96, mode=mode, k=k)
+
+
+@pytest.mark.parametrize("mode,k", [("plain", 1), ("fused", 16)])
+def test_tree_given_levels(cuda_lib, mode, k):
+    w, b, o, torch = make(n_envs=64, seed=9)
+    rng = np.random.default_rng(1)
+    acts = rng.integers(0, 11, size=(b.P, 64)).astype(np.int8)
+    compare_traj(w, b, o, torch, 64, mode=mode, k=k, actions=acts)
+
+
+@pytest.mark.parametrize("mode,k", [("plain", 1), ("fused", 24)])
+def test_tree_v2g(cuda_lib, mode, k):
+    w, b, o, torch = make(**V2G)
+    compare_traj_v2g(w, b, o, torch, 72, mode=mode, k=k)
+
+
+@pytest.mark.parametrize("mode,k", [("plain", 1), ("fused", 32)])
+def test_tree_with_charge_sensitive_users_and_delta(cuda_lib, mode, k):
+    w, b, o, torch = make(**CS, action_delta=1, n_levels=21)
+    compare_cs(w, b, o, torch, 96, mode=mode, k=k)
+
+
+def test_tree_fused_two_episodes(cuda_lib):
+    w, b, o, torch = make(n_envs=384, seed=12)
+    compare_traj(w, b, o, torch, 2 * 288, mode="fused", k=96)
+
+
+@pytest.mark.parametrize("mode", ["plain", "fused"])
+def test_tree_single_step_from_oracle_state(cuda_lib, mode):
+    w, b, o, torch = make()
+    rng = np.random.default_rng(6)
+    for _ in range(25):
+        o.step(None)
+    for trial in range(3):
+        s32 = to_f32_state(o.state())
+        o.set_state(widen(s32))
+        b.set_state(s32)
+        acts = rng.integers(0, 11, b.P).astype(np.int8)
+        reward = torch.zeros(b.E, device="cuda")
+        a = torch.from_numpy(acts).cuda()
+        if mode == "plain":
+            b.step(actions=a, reward=reward)
+        else:
+            b.step_n(1, actions=a, reward=reward, lda=1, ld_out=1)
+        ro, _ = o.step(acts)
+        gs, os_ = b.get_state(), o.state()
+        assert_events_equal(gs, os_, where=f"trial {trial}")
+        assert_floats_close(gs, os_, STEP_RTOL, where=f"trial {trial}", cap_hi=w.params.cap_kwh[1])
+        assert_reward_close(reward.cpu().numpy(), ro, reward_scale(o.info(), w.params), STEP_RTOL, where=f"trial {trial}")
+        for _ in range(5):
+            o.step(None)
+
+
+def test_tree_rejections(cuda_lib):
+    from paper_2507_01522_b300.chargax import CHX_EINVAL, Batch, ChxError
+    w = I.tree_workload(4, seed=1)
+    st = w.stations
+    bad = [
+        dict(upper_parent=np.where(np.arange(len(st.upper_parent)) == 0, 0, st.upper_parent)),   # a cycle
+        dict(group_parent=np.full_like(st.group_parent, 99)),                                      # out of range
+        dict(upper_limit_kw=np.zeros_like(st.upper_limit_kw)),                                     # limit 0
+    ]
+    for change in bad:
+        w2 = I.Workload(w.name, w.params, I.Stations(**{**st.__dict__, **change}), w.exo, 0)
+        with pytest.raises(ChxError) as ei:
+            Batch(w2)
+        assert ei.value.code == CHX_EINVAL
+    # groups of one node that are not consecutive
+    from test_oracle_tree_pins import tree_station
+    w3 = tree_station([2, 2, 2], [50.0] * 3, [0, -1, 0], [-1], [60.0])
+    with pytest.raises(ChxError) as ei:
+        Batch(w3)
+    assert ei.value.code == CHX_EINVAL
+    # four levels above the groups
+    w4 = tree_station([2], [50.0], [3], [-1, 0, 1, 2], [60.0] * 4)
+    with pytest.raises(ChxError) as ei:
+        Batch(w4)
+    assert ei.value.code == CHX_EINVAL
+    b = Batch(w)
+    pw = I.policy_weights(8 + 6 * 63, 63)
+    with pytest.raises(ChxError):
+        b.policy_load(pw.w1, pw.b1, pw.w2, pw.b2, pw.w3, pw.b3)
