@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-policy", action="store_true", help="skip the on-device policy rollout leg")
     ap.add_argument("--no-v2g", action="store_true", help="skip the vehicle-to-grid leg")
+    ap.add_argument("--no-variants", action="store_true", help="skip the charge-sensitive and deeper-tree legs")
     ap.add_argument("--policy-steps", type=int, default=128, help="rollout buffer length of the policy leg")
     ap.add_argument("--policy-only", action="store_true",
                     help="time only the policy rollout leg and print its JSON object (profiling aid)")
@@ -427,8 +428,14 @@ def run_b300(args):
 
     line["clocks"] = ck.summary()
     if not args.no_v2g:
-        line["v2g"] = run_v2g(args, rank, ws, dev, timed, w, line["value"])
+        line["v2g"] = run_variant(args, rank, ws, timed, I.v2g_variant(w), line["value"], dev)
         line["gpu_launches"] += line["v2g"]["gpu_launches"]
+    if not args.no_variants:
+        wc = I.Workload(w.name + "-cs128", I.EnvParams(**{**w.params.__dict__, "cs_share_256": 128,
+                                                          "soc_target": 0.8}), w.stations, w.exo, w.seed)
+        line["charge_sensitive"] = run_variant(args, rank, ws, timed, wc, line["value"], dev)
+        line["tree"] = run_variant(args, rank, ws, timed, I.tree_workload(args.n_envs, seed=0), line["value"], dev)
+        line["gpu_launches"] += line["charge_sensitive"]["gpu_launches"] + line["tree"]["gpu_launches"]
     if not args.no_policy:
         del reward, done, obs
         pol = run_policy_rollout(args, rank, ws, dev, timed, pk)
@@ -446,15 +453,14 @@ def run_b300(args):
     barrier(ws)
 
 
-def run_v2g(args, rank, ws, dev, timed, w, charge_only_value):
-    """The same batch in vehicle-to-grid mode (signed levels, discharge
-    taper, station battery, feed-in price, degradation), fused form, same
-    timing protocol as the headline leg."""
+def run_variant(args, rank, ws, timed, wv, charge_only_value, dev):
+    """A variant of the method on the same scale, fused form, the headline
+    leg's timing protocol: vehicle-to-grid mode (signed levels, discharge
+    taper, station battery, feed-in price, degradation), charge-sensitive
+    users, or the deeper trees of Fig. charge-tree c."""
     import torch
     from paper_2507_01522_b300 import chargax
-    from paper_2507_01522_b300 import inputs as I
 
-    wv = I.v2g_variant(w)
     T = wv.params.ep_len
     b = chargax.Batch(wv, seed=rank_seed(rank))
     K, W = b.autotune(T)
@@ -471,9 +477,11 @@ def run_v2g(args, rank, ws, dev, timed, w, charge_only_value):
     total = max_over_ranks(sum(ms) / 1e3, ws)
     value = b.E * T * args.steps * ws / total
     out = {"value": value, "unit": "env-steps/s", "ms_per_step": 1e3 * total / args.steps, "workload": wv.name,
-           "n_levels": wv.params.n_levels, "steps_per_launch": K, "warps_per_block": W,
-           "actions": f"Philox uniform {wv.params.n_levels} signed levels per charger and battery, in-kernel",
-           "v2g_over_charge_only": value / charge_only_value,
+           "n_envs": b.E, "n_chargers": b.P, "n_levels": wv.params.n_levels, "steps_per_launch": K,
+           "warps_per_block": W,
+           "actions": f"Philox uniform {wv.params.n_levels} levels per charger" + (" and battery" if wv.params.v2g else "")
+                      + ", in-kernel",
+           "over_charge_only": value / charge_only_value,
            "gpu_launches": math.ceil(T / K) * args.steps}
     del b
     return out
