@@ -226,6 +226,8 @@ struct WarpSmemExt : WarpSmem {
     float ucap[kMaxUpperDepth][64];
     float uinv[kMaxUpperDepth][64];
     float uscale[kMaxUpperDepth][64];
+    uint32_t m2[4][32];                    // per lane: its chargers' meta2 words
+    int dhu[kMaxUpperDepth][32];           // per lane: head distance at each level
 };
 
 // level j's byte of meta2 in the layout of the group bits of meta
@@ -239,7 +241,7 @@ __device__ __forceinline__ uint32_t level_meta(uint32_t m2, int j)
 // station's lanes, its level after the chargers' or drawn at charger index
 // n), signed limits, discharge energy after the port loss, two-case profit,
 // degradation penalty; observation with the battery features.
-template <int C, bool V2G, bool EXT, class SM>
+template <int C, bool V2G, bool EXT, bool TREE, class SM>
 __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, const FusedIO& io, int tile,
                                          SM* ws)
 {
@@ -328,14 +330,14 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
     }
     // deeper trees (extended instances): per level the chargers' node bits,
     // its head distance, and the nodes' limits at their tails
-    const int TL = EXT ? p.tree_levels : 0;
-    uint32_t m2[PPL];
-    int dhu[kMaxUpperDepth] = {0, 0, 0};
-#pragma unroll
-    for (int q = 0; q < PPL; ++q) m2[q] = 0u;
-    if constexpr (EXT) {
+    // (kept in shared memory per lane: live for the whole tile)
+    const int TL = TREE ? p.tree_levels : 0;
+    if constexpr (TREE) {
         if (TL > 0) {
+            uint32_t m2[PPL];
             ld_vec_u32(b.meta2 + pb, m2);
+#pragma unroll
+            for (int q = 0; q < PPL; ++q) ws->m2[q][lane] = m2[q];
 #pragma unroll
             for (int j = 0; j < kMaxUpperDepth; ++j) {
                 if (j >= TL) break;
@@ -349,7 +351,7 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
                         ws->uinv[j][us] = b.uinv[(long long)j * b.port_slots + pb + q];
                     }
                 }
-                dhu[j] = head_distance<PPL, LPE>(lm, le);
+                ws->dhu[j][lane] = head_distance<PPL, LPE>(lm, le);
             }
         }
     }
@@ -433,10 +435,30 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
             }
         }
         __syncwarp();
-        float raw = 0.f, sp = 0.f, se = 0.f, sn = 0.f;
-        float Preq[PPL];                   // requested power (the upper nodes' penalty)
+        if constexpr (TREE) {
+            // the upper nodes' penalty, on the requested power (P still is)
+            if (TL > 0 && p.a_con != 0.f) {
 #pragma unroll
-        for (int q = 0; q < PPL; ++q) Preq[q] = P[q];
+                for (int j = 0; j < kMaxUpperDepth; ++j) {
+                    if (j >= TL) break;
+                    uint32_t lm[PPL];
+                    float Sr[PPL];
+#pragma unroll
+                    for (int q = 0; q < PPL; ++q) {
+                        lm[q] = level_meta(ws->m2[q][lane], j);
+                        Sr[q] = P[q];
+                    }
+                    seg_scan<PPL, LPE>(Sr, lm, le, ws->dhu[j][lane]);
+#pragma unroll
+                    for (int q = 0; q < PPL; ++q)
+                        if (lm[q] & kMetaTail) {
+                            const int us = ew * GPS + (int)((lm[q] >> kMetaGroupShift) & 31u);
+                            over = fmaxf(over, ((V2G ? fabsf(Sr[q]) : Sr[q]) - ws->ucap[j][us]) * ws->uinv[j][us]);
+                        }
+                }
+            }
+        }
+        float raw = 0.f, sp = 0.f, se = 0.f, sn = 0.f;
 #pragma unroll
         for (int q = 0; q < PPL; ++q) {
             raw += P[q];
@@ -450,7 +472,7 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
                 se += P[q] * (dcq ? p.inv_eta1 : p.inv_eta0);
             }
         }
-        if constexpr (EXT) {
+        if constexpr (TREE) {
             if (TL > 0) {
                 // the upper levels, deepest first: each node rescales its
                 // chargers' power, then the station sums are taken again
@@ -458,15 +480,13 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
                 for (int j = 0; j < kMaxUpperDepth; ++j) {
                     if (j >= TL) break;
                     uint32_t lm[PPL];
-                    float Su[PPL], Sr[PPL];
+                    float Su[PPL];
 #pragma unroll
                     for (int q = 0; q < PPL; ++q) {
-                        lm[q] = level_meta(m2[q], j);
+                        lm[q] = level_meta(ws->m2[q][lane], j);
                         Su[q] = P[q];
-                        Sr[q] = Preq[q];
                     }
-                    seg_scan<PPL, LPE>(Su, lm, le, dhu[j]);
-                    if (p.a_con != 0.f) seg_scan<PPL, LPE>(Sr, lm, le, dhu[j]);
+                    seg_scan<PPL, LPE>(Su, lm, le, ws->dhu[j][lane]);
 #pragma unroll
                     for (int q = 0; q < PPL; ++q) {
                         if (lm[q] & kMetaTail) {
@@ -474,8 +494,6 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
                             const float cu = ws->ucap[j][us];
                             const float mag = V2G ? fabsf(Su[q]) : Su[q];
                             ws->uscale[j][us] = mag > cu ? __fdividef(cu, mag) : 1.0f;
-                            if (p.a_con != 0.f)
-                                over = fmaxf(over, ((V2G ? fabsf(Sr[q]) : Sr[q]) - cu) * ws->uinv[j][us]);
                         }
                     }
                     __syncwarp();
@@ -733,18 +751,18 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
 // instantiation for the 128-charger class (4 chargers per lane, more
 // registers), one for the others, so the smaller classes keep more warps
 // resident.
-template <int CLO, int CHI, int MINB, bool V2G, bool EXT>
+template <int CLO, int CHI, int MINB, bool V2G, bool EXT, bool TREE>
 __global__ void __launch_bounds__(256, MINB) k_step_fused(DevBatch b, DevParams p, FusedIO io)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    using SM = std::conditional_t<EXT, WarpSmemExt, WarpSmem>;
+    using SM = std::conditional_t<TREE, WarpSmemExt, WarpSmem>;
     SM* ws = reinterpret_cast<SM*>(smem_raw) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     for (int i = lane; i < 64; i += 32) {   // padding chargers read defined values
         ws->scale[i] = 1.0f;
         ws->gcap[i] = 0.f;
         ws->ginv[i] = 1.f;
-        if constexpr (EXT) {
+        if constexpr (TREE) {
             for (int j = 0; j < kMaxUpperDepth; ++j) {
                 ws->uscale[j][i] = 1.0f;
                 ws->ucap[j][i] = FLT_MAX;
@@ -766,26 +784,29 @@ __global__ void __launch_bounds__(256, MINB) k_step_fused(DevBatch b, DevParams 
                 tile = tile_id - io.sched_tile_base[i];
             }
         }
-        if (CLO <= 0 && 0 <= CHI && cls == 0) run_tile<8, V2G, EXT>(b, p, io, tile, ws);
-        if (CLO <= 1 && 1 <= CHI && cls == 1) run_tile<16, V2G, EXT>(b, p, io, tile, ws);
-        if (CLO <= 2 && 2 <= CHI && cls == 2) run_tile<32, V2G, EXT>(b, p, io, tile, ws);
-        if (CLO <= 3 && 3 <= CHI && cls == 3) run_tile<64, V2G, EXT>(b, p, io, tile, ws);
-        if (CLO <= 4 && 4 <= CHI && cls == 4) run_tile<128, V2G, EXT>(b, p, io, tile, ws);
+        if (CLO <= 0 && 0 <= CHI && cls == 0) run_tile<8, V2G, EXT, TREE>(b, p, io, tile, ws);
+        if (CLO <= 1 && 1 <= CHI && cls == 1) run_tile<16, V2G, EXT, TREE>(b, p, io, tile, ws);
+        if (CLO <= 2 && 2 <= CHI && cls == 2) run_tile<32, V2G, EXT, TREE>(b, p, io, tile, ws);
+        if (CLO <= 3 && 3 <= CHI && cls == 3) run_tile<64, V2G, EXT, TREE>(b, p, io, tile, ws);
+        if (CLO <= 4 && 4 <= CHI && cls == 4) run_tile<128, V2G, EXT, TREE>(b, p, io, tile, ws);
     }
 }
 
 namespace {
 
-// [v2g | ext << 1]: charge-only / vehicle-to-grid; ext instances add, switched
-// at run time, the Delta-current form, charge-sensitive users and deeper trees
-constexpr int kForms = 4;
-constexpr size_t smem_per_warp(int v) { return (v & 2) ? sizeof(WarpSmemExt) : sizeof(WarpSmem); }
-void (*const kSmallKernel[kForms])(DevBatch, DevParams, FusedIO) = {
-    &k_step_fused<0, 3, 3, false, false>, &k_step_fused<0, 3, 3, true, false>,
-    &k_step_fused<0, 3, 3, false, true>, &k_step_fused<0, 3, 3, true, true>};
-void (*const kLargeKernel[kForms])(DevBatch, DevParams, FusedIO) = {
-    &k_step_fused<4, 4, 2, false, false>, &k_step_fused<4, 4, 2, true, false>,
-    &k_step_fused<4, 4, 2, false, true>, &k_step_fused<4, 4, 2, true, true>};
+// [v2g | ext << 1 | tree << 2]: charge-only / vehicle-to-grid; ext instances
+// add, switched at run time, the Delta-current form and charge-sensitive
+// users, tree instances the levels of nodes above the groups
+constexpr int kForms = 8;
+constexpr size_t smem_per_warp(int v) { return (v & 4) ? sizeof(WarpSmemExt) : sizeof(WarpSmem); }
+#define CHX_FORMS(CLO, CHI, MINB)                                                                              \
+    {&k_step_fused<CLO, CHI, MINB, false, false, false>, &k_step_fused<CLO, CHI, MINB, true, false, false>,  \
+     &k_step_fused<CLO, CHI, MINB, false, true, false>, &k_step_fused<CLO, CHI, MINB, true, true, false>,    \
+     &k_step_fused<CLO, CHI, MINB, false, false, true>, &k_step_fused<CLO, CHI, MINB, true, false, true>,    \
+     &k_step_fused<CLO, CHI, MINB, false, true, true>, &k_step_fused<CLO, CHI, MINB, true, true, true>}
+void (*const kSmallKernel[kForms])(DevBatch, DevParams, FusedIO) = CHX_FORMS(0, 3, 3);
+void (*const kLargeKernel[kForms])(DevBatch, DevParams, FusedIO) = CHX_FORMS(4, 4, 2);
+#undef CHX_FORMS
 
 // the part of a schedule whose classes lie in [clo, chi], tiles renumbered
 FusedIO sub_schedule(const FusedIO& io, int clo, int chi, int* counter)
@@ -848,7 +869,7 @@ void launch_step_fused(const DevBatch& b, const DevParams& p, const FusedIO& io,
                        cudaStream_t st)
 {
     const int warps = threads / 32;
-    const int v = (p.v2g ? 1 : 0) | ((p.delta || p.cs_share || p.tree_levels) ? 2 : 0);
+    const int v = (p.v2g ? 1 : 0) | ((p.delta || p.cs_share) ? 2 : 0) | (p.tree_levels ? 4 : 0);
     const size_t smem = (size_t)warps * smem_per_warp(v);
     const FusedIO big = sub_schedule(io, 4, 4, io.counter);
     const FusedIO small = sub_schedule(io, 0, 3, io.counter + 1);
