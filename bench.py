@@ -463,7 +463,11 @@ def run_variant(args, rank, ws, timed, wv, charge_only_value, dev):
 
     T = wv.params.ep_len
     b = chargax.Batch(wv, seed=rank_seed(rank))
-    K, W = b.autotune(T)
+    if args.shape:
+        K, W = (int(x) for x in args.shape.split(","))
+        b.set_launch(K, W)
+    else:
+        K, W = b.autotune(T)
     reward = torch.empty(b.E, T, device=dev)
     done = torch.empty(b.E, T, dtype=torch.uint8, device=dev)
     obs = torch.empty(b.obs_size, device=dev)
