@@ -239,10 +239,12 @@ int chx_step_n(chx_handle* h, int32_t k_steps, const int8_t* d_actions, int64_t 
 int chx_rollout(chx_handle* h, int32_t n_steps, float* d_reward, uint8_t* d_done, float* d_obs,
                 void* stream);
 
-/* Same as chx_rollout with HOST outputs: the device results are copied to
- * h_reward [n_envs*n_steps], h_done [n_envs*n_steps] and h_obs (any may be
- * NULL; pinned memory gives full copy bandwidth) and the call returns when
- * they are there. */
+/* chx_rollout with HOST outputs, step-major: h_reward[k*n_envs + e] and
+ * h_done[k*n_envs + e] for step k of env e ([n_steps][n_envs], a rollout
+ * buffer's layout), h_obs as chx_rollout (any may be NULL; pinned memory
+ * gives full copy bandwidth).  The steps run in up to 4 launches whose
+ * outputs are copied while the next launch computes; the call returns when
+ * everything is on the host. */
 int chx_rollout_host(chx_handle* h, int32_t n_steps, float* h_reward, uint8_t* h_done, float* h_obs,
                      void* stream);
 

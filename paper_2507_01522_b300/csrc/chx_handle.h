@@ -12,6 +12,8 @@ namespace chx {
 
 using Buffers = std::vector<void*>;
 
+constexpr int kHostChunks = 4;            // launches of a host-call rollout (copies overlap the next)
+
 struct GraphKey {
     int n_steps = 0;
     float* reward = nullptr;
@@ -86,6 +88,8 @@ struct chx_handle {
     int warps_per_block = 8, steps_per_launch = 32;
     float tuned_ms = 0.f;
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t copy_stream = nullptr;    // device-to-host copies of the host-call rollout
+    cudaEvent_t chunk_done[chx::kHostChunks] = {};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     chx::GraphKey graph_key{};
@@ -104,7 +108,7 @@ void build_poisson_cdf(const float* lam, size_t n_rows_steps, std::vector<float>
 int build_handle(const chx_stations* st, const chx_env_params* prm, const chx_exo* exo, uint64_t seed,
                  int min_pad_envs_per_class, chx_handle** out);
 int enqueue_fused(chx_handle* h, int k_steps, const int8_t* actions, long long lda, float* reward, uint8_t* done,
-                  long long ld_out, float* obs, int warps, cudaStream_t st);
+                  long long ld_out, float* obs, int warps, cudaStream_t st, long long ld_step = 1);
 void free_graph(chx_handle* h);
 void free_policy(chx_handle* h);
 }  // namespace chx

@@ -17,7 +17,8 @@ struct FusedIO {
     long long lda;
     float* reward;
     uint8_t* done;
-    long long ld_out;
+    long long ld_out;                      // env e, step k at e * ld_out + k * ld_step
+    long long ld_step;
     float* obs;
     int n_sched;
     int sched_cls[kNumClasses];

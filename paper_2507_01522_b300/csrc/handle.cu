@@ -552,6 +552,8 @@ int build_handle(const chx_stations* st, const chx_env_params* prm, const chx_ex
     h->warps_per_block = 8;
     h->steps_per_launch = 32;
     CUDA_TRY(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    CUDA_TRY(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+    for (auto& ev : h->chunk_done) CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
 
     launch_reset(b, h->dp, h->d_user_to_slot, nullptr, E, seed, 0);
     CUDA_TRY(cudaGetLastError());
@@ -587,6 +589,9 @@ extern "C" int chx_destroy(chx_handle* h)
     for (void* p : h->bufs) cudaFree(p);
     for (void* p : h->staging) cudaFree(p);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+    for (auto ev : h->chunk_done)
+        if (ev) cudaEventDestroy(ev);
     delete h;
     return CHX_OK;
 }
@@ -646,7 +651,7 @@ extern "C" int chx_step(chx_handle* h, const int8_t* d_actions, int64_t lda, flo
 namespace chx {
 
 int enqueue_fused(chx_handle* h, int k_steps, const int8_t* actions, long long lda, float* reward, uint8_t* done,
-                  long long ld_out, float* obs, int warps, cudaStream_t st)
+                  long long ld_out, float* obs, int warps, cudaStream_t st, long long ld_step)
 {
     FusedIO io = h->sched;
     io.k_steps = k_steps;
@@ -655,6 +660,7 @@ int enqueue_fused(chx_handle* h, int k_steps, const int8_t* actions, long long l
     io.reward = reward;
     io.done = done;
     io.ld_out = ld_out;
+    io.ld_step = ld_step;
     io.obs = obs;
     const int threads = warps * 32;
     if (!fused_block_size_ok(threads)) return fail(CHX_ECUDA, "fused kernel cannot be resident with this block size");
@@ -756,23 +762,38 @@ extern "C" int chx_rollout(chx_handle* h, int32_t n_steps, float* d_reward, uint
     return rollout(h, n_steps, d_reward, d_done, d_obs, (cudaStream_t)stream);
 }
 
+// Host-call rollout: the steps run in up to kHostChunks fused launches on the
+// caller's stream, outputs step-major in device staging; after each launch an
+// event lets the copy stream bring that chunk's rows (contiguous) to the host
+// while the next chunk computes; the observation follows the last chunk.
 extern "C" int chx_rollout_host(chx_handle* h, int32_t n_steps, float* h_reward, uint8_t* h_done, float* h_obs,
                                 void* stream)
 {
     if (!h) return fail(CHX_EINVAL, "null handle");
     if (n_steps < 1) return fail(CHX_EINVAL, "n_steps must be >= 1");
-    const size_t ne = (size_t)h->E * (size_t)n_steps;
-    const size_t nobs = (size_t)h->dp.obs_env * (size_t)h->E + (size_t)h->dp.obs_port * (size_t)h->P;
+    const size_t E = (size_t)h->E, ne = E * (size_t)n_steps;
+    const size_t nobs = (size_t)h->dp.obs_env * E + (size_t)h->dp.obs_port * (size_t)h->P;
     float* dr = h_reward ? (float*)staging(h, 0, ne * sizeof(float)) : nullptr;
     uint8_t* dd = h_done ? (uint8_t*)staging(h, 1, ne) : nullptr;
     float* dob = h_obs ? (float*)staging(h, 2, nobs * sizeof(float)) : nullptr;
     if ((h_reward && !dr) || (h_done && !dd) || (h_obs && !dob)) return fail(CHX_ENOMEM, "staging allocation failed");
-    cudaStream_t st = (cudaStream_t)stream;
-    int rc = rollout(h, n_steps, dr, dd, dob, st);
-    if (rc) return rc;
-    if (h_reward) CUDA_TRY(cudaMemcpyAsync(h_reward, dr, ne * sizeof(float), cudaMemcpyDeviceToHost, st));
-    if (h_done) CUDA_TRY(cudaMemcpyAsync(h_done, dd, ne, cudaMemcpyDeviceToHost, st));
-    if (h_obs) CUDA_TRY(cudaMemcpyAsync(h_obs, dob, nobs * sizeof(float), cudaMemcpyDeviceToHost, st));
+    cudaStream_t st = (cudaStream_t)stream, cs = h->copy_stream;
+    const int n_chunks = std::min(kHostChunks, (int)n_steps);
+    const int chunk = (n_steps + n_chunks - 1) / n_chunks;
+    for (int c = 0, k0 = 0; k0 < n_steps; ++c, k0 += chunk) {
+        const int k = std::min(chunk, n_steps - k0);
+        const bool last = k0 + k >= n_steps;
+        const size_t off = (size_t)k0 * E, n = (size_t)k * E;
+        int rc = enqueue_fused(h, k, nullptr, 0, dr ? dr + off : nullptr, dd ? dd + off : nullptr, 1,
+                               last ? dob : nullptr, h->warps_per_block, st, (long long)E);
+        if (rc) return rc;
+        CUDA_TRY(cudaEventRecord(h->chunk_done[c], st));
+        CUDA_TRY(cudaStreamWaitEvent(cs, h->chunk_done[c], 0));
+        if (h_reward) CUDA_TRY(cudaMemcpyAsync(h_reward + off, dr + off, n * sizeof(float), cudaMemcpyDeviceToHost, cs));
+        if (h_done) CUDA_TRY(cudaMemcpyAsync(h_done + off, dd + off, n, cudaMemcpyDeviceToHost, cs));
+        if (last && h_obs) CUDA_TRY(cudaMemcpyAsync(h_obs, dob, nobs * sizeof(float), cudaMemcpyDeviceToHost, cs));
+    }
+    CUDA_TRY(cudaStreamSynchronize(cs));
     CUDA_TRY(cudaStreamSynchronize(st));
     return CHX_OK;
 }

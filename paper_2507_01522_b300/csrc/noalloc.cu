@@ -83,6 +83,7 @@ extern "C" int chx_rollout_noalloc(chx_handle* h, int32_t n_steps, float* d_rewa
         io.reward = d_reward ? d_reward + k0 : nullptr;
         io.done = d_done ? d_done + k0 : nullptr;
         io.ld_out = n_steps;
+        io.ld_step = 1;
         io.obs = (i == launches - 1) ? d_obs : nullptr;
         io.counter = counters + i * chx::kFusedCounters;
         chx::launch_step_fused(h->b, h->dp, io, threads, h->sm_count, st);

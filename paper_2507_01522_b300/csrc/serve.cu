@@ -328,6 +328,7 @@ int launch_tick(chx_srv* s, int ti, const std::vector<Request*>& rq)
     io.reward = t.d_rew;
     io.done = t.d_done;
     io.ld_out = 1;
+    io.ld_step = 1;
     io.obs = obs_used > 0 ? t.d_obs : nullptr;
     io.counter = t.d_counter;
     io.gather = t.d_entries;

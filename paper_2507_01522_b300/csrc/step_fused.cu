@@ -675,8 +675,8 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
                 ws->st_u[ew][3] = 1u;
             }
             if (live) {
-                if (io.reward) io.reward[(long long)out_idx * io.ld_out + k] = r;
-                if (io.done) io.done[(long long)out_idx * io.ld_out + k] = fin ? 1 : 0;
+                if (io.reward) io.reward[(long long)out_idx * io.ld_out + (long long)k * io.ld_step] = r;
+                if (io.done) io.done[(long long)out_idx * io.ld_out + (long long)k * io.ld_step] = fin ? 1 : 0;
             }
         }
         if (fin) {                         // episode end: start a new one

@@ -278,24 +278,29 @@ def test_autotune_keeps_state(cuda_lib):
         np.testing.assert_array_equal(before[key], after[key])
 
 
-def test_host_api_matches_device(cuda_lib):
+@pytest.mark.parametrize("n", [20, 7, 3, 1])
+def test_host_api_matches_device(cuda_lib, n):
+    """The host-call rollout (step-major outputs, launches whose copies
+    overlap the next) equals the device rollout, bit for bit."""
     import torch
     from paper_2507_01522_b300.chargax import Batch
     w = odd_sizes()
     b1, b2 = Batch(w), Batch(w)
-    n = 20
     hr = np.zeros(b1.E * n, np.float32)
     hd = np.zeros(b1.E * n, np.uint8)
     ho = np.zeros(b1.obs_size, np.float32)
-    b1.rollout_host(n, hr, hd, ho)
-    r = torch.zeros(b2.E, n, device="cuda")
-    d = torch.zeros(b2.E, n, dtype=torch.uint8, device="cuda")
-    ob = torch.zeros(b2.obs_size, device="cuda")
-    b2.rollout(n, reward=r, done=d, obs=ob)
-    torch.cuda.synchronize()
-    np.testing.assert_array_equal(hr, r.cpu().numpy().ravel())
-    np.testing.assert_array_equal(hd, d.cpu().numpy().ravel())
-    np.testing.assert_array_equal(ho, ob.cpu().numpy())
+    for _ in range(2):                                  # back-to-back calls continue the episode
+        b1.rollout_host(n, hr, hd, ho)
+        r = torch.zeros(b2.E, n, device="cuda")
+        d = torch.zeros(b2.E, n, dtype=torch.uint8, device="cuda")
+        ob = torch.zeros(b2.obs_size, device="cuda")
+        b2.rollout(n, reward=r, done=d, obs=ob)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(hr.reshape(n, b1.E), r.cpu().numpy().T)
+        np.testing.assert_array_equal(hd.reshape(n, b1.E), d.cpu().numpy().T)
+        np.testing.assert_array_equal(ho, ob.cpu().numpy())
+    if n != 20:
+        return
     # plain step with host buffers
     acts = I.random_actions(np.random.default_rng(1), b1.P)
     hr1 = np.zeros(b1.E, np.float32)
