@@ -5,12 +5,14 @@ the V2G mode and the Delta-current form.
 The departure of a charge-sensitive car is a decision on a float: its
 demand counts as met once at most eps_cap = 1e-3 of its capacity remains.
 The kernel's remaining demand (FP32, a running sum) differs from the
-oracle's by at most TRAJ_RTOL x capacity, which the trajectory comparison
-asserts, a tenth of that threshold; so the two sides can only decide
-differently for a car the oracle finds within that distance of the
-threshold.  The tests take the oracle's decision first: in a launch where
-the oracle saw a tested car within TIE_MARGIN = 0.2 of the threshold
-(twice the asserted error), that station's rewards are not compared, and
+oracle's by the rounding of that sum: at most about 2e-5 x capacity along a
+linear approach (some 300 rounded subtractions), and a constant relative
+1e-6..1e-3 along the geometric approach of a demand-capped car under a
+binding node (each step keeps (1 - scale) of what is left, so the error
+shrinks with it); both stay below 2 % of the threshold (1e-3 x capacity).
+The tests take the oracle's decision first: in a launch where
+the oracle saw a tested car within TIE_MARGIN = 0.05 of the threshold
+(2.5 times that bound), that station's rewards are not compared, and
 if the two sides' states then differ it is re-synchronised, the oracle
 taking over the kernel's state of the station, before the comparison goes
 on; every other station is compared as everywhere else (events and Delta
@@ -30,7 +32,7 @@ from test_gpu_v2g import V2G, v2g_scale
 
 pytestmark = pytest.mark.gpu
 
-TIE_MARGIN = 0.2
+TIE_MARGIN = 0.05
 CS = dict(cs_share_256=128, alpha_sat1=0.05, beta_early=0.5, eps_cap=1e-3, soc_target=0.8)
 BASE = {"odd150": odd_sizes, "stressed": stressed, "hetero64": lambda: I.heterogeneous(n_envs=64),
         "hetero512": lambda: I.heterogeneous(n_envs=512, seed=2)}
@@ -254,3 +256,50 @@ def test_cs_rejections(cuda_lib):
     with pytest.raises(ChxError) as ei:
         b.policy_load(pw.w1, pw.b1, pw.w2, pw.b2, pw.w3, pw.b3)
     assert ei.value.code == CHX_EINVAL
+
+
+def test_cs_fullsize_sampled(cuda_lib):
+    """The benchmark's charge-sensitive leg: the 65536-station mixed batch
+    with half the users charge-sensitive, in the benchmark's launch shape
+    (one 288-step launch, 8 warps per block); 400 sampled stations
+    re-simulated by the oracle (a station drops out from a near-tie on, see
+    the module docstring; here about half of them stay in)."""
+    import torch
+    from paper_2507_01522_b300.chargax import Batch
+    w = I.heterogeneous(n_envs=65536)
+    w.params = I.EnvParams(**{**w.params.__dict__, **CS})
+    b = Batch(w)
+    b.set_launch(288, 8)
+    n = 287                                             # one launch; the state is mid-episode at the end
+    r = torch.zeros(b.E, n, device="cuda")
+    rng = np.random.default_rng(4)
+    ids = np.sort(rng.choice(w.stations.n_envs, 400, replace=False)).astype(np.int64)
+    sub = I.Workload(w.name, w.params, w.stations.subset(ids), w.exo, w.seed)
+    o = Oracle(sub, streams=ids)
+    b.rollout(n, reward=r)
+    torch.cuda.synchronize()
+    rg = r.cpu().numpy()[ids]
+    live = np.ones(len(ids), bool)
+    for j in range(n):
+        ro, _ = o.step(None)
+        live &= o.info_cs()["margin"] >= TIE_MARGIN
+        info = o.info()
+        sc = reward_scale(info, sub.params) + station_step_scale(sub, info) + sub.params.alpha_sat1 * (
+            np.abs(o.info_cs()["csat1"]) + 1.0)
+        assert_reward_close(rg[live, j], ro[live], sc[live], TRAJ_RTOL, where=f"step {j}")
+    # one launch of 287 steps cannot be re-synchronised: a station whose
+    # demand approached its threshold geometrically (binding group and grid
+    # limits, the rule in this batch) is dropped from its first near-tie on
+    assert live.sum() >= 120, int(live.sum())   # about half stay in (192 of 400 measured)
+    po = w.stations.port_off
+    sel = np.concatenate([np.arange(po[e], po[e + 1]) for e in ids])
+    gs = b.get_state()
+    s = {k: (v[sel] if v.shape[0] == b.P else v[ids]) for k, v in gs.items()}
+    os_ = o.state()
+    spo = sub.stations.port_off
+    keep_p = np.repeat(live, np.diff(spo))
+    g, rr = restrict(s, live, keep_p), restrict(os_, live, keep_p)
+    assert_events_equal(g, rr, "sampled")
+    np.testing.assert_array_equal(b.due()[sel][keep_p].astype(np.int32), o.due()[keep_p])
+    assert_traj_close(g, rr, charger_pmax(sub)[keep_p], TRAJ_RTOL, "sampled")
+    assert (gs["trem"] == 255).any()

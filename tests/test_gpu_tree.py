@@ -113,3 +113,55 @@ def test_tree_rejections(cuda_lib):
     pw = I.policy_weights(8 + 6 * 63, 63)
     with pytest.raises(ChxError):
         b.policy_load(pw.w1, pw.b1, pw.w2, pw.b2, pw.w3, pw.b3)
+
+
+def test_tree_fullsize_sampled(cuda_lib):
+    """The benchmark's Fig. c leg: 65536 tree stations through the rollout in
+    the benchmark's launch shape (one 288-step launch, 8 warps per block);
+    160 sampled stations re-simulated by the oracle, every node's constraint
+    checked on all stations."""
+    import torch
+    from paper_2507_01522_b300.chargax import Batch
+    from parity import TRAJ_RTOL, assert_traj_close, charger_pmax, station_step_scale
+    w = I.tree_workload(65536, seed=0)
+    b = Batch(w)
+    b.set_launch(288, 8)
+    n = 287                                             # one launch; the state is mid-episode at the end
+    r = torch.zeros(b.E, n, device="cuda")
+    rng = np.random.default_rng(3)
+    ids = np.sort(rng.choice(w.stations.n_envs, 160, replace=False)).astype(np.int64)
+    sub = I.Workload(w.name, w.params, w.stations.subset(ids), w.exo, w.seed)
+    o = Oracle(sub, streams=ids)
+    b.rollout(n, reward=r)
+    torch.cuda.synchronize()
+    rg = r.cpu().numpy()[ids]
+    for j in range(n):
+        ro, _ = o.step(None)
+        info = o.info()
+        assert_reward_close(rg[:, j], ro, reward_scale(info, sub.params) + station_step_scale(sub, info), TRAJ_RTOL,
+                            where=f"step {j}")
+    st = w.stations
+    po = st.port_off
+    sel = np.concatenate([np.arange(po[e], po[e + 1]) for e in ids])
+    gs = b.get_state()
+    s = {k: (v[sel] if v.shape[0] == b.P else v[ids]) for k, v in gs.items()}
+    assert_events_equal(s, o.state(), "sampled")
+    assert_traj_close(s, o.state(), charger_pmax(sub), TRAJ_RTOL, "sampled")
+    # every upper node within eta x I on all stations (last step's power)
+    pw = gs["p"].astype(np.float64)
+    go, uo = st.group_off, st.upper_off
+    gstart = np.concatenate([[0], np.cumsum(st.group_size)[:-1]])
+    gsum = np.add.reduceat(pw, gstart)
+    gcap = st.group_eta.astype(np.float64) * st.group_limit_kw
+    assert np.all(gsum <= gcap * (1 + 1e-5) + 1e-4)
+    for e in rng.choice(st.n_envs, 2000, replace=False):
+        gpar, upar = st.group_parent[go[e]:go[e + 1]], st.upper_parent[uo[e]:uo[e + 1]]
+        for u in range(st.n_upper[e]):
+            under = np.zeros(go[e + 1] - go[e], bool)
+            for g in range(len(under)):
+                a = gpar[g]
+                while a >= 0 and a != u:
+                    a = upar[a]
+                under[g] = a == u
+            cap = float(st.upper_eta[uo[e] + u]) * float(st.upper_limit_kw[uo[e] + u])
+            assert gsum[go[e]:go[e + 1]][under].sum() <= cap * (1 + 1e-5) + 1e-4
