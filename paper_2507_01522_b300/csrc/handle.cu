@@ -549,6 +549,8 @@ int build_handle(const chx_stations* st, const chx_env_params* prm, const chx_ex
     h->sched.sched_tile_base[h->sched.n_sched] = tb;
     h->sched.total_tiles = tb;
     h->sched.counter = h->d_counter;
+    h->sched.ld_out = 1;
+    h->sched.ld_step = 1;
     h->warps_per_block = 8;
     h->steps_per_launch = 32;
     CUDA_TRY(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
