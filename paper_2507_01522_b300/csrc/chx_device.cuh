@@ -232,16 +232,31 @@ __device__ __forceinline__ uint4 car_words(uint32_t uid, uint32_t n, uint32_t k0
     return philox4x32_10(make_uint4(uid, n, 0u, kPurposeCar), k0, k1);
 }
 
-// car and user profile from its Philox words, at a charger of type dc
-__device__ __forceinline__ Car car_from_words(uint4 w, bool dc, const DevParams& p)
+// the part of a car and user profile that does not depend on the charger
+// the car parks at (capacity, SoC, demand, stay, user preference)
+__device__ __forceinline__ Car car_core(uint4 w, const DevParams& p)
 {
     Car c;
     c.cap = p.cap_lo + p.cap_span * unit_of(w.x);
     c.soc = p.soc_lo + p.soc_span * unit_of(w.y);
     c.stay = p.stay_lo + (int)range_of(w.z, p.stay_span);
-    c.rbar = dc ? p.rb_lo1 + p.rb_span1 * unit_of(w.w) : p.rb_lo0 + p.rb_span0 * unit_of(w.w);
+    c.rbar = 0.f;
     c.erem = fmaxf(p.soc_target - c.soc, 0.0f) * c.cap;
     c.cs = (int)(w.x & 0xFFu) < p.cs_share;   // user preference: the low byte the capacity leaves unused
+    return c;
+}
+
+// the car's maximum rate from its fourth profile word, at a charger of type dc
+__device__ __forceinline__ float car_rbar(uint32_t w3, bool dc, const DevParams& p)
+{
+    return dc ? p.rb_lo1 + p.rb_span1 * unit_of(w3) : p.rb_lo0 + p.rb_span0 * unit_of(w3);
+}
+
+// car and user profile from its Philox words, at a charger of type dc
+__device__ __forceinline__ Car car_from_words(uint4 w, bool dc, const DevParams& p)
+{
+    Car c = car_core(w, p);
+    c.rbar = car_rbar(w.w, dc, p);
     return c;
 }
 

@@ -217,7 +217,8 @@ struct WarpSmem {
     uint32_t st_u[8][4];                   // per station: admitted, rejected, episodes, episode ended
     uint32_t arrw[4][32];                  // arrival words: word w of block (blk0 + x - station's first lane) at [w][x]
     uint32_t aw[4][32 * 4];                // action words: word w of charger slot q*32 + lane
-    uint32_t carw[4][128];                 // pre-drawn car words: station ew's i-th buffered car at ew*C + i
+    uint32_t carw[5][128];                 // pre-drawn cars, station ew's i-th buffered car at ew*C + i:
+                                           // capacity, SoC, demand (FP32 bits), stay | u << 8, rate word
 };
 
 // extended instances: also the nodes above the groups, per level, at the
@@ -614,13 +615,15 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
         if (__any_sync(0xFFFFFFFFu, m_adm > 0)) {
             if (ncar + (uint32_t)m_adm > cend) {   // buffer exhausted: draw cars ncar .. ncar+C-1
 #pragma unroll
-                for (int q = 0; q < PPL; ++q) {
+                for (int q = 0; q < PPL; ++q) {   // profiles computed here, in one dense pass
                     const int i = q * LPE + le;
                     const uint4 w = car_words(uidu, ncar + (uint32_t)i, k0, k1);
-                    ws->carw[0][ew * C + i] = w.x;
-                    ws->carw[1][ew * C + i] = w.y;
-                    ws->carw[2][ew * C + i] = w.z;
-                    ws->carw[3][ew * C + i] = w.w;
+                    const Car core = car_core(w, p);
+                    ws->carw[0][ew * C + i] = __float_as_uint(core.cap);
+                    ws->carw[1][ew * C + i] = __float_as_uint(core.soc);
+                    ws->carw[2][ew * C + i] = __float_as_uint(core.erem);
+                    ws->carw[3][ew * C + i] = (uint32_t)core.stay | (core.cs ? 1u << 8 : 0u);
+                    ws->carw[4][ew * C + i] = w.w;
                 }
                 cend = ncar + (uint32_t)C;
             }
@@ -632,14 +635,16 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
                 const bool f = fr & (1u << q);
                 if (f && rank < m_adm) {
                     const int x = x0 + rank;
-                    const uint4 w = make_uint4(ws->carw[0][x], ws->carw[1][x], ws->carw[2][x], ws->carw[3][x]);
-                    const Car car = car_from_words(w, meta[q] & kMetaDC, p);
-                    cap[q] = car.cap; soc[q] = car.soc; erem[q] = car.erem; rbar[q] = car.rbar;
-                    if (EXT && car.cs) {   // charge-sensitive user: stays until charged
+                    cap[q] = __uint_as_float(ws->carw[0][x]);
+                    soc[q] = __uint_as_float(ws->carw[1][x]);
+                    erem[q] = __uint_as_float(ws->carw[2][x]);
+                    rbar[q] = car_rbar(ws->carw[4][x], meta[q] & kMetaDC, p);
+                    const uint32_t su = ws->carw[3][x];
+                    if (EXT && (su >> 8)) {   // charge-sensitive user: stays until charged
                         trem[q] = kTremCS;
-                        due[q] = car.stay;
+                        due[q] = (int)(su & 0xFFu);
                     } else {
-                        trem[q] = car.stay;
+                        trem[q] = (int)(su & 0xFFu);
                     }
                 }
                 rank += f ? 1 : 0;
