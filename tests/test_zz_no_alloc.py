@@ -14,11 +14,22 @@ from parity import STEP_RTOL
 pytestmark = pytest.mark.gpu
 
 
-def test_rollout_noalloc_matches_rollout_twice(cuda_lib):
+def _extended():
+    """Fig. c trees in V2G mode with increment levels and charge-sensitive
+    users: the extended tree instances."""
+    from paper_2507_01522_b300 import inputs as I
+    w = I.tree_workload(300, seed=8)
+    w.params = I.EnvParams(**{**w.params.__dict__, "v2g": 1, "n_levels": 21, "action_delta": 1,
+                              "cs_share_256": 128, "soc_target": 0.8})
+    return w
+
+
+@pytest.mark.parametrize("form", ["charge-only", "extended"])
+def test_rollout_noalloc_matches_rollout_twice(cuda_lib, form):
     import torch
     from paper_2507_01522_b300 import inputs as I
     from paper_2507_01522_b300.chargax import Batch
-    w = I.heterogeneous(n_envs=1000)
+    w = I.heterogeneous(n_envs=1000) if form == "charge-only" else _extended()
     a, b = Batch(w), Batch(w)                      # identical batches, identical seeds
     for x in (a, b):
         x.set_launch(steps_per_launch=24, warps_per_block=4)
@@ -39,6 +50,8 @@ def test_rollout_noalloc_matches_rollout_twice(cuda_lib):
             np.testing.assert_array_equal(sa[k], sb[k], err_msg=f"{k} on call {call}")
         for k in ("soc", "erem", "p"):
             np.testing.assert_allclose(sb[k], sa[k], rtol=STEP_RTOL, atol=1e-6)
+        np.testing.assert_array_equal(a.due(), b.due())
+        np.testing.assert_allclose(b.battery()["soc"], a.battery()["soc"], rtol=STEP_RTOL, atol=1e-6)
 
 
 def test_rollout_noalloc_rejects_too_many_launches(cuda_lib):
