@@ -165,3 +165,45 @@ def test_tree_fullsize_sampled(cuda_lib):
                 under[g] = a == u
             cap = float(st.upper_eta[uo[e] + u]) * float(st.upper_limit_kw[uo[e] + u])
             assert gsum[go[e]:go[e + 1]][under].sum() <= cap * (1 + 1e-5) + 1e-4
+
+
+def test_extended_reset_subset_and_host_step(cuda_lib):
+    """A subset reset and the host-buffer step on Fig. c trees in V2G mode
+    with increment levels and charge-sensitive users: the reset stations
+    start over (empty, battery at its initial SoC, no Delta t_remain left)
+    exactly as in the oracle, and the host step (charger and battery levels
+    copied in) equals the device step."""
+    w, b, o, torch = make(n_envs=64, seed=13, **V2G, **CS, action_delta=1)
+    for _ in range(20):
+        b.step()
+        o.step(None)
+    ids = np.array([0, 5, 17, 40, 63], np.int32)
+    b.reset(torch.from_numpy(ids).cuda(), seed=77)
+    o.reset(ids, seed=77)
+    gs = b.get_state()
+    assert_events_equal(gs, o.state(), "after reset")
+    po = w.stations.port_off
+    for e in ids:
+        assert np.all(gs["trem"][po[e]:po[e + 1]] == 0) and np.all(b.due()[po[e]:po[e + 1]] == 0)
+    np.testing.assert_allclose(b.battery()["soc"][ids], w.params.batt_soc0, rtol=0, atol=0)
+    np.testing.assert_allclose(b.battery()["soc"], o.battery()["soc"], rtol=0, atol=2e-4)
+    compare_cs(w, b, o, torch, 24, mode="fused", k=8)
+    # host step = device step, on two identical batches
+    from paper_2507_01522_b300.chargax import Batch
+    b1, b2 = Batch(w), Batch(w)
+    rng = np.random.default_rng(3)
+    for _ in range(5):
+        acts = rng.integers(0, 21, b1.n_actions).astype(np.int8)
+        hr = np.zeros(b1.E, np.float32)
+        hd = np.zeros(b1.E, np.uint8)
+        ho = np.zeros(b1.obs_size, np.float32)
+        b1.step_host(acts, hr, hd, ho)
+        r2 = torch.zeros(b2.E, device="cuda")
+        d2 = torch.zeros(b2.E, dtype=torch.uint8, device="cuda")
+        o2 = torch.zeros(b2.obs_size, device="cuda")
+        b2.step(actions=torch.from_numpy(acts).cuda(), reward=r2, done=d2)
+        b2.observe(o2)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(hr, r2.cpu().numpy())
+        np.testing.assert_array_equal(hd, d2.cpu().numpy())
+        np.testing.assert_array_equal(ho, o2.cpu().numpy())
