@@ -362,7 +362,13 @@ def run_b300(args):
                 "warps_per_block": W, "ops_per_launch": ops_launch,
                 "peak_source": f"{sm_count} SMs x {LANES_PER_SM} lanes x {sm_mhz:.0f} MHz ({pk_kind} max clock)",
                 "hbm_gbs_algorithmic": fused_bytes_launch / (launch_ms * 1e-3) / 1e9,
-                "hbm_frac_algorithmic": fused_bytes_launch / (launch_ms * 1e-3) / 1e9 / pk["hbm_gbs"]}
+                "hbm_frac_algorithmic": fused_bytes_launch / (launch_ms * 1e-3) / 1e9 / pk["hbm_gbs"],
+                # the plain form's bytes for the same steps over the fused time:
+                # the HBM roofline the fused form leaves behind (can exceed 1)
+                "plain_equivalent_gbs": (PLAIN_BYTES_PER_PORT_STEP * P + PLAIN_BYTES_PER_ENV_STEP * E) * K
+                                        / (launch_ms * 1e-3) / 1e9,
+                "plain_equivalent_frac": (PLAIN_BYTES_PER_PORT_STEP * P + PLAIN_BYTES_PER_ENV_STEP * E) * K
+                                         / (launch_ms * 1e-3) / 1e9 / pk["hbm_gbs"]}
 
     line = {"metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
