@@ -66,14 +66,27 @@ class Clocks:
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, period_ms: int = 20):
         self.index = index
+        self.period_ms = period_ms
         self.p = None
+        self.lines = []
+
+    def _read(self):
+        for line in self.p.stdout:
+            self.lines.append(line)
 
     def __enter__(self):
+        import threading
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                       "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                                       "-lms", str(self.period_ms)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                      text=True)
+            self.reader = threading.Thread(target=self._read, daemon=True)
+            self.reader.start()
+            t0 = time.perf_counter()            # the timed region starts once the sampler runs
+            while not self.lines and time.perf_counter() - t0 < 3.0 and self.p.poll() is None:
+                time.sleep(0.005)
         except Exception:
             self.p = None
         return self
@@ -83,9 +96,11 @@ class Clocks:
         if self.p is not None:
             self.p.terminate()
             try:
-                self.out, _ = self.p.communicate(timeout=5)
+                self.p.wait(timeout=5)
             except Exception:
                 self.p.kill()
+            self.reader.join(timeout=5)
+            self.out = "".join(self.lines)
 
     def summary(self):
         rows = []
