@@ -162,3 +162,26 @@ def test_upper_levels_deepest_first():
     fill(o, 3)
     o.step(np.full(3, 10, np.int8))
     np.testing.assert_allclose(o.state()["p"], [10 * 30 / 42, 10 * 30 / 42, 22 * 30 / 42], rtol=1e-12)
+
+
+def test_penalty_divides_by_node_efficiency():
+    """c_con = max over nodes of (1/eta_H) x requested sum - I_H (Eq.
+    ArchConst as a soft constraint): a group with eta 0.8 and limit 20 kW
+    under two 22 kW requests gives 44/0.8 - 20 = 35; an upper node with eta
+    0.5 and limit 60 kW over four such requests gives 88/0.5 - 60 = 116."""
+    f32 = lambda x: float(np.float32(x))
+    out = {}
+    for case, kw in (("group", dict(groups=[2], group_limit=[20.0], group_parent=[-1], upper_parent=[], upper_limit=[],
+                                     group_eta=[0.8])),
+                     ("upper", dict(groups=[2, 2], group_limit=[1e6, 1e6], group_parent=[0, 0], upper_parent=[-1],
+                                     upper_limit=[60.0], upper_eta=[0.5]))):
+        r = {}
+        for a in (0.0, 1.0):
+            w = tree_station(alpha_con=a, alpha_sat=0.0, alpha_decl=0.0, **kw)
+            o = Oracle(w)
+            fill(o, int(sum(kw["groups"])))
+            rr, _ = o.step(np.full(int(sum(kw["groups"])), 10, np.int8))
+            r[a] = rr[0]
+        out[case] = r[0.0] - r[1.0]
+    np.testing.assert_allclose(out["group"], 44.0 / f32(0.8) - 20.0, rtol=1e-9)
+    np.testing.assert_allclose(out["upper"], 88.0 / f32(0.5) - 60.0, rtol=1e-9)
