@@ -140,3 +140,16 @@ def test_discharge_maximum_caps_only_discharge():
     park(o, 1, soc=0.3, cap=500.0, rbar=120.0, trem=250, erem=300.0)
     o.step(np.array([10, 20, 10], np.int8))
     assert o.state()["p"][1] == 120.0
+
+
+def test_delta_request_capped_at_charger_maximum():
+    """Charge-only Delta form on a 22 kW charger with a car able to take
+    50 kW: level 20 adds 22 kW per step, so the request climbs 22, 44, 66
+    ...; the charger maximum holds the power at 22 kW (only the Delta form
+    can request more than the maximum)."""
+    w = hand_workload(n_ports=1, n_levels=21, action_delta=1, alpha_sat=0.0, alpha_decl=0.0)
+    o = Oracle(w)
+    park(o, 0, soc=0.2, cap=80.0, rbar=50.0, trem=100)
+    for _ in range(3):
+        o.step(np.array([20], np.int8))
+        assert o.state()["p"][0] == 22.0
