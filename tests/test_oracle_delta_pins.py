@@ -7,6 +7,7 @@ form to the absolute form wherever no cap binds, the clip at 0 from below
 without V2G, the zero power an arriving car starts from, and linear
 discharge at the port's discharge maximum."""
 import numpy as np
+import pytest
 
 from oracle import Oracle
 
@@ -142,14 +143,20 @@ def test_discharge_maximum_caps_only_discharge():
     assert o.state()["p"][1] == 120.0
 
 
-def test_delta_request_capped_at_charger_maximum():
-    """Charge-only Delta form on a 22 kW charger with a car able to take
-    50 kW: level 20 adds 22 kW per step, so the request climbs 22, 44, 66
-    ...; the charger maximum holds the power at 22 kW (only the Delta form
-    can request more than the maximum)."""
-    w = hand_workload(n_ports=1, n_levels=21, action_delta=1, alpha_sat=0.0, alpha_decl=0.0)
+@pytest.mark.parametrize("v2g", [0, 1])
+def test_delta_request_capped_at_charger_maximum(v2g):
+    """Delta form on a 22 kW charger with a car able to take 50 kW: level
+    20 adds 22 kW per step, so the request climbs 22, 44, 66 ...; the
+    charger maximum holds the power at 22 kW (only the Delta form can
+    request more than the maximum), in the charge-only and the V2G clip;
+    level 0 then takes 22 kW per step off, down to 0 (charge-only) or
+    through 0 to the discharge maximum (V2G)."""
+    w = hand_workload(n_ports=1, n_levels=21, action_delta=1, v2g=v2g, alpha_sat=0.0, alpha_decl=0.0)
     o = Oracle(w)
-    park(o, 0, soc=0.2, cap=80.0, rbar=50.0, trem=100)
-    for _ in range(3):
-        o.step(np.array([20], np.int8))
+    park(o, 0, soc=0.5, cap=80.0, rbar=50.0, trem=100)
+    for _ in range(3):                                  # V2G: the battery holds its level (10 = idle)
+        o.step(np.array([20] if not v2g else [20, 10], np.int8))
         assert o.state()["p"][0] == 22.0
+    for want in (0.0, 0.0) if not v2g else (0.0, -22.0, -22.0):
+        o.step(np.array([0] if not v2g else [0, 10], np.int8))
+        assert o.state()["p"][0] == want
