@@ -207,3 +207,48 @@ def test_extended_reset_subset_and_host_step(cuda_lib):
         np.testing.assert_array_equal(hr, r2.cpu().numpy())
         np.testing.assert_array_equal(hd, d2.cpu().numpy())
         np.testing.assert_array_equal(ho, o2.cpu().numpy())
+
+
+def wrap_tree(st, frac=0.6):
+    """Upper nodes over stations that had none: every station one node over
+    all its groups (frac of the summed group limits), every second station
+    also a node over its first half of the groups, every third one a node
+    above all (uneven depth up to three levels)."""
+    go = st.group_off
+    n_upper, gpar, upar, ulim = [], [], [], []
+    for e in range(st.n_envs):
+        G = int(st.n_groups[e])
+        glim = st.group_limit_kw[go[e]:go[e + 1]].astype(np.float64)
+        nodes = []                                         # (parent, limit)
+        top = -1
+        if e % 3 == 0:
+            nodes.append((-1, 0.9 * frac * glim.sum()))
+            top = 0
+        nodes.append((top, frac * glim.sum()))
+        all_node = len(nodes) - 1
+        parents = [all_node] * G
+        if e % 2 == 0 and G >= 2:
+            nodes.append((all_node, frac * glim[:G // 2].sum()))
+            parents[:G // 2] = [len(nodes) - 1] * (G // 2)
+        n_upper.append(len(nodes))
+        gpar.extend(parents)
+        upar.extend(p for p, _ in nodes)
+        ulim.extend(l for _, l in nodes)
+    return I.Stations(**{**st.__dict__, "n_upper": np.array(n_upper, np.int32),
+                         "group_parent": np.array(gpar, np.int32), "upper_parent": np.array(upar, np.int32),
+                         "upper_limit_kw": np.array(ulim, np.float32),
+                         "upper_eta": np.full(len(ulim), 0.97, np.float32)})
+
+
+@pytest.mark.parametrize("mode,k", [("plain", 1), ("fused", 24)])
+def test_tree_on_every_class_edge(cuda_lib, mode, k):
+    """Stations of 1, 8, 9, 16, 17, 32, 33, 64, 65 and 128 chargers (padding
+    chargers, both kernel size ranges) with upper nodes of uneven depth."""
+    import torch
+    from paper_2507_01522_b300.chargax import Batch
+    from test_gpu_parity import odd_sizes
+    w = odd_sizes()
+    w.stations = wrap_tree(w.stations)
+    w.params = I.EnvParams(**{**w.params.__dict__, "alpha_con": 0.05})
+    b, o = Batch(w), Oracle(w)
+    compare_traj(w, b, o, torch, 72, mode=mode, k=k)
