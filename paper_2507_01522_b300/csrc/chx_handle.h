@@ -89,6 +89,7 @@ struct chx_handle {
     float tuned_ms = 0.f;
     cudaStream_t cap_stream = nullptr;
     cudaStream_t copy_stream = nullptr;    // device-to-host copies of the host-call rollout
+    chx::FusedSide side;                   // the 128-charger class's launch beside the others
     cudaEvent_t chunk_done[chx::kHostChunks] = {};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;

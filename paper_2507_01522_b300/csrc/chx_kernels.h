@@ -39,8 +39,15 @@ void launch_step_plain(const DevBatch& b, const DevParams& p, const int8_t* acti
 // the resident blocks on sm_count SMs.  io.counter must point to
 // kFusedCounters zeroed ints (one work counter per kernel).
 constexpr int kFusedCounters = 2;
+// A side stream for the 128-charger class: with one, that launch runs beside
+// the smaller classes' (forked from and joined back to st by the two events,
+// which CUDA-graph capture supports); without, the two launches run in turn.
+struct FusedSide {
+    cudaStream_t aux = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
 void launch_step_fused(const DevBatch& b, const DevParams& p, const FusedIO& io, int threads, int sm_count,
-                       cudaStream_t st);
+                       cudaStream_t st, const FusedSide* side = nullptr);
 // both fused kernels can be resident with blocks of `threads` threads
 bool fused_block_size_ok(int threads);
 

@@ -555,6 +555,9 @@ int build_handle(const chx_stations* st, const chx_env_params* prm, const chx_ex
     h->steps_per_launch = 32;
     CUDA_TRY(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
     CUDA_TRY(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+    CUDA_TRY(cudaStreamCreateWithFlags(&h->side.aux, cudaStreamNonBlocking));
+    CUDA_TRY(cudaEventCreateWithFlags(&h->side.fork, cudaEventDisableTiming));
+    CUDA_TRY(cudaEventCreateWithFlags(&h->side.join, cudaEventDisableTiming));
     for (auto& ev : h->chunk_done) CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
 
     launch_reset(b, h->dp, h->d_user_to_slot, nullptr, E, seed, 0);
@@ -592,6 +595,9 @@ extern "C" int chx_destroy(chx_handle* h)
     for (void* p : h->staging) cudaFree(p);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+    if (h->side.aux) cudaStreamDestroy(h->side.aux);
+    if (h->side.fork) cudaEventDestroy(h->side.fork);
+    if (h->side.join) cudaEventDestroy(h->side.join);
     for (auto ev : h->chunk_done)
         if (ev) cudaEventDestroy(ev);
     delete h;
@@ -667,7 +673,7 @@ int enqueue_fused(chx_handle* h, int k_steps, const int8_t* actions, long long l
     const int threads = warps * 32;
     if (!fused_block_size_ok(threads)) return fail(CHX_ECUDA, "fused kernel cannot be resident with this block size");
     CUDA_TRY(cudaMemsetAsync(h->d_counter, 0, kFusedCounters * sizeof(int), st));
-    launch_step_fused(h->b, h->dp, io, threads, h->sm_count, st);
+    launch_step_fused(h->b, h->dp, io, threads, h->sm_count, st, &h->side);
     CUDA_TRY(cudaGetLastError());
     return CHX_OK;
 }

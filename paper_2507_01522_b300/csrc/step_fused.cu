@@ -871,23 +871,34 @@ bool fused_block_size_ok(int threads)
 }
 
 void launch_step_fused(const DevBatch& b, const DevParams& p, const FusedIO& io, int threads, int sm_count,
-                       cudaStream_t st)
+                       cudaStream_t st, const FusedSide* side)
 {
     const int warps = threads / 32;
     const int v = (p.v2g ? 1 : 0) | ((p.delta || p.cs_share) ? 2 : 0) | (p.tree_levels ? 4 : 0);
     const size_t smem = (size_t)warps * smem_per_warp(v);
     const FusedIO big = sub_schedule(io, 4, 4, io.counter);
     const FusedIO small = sub_schedule(io, 0, 3, io.counter + 1);
-    if (big.total_tiles > 0) {             // the heavy class first
+    // the heavy class first; beside the others when a side stream is given
+    // (its few stations would otherwise run alone on a mostly idle GPU)
+    const bool fork = side && side->aux && big.total_tiles > 0 && small.total_tiles > 0;
+    if (big.total_tiles > 0) {
+        cudaStream_t sb = st;
+        if (fork) {
+            cudaEventRecord(side->fork, st);
+            cudaStreamWaitEvent(side->aux, side->fork, 0);
+            sb = side->aux;
+        }
         const int per_sm = blocks_per_sm((const void*)kLargeKernel[v], v, threads);
         const int blocks = std::max(1, std::min(per_sm * sm_count, (big.total_tiles + warps - 1) / warps));
-        kLargeKernel[v]<<<blocks, threads, smem, st>>>(b, p, big);
+        kLargeKernel[v]<<<blocks, threads, smem, sb>>>(b, p, big);
+        if (fork) cudaEventRecord(side->join, side->aux);
     }
     if (small.total_tiles > 0) {
         const int per_sm = blocks_per_sm((const void*)kSmallKernel[v], v, threads);
         const int blocks = std::max(1, std::min(per_sm * sm_count, (small.total_tiles + warps - 1) / warps));
         kSmallKernel[v]<<<blocks, threads, smem, st>>>(b, p, small);
     }
+    if (fork) cudaStreamWaitEvent(st, side->join, 0);
 }
 
 }  // namespace chx
