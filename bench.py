@@ -259,6 +259,42 @@ def cpu_baseline(w, n_sample_envs, steps):
                 charger_steps_per_s=ports * steps / dt)
 
 
+def _oracle_slice(job):
+    """One worker of the all-cores CPU baseline: the oracle on its slice of
+    the stations (their own Philox streams) for ``steps`` steps; returns the
+    compute time."""
+    import oracle
+    sub, ids, steps = job
+    o = oracle.Oracle(sub, streams=ids)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        o.step(None)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline_all_cores(w, n_per_core, steps):
+    """The same oracle on every host core at once (processes, spawned: the
+    benchmark has touched the GPU), each on its own slice of stations; the
+    rate is all their env-steps over the slowest worker's compute time."""
+    import multiprocessing as mp
+    import numpy as np
+    from paper_2507_01522_b300 import inputs as I
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    n_total = min(w.stations.n_envs, cores * n_per_core)
+    bounds = [round(i * n_total / cores) for i in range(cores + 1)]
+    jobs = []
+    for i in range(cores):
+        if bounds[i + 1] > bounds[i]:
+            ids = np.arange(bounds[i], bounds[i + 1])
+            jobs.append((I.Workload(w.name, w.params, w.stations.subset(ids), w.exo, w.seed), ids, steps))
+    with mp.get_context("spawn").Pool(len(jobs)) as pool:
+        times = pool.map(_oracle_slice, jobs)
+    dt = max(times)
+    return dict(value=n_total * steps / dt, unit="env-steps/s", cores=len(jobs), kind="oracle",
+                sample=f"first {n_total} of {w.stations.n_envs} stations in {len(jobs)} slices x {steps} steps, "
+                       f"one process per core, FP64", seconds=round(dt, 3))
+
+
 def calibrate_sample(w, target_s, steps):
     import numpy as np
     import oracle
@@ -470,6 +506,7 @@ def run_b300(args):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         n = calibrate_sample(w, 12.0, T)
         line["cpu_baseline"] = cpu_baseline(w, n, T)
+        line["cpu_baseline"]["all_cores"] = cpu_baseline_all_cores(w, max(16, n // 2), T)
     if rank == 0:
         print(json.dumps(line), flush=True)
     barrier(ws)
