@@ -481,7 +481,7 @@ def run_b300(args):
                        "h2d_bytes_per_step": 0, "d2h_bytes_per_step": int(hr.nbytes + hd.nbytes + ho.nbytes),
                        "ms_per_step": 1e3 * etot / args.steps,
                        "api": "chx_rollout_host (pinned host outputs: reward, done step-major, observation; "
-                              "4 launches, each one's outputs copied while the next computes)"}
+                              "4 launches of 5:4:2:1 shares, each one's outputs copied while the next computes)"}
         line["gpu_launches"] += min(4, T) * args.steps
 
     line["clocks"] = ck.summary()

@@ -242,9 +242,9 @@ int chx_rollout(chx_handle* h, int32_t n_steps, float* d_reward, uint8_t* d_done
 /* chx_rollout with HOST outputs, step-major: h_reward[k*n_envs + e] and
  * h_done[k*n_envs + e] for step k of env e ([n_steps][n_envs], a rollout
  * buffer's layout), h_obs as chx_rollout (any may be NULL; pinned memory
- * gives full copy bandwidth).  The steps run in up to 4 launches whose
- * outputs are copied while the next launch computes; the call returns when
- * everything is on the host. */
+ * gives full copy bandwidth).  The steps run in up to 4 launches of
+ * shrinking size (5:4:2:1 shares) whose outputs are copied while the next
+ * launch computes; the call returns when everything is on the host. */
 int chx_rollout_host(chx_handle* h, int32_t n_steps, float* h_reward, uint8_t* h_done, float* h_obs,
                      void* stream);
 

@@ -770,6 +770,27 @@ extern "C" int chx_rollout(chx_handle* h, int32_t n_steps, float* d_reward, uint
     return rollout(h, n_steps, d_reward, d_done, d_obs, (cudaStream_t)stream);
 }
 
+namespace chx {
+
+// Launch sizes of a host-buffer rollout: shrinking 5:4:2:1 shares, so each
+// chunk's copy out hides behind the next chunk's compute and only the last,
+// smallest chunk (and the final observation) is copied after the last launch.
+int host_chunks(int n_steps, int* sizes)
+{
+    static_assert(kHostChunks == 4, "the shares below are for four chunks");
+    if (n_steps < kHostChunks) {
+        for (int c = 0; c < n_steps; ++c) sizes[c] = 1;
+        return n_steps;
+    }
+    sizes[1] = std::max(1, n_steps * 4 / 12);
+    sizes[2] = std::max(1, n_steps * 2 / 12);
+    sizes[3] = std::max(1, n_steps / 12);
+    sizes[0] = n_steps - sizes[1] - sizes[2] - sizes[3];
+    return kHostChunks;
+}
+
+}  // namespace chx
+
 // Host-call rollout: the steps run in up to kHostChunks fused launches on the
 // caller's stream, outputs step-major in device staging; after each launch an
 // event lets the copy stream bring that chunk's rows (contiguous) to the host
@@ -786,11 +807,11 @@ extern "C" int chx_rollout_host(chx_handle* h, int32_t n_steps, float* h_reward,
     float* dob = h_obs ? (float*)staging(h, 2, nobs * sizeof(float)) : nullptr;
     if ((h_reward && !dr) || (h_done && !dd) || (h_obs && !dob)) return fail(CHX_ENOMEM, "staging allocation failed");
     cudaStream_t st = (cudaStream_t)stream, cs = h->copy_stream;
-    const int n_chunks = std::min(kHostChunks, (int)n_steps);
-    const int chunk = (n_steps + n_chunks - 1) / n_chunks;
-    for (int c = 0, k0 = 0; k0 < n_steps; ++c, k0 += chunk) {
-        const int k = std::min(chunk, n_steps - k0);
-        const bool last = k0 + k >= n_steps;
+    int sizes[kHostChunks];
+    const int n_chunks = host_chunks(n_steps, sizes);
+    for (int c = 0, k0 = 0; c < n_chunks; k0 += sizes[c], ++c) {
+        const int k = sizes[c];
+        const bool last = c == n_chunks - 1;
         const size_t off = (size_t)k0 * E, n = (size_t)k * E;
         int rc = enqueue_fused(h, k, nullptr, 0, dr ? dr + off : nullptr, dd ? dd + off : nullptr, 1,
                                last ? dob : nullptr, h->warps_per_block, st, (long long)E);
