@@ -231,3 +231,102 @@ def test_serving_wait_timeout():
         assert lat > 0 and np.all(np.isfinite(r))
     assert seen
     srv.stop()
+
+
+def test_serving_fullsize_sampled():
+    """The benchmark's serving pool: 1,048,576 resident stations of 8-128
+    chargers (log-uniform, about 45 M chargers), admitted with the
+    benchmark's class capacities and tick size.  Rounds that step every
+    station (requests of 256 stations, Philox actions) alternate with rounds
+    that step only a sample (64 stations of each size class, the first and
+    the last admitted) in random partitions, with observations, given
+    actions and one reset; the oracle runs the sample alone, on the same
+    Philox streams, and must agree on every sampled reward, done flag,
+    observation and occupancy."""
+    from paper_2507_01522_b300.chargax import CHX_SRV_RESET, Server
+    w = I.serving_pool(1 << 20, seed=0)
+    st = w.stations
+    n = st.n_ports
+    cap = [int(np.sum(n <= 8))] + [int(np.sum((n > (4 << c)) & (n <= (8 << c)))) for c in range(1, 5)]
+    rng = np.random.default_rng(12)
+    bounds = [(1, 8), (9, 16), (17, 32), (33, 64), (65, 128)]
+    sample = np.unique(np.concatenate(
+        [rng.choice(np.flatnonzero((n >= lo) & (n <= hi)), 64, replace=False) for lo, hi in bounds]
+        + [np.array([0, st.n_envs - 1])]))
+    sub = st.subset(sample)
+    obs_floats = 8 * len(sample) + 6 * int(sub.total_ports)
+    srv = Server(w.params, w.exo, cap, hbm_budget_bytes=150e9, max_tick_envs=65536, n_streams=2,
+                 max_tick_obs_floats=obs_floats)
+    seed = 2000
+    ids = srv.admit(st, seed=seed)
+    assert len(np.unique(ids)) == st.n_envs
+    ws = I.Workload(w.name, w.params, sub, w.exo, w.seed)
+    o = Oracle(ws, seed=seed, streams=ids[sample])
+    po = sub.port_off
+    active = []
+
+    def compare(rnd, r_s, d_s, ob_parts=None):
+        ro, do = o.step(acts)
+        info = o.info()
+        scale = reward_scale(info, ws.params) + station_step_scale(ws, info)
+        assert_reward_close(r_s, ro, scale, TRAJ_RTOL, where=f"round {rnd}")
+        np.testing.assert_array_equal(d_s, do, err_msg=f"done round {rnd}")
+        active.append((int(np.count_nonzero(ro)), int(np.count_nonzero(o.state()["trem"]))))
+        if ob_parts is None:
+            return
+        oo = o.observe()
+        trem_o = o.state()["trem"]
+        for part, ob in ob_parts:
+            np.testing.assert_allclose(ob, obs_of(ws, oo, part), rtol=0, atol=2e-4, err_msg=f"obs round {rnd}")
+            blocks, k = [], 0
+            for e in part:
+                m = po[e + 1] - po[e]
+                blocks.append(ob[k + 8: k + 8 + 6 * m].reshape(m, 6))
+                k += 8 + 6 * m
+            pb = np.concatenate(blocks)
+            tr = trem_o[np.concatenate([np.arange(po[e], po[e + 1]) for e in part])]
+            np.testing.assert_array_equal(np.rint(pb[:, 2] * ws.params.stay_steps[1]).astype(int), tr)
+
+    for rnd in range(9):
+        acts = None
+        if rnd in (0, 1, 8):                               # every resident station, 4096 requests of 256
+            r_all = np.zeros(st.n_envs, np.float32)
+            d_all = np.zeros(st.n_envs, np.uint8)
+            perm = rng.permutation(st.n_envs)
+            reqs = []
+            for j in range(0, st.n_envs, 256):
+                part = perm[j:j + 256]
+                r = np.zeros(len(part), np.float32)
+                d = np.zeros(len(part), np.uint8)
+                reqs.append((part, r, d, srv.submit(ids[part], reward=r, done=d)))
+            for part, r, d, t in reqs:
+                srv.wait(t)
+                r_all[part] = r
+                d_all[part] = d
+            compare(rnd, r_all[sample], d_all[sample])
+            continue
+        if rnd == 5:                                       # a reset for a third of the sample
+            rs = np.sort(rng.choice(len(sample), len(sample) // 3, replace=False))
+            srv.wait(srv.submit(ids[sample[rs]], kind=CHX_SRV_RESET, seed=77))
+            o.reset(rs, seed=77)
+        if rnd % 2:
+            acts = I.random_actions(rng, int(sub.total_ports))
+        r_s = np.zeros(len(sample), np.float32)
+        d_s = np.zeros(len(sample), np.uint8)
+        reqs = []
+        for part in partition(rng, len(sample)):
+            r = np.zeros(len(part), np.float32)
+            d = np.zeros(len(part), np.uint8)
+            ob = np.zeros(8 * len(part) + 6 * int(sum(po[e + 1] - po[e] for e in part)), np.float32)
+            a = None if acts is None else np.concatenate([acts[po[e]:po[e + 1]] for e in part])
+            reqs.append((part, r, d, ob, srv.submit(ids[sample[part]], actions=a, reward=r, done=d, obs=ob)))
+        for part, r, d, ob, t in reqs:
+            srv.wait(t)
+            r_s[part] = r
+            d_s[part] = d
+        compare(rnd, r_s, d_s, [(part, ob) for part, _, _, ob, _ in reqs])
+    stats = srv.stats()
+    assert stats["env_steps"] == 3 * st.n_envs + 6 * len(sample)
+    # the sample was busy: most stations earn a reward and hold cars in the later rounds
+    assert min(a for a, _ in active[2:]) > len(sample) // 2 and min(c for _, c in active[2:]) > len(sample)
+    srv.stop()
