@@ -193,7 +193,9 @@ int chx_obs_size(const chx_handle* h, int64_t* out);
  * Start a new episode for the listed envs (d_env_ids: device int32 [n] in
  * batch numbering; NULL = all envs): Philox key := seed, global step := 0,
  * every charger empty, step of day 0, day drawn from the price bank.
- * Statistics are kept.  CHX_EINVAL for n < 0. */
+ * Statistics are kept.  CHX_EINVAL for n < 0; n = 0 with a list does
+ * nothing.  A listed id outside 0..n_envs-1 is skipped (the others are
+ * reset) and makes the next chx_check return CHX_EFAULT. */
 int chx_reset(chx_handle* h, const int32_t* d_env_ids, int32_t n, uint64_t seed, void* stream);
 
 /* ---- one step, plain form ------------------------------------------------

@@ -244,6 +244,8 @@ class Batch:
     # ---- stepping -------------------------------------------------------
     def reset(self, env_ids=None, seed: int = 0, stream=None):
         n = 0 if env_ids is None else int(env_ids.numel())
+        if env_ids is not None and n == 0:       # an empty list (its pointer may be NULL, which means "all")
+            return
         _check(_lib.chx_reset(self.h, _dev_ptr(env_ids), n, C.c_uint64(seed), _stream_ptr(stream)))
 
     def step(self, actions=None, reward=None, done=None, lda: int = 1, stream=None):

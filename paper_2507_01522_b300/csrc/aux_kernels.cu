@@ -8,11 +8,15 @@ namespace chx {
 // listed station; threads clear the chargers, thread 0 sets the per-station
 // fields and draws the day.
 __global__ void k_reset(DevBatch b, DevParams p, const int32_t* __restrict__ user_to_slot,
-                        const int32_t* __restrict__ env_ids, int n, uint32_t seed_lo, uint32_t seed_hi)
+                        const int32_t* __restrict__ env_ids, int n, int n_users, uint32_t seed_lo, uint32_t seed_hi)
 {
     const int j = blockIdx.x;
     if (j >= n) return;
     const int uid = env_ids ? env_ids[j] : j;
+    if (uid < 0 || uid >= n_users) {       // caller's list: skip and flag
+        if (threadIdx.x == 0) atomicOr(b.err, kErrEnvId);
+        return;
+    }
     const int s = user_to_slot[uid];
     const int c = class_of_slot(b, s);
     const int C = 8 << c;
@@ -38,10 +42,10 @@ __global__ void k_reset(DevBatch b, DevParams p, const int32_t* __restrict__ use
 }
 
 void launch_reset(const DevBatch& b, const DevParams& p, const int32_t* user_to_slot, const int32_t* env_ids, int n,
-                  uint64_t seed, cudaStream_t st)
+                  int n_users, uint64_t seed, cudaStream_t st)
 {
     if (n <= 0) return;
-    k_reset<<<n, 128, 0, st>>>(b, p, user_to_slot, env_ids, n, (uint32_t)seed, (uint32_t)(seed >> 32));
+    k_reset<<<n, 128, 0, st>>>(b, p, user_to_slot, env_ids, n, n_users, (uint32_t)seed, (uint32_t)(seed >> 32));
 }
 
 // Reset of listed station slots with one seed each (the serving pool, where a

@@ -40,6 +40,7 @@ constexpr int kMaxUpperDepth = 3;          // levels of tree nodes above the gro
 // device error bits
 constexpr uint32_t kErrActionRange = 1u;
 constexpr uint32_t kErrPolicyWait = 2u;     // a tensor-core wait of the policy kernel timed out
+constexpr uint32_t kErrEnvId = 4u;          // a reset listed an env id outside 0..n_envs-1 (skipped)
 
 struct DevParams {
     int ep_len, n_levels, n_days;

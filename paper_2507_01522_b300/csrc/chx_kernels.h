@@ -53,7 +53,7 @@ bool fused_block_size_ok(int threads);
 
 // reset the stations whose batch ids are listed (NULL = all)
 void launch_reset(const DevBatch& b, const DevParams& p, const int32_t* user_to_slot, const int32_t* env_ids, int n,
-                  uint64_t seed, cudaStream_t st);
+                  int n_users, uint64_t seed, cudaStream_t st);
 void launch_observe(const DevBatch& b, const DevParams& p, float* obs, cudaStream_t st);
 // reset listed slots (station id = slot), one 64-bit seed per entry
 void launch_reset_slots(const DevBatch& b, const DevParams& p, const int32_t* slots, const unsigned long long* seeds,

@@ -560,7 +560,7 @@ int build_handle(const chx_stations* st, const chx_env_params* prm, const chx_ex
     CUDA_TRY(cudaEventCreateWithFlags(&h->side.join, cudaEventDisableTiming));
     for (auto& ev : h->chunk_done) CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
 
-    launch_reset(b, h->dp, h->d_user_to_slot, nullptr, E, seed, 0);
+    launch_reset(b, h->dp, h->d_user_to_slot, nullptr, E, E, seed, 0);
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(cudaDeviceSynchronize());
     *out = h;
@@ -641,7 +641,7 @@ extern "C" int chx_reset(chx_handle* h, const int32_t* d_env_ids, int32_t n, uin
     if (!h) return fail(CHX_EINVAL, "null handle");
     if (n < 0) return fail(CHX_EINVAL, "n < 0");
     const int count = d_env_ids ? n : h->E;
-    launch_reset(h->b, h->dp, h->d_user_to_slot, d_env_ids, count, seed, (cudaStream_t)stream);
+    launch_reset(h->b, h->dp, h->d_user_to_slot, d_env_ids, count, h->E, seed, (cudaStream_t)stream);
     CUDA_TRY(cudaGetLastError());
     return CHX_OK;
 }
@@ -1260,6 +1260,7 @@ extern "C" int chx_check(chx_handle* h, void* stream)
     if (err) {
         CUDA_TRY(cudaMemset(h->b.err, 0, sizeof(uint32_t)));
         if (err & kErrPolicyWait) return fail(CHX_ETIMEOUT, "a tensor-core wait of the policy kernel ran out of time");
+        if (err & kErrEnvId) return fail(CHX_EFAULT, "a reset listed an env id outside 0..n_envs-1 (skipped)");
         return fail(CHX_EFAULT, "a kernel saw an action level outside 0..n_levels-1 (clamped)");
     }
     return CHX_OK;

@@ -415,3 +415,97 @@ def test_fullsize_fixed_station_plain_sampled(cuda_lib):
     assert_events_equal(sub, o.state(), "sampled")
     assert_traj_close(sub, o.state(), charger_pmax(ws), TRAJ_RTOL, "sampled")
     assert_reward_close(r.cpu().numpy()[ids], ro, reward_scale(info, w.params) + station_step_scale(ws, info), TRAJ_RTOL)
+
+
+def test_reset_list_out_of_range_and_empty(cuda_lib):
+    """chx_reset with a list: ids outside 0..n_envs-1 are skipped (nothing
+    outside the batch is written), the valid ones are reset exactly as the
+    oracle resets them, and the next chx_check reports CHX_EFAULT once; an
+    empty list changes nothing."""
+    from paper_2507_01522_b300.chargax import CHX_EFAULT, ChxError
+    w, b, o, torch = make("odd150")
+    for _ in range(20):
+        b.step()
+        o.step(None)
+    before = b.get_state()
+    b.reset(torch.zeros(0, dtype=torch.int32, device="cuda"), seed=5)
+    b.check()
+    after = b.get_state()
+    for key in before:
+        np.testing.assert_array_equal(after[key], before[key], err_msg=key)
+    ids = np.array([3, b.E, -1, 1 << 30, 17, -(1 << 31)], np.int32)
+    b.reset(torch.from_numpy(ids).cuda(), seed=99)
+    with pytest.raises(ChxError) as ei:
+        b.check()
+    assert ei.value.code == CHX_EFAULT and "env id" in str(ei.value)
+    b.check()                               # flag cleared
+    o.reset(np.array([3, 17]), seed=99)
+    assert_events_equal(b.get_state(), o.state(), "after reset")
+    compare_traj(w, b, o, torch, 20, mode="fused", k=10)
+
+
+def one_station(n_ports, group_sizes, group_limit=50.0, grid_limit=100.0):
+    st = I.Stations(
+        n_ports=np.array([n_ports], np.int32), port_type=np.zeros(max(n_ports, 0), np.uint8),
+        n_groups=np.array([len(group_sizes)], np.int32), group_size=np.array(group_sizes, np.int32),
+        group_limit_kw=np.full(len(group_sizes), group_limit, np.float32),
+        group_eta=np.ones(len(group_sizes), np.float32), grid_limit_kw=np.array([grid_limit], np.float32),
+        grid_eta=np.ones(1, np.float32), arrival_class=np.zeros(1, np.int32))
+    base = I.small_uniform()
+    return I.Workload("degenerate", base.params, st, base.exo, 0)
+
+
+@pytest.mark.parametrize("case,reason", [
+    ("no stations", "n_envs out of range"),
+    ("129 chargers", "n_ports out of 1..128"),
+    ("0 chargers", "n_ports out of 1..128"),
+    ("empty group", "empty group"),
+    ("groups short", "do not cover"),
+    ("group limit 0", "group limit must be > 0"),
+    ("grid limit 0", "grid limit must be > 0"),
+    ("33 groups", "n_groups out of"),
+])
+def test_degenerate_configurations_rejected(cuda_lib, case, reason):
+    """Configurations outside the documented ranges fail with CHX_EINVAL
+    and the reason, before anything is allocated."""
+    from paper_2507_01522_b300.chargax import CHX_EINVAL, Batch, ChxError
+    if case == "no stations":
+        base = I.small_uniform()
+        w = I.Workload(base.name, base.params, base.stations.subset(np.array([], np.int64)), base.exo, 0)
+    else:
+        w = {"129 chargers": lambda: one_station(129, [64, 65]),
+             "0 chargers": lambda: one_station(0, [1]),
+             "empty group": lambda: one_station(8, [8, 0]),
+             "groups short": lambda: one_station(8, [4, 3]),
+             "group limit 0": lambda: one_station(8, [8], group_limit=0.0),
+             "grid limit 0": lambda: one_station(8, [8], grid_limit=0.0),
+             "33 groups": lambda: one_station(66, [2] * 33)}[case]()
+    with pytest.raises(ChxError) as ei:
+        Batch(w)
+    assert ei.value.code == CHX_EINVAL and reason in str(ei.value), str(ei.value)
+
+
+def test_degenerate_launch_arguments_rejected(cuda_lib):
+    """Zero steps, a launch shape outside 1..8 warps, and a negative reset
+    count fail with CHX_EINVAL and leave the state as it was; the smallest
+    valid station (one charger, one group) steps like the oracle."""
+    from paper_2507_01522_b300.chargax import CHX_EINVAL, ChxError
+    w, b, o, torch = make("odd150")
+    b.step()
+    o.step(None)
+    before = b.get_state()
+    r = torch.zeros(b.E, device="cuda")
+    for call in (lambda: b.step_n(0, reward=r), lambda: b.rollout(0, reward=r),
+                 lambda: b.set_launch(0, 9)):
+        with pytest.raises(ChxError) as ei:
+            call()
+        assert ei.value.code == CHX_EINVAL
+    from paper_2507_01522_b300 import chargax
+    assert chargax.load_library().chx_reset(b.h, None, -1, 0, None) == CHX_EINVAL
+    after = b.get_state()
+    for key in before:
+        np.testing.assert_array_equal(after[key], before[key], err_msg=key)
+    w1 = one_station(1, [1], group_limit=5.0, grid_limit=7.0)
+    from paper_2507_01522_b300.chargax import Batch
+    b1, o1 = Batch(w1), Oracle(w1)
+    compare_traj(w1, b1, o1, torch, 300, mode="fused", k=100)
