@@ -1,5 +1,5 @@
 // step_plain.cu -- the plain form of the step: one thread per station, one
-// launch per step, all state read from and written back to HBM.
+// launch per step, all state read from and written back to memory.
 //
 // It is the baseline the fused kernel is measured against and a second,
 // structurally different CUDA implementation of the same transition
@@ -9,10 +9,25 @@
 
 namespace chx {
 
+// Four consecutive chargers of a station slot (slots start on a multiple of
+// 8 chargers, so every chunk is 16-byte aligned for floats and words).
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+constexpr int kMaxPorts = 128;             // chargers per station slot at most
+__device__ __forceinline__ float& at(float4& v, int j) { return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w; }
+__device__ __forceinline__ float get(const float4& v, int j) { return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w; }
+__device__ __forceinline__ uint32_t at(const uint4& v, int j) { return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w; }
+
 // One station's step.  V2G: signed levels (clip_power_v2g), the station
 // battery at the root (its level after the chargers' in the action array, or
 // drawn at charger index n), signed limits (|sum| <= eta * I), discharge
 // energy after the port loss, two-case profit and degradation penalty.
+//
+// The chargers are walked in chunks of four with 16-byte loads.  Pass (i)
+// draws each charger's level once, clips it and keeps the clipped power in a
+// per-thread array (local memory: consecutive threads' copies of one element
+// are adjacent, so a warp's accesses are coalesced); the node passes and the
+// charge pass read it from there.  Sums run charger by charger in index order.
 template <bool V2G>
 __device__ __forceinline__ void step_station(const DevBatch& b, const DevParams& p, const int8_t* __restrict__ actions,
                                              long long lda, float* __restrict__ reward, uint8_t* __restrict__ done,
@@ -24,6 +39,7 @@ __device__ __forceinline__ void step_station(const DevBatch& b, const DevParams&
     const int C = 8 << c;
     const long long pb = b.cls_port_base[c] + (long long)(s - b.cls_env_base[c]) * C;
     const int n = b.n_ports[s];
+    const int nv = (n + 3) >> 2;                        // chunks of four chargers (inside the slot)
     const uint32_t g = b.gstep[s];
     const int t = b.tod[s];
     const uint32_t k0 = b.key0[s], k1 = b.key1[s];
@@ -43,40 +59,53 @@ __device__ __forceinline__ void step_station(const DevBatch& b, const DevParams&
         }
         return lvl;
     };
-    auto clip = [&](int lvl, bool dc, float soc, float erem, float cap, float rbar, float last) -> float {
-        const float preq = request(lvl, dc ? p.lvl1 : p.lvl0, last, p);
-        return V2G ? clip_power_v2g(preq, dc, soc, erem, cap, rbar, p) : clip_power(preq, dc, soc, erem, cap, rbar, p);
-    };
 
     // -- (i) apply actions: per-charger clip, then group sums (Eq. ArchConst)
+    float Pst[kMaxPorts];                               // clipped (requested) power of each charger
     float gscale[32];
     float S = 0.f, Se = 0.f, Sn = 0.f, s_raw = 0.f, s_grp = 0.f, se_grp = 0.f, sn_grp = 0.f, over_max = 0.f;
-    for (int q = 0; q < n; ++q) {
-        const long long i = pb + q;
-        const uint32_t m = b.meta[i];
-        const bool dc = m & kMetaDC;
-        float P = 0.f;
-        if (b.trem[i] > 0) P = clip(level_of(q), dc, b.soc[i], b.erem[i], b.cap[i], b.rbar[i], b.pw[i]);
-        S += P;
-        if (V2G) {
-            if (P >= 0.f) Se += P * (dc ? p.inv_eta1 : p.inv_eta0);
-            else Sn += P * (dc ? p.eta1 : p.eta0);
-        } else {
-            Se += P * (dc ? p.inv_eta1 : p.inv_eta0);
-        }
-        s_raw += P;
-        if (m & kMetaTail) {
-            const float gc = b.gcap[i];
-            const float mag = V2G ? fabsf(S) : S;
-            const float sc = mag > gc ? __fdividef(gc, mag) : 1.0f;
-            gscale[(m >> kMetaGroupShift) & 31] = sc;
-            over_max = fmaxf(over_max, (mag - gc) * b.ginv_eta[i]);
-            s_grp += S * sc;
-            se_grp += Se * sc;
-            sn_grp += Sn * sc;
-            S = 0.f;
-            Se = 0.f;
-            Sn = 0.f;
+#pragma unroll 2
+    for (int v = 0; v < nv; ++v) {
+        const long long i0 = pb + 4 * v;
+        const float4 so = ld4(b.soc + i0), er = ld4(b.erem + i0), ca = ld4(b.cap + i0), rb = ld4(b.rbar + i0),
+                     pl = ld4(b.pw + i0);
+        const uint4 me = __ldg(reinterpret_cast<const uint4*>(b.meta + i0));
+        const uint32_t tr4 = *reinterpret_cast<const uint32_t*>(b.trem + i0);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int q = 4 * v + j;
+            if (q >= n) break;
+            const uint32_t m = at(me, j);
+            const bool dc = m & kMetaDC;
+            float P = 0.f;
+            if ((tr4 >> (8 * j)) & 0xFFu) {
+                const float preq = request(level_of(q), dc ? p.lvl1 : p.lvl0, get(pl, j), p);
+                P = V2G ? clip_power_v2g(preq, dc, get(so, j), get(er, j), get(ca, j), get(rb, j), p)
+                        : clip_power(preq, dc, get(so, j), get(er, j), get(ca, j), get(rb, j), p);
+            }
+            Pst[q] = P;
+            S += P;
+            if (V2G) {
+                if (P >= 0.f) Se += P * (dc ? p.inv_eta1 : p.inv_eta0);
+                else Sn += P * (dc ? p.eta1 : p.eta0);
+            } else {
+                Se += P * (dc ? p.inv_eta1 : p.inv_eta0);
+            }
+            s_raw += P;
+            if (m & kMetaTail) {
+                const long long i = i0 + j;
+                const float gc = __ldg(b.gcap + i);
+                const float mag = V2G ? fabsf(S) : S;
+                const float sc = mag > gc ? __fdividef(gc, mag) : 1.0f;
+                gscale[(m >> kMetaGroupShift) & 31] = sc;
+                over_max = fmaxf(over_max, (mag - gc) * __ldg(b.ginv_eta + i));
+                s_grp += S * sc;
+                se_grp += Se * sc;
+                sn_grp += Sn * sc;
+                S = 0.f;
+                Se = 0.f;
+                Sn = 0.f;
+            }
         }
     }
     // deeper trees: the nodes above the groups, level by level (deepest
@@ -95,9 +124,7 @@ __device__ __forceinline__ void step_station(const DevBatch& b, const DevParams&
             for (int q = 0; q < n; ++q) {
                 const long long i = pb + q;
                 const uint32_t m = b.meta[i], m2 = b.meta2[i] >> (8 * j);
-                float Pr = 0.f;
-                if (b.trem[i] > 0)
-                    Pr = clip(level_of(q), m & kMetaDC, b.soc[i], b.erem[i], b.cap[i], b.rbar[i], b.pw[i]);
+                const float Pr = Pst[q];
                 if (m2 & 1u) {
                     Su = 0.f;
                     Sr = 0.f;
@@ -120,8 +147,7 @@ __device__ __forceinline__ void step_station(const DevBatch& b, const DevParams&
             if (b.trem[i] == 0) continue;
             const uint32_t m = b.meta[i];
             const bool dc = m & kMetaDC;
-            const float P = clip(level_of(q), dc, b.soc[i], b.erem[i], b.cap[i], b.rbar[i], b.pw[i]) *
-                            gscale[(m >> kMetaGroupShift) & 31] * upper_mult(i, TL);
+            const float P = Pst[q] * gscale[(m >> kMetaGroupShift) & 31] * upper_mult(i, TL);
             s_grp += P;
             if (V2G) {
                 if (P >= 0.f) se_grp += P * (dc ? p.inv_eta1 : p.inv_eta0);
@@ -144,54 +170,99 @@ __device__ __forceinline__ void step_station(const DevBatch& b, const DevParams&
     const float raw = V2G ? fabsf(s_raw + Pb) : s_raw;
     const float c_con = fmaxf(fmaxf(over_max, (raw - grid_cap) * b.grid_inv_eta[s]), 0.0f);
 
-    // -- (ii) charge, time advance, (iii) departures
+    // -- (ii) charge, time advance, (iii) departures; chunk v + 1 is loaded
+    // before chunk v is stored
     float c_sat = 0.f, c_sat1 = 0.f;
     int n_free = 0;
-    for (int q = 0; q < n; ++q) {
-        const long long i = pb + q;
-        const uint32_t m = b.meta[i];
-        const bool dc = m & kMetaDC;
-        int tr = b.trem[i];
-        float P = 0.f;
-        if (tr > 0) {
-            float soc = b.soc[i], erem = b.erem[i];
-            const float cap = b.cap[i];
-            P = clip(level_of(q), dc, soc, erem, cap, b.rbar[i], b.pw[i]);
-            P = P * gscale[(m >> kMetaGroupShift) & 31];
-            if (TL > 0) P *= upper_mult(i, TL);
-            P *= s_root;
-            const float dE = P * p.dt;
-            soc = fminf(soc + __fdividef(dE, cap), 1.0f);
-            if (V2G) soc = fmaxf(soc, 0.0f);
-            erem = fmaxf(erem - dE, 0.0f);
-            bool leave;
-            if (p.cs_share && tr == kTremCS) {
-                // charge-sensitive: one step nearer the desired departure;
-                // leaves once the demand is met (c_Sat,1: overdue - beta early)
-                const int d = (int)b.due[i] - 1;
-                leave = erem <= p.eps * cap;     // demand met: target SoC within eps
-                if (leave) {
-                    c_sat1 += (float)max(-d, 0) - p.beta * (float)max(d, 0);
-                    tr = 0;
-                    b.due[i] = 0;
-                } else {
-                    b.due[i] = (int16_t)d;
-                }
-            } else {
-                tr -= 1;
-                leave = tr == 0;
-                if (leave) c_sat += erem;
-            }
-            if (leave) {
-                b.soc[i] = 0.f; b.erem[i] = 0.f; b.cap[i] = 0.f; b.rbar[i] = 0.f;
-            } else {
-                b.soc[i] = soc; b.erem[i] = erem;
-            }
-            b.trem[i] = (uint8_t)tr;
+    uint32_t free_mask[kMaxPorts / 32] = {};
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 so = z4, er = z4, ca = z4;
+    uint4 me = make_uint4(0u, 0u, 0u, 0u);
+    uint32_t tr4 = 0;
+    if (nv > 0) {
+        so = ld4(b.soc + pb); er = ld4(b.erem + pb); ca = ld4(b.cap + pb);
+        me = __ldg(reinterpret_cast<const uint4*>(b.meta + pb));
+        tr4 = *reinterpret_cast<const uint32_t*>(b.trem + pb);
+    }
+    for (int v = 0; v < nv; ++v) {
+        const long long i0 = pb + 4 * v;
+        float4 so1 = z4, er1 = z4, ca1 = z4;
+        uint4 me1 = make_uint4(0u, 0u, 0u, 0u);
+        uint32_t tr41 = 0;
+        if (v + 1 < nv) {
+            so1 = ld4(b.soc + i0 + 4); er1 = ld4(b.erem + i0 + 4); ca1 = ld4(b.cap + i0 + 4);
+            me1 = __ldg(reinterpret_cast<const uint4*>(b.meta + i0 + 4));
+            tr41 = *reinterpret_cast<const uint32_t*>(b.trem + i0 + 4);
         }
-        // Delta form: a departed car's charger drops to 0, the next car's base
-        b.pw[i] = (p.delta && tr == 0) ? 0.f : P;
-        n_free += (tr == 0);
+        float4 pw4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        uint32_t tr_out = tr4;
+        bool any_leave = false;
+        uint32_t leave_bits = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int q = 4 * v + j;
+            if (q >= n) break;
+            const long long i = i0 + j;
+            const uint32_t m = at(me, j);
+            int tr = (tr4 >> (8 * j)) & 0xFFu;
+            float P = 0.f;
+            if (tr > 0) {
+                float soc = at(so, j), erem = at(er, j);
+                const float cap = at(ca, j);
+                P = Pst[q] * gscale[(m >> kMetaGroupShift) & 31];
+                if (TL > 0) P *= upper_mult(i, TL);
+                P *= s_root;
+                const float dE = P * p.dt;
+                soc = fminf(soc + __fdividef(dE, cap), 1.0f);
+                if (V2G) soc = fmaxf(soc, 0.0f);
+                erem = fmaxf(erem - dE, 0.0f);
+                bool leave;
+                if (p.cs_share && tr == kTremCS) {
+                    // charge-sensitive: one step nearer the desired departure;
+                    // leaves once the demand is met (c_Sat,1: overdue - beta early)
+                    const int d = (int)b.due[i] - 1;
+                    leave = erem <= p.eps * cap;     // demand met: target SoC within eps
+                    if (leave) {
+                        c_sat1 += (float)max(-d, 0) - p.beta * (float)max(d, 0);
+                        tr = 0;
+                        b.due[i] = 0;
+                    } else {
+                        b.due[i] = (int16_t)d;
+                    }
+                } else {
+                    tr -= 1;
+                    leave = tr == 0;
+                    if (leave) c_sat += erem;
+                }
+                if (leave) {
+                    soc = 0.f;
+                    erem = 0.f;
+                    at(ca, j) = 0.f;
+                    leave_bits |= 1u << j;
+                    any_leave = true;
+                }
+                at(so, j) = soc;
+                at(er, j) = erem;
+                tr_out = (tr_out & ~(0xFFu << (8 * j))) | ((uint32_t)tr << (8 * j));
+            }
+            // Delta form: a departed car's charger drops to 0, the next car's base
+            at(pw4, j) = (p.delta && tr == 0) ? 0.f : P;
+            if (tr == 0) {
+                ++n_free;
+                free_mask[q >> 5] |= 1u << (q & 31);
+            }
+        }
+        st4(b.soc + i0, so);
+        st4(b.erem + i0, er);
+        st4(b.pw + i0, pw4);
+        *reinterpret_cast<uint32_t*>(b.trem + i0) = tr_out;
+        if (any_leave) {
+            st4(b.cap + i0, ca);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (leave_bits & (1u << j)) b.rbar[i0 + j] = 0.f;
+        }
+        so = so1; er = er1; ca = ca1; me = me1; tr4 = tr41;
     }
     const float e_net = s_grp * s_root * p.dt;
     const float e_grid = se_grp * s_root * p.dt;
@@ -204,22 +275,27 @@ __device__ __forceinline__ void step_station(const DevBatch& b, const DevParams&
         b.bp[s] = pb_applied;
     }
 
-    // -- (iv) arrivals: Poisson count, first come first served
+    // -- (iv) arrivals: Poisson count, first come first served (free chargers
+    // in ascending index)
     const int M = arrivals(b, p, (uint32_t)uid, g, t, b.arrival_class[s], k0, k1);
     const int m_adm = min(M, n_free);
     const uint32_t ncar = b.ncar[s];
-    for (int q = 0, j = 0; q < n && j < m_adm; ++q) {
-        const long long i = pb + q;
-        if (b.trem[i] != 0) continue;
-        const Car car = car_from_words(car_words((uint32_t)uid, ncar + (uint32_t)j, k0, k1), b.meta[i] & kMetaDC, p);
-        b.cap[i] = car.cap; b.soc[i] = car.soc; b.erem[i] = car.erem; b.rbar[i] = car.rbar;
-        if (car.cs) {                      // charge-sensitive user: stays until charged
-            b.trem[i] = (uint8_t)kTremCS;
-            b.due[i] = (int16_t)car.stay;
-        } else {
-            b.trem[i] = (uint8_t)car.stay;
+    for (int w = 0, j = 0; w < kMaxPorts / 32 && j < m_adm; ++w) {
+        uint32_t fm = free_mask[w];
+        while (fm && j < m_adm) {
+            const int q = 32 * w + __ffs(fm) - 1;
+            fm &= fm - 1;
+            const long long i = pb + q;
+            const Car car = car_from_words(car_words((uint32_t)uid, ncar + (uint32_t)j, k0, k1), b.meta[i] & kMetaDC, p);
+            b.cap[i] = car.cap; b.soc[i] = car.soc; b.erem[i] = car.erem; b.rbar[i] = car.rbar;
+            if (car.cs) {                  // charge-sensitive user: stays until charged
+                b.trem[i] = (uint8_t)kTremCS;
+                b.due[i] = (int16_t)car.stay;
+            } else {
+                b.trem[i] = (uint8_t)car.stay;
+            }
+            ++j;
         }
-        ++j;
     }
 
     // -- reward, Appendix A.3: E_grid,net = bought + pushed into the grid + battery
@@ -250,10 +326,12 @@ __device__ __forceinline__ void step_station(const DevBatch& b, const DevParams&
         b.last_ret[s] = ret;
         ret = 0.f;
         b.n_episodes[s] += 1u;
-        for (int q = 0; q < C; ++q) {
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int q = 0; q < C; q += 4) {
             const long long i = pb + q;
-            b.soc[i] = 0.f; b.erem[i] = 0.f; b.cap[i] = 0.f; b.rbar[i] = 0.f; b.pw[i] = 0.f; b.trem[i] = 0;
-            if (p.cs_share) b.due[i] = 0;
+            st4(b.soc + i, z); st4(b.erem + i, z); st4(b.cap + i, z); st4(b.rbar + i, z); st4(b.pw + i, z);
+            *reinterpret_cast<uint32_t*>(b.trem + i) = 0u;
+            if (p.cs_share) *reinterpret_cast<uint2*>(b.due + i) = make_uint2(0u, 0u);
         }
         if (V2G) {
             b.bsoc[s] = p.batt_soc0;
