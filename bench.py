@@ -456,7 +456,7 @@ def run_b300(args):
                          "launches_per_step": T,
                          "roofline": {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
                                       "frac": gbs / pk["hbm_gbs"], "traffic": None, "kernel": "k_step_plain",
-                                      "note": "state L2-resident across the 288 launches of a step"}}
+                                      "note": "one thread per station: memory-latency bound (state read and written every step)"}}
         line["fused_over_plain"] = line["value"] / line["plain"]["value"]
         line["gpu_launches"] += T * args.steps
         del bp

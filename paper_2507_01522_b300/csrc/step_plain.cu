@@ -14,6 +14,7 @@ namespace chx {
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
 constexpr int kMaxPorts = 128;             // chargers per station slot at most
+constexpr int kPlainThreads = 128;         // threads (stations) per block
 __device__ __forceinline__ float& at(float4& v, int j) { return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w; }
 __device__ __forceinline__ float get(const float4& v, int j) { return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w; }
 __device__ __forceinline__ uint32_t at(const uint4& v, int j) { return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w; }
@@ -31,7 +32,7 @@ __device__ __forceinline__ uint32_t at(const uint4& v, int j) { return j == 0 ? 
 template <bool V2G>
 __device__ __forceinline__ void step_station(const DevBatch& b, const DevParams& p, const int8_t* __restrict__ actions,
                                              long long lda, float* __restrict__ reward, uint8_t* __restrict__ done,
-                                             int s)
+                                             int s, float* __restrict__ gscale)
 {
     const int uid = b.user_id[s];
     if (uid < 0) return;
@@ -61,16 +62,28 @@ __device__ __forceinline__ void step_station(const DevBatch& b, const DevParams&
     };
 
     // -- (i) apply actions: per-charger clip, then group sums (Eq. ArchConst)
-    float Pst[kMaxPorts];                               // clipped (requested) power of each charger
-    float gscale[32];
+    __align__(16) float Pst[kMaxPorts];                 // clipped (requested) power of each charger
+    // gscale[g * kPlainThreads]: scale of group slot g (this thread's column
+    // of a block-wide shared array: no bank conflicts, no local memory)
     float S = 0.f, Se = 0.f, Sn = 0.f, s_raw = 0.f, s_grp = 0.f, se_grp = 0.f, sn_grp = 0.f, over_max = 0.f;
-#pragma unroll 2
-    for (int v = 0; v < nv; ++v) {
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const uint4 zu4 = make_uint4(0u, 0u, 0u, 0u);
+    float4 xso = ld4(b.soc + pb), xer = ld4(b.erem + pb), xca = ld4(b.cap + pb), xrb = ld4(b.rbar + pb),
+           xpl = ld4(b.pw + pb), xgc = ld4(b.gcap + pb), xgi = ld4(b.ginv_eta + pb);
+    uint4 xme = __ldg(reinterpret_cast<const uint4*>(b.meta + pb));
+    uint32_t xtr = *reinterpret_cast<const uint32_t*>(b.trem + pb);
+    for (int v = 0; v < nv; ++v) {                      // chunk v + 1 is loaded before chunk v is computed
         const long long i0 = pb + 4 * v;
-        const float4 so = ld4(b.soc + i0), er = ld4(b.erem + i0), ca = ld4(b.cap + i0), rb = ld4(b.rbar + i0),
-                     pl = ld4(b.pw + i0);
-        const uint4 me = __ldg(reinterpret_cast<const uint4*>(b.meta + i0));
-        const uint32_t tr4 = *reinterpret_cast<const uint32_t*>(b.trem + i0);
+        const float4 so = xso, er = xer, ca = xca, rb = xrb, pl = xpl, gc4 = xgc, gi4 = xgi;
+        const uint4 me = xme;
+        const uint32_t tr4 = xtr;
+        if (v + 1 < nv) {
+            xso = ld4(b.soc + i0 + 4); xer = ld4(b.erem + i0 + 4); xca = ld4(b.cap + i0 + 4);
+            xrb = ld4(b.rbar + i0 + 4); xpl = ld4(b.pw + i0 + 4);
+            xgc = ld4(b.gcap + i0 + 4); xgi = ld4(b.ginv_eta + i0 + 4);   // group limits, read at group tails
+            xme = __ldg(reinterpret_cast<const uint4*>(b.meta + i0 + 4));
+            xtr = *reinterpret_cast<const uint32_t*>(b.trem + i0 + 4);
+        }
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int q = 4 * v + j;
@@ -93,12 +106,11 @@ __device__ __forceinline__ void step_station(const DevBatch& b, const DevParams&
             }
             s_raw += P;
             if (m & kMetaTail) {
-                const long long i = i0 + j;
-                const float gc = __ldg(b.gcap + i);
+                const float gc = get(gc4, j);
                 const float mag = V2G ? fabsf(S) : S;
                 const float sc = mag > gc ? __fdividef(gc, mag) : 1.0f;
-                gscale[(m >> kMetaGroupShift) & 31] = sc;
-                over_max = fmaxf(over_max, (mag - gc) * __ldg(b.ginv_eta + i));
+                gscale[((m >> kMetaGroupShift) & 31) * kPlainThreads] = sc;
+                over_max = fmaxf(over_max, (mag - gc) * get(gi4, j));
                 s_grp += S * sc;
                 se_grp += Se * sc;
                 sn_grp += Sn * sc;
@@ -129,7 +141,7 @@ __device__ __forceinline__ void step_station(const DevBatch& b, const DevParams&
                     Su = 0.f;
                     Sr = 0.f;
                 }
-                Su += Pr * gscale[(m >> kMetaGroupShift) & 31] * upper_mult(i, j);
+                Su += Pr * gscale[((m >> kMetaGroupShift) & 31) * kPlainThreads] * upper_mult(i, j);
                 Sr += Pr;
                 if (m2 & 2u) {
                     const float cap_u = b.ucap[(long long)j * b.port_slots + i];
@@ -147,7 +159,7 @@ __device__ __forceinline__ void step_station(const DevBatch& b, const DevParams&
             if (b.trem[i] == 0) continue;
             const uint32_t m = b.meta[i];
             const bool dc = m & kMetaDC;
-            const float P = Pst[q] * gscale[(m >> kMetaGroupShift) & 31] * upper_mult(i, TL);
+            const float P = Pst[q] * gscale[((m >> kMetaGroupShift) & 31) * kPlainThreads] * upper_mult(i, TL);
             s_grp += P;
             if (V2G) {
                 if (P >= 0.f) se_grp += P * (dc ? p.inv_eta1 : p.inv_eta0);
@@ -174,23 +186,24 @@ __device__ __forceinline__ void step_station(const DevBatch& b, const DevParams&
     // before chunk v is stored
     float c_sat = 0.f, c_sat1 = 0.f;
     int n_free = 0;
-    uint32_t free_mask[kMaxPorts / 32] = {};
-    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 so = z4, er = z4, ca = z4;
-    uint4 me = make_uint4(0u, 0u, 0u, 0u);
+    unsigned long long free_lo = 0ull, free_hi = 0ull;  // free chargers 0-63, 64-127
+    float4 so = z4, er = z4, ca = z4, ps = z4;
+    uint4 me = zu4;
     uint32_t tr4 = 0;
     if (nv > 0) {
         so = ld4(b.soc + pb); er = ld4(b.erem + pb); ca = ld4(b.cap + pb);
+        ps = *reinterpret_cast<const float4*>(Pst);
         me = __ldg(reinterpret_cast<const uint4*>(b.meta + pb));
         tr4 = *reinterpret_cast<const uint32_t*>(b.trem + pb);
     }
     for (int v = 0; v < nv; ++v) {
         const long long i0 = pb + 4 * v;
-        float4 so1 = z4, er1 = z4, ca1 = z4;
-        uint4 me1 = make_uint4(0u, 0u, 0u, 0u);
+        float4 so1 = z4, er1 = z4, ca1 = z4, ps1 = z4;
+        uint4 me1 = zu4;
         uint32_t tr41 = 0;
         if (v + 1 < nv) {
             so1 = ld4(b.soc + i0 + 4); er1 = ld4(b.erem + i0 + 4); ca1 = ld4(b.cap + i0 + 4);
+            ps1 = *reinterpret_cast<const float4*>(Pst + 4 * v + 4);
             me1 = __ldg(reinterpret_cast<const uint4*>(b.meta + i0 + 4));
             tr41 = *reinterpret_cast<const uint32_t*>(b.trem + i0 + 4);
         }
@@ -209,7 +222,7 @@ __device__ __forceinline__ void step_station(const DevBatch& b, const DevParams&
             if (tr > 0) {
                 float soc = at(so, j), erem = at(er, j);
                 const float cap = at(ca, j);
-                P = Pst[q] * gscale[(m >> kMetaGroupShift) & 31];
+                P = get(ps, j) * gscale[((m >> kMetaGroupShift) & 31) * kPlainThreads];
                 if (TL > 0) P *= upper_mult(i, TL);
                 P *= s_root;
                 const float dE = P * p.dt;
@@ -249,7 +262,8 @@ __device__ __forceinline__ void step_station(const DevBatch& b, const DevParams&
             at(pw4, j) = (p.delta && tr == 0) ? 0.f : P;
             if (tr == 0) {
                 ++n_free;
-                free_mask[q >> 5] |= 1u << (q & 31);
+                if (q < 64) free_lo |= 1ull << q;
+                else free_hi |= 1ull << (q - 64);
             }
         }
         st4(b.soc + i0, so);
@@ -262,7 +276,7 @@ __device__ __forceinline__ void step_station(const DevBatch& b, const DevParams&
             for (int j = 0; j < 4; ++j)
                 if (leave_bits & (1u << j)) b.rbar[i0 + j] = 0.f;
         }
-        so = so1; er = er1; ca = ca1; me = me1; tr4 = tr41;
+        so = so1; er = er1; ca = ca1; ps = ps1; me = me1; tr4 = tr41;
     }
     const float e_net = s_grp * s_root * p.dt;
     const float e_grid = se_grp * s_root * p.dt;
@@ -280,10 +294,10 @@ __device__ __forceinline__ void step_station(const DevBatch& b, const DevParams&
     const int M = arrivals(b, p, (uint32_t)uid, g, t, b.arrival_class[s], k0, k1);
     const int m_adm = min(M, n_free);
     const uint32_t ncar = b.ncar[s];
-    for (int w = 0, j = 0; w < kMaxPorts / 32 && j < m_adm; ++w) {
-        uint32_t fm = free_mask[w];
+    for (int w = 0, j = 0; w < 2 && j < m_adm; ++w) {
+        unsigned long long fm = w == 0 ? free_lo : free_hi;
         while (fm && j < m_adm) {
-            const int q = 32 * w + __ffs(fm) - 1;
+            const int q = 64 * w + __ffsll((long long)fm) - 1;
             fm &= fm - 1;
             const long long i = pb + q;
             const Car car = car_from_words(car_words((uint32_t)uid, ncar + (uint32_t)j, k0, k1), b.meta[i] & kMetaDC, p);
@@ -348,14 +362,15 @@ __device__ __forceinline__ void step_station(const DevBatch& b, const DevParams&
 }
 
 template <bool V2G>
-__global__ void __launch_bounds__(128) k_step_plain(DevBatch b, DevParams p, const int8_t* __restrict__ actions,
+__global__ void __launch_bounds__(kPlainThreads) k_step_plain(DevBatch b, DevParams p, const int8_t* __restrict__ actions,
                                                     long long lda, float* __restrict__ reward,
                                                     uint8_t* __restrict__ done, const int* __restrict__ slot_list,
                                                     int n_list)
 {
+    __shared__ float gscale[32 * kPlainThreads];
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (slot_list ? n_list : b.n_slots)) return;
-    step_station<V2G>(b, p, actions, lda, reward, done, slot_list ? slot_list[idx] : idx);
+    step_station<V2G>(b, p, actions, lda, reward, done, slot_list ? slot_list[idx] : idx, gscale + threadIdx.x);
 }
 
 void launch_step_plain(const DevBatch& b, const DevParams& p, const int8_t* actions, long long lda, float* reward,
@@ -363,7 +378,7 @@ void launch_step_plain(const DevBatch& b, const DevParams& p, const int8_t* acti
 {
     const int n = slot_list ? n_list : b.n_slots;
     if (n <= 0) return;
-    const int threads = 128;
+    const int threads = kPlainThreads;
     if (p.v2g)
         k_step_plain<true><<<(n + threads - 1) / threads, threads, 0, st>>>(b, p, actions, lda, reward, done, slot_list,
                                                                               n_list);
