@@ -539,7 +539,6 @@ int build_handle(const chx_stations* st, const chx_env_params* prm, const chx_ex
     int tb = 0;
     for (int c = kNumClasses - 1; c >= 0; --c) {
         if (h->cls_n_env[c] == 0) continue;
-        const int C = 8 << c;
         const int epw = tile_epw(c);
         h->sched.sched_cls[h->sched.n_sched] = c;
         h->sched.sched_tile_base[h->sched.n_sched] = tb;

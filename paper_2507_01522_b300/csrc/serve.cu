@@ -77,18 +77,24 @@ struct Request {
     bool failed = false;
 };
 
+constexpr size_t kUpHead = 16;             // work counters at the head of a tick's upload
+static_assert(kFusedCounters * sizeof(int) <= kUpHead, "counters fit the upload head");
+
 struct Tick {
     cudaStream_t st = nullptr;
     cudaEvent_t ev_start = nullptr, ev_end = nullptr;
-    // pinned host and device buffers
-    int4 *h_entries = nullptr, *d_entries = nullptr;
-    int8_t *h_act = nullptr, *d_act = nullptr;
-    float *h_rew = nullptr, *d_rew = nullptr;
-    uint8_t *h_done = nullptr, *d_done = nullptr;
-    float *h_obs = nullptr, *d_obs = nullptr;
+    // pinned host and device buffers, one copy each way per tick:
+    // up   = [zeroed work counters (kUpHead bytes)][entries][actions]
+    // down = [rewards][done flags][observations, 16-byte aligned]
+    unsigned char *h_up = nullptr, *d_up = nullptr;
+    unsigned char *h_down = nullptr, *d_down = nullptr;
+    int4 *h_entries = nullptr, *d_entries = nullptr;   // up + kUpHead
+    int* d_counter = nullptr;                          // d_up
+    float* h_rew = nullptr;                            // this tick's outputs inside h_down
+    uint8_t* h_done = nullptr;
+    float* h_obs = nullptr;
     int32_t *h_rslots = nullptr, *d_rslots = nullptr;
     unsigned long long *h_rseeds = nullptr, *d_rseeds = nullptr;
-    int* d_counter = nullptr;
     std::vector<uint32_t> recs;             // request records in this tick
     std::vector<int64_t> rew_off, obs_off;  // per record: where its outputs start in the tick buffers
     bool busy = false;
@@ -218,31 +224,28 @@ int alloc_tick(chx_srv* s, Tick& t)
     SRV_TRY(cudaStreamCreateWithFlags(&t.st, cudaStreamNonBlocking));
     SRV_TRY(cudaEventCreate(&t.ev_start));
     SRV_TRY(cudaEventCreate(&t.ev_end));
-    SRV_TRY(cudaHostAlloc(&t.h_entries, ne * sizeof(int4), cudaHostAllocDefault));
-    SRV_TRY(cudaHostAlloc(&t.h_act, na, cudaHostAllocDefault));
-    SRV_TRY(cudaHostAlloc(&t.h_rew, ne * sizeof(float), cudaHostAllocDefault));
-    SRV_TRY(cudaHostAlloc(&t.h_done, ne, cudaHostAllocDefault));
-    SRV_TRY(cudaHostAlloc(&t.h_obs, no * sizeof(float), cudaHostAllocDefault));
+    const size_t up = kUpHead + ne * sizeof(int4) + na;
+    const size_t down = ((ne * 5 + 15) & ~size_t(15)) + no * sizeof(float);
+    SRV_TRY(cudaHostAlloc(&t.h_up, up, cudaHostAllocDefault));
+    SRV_TRY(cudaHostAlloc(&t.h_down, down, cudaHostAllocDefault));
     SRV_TRY(cudaHostAlloc(&t.h_rslots, ne * sizeof(int32_t), cudaHostAllocDefault));
     SRV_TRY(cudaHostAlloc(&t.h_rseeds, ne * sizeof(unsigned long long), cudaHostAllocDefault));
-    SRV_TRY(cudaMalloc(&t.d_entries, ne * sizeof(int4)));
-    SRV_TRY(cudaMalloc(&t.d_act, na));
-    SRV_TRY(cudaMalloc(&t.d_rew, ne * sizeof(float)));
-    SRV_TRY(cudaMalloc(&t.d_done, ne));
-    SRV_TRY(cudaMalloc(&t.d_obs, no * sizeof(float)));
+    SRV_TRY(cudaMalloc(&t.d_up, up));
+    SRV_TRY(cudaMalloc(&t.d_down, down));
     SRV_TRY(cudaMalloc(&t.d_rslots, ne * sizeof(int32_t)));
     SRV_TRY(cudaMalloc(&t.d_rseeds, ne * sizeof(unsigned long long)));
-    SRV_TRY(cudaMalloc(&t.d_counter, kFusedCounters * sizeof(int)));
+    std::memset(t.h_up, 0, kUpHead);       // the counters every tick uploads as zero
+    t.h_entries = reinterpret_cast<int4*>(t.h_up + kUpHead);
+    t.d_entries = reinterpret_cast<int4*>(t.d_up + kUpHead);
+    t.d_counter = reinterpret_cast<int*>(t.d_up);
     return CHX_OK;
 }
 
 void free_tick(Tick& t)
 {
     if (t.st) cudaStreamSynchronize(t.st);
-    cudaFreeHost(t.h_entries); cudaFreeHost(t.h_act); cudaFreeHost(t.h_rew); cudaFreeHost(t.h_done);
-    cudaFreeHost(t.h_obs); cudaFreeHost(t.h_rslots); cudaFreeHost(t.h_rseeds);
-    cudaFree(t.d_entries); cudaFree(t.d_act); cudaFree(t.d_rew); cudaFree(t.d_done); cudaFree(t.d_obs);
-    cudaFree(t.d_rslots); cudaFree(t.d_rseeds); cudaFree(t.d_counter);
+    cudaFreeHost(t.h_up); cudaFreeHost(t.h_down); cudaFreeHost(t.h_rslots); cudaFreeHost(t.h_rseeds);
+    cudaFree(t.d_up); cudaFree(t.d_down); cudaFree(t.d_rslots); cudaFree(t.d_rseeds);
     if (t.ev_start) cudaEventDestroy(t.ev_start);
     if (t.ev_end) cudaEventDestroy(t.ev_end);
     if (t.st) cudaStreamDestroy(t.st);
@@ -286,7 +289,6 @@ int launch_tick(chx_srv* s, int ti, const std::vector<Request*>& rq)
     io.n_sched = 0;
     for (int c = kNumClasses - 1; c >= 0; --c) {
         if (count[c] == 0) continue;
-        const int C = 8 << c;
         const int epw = tile_epw(c);
         const int padded = (count[c] + epw - 1) / epw * epw;
         io.gather_base[c] = n_entries;
@@ -300,13 +302,21 @@ int launch_tick(chx_srv* s, int ti, const std::vector<Request*>& rq)
     }
     io.sched_tile_base[io.n_sched] = tb;
     io.total_tiles = tb;
+    // actions right after the used entries (one upload); outputs packed
+    int8_t* h_act = reinterpret_cast<int8_t*>(t.h_up + kUpHead + (size_t)n_entries * sizeof(int4));
+    int8_t* d_act = reinterpret_cast<int8_t*>(t.d_up + kUpHead + (size_t)n_entries * sizeof(int4));
+    const size_t done_at = (size_t)rew_used * sizeof(float);
+    const size_t obs_at = ((size_t)rew_used * 5 + 15) & ~size_t(15);
+    t.h_rew = reinterpret_cast<float*>(t.h_down);
+    t.h_done = t.h_down + done_at;
+    t.h_obs = reinterpret_cast<float*>(t.h_down + obs_at);
     // pass 2: entries straight into the pinned buffer, actions concatenated
     for (size_t r = 0; r < rq.size(); ++r) {
         Request& q = *rq[r];
         if (q.kind == CHX_SRV_RESET) continue;
         int64_t act_base = -1;
         if (!q.actions.empty()) {
-            std::memcpy(t.h_act + act_used, q.actions.data(), q.actions.size());
+            std::memcpy(h_act + act_used, q.actions.data(), q.actions.size());
             act_base = act_used;
             act_used += (int64_t)q.actions.size();
         }
@@ -323,13 +333,13 @@ int launch_tick(chx_srv* s, int ti, const std::vector<Request*>& rq)
     io.k_steps = 1;
     // a tick is either all Philox actions or all given actions (the scheduler
     // never mixes them), so io.actions applies to every entry
-    io.actions = act_used > 0 ? t.d_act : nullptr;
+    io.actions = act_used > 0 ? d_act : nullptr;
     io.lda = 1;
-    io.reward = t.d_rew;
-    io.done = t.d_done;
+    io.reward = reinterpret_cast<float*>(t.d_down);
+    io.done = t.d_down + done_at;
     io.ld_out = 1;
     io.ld_step = 1;
-    io.obs = obs_used > 0 ? t.d_obs : nullptr;
+    io.obs = obs_used > 0 ? reinterpret_cast<float*>(t.d_down + obs_at) : nullptr;
     io.counter = t.d_counter;
     io.gather = t.d_entries;
     s->ns_pack += now_ns() - t_p0;
@@ -343,15 +353,12 @@ int launch_tick(chx_srv* s, int ti, const std::vector<Request*>& rq)
         SRV_TRY(cudaGetLastError());
     }
     if (tb > 0) {
-        SRV_TRY(cudaMemcpyAsync(t.d_entries, t.h_entries, n_entries * sizeof(int4), cudaMemcpyHostToDevice, st));
-        if (act_used > 0) SRV_TRY(cudaMemcpyAsync(t.d_act, t.h_act, act_used, cudaMemcpyHostToDevice, st));
-        SRV_TRY(cudaMemsetAsync(t.d_counter, 0, kFusedCounters * sizeof(int), st));
+        SRV_TRY(cudaMemcpyAsync(t.d_up, t.h_up, kUpHead + (size_t)n_entries * sizeof(int4) + (size_t)act_used,
+                                cudaMemcpyHostToDevice, st));
         launch_step_fused(s->b, s->dp, io, s->threads, s->sm_count, st);
         SRV_TRY(cudaGetLastError());
-        SRV_TRY(cudaMemcpyAsync(t.h_rew, t.d_rew, rew_used * sizeof(float), cudaMemcpyDeviceToHost, st));
-        SRV_TRY(cudaMemcpyAsync(t.h_done, t.d_done, rew_used, cudaMemcpyDeviceToHost, st));
-        if (obs_used > 0)
-            SRV_TRY(cudaMemcpyAsync(t.h_obs, t.d_obs, obs_used * sizeof(float), cudaMemcpyDeviceToHost, st));
+        const size_t down = obs_used > 0 ? obs_at + (size_t)obs_used * sizeof(float) : done_at + (size_t)rew_used;
+        SRV_TRY(cudaMemcpyAsync(t.h_down, t.d_down, down, cudaMemcpyDeviceToHost, st));
     }
     SRV_TRY(cudaEventRecord(t.ev_end, st));
     return CHX_OK;

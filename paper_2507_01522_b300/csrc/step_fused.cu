@@ -14,6 +14,7 @@
 // segment.  Both depend only on a charger's position inside its station, so a
 // station's result does not depend on which tile or lane offset it runs in.
 #include <algorithm>
+#include <atomic>
 #include <cfloat>
 #include <type_traits>
 
@@ -858,6 +859,20 @@ int blocks_per_sm(const void* kernel, int v, int threads)
     return n;
 }
 
+// blocks_per_sm of a range's kernel, asked of the runtime once per (range,
+// form, block size): launches on the serving path happen every tick
+int blocks_per_sm_memo(bool large, int v, int threads)
+{
+    static std::atomic<int> memo[2][kForms][9] = {};
+    std::atomic<int>& m = memo[large ? 1 : 0][v][std::min(std::max(threads / 32, 0), 8)];
+    int n = m.load(std::memory_order_relaxed);
+    if (n <= 0) {
+        n = blocks_per_sm(large ? (const void*)kLargeKernel[v] : (const void*)kSmallKernel[v], v, threads);
+        if (n > 0) m.store(n, std::memory_order_relaxed);
+    }
+    return n;
+}
+
 }  // namespace
 
 bool fused_block_size_ok(int threads)
@@ -888,13 +903,13 @@ void launch_step_fused(const DevBatch& b, const DevParams& p, const FusedIO& io,
             cudaStreamWaitEvent(side->aux, side->fork, 0);
             sb = side->aux;
         }
-        const int per_sm = blocks_per_sm((const void*)kLargeKernel[v], v, threads);
+        const int per_sm = blocks_per_sm_memo(true, v, threads);
         const int blocks = std::max(1, std::min(per_sm * sm_count, (big.total_tiles + warps - 1) / warps));
         kLargeKernel[v]<<<blocks, threads, smem, sb>>>(b, p, big);
         if (fork) cudaEventRecord(side->join, side->aux);
     }
     if (small.total_tiles > 0) {
-        const int per_sm = blocks_per_sm((const void*)kSmallKernel[v], v, threads);
+        const int per_sm = blocks_per_sm_memo(false, v, threads);
         const int blocks = std::max(1, std::min(per_sm * sm_count, (small.total_tiles + warps - 1) / warps));
         kSmallKernel[v]<<<blocks, threads, smem, st>>>(b, p, small);
     }
