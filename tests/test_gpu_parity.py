@@ -278,17 +278,25 @@ def test_autotune_keeps_state(cuda_lib):
         np.testing.assert_array_equal(before[key], after[key])
 
 
-@pytest.mark.parametrize("n", [20, 7, 3, 1])
-def test_host_api_matches_device(cuda_lib, n):
+@pytest.mark.parametrize("n,pinned", [(20, False), (7, False), (3, False), (1, False), (20, True), (7, True)])
+def test_host_api_matches_device(cuda_lib, n, pinned):
     """The host-call rollout (step-major outputs, launches whose copies
-    overlap the next) equals the device rollout, bit for bit."""
+    overlap the next) equals the device rollout, bit for bit, with pageable
+    and with pinned host buffers."""
     import torch
     from paper_2507_01522_b300.chargax import Batch
     w = odd_sizes()
     b1, b2 = Batch(w), Batch(w)
-    hr = np.zeros(b1.E * n, np.float32)
-    hd = np.zeros(b1.E * n, np.uint8)
-    ho = np.zeros(b1.obs_size, np.float32)
+
+    def host(n_items, dtype):
+        if not pinned:
+            return np.zeros(n_items, dtype)
+        t = torch.zeros(n_items, dtype={np.float32: torch.float32, np.uint8: torch.uint8}[dtype], pin_memory=True)
+        return t.numpy()
+
+    hr = host(b1.E * n, np.float32)
+    hd = host(b1.E * n, np.uint8)
+    ho = host(b1.obs_size, np.float32)
     for _ in range(2):                                  # back-to-back calls continue the episode
         b1.rollout_host(n, hr, hd, ho)
         r = torch.zeros(b2.E, n, device="cuda")
