@@ -61,7 +61,6 @@ constexpr int kBarWorkers = 1;             // named barrier of the worker warps
 constexpr int kColSoc = 352, kColErem = 384, kColCap = 416, kColRbar = 448;
 constexpr int kColPack = 480;              // remaining stay | meta << 8
 constexpr int kColPw = 0;                  // last applied power, parked in accumulator columns between MLP passes
-constexpr int kMaxObs = 8 + 6 * kPolicyMaxPorts;
 
 struct Sync {
     uint64_t full[kMaxStages], empty[kMaxStages];
