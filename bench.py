@@ -175,7 +175,11 @@ def peaks():
         return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
 
 
-# Algorithmic work per unit (derivation in DESIGN.md, "Roofline accounting").
+# Algorithmic work per unit: the bytes one plain step must read and write per
+# charger and per station, the ALU operations of one charger-step (Philox
+# share, level map, clip, rescale and sums, charge and departure, arrival
+# rank) and of one station-step (arrival draw, Poisson search, reward, car
+# profiles), and the state bytes a fused launch loads and stores.
 PLAIN_BYTES_PER_PORT_STEP = 34.0     # read trem,meta,soc,erem,cap,rbar (21) + write soc,erem,p,trem (13)
 PLAIN_BYTES_PER_ENV_STEP = 97.0      # station fields read + written, reward + done
 FUSED_OPS_PER_PORT_STEP = 48.0       # algorithmic ALU ops of one charger-step
