@@ -425,6 +425,49 @@ def test_fullsize_fixed_station_plain_sampled(cuda_lib):
     assert_reward_close(r.cpu().numpy()[ids], ro, reward_scale(info, w.params) + station_step_scale(ws, info), TRAJ_RTOL)
 
 
+def test_fullsize_heterogeneous_plain_sampled(cuda_lib):
+    """The benchmark's plain leg: 65536 mixed stations, one launch per step,
+    290 steps (past the episode end at 288); 64 stations of each size class
+    and the first and last re-simulated by the oracle: every step's reward
+    and done flag, the final state, the episode returns and counters."""
+    import torch
+    from paper_2507_01522_b300.chargax import Batch
+    w = I.heterogeneous(n_envs=65536)
+    b = Batch(w)
+    T = 290
+    r = torch.zeros(T, b.E, device="cuda")
+    d = torch.zeros(T, b.E, dtype=torch.uint8, device="cuda")
+    for k in range(T):
+        b.step(reward=r[k], done=d[k])
+    torch.cuda.synchronize()
+    b.check()
+    n = w.stations.n_ports
+    rng = np.random.default_rng(5)
+    ids = np.unique(np.concatenate([rng.choice(np.flatnonzero(n == c), 64, replace=False) for c in (8, 16, 32, 64)]
+                                   + [np.array([0, b.E - 1])]))
+    o, ws = sampled_oracle(w, ids)
+    rg, dg = r.cpu().numpy()[:, ids], d.cpu().numpy()[:, ids]
+    for k in range(T):
+        ro, do = o.step(None)
+        info = o.info()
+        assert_reward_close(rg[k], ro, reward_scale(info, w.params) + station_step_scale(ws, info), TRAJ_RTOL,
+                            where=f"step {k}")
+        np.testing.assert_array_equal(dg[k], do, err_msg=f"done step {k}")
+    gs = b.get_state()
+    po = w.stations.port_off
+    sel = np.concatenate([np.arange(po[e], po[e + 1]) for e in ids])
+    sub = {key: (v[sel] if v.shape[0] == b.P else v[ids]) for key, v in gs.items()}
+    assert_events_equal(sub, o.state(), "sampled")
+    assert_traj_close(sub, o.state(), charger_pmax(ws), TRAJ_RTOL, "sampled")
+    stg, sto = b.stats(), o.stats()
+    np.testing.assert_array_equal(stg["arrived"][ids], sto["arrived"].astype(np.uint32))
+    np.testing.assert_array_equal(stg["rejected"][ids], sto["rejected"].astype(np.uint32))
+    np.testing.assert_array_equal(stg["n_episodes"][ids], sto["n_episodes"])
+    assert np.all(sto["n_episodes"] == 1)
+    dret = np.abs(stg["last_ret"][ids] - sto["last_ret"])
+    assert np.all(dret <= RETURN_RTOL * np.maximum(np.abs(sto["last_ret"]), 1.0)), dret.max()
+
+
 def test_reset_list_out_of_range_and_empty(cuda_lib):
     """chx_reset with a list: ids outside 0..n_envs-1 are skipped (nothing
     outside the batch is written), the valid ones are reset exactly as the
