@@ -1,0 +1,39 @@
+"""The benchmark script's CPU side (no GPU): the reference arm prints one JSON
+line with the keys and kinds of values the benchmark contract names, and the
+all-cores oracle baseline splits the stations over worker processes."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_reference_arm_json_line():
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "0"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference"
+    for key in ("metric", "unit", "dtype", "data", "scaling"):
+        assert isinstance(d[key], str) and d[key]
+    assert d["value"] > 0 and d["ms_per_step"] > 0
+    assert d["n_gpus"] == 1 and d["steps"] == 1 and d["warmup"] == 0
+    assert d["higher_is_better"] is True and d["vs_baseline"] is None
+    assert d["config"]["workload"] == "hetero-65536-8/16/32/64"
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_all_cores_baseline_splits_the_stations():
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2507_01522_b300 import inputs as I
+    w = I.heterogeneous(n_envs=96)
+    res = bench.cpu_baseline_all_cores(w, 12, 3)
+    assert res["kind"] == "oracle" and res["unit"] == "env-steps/s"
+    assert 1 <= res["cores"] <= 96 and res["value"] > 0 and res["seconds"] >= 0
+    assert "slices x 3 steps" in res["sample"]
