@@ -1,10 +1,13 @@
-"""The benchmark script's CPU side (no GPU): the reference arm prints one JSON
-line with the keys and kinds of values the benchmark contract names, and the
-all-cores oracle baseline splits the stations over worker processes."""
+"""The benchmark script's output: the reference arm (CPU) prints one JSON line
+with the keys and kinds of values the benchmark contract names, the
+all-cores oracle baseline splits the stations over worker processes, and a
+short GPU-arm run carries the roofline, end-to-end, clock and launch keys."""
 import json
 import os
 import subprocess
 import sys
+
+import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -37,3 +40,22 @@ def test_all_cores_baseline_splits_the_stations():
     assert res["kind"] == "oracle" and res["unit"] == "env-steps/s"
     assert 1 <= res["cores"] <= 96 and res["value"] > 0 and res["seconds"] >= 0
     assert "slices x 3 steps" in res["sample"]
+
+
+@pytest.mark.gpu
+def test_gpu_arm_json_line():
+    """A short run of the GPU arm (4096 stations, one timed episode): the
+    line carries the roofline, end-to-end, clock and launch-count keys."""
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--steps", "1", "--warmup", "1",
+                          "--n-envs", "4096", "--no-serve", "--no-policy", "--no-variants", "--no-v2g",
+                          "--no-cpu-baseline"], cwd=ROOT, capture_output=True, text=True, timeout=900)
+    assert out.returncode == 0, out.stderr[-2000:]
+    d = json.loads([l for l in out.stdout.splitlines() if l.startswith("{")][-1])
+    assert d["value"] > 0 and d["n_gpus"] == 1 and d["higher_is_better"] is True
+    rf = d["roofline"]
+    assert rf["bound"] in ("alu", "hbm", "tensor") and rf["achieved"] > 0 and rf["peak"] > 0
+    assert abs(rf["frac"] - rf["achieved"] / rf["peak"]) < 1e-9
+    e2e = d["e2e"]
+    assert e2e["value"] > 0 and e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] > 0
+    assert d["gpu_launches"] > 0 and d["plain"]["value"] > 0
+    assert {"sm_mhz", "sm_max_mhz", "reasons"} <= set(d["clocks"])
