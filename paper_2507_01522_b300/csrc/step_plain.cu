@@ -17,18 +17,21 @@ constexpr int kMaxPorts = 128;             // chargers per station slot at most
 constexpr int kPlainThreads = 128;         // threads (stations) per block
 __device__ __forceinline__ float& at(float4& v, int j) { return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w; }
 __device__ __forceinline__ float get(const float4& v, int j) { return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w; }
-__device__ __forceinline__ uint32_t at(const uint4& v, int j) { return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w; }
+__device__ __forceinline__ uint32_t get(const uint4& v, int j) { return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w; }
 
 // One station's step.  V2G: signed levels (clip_power_v2g), the station
 // battery at the root (its level after the chargers' in the action array, or
 // drawn at charger index n), signed limits (|sum| <= eta * I), discharge
 // energy after the port loss, two-case profit and degradation penalty.
 //
-// The chargers are walked in chunks of four with 16-byte loads.  Pass (i)
-// draws each charger's level once, clips it and keeps the clipped power in a
-// per-thread array (local memory: consecutive threads' copies of one element
-// are adjacent, so a warp's accesses are coalesced); the node passes and the
-// charge pass read it from there.  Sums run charger by charger in index order.
+// The chargers are walked in chunks of four with 16-byte loads, the next
+// chunk loaded before the current one is used.  Pass (i) draws each
+// charger's level once, clips it and keeps the clipped power in a per-thread
+// array (local memory: consecutive threads' copies of one element are
+// adjacent, so a warp's accesses are coalesced); the node passes and the
+// charge pass read it from there.  Group scales live in this thread's column
+// of a block-wide shared array (gscale[g * kPlainThreads]).  Sums run charger
+// by charger in index order.
 template <bool V2G>
 __device__ __forceinline__ void step_station(const DevBatch& b, const DevParams& p, const int8_t* __restrict__ actions,
                                              long long lda, float* __restrict__ reward, uint8_t* __restrict__ done,
@@ -88,7 +91,7 @@ __device__ __forceinline__ void step_station(const DevBatch& b, const DevParams&
         for (int j = 0; j < 4; ++j) {
             const int q = 4 * v + j;
             if (q >= n) break;
-            const uint32_t m = at(me, j);
+            const uint32_t m = get(me, j);
             const bool dc = m & kMetaDC;
             float P = 0.f;
             if ((tr4 >> (8 * j)) & 0xFFu) {
@@ -216,7 +219,7 @@ __device__ __forceinline__ void step_station(const DevBatch& b, const DevParams&
             const int q = 4 * v + j;
             if (q >= n) break;
             const long long i = i0 + j;
-            const uint32_t m = at(me, j);
+            const uint32_t m = get(me, j);
             int tr = (tr4 >> (8 * j)) & 0xFFu;
             float P = 0.f;
             if (tr > 0) {
