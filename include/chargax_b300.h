@@ -377,6 +377,14 @@ int chx_load(chx_handle* h, const void* h_buf, size_t size);
  *   function (FP32 sums may round differently) and leave the same state.
  * A tensor-core wait that runs out of time (it should not) makes chx_check
  * return CHX_ETIMEOUT; the results of that call are then invalid. */
+/* Diagnostics: one bounded wait, the kind every role of the tensor-core
+ * kernels uses, on a barrier nothing releases.  It must give up after its
+ * limit (2^31 SM cycles, about a second), set the handle's fault flag (the
+ * next chx_check returns CHX_ETIMEOUT) and leave the context usable.
+ * h_result[0] = 1 if the wait gave up and raised the flag; h_result[1] =
+ * cycles it waited / 2^20. */
+int chx_selftest_wait(chx_handle* h, int32_t* h_result);
+
 #define CHX_ROLLOUT_FUSED 0
 #define CHX_ROLLOUT_SPLIT 1
 int chx_policy_load(chx_handle* h, int32_t hidden, const uint16_t* h_w1, const float* h_b1,

@@ -26,7 +26,7 @@ EXPORTS = (
     "chx_obs_size", "chx_reset", "chx_step", "chx_step_n", "chx_rollout", "chx_rollout_host", "chx_step_host",
     "chx_autotune", "chx_set_launch", "chx_observe", "chx_get_state", "chx_set_state", "chx_stats", "chx_save",
     "chx_load", "chx_check", "chx_rollout_noalloc", "chx_policy_load", "chx_policy_act", "chx_policy_rollout",
-    "chx_get_battery", "chx_set_battery", "chx_get_due", "chx_set_due",
+    "chx_get_battery", "chx_set_battery", "chx_get_due", "chx_set_due", "chx_selftest_wait",
     "chx_srv_start", "chx_srv_stop", "chx_srv_admit", "chx_srv_evict", "chx_srv_submit", "chx_srv_wait",
     "chx_srv_test", "chx_srv_stats", "chx_srv_simulate",
 )
@@ -129,7 +129,7 @@ def load_library(path: str = LIB_PATH):
         "chx_policy_load": [vp, i32, vp, vp, vp, vp, vp, vp], "chx_policy_act": [vp, vp, vp, vp, vp],
         "chx_policy_rollout": [vp, i32, vp, vp, vp, vp, vp, i32, vp],
         "chx_get_battery": [vp, vp, vp], "chx_set_battery": [vp, vp, vp],
-        "chx_get_due": [vp, vp], "chx_set_due": [vp, vp],
+        "chx_get_due": [vp, vp], "chx_set_due": [vp, vp], "chx_selftest_wait": [vp, vp],
         "chx_srv_start": [vp, vp], "chx_srv_stop": [vp], "chx_srv_admit": [vp, vp, u64, vp],
         "chx_srv_evict": [vp, vp, i32], "chx_srv_submit": [vp, vp, vp], "chx_srv_wait": [vp, u64, i64, vp],
         "chx_srv_test": [vp, u64, vp, vp], "chx_srv_stats": [vp, vp], "chx_srv_simulate": [vp, vp, vp, vp],
@@ -286,6 +286,12 @@ class Batch:
 
     def check(self, stream=None):
         _check(_lib.chx_check(self.h, _stream_ptr(stream)))
+
+    def selftest_wait(self):
+        """chx_selftest_wait: (gave_up, cycles waited / 2^20)."""
+        res = np.zeros(2, np.int32)
+        _check(_lib.chx_selftest_wait(self.h, _np_ptr(res)))
+        return bool(res[0]), int(res[1])
 
     # ---- state ----------------------------------------------------------
     def get_state(self) -> dict:

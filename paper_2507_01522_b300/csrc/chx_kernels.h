@@ -111,5 +111,7 @@ cudaError_t launch_policy(const WMaps& wm, const PolicyArgs& a, int sm_count, cu
 bool rollout_fits(int n_out_pad);          // logits leave TMEM room for the env state
 int rollout_cluster();                     // CTAs sharing the weight stages (TMA multicast)
 cudaError_t launch_rollout(const WMaps& wm, const RolloutArgs& r, cudaStream_t st);
+// one bounded wait on a barrier nothing releases (d_out: 3 ints, device)
+cudaError_t wait_selftest(uint32_t* err, int* d_out, cudaStream_t st);
 
 }  // namespace chx

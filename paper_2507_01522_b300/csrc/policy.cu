@@ -1058,7 +1058,32 @@ static_assert(kPolicySmem <= 227 * 1024 - 256, "k_policy shared memory");
 static_assert(kRolloutSmem + (2 * kPolicyHidden + kPolicyMaxPorts * kPolicyGroup) * 4 <= 227 * 1024 - 256,
               "k_rollout shared memory");
 
+// Bounded-wait self-test: one thread runs the kernels' wait on an mbarrier
+// that nothing arrives on.  The wait must give up after kWaitCycles, raise
+// the error flag and return; out = {gave up, shared flag set, elapsed cycles
+// / 2^20}.
+__global__ void k_wait_selftest(uint32_t* err, int* out)
+{
+    __shared__ Sync S;
+    __shared__ uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    S.bad = 0;
+    mbar_fence_init();
+    const long long t0 = clock64();
+    const bool done = wait_sync<true>(&bar, 0, S, err);
+    out[0] = done ? 0 : 1;
+    out[1] = is_bad(S) ? 1 : 0;
+    out[2] = (int)((clock64() - t0) >> 20);
+}
+
 }  // namespace
+
+cudaError_t wait_selftest(uint32_t* err, int* d_out, cudaStream_t st)
+{
+    k_wait_selftest<<<1, 32, 0, st>>>(err, d_out);
+    return cudaGetLastError();
+}
 
 int policy_smem_bytes() { return kPolicySmem; }
 

@@ -221,6 +221,21 @@ extern "C" int chx_policy_act(chx_handle* h, const float* d_obs, int8_t* d_actio
     return enqueue_policy(h, d_obs, d_actions, d_logits, (cudaStream_t)stream);
 }
 
+extern "C" int chx_selftest_wait(chx_handle* h, int32_t* h_result)
+{
+    if (!h || !h_result) return fail(CHX_EINVAL, "null argument");
+    int* d = nullptr;
+    CUDA_TRY(cudaMalloc(&d, 3 * sizeof(int)));
+    int out[3] = {0, 0, 0};
+    cudaError_t e = chx::wait_selftest(h->b.err, d, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(out, d, sizeof out, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return chx::cuda_fail(e, "wait self-test");
+    h_result[0] = out[0] && out[1];
+    h_result[1] = out[2];
+    return CHX_OK;
+}
+
 extern "C" int chx_policy_rollout(chx_handle* h, int32_t n_steps, float* d_obs, int8_t* d_actions, float* d_reward,
                                   uint8_t* d_done, float* d_logits, int32_t form, void* stream)
 {

@@ -319,3 +319,35 @@ def test_policy_rollout_fullsize_sampled(cuda_lib):
     gs, os_ = b.get_state(), o.state()
     assert_events_equal(gs, os_, where="after rollout")
     assert_traj_close(gs, os_, charger_pmax(w), TRAJ_RTOL, where="after rollout")
+
+
+def test_bounded_wait_gives_up_and_context_survives(cuda_lib):
+    """The tensor-core kernels' bounded wait, run on a barrier nothing
+    releases: it gives up after its limit (2^31 cycles), raises the fault
+    flag (chx_check: CHX_ETIMEOUT, once) and the context keeps working (a
+    policy rollout afterwards equals one on a fresh batch)."""
+    import torch
+    from paper_2507_01522_b300.chargax import CHX_ETIMEOUT, Batch, ChxError
+    w = uniform_workload(200, 16)
+    b, ref = Batch(w), Batch(w)
+    gave_up, mcycles = b.selftest_wait()
+    assert gave_up and 2048 <= mcycles < 4096
+    with pytest.raises(ChxError) as ei:
+        b.check()
+    assert ei.value.code == CHX_ETIMEOUT
+    b.check()
+    N = int(w.stations.n_ports[0])
+    D, L = 8 + 6 * N, w.params.n_levels
+    pw = I.policy_weights(D, N, n_levels=L, seed=3)
+    outs = []
+    for bb in (b, ref):
+        bb.policy_load(pw.w1, pw.b1, pw.w2, pw.b2, pw.w3, pw.b3)
+        obs = torch.zeros(4, bb.E, D, device="cuda")
+        acts = torch.zeros(4, bb.E, N, dtype=torch.int8, device="cuda")
+        rew = torch.zeros(4, bb.E, device="cuda")
+        bb.policy_rollout(4, obs, acts, rew)
+        torch.cuda.synchronize()
+        bb.check()
+        outs.append((obs.cpu().numpy(), acts.cpu().numpy(), rew.cpu().numpy()))
+    for x, y in zip(*outs):
+        np.testing.assert_array_equal(x, y)
