@@ -53,7 +53,6 @@ constexpr int kThreads = (2 + kWorkerWarps) * 32;
 constexpr uint32_t kTmemCols = 512;
 constexpr int kPolStages = 4;              // weight ring of k_policy
 constexpr int kRollStages = 3;             // weight ring of k_rollout
-constexpr int kRollCluster = 2;            // k_rollout CTAs sharing each weight stage (TMA multicast)
 constexpr int kMaxStages = kPolStages;
 constexpr int kBarWorkers = 1;             // named barrier of the worker warps
 
@@ -101,11 +100,11 @@ __device__ __forceinline__ bool wait_sync(uint64_t* bar, uint32_t parity, Sync& 
     }
 }
 
-__device__ __forceinline__ void init_sync(Sync& S, int n_stages, int cluster)
+__device__ __forceinline__ void init_sync(Sync& S, int n_stages)
 {
     for (int s = 0; s < n_stages; ++s) {
         mbar_init(&S.full[s], 1);
-        mbar_init(&S.empty[s], cluster);       // one MMA commit from every CTA sharing the stage
+        mbar_init(&S.empty[s], 1);             // the MMA commit that has read the stage
     }
     mbar_init(&S.acc, 1);
     mbar_init(&S.fin, 1);
@@ -118,18 +117,16 @@ __device__ __forceinline__ void init_sync(Sync& S, int n_stages, int cluster)
 // ---- TMA producer: n_passes MLP passes worth of weight stages ------------
 // A stage is one 64-column K chunk of one layer part: 256 weight rows (the
 // MMA's N), or n3_last rows for the last part of layer 3.
-// CS > 1: the CTAs of a cluster of CS share every stage; each loads rows
-// [rank * rows / CS, +rows / CS) of it into all of them (the maps' boxes are
-// that tall), and a slot is refilled once every CTA's MMAs have read it.
+// Every CTA loads its own stages (the 0.44 MB of weights stay in L2); a slot
+// is refilled once the MMAs that read it have completed.
 __device__ __forceinline__ int part_rows(const PolicyArgs& a, int L, int p)
 {
     return (L == 2 && p == a.parts3 - 1) ? a.n3_last : kStageRows;
 }
 
-template <int NS, int CS>
+template <int NS>
 __device__ void produce(const WMaps* wm, const PolicyArgs& a, unsigned char* ring, Sync& S, int n_passes)
 {
-    const uint32_t rank = CS > 1 ? cluster_rank() : 0u;
     uint32_t s = 0;
     int last[NS];
 #pragma unroll
@@ -140,19 +137,13 @@ __device__ void produce(const WMaps* wm, const PolicyArgs& a, unsigned char* rin
             const int chunks = L == 0 ? a.ch1 : 4;
             for (int p = 0; p < parts; ++p) {
                 const int rows = part_rows(a, L, p);
-                const int piece = rows / CS;
                 const CUtensorMap* map = rows == kStageRows ? &wm->main : &wm->tail;
                 for (int k = 0; k < chunks; ++k, ++s) {
                     const uint32_t slot = s % NS;
                     if (s >= (uint32_t)NS) wait_sync<false>(&S.empty[slot], ((s / NS) - 1) & 1, S, a.err);
                     if (is_bad(S)) continue;
                     mbar_arrive_expect_tx(&S.full[slot], (uint32_t)rows * 128u);
-                    unsigned char* dst = ring + slot * kStageBytes + rank * piece * 128;
-                    const int y = L * 256 + p * kStageRows + (int)rank * piece;
-                    if (CS == 1)
-                        tma_load_2d(dst, map, k * 64, y, &S.full[slot]);
-                    else
-                        tma_load_2d_multicast(dst, map, k * 64, y, &S.full[slot], (uint16_t)((1u << CS) - 1u));
+                    tma_load_2d(ring + slot * kStageBytes, map, k * 64, L * 256 + p * kStageRows, &S.full[slot]);
 #pragma unroll
                     for (int j = 0; j < NS; ++j)
                         if (j == (int)slot) last[j] = (int)s;
@@ -166,7 +157,7 @@ __device__ void produce(const WMaps* wm, const PolicyArgs& a, unsigned char* rin
 }
 
 // ---- MMA issuer ------------------------------------------------------------
-template <int NS, int CS>
+template <int NS>
 __device__ void issue(const PolicyArgs& a, unsigned char* A, unsigned char* ring, Sync& S, uint32_t tmem,
                       int n_passes)
 {
@@ -193,8 +184,7 @@ __device__ void issue(const PolicyArgs& a, unsigned char* A, unsigned char* ring
                     for (int j = 0; j < nks; ++j)          // onto the bias the workers placed in TMEM
                         mma_bf16(tmem + (uint32_t)(p * kStageRows), sdesc_sw128(A + k * kChunkBytes + j * 32),
                                  sdesc_sw128(bst + j * 32), id, true);
-                    if (CS == 1) mma_commit(&S.empty[slot]);
-                    else mma_commit_multicast(&S.empty[slot], (uint16_t)((1u << CS) - 1u));
+                    mma_commit(&S.empty[slot]);
                 }
             }
             if (!is_bad(S)) mma_commit(&S.acc);
@@ -371,7 +361,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_policy(const __grid_constant__ 
     __shared__ __align__(16) float bias_s[2 * kPolicyHidden + kPolicyMaxPorts * kPolicyGroup];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int j = threadIdx.x; j < 2 * kPolicyHidden + a.n_out_pad; j += blockDim.x) bias_s[j] = a.bias[j];
-    if (threadIdx.x == 0) init_sync(S, kPolStages, 1);
+    if (threadIdx.x == 0) init_sync(S, kPolStages);
     if (warp == 1) tmem_alloc(&S.tmem, kTmemCols);
     fence_before();
     __syncthreads();
@@ -380,10 +370,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_policy(const __grid_constant__ 
     const int n_tiles = (a.E + kM - 1) / kM;
     const int my_tiles = blockIdx.x < n_tiles ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     if (warp == 0) {
-        if (lane == 0) produce<kPolStages, 1>(&wm, a, ring, S, my_tiles);
+        if (lane == 0) produce<kPolStages>(&wm, a, ring, S, my_tiles);
         __syncwarp();
     } else if (warp == 1) {
-        if (lane == 0) issue<kPolStages, 1>(a, A, ring, S, tmem, my_tiles);
+        if (lane == 0) issue<kPolStages>(a, A, ring, S, tmem, my_tiles);
         __syncwarp();
     } else {
         const int ew = warp - 2, q = warp & 3, h = ew >> 2;
@@ -989,18 +979,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_rollout(const __grid_constant__
     const PolicyArgs& a = R.pol;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int j = threadIdx.x; j < 2 * kPolicyHidden + a.n_out_pad; j += blockDim.x) bias_s[j] = a.bias[j];
-    if (threadIdx.x == 0) init_sync(S, kRollStages, kRollCluster);
+    if (threadIdx.x == 0) init_sync(S, kRollStages);
     if (warp == 1) tmem_alloc(&S.tmem, kTmemCols);
     fence_before();
-    cluster_sync();                        // barriers of every CTA initialised before any multicast
+    __syncthreads();
     fence_after();
     const uint32_t tmem = S.tmem;
     const int tile = blockIdx.x;
     if (warp == 0) {
-        if (lane == 0) produce<kRollStages, kRollCluster>(&wm, a, ring, S, R.T);
+        if (lane == 0) produce<kRollStages>(&wm, a, ring, S, R.T);
         __syncwarp();
     } else if (warp == 1) {
-        if (lane == 0) issue<kRollStages, kRollCluster>(a, A, ring, S, tmem, R.T);
+        if (lane == 0) issue<kRollStages>(a, A, ring, S, tmem, R.T);
         __syncwarp();
     } else {
         const int ew = warp - 2, q = warp & 3, h = ew >> 2;
@@ -1045,7 +1035,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rollout(const __grid_constant__
         owner_store(o, R, tl);
     }
     fence_before();
-    cluster_sync();                        // no peer still commits to or multicasts into this CTA
+    __syncthreads();
     if (warp == 1) {
         fence_after();
         tmem_dealloc(tmem, kTmemCols);
@@ -1111,26 +1101,16 @@ cudaError_t launch_policy(const WMaps& wm, const PolicyArgs& a, int sm_count, cu
 
 bool rollout_fits(int n_out_pad) { return n_out_pad <= kColSoc; }
 int policy_stage_rows() { return kStageRows; }
-int rollout_cluster() { return kRollCluster; }
 
 cudaError_t launch_rollout(const WMaps& wm, const RolloutArgs& r, cudaStream_t st)
 {
     const int n_tiles = (r.pol.E + kM - 1) / kM;
     if (n_tiles <= 0 || r.T <= 0) return cudaSuccess;
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3((unsigned)((n_tiles + kRollCluster - 1) / kRollCluster * kRollCluster));
-    cfg.blockDim = dim3(kThreads);
-    cfg.dynamicSmemBytes = kRolloutSmem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = kRollCluster;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    if (r.pol.n_levels == 11) return cudaLaunchKernelEx(&cfg, k_rollout<11>, wm, r);
-    return cudaLaunchKernelEx(&cfg, k_rollout<0>, wm, r);
+    if (r.pol.n_levels == 11)
+        k_rollout<11><<<n_tiles, kThreads, kRolloutSmem, st>>>(wm, r);
+    else
+        k_rollout<0><<<n_tiles, kThreads, kRolloutSmem, st>>>(wm, r);
+    return cudaGetLastError();
 }
 
 }  // namespace chx

@@ -184,9 +184,7 @@ extern "C" int chx_policy_load(chx_handle* h, int32_t hidden, const uint16_t* h_
         const cuuint32_t estr[2] = {1, 1};
         const int sr = chx::policy_stage_rows();
         const int parts3 = (n_out_pad + sr - 1) / sr, n3_last = n_out_pad - sr * (parts3 - 1);
-        const int cs = chx::rollout_cluster();
-        struct { CUtensorMap* m; int box_rows; } want[4] = {
-            {&P.maps.main, sr}, {&P.maps.tail, n3_last}, {&P.maps_roll.main, sr / cs}, {&P.maps_roll.tail, n3_last / cs}};
+        struct { CUtensorMap* m; int box_rows; } want[2] = {{&P.maps.main, sr}, {&P.maps.tail, n3_last}};
         for (auto& w : want) {
             const cuuint32_t box[2] = {64, (cuuint32_t)w.box_rows};
             const CUresult r = enc(w.m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, P.d_w, dims, strides, box, estr,
@@ -260,7 +258,7 @@ extern "C" int chx_policy_rollout(chx_handle* h, int32_t n_steps, float* d_obs, 
         r.port_base = h->cls_port_base[cls];
         r.env_base = h->cls_env_base[cls];
         r.C = 8 << cls;
-        CUDA_TRY(chx::launch_rollout(P.maps_roll, r, (cudaStream_t)stream));
+        CUDA_TRY(chx::launch_rollout(P.maps, r, (cudaStream_t)stream));
         return CHX_OK;
     }
     if (!d_obs) return fail(CHX_EINVAL, "the split rollout needs the observation buffer");
