@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--no-policy", action="store_true", help="skip the on-device policy rollout leg")
     ap.add_argument("--no-v2g", action="store_true", help="skip the vehicle-to-grid leg")
     ap.add_argument("--no-variants", action="store_true", help="skip the charge-sensitive and deeper-tree legs")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the uniform-station legs (16 x 16, and 4096 x 16 in two groups)")
     ap.add_argument("--policy-steps", type=int, default=128, help="rollout buffer length of the policy leg")
     ap.add_argument("--policy-only", action="store_true",
                     help="time only the policy rollout leg and print its JSON object (profiling aid)")
@@ -175,15 +177,11 @@ def peaks():
         return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
 
 
-# Algorithmic work per unit: the bytes one plain step must read and write per
-# charger and per station, the ALU operations of one charger-step (Philox
-# share, level map, clip, rescale and sums, charge and departure, arrival
-# rank) and of one station-step (arrival draw, Poisson search, reward, car
-# profiles), and the state bytes a fused launch loads and stores.
+# Algorithmic bytes per unit (the roofline of both forms): what one plain
+# step must read and write per charger and per station, and the state bytes
+# a fused launch loads and stores once for all its steps.
 PLAIN_BYTES_PER_PORT_STEP = 34.0     # read trem,meta,soc,erem,cap,rbar (21) + write soc,erem,p,trem (13)
 PLAIN_BYTES_PER_ENV_STEP = 97.0      # station fields read + written, reward + done
-FUSED_OPS_PER_PORT_STEP = 48.0       # algorithmic ALU ops of one charger-step
-FUSED_OPS_PER_ENV_STEP = 130.0       # arrival Philox + Poisson + reward of one station-step
 FUSED_STATE_BYTES_PER_PORT = 54.0    # per launch: state in (21) + out (21) + statics (12)
 FUSED_STATE_BYTES_PER_ENV = 80.0
 LANES_PER_SM = 128
@@ -202,10 +200,10 @@ def policy_bytes_per_env_step(D, N):
     return 4.0 * D + N + 4.0 + 1.0
 
 
-def _recorded(name, sources, **want):
-    """A per-launch DRAM byte count from a committed ncu record (profiles/
-    <name>), if the kernel sources and the launch parameters are those the
-    counters were taken on; else None."""
+def _record(name, sources, **want):
+    """The fields of a committed ncu record (profiles/<name>: per-launch DRAM
+    bytes, thread instructions, issue utilisation), if the kernel sources and
+    the launch parameters are those the counters were taken on; else None."""
     import hashlib
     try:
         rec = dict(l.split() for l in open(os.path.join(ROOT, "profiles", name))
@@ -215,15 +213,34 @@ def _recorded(name, sources, **want):
             return None
         if any(int(rec[k]) != int(v) for k, v in want.items()):
             return None
-        return int(rec["dram_bytes_per_launch"])
+        return rec
     except Exception:
         return None
 
 
+def _recorded(name, sources, **want):
+    rec = _record(name, sources, **want)
+    return None if rec is None else int(rec["dram_bytes_per_launch"])
+
+
+FUSED_SOURCES = ("step_fused.cu", "chx_device.cuh", "chx_kernels.h")
+
+
 def recorded_traffic(n_envs, K, W):
     """DRAM bytes per fused step launch (k_step_fused record)."""
-    return _recorded("k_step_fused_traffic.txt", ("step_fused.cu", "chx_device.cuh"), n_envs=n_envs,
-                     steps_per_launch=K, warps_per_block=W)
+    return _recorded("k_step_fused_traffic.txt", FUSED_SOURCES, n_envs=n_envs, steps_per_launch=K,
+                     warps_per_block=W)
+
+
+def recorded_issue(n_envs, K, W):
+    """Thread instructions per launch and issue-slot utilisation of the fused
+    kernel (k_step_fused record), or None."""
+    rec = _record("k_step_fused_traffic.txt", FUSED_SOURCES, n_envs=n_envs, steps_per_launch=K,
+                  warps_per_block=W)
+    try:
+        return float(rec["thread_inst_per_launch"]), float(rec["issue_active_pct"])
+    except Exception:
+        return None
 
 
 ROLLOUT_SOURCES = ("policy.cu", "chx_tc.cuh", "chx_device.cuh", "chx_kernels.h")
@@ -349,6 +366,40 @@ def run_reference(args):
 # the B300 arm
 # ----------------------------------------------------------------------------
 
+def fused_roofline(P, E, K, W, launch_ms, pk, pk_kind, dev):
+    """Roofline of one fused launch (K steps of every station): the plain
+    form's algorithmic bytes for the same steps over the fused launch time,
+    against the measured HBM bandwidth (the fused form keeps the state on
+    chip, so the fraction can exceed 1), with the SM issue utilisation and
+    the lane-instruction rate from the committed ncu record beside it."""
+    import torch
+    hbm = pk["hbm_gbs"]
+    plain_bytes = (PLAIN_BYTES_PER_PORT_STEP * P + PLAIN_BYTES_PER_ENV_STEP * E) * K
+    fused_bytes = FUSED_STATE_BYTES_PER_PORT * P + FUSED_STATE_BYTES_PER_ENV * E + 5.0 * E * K
+    gbs = plain_bytes / (launch_ms * 1e-3) / 1e9
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_mhz = pk.get("sm_max_mhz", 2032.0)
+    lane_peak = sm_count * LANES_PER_SM * sm_mhz * 1e6
+    rec = recorded_issue(E, K, W)
+    alu = None
+    if rec is not None:
+        ti, issue = rec
+        alu = {"achieved": ti / (launch_ms * 1e-3) / 1e12, "peak": lane_peak / 1e12, "unit": "T lane-instructions/s",
+               "frac": ti / (launch_ms * 1e-3) / lane_peak, "thread_inst_per_launch": ti,
+               "source": "smsp__thread_inst_executed.sum of the committed ncu record (profiles/k_step_fused_traffic.txt)",
+               "peak_source": f"{sm_count} SMs x {LANES_PER_SM} lanes x {sm_mhz:.0f} MHz ({pk_kind} max clock)"}
+    return {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+            "traffic": recorded_traffic(E, K, W), "kernel": "k_step_fused",
+            "basis": "plain-form algorithmic bytes (34 B per charger-step + 97 B per station-step) of the "
+                     "launch's K steps over the fused launch's CUDA-event time, of %s HBM bandwidth" % pk_kind,
+            "algorithmic_bytes_per_launch": plain_bytes, "launch_ms": launch_ms, "steps_per_launch": K,
+            "warps_per_block": W,
+            "sm_issue_active": None if rec is None else rec[1] / 100.0,
+            "fused_state_bytes_per_launch": fused_bytes,
+            "fused_state_gbs": fused_bytes / (launch_ms * 1e-3) / 1e9,
+            "alu": alu}
+
+
 def run_b300(args):
     import numpy as np
     import torch
@@ -403,28 +454,8 @@ def run_b300(args):
     ms_step = 1e3 * total_s / args.steps
     value = whole_job_rate(E * T * args.steps, sum(ms) / 1e3, ws)
 
-    # roofline of the fused kernel (ALU-bound: state stays in registers)
     pk, pk_kind = peaks()
-    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    sm_mhz = pk.get("sm_max_mhz", 2032.0)
-    alu_peak = sm_count * LANES_PER_SM * sm_mhz * 1e6 / 1e12       # Tops/s
-    launch_ms = ms_step / launches_per_step
-    ops_launch = (FUSED_OPS_PER_PORT_STEP * P + FUSED_OPS_PER_ENV_STEP * E) * K
-    achieved = ops_launch / (launch_ms * 1e-3) / 1e12
-    fused_bytes_launch = FUSED_STATE_BYTES_PER_PORT * P + FUSED_STATE_BYTES_PER_ENV * E + 5.0 * E * K
-    roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s", "frac": achieved / alu_peak,
-                "traffic": recorded_traffic(E, K, W), "algorithmic_bytes_per_launch": fused_bytes_launch, "kernel": "k_step_fused", "launch_ms": launch_ms, "steps_per_launch": K,
-                "warps_per_block": W, "ops_per_launch": ops_launch,
-                "peak_source": f"{sm_count} SMs x {LANES_PER_SM} lanes x {sm_mhz:.0f} MHz ({pk_kind} max clock)",
-                "hbm_gbs_algorithmic": fused_bytes_launch / (launch_ms * 1e-3) / 1e9,
-                "hbm_frac_algorithmic": fused_bytes_launch / (launch_ms * 1e-3) / 1e9 / pk["hbm_gbs"],
-                # the plain form's bytes for the same steps over the fused time:
-                # the HBM roofline the fused form leaves behind (can exceed 1)
-                "plain_equivalent_gbs": (PLAIN_BYTES_PER_PORT_STEP * P + PLAIN_BYTES_PER_ENV_STEP * E) * K
-                                        / (launch_ms * 1e-3) / 1e9,
-                "plain_equivalent_frac": (PLAIN_BYTES_PER_PORT_STEP * P + PLAIN_BYTES_PER_ENV_STEP * E) * K
-                                         / (launch_ms * 1e-3) / 1e9 / pk["hbm_gbs"]}
-
+    roofline = fused_roofline(P, E, K, W, ms_step / launches_per_step, pk, pk_kind, dev)
     line = {"metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -465,28 +496,49 @@ def run_b300(args):
         line["gpu_launches"] += T * args.steps
         del bp
 
-    # end to end through the C interface with host buffers
+    # end to end through the C interface with host buffers: every step's
+    # levels in (host actions, step-major), rewards, done flags and the final
+    # observation out, copies inside the timed region
     if not args.no_e2e:
+        n_act = b.P
+        ha = torch.empty(T * n_act, dtype=torch.int8, pin_memory=True).numpy()
+        ha[:] = I.random_actions(np.random.default_rng(rank), n_act, n_levels=w.params.n_levels,
+                                 steps=T).T.reshape(-1)
         hr = torch.empty(E * T, dtype=torch.float32, pin_memory=True).numpy()
         hd = torch.empty(E * T, dtype=torch.uint8, pin_memory=True).numpy()
         ho = torch.empty(b.obs_size, dtype=torch.float32, pin_memory=True).numpy()
-        b.rollout_host(T, hr, hd, ho)
-        torch.cuda.synchronize()
-        barrier(ws)
-        et = []
-        for _ in range(args.steps):
-            flush.zero_()
+
+        def e2e_time(fn):
+            fn()
             torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            b.rollout_host(T, hr, hd, ho)
-            et.append(time.perf_counter() - t0)
-        etot = max_over_ranks(sum(et), ws)
+            barrier(ws)
+            et = []
+            for _ in range(args.steps):
+                flush.zero_()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                fn()
+                et.append(time.perf_counter() - t0)
+            return max_over_ranks(sum(et), ws)
+
+        etot = e2e_time(lambda: b.rollout_host_actions(T, ha, hr, hd, ho))
         line["e2e"] = {"value": E * T * args.steps * ws / etot, "unit": "env-steps/s",
-                       "h2d_bytes_per_step": 0, "d2h_bytes_per_step": int(hr.nbytes + hd.nbytes + ho.nbytes),
+                       "h2d_bytes_per_step": int(ha.nbytes),
+                       "d2h_bytes_per_step": int(hr.nbytes + hd.nbytes + ho.nbytes),
                        "ms_per_step": 1e3 * etot / args.steps,
-                       "api": "chx_rollout_host (pinned host outputs: reward, done step-major, observation; "
-                              "4 launches of 5:4:2:1 shares, each one's outputs copied while the next computes)"}
+                       "api": "chx_rollout_host_actions (pinned host levels in, step-major [T][chargers] int8; "
+                              "rewards, done flags step-major and the final observation out; 12 launches, each "
+                              "one's levels copied in while the previous computes and its outputs copied out "
+                              "while the next computes)"}
+        line["gpu_launches"] += min(12, T) * args.steps
+        ptot = e2e_time(lambda: b.rollout_host(T, hr, hd, ho))
+        line["e2e_philox_actions"] = {
+            "value": E * T * args.steps * ws / ptot, "unit": "env-steps/s", "h2d_bytes_per_step": 0,
+            "d2h_bytes_per_step": int(hr.nbytes + hd.nbytes + ho.nbytes), "ms_per_step": 1e3 * ptot / args.steps,
+            "api": "chx_rollout_host (levels drawn in the kernel; outputs as above; 4 launches of 5:4:2:1 "
+                   "shares, each one's outputs copied while the next computes)"}
         line["gpu_launches"] += min(4, T) * args.steps
+        del ha, hr, hd, ho
 
     line["clocks"] = ck.summary()
     if not args.no_v2g:
@@ -503,10 +555,22 @@ def run_b300(args):
         pol = run_policy_rollout(args, rank, ws, dev, timed, pk)
         line["policy_rollout"] = pol
         line["gpu_launches"] += pol["gpu_launches"]
+    if not args.no_configs:
+        line["configs"] = {}
+        for wc in (I.small_uniform(seed=0), I.fixed_station(seed=0)):
+            leg = run_config_leg(args, rank, ws, timed, wc, pk, dev)
+            line["configs"][wc.name] = leg
+            line["gpu_launches"] += leg["gpu_launches"]
     if not args.no_serve:
         del b
         torch.cuda.empty_cache()
-        line["serving"] = run_serving(args, rank)
+        # one server on rank 0 (its host threads would contend with other
+        # ranks' servers on the shared host cores); the other ranks wait
+        if rank == 0:
+            line["serving"] = run_serving(args, rank)
+            if ws > 1:
+                line["serving"]["ranks"] = "rank 0 only (one GPU's server; the other ranks wait)"
+        barrier(ws)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         n = calibrate_sample(w, 12.0, T)
         line["cpu_baseline"] = cpu_baseline(w, n, T)
@@ -514,6 +578,74 @@ def run_b300(args):
     if rank == 0:
         print(json.dumps(line), flush=True)
     barrier(ws)
+
+
+def run_config_leg(args, rank, ws, timed, wc, pk, dev):
+    """A uniform-station configuration (16 x 16 chargers, or 4096 x 16 in two
+    groups of 8 at 80 kW), one 288-step episode per timed step with in-kernel
+    random levels, plain form (one launch per step, graph replay) against the
+    fused form (CUDA graph of fused launches, autotuned shape); both against
+    the plain form's algorithmic HBM bytes."""
+    import torch
+    from paper_2507_01522_b300 import chargax
+    T = wc.params.ep_len
+    hbm = pk["hbm_gbs"]
+    bf = chargax.Batch(wc, seed=rank_seed(rank))
+    E, P = bf.E, bf.P
+    plain_bytes_step = PLAIN_BYTES_PER_PORT_STEP * P + PLAIN_BYTES_PER_ENV_STEP * E
+    if args.shape:
+        K, W = (int(x) for x in args.shape.split(","))
+        bf.set_launch(K, W)
+    else:
+        K, W = bf.autotune(T)
+    reward = torch.empty(E, T, device=dev)
+    done = torch.empty(E, T, dtype=torch.uint8, device=dev)
+    fn = lambda: bf.rollout(T, reward=reward, done=done)
+    for _ in range(args.warmup):
+        fn()
+    torch.cuda.synchronize()
+    barrier(ws)
+    ms = timed(fn, args.steps)
+    bf.check()
+    ftot = max_over_ranks(sum(ms) / 1e3, ws)
+    fms = 1e3 * ftot / args.steps
+    n_launch = math.ceil(T / K)
+    fgbs = plain_bytes_step * T / (fms * 1e-3) / 1e9
+    out = {"n_envs": E, "n_chargers": P, "horizon_steps": T, "actions": "Philox uniform 11 levels in-kernel",
+           "fused": {"value": E * T * args.steps * ws / ftot, "unit": "env-steps/s", "ms_per_step": fms,
+                     "steps_per_launch": K, "warps_per_block": W, "launches_per_step": n_launch,
+                     "charger_steps_per_s": P * T * args.steps * ws / ftot,
+                     "roofline": {"bound": "hbm", "achieved": fgbs, "peak": hbm, "unit": "GB/s", "frac": fgbs / hbm,
+                                  "kernel": "k_step_fused", "traffic": None,
+                                  "basis": "plain-form algorithmic bytes over the fused time"}}}
+    del bf
+    bp = chargax.Batch(wc, seed=rank_seed(rank))
+    rp = torch.empty(T, E, device=dev)
+    dp = torch.empty(T, E, dtype=torch.uint8, device=dev)
+    bp.step(reward=rp[0], done=dp[0])
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for k in range(T):
+            bp.step(reward=rp[k], done=dp[k])
+    for _ in range(args.warmup):
+        g.replay()
+    torch.cuda.synchronize()
+    barrier(ws)
+    pms = timed(g.replay, args.steps)
+    bp.check()
+    ptot = max_over_ranks(sum(pms) / 1e3, ws)
+    pms_step = 1e3 * ptot / args.steps
+    pgbs = plain_bytes_step * T / (pms_step * 1e-3) / 1e9
+    out["plain"] = {"value": E * T * args.steps * ws / ptot, "unit": "env-steps/s", "ms_per_step": pms_step,
+                    "launches_per_step": T, "charger_steps_per_s": P * T * args.steps * ws / ptot,
+                    "roofline": {"bound": "hbm", "achieved": pgbs, "peak": hbm, "unit": "GB/s", "frac": pgbs / hbm,
+                                 "kernel": "k_step_plain", "traffic": None,
+                                 "basis": "34 B per charger-step + 97 B per station-step"}}
+    out["fused_over_plain"] = out["fused"]["value"] / out["plain"]["value"]
+    out["gpu_launches"] = (n_launch + T) * args.steps
+    del bp, g
+    return out
 
 
 def run_variant(args, rank, ws, timed, wv, charge_only_value, dev):

@@ -7,7 +7,9 @@
  *   - station layout: a tree whose root is the grid connection, inner nodes
  *     are groups (splitters/cables) with a power limit I_H and efficiency
  *     eta_H, and leaves are the chargers (Sec. "EV Station Layout");
- *     this library supports depth-2 trees: root -> groups -> chargers;
+ *     root -> groups -> chargers by default, with up to three levels of
+ *     upper nodes between the root and the groups (Fig. c trees, see
+ *     chx_stations.h_n_upper): trees of depth up to five;
  *   - transition, Appendix A.2, in order: apply actions (per-charger clip),
  *     architecture constraint Eq. (ArchConst) by proportional rescaling,
  *     charge stationed cars with the SoC taper of Appendix A.1, time advance,
@@ -250,6 +252,22 @@ int chx_rollout(chx_handle* h, int32_t n_steps, float* d_reward, uint8_t* d_done
 int chx_rollout_host(chx_handle* h, int32_t n_steps, float* h_reward, uint8_t* h_done, float* h_obs,
                      void* stream);
 
+/* chx_rollout_host with the levels of every step given by the host: the Gym
+ * loop of an actor that chose its actions on the host (Appendix "Practical
+ * Considerations": one action per charger, plus the battery's in V2G mode).
+ * h_actions is step-major, h_actions[k * n_act + q] for action slot q of
+ * step k, n_act = total chargers (+ n_envs in V2G mode), each station's
+ * slots in batch order (its chargers, then its battery); levels outside
+ * 0..n_levels-1 are clamped and flagged (chx_check).  Outputs as
+ * chx_rollout_host.  The steps run in up to 12 fused launches of near-equal
+ * size: the levels of launch c are copied in while launch c - 1 computes and
+ * its rewards and done flags are copied out while launch c + 1 computes
+ * (pinned host memory gives full copy bandwidth); the observation follows
+ * the last launch.  The call returns when everything is on the host.
+ * h_actions NULL: CHX_EINVAL. */
+int chx_rollout_host_actions(chx_handle* h, int32_t n_steps, const int8_t* h_actions, float* h_reward,
+                             uint8_t* h_done, float* h_obs, void* stream);
+
 /* One plain step with HOST buffers: actions are copied in (h_actions NULL =
  * Philox levels), reward/done/observation copied out; returns when done. */
 int chx_step_host(chx_handle* h, const int8_t* h_actions, float* h_reward, uint8_t* h_done,
@@ -269,7 +287,12 @@ int chx_step_host(chx_handle* h, const int8_t* h_actions, float* h_reward, uint8
  * (ceil(n_steps / steps per launch)); more returns CHX_EINVAL.
  *   - The first call on a device looks up the array's device address (with
  *     that device current) and caches it; make that first call before any
- *     stream capture.
+ *     stream capture.  The cached address is valid until the device's
+ *     context is reset (cudaDeviceReset); do not call the library after that.
+ *   - The handle's device must be the current device (else CHX_EINVAL).
+ *   - The 128-charger class runs beside the smaller classes on the handle's
+ *     side stream, as in chx_rollout (that stream and its two events are
+ *     created with the handle, not by this call).
  *   - All calls share the array.  Each call clears the counters it uses on
  *     `stream` first; calls that overlap on the GPU (other streams, other
  *     handles on the same device) race on the counters and must be ordered

@@ -13,6 +13,7 @@ namespace chx {
 using Buffers = std::vector<void*>;
 
 constexpr int kHostChunks = 4;            // launches of a host-call rollout (copies overlap the next)
+constexpr int kActChunks = 12;            // launches of a host-actions rollout (copies in and out overlap)
 
 struct GraphKey {
     int n_steps = 0;
@@ -52,8 +53,7 @@ struct PolicyState {
     int ch1 = 0, ks1_last = 0, parts3 = 0, n3_last = 0;
     uint16_t* d_w = nullptr;               // [rows][256] BF16 bits
     float* d_bias = nullptr;               // [512 + n_out_pad]
-    WMaps maps{};                          // k_policy (over-aligned; the handle is allocated with new)
-    WMaps maps_roll{};                     // k_rollout (boxes split across the cluster)
+    WMaps maps{};                          // k_policy and k_rollout (over-aligned; the handle is allocated with new)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     PolicyGraphKey key{};
@@ -91,6 +91,8 @@ struct chx_handle {
     cudaStream_t copy_stream = nullptr;    // device-to-host copies of the host-call rollout
     chx::FusedSide side;                   // the 128-charger class's launch beside the others
     cudaEvent_t chunk_done[chx::kHostChunks] = {};
+    cudaStream_t in_stream = nullptr;      // host-to-device copies of the host-actions rollout
+    cudaEvent_t act_in[chx::kActChunks] = {}, act_done[chx::kActChunks] = {};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     chx::GraphKey graph_key{};
@@ -109,7 +111,8 @@ void build_poisson_cdf(const float* lam, size_t n_rows_steps, std::vector<float>
 int build_handle(const chx_stations* st, const chx_env_params* prm, const chx_exo* exo, uint64_t seed,
                  int min_pad_envs_per_class, chx_handle** out);
 int enqueue_fused(chx_handle* h, int k_steps, const int8_t* actions, long long lda, float* reward, uint8_t* done,
-                  long long ld_out, float* obs, int warps, cudaStream_t st, long long ld_step = 1);
+                  long long ld_out, float* obs, int warps, cudaStream_t st, long long ld_step = 1,
+                  long long lda_step = 1);
 void free_graph(chx_handle* h);
 void free_policy(chx_handle* h);
 }  // namespace chx

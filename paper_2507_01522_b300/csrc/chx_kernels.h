@@ -13,8 +13,9 @@ namespace chx {
 // sched_tile_base[i] .. sched_tile_base[i+1]-1.
 struct FusedIO {
     int k_steps;
-    const int8_t* actions;
+    const int8_t* actions;                 // given level of action slot q at step k: actions[q * lda + k * lda_step]
     long long lda;
+    long long lda_step;
     float* reward;
     uint8_t* done;
     long long ld_out;                      // env e, step k at e * ld_out + k * ld_step
@@ -69,9 +70,9 @@ constexpr int kPolicyGroup = 12;           // most action levels the sampler han
 // TMA with 128-byte swizzle.  Rows 0-255 = W1 (columns >= obs_dim zero),
 // 256-511 = W2, 512 + c * L + j = level j of charger c (W3; rows up to
 // n_out_pad zero).  bias = b1 | b2 | b3 in the same order.  Two maps over
-// it: boxes of 64 columns x (policy_stage_rows() / CS) rows, and x (n3_last
-// / CS) rows for the last part of layer 3; CS = 1 for k_policy and
-// rollout_cluster() for the fused rollout.
+// it, used by k_policy and k_rollout alike: boxes of 64 columns x
+// policy_stage_rows() rows, and 64 x n3_last rows for the last part of
+// layer 3.
 struct WMaps {
     CUtensorMap main, tail;
 };
@@ -109,7 +110,6 @@ cudaError_t policy_prepare();              // once per process, before capture
 int policy_stage_rows();                   // weight rows (MMA N) of a full layer part
 cudaError_t launch_policy(const WMaps& wm, const PolicyArgs& a, int sm_count, cudaStream_t st);
 bool rollout_fits(int n_out_pad);          // logits leave TMEM room for the env state
-int rollout_cluster();                     // CTAs sharing the weight stages (TMA multicast)
 cudaError_t launch_rollout(const WMaps& wm, const RolloutArgs& r, cudaStream_t st);
 // one bounded wait on a barrier nothing releases (d_out: 3 ints, device)
 cudaError_t wait_selftest(uint32_t* err, int* d_out, cudaStream_t st);

@@ -558,6 +558,11 @@ int build_handle(const chx_stations* st, const chx_env_params* prm, const chx_ex
     CUDA_TRY(cudaEventCreateWithFlags(&h->side.fork, cudaEventDisableTiming));
     CUDA_TRY(cudaEventCreateWithFlags(&h->side.join, cudaEventDisableTiming));
     for (auto& ev : h->chunk_done) CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    CUDA_TRY(cudaStreamCreateWithFlags(&h->in_stream, cudaStreamNonBlocking));
+    for (int c = 0; c < kActChunks; ++c) {
+        CUDA_TRY(cudaEventCreateWithFlags(&h->act_in[c], cudaEventDisableTiming));
+        CUDA_TRY(cudaEventCreateWithFlags(&h->act_done[c], cudaEventDisableTiming));
+    }
 
     launch_reset(b, h->dp, h->d_user_to_slot, nullptr, E, E, seed, 0);
     CUDA_TRY(cudaGetLastError());
@@ -599,6 +604,11 @@ extern "C" int chx_destroy(chx_handle* h)
     if (h->side.join) cudaEventDestroy(h->side.join);
     for (auto ev : h->chunk_done)
         if (ev) cudaEventDestroy(ev);
+    if (h->in_stream) cudaStreamDestroy(h->in_stream);
+    for (int c = 0; c < chx::kActChunks; ++c) {
+        if (h->act_in[c]) cudaEventDestroy(h->act_in[c]);
+        if (h->act_done[c]) cudaEventDestroy(h->act_done[c]);
+    }
     delete h;
     return CHX_OK;
 }
@@ -658,12 +668,13 @@ extern "C" int chx_step(chx_handle* h, const int8_t* d_actions, int64_t lda, flo
 namespace chx {
 
 int enqueue_fused(chx_handle* h, int k_steps, const int8_t* actions, long long lda, float* reward, uint8_t* done,
-                  long long ld_out, float* obs, int warps, cudaStream_t st, long long ld_step)
+                  long long ld_out, float* obs, int warps, cudaStream_t st, long long ld_step, long long lda_step)
 {
     FusedIO io = h->sched;
     io.k_steps = k_steps;
     io.actions = actions;
     io.lda = lda;
+    io.lda_step = lda_step;
     io.reward = reward;
     io.done = done;
     io.ld_out = ld_out;
@@ -817,6 +828,58 @@ extern "C" int chx_rollout_host(chx_handle* h, int32_t n_steps, float* h_reward,
         if (rc) return rc;
         CUDA_TRY(cudaEventRecord(h->chunk_done[c], st));
         CUDA_TRY(cudaStreamWaitEvent(cs, h->chunk_done[c], 0));
+        if (h_reward) CUDA_TRY(cudaMemcpyAsync(h_reward + off, dr + off, n * sizeof(float), cudaMemcpyDeviceToHost, cs));
+        if (h_done) CUDA_TRY(cudaMemcpyAsync(h_done + off, dd + off, n, cudaMemcpyDeviceToHost, cs));
+        if (last && h_obs) CUDA_TRY(cudaMemcpyAsync(h_obs, dob, nobs * sizeof(float), cudaMemcpyDeviceToHost, cs));
+    }
+    CUDA_TRY(cudaStreamSynchronize(cs));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return CHX_OK;
+}
+
+// Host-actions rollout: the given levels of every step come from the host.
+// The steps run in up to kActChunks fused launches of near-equal size on the
+// caller's stream.  The input stream copies chunk c's levels (contiguous,
+// step-major) to device staging while chunk c - 1 computes; the copy stream
+// brings chunk c's rewards and done flags back while chunk c + 1 computes;
+// the observation follows the last chunk.
+extern "C" int chx_rollout_host_actions(chx_handle* h, int32_t n_steps, const int8_t* h_actions, float* h_reward,
+                                        uint8_t* h_done, float* h_obs, void* stream)
+{
+    if (!h) return fail(CHX_EINVAL, "null handle");
+    if (!h_actions) return fail(CHX_EINVAL, "h_actions is null (use chx_rollout_host for Philox actions)");
+    if (n_steps < 1) return fail(CHX_EINVAL, "n_steps must be >= 1");
+    const size_t E = (size_t)h->E, ne = E * (size_t)n_steps;
+    const size_t nact = (size_t)h->P + (h->dp.v2g ? E : 0);
+    const size_t nobs = (size_t)h->dp.obs_env * E + (size_t)h->dp.obs_port * (size_t)h->P;
+    int8_t* da = (int8_t*)staging(h, 6, nact * (size_t)n_steps);
+    float* dr = h_reward ? (float*)staging(h, 0, ne * sizeof(float)) : nullptr;
+    uint8_t* dd = h_done ? (uint8_t*)staging(h, 1, ne) : nullptr;
+    float* dob = h_obs ? (float*)staging(h, 2, nobs * sizeof(float)) : nullptr;
+    if (!da || (h_reward && !dr) || (h_done && !dd) || (h_obs && !dob))
+        return fail(CHX_ENOMEM, "staging allocation failed");
+    cudaStream_t st = (cudaStream_t)stream, cs = h->copy_stream, is = h->in_stream;
+    const int n_chunks = n_steps < kActChunks ? n_steps : kActChunks;
+    // the staging of the previous call may still be read by its last launch
+    CUDA_TRY(cudaEventRecord(h->act_done[0], st));
+    CUDA_TRY(cudaStreamWaitEvent(is, h->act_done[0], 0));
+    for (int c = 0; c < n_chunks; ++c) {
+        const int k0 = (int)((long long)n_steps * c / n_chunks), k1 = (int)((long long)n_steps * (c + 1) / n_chunks);
+        CUDA_TRY(cudaMemcpyAsync(da + (size_t)k0 * nact, h_actions + (size_t)k0 * nact, (size_t)(k1 - k0) * nact,
+                                 cudaMemcpyHostToDevice, is));
+        CUDA_TRY(cudaEventRecord(h->act_in[c], is));
+    }
+    for (int c = 0; c < n_chunks; ++c) {
+        const int k0 = (int)((long long)n_steps * c / n_chunks), k1 = (int)((long long)n_steps * (c + 1) / n_chunks);
+        const bool last = c == n_chunks - 1;
+        const size_t off = (size_t)k0 * E, n = (size_t)(k1 - k0) * E;
+        CUDA_TRY(cudaStreamWaitEvent(st, h->act_in[c], 0));
+        int rc = enqueue_fused(h, k1 - k0, da + (size_t)k0 * nact, 1, dr ? dr + off : nullptr,
+                               dd ? dd + off : nullptr, 1, last ? dob : nullptr, h->warps_per_block, st,
+                               (long long)E, (long long)nact);
+        if (rc) return rc;
+        CUDA_TRY(cudaEventRecord(h->act_done[c], st));
+        CUDA_TRY(cudaStreamWaitEvent(cs, h->act_done[c], 0));
         if (h_reward) CUDA_TRY(cudaMemcpyAsync(h_reward + off, dr + off, n * sizeof(float), cudaMemcpyDeviceToHost, cs));
         if (h_done) CUDA_TRY(cudaMemcpyAsync(h_done + off, dd + off, n, cudaMemcpyDeviceToHost, cs));
         if (last && h_obs) CUDA_TRY(cudaMemcpyAsync(h_obs, dob, nobs * sizeof(float), cudaMemcpyDeviceToHost, cs));

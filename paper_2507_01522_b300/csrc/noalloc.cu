@@ -29,7 +29,10 @@ int* g_counters_addr[kMaxDevices] = {};
 
 // Device address of g_noalloc_counters on `device`, looked up once per device
 // with that device current.  In host code the array's name is only a host-side
-// stand-in, so kernels must be given this address, never the name.
+// stand-in, so kernels must be given this address, never the name.  The cached
+// address belongs to the device's primary context: it is valid until that
+// context is destroyed (cudaDeviceReset), after which this library must not
+// be called again in the process.
 int counters_on(int device, int** out)
 {
     if (device < 0 || device >= kMaxDevices) return chx::fail(CHX_EINVAL, "device ordinal out of range");
@@ -63,6 +66,12 @@ extern "C" int chx_rollout_noalloc(chx_handle* h, int32_t n_steps, float* d_rewa
                                          std::to_string(launches) + " launches of " + std::to_string(K) +
                                          " steps; the scratch holds at most " +
                                          std::to_string(CHX_NOALLOC_MAX_LAUNCHES));
+    int cur = -1;
+    cudaError_t ce = cudaGetDevice(&cur);
+    if (ce != cudaSuccess) return chx::cuda_fail(ce, "cudaGetDevice");
+    if (cur != h->device)
+        return chx::fail(CHX_EINVAL, "chx_rollout_noalloc: the current device (" + std::to_string(cur) +
+                                         ") is not the handle's device (" + std::to_string(h->device) + ")");
     int* counters = nullptr;
     int rc = counters_on(h->device, &counters);
     if (rc) return rc;
@@ -80,13 +89,16 @@ extern "C" int chx_rollout_noalloc(chx_handle* h, int32_t n_steps, float* d_rewa
         io.k_steps = k;
         io.actions = nullptr;
         io.lda = 0;
+        io.lda_step = 0;
         io.reward = d_reward ? d_reward + k0 : nullptr;
         io.done = d_done ? d_done + k0 : nullptr;
         io.ld_out = n_steps;
         io.ld_step = 1;
         io.obs = (i == launches - 1) ? d_obs : nullptr;
         io.counter = counters + i * chx::kFusedCounters;
-        chx::launch_step_fused(h->b, h->dp, io, threads, h->sm_count, st);
+        // the 128-charger class beside the others, on the handle's own side
+        // stream and events (created with the handle, so nothing is allocated)
+        chx::launch_step_fused(h->b, h->dp, io, threads, h->sm_count, st, &h->side);
         e = cudaGetLastError();
         if (e != cudaSuccess) return chx::cuda_fail(e, "k_step_fused launch");
     }

@@ -335,6 +335,7 @@ int launch_tick(chx_srv* s, int ti, const std::vector<Request*>& rq)
     // never mixes them), so io.actions applies to every entry
     io.actions = act_used > 0 ? d_act : nullptr;
     io.lda = 1;
+    io.lda_step = 1;
     io.reward = reinterpret_cast<float*>(t.d_down);
     io.done = t.d_down + done_at;
     io.ld_out = 1;

@@ -3,9 +3,10 @@
 // A persistent kernel.  Each warp repeatedly takes a tile from a global work
 // counter (tiles of the largest stations first), loads the tile's state into
 // registers, runs K steps without touching HBM except for the per-step
-// reward/done outputs, and stores the state back.  A tile is 32 charger slots
-// per lane-column: 32/C stations of size class C <= 32 (one charger per
-// lane), or one station of C = 64/128 (2/4 consecutive chargers per lane).
+// reward/done outputs, and stores the state back.  A lane holds PPL
+// consecutive chargers of one station (PPL = 2 for the classes of 8..64
+// chargers, 4 for 128), so a tile is 32 * PPL charger slots: 8, 4, 2 or 1
+// stations of 8, 16, 32 or 64 chargers, or one station of 128.
 //
 // Reductions over chargers (Eq. ArchConst and the reward sums) are warp
 // shuffles: a segmented inclusive scan gives each group node's power at its
@@ -385,7 +386,7 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
                 const uint32_t half = (g & 1u) ? (word >> 16) : (word & 0xFFFFu);
                 lvl = (int)((half * (uint32_t)p.n_levels) >> 16);
             } else if (trem[q] > 0) {
-                lvl = io.actions[((long long)act_base + port) * io.lda + k];
+                lvl = io.actions[((long long)act_base + port) * io.lda + (long long)k * io.lda_step];
                 if (lvl < 0 || lvl >= p.n_levels) {
                     atomicOr(b.err, kErrActionRange);
                     lvl = min(max(lvl, 0), p.n_levels - 1);
@@ -409,7 +410,7 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
                     bwords = philox4x32_10(make_uint4(uidu, g >> 3, (uint32_t)n_st, kPurposeAction), k0, k1);
                 lvl = random_level(bwords, g, p.n_levels);
             } else {
-                lvl = io.actions[((long long)act_base + n_st) * io.lda + k];
+                lvl = io.actions[((long long)act_base + n_st) * io.lda + (long long)k * io.lda_step];
                 if (lvl < 0 || lvl >= p.n_levels) {
                     atomicOr(b.err, kErrActionRange);
                     lvl = min(max(lvl, 0), p.n_levels - 1);

@@ -48,14 +48,19 @@ def test_gpu_arm_json_line():
     line carries the roofline, end-to-end, clock and launch-count keys."""
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--steps", "1", "--warmup", "1",
                           "--n-envs", "4096", "--no-serve", "--no-policy", "--no-variants", "--no-v2g",
-                          "--no-cpu-baseline"], cwd=ROOT, capture_output=True, text=True, timeout=900)
+                          "--no-cpu-baseline", "--no-configs"], cwd=ROOT, capture_output=True, text=True,
+                         timeout=900)
     assert out.returncode == 0, out.stderr[-2000:]
     d = json.loads([l for l in out.stdout.splitlines() if l.startswith("{")][-1])
     assert d["value"] > 0 and d["n_gpus"] == 1 and d["higher_is_better"] is True
     rf = d["roofline"]
-    assert rf["bound"] in ("alu", "hbm", "tensor") and rf["achieved"] > 0 and rf["peak"] > 0
+    assert rf["bound"] == "hbm" and rf["unit"] == "GB/s" and rf["achieved"] > 0 and rf["peak"] > 0
     assert abs(rf["frac"] - rf["achieved"] / rf["peak"]) < 1e-9
+    # achieved = the plain form's algorithmic bytes of the launch's steps over the launch time
+    assert abs(rf["achieved"] - rf["algorithmic_bytes_per_launch"] / (rf["launch_ms"] * 1e-3) / 1e9) < 1e-6 * rf["achieved"]
     e2e = d["e2e"]
-    assert e2e["value"] > 0 and e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] > 0
+    assert e2e["value"] > 0 and e2e["d2h_bytes_per_step"] > 0
+    assert e2e["h2d_bytes_per_step"] == d["config"]["n_chargers"] * d["config"]["horizon_steps"]
+    assert d["e2e_philox_actions"]["h2d_bytes_per_step"] == 0
     assert d["gpu_launches"] > 0 and d["plain"]["value"] > 0
     assert {"sm_mhz", "sm_max_mhz", "reasons"} <= set(d["clocks"])

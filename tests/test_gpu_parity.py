@@ -320,6 +320,57 @@ def test_host_api_matches_device(cuda_lib, n, pinned):
     np.testing.assert_array_equal(hr1, r1.cpu().numpy())
 
 
+@pytest.mark.parametrize("n,v2g", [(30, False), (5, False), (1, False), (26, True)])
+def test_host_actions_rollout(cuda_lib, n, v2g):
+    """The host-actions rollout (step-major host levels in, launches whose
+    copies in and out overlap their neighbours) equals the device fused form
+    given the same levels (charger-major, one launch), bit for bit, on the
+    class-edge stations (128-charger class beside the others), and matches the
+    oracle step by step; two calls in a row continue the episode."""
+    import torch
+    from paper_2507_01522_b300.chargax import Batch
+    w = odd_sizes()
+    if v2g:
+        w = I.v2g_variant(w)
+    b1, b2, o = Batch(w), Batch(w), Oracle(w)
+    E, P = b1.E, b1.P
+    n_act = P + (E if v2g else 0)
+    rng = np.random.default_rng(17 + n)
+    hr = torch.zeros(n * E, dtype=torch.float32, pin_memory=True).numpy()
+    hd = torch.zeros(n * E, dtype=torch.uint8, pin_memory=True).numpy()
+    ho = torch.zeros(b1.obs_size, dtype=torch.float32, pin_memory=True).numpy()
+    for call in range(2):
+        acts = rng.integers(0, w.params.n_levels, size=(n, n_act), dtype=np.int8)     # step-major
+        ha = torch.from_numpy(acts.reshape(-1)).pin_memory().numpy()
+        b1.rollout_host_actions(n, ha, hr, hd, ho)
+        r = torch.zeros(E, n, device="cuda")
+        d = torch.zeros(E, n, dtype=torch.uint8, device="cuda")
+        ob = torch.zeros(b2.obs_size, device="cuda")
+        b2.step_n(n, actions=torch.from_numpy(np.ascontiguousarray(acts.T)).cuda(), reward=r, done=d, obs=ob)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(hr.reshape(n, E), r.cpu().numpy().T, err_msg=f"reward, call {call}")
+        np.testing.assert_array_equal(hd.reshape(n, E), d.cpu().numpy().T, err_msg=f"done, call {call}")
+        np.testing.assert_array_equal(ho, ob.cpu().numpy(), err_msg=f"observation, call {call}")
+        for k in range(n):
+            ro, do = o.step(acts[k])
+            info = o.info()
+            assert_reward_close(hr[k * E:(k + 1) * E], ro, reward_scale(info, w.params) + station_step_scale(w, info),
+                                TRAJ_RTOL, where=f"call {call} step {k}")
+            np.testing.assert_array_equal(hd[k * E:(k + 1) * E], do)
+        gs, os_ = b1.get_state(), o.state()
+        assert_events_equal(gs, os_, where=f"after call {call}")
+        assert_traj_close(gs, os_, charger_pmax(w), TRAJ_RTOL, where=f"after call {call}")
+    b1.check()
+
+
+def test_host_actions_rollout_rejects_null_actions(cuda_lib):
+    from paper_2507_01522_b300.chargax import CHX_EINVAL, Batch, ChxError
+    b = Batch(I.small_uniform())
+    with pytest.raises(ChxError) as ei:
+        b.rollout_host_actions(4, None, np.zeros(4 * b.E, np.float32))
+    assert ei.value.code == CHX_EINVAL
+
+
 def test_action_out_of_range_is_flagged(cuda_lib):
     from paper_2507_01522_b300.chargax import CHX_EFAULT, ChxError
     w, b, o, torch = make("fixed203")

@@ -3,8 +3,10 @@ memory during the call (for example code running under a memory pool it does
 not own): it must give the same results as chx_rollout, call after call,
 while keeping its scratch in a static device array.
 
-Kept in its own file so that it is collected last; it passes alone in a fresh
-process and after the other tests.
+Kept in a file of its own whose name sorts last, so pytest collects it after
+every other test: a run that stops at the first failure (-x) has then run all
+the other tests before this one.  It does not depend on that order; it passes
+alone in a fresh process and after the other tests.
 """
 import numpy as np
 import pytest
@@ -52,6 +54,31 @@ def test_rollout_noalloc_matches_rollout_twice(cuda_lib, form):
             np.testing.assert_allclose(sb[k], sa[k], rtol=STEP_RTOL, atol=1e-6)
         np.testing.assert_array_equal(a.due(), b.due())
         np.testing.assert_allclose(b.battery()["soc"], a.battery()["soc"], rtol=STEP_RTOL, atol=1e-6)
+
+
+def test_rollout_noalloc_allocates_nothing(cuda_lib):
+    """After a first call (which looks up the static array's address), further
+    calls with a new step count and new output pointers must leave the device's
+    free memory and torch's allocator untouched."""
+    import torch
+    from paper_2507_01522_b300 import inputs as I
+    from paper_2507_01522_b300.chargax import Batch
+    b = Batch(I.heterogeneous(n_envs=1000))
+    b.set_launch(steps_per_launch=24, warps_per_block=4)
+    outs = [(torch.zeros(b.E, n, device="cuda"), torch.zeros(b.E, n, dtype=torch.uint8, device="cuda"),
+             torch.zeros(b.obs_size, device="cuda")) for n in (30, 77, 130)]
+    b.rollout_noalloc(30, reward=outs[0][0], done=outs[0][1], obs=outs[0][2])
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    stats0 = torch.cuda.memory_stats()
+    for n, (r, d, o) in zip((77, 130), outs[1:]):
+        b.rollout_noalloc(n, reward=r, done=d, obs=o)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    stats1 = torch.cuda.memory_stats()
+    assert free1 == free0, f"device free memory changed by {free0 - free1} bytes"
+    for k in ("allocation.all.allocated", "segment.all.allocated", "reserved_bytes.all.current"):
+        assert stats1.get(k, 0) == stats0.get(k, 0), k
 
 
 def test_rollout_noalloc_rejects_too_many_launches(cuda_lib):
