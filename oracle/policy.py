@@ -33,8 +33,10 @@ import numpy as np
 # u = 2^-24 per addition; 2^-23 leaves room for a tensor core that truncates
 # instead of rounding.
 ACC_UNIT = 2.0 ** -23
-# BF16 rounding: |bf16(x) - x| <= 2^-9 |x| (8 significant bits, nearest).
-BF16_HALF_STEP = 2.0 ** -9
+# BF16 rounding: |bf16(x) - x| <= 2^-8 |x|.  With 8 significant bits the
+# spacing of BF16 numbers in [2^e, 2^(e+1)) is 2^(e-7); half of it is
+# 2^(e-8) <= 2^-8 |x|, reached for x just above 2^e (1 + 2^-8 rounds to 1).
+BF16_HALF_STEP = 2.0 ** -8
 
 
 def bf16(x) -> np.ndarray:
@@ -69,7 +71,10 @@ def mlp_bound(obs, w):
     If the inputs differ by da, z differs by at most sum_k |W_jk| da_k more.
     ReLU does not increase a difference, and BF16 rounding of two values
     that differ by dz gives results that differ by at most
-    dz + 2^-9 (|x| + |x'|) <= dz + 2^-8 (|x| + dz)."""
+    dz + h (|x| + |x'|) <= dz + 2 h (|x| + dz), h = BF16_HALF_STEP.
+    Both parts are reached: an FP32 sum that truncates every partial sum
+    loses almost K u of the largest partial sum, and two values on either
+    side of a BF16 tie just above a power of two round one step apart."""
     W1, b1, W2, b2, W3, b3 = (np.asarray(a, np.float64) for a in (w.w1, w.b1, w.w2, w.b2, w.w3, w.b3))
     x = bf16(obs)
     A1, A2, A3 = np.abs(W1), np.abs(W2), np.abs(W3)

@@ -2,7 +2,9 @@
 rounding against a library conversion and hand values, the MLP against
 closed forms (bias only, two-hot layers), the sampler against its
 closed form for equal logits, a dominant logit and the categorical
-frequencies, and the error bound against an independent FP32 evaluation."""
+frequencies, and the error bound against an independent FP32 evaluation
+(sound) and against hand networks on which an adversarial FP32 evaluation
+reaches it (tight)."""
 import numpy as np
 import pytest
 import torch
@@ -146,7 +148,9 @@ def test_bound_covers_fp32_evaluation(reverse):
     bound = OP.mlp_bound(obs, w)
     got = _fp32_forward(obs, w, reverse)
     assert np.all(np.abs(got - ref) <= bound)
-    assert np.all(bound < 0.05 * (np.abs(ref).max() + 1))       # the bound is not vacuous
+    # not vacuous (a worst case over every rounding position: about a tenth
+    # of the logits' range for this 64-unit network)
+    assert np.all(bound < 0.15 * (np.abs(ref).max() + 1))
 
 
 def test_policy_uniforms_are_the_policy_philox_words():
@@ -162,3 +166,81 @@ def test_policy_uniforms_are_the_policy_philox_words():
         for q in range(n):
             words = philox([e, int(st["gstep"][e]), q // 4, 4], [int(st["key0"][e]), int(st["key1"][e])])
             assert u[e, q] == (int(words[q % 4]) >> 8) * 2.0 ** -24
+
+
+# ----------------------------------------------------------------------------
+# tightness of the bound: hand networks on which a legitimate FP32 evaluation
+# reaches the worst case the bound allows
+# ----------------------------------------------------------------------------
+
+def _rtz32(x: float) -> float:
+    """Round a double to FP32 toward zero (a tensor core that truncates)."""
+    f = np.float32(x)
+    if abs(float(f)) > abs(x):
+        f = np.nextafter(f, np.float32(0.0))
+    return float(f)
+
+
+def _truncating_forward(obs, w):
+    """FP32 evaluation in which every partial sum is truncated (round toward
+    zero), starting from the bias as the kernel does, products exact (BF16
+    x BF16 fits FP32), BF16 rounding to nearest even at the same points as
+    the oracle.  The bound must cover it (its FP32 unit is 2^-23, room for
+    truncation)."""
+    def layer(a, W, b):
+        out = np.empty((a.shape[0], W.shape[0]))
+        for r in range(a.shape[0]):
+            for j in range(W.shape[0]):
+                acc = float(np.float32(b[j]))
+                for k in range(W.shape[1]):
+                    acc = _rtz32(acc + float(W[j, k]) * float(a[r, k]))
+                out[r, j] = acc
+        return out
+    x = OP.bf16(obs)
+    h1 = OP.bf16(OP.relu(layer(x, w.w1, w.b1)))
+    h2 = OP.bf16(OP.relu(layer(h1, w.w2, w.b2)))
+    return layer(h2, w.w3, w.b3)
+
+
+def _net(w1, b1, w2, b2, w3, b3):
+    f = lambda a: np.asarray(a, np.float32)
+    return I.PolicyWeights(f(w1), f(b1), f(w2), f(b2), f(w3), f(b3))
+
+
+def test_bound_is_reached_by_bf16_ties():
+    """One unit per layer.  Layer 1 sums 1 + 2^-8 (a BF16 tie just above 1)
+    and 62 inputs of 2^-30: exactly the sum lies above the tie and rounds up
+    to 1 + 2^-7, while the truncating sum drops the small inputs, sits on the
+    tie and rounds to 1.  Layer 2 adds 2^-8: 1 + 3 2^-8 is again a tie, which
+    rounds up to 1 + 2^-6, and 1 + 2^-8 rounds down to 1.  The logits then
+    differ by 2^-6, one step of each rounding; the bound may exceed that only
+    by its accumulation terms (a few parts in 1e3)."""
+    D = 64
+    obs = np.array([[1.0, 2.0 ** -8] + [2.0 ** -30] * (D - 2)])
+    w = _net(np.ones((1, D)), [0.0], [[1.0]], [2.0 ** -8], [[1.0]], [0.0])
+    ref, h1, h2 = OP.mlp_forward(obs, w)
+    assert h1[0, 0] == 1 + 2.0 ** -7 and h2[0, 0] == 1 + 2.0 ** -6
+    got = _truncating_forward(obs, w)
+    attained = abs(got[0, 0] - ref[0, 0])
+    assert attained == 2.0 ** -6
+    bound = OP.mlp_bound(obs, w)[0, 0]
+    assert attained <= bound <= 1.05 * attained, (attained, bound)
+
+
+def test_bound_is_reached_by_truncated_accumulation():
+    """256 hidden units of 15/128 (biases through identity layers) and a
+    logit that starts from a bias of 2^20: each product 15/128 is below the
+    FP32 spacing at 2^20 (2^-3), so a truncating sum keeps 2^20 while the
+    exact logit is 2^20 + 30.  The bound's accumulation term, 256 2^-23
+    (2^20 + 30) = 32.0, must cover the 30 and may exceed it only by that
+    term's slack and the small rounding terms of the hidden layers."""
+    H, D = 256, 8
+    obs = np.zeros((1, D))
+    w = _net(np.zeros((H, D)), np.full(H, 15.0 / 128.0), np.eye(H), np.zeros(H), np.ones((1, H)), [2.0 ** 20])
+    ref, h1, h2 = OP.mlp_forward(obs, w)
+    assert np.all(h2 == 15.0 / 128.0) and ref[0, 0] == 2.0 ** 20 + 30.0
+    got = _truncating_forward(obs, w)
+    attained = abs(got[0, 0] - ref[0, 0])
+    assert attained == 30.0
+    bound = OP.mlp_bound(obs, w)[0, 0]
+    assert attained <= bound <= 1.25 * attained, (attained, bound)
