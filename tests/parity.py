@@ -17,7 +17,31 @@ Tolerances (all stated here, used by every parity test):
   against 1, remaining demand and capacity against the car's capacity, power
   against the charger's maximum, and a step's reward against the largest
   profit the station could make in one step;
-* episode returns (``RETURN_RTOL`` = 1e-4) relative to max(|return|, 1 EUR).
+* episode returns (``RETURN_RTOL`` = 1e-4) relative to max(|return|, 1 EUR);
+* a step's reward along independent trajectories (``traj_reward_scale``):
+  TRAJ_RTOL relative to the sum of its terms' magnitudes, plus what the
+  drift of the FP32 state can change.  The charger power is a minimum of
+  terms of which three depend on the state: the taper r_bar (1 - SoC) /
+  (1 - tau) (V2G: SoC r_bar / (1 - tau) when discharging), the SoC cap
+  (1 - SoC) C / dt and the demand cap e_rem / dt.  A SoC that differs by
+  dS moves them by at most S dS, S = max(r_bar / (1 - tau), C / dt), and
+  e_rem by de moves the demand cap by de / dt; node rescaling only
+  redistributes or scales such differences down.  Near SoC = 1 this is not
+  small against the step's own energy: FP32 resolves SoC to 6e-8, while
+  1 - SoC of a car deep in the taper is 1e-4 or less, so a tail car's
+  power carries a relative error of a few percent (an FP32-stored-state
+  model of the oracle shows the same).  The allowance per station is
+  sum_i dt (p_sell + |p_buy| / eta_min + alpha_sat + alpha_con / eta_node)
+  dP_i + alpha_sat de_i over the occupied chargers whose power can depend
+  on SoC or e_rem (in or near the taper or a cap; V2G: all occupied), with
+  dP_i = S_i dS_i + de_i / dt (+ the drift of the last applied power in the
+  increment form), where dS_i and de_i are the state differences measured
+  at the start and at the end of the launch (the larger) plus
+  ``DRIFT_PER_STEP`` per step of the launch for cars that came and went
+  inside it (each step rounds SoC once in the addition and once in the
+  increment; the taper's feedback on SoC is contracting, factor |1 -
+  r_bar dt / ((1 - tau) C)| <= 1).  Chargers in the bulk phase, away from
+  every cap, get no allowance.
 """
 from __future__ import annotations
 
@@ -71,14 +95,65 @@ def _report(k, where, d, tol, g, o):
                              f"oracle {o[i]!r} (tol {tol[i]:.3g})")
 
 
-def station_step_scale(w, info):
-    """Largest one-step profit magnitude of each station: selling and buying
-    all energy its chargers could deliver in one step at full power."""
+DRIFT_PER_STEP = 3 * 2.0 ** -24
+
+
+def state_drift(gs: dict | None, os_: dict | None, n: int | None = None, gb=None, ob=None) -> dict:
+    """|GPU - oracle| per charger (soc, erem, p) and per station (battery
+    SoC, V2G) for two states of the same chargers; zeros (n chargers) when
+    the states are the same by construction (gs is None)."""
+    if gs is None:
+        z = np.zeros(n)
+        return dict(soc=z, erem=z, p=z, bsoc=None)
+    d = {k: np.abs(gs[k].astype(np.float64) - os_[k]) for k in ("soc", "erem", "p")}
+    d["bsoc"] = None if gb is None else np.abs(gb["soc"].astype(np.float64) - ob["soc"])
+    return d
+
+
+def traj_reward_scale(w, info, o_before: dict, d0: dict, d1: dict, kk: int, b_before=None):
+    """Reward scale of one step along independent trajectories (see the
+    module docstring): reward_scale plus the drift allowance / TRAJ_RTOL, so
+    that assert_reward_close(..., TRAJ_RTOL) allows TRAJ_RTOL x the terms'
+    magnitudes plus the allowance.  o_before: the oracle's state before the
+    step; d0, d1: state_drift at the launch's start and end; kk: steps of
+    the launch; b_before: the oracle's battery before the step (V2G)."""
     st, p = w.stations, w.params
     pmax = np.asarray(p.p_max_kw, np.float64)[st.port_type]
-    e_max = np.add.reduceat(pmax, st.port_off[:-1]) * p.dt_h
-    eta_min = min(p.eta_port)
-    return (p.p_sell + np.abs(info["price"]) / eta_min) * e_max
+    eta = np.asarray(p.eta_port, np.float64)[st.port_type]
+    grow = kk * DRIFT_PER_STEP
+    dS = np.maximum(d0["soc"], d1["soc"]) + grow
+    cap = np.asarray(o_before["cap"], np.float64)
+    de = np.maximum(d0["erem"], d1["erem"]) + grow * np.maximum(cap, 1.0)
+    soc, erem = np.asarray(o_before["soc"], np.float64), np.asarray(o_before["erem"], np.float64)
+    rbar = np.asarray(o_before["rbar"], np.float64)
+    occ = np.asarray(o_before["trem"]) > 0
+    if p.v2g:
+        sens = occ
+    else:
+        sens = occ & ((soc >= p.tau - dS - 1e-6) | ((1.0 - soc) * cap / p.dt_h <= pmax * (1 + 1e-6))
+                      | (erem / p.dt_h <= pmax * (1 + 1e-6)))
+    S = np.maximum(rbar / (1.0 - p.tau), cap / p.dt_h)
+    dP = np.where(sens, S * dS + de / p.dt_h, 0.0)
+    if p.action_delta:
+        dP = dP + np.where(occ, np.maximum(d0["p"], d1["p"]) + grow * pmax, 0.0)
+    dP = np.minimum(dP, 2.0 * pmax)
+    etas = [np.asarray(st.group_eta, np.float64), np.asarray(st.grid_eta, np.float64)]
+    if getattr(st, "upper_eta", None) is not None and len(st.upper_eta):
+        etas.append(np.asarray(st.upper_eta, np.float64))
+    eta_node = min(float(e.min()) for e in etas if len(e))
+    price = np.abs(np.asarray(info["price"], np.float64))
+    starts = st.port_off[:-1]
+    coef_env = p.p_sell + price / float(eta.min()) + p.alpha_sat + p.alpha_con / eta_node
+    if p.v2g:
+        coef_env = coef_env + price * p.sell_grid_ratio + p.alpha_degrad
+    per_port = p.dt_h * dP
+    allow = coef_env * np.add.reduceat(per_port, starts) + p.alpha_sat * np.add.reduceat(np.where(occ, de, 0.0), starts)
+    if p.v2g and b_before is not None:
+        db = (np.zeros(len(starts)) if d1.get("bsoc") is None else np.maximum(
+            d1["bsoc"], 0.0 if d0.get("bsoc") is None else d0["bsoc"])) + grow
+        Sb = max(p.batt_rate_kw / (1.0 - p.batt_tau), p.batt_cap_kwh / p.dt_h)
+        allow = allow + coef_env * p.dt_h * np.minimum(Sb * db, 2.0 * p.batt_rate_kw)
+    return reward_scale(info, p) + allow / TRAJ_RTOL
 
 
 def charger_pmax(w):

@@ -25,10 +25,10 @@ from oracle import Oracle
 from paper_2507_01522_b300 import inputs as I
 
 from parity import (RETURN_RTOL, STEP_RTOL, TRAJ_RTOL, assert_events_equal, assert_floats_close,
-                    assert_reward_close, assert_traj_close, charger_pmax, reward_scale, station_step_scale,
-                    to_f32_state, widen)
+                    assert_reward_close, assert_traj_close, charger_pmax, reward_scale, state_drift,
+                    to_f32_state, traj_reward_scale, widen)
 from test_gpu_parity import odd_sizes, stressed
-from test_gpu_v2g import V2G, v2g_scale
+from test_gpu_v2g import V2G, v2g_drift, v2g_scale
 
 pytestmark = pytest.mark.gpu
 
@@ -82,6 +82,8 @@ def compare_cs(w, b, o, torch, steps, mode="plain", k=1, actions=None, max_resyn
     reward = torch.zeros(E, k, device="cuda")
     done = torch.zeros(E, k, dtype=torch.uint8, device="cuda")
     cs_seen = 0
+    drift = lambda: v2g_drift(b.get_state(), o.state(), b.battery(), o.battery())
+    d0 = drift()
     for s0 in range(0, steps, k):
         kk = min(k, steps - s0)
         if mode == "plain":
@@ -93,17 +95,21 @@ def compare_cs(w, b, o, torch, steps, mode="plain", k=1, actions=None, max_resyn
         torch.cuda.synchronize()
         rg, dg = reward.cpu().numpy(), done.cpu().numpy()
         near = np.zeros(E, bool)
+        recs = []
         for j in range(kk):
+            before, bb = o.state(), o.battery()
             ro, do = o.step(None if actions is None else actions[:, s0 + j])
             near |= o.info_cs()["margin"] < TIE_MARGIN
-            ok = ~near
-            info = o.info()
-            sc = (v2g_scale(w, info, o.info_v2g()) if w.params.v2g else
-                  reward_scale(info, w.params) + station_step_scale(w, info))
-            sc = sc + w.params.alpha_sat1 * (np.abs(o.info_cs()["csat1"]) + 1.0)
-            assert_reward_close(rg[ok, j], ro[ok], sc[ok], TRAJ_RTOL, where=f"step {s0 + j}")
-            np.testing.assert_array_equal(dg[ok, j], do[ok], err_msg=f"done step {s0 + j}")
+            recs.append((ro, o.info(), o.info_v2g(), o.info_cs()["csat1"], before, bb, near.copy()))
+            np.testing.assert_array_equal(dg[~near, j], do[~near], err_msg=f"done step {s0 + j}")
         gs, os_ = b.get_state(), o.state()
+        d1 = v2g_drift(gs, os_, b.battery(), o.battery())
+        for j, (ro, info, vi, csat1, before, bb, nr) in enumerate(recs):
+            ok = ~nr
+            sc = (v2g_scale(w, info, vi, before, d0, d1, kk, bb) if w.params.v2g else
+                  traj_reward_scale(w, info, before, d0, d1, kk))
+            sc = sc + w.params.alpha_sat1 * (np.abs(csat1) + 1.0)
+            assert_reward_close(rg[ok, j], ro[ok], sc[ok], TRAJ_RTOL, where=f"step {s0 + j}")
         ok = ~near
         keep_p = ok[port_env]
         g, r = restrict(gs, ok, keep_p), restrict(os_, ok, keep_p)
@@ -117,6 +123,7 @@ def compare_cs(w, b, o, torch, steps, mode="plain", k=1, actions=None, max_resyn
             if differ.any():
                 resync(o, b, w, np.flatnonzero(differ))
                 clean &= ~differ
+        d0 = drift() if near.any() else d1
     assert cs_seen > 0, "no charge-sensitive car was compared"
     assert (~clean).mean() <= max_resync_frac, f"{(~clean).sum()} of {E} stations re-synchronised"
     stg, sto = b.stats(), o.stats()
@@ -260,46 +267,75 @@ def test_cs_rejections(cuda_lib):
 
 def test_cs_fullsize_sampled(cuda_lib):
     """The benchmark's charge-sensitive leg: the 65536-station mixed batch
-    with half the users charge-sensitive, in the benchmark's launch shape
-    (one 288-step launch, 8 warps per block); 400 sampled stations
-    re-simulated by the oracle (a station drops out from a near-tie on, see
-    the module docstring; here about half of them stay in)."""
+    with half the users charge-sensitive, the benchmark's fused kernel (8
+    warps per block) in launches of 12 steps over 287 steps; 400 sampled
+    stations re-simulated by the oracle.  The oracle decides first: a
+    station whose launch held a near-tie is not compared in that launch, and
+    the oracle takes over the kernel's state of that station before the next
+    launch (its floats may legitimately differ by more than the trajectory
+    tolerance even where the events agree).  At every step at least 90 % of
+    the sample is compared."""
     import torch
     from paper_2507_01522_b300.chargax import Batch
     w = I.heterogeneous(n_envs=65536)
     w.params = I.EnvParams(**{**w.params.__dict__, **CS})
     b = Batch(w)
-    b.set_launch(288, 8)
-    n = 287                                             # one launch; the state is mid-episode at the end
-    r = torch.zeros(b.E, n, device="cuda")
+    b.set_launch(12, 8)
+    n, K = 287, 12
+    r = torch.zeros(b.E, K, device="cuda")
     rng = np.random.default_rng(4)
     ids = np.sort(rng.choice(w.stations.n_envs, 400, replace=False)).astype(np.int64)
     sub = I.Workload(w.name, w.params, w.stations.subset(ids), w.exo, w.seed)
     o = Oracle(sub, streams=ids)
-    b.rollout(n, reward=r)
-    torch.cuda.synchronize()
-    rg = r.cpu().numpy()[ids]
-    live = np.ones(len(ids), bool)
-    for j in range(n):
-        ro, _ = o.step(None)
-        live &= o.info_cs()["margin"] >= TIE_MARGIN
-        info = o.info()
-        sc = reward_scale(info, sub.params) + station_step_scale(sub, info) + sub.params.alpha_sat1 * (
-            np.abs(o.info_cs()["csat1"]) + 1.0)
-        assert_reward_close(rg[live, j], ro[live], sc[live], TRAJ_RTOL, where=f"step {j}")
-    # one launch of 287 steps cannot be re-synchronised: a station whose
-    # demand approached its threshold geometrically (binding group and grid
-    # limits, the rule in this batch) is dropped from its first near-tie on
-    assert live.sum() >= 120, int(live.sum())   # about half stay in (192 of 400 measured)
-    po = w.stations.port_off
+    po, spo = w.stations.port_off, sub.stations.port_off
     sel = np.concatenate([np.arange(po[e], po[e + 1]) for e in ids])
-    gs = b.get_state()
-    s = {k: (v[sel] if v.shape[0] == b.P else v[ids]) for k, v in gs.items()}
-    os_ = o.state()
-    spo = sub.stations.port_off
-    keep_p = np.repeat(live, np.diff(spo))
-    g, rr = restrict(s, live, keep_p), restrict(os_, live, keep_p)
-    assert_events_equal(g, rr, "sampled")
-    np.testing.assert_array_equal(b.due()[sel][keep_p].astype(np.int32), o.due()[keep_p])
-    assert_traj_close(g, rr, charger_pmax(sub)[keep_p], TRAJ_RTOL, "sampled")
-    assert (gs["trem"] == 255).any()
+    port_env = np.repeat(np.arange(len(ids)), np.diff(spo))
+
+    def sampled():
+        gs = b.get_state()
+        return {k: (v[sel] if v.shape[0] == b.P else v[ids]) for k, v in gs.items()}, b.due()[sel]
+
+    d0 = state_drift(None, None, len(sel))
+    compared, resynced, cs_seen = [], 0, 0
+    for s0 in range(0, n, K):
+        kk = min(K, n - s0)
+        b.step_n(kk, reward=r, ld_out=K)
+        torch.cuda.synchronize()
+        rg = r.cpu().numpy()[ids]
+        near = np.zeros(len(ids), bool)
+        recs = []
+        for j in range(kk):
+            before = o.state()
+            ro, _ = o.step(None)
+            near |= o.info_cs()["margin"] < TIE_MARGIN
+            recs.append((ro, o.info(), o.info_cs()["csat1"], before, near.copy()))
+        g, gdue = sampled()
+        os_ = o.state()
+        d1 = state_drift(g, os_)
+        for j, (ro, info, csat1, before, nr) in enumerate(recs):
+            ok = ~nr
+            compared.append(int(ok.sum()))
+            sc = traj_reward_scale(sub, info, before, d0, d1, kk) + sub.params.alpha_sat1 * (np.abs(csat1) + 1.0)
+            assert_reward_close(rg[ok, j], ro[ok], sc[ok], TRAJ_RTOL, where=f"step {s0 + j}")
+        ok = ~near
+        keep_p = ok[port_env]
+        assert_events_equal(restrict(g, ok, keep_p), restrict(os_, ok, keep_p), f"after step {s0 + kk}")
+        np.testing.assert_array_equal(gdue[keep_p].astype(np.int32), o.due()[keep_p], err_msg=f"due {s0 + kk}")
+        assert_traj_close(restrict(g, ok, keep_p), restrict(os_, ok, keep_p), charger_pmax(sub)[keep_p], TRAJ_RTOL,
+                          f"after step {s0 + kk}")
+        cs_seen += int((os_["trem"][keep_p] == 255).sum())
+        if near.any():                      # the oracle takes over the kernel's state of those stations
+            envs = np.flatnonzero(near)
+            ports = np.concatenate([np.arange(spo[e], spo[e + 1]) for e in envs])
+            for k, v in os_.items():
+                idx = envs if k in ENV_KEYS else ports
+                v[idx] = g[k][idx]
+            o.set_state(os_)
+            dd = o.due()
+            dd[ports] = gdue[ports]
+            o.set_due(dd)
+            resynced += len(envs)
+            d1 = state_drift(g, o.state())
+        d0 = d1
+    assert min(compared) >= 0.9 * len(ids), min(compared)
+    assert cs_seen > 0 and resynced > 0, (cs_seen, resynced)

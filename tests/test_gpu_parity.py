@@ -13,8 +13,8 @@ from oracle import Oracle
 from paper_2507_01522_b300 import inputs as I
 
 from parity import (RETURN_RTOL, STEP_RTOL, TRAJ_RTOL, assert_events_equal, assert_floats_close,
-                    assert_reward_close, assert_traj_close, charger_pmax, reward_scale, station_step_scale,
-                    to_f32_state, widen)
+                    assert_reward_close, assert_traj_close, charger_pmax, reward_scale, state_drift,
+                    to_f32_state, traj_reward_scale, widen)
 
 pytestmark = pytest.mark.gpu
 
@@ -89,6 +89,7 @@ def compare_traj(w, b, o, torch, steps, mode="plain", k=1, actions=None):
     reward = torch.zeros(E, k, device="cuda")
     done = torch.zeros(E, k, dtype=torch.uint8, device="cuda")
     n_done = 0
+    d0 = state_drift(None, None, w.stations.total_ports)
     for s0 in range(0, steps, k):
         kk = min(k, steps - s0)
         if mode == "plain":
@@ -100,14 +101,19 @@ def compare_traj(w, b, o, torch, steps, mode="plain", k=1, actions=None):
         torch.cuda.synchronize()
         rg = reward.cpu().numpy()
         dg = done.cpu().numpy()
+        recs = []
         for j in range(kk):
+            before = o.state()
             ro, do = o.step(None if actions is None else actions[:, s0 + j])
-            info = o.info()
-            assert_reward_close(rg[:, j], ro, reward_scale(info, params) + station_step_scale(w, info), TRAJ_RTOL,
-                                where=f"step {s0 + j}")
+            recs.append((ro, o.info(), before))
             np.testing.assert_array_equal(dg[:, j], do, err_msg=f"done step {s0 + j}")
             n_done += int(do.sum())
         gs, os_ = b.get_state(), o.state()
+        d1 = state_drift(gs, os_)
+        for j, (ro, info, before) in enumerate(recs):
+            assert_reward_close(rg[:, j], ro, traj_reward_scale(w, info, before, d0, d1, kk), TRAJ_RTOL,
+                                where=f"step {s0 + j}")
+        d0 = d1
         assert_events_equal(gs, os_, where=f"after step {s0 + kk}")
         assert_traj_close(gs, os_, charger_pmax(w), TRAJ_RTOL, where=f"after step {s0 + kk}")
         stg, sto = b.stats(), o.stats()
@@ -329,6 +335,7 @@ def test_host_actions_rollout(cuda_lib, n, v2g):
     oracle step by step; two calls in a row continue the episode."""
     import torch
     from paper_2507_01522_b300.chargax import Batch
+    from test_gpu_v2g import v2g_scale
     w = odd_sizes()
     if v2g:
         w = I.v2g_variant(w)
@@ -339,6 +346,7 @@ def test_host_actions_rollout(cuda_lib, n, v2g):
     hr = torch.zeros(n * E, dtype=torch.float32, pin_memory=True).numpy()
     hd = torch.zeros(n * E, dtype=torch.uint8, pin_memory=True).numpy()
     ho = torch.zeros(b1.obs_size, dtype=torch.float32, pin_memory=True).numpy()
+    d0 = state_drift(None, None, P)
     for call in range(2):
         acts = rng.integers(0, w.params.n_levels, size=(n, n_act), dtype=np.int8)     # step-major
         ha = torch.from_numpy(acts.reshape(-1)).pin_memory().numpy()
@@ -351,13 +359,18 @@ def test_host_actions_rollout(cuda_lib, n, v2g):
         np.testing.assert_array_equal(hr.reshape(n, E), r.cpu().numpy().T, err_msg=f"reward, call {call}")
         np.testing.assert_array_equal(hd.reshape(n, E), d.cpu().numpy().T, err_msg=f"done, call {call}")
         np.testing.assert_array_equal(ho, ob.cpu().numpy(), err_msg=f"observation, call {call}")
+        recs = []
         for k in range(n):
+            before, bb = o.state(), o.battery()
             ro, do = o.step(acts[k])
-            info = o.info()
-            assert_reward_close(hr[k * E:(k + 1) * E], ro, reward_scale(info, w.params) + station_step_scale(w, info),
-                                TRAJ_RTOL, where=f"call {call} step {k}")
+            recs.append((ro, o.info(), o.info_v2g(), before, bb))
             np.testing.assert_array_equal(hd[k * E:(k + 1) * E], do)
         gs, os_ = b1.get_state(), o.state()
+        d1 = state_drift(gs, os_, None, b1.battery(), o.battery())
+        for k, (ro, info, vi, before, bb) in enumerate(recs):
+            sc = v2g_scale(w, info, vi, before, d0, d1, n, bb) if v2g else traj_reward_scale(w, info, before, d0, d1, n)
+            assert_reward_close(hr[k * E:(k + 1) * E], ro, sc, TRAJ_RTOL, where=f"call {call} step {k}")
+        d0 = d1
         assert_events_equal(gs, os_, where=f"after call {call}")
         assert_traj_close(gs, os_, charger_pmax(w), TRAJ_RTOL, where=f"after call {call}")
     b1.check()
@@ -421,19 +434,25 @@ def test_fullsize_heterogeneous_sampled(cuda_lib):
     o, ws = sampled_oracle(w, ids)
     po = w.stations.port_off
     sel = np.concatenate([np.arange(po[e], po[e + 1]) for e in ids])
+    d0 = state_drift(None, None, len(sel))
     for rep in range(2):
         b.rollout(n, reward=r, done=d)
         torch.cuda.synchronize()
         gs = b.get_state()
         rg, dg = r.cpu().numpy()[ids], d.cpu().numpy()[ids]
+        recs = []
         for j in range(n):
+            before = o.state()
             ro, do = o.step(None)
-            inf = o.info()
-            assert_reward_close(rg[:, j], ro, reward_scale(inf, w.params) + station_step_scale(ws, inf), TRAJ_RTOL,
-                                where=f"rep {rep} step {j}")
+            recs.append((ro, o.info(), before))
             np.testing.assert_array_equal(dg[:, j], do)
         sub = {k: (v[sel] if v.shape[0] == b.P else v[ids]) for k, v in gs.items()}
         os_ = o.state()
+        d1 = state_drift(sub, os_)
+        for j, (ro, inf, before) in enumerate(recs):
+            assert_reward_close(rg[:, j], ro, traj_reward_scale(ws, inf, before, d0, d1, n), TRAJ_RTOL,
+                                where=f"rep {rep} step {j}")
+        d0 = d1
         assert_events_equal(sub, os_, f"sampled rep {rep}")
         assert_traj_close(sub, os_, charger_pmax(ws), TRAJ_RTOL, f"sampled rep {rep}")
         np.testing.assert_allclose(sub["ep_ret"], os_["ep_ret"], rtol=RETURN_RTOL, atol=1e-3)
@@ -465,6 +484,7 @@ def test_fullsize_fixed_station_plain_sampled(cuda_lib):
     o, ws = sampled_oracle(w, ids)
     for _ in range(99):
         o.step(None)
+    before = o.state()
     ro, _ = o.step(None)
     info = o.info()
     gs = b.get_state()
@@ -473,7 +493,9 @@ def test_fullsize_fixed_station_plain_sampled(cuda_lib):
     sub = {k: (v[sel] if v.shape[0] == b.P else v[ids]) for k, v in gs.items()}
     assert_events_equal(sub, o.state(), "sampled")
     assert_traj_close(sub, o.state(), charger_pmax(ws), TRAJ_RTOL, "sampled")
-    assert_reward_close(r.cpu().numpy()[ids], ro, reward_scale(info, w.params) + station_step_scale(ws, info), TRAJ_RTOL)
+    d1 = state_drift(sub, o.state())
+    assert_reward_close(r.cpu().numpy()[ids], ro,
+                        traj_reward_scale(ws, info, before, state_drift(None, None, len(sel)), d1, 100), TRAJ_RTOL)
 
 
 def test_fullsize_heterogeneous_plain_sampled(cuda_lib):
@@ -498,16 +520,19 @@ def test_fullsize_heterogeneous_plain_sampled(cuda_lib):
                                    + [np.array([0, b.E - 1])]))
     o, ws = sampled_oracle(w, ids)
     rg, dg = r.cpu().numpy()[:, ids], d.cpu().numpy()[:, ids]
+    recs = []
     for k in range(T):
+        before = o.state()
         ro, do = o.step(None)
-        info = o.info()
-        assert_reward_close(rg[k], ro, reward_scale(info, w.params) + station_step_scale(ws, info), TRAJ_RTOL,
-                            where=f"step {k}")
+        recs.append((ro, o.info(), before))
         np.testing.assert_array_equal(dg[k], do, err_msg=f"done step {k}")
     gs = b.get_state()
     po = w.stations.port_off
     sel = np.concatenate([np.arange(po[e], po[e + 1]) for e in ids])
     sub = {key: (v[sel] if v.shape[0] == b.P else v[ids]) for key, v in gs.items()}
+    d0, d1 = state_drift(None, None, len(sel)), state_drift(sub, o.state())
+    for k, (ro, info, before) in enumerate(recs):
+        assert_reward_close(rg[k], ro, traj_reward_scale(ws, info, before, d0, d1, T), TRAJ_RTOL, where=f"step {k}")
     assert_events_equal(sub, o.state(), "sampled")
     assert_traj_close(sub, o.state(), charger_pmax(ws), TRAJ_RTOL, "sampled")
     stg, sto = b.stats(), o.stats()

@@ -22,7 +22,7 @@ from oracle import policy as OP
 from paper_2507_01522_b300 import inputs as I
 
 from parity import (TRAJ_RTOL, assert_events_equal, assert_reward_close, assert_traj_close, charger_pmax,
-                    reward_scale, station_step_scale)
+                    state_drift, traj_reward_scale)
 
 pytestmark = pytest.mark.gpu
 
@@ -138,21 +138,28 @@ def run_policy_rollout(w, b, pw, N, T, with_logits=True, form=0):
 
 def replay_in_oracle(w, b, o, pw, N, T, obs, acts, rew, done, logits, where=""):
     """Step the oracle with the kernel's actions and compare everything the
-    rollout wrote; returns the number of episode ends."""
+    rollout wrote; returns the number of episode ends.  The state drift at
+    the start is measured on both sides (the second of back-to-back calls
+    starts from where the first left the two)."""
     L = w.params.n_levels
     n_done = 0
+    d0 = state_drift(b.get_state(), o.state())
+    recs = []
     for t in range(T):
         oo = o.observe().reshape(b.E, -1)
         np.testing.assert_allclose(obs[t], oo, rtol=0, atol=OBS_ATOL, err_msg=f"obs step {t} {where}")
         check_logits(logits[t], obs[t], pw, where=f"step {t} {where}")
         check_levels(acts[t], logits[t], o.policy_uniforms(N), L, where=f"step {t} {where}")
+        before = o.state()
         ro, do = o.step(acts[t].reshape(-1))
-        info = o.info()
-        assert_reward_close(rew[t], ro, reward_scale(info, w.params) + station_step_scale(w, info), TRAJ_RTOL,
-                            where=f"step {t} {where}")
+        recs.append((ro, o.info(), before))
         np.testing.assert_array_equal(done[t], do, err_msg=f"done step {t} {where}")
         n_done += int(do.sum())
     gs, os_ = b.get_state(), o.state()
+    d1 = state_drift(gs, os_)
+    for t, (ro, info, before) in enumerate(recs):
+        assert_reward_close(rew[t], ro, traj_reward_scale(w, info, before, d0, d1, T), TRAJ_RTOL,
+                            where=f"step {t} {where}")
     assert_events_equal(gs, os_, where=f"after rollout {where}")
     assert_traj_close(gs, os_, charger_pmax(w), TRAJ_RTOL, where=f"after rollout {where}")
     stg, sto = b.stats(), o.stats()
@@ -303,6 +310,7 @@ def test_policy_rollout_fullsize_sampled(cuda_lib):
     obs, acts, rew, done = (x.cpu().numpy() for x in (obs, acts, rew, done))
     rng = np.random.default_rng(0)
     sample = np.sort(rng.choice(b.E, 256, replace=False))
+    recs = []
     for t in range(T):
         if t % 16 == 0 or t == T - 1:
             oo = o.observe().reshape(b.E, -1)
@@ -311,12 +319,14 @@ def test_policy_rollout_fullsize_sampled(cuda_lib):
             bound = OP.mlp_bound(obs[t][sample], pw)
             u = o.policy_uniforms(N)[sample]
             check_levels(acts[t][sample], ref, u, L, margin_tol=MARGIN + 2 * bound.max(), where=f"step {t}")
+        before = o.state()
         ro, do = o.step(acts[t].reshape(-1))
-        info = o.info()
-        assert_reward_close(rew[t], ro, reward_scale(info, w.params) + station_step_scale(w, info), TRAJ_RTOL,
-                            where=f"step {t}")
+        recs.append((ro, o.info(), before))
         np.testing.assert_array_equal(done[t], do, err_msg=f"done step {t}")
     gs, os_ = b.get_state(), o.state()
+    d0, d1 = state_drift(None, None, b.P), state_drift(gs, os_)
+    for t, (ro, info, before) in enumerate(recs):
+        assert_reward_close(rew[t], ro, traj_reward_scale(w, info, before, d0, d1, T), TRAJ_RTOL, where=f"step {t}")
     assert_events_equal(gs, os_, where="after rollout")
     assert_traj_close(gs, os_, charger_pmax(w), TRAJ_RTOL, where="after rollout")
 

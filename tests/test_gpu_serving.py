@@ -7,7 +7,7 @@ import pytest
 from oracle import Oracle
 from paper_2507_01522_b300 import inputs as I
 
-from parity import TRAJ_RTOL, assert_reward_close, reward_scale, station_step_scale
+from parity import TRAJ_RTOL, assert_reward_close, state_drift, traj_reward_scale
 from test_gpu_parity import odd_sizes
 
 pytestmark = pytest.mark.gpu
@@ -63,9 +63,13 @@ def test_serving_matches_oracle():
             reqs.append((part, r, d, ob, srv.submit(ids[part], actions=a, reward=r, done=d, obs=ob)))
         for _, _, _, _, t in reqs:
             srv.wait(t)
+        before = o.state()
         ro, do = o.step(acts)
         info = o.info()
-        scale = reward_scale(info, w.params) + station_step_scale(w, info)
+        # the pool's state is not read back: the drift allowance is the
+        # per-step bound over the rounds so far (tests/parity.py)
+        zero = state_drift(None, None, w.stations.total_ports)
+        scale = traj_reward_scale(w, info, before, zero, zero, rnd + 1)
         oo = o.observe()
         for part, r, d, ob, _ in reqs:
             assert_reward_close(r, ro[part], scale[part], TRAJ_RTOL, where=f"round {rnd}")
@@ -266,9 +270,11 @@ def test_serving_fullsize_sampled():
     active = []
 
     def compare(rnd, r_s, d_s, ob_parts=None):
+        before = o.state()
         ro, do = o.step(acts)
         info = o.info()
-        scale = reward_scale(info, ws.params) + station_step_scale(ws, info)
+        zero = state_drift(None, None, ws.stations.total_ports)
+        scale = traj_reward_scale(ws, info, before, zero, zero, rnd + 1)
         assert_reward_close(r_s, ro, scale, TRAJ_RTOL, where=f"round {rnd}")
         np.testing.assert_array_equal(d_s, do, err_msg=f"done round {rnd}")
         active.append((int(np.count_nonzero(ro)), int(np.count_nonzero(o.state()["trem"]))))

@@ -122,7 +122,7 @@ def test_tree_fullsize_sampled(cuda_lib):
     checked on all stations."""
     import torch
     from paper_2507_01522_b300.chargax import Batch
-    from parity import TRAJ_RTOL, assert_traj_close, charger_pmax, station_step_scale
+    from parity import TRAJ_RTOL, assert_traj_close, charger_pmax, state_drift, traj_reward_scale
     w = I.tree_workload(65536, seed=0)
     b = Batch(w)
     b.set_launch(288, 8)
@@ -135,16 +135,20 @@ def test_tree_fullsize_sampled(cuda_lib):
     b.rollout(n, reward=r)
     torch.cuda.synchronize()
     rg = r.cpu().numpy()[ids]
+    recs = []
     for j in range(n):
+        before = o.state()
         ro, _ = o.step(None)
-        info = o.info()
-        assert_reward_close(rg[:, j], ro, reward_scale(info, sub.params) + station_step_scale(sub, info), TRAJ_RTOL,
-                            where=f"step {j}")
+        recs.append((ro, o.info(), before))
     st = w.stations
     po = st.port_off
     sel = np.concatenate([np.arange(po[e], po[e + 1]) for e in ids])
     gs = b.get_state()
     s = {k: (v[sel] if v.shape[0] == b.P else v[ids]) for k, v in gs.items()}
+    d0, d1 = state_drift(None, None, len(sel)), state_drift(s, o.state())
+    for j, (ro, info, before) in enumerate(recs):
+        assert_reward_close(rg[:, j], ro, traj_reward_scale(sub, info, before, d0, d1, n), TRAJ_RTOL,
+                            where=f"step {j}")
     assert_events_equal(s, o.state(), "sampled")
     assert_traj_close(s, o.state(), charger_pmax(sub), TRAJ_RTOL, "sampled")
     # every upper node within eta x I on all stations (last step's power)

@@ -10,8 +10,8 @@ from oracle import Oracle
 from paper_2507_01522_b300 import inputs as I
 
 from parity import (RETURN_RTOL, STEP_RTOL, TRAJ_RTOL, assert_events_equal, assert_floats_close,
-                    assert_reward_close, assert_traj_close, charger_pmax, reward_scale, station_step_scale,
-                    to_f32_state, widen)
+                    assert_reward_close, assert_traj_close, charger_pmax, reward_scale, state_drift,
+                    to_f32_state, traj_reward_scale, widen)
 from test_gpu_parity import odd_sizes, stressed
 
 pytestmark = pytest.mark.gpu
@@ -39,13 +39,21 @@ def make(name):
     return w, Batch(w), Oracle(w), torch
 
 
-def v2g_scale(w, info, vi):
-    """Reward scale: the charge-only terms plus the battery's largest one-step
-    energy at the buy price and the discharge and degradation terms."""
+def v2g_scale(w, info, vi, before=None, d0=None, d1=None, kk=1, b_before=None):
+    """Reward scale of the V2G mode: the charge-only terms, the battery's
+    energy and the discharge, degradation and feed-in terms of the step;
+    with a state before the step and drifts (see tests/parity.py), the
+    trajectory allowance for the drift of the FP32 state (chargers and
+    battery); without, one step from a shared state."""
     p = w.params
-    e_bmax = p.batt_rate_kw * p.dt_h
-    return (reward_scale(info, p) + station_step_scale(w, info) + np.abs(info["price"]) * (e_bmax + np.abs(vi["e_to"]))
-            + p.alpha_degrad * (e_bmax + np.abs(vi["degrad"])) + np.abs(p.sell_grid_ratio * info["price"] * vi["e_grid_net"]))
+    base = (traj_reward_scale(w, info, before, d0, d1, kk, b_before) if before is not None
+            else reward_scale(info, p))
+    return (base + np.abs(info["price"]) * (np.abs(vi["e_b"]) + np.abs(vi["e_to"]))
+            + p.alpha_degrad * np.abs(vi["degrad"]) + np.abs(p.sell_grid_ratio * info["price"] * vi["e_grid_net"]))
+
+
+def v2g_drift(gs, os_, gb, ob, n=None):
+    return state_drift(gs, os_, n, gb, ob)
 
 
 def assert_battery_close(bg, bo, w, rtol, where=""):
@@ -58,6 +66,7 @@ def compare_traj(w, b, o, torch, steps, mode="plain", k=1, actions=None):
     reward = torch.zeros(E, k, device="cuda")
     done = torch.zeros(E, k, dtype=torch.uint8, device="cuda")
     n_done = 0
+    d0 = v2g_drift(None, None, None, None, w.stations.total_ports)
     for s0 in range(0, steps, k):
         kk = min(k, steps - s0)
         if mode == "plain":
@@ -68,12 +77,19 @@ def compare_traj(w, b, o, torch, steps, mode="plain", k=1, actions=None):
             b.step_n(kk, actions=a, reward=reward, done=done, lda=kk, ld_out=k)
         torch.cuda.synchronize()
         rg, dg = reward.cpu().numpy(), done.cpu().numpy()
+        recs = []
         for j in range(kk):
+            before, bb = o.state(), o.battery()
             ro, do = o.step(None if actions is None else actions[:, s0 + j])
-            assert_reward_close(rg[:, j], ro, v2g_scale(w, o.info(), o.info_v2g()), TRAJ_RTOL, where=f"step {s0 + j}")
+            recs.append((ro, o.info(), o.info_v2g(), before, bb))
             np.testing.assert_array_equal(dg[:, j], do, err_msg=f"done step {s0 + j}")
             n_done += int(do.sum())
         gs, os_ = b.get_state(), o.state()
+        d1 = v2g_drift(gs, os_, b.battery(), o.battery())
+        for j, (ro, info, vi, before, bb) in enumerate(recs):
+            assert_reward_close(rg[:, j], ro, v2g_scale(w, info, vi, before, d0, d1, kk, bb), TRAJ_RTOL,
+                                where=f"step {s0 + j}")
+        d0 = d1
         assert_events_equal(gs, os_, where=f"after step {s0 + kk}")
         assert_traj_close(gs, os_, charger_pmax(w), TRAJ_RTOL, where=f"after step {s0 + kk}")
         assert_battery_close(b.battery(), o.battery(), w, TRAJ_RTOL, where=f"after step {s0 + kk}")
@@ -271,12 +287,19 @@ def test_v2g_fullsize_heterogeneous_sampled(cuda_lib):
     b.rollout(n, reward=r, done=d)
     torch.cuda.synchronize()
     rg = r.cpu().numpy()[ids]
+    recs = []
     for j in range(n):
+        before, bb = o.state(), o.battery()
         ro, do = o.step(None)
-        assert_reward_close(rg[:, j], ro, v2g_scale(sub, o.info(), o.info_v2g()), TRAJ_RTOL, where=f"step {j}")
+        recs.append((ro, o.info(), o.info_v2g(), before, bb))
     gs = b.get_state()
     s = {k: (v[sel] if v.shape[0] == b.P else v[ids]) for k, v in gs.items()}
     os_ = o.state()
+    d0 = v2g_drift(None, None, None, None, len(sel))
+    d1 = v2g_drift(s, os_, {k: v[ids] for k, v in b.battery().items()}, o.battery())
+    for j, (ro, info, vi, before, bb) in enumerate(recs):
+        assert_reward_close(rg[:, j], ro, v2g_scale(sub, info, vi, before, d0, d1, n, bb), TRAJ_RTOL,
+                            where=f"step {j}")
     assert_events_equal(s, os_, "sampled")
     assert_traj_close(s, os_, charger_pmax(sub), TRAJ_RTOL, "sampled")
     bt = b.battery()
