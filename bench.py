@@ -758,7 +758,10 @@ def run_serving(args, rank):
     ids = srv.admit(w.stations, seed=2000 + rank)
     t_admit = time.perf_counter() - t0
     per = args.serve_envs // args.serve_actors
-    threads = max(2, min(16, (os.cpu_count() or 8) // 2))
+    # simulated actors' host threads: every host core but those of the
+    # server's scheduler thread and this process
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 8)
+    threads = max(2, min(16, cores - 4))
     # peak: every actor resubmits at once (no think time)
     peak = srv.simulate(ids, n_actors=args.serve_actors, envs_per_actor=per, mean_think_us=0.0,
                         duration_s=2.0, warmup_s=0.5, n_threads=threads, seed=rank)

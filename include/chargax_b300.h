@@ -422,13 +422,22 @@ int chx_policy_rollout(chx_handle* h, int32_t n_steps, float* d_obs, int8_t* d_a
  * environment, App. "Practical Considerations", served to many clients).
  * Stations are admitted into slots of their size class while the bytes they
  * occupy stay within an HBM budget; a station's id is its slot and also its
- * Philox stream id.  Requests wait in a queue; a scheduler thread packs every
- * request whose stations are not in flight into the next tick (in arrival
- * order, up to max_tick_envs stations) and keeps up to n_streams ticks on the
- * device at once; a completion thread copies results back and completes
- * tickets.  A request's results do not depend on what else shares its tick.
- * Requests for one station are applied in submission order.  All server calls
- * are thread-safe. */
+ * Philox stream id.
+ *   - chx_srv_submit checks a request in the caller's thread and writes it,
+ *     with its station list and given levels, into a record of pinned host
+ *     memory the device reads; it returns a ticket.
+ *   - A scheduler thread hands the device the window of tickets not yet
+ *     finished; each tick (a CUDA graph, up to n_streams of them queued at
+ *     once) takes, in arrival order, every request whose stations no earlier
+ *     request of the window lists, steps or resets them (the fused kernel in
+ *     gather mode), writes each taken request's results into its record and
+ *     then raises the record's completion flag.  Requests that arrive while a
+ *     tick runs join the next one; requests for one station are applied in
+ *     submission order.
+ *   - chx_srv_wait / chx_srv_test read the flag and copy the results to the
+ *     caller's buffers (in the caller's thread).
+ * A request's results do not depend on what else shares its tick.  All server
+ * calls are thread-safe. */
 #define CHX_SRV_STEP 0
 #define CHX_SRV_RESET 1
 
@@ -441,9 +450,12 @@ typedef struct chx_srv_cfg {
     int32_t class_capacity[5];      /* station slots of size class 8,16,32,64,128     */
     double hbm_budget_bytes;        /* admission limit on the bytes admitted stations
                                        occupy (33 B per charger slot + 128 B)        */
-    int32_t max_tick_envs;          /* most stations in one tick and in one request   */
-    int32_t n_streams;              /* ticks on the device at once, 1..8              */
-    int64_t max_tick_obs_floats;    /* observation floats one tick can return, 0 = none */
+    int32_t max_tick_envs;          /* most stations in one request; a tick takes at
+                                       most (n_streams + 1) x this many               */
+    int32_t n_streams;              /* tick slots: ticks queued on the device at once,
+                                       1..8                                           */
+    int64_t max_tick_obs_floats;    /* observation floats one request can return, 0 =
+                                       none; x (n_streams + 1) must stay below 2^31   */
 } chx_srv_cfg;
 
 typedef struct chx_srv_req {
@@ -465,10 +477,10 @@ typedef struct chx_srv_stats_t {
     int32_t resident;               /* admitted stations                              */
     double used_bytes, budget_bytes;
     double device_busy_ms, elapsed_ms;
-    /* host time spent (ms) in: submissions holding the server lock, the
-     * scheduler's scans choosing requests, packing tick buffers, packing plus
-     * launching ticks (includes the packing), delivering results; number of
-     * scans */
+    /* host time spent (ms) in: submissions, the scheduler's bookkeeping
+     * (window, completed ticks; its idle spinning included), packing (0: the
+     * device builds each tick), launching ticks, copying results to the
+     * callers (in chx_srv_wait / chx_srv_test); ticks launched */
     double host_submit_ms, host_scan_ms, host_pack_ms, host_launch_ms, host_complete_ms;
     int64_t n_scans;
 } chx_srv_stats_t;
@@ -482,19 +494,23 @@ int chx_srv_stop(chx_srv* s);
  * `seed`; their ids go to h_ids [n_envs].  CHX_ENOMEM if a class has no free
  * slot or the HBM budget would be exceeded. */
 int chx_srv_admit(chx_srv* s, const chx_stations* st, uint64_t seed, int32_t* h_ids);
-/* Free the slots of stations with no queued or in-flight request (else
- * CHX_EINVAL and nothing is evicted). */
+/* Free the slots of stations that no unreleased ticket lists (queued, in
+ * flight, or finished and not yet collected by chx_srv_wait / chx_srv_test);
+ * else CHX_EINVAL and nothing is evicted. */
 int chx_srv_evict(chx_srv* s, const int32_t* h_ids, int32_t n);
 /* Queue a request; *ticket identifies it.  The output buffers must stay valid
  * until the ticket completes.  At most 65536 tickets may be outstanding
  * (submitted and not yet released by chx_srv_wait / chx_srv_test), else
  * CHX_ENOMEM.  A ticket is waited on or tested by one thread at a time. */
 int chx_srv_submit(chx_srv* s, const chx_srv_req* r, uint64_t* ticket);
-/* Block until the ticket completes (CHX_ETIMEOUT after timeout_us); the
- * ticket is then released.  latency_ns (may be NULL) = completion - submission.
- * CHX_ECUDA if the device work carrying it failed. */
+/* Block until the ticket completes (CHX_ETIMEOUT after timeout_us), copy its
+ * results to the request's buffers and release the ticket.  latency_ns (may be
+ * NULL) = the moment the completion is seen - submission.  CHX_ECUDA (with the
+ * CUDA error) if the server's device work failed; the server then takes no
+ * further ticks. */
 int chx_srv_wait(chx_srv* s, uint64_t ticket, int64_t timeout_us, int64_t* latency_ns);
-/* Non-blocking: *h_done = 1 and the ticket is released if it has completed. */
+/* Non-blocking: if the ticket has completed, its results are copied, the
+ * ticket is released and *h_done = 1. */
 int chx_srv_test(chx_srv* s, uint64_t ticket, int32_t* h_done, int64_t* latency_ns);
 int chx_srv_stats(chx_srv* s, chx_srv_stats_t* out);
 

@@ -49,41 +49,26 @@ void launch_reset(const DevBatch& b, const DevParams& p, const int32_t* user_to_
 }
 
 // Reset of listed station slots with one seed each (the serving pool, where a
-// station's id is its slot): same episode start as k_reset.
+// station's id is its slot): same episode start as k_reset.  The count is n,
+// or *d_n when d_n is given (the list was built on the device).
 __global__ void k_reset_slots(DevBatch b, DevParams p, const int32_t* __restrict__ slots,
-                              const unsigned long long* __restrict__ seeds, int n)
+                              const unsigned long long* __restrict__ seeds, int n, const int* __restrict__ d_n)
 {
-    const int j = blockIdx.x;
-    if (j >= n) return;
-    const int s = slots[j];
-    const int c = class_of_slot(b, s);
-    const int C = 8 << c;
-    const long long pb = b.cls_port_base[c] + (long long)(s - b.cls_env_base[c]) * C;
-    for (int q = threadIdx.x; q < C; q += blockDim.x) {
-        const long long i = pb + q;
-        b.soc[i] = 0.f; b.erem[i] = 0.f; b.cap[i] = 0.f; b.rbar[i] = 0.f; b.pw[i] = 0.f; b.trem[i] = 0;
-        if (p.cs_share) b.due[i] = 0;      // the array exists only with charge-sensitive users
-    }
-    if (threadIdx.x == 0) {
-        const uint32_t lo = (uint32_t)seeds[j], hi = (uint32_t)(seeds[j] >> 32);
-        b.key0[s] = lo;
-        b.key1[s] = hi;
-        b.gstep[s] = 0u;
-        b.ncar[s] = 0u;
-        b.tod[s] = 0;
-        b.ep_ret[s] = 0.f;
-        if (p.v2g) {  // the battery arrays exist only in V2G mode
-            b.bsoc[s] = p.batt_soc0;
-            b.bp[s] = 0.f;
-        }
-        b.day[s] = draw_day((uint32_t)s, 0u, 1u, lo, hi, p.n_days);
-    }
+    const int cnt = d_n ? *d_n : n;
+    for (int j = blockIdx.x; j < cnt; j += gridDim.x)
+        reset_one_slot(b, p, slots[j], seeds[j]);
 }
 
 void launch_reset_slots(const DevBatch& b, const DevParams& p, const int32_t* slots, const unsigned long long* seeds,
                         int n, cudaStream_t st)
 {
-    if (n > 0) k_reset_slots<<<n, 128, 0, st>>>(b, p, slots, seeds, n);
+    if (n > 0) k_reset_slots<<<n, 128, 0, st>>>(b, p, slots, seeds, n, nullptr);
+}
+
+void launch_reset_slots_dev(const DevBatch& b, const DevParams& p, const int32_t* slots,
+                            const unsigned long long* seeds, const int* d_n, int grid, cudaStream_t st)
+{
+    k_reset_slots<<<grid, 128, 0, st>>>(b, p, slots, seeds, 0, d_n);
 }
 
 // Observation: one warp per station slot; lanes stride over the chargers.

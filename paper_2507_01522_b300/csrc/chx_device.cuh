@@ -336,4 +336,34 @@ __device__ __forceinline__ int class_of_slot(const DevBatch& b, int s)
     return c;
 }
 
+// Start a new episode at station slot s with Philox key `seed` (the serving
+// pool's reset, where a station's id is its slot; same start as chx_reset):
+// the block's threads clear its chargers, thread 0 its station fields.
+__device__ __forceinline__ void reset_one_slot(const DevBatch& b, const DevParams& p, int s, unsigned long long seed)
+{
+    const int c = class_of_slot(b, s);
+    const int C = 8 << c;
+    const long long pb = b.cls_port_base[c] + (long long)(s - b.cls_env_base[c]) * C;
+    for (int q = threadIdx.x; q < C; q += blockDim.x) {
+        const long long i = pb + q;
+        b.soc[i] = 0.f; b.erem[i] = 0.f; b.cap[i] = 0.f; b.rbar[i] = 0.f; b.pw[i] = 0.f; b.trem[i] = 0;
+        if (p.cs_share) b.due[i] = 0;      // the array exists only with charge-sensitive users
+    }
+    if (threadIdx.x == 0) {
+        const uint32_t lo = (uint32_t)seed, hi = (uint32_t)(seed >> 32);
+        b.key0[s] = lo;
+        b.key1[s] = hi;
+        b.gstep[s] = 0u;
+        b.ncar[s] = 0u;
+        b.tod[s] = 0;
+        b.ep_ret[s] = 0.f;
+        if (p.v2g) {  // the battery arrays exist only in V2G mode
+            b.bsoc[s] = p.batt_soc0;
+            b.bp[s] = 0.f;
+        }
+        b.day[s] = draw_day((uint32_t)s, 0u, 1u, lo, hi, p.n_days);
+    }
+}
+
+
 }  // namespace chx

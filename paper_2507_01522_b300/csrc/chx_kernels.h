@@ -28,9 +28,17 @@ struct FusedIO {
     int* counter;                          // work counter, zero at launch
     // gather mode (NULL = every station of the batch): per class, a list of
     // entries (station slot, action offset, output index, observation offset)
-    // padded with a padding slot to whole tiles; class c starts at gather_base[c]
+    // padded with a padding slot to whole tiles; class c starts at gather_base[c].
+    // An action offset < 0 draws that station's levels with Philox; an
+    // observation offset < 0 writes no observation for that station.
     const int4* gather;
     int gather_base[kNumClasses];
+    // gather mode with a device-side schedule (NULL = the host schedule
+    // above): entries of class c in dcount[c]; tiles run largest class first.
+    // dmax_small / dmax_large bound the tiles of the classes of 8..64 and of
+    // 128 chargers (grid sizes; 0 = no launch for that range)
+    const int* dcount;
+    int dmax_small, dmax_large;
 };
 
 void launch_step_plain(const DevBatch& b, const DevParams& p, const int8_t* actions, long long lda, float* reward,
@@ -59,6 +67,9 @@ void launch_observe(const DevBatch& b, const DevParams& p, float* obs, cudaStrea
 // reset listed slots (station id = slot), one 64-bit seed per entry
 void launch_reset_slots(const DevBatch& b, const DevParams& p, const int32_t* slots, const unsigned long long* seeds,
                         int n, cudaStream_t st);
+// the same with the entry count *d_n in device memory, `grid` blocks striding over it
+void launch_reset_slots_dev(const DevBatch& b, const DevParams& p, const int32_t* slots,
+                            const unsigned long long* seeds, const int* d_n, int grid, cudaStream_t st);
 
 
 // ---- policy (3-layer BF16 MLP on the tensor cores + fused sampling) ------

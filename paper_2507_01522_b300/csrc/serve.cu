@@ -1,22 +1,41 @@
 // serve.cu -- the serving loop: a pool of device-resident stations stepped by
-// requests from many actors with continuous batching.
+// requests from many actors with continuous batching, each tick built on the
+// device.
 //
 // * Pool: station slots bucketed by size class (the layout of chx_device.cuh),
 //   allocated once; stations are admitted into free slots while the bytes they
 //   occupy stay within an HBM budget, and evicted to free them.  A station's
 //   id is its slot, which is also its Philox stream id.
-// * Requests (step or reset of a list of stations) are queued by
-//   chx_srv_submit.  A scheduler thread packs pending requests into a tick --
-//   every request whose stations are not in flight, in arrival order, up to a
-//   tick size -- and launches it on one of several streams: up to n_streams
-//   ticks run on the device at once while the next one is being packed, so a
-//   request that arrives while others are on the GPU joins the next tick as
-//   soon as its stations are free.  A completion thread waits for each tick,
-//   copies results to the requesters' buffers and completes their tickets.
-// * A tick's step is the warp-cooperative kernel of step_fused.cu in gather
-//   mode (one step, tiles formed from the tick's stations of one class).  Its
-//   reductions depend only on a charger's position inside its station, so a
-//   request's results are the same whatever else shares its tick.
+// * Requests: chx_srv_submit validates a request in the caller's thread,
+//   takes the next ticket and writes the request into a record of pinned,
+//   device-mapped host memory (station list, given levels, output buffers);
+//   nothing else is done per station on the host.
+// * Ticks: one scheduler thread hands the device a window of tickets [lo, hi)
+//   -- the requests not yet known to be finished -- and the device does the
+//   rest, on one stream, in order:
+//     claim    each open request of the window copies its list into a device
+//              arena and writes its rank (arrival order) into every station
+//              it lists with atomicMin;
+//     select   a request whose rank won every one of its stations is taken
+//              (the earliest request for each station runs first, later ones
+//              wait for a later tick); its stations become gather entries of
+//              their size class, or reset entries;
+//     prep     each class's entries are padded to whole warp tiles, and the
+//              reset entries start new episodes;
+//     step     the fused kernel of step_fused.cu runs one step in gather mode
+//              over the device-side entry counts;
+//     finish   each taken request's rewards, done flags and observations go
+//              straight into its pinned buffers, then its completion flag
+//              (after a system-wide fence); the window's claims are cleared.
+//   Each of the n_streams tick slots is one CUDA graph, captured at start,
+//   whose kernels read the window from the slot's pinned argument record; up
+//   to n_streams ticks are queued on the device at once, and requests that
+//   arrive while a tick runs join the next one.
+// * Completion: chx_srv_wait / chx_srv_test read the request's completion
+//   flag and copy its results to the caller's buffers in the caller's thread.
+// * A station's result depends only on its own state and its position inside
+//   its station tile, so a request's results are the same whatever else
+//   shares its tick.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -27,6 +46,7 @@
 #include <memory>
 #include <mutex>
 #include <random>
+#include <shared_mutex>
 #include <string>
 #include <thread>
 #include <vector>
@@ -56,50 +76,372 @@ constexpr uint64_t kMaxOutstanding = 1u << 16;   // request records (power of tw
 // bytes a station of class c occupies in the pool (state + statics)
 inline double slot_bytes(int c) { return (double)(8 << c) * 33.0 + 128.0; }
 
-constexpr int kFree = 0, kQueued = 1, kDone = 2;
+constexpr int kFree = 0, kFilling = 1, kQueued = 2;
 
-// A request record.  Records live in a fixed table indexed by ticket modulo
-// its size, so their addresses never change and a ticket's state can be read
-// without the server lock.
+// What the device reads of a request: one per record, in pinned host memory
+// mapped into the device's address space.
+struct DevReq {
+    unsigned long long ticket;
+    int kind, n;                           // CHX_SRV_STEP / CHX_SRV_RESET, stations listed
+    int n_act;                             // chargers of the listed stations
+    int has_act;                           // given levels (else Philox)
+    int obs_floats;                        // observation floats to return (0 = none)
+    int unused;
+    long long cum_envs, cum_act, cum_obs;  // totals of every earlier submission
+    const int32_t* ids;                    // [n] station slots
+    const int8_t* acts;                    // [n_act] given levels
+    float* rew;                            // [n] outputs, written by the device
+    uint8_t* done;                         // [n]
+    float* obs;                            // [obs_floats]
+    unsigned long long seed;               // reset: new Philox key
+};
+
+// a block of pinned, device-mapped host memory from PinnedPool
+template <class T>
+struct PinnedBuf {
+    T* h = nullptr;                        // host address
+    T* d = nullptr;                        // device address
+    size_t cap = 0;                        // elements
+    int cls = 0;                           // log2 of the block's bytes
+};
+
+struct PinnedPool {
+    static constexpr size_t kChunk = 64u << 20;
+    std::mutex mu;
+    std::vector<void*> chunks;
+    char *cur_h = nullptr, *cur_d = nullptr;
+    size_t left = 0;
+    std::vector<std::pair<void*, void*>> free_list[48];
+    int get(size_t bytes, void** host, void** dev, int* cls);
+    void put(void* host, void* dev, int cls);
+    ~PinnedPool();
+};
+
+// A request record (host side).  Records live in a fixed table indexed by
+// ticket modulo its size; each keeps its pinned buffers for reuse.
 struct Request {
     std::atomic<int> state{kFree};
     std::atomic<uint64_t> ticket{0};
-    int32_t kind = 0;
-    std::vector<int32_t> envs;
-    std::vector<int8_t> actions;          // empty = Philox levels
-    std::vector<int32_t> act_off;         // [n+1]: charger offsets of the listed stations
+    int32_t kind = 0, n = 0;
+    int64_t t_submit = 0;
     float* h_reward = nullptr;
     uint8_t* h_done = nullptr;
     float* h_obs = nullptr;
-    uint64_t seed = 0;
     int64_t obs_floats = 0;
-    int64_t t_submit = 0, t_done = 0;
-    bool failed = false;
+    int64_t cum_envs = 0, cum_act = 0, cum_obs = 0;
+    // pinned, device-mapped buffers
+    PinnedBuf<int32_t> ids;
+    PinnedBuf<int8_t> acts;
+    PinnedBuf<float> rew;
+    PinnedBuf<uint8_t> done;
+    PinnedBuf<float> obs;
 };
 
-constexpr size_t kUpHead = 16;             // work counters at the head of a tick's upload
-static_assert(kFusedCounters * sizeof(int) <= kUpHead, "counters fit the upload head");
+// A record's descriptor as the claim kernel read it (host memory is read
+// once per record and tick), with its arena offsets in that tick.
+struct RecMeta {
+    long long off, aoff, ooff;             // arena offsets: stations, given levels, observation floats
+    unsigned long long seed;
+    float* rew;
+    uint8_t* done;
+    float* obs;
+    int n, kind, has_act, obs_floats;
+};
 
-struct Tick {
-    cudaStream_t st = nullptr;
+// counters of a tick, in device memory (zeroed by the claim kernel)
+enum { kCntClass = 0, kCntAdmitted = 5, kCntReset = 6, kCntBlocked = 7, kCntWork = 8, kCnt = 10 };
+static_assert(kCntWork + kFusedCounters <= kCnt, "counter layout");
+
+// what a tick reports to the host (pinned, mapped)
+struct TickResult {
+    int admitted, stepped, resets, blocked;
+};
+
+struct TickArgs {
+    unsigned long long lo, hi;             // the window's tickets
+    long long base_envs, base_act, base_obs;   // totals of the submissions before ticket lo
+    int tick;                              // tick number (>= 1)
+    int slot;                              // TickResult slot
+};
+
+// device-side state of the server
+struct DevSrv {
+    const DevReq* req;                     // [kMaxOutstanding] mapped
+    unsigned long long* done_flag;         // [kMaxOutstanding] mapped: ticket finished
+    unsigned long long* executed;          // [kMaxOutstanding]: ticket taken by a tick
+    int* claimed_tick;                     // [kMaxOutstanding]: tick whose claim pass the record joined
+    RecMeta* meta;                         // [kMaxOutstanding]: the record as that claim pass read it
+    unsigned long long* adm;               // [kMaxOutstanding]: tickets taken by the tick
+    uint32_t* claim;                       // [n_slots]: lowest rank claiming a station
+    int32_t* ids;                          // [A] station lists of the window
+    int8_t* acts;                          // [A_act] given levels of the window
+    float* rew;                            // [A] step outputs
+    uint8_t* done;                         // [A]
+    float* obs;                            // [A_obs]
+    int4* gather;                          // [kNumClasses][G] entries, G = A + padding
+    int32_t* rslot;                        // [A] reset entries
+    unsigned long long* rseed;             // [A]
+    int* cnt;                              // [kCnt]
+    TickResult* result;                    // [n_streams] mapped
+    TickArgs* targs;                       // [n_streams] the ticks' arguments (device copy)
+    long long A, A_act, A_obs;
+    int G, max_tick_envs;
+    int pad_slot[kNumClasses];
+    unsigned long long mask;
+};
+
+__device__ __forceinline__ long long warp_global()
+{
+    return ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+}
+__device__ __forceinline__ long long warps_total() { return ((long long)gridDim.x * blockDim.x) >> 5; }
+
+// claim: copy each open request's list (and levels) into the arenas and mark
+// its stations with its rank.  A request whose arena span does not fit waits
+// for a later tick; spans grow with the ticket, so every later one waits too.
+// Host memory is read in two dependent rounds per record (descriptor, then
+// its list with up to 8 loads in flight per lane).
+__global__ void k_tick_claim(DevSrv d, const TickArgs* __restrict__ host_args, int slot)
+{
+    // the tick's arguments: written by the host into pinned memory before
+    // the launch; kept in device memory for the tick's later kernels
+    const TickArgs a = host_args[slot];
+    if (blockIdx.x == 0 && threadIdx.x == 0) d.targs[slot] = a;
+    if (blockIdx.x == 0 && threadIdx.x < kCnt) d.cnt[threadIdx.x] = 0;
+    const int lane = threadIdx.x & 31;
+    const long long nw = (long long)(a.hi - a.lo);
+    for (long long w = warp_global(); w < nw; w += warps_total()) {
+        const unsigned long long t = a.lo + (unsigned long long)w;
+        const int rec = (int)(t & d.mask);
+        if (d.executed[rec] == t) continue;
+        const DevReq q = d.req[rec];
+        RecMeta m;
+        m.n = q.n;
+        m.kind = q.kind;
+        m.has_act = q.has_act;
+        m.obs_floats = q.obs_floats;
+        m.off = q.cum_envs - a.base_envs;
+        m.aoff = q.cum_act - a.base_act;
+        m.ooff = q.cum_obs - a.base_obs;
+        m.seed = q.seed;
+        m.rew = q.rew;
+        m.done = q.done;
+        m.obs = q.obs;
+        const int n = m.n;
+        if (m.off < 0 || m.off + n > d.A || (m.has_act && m.aoff + q.n_act > d.A_act) ||
+            (m.obs_floats && m.ooff + m.obs_floats > d.A_obs))
+            continue;
+        const uint32_t rank = (uint32_t)w;
+        const int32_t* ids = q.ids;
+        int sv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) sv[u] = lane + 32 * u < n ? ids[lane + 32 * u] : -1;
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (sv[u] >= 0) {
+                d.ids[m.off + lane + 32 * u] = sv[u];
+                atomicMin(d.claim + sv[u], rank);
+            }
+        for (int j = 256 + lane; j < n; j += 32) {
+            const int s = ids[j];
+            d.ids[m.off + j] = s;
+            atomicMin(d.claim + s, rank);
+        }
+        if (m.has_act) {
+            const int8_t* acts = q.acts;
+            for (int j = lane; j < q.n_act; j += 32) d.acts[m.aoff + j] = acts[j];
+        }
+        if (lane == 0) {
+            d.claimed_tick[rec] = a.tick;
+            d.meta[rec] = m;
+        }
+    }
+}
+
+// select: take every request that won all of its stations (its arena span
+// bounds the tick's stations: at most A); write its stations' gather or reset
+// entries.  Per 256 stations of a request: one round of list loads, one of
+// claim (or charger-count) loads, one atomicAdd per size class present.
+__global__ void __launch_bounds__(256, 2) k_tick_select(DevSrv d, DevBatch b, int slot)
+{
+    const TickArgs a = d.targs[slot];
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const long long nw = (long long)(a.hi - a.lo);
+    for (long long w = warp_global(); w < nw; w += warps_total()) {
+        const unsigned long long t = a.lo + (unsigned long long)w;
+        const int rec = (int)(t & d.mask);
+        if (d.executed[rec] == t) continue;
+        if (d.claimed_tick[rec] != a.tick) {                   // its span did not fit this tick's arenas
+            if (lane == 0) atomicAdd(d.cnt + kCntBlocked, 1);
+            continue;
+        }
+        const RecMeta m = d.meta[rec];
+        const int n = m.n;
+        const int32_t* ids = d.ids + m.off;
+        const uint32_t rank = (uint32_t)w;
+        bool mine = true;
+        for (int j0 = 0; j0 < n; j0 += 256) {
+            int sv[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) sv[u] = j0 + lane + 32 * u < n ? ids[j0 + lane + 32 * u] : -1;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) mine &= sv[u] < 0 || d.claim[sv[u]] == rank;
+        }
+        mine = __all_sync(0xFFFFFFFFu, mine);
+        if (!mine) {                                            // an earlier request holds one of its stations
+            if (lane == 0) atomicAdd(d.cnt + kCntBlocked, 1);
+            continue;
+        }
+        if (lane == 0) {
+            d.executed[rec] = t;
+            d.adm[atomicAdd(d.cnt + kCntAdmitted, 1)] = t;
+        }
+        if (m.kind == CHX_SRV_RESET) {
+            int rb = 0;
+            if (lane == 0) rb = atomicAdd(d.cnt + kCntReset, n);
+            rb = __shfl_sync(0xFFFFFFFFu, rb, 0);
+            for (int j = lane; j < n; j += 32) {
+                d.rslot[rb + j] = ids[j];
+                d.rseed[rb + j] = m.seed;
+            }
+            continue;
+        }
+        int carry = 0;                                          // chargers of the request's earlier stations
+        for (int j0 = 0; j0 < n; j0 += 256) {
+            int sv[8], np[8], cl[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) sv[u] = j0 + lane + 32 * u < n ? ids[j0 + lane + 32 * u] : -1;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                np[u] = sv[u] >= 0 ? b.n_ports[sv[u]] : 0;
+                cl[u] = sv[u] >= 0 ? class_of_slot(b, sv[u]) : -1;
+            }
+            // per class: stations of this block of 256, then one atomicAdd
+            unsigned bal[8][kNumClasses];
+            int tot = 0;                                        // lane c < kNumClasses: stations of class c
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+#pragma unroll
+                for (int c = 0; c < kNumClasses; ++c) {
+                    bal[u][c] = __ballot_sync(0xFFFFFFFFu, cl[u] == c);
+                    if (lane == c) tot += __popc(bal[u][c]);
+                }
+            int base = 0;
+            if (lane < kNumClasses && tot > 0) base = atomicAdd(d.cnt + kCntClass + lane, tot);
+            int before[kNumClasses];                            // stations of class c in earlier rows u
+#pragma unroll
+            for (int c = 0; c < kNumClasses; ++c) before[c] = __shfl_sync(0xFFFFFFFFu, base, c);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                int incl = np[u];
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                const int excl = carry + incl - np[u];
+                carry += __shfl_sync(0xFFFFFFFFu, incl, 31);
+                int pos = 0;
+#pragma unroll
+                for (int c = 0; c < kNumClasses; ++c) {
+                    if (cl[u] == c) pos = before[c] + __popc(bal[u][c] & lt);
+                    before[c] += __popc(bal[u][c]);
+                }
+                if (sv[u] >= 0) {
+                    const int j = j0 + lane + 32 * u;
+                    const int act = m.has_act ? (int)(m.aoff + excl) : -1;
+                    const int ob = m.obs_floats ? (int)(m.ooff + 8LL * j + 6LL * excl) : -1;
+                    d.gather[(long long)cl[u] * d.G + pos] = make_int4(sv[u], act, (int)(m.off + j), ob);
+                }
+            }
+        }
+    }
+}
+
+// prepare the step: block 0 pads each class's entries to whole warp tiles
+// with the class's padding slot and zeroes the fused kernel's work counters;
+// every block then starts new episodes for the reset entries
+__global__ void k_tick_prep(DevSrv d, DevBatch b, DevParams p)
+{
+    if (blockIdx.x == 0) {
+        const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        if (c < kNumClasses) {
+            const int n = d.cnt[kCntClass + c], epw = tile_epw(c);
+            const int padded = (n + epw - 1) / epw * epw;
+            for (int i = n + lane; i < padded; i += 32)
+                d.gather[(long long)c * d.G + i] = make_int4(d.pad_slot[c], -1, 0, -1);
+        }
+        if (threadIdx.x < kFusedCounters) d.cnt[kCntWork + threadIdx.x] = 0;
+    }
+    const int n_reset = d.cnt[kCntReset];
+    for (int j = blockIdx.x; j < n_reset; j += gridDim.x) reset_one_slot(b, p, d.rslot[j], d.rseed[j]);
+}
+
+// finish: clear the claims of the tick's window; deliver the taken requests'
+// outputs into their pinned buffers and raise their completion flags
+__global__ void k_tick_finish(DevSrv d, int slot)
+{
+    const TickArgs a = d.targs[slot];
+    const int lane = threadIdx.x & 31;
+    const long long nw = (long long)(a.hi - a.lo);
+    for (long long w = warp_global(); w < nw; w += warps_total()) {
+        const unsigned long long t = a.lo + (unsigned long long)w;
+        const int rec = (int)(t & d.mask);
+        if (d.claimed_tick[rec] != a.tick) continue;
+        const long long off = d.meta[rec].off;
+        const int n = d.meta[rec].n;
+        for (int j0 = 0; j0 < n; j0 += 256) {
+            int sv[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) sv[u] = j0 + lane + 32 * u < n ? d.ids[off + j0 + lane + 32 * u] : -1;
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (sv[u] >= 0) d.claim[sv[u]] = 0xFFFFFFFFu;
+        }
+    }
+    const int n_adm = d.cnt[kCntAdmitted];
+    for (long long k = warp_global(); k < n_adm; k += warps_total()) {
+        const unsigned long long t = d.adm[k];
+        const int rec = (int)(t & d.mask);
+        const RecMeta m = d.meta[rec];
+        if (m.kind == CHX_SRV_STEP) {
+            for (int j = lane; j < m.n; j += 32) {
+                m.rew[j] = d.rew[m.off + j];
+                m.done[j] = d.done[m.off + j];
+            }
+            for (int j = lane; j < m.obs_floats; j += 32) m.obs[j] = d.obs[m.ooff + j];
+        }
+        __threadfence_system();
+        __syncwarp();
+        if (lane == 0) *reinterpret_cast<volatile unsigned long long*>(d.done_flag + rec) = t;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        TickResult r;
+        r.admitted = d.cnt[kCntAdmitted];
+        r.stepped = d.cnt[kCntClass] + d.cnt[kCntClass + 1] + d.cnt[kCntClass + 2] + d.cnt[kCntClass + 3] +
+                    d.cnt[kCntClass + 4];
+        r.resets = d.cnt[kCntReset];
+        r.blocked = d.cnt[kCntBlocked];
+        volatile int* dst = reinterpret_cast<volatile int*>(d.result + a.slot);
+        dst[0] = r.admitted;
+        dst[1] = r.stepped;
+        dst[2] = r.resets;
+        dst[3] = r.blocked;
+    }
+}
+
+struct TickSlot {
     cudaEvent_t ev_start = nullptr, ev_end = nullptr;
-    // pinned host and device buffers, one copy each way per tick:
-    // up   = [zeroed work counters (kUpHead bytes)][entries][actions]
-    // down = [rewards][done flags][observations, 16-byte aligned]
-    unsigned char *h_up = nullptr, *d_up = nullptr;
-    unsigned char *h_down = nullptr, *d_down = nullptr;
-    int4 *h_entries = nullptr, *d_entries = nullptr;   // up + kUpHead
-    int* d_counter = nullptr;                          // d_up
-    float* h_rew = nullptr;                            // this tick's outputs inside h_down
-    uint8_t* h_done = nullptr;
-    float* h_obs = nullptr;
-    int32_t *h_rslots = nullptr, *d_rslots = nullptr;
-    unsigned long long *h_rseeds = nullptr, *d_rseeds = nullptr;
-    std::vector<uint32_t> recs;             // request records in this tick
-    std::vector<int64_t> rew_off, obs_off;  // per record: where its outputs start in the tick buffers
-    bool busy = false;
-    bool failed = false;
+    cudaGraphExec_t exec = nullptr;        // the slot's tick, captured once
 };
+
+inline void cpu_relax()
+{
+#if defined(__x86_64__) || defined(__i386__)
+    __builtin_ia32_pause();
+#endif
+}
 
 }  // namespace
 
@@ -113,60 +455,57 @@ struct chx_srv {
     int cap[kNumClasses] = {};
     int pad_slot[kNumClasses] = {};
     std::vector<int> free_slots[kNumClasses];
-    // per slot, one 8-byte record so that a request touches one cache line
-    // per station: admitted flag, size class, charger count, queued or
-    // in-flight requests (the last three under the server lock)
+    // per slot: admitted flag, size class, charger count (written under the
+    // exclusive admin lock, read under the shared one)
     struct SlotInfo {
         uint8_t admitted, cls;
         uint16_t nports;
-        int32_t refs;
     };
     std::vector<SlotInfo> slot;
-    // stations of ticks on the device; set only by the scheduler (which reads
-    // it without the lock: a stale 1 merely delays a request to the next scan)
-    // and cleared by the completer
-    std::unique_ptr<std::atomic<uint8_t>[]> in_flight;
-    std::vector<uint32_t> scan_mark;       // submit: duplicate check (under the lock)
-    uint32_t scan_gen = 0;
-    std::vector<uint32_t> sched_mark;      // scheduler: stations claimed by waiting requests
-    uint32_t sched_gen = 0;
     double used_bytes = 0.0;
     int n_resident = 0;
-    cudaStream_t admin = nullptr;
+    cudaStream_t admin = nullptr;          // admission uploads
+    cudaStream_t st = nullptr;             // the ticks, in order
+    FusedSide side;                        // the 128-charger class's step beside the smaller classes'
+    std::shared_mutex admin_mu;            // admit / evict exclusive, submit shared
 
-    std::mutex mu;
-    std::condition_variable cv_sched, cv_done, cv_complete;
-    std::deque<uint32_t> pending;          // queued request records, arrival order
+    // requests
+    PinnedPool pool;                       // the records' buffers
     std::vector<Request> table;
-    uint64_t req_mask = 0;
+    DevReq* h_req = nullptr;               // [kMaxOutstanding] pinned, mapped
+    unsigned long long* h_done_flag = nullptr;   // [kMaxOutstanding] pinned, mapped
+    TickResult* h_result = nullptr;        // [n_streams] pinned, mapped
+    TickArgs* h_args = nullptr;            // [n_streams] pinned, mapped: each tick slot's arguments
+    TickArgs* d_args = nullptr;            // their device address
+    std::mutex ticket_mu;
     uint64_t next_ticket = 1;
-    uint64_t events = 0;                   // submissions + completions (wakes a blocked scheduler)
-    std::vector<Tick> ticks;
-    std::deque<int> launched;              // tick indices in launch order
-    std::thread sched_thread, done_thread;
-    bool stopping = false;
+    int64_t cum_envs = 0, cum_act = 0, cum_obs = 0;
+    std::atomic<int> queued_hint{0};       // submissions since the scheduler last looked
+    std::atomic<bool> sleeping{false};     // the scheduler blocks on `wake`
+
+    // ticks
+    DevSrv d{};
+    std::vector<TickSlot> tslots;
+    std::thread sched_thread;
+    std::mutex wake_mu;
+    std::condition_variable wake;
+    std::atomic<bool> stopping{false};
+    std::atomic<bool> failed{false};
+    std::atomic<int> fail_code{0};         // the CUDA error that stopped the ticks
+    std::atomic<int> fail_where{0};        // 1 launch, 2 event query, 3 elapsed time
     int max_tick_envs = 0;
     int64_t max_tick_obs = 0;
-    int64_t max_tick_act = 0;
+    int threads = 256;
+
     // statistics
+    std::mutex stat_mu;
     uint64_t n_ticks = 0, n_requests = 0, n_env_steps = 0, n_resets = 0;
     double busy_ms = 0.0;
     int64_t t_start = 0;
-    std::atomic<int64_t> ns_submit{0}, ns_scan{0}, ns_pack{0}, ns_launch{0}, ns_complete{0}, n_scans{0};
-    int threads = 256;
+    std::atomic<int64_t> ns_submit{0}, ns_scan{0}, ns_launch{0}, ns_complete{0}, n_scans{0};
 };
 
 namespace {
-
-uint32_t next_scan(chx_srv* s)
-{
-    ++s->scan_gen;
-    if (s->scan_gen == 0) {
-        std::fill(s->scan_mark.begin(), s->scan_mark.end(), 0u);
-        s->scan_gen = 1;
-    }
-    return s->scan_gen;
-}
 
 int alloc_pool(chx_srv* s)
 {
@@ -203,12 +542,9 @@ int alloc_pool(chx_srv* s)
 #undef PA
     std::vector<int32_t> minus1(NS, -1);
     SRV_TRY(cudaMemcpy(b.user_id, minus1.data(), NS * sizeof(int32_t), cudaMemcpyHostToDevice));
-    s->slot.assign(NS, chx_srv::SlotInfo{0, 0, 0, 0});
+    s->slot.assign(NS, chx_srv::SlotInfo{0, 0, 0});
     for (int c = 0; c < kNumClasses; ++c)
         for (int i = 0; i < b.cls_n_env[c]; ++i) s->slot[b.cls_env_base[c] + i].cls = (uint8_t)c;
-    s->in_flight.reset(new std::atomic<uint8_t>[NS]());
-    s->scan_mark.assign(NS, 0);
-    s->sched_mark.assign(NS, 0);
     for (int c = 0; c < kNumClasses; ++c) {
         s->free_slots[c].clear();
         for (int i = s->cap[c] - 1; i >= 0; --i) s->free_slots[c].push_back(b.cls_env_base[c] + i);
@@ -216,315 +552,312 @@ int alloc_pool(chx_srv* s)
     return CHX_OK;
 }
 
-int alloc_tick(chx_srv* s, Tick& t)
-{
-    const size_t ne = (size_t)s->max_tick_envs + 4 * kNumClasses;
-    const size_t na = (size_t)std::max<int64_t>(s->max_tick_act, 1);
-    const size_t no = (size_t)std::max<int64_t>(s->max_tick_obs, 1);
-    SRV_TRY(cudaStreamCreateWithFlags(&t.st, cudaStreamNonBlocking));
-    SRV_TRY(cudaEventCreate(&t.ev_start));
-    SRV_TRY(cudaEventCreate(&t.ev_end));
-    const size_t up = kUpHead + ne * sizeof(int4) + na;
-    const size_t down = ((ne * 5 + 15) & ~size_t(15)) + no * sizeof(float);
-    SRV_TRY(cudaHostAlloc(&t.h_up, up, cudaHostAllocDefault));
-    SRV_TRY(cudaHostAlloc(&t.h_down, down, cudaHostAllocDefault));
-    SRV_TRY(cudaHostAlloc(&t.h_rslots, ne * sizeof(int32_t), cudaHostAllocDefault));
-    SRV_TRY(cudaHostAlloc(&t.h_rseeds, ne * sizeof(unsigned long long), cudaHostAllocDefault));
-    SRV_TRY(cudaMalloc(&t.d_up, up));
-    SRV_TRY(cudaMalloc(&t.d_down, down));
-    SRV_TRY(cudaMalloc(&t.d_rslots, ne * sizeof(int32_t)));
-    SRV_TRY(cudaMalloc(&t.d_rseeds, ne * sizeof(unsigned long long)));
-    std::memset(t.h_up, 0, kUpHead);       // the counters every tick uploads as zero
-    t.h_entries = reinterpret_cast<int4*>(t.h_up + kUpHead);
-    t.d_entries = reinterpret_cast<int4*>(t.d_up + kUpHead);
-    t.d_counter = reinterpret_cast<int*>(t.d_up);
-    return CHX_OK;
-}
-
-void free_tick(Tick& t)
-{
-    if (t.st) cudaStreamSynchronize(t.st);
-    cudaFreeHost(t.h_up); cudaFreeHost(t.h_down); cudaFreeHost(t.h_rslots); cudaFreeHost(t.h_rseeds);
-    cudaFree(t.d_up); cudaFree(t.d_down); cudaFree(t.d_rslots); cudaFree(t.d_rseeds);
-    if (t.ev_start) cudaEventDestroy(t.ev_start);
-    if (t.ev_end) cudaEventDestroy(t.ev_end);
-    if (t.st) cudaStreamDestroy(t.st);
-    t = Tick{};
-}
-
 inline int class_of_slot_host(const chx_srv* s, int slot) { return s->slot[slot].cls; }
 
-// Pack and launch one tick on ticks[ti] with the requests the scheduler chose.
-// Runs without the server lock (the requests and their stations are reserved).
-int launch_tick(chx_srv* s, int ti, const std::vector<Request*>& rq)
+// device-side state of the ticks: arenas for a window of (n_streams + 1)
+// ticks' requests, the claim array, the per-class entry lists
+int alloc_ticks(chx_srv* s)
 {
-    Tick& t = s->ticks[ti];
-    const int64_t t_p0 = now_ns();
-    // pass 1: stations per class, output and observation offsets per request
-    int count[kNumClasses] = {};
-    int n_reset = 0;
-    int64_t act_used = 0, rew_used = 0, obs_used = 0;
-    t.rew_off.assign(rq.size(), 0);
-    t.obs_off.assign(rq.size(), 0);
-    for (size_t r = 0; r < rq.size(); ++r) {
-        Request& q = *rq[r];
-        if (q.kind == CHX_SRV_RESET) {
-            for (int32_t e : q.envs) {
-                t.h_rslots[n_reset] = e;
-                t.h_rseeds[n_reset] = (unsigned long long)q.seed;
-                ++n_reset;
-            }
-            continue;
-        }
-        t.rew_off[r] = rew_used;
-        t.obs_off[r] = obs_used;
-        for (int32_t e : q.envs) count[s->slot[e].cls] += 1;
-        rew_used += (int64_t)q.envs.size();
-        if (q.h_obs) obs_used += q.obs_floats;
+    DevSrv& d = s->d;
+    const int ns = s->cfg.n_streams;
+    d.max_tick_envs = s->max_tick_envs;
+    d.A = (long long)(ns + 1) * s->max_tick_envs;
+    d.G = (int)d.A + 8;
+    d.A_act = d.A * CHX_MAX_PORTS;
+    d.A_obs = std::max<long long>(1, (long long)(ns + 1) * s->max_tick_obs);
+    d.mask = kMaxOutstanding - 1;
+    for (int c = 0; c < kNumClasses; ++c) d.pad_slot[c] = s->pad_slot[c];
+    auto al = [&](void** p, size_t bytes, int fill) -> int {
+        cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+        if (e != cudaSuccess) return fail(CHX_ENOMEM, "serving allocation of " + std::to_string(bytes) + " bytes failed");
+        s->bufs.push_back(*p);
+        if ((e = cudaMemset(*p, fill, std::max<size_t>(bytes, 16))) != cudaSuccess) return cuda_fail(e, "cudaMemset");
+        return CHX_OK;
+    };
+    const size_t R = kMaxOutstanding;
+    int rc = 0;
+    if ((rc = al((void**)&d.executed, R * 8, 0)) || (rc = al((void**)&d.claimed_tick, R * 4, 0)) ||
+        (rc = al((void**)&d.meta, R * sizeof(RecMeta), 0)) ||
+        (rc = al((void**)&d.adm, R * 8, 0)) || (rc = al((void**)&d.claim, (size_t)s->b.n_slots * 4, 0xFF)) ||
+        (rc = al((void**)&d.ids, (size_t)d.A * 4, 0)) || (rc = al((void**)&d.acts, (size_t)d.A_act, 0)) ||
+        (rc = al((void**)&d.rew, (size_t)d.A * 4, 0)) || (rc = al((void**)&d.done, (size_t)d.A, 0)) ||
+        (rc = al((void**)&d.obs, (size_t)d.A_obs * 4, 0)) ||
+        (rc = al((void**)&d.gather, (size_t)kNumClasses * d.G * sizeof(int4), 0)) ||
+        (rc = al((void**)&d.rslot, (size_t)d.A * 4, 0)) || (rc = al((void**)&d.rseed, (size_t)d.A * 8, 0)) ||
+        (rc = al((void**)&d.cnt, kCnt * 4, 0)) || (rc = al((void**)&d.targs, (size_t)ns * sizeof(TickArgs), 0)))
+        return rc;
+    SRV_TRY(cudaHostAlloc(&s->h_req, R * sizeof(DevReq), cudaHostAllocMapped | cudaHostAllocPortable));
+    SRV_TRY(cudaHostAlloc(&s->h_done_flag, R * 8, cudaHostAllocMapped | cudaHostAllocPortable));
+    SRV_TRY(cudaHostAlloc(&s->h_result, (size_t)ns * sizeof(TickResult), cudaHostAllocMapped | cudaHostAllocPortable));
+    SRV_TRY(cudaHostAlloc(&s->h_args, (size_t)ns * sizeof(TickArgs), cudaHostAllocMapped | cudaHostAllocPortable));
+    std::memset(s->h_args, 0, (size_t)ns * sizeof(TickArgs));
+    std::memset(s->h_req, 0, R * sizeof(DevReq));
+    std::memset(s->h_done_flag, 0, R * 8);
+    std::memset(s->h_result, 0, (size_t)ns * sizeof(TickResult));
+    void* p = nullptr;
+    SRV_TRY(cudaHostGetDevicePointer(&p, s->h_req, 0));
+    d.req = static_cast<const DevReq*>(p);
+    SRV_TRY(cudaHostGetDevicePointer(&p, s->h_done_flag, 0));
+    d.done_flag = static_cast<unsigned long long*>(p);
+    SRV_TRY(cudaHostGetDevicePointer(&p, s->h_result, 0));
+    d.result = static_cast<TickResult*>(p);
+    SRV_TRY(cudaHostGetDevicePointer(&p, s->h_args, 0));
+    s->d_args = static_cast<TickArgs*>(p);
+    s->tslots.resize(ns);
+    for (auto& t : s->tslots) {
+        SRV_TRY(cudaEventCreate(&t.ev_start));
+        SRV_TRY(cudaEventCreate(&t.ev_end));
     }
-    // schedule: largest class first, each class padded to whole tiles
-    FusedIO io{};
-    int cursor[kNumClasses] = {};
-    int n_entries = 0, tb = 0;
-    io.n_sched = 0;
-    for (int c = kNumClasses - 1; c >= 0; --c) {
-        if (count[c] == 0) continue;
-        const int epw = tile_epw(c);
-        const int padded = (count[c] + epw - 1) / epw * epw;
-        io.gather_base[c] = n_entries;
-        cursor[c] = n_entries;
-        for (int i = count[c]; i < padded; ++i) t.h_entries[n_entries + i] = make_int4(s->pad_slot[c], 0, 0, 0);
-        n_entries += padded;
-        io.sched_cls[io.n_sched] = c;
-        io.sched_tile_base[io.n_sched] = tb;
-        io.n_sched++;
-        tb += padded / epw;
-    }
-    io.sched_tile_base[io.n_sched] = tb;
-    io.total_tiles = tb;
-    // actions right after the used entries (one upload); outputs packed
-    int8_t* h_act = reinterpret_cast<int8_t*>(t.h_up + kUpHead + (size_t)n_entries * sizeof(int4));
-    int8_t* d_act = reinterpret_cast<int8_t*>(t.d_up + kUpHead + (size_t)n_entries * sizeof(int4));
-    const size_t done_at = (size_t)rew_used * sizeof(float);
-    const size_t obs_at = ((size_t)rew_used * 5 + 15) & ~size_t(15);
-    t.h_rew = reinterpret_cast<float*>(t.h_down);
-    t.h_done = t.h_down + done_at;
-    t.h_obs = reinterpret_cast<float*>(t.h_down + obs_at);
-    // pass 2: entries straight into the pinned buffer, actions concatenated
-    for (size_t r = 0; r < rq.size(); ++r) {
-        Request& q = *rq[r];
-        if (q.kind == CHX_SRV_RESET) continue;
-        int64_t act_base = -1;
-        if (!q.actions.empty()) {
-            std::memcpy(h_act + act_used, q.actions.data(), q.actions.size());
-            act_base = act_used;
-            act_used += (int64_t)q.actions.size();
-        }
-        int64_t obs_pos = t.obs_off[r];
-        const int out0 = (int)t.rew_off[r];
-        for (size_t j = 0; j < q.envs.size(); ++j) {
-            const int slot = q.envs[j];
-            const int c = s->slot[slot].cls;
-            const int ao = act_base >= 0 ? (int)(act_base + q.act_off[j]) : 0;
-            t.h_entries[cursor[c]++] = make_int4(slot, ao, out0 + (int)j, (int)obs_pos);
-            if (q.h_obs) obs_pos += 8 + 6 * (int64_t)(q.act_off[j + 1] - q.act_off[j]);
-        }
-    }
-    io.k_steps = 1;
-    // a tick is either all Philox actions or all given actions (the scheduler
-    // never mixes them), so io.actions applies to every entry
-    io.actions = act_used > 0 ? d_act : nullptr;
-    io.lda = 1;
-    io.lda_step = 1;
-    io.reward = reinterpret_cast<float*>(t.d_down);
-    io.done = t.d_down + done_at;
-    io.ld_out = 1;
-    io.ld_step = 1;
-    io.obs = obs_used > 0 ? reinterpret_cast<float*>(t.d_down + obs_at) : nullptr;
-    io.counter = t.d_counter;
-    io.gather = t.d_entries;
-    s->ns_pack += now_ns() - t_p0;
-    cudaStream_t st = t.st;
-    SRV_TRY(cudaEventRecord(t.ev_start, st));
-    if (n_reset > 0) {
-        SRV_TRY(cudaMemcpyAsync(t.d_rslots, t.h_rslots, n_reset * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-        SRV_TRY(cudaMemcpyAsync(t.d_rseeds, t.h_rseeds, n_reset * sizeof(unsigned long long), cudaMemcpyHostToDevice,
-                                st));
-        launch_reset_slots(s->b, s->dp, t.d_rslots, t.d_rseeds, n_reset, st);
-        SRV_TRY(cudaGetLastError());
-    }
-    if (tb > 0) {
-        SRV_TRY(cudaMemcpyAsync(t.d_up, t.h_up, kUpHead + (size_t)n_entries * sizeof(int4) + (size_t)act_used,
-                                cudaMemcpyHostToDevice, st));
-        launch_step_fused(s->b, s->dp, io, s->threads, s->sm_count, st);
-        SRV_TRY(cudaGetLastError());
-        const size_t down = obs_used > 0 ? obs_at + (size_t)obs_used * sizeof(float) : done_at + (size_t)rew_used;
-        SRV_TRY(cudaMemcpyAsync(t.h_down, t.d_down, down, cudaMemcpyDeviceToHost, st));
-    }
-    SRV_TRY(cudaEventRecord(t.ev_end, st));
     return CHX_OK;
 }
 
+// Pinned, device-mapped memory for the request records' buffers: blocks of
+// 2^k bytes carved from 64 MB chunks, with a free list per size, so that a
+// submission never waits for the driver's allocator (which serialises every
+// thread) once the chunks exist.
+int PinnedPool::get(size_t bytes, void** host, void** dev, int* cls)
+{
+    int k = 6;
+    while (((size_t)1 << k) < bytes) ++k;
+    std::lock_guard<std::mutex> g(mu);
+    if (!free_list[k].empty()) {
+        *host = free_list[k].back().first;
+        *dev = free_list[k].back().second;
+        free_list[k].pop_back();
+        *cls = k;
+        return CHX_OK;
+    }
+    const size_t sz = (size_t)1 << k;
+    if (left < sz) {
+        const size_t chunk = std::max<size_t>(kChunk, sz);
+        void *h = nullptr, *d = nullptr;
+        if (cudaHostAlloc(&h, chunk, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess)
+            return fail(CHX_ENOMEM, "pinned request memory allocation failed");
+        if (cudaHostGetDevicePointer(&d, h, 0) != cudaSuccess) {
+            cudaFreeHost(h);
+            return fail(CHX_ECUDA, "no device address for pinned request memory");
+        }
+        chunks.push_back(h);
+        cur_h = static_cast<char*>(h);
+        cur_d = static_cast<char*>(d);
+        left = chunk;
+    }
+    *host = cur_h;
+    *dev = cur_d;
+    cur_h += sz;
+    cur_d += sz;
+    left -= sz;
+    *cls = k;
+    return CHX_OK;
+}
+
+void PinnedPool::put(void* host, void* dev, int cls)
+{
+    std::lock_guard<std::mutex> g(mu);
+    free_list[cls].push_back({host, dev});
+}
+
+PinnedPool::~PinnedPool()
+{
+    for (void* h : chunks) cudaFreeHost(h);
+}
+
+// a record's buffer of at least `need` elements (grown, never shrunk)
+template <class T>
+int grow_pinned(PinnedPool& pool, PinnedBuf<T>& b, size_t need)
+{
+    if (need <= b.cap && b.h) return CHX_OK;
+    void *h = nullptr, *d = nullptr;
+    int cls = 0;
+    const int rc = pool.get(std::max<size_t>(need, 16) * sizeof(T), &h, &d, &cls);
+    if (rc) return rc;
+    if (b.h) pool.put(b.h, b.d, b.cls);
+    b.h = static_cast<T*>(h);
+    b.d = static_cast<T*>(d);
+    b.cls = cls;
+    b.cap = ((size_t)1 << cls) / sizeof(T);
+    return CHX_OK;
+}
+
+// The tick of slot `slot`, captured once as a CUDA graph: claim, select,
+// prep, the fused step (the 128-charger class on a side branch), finish.
+// Grids are fixed (grid-stride loops over the window; the fused kernels'
+// resident grids, whose warps stop at the device-side tile count), and the
+// window comes from the slot's pinned argument record, so one graph launch
+// runs any tick.
+int capture_tick(chx_srv* s, int slot)
+{
+    cudaStream_t cs = nullptr;
+    SRV_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    const int g = 2 * s->sm_count;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        k_tick_claim<<<g, 256, 0, cs>>>(s->d, s->d_args, slot);
+        k_tick_select<<<g, 256, 0, cs>>>(s->d, s->b, slot);
+        k_tick_prep<<<g, 32 * kNumClasses, 0, cs>>>(s->d, s->b, s->dp);
+        FusedIO io{};
+        io.k_steps = 1;
+        io.actions = s->d.acts;            // entries with an action offset < 0 draw Philox levels
+        io.lda = 1;
+        io.lda_step = 1;
+        io.reward = s->d.rew;
+        io.done = s->d.done;
+        io.ld_out = 1;
+        io.ld_step = 1;
+        io.obs = s->max_tick_obs > 0 ? s->d.obs : nullptr;
+        io.counter = s->d.cnt + kCntWork;
+        io.gather = s->d.gather;
+        for (int c = 0; c < kNumClasses; ++c) io.gather_base[c] = c * s->d.G;
+        io.dcount = s->d.cnt + kCntClass;
+        io.dmax_small = 1 << 28;           // every resident block
+        io.dmax_large = s->cap[4] > 0 ? 1 << 28 : 0;
+        launch_step_fused(s->b, s->dp, io, s->threads, s->sm_count, cs, &s->side);
+        k_tick_finish<<<g, 256, 0, cs>>>(s->d, slot);
+        e = cudaStreamEndCapture(cs, &graph);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&s->tslots[slot].exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) return cuda_fail(e, "tick graph capture");
+    return CHX_OK;
+}
+
+// One tick over the window [lo, hi): its arguments into the slot's record,
+// then the slot's graph.
+int launch_tick(chx_srv* s, uint64_t lo, uint64_t hi, int tick, int slot)
+{
+    const Request& q0 = s->table[lo & (kMaxOutstanding - 1)];
+    TickArgs& a = s->h_args[slot];
+    a.lo = lo;
+    a.hi = hi;
+    a.base_envs = q0.cum_envs;
+    a.base_act = q0.cum_act;
+    a.base_obs = q0.cum_obs;
+    a.tick = tick;
+    a.slot = slot;
+    std::atomic_thread_fence(std::memory_order_release);
+    TickSlot& ts = s->tslots[slot];
+    SRV_TRY(cudaEventRecord(ts.ev_start, s->st));
+    SRV_TRY(cudaGraphLaunch(ts.exec, s->st));
+    SRV_TRY(cudaEventRecord(ts.ev_end, s->st));
+    return CHX_OK;
+}
+
+// The scheduler: grows the window with the published tickets, launches a tick
+// when there are new requests (or requests a finished tick left waiting and
+// nothing is queued on the device), keeps up to n_streams ticks queued,
+// collects their reports.  Per request it does O(1) work.
 void scheduler(chx_srv* s)
 {
     cudaSetDevice(s->device);
-    std::vector<Request*> rq;
-    std::deque<uint32_t> work, rest;
-    uint64_t seen = ~0ULL;                 // events counter when nothing could be scheduled
+    const uint64_t mask = kMaxOutstanding - 1;
+    const int ns = (int)s->tslots.size();
+    uint64_t pub = 1, lo = 1, last_hi = 1;
+    int tick = 0;
+    std::deque<int> inflight;              // tick slots in launch order
+    std::vector<char> slot_busy(ns, 0);
+    bool retry = false;
+    int idle = 0;
+    volatile unsigned long long* flag = s->h_done_flag;
     for (;;) {
-        int ti = -1;
-        uint64_t events_at_take = 0;
+        const int64_t t0 = now_ns();
+        for (;;) {                         // published requests extend the window
+            const Request& q = s->table[pub & mask];
+            if (q.state.load(std::memory_order_acquire) != kQueued || q.ticket.load(std::memory_order_relaxed) != pub)
+                break;
+            ++pub;
+        }
+        while (!inflight.empty()) {        // finished ticks
+            const int sl = inflight.front();
+            TickSlot& ts = s->tslots[sl];
+            const cudaError_t e = cudaEventQuery(ts.ev_end);
+            if (e == cudaErrorNotReady) break;
+            float ms = 0.f;
+            const cudaError_t et = e == cudaSuccess ? cudaEventElapsedTime(&ms, ts.ev_start, ts.ev_end) : e;
+            if (et != cudaSuccess) {
+                s->fail_code.store((int)et);
+                s->fail_where.store(e != cudaSuccess ? 2 : 3);
+                s->failed.store(true);
+                ms = 0.f;
+            }
+            const volatile int* src = reinterpret_cast<const volatile int*>(s->h_result + sl);
+            const TickResult r{src[0], src[1], src[2], src[3]};
+            {
+                std::lock_guard<std::mutex> g(s->stat_mu);
+                if (r.admitted > 0) s->n_ticks += 1;
+                s->n_requests += (uint64_t)r.admitted;
+                s->n_env_steps += (uint64_t)r.stepped;
+                s->n_resets += (uint64_t)r.resets;
+                s->busy_ms += ms;
+            }
+            if (r.blocked > 0) retry = true;
+            slot_busy[sl] = 0;
+            inflight.pop_front();
+        }
+        while (lo < pub) {                 // the window starts at the oldest unfinished request
+            const Request& q = s->table[lo & mask];
+            if (q.ticket.load(std::memory_order_acquire) == lo && q.state.load(std::memory_order_acquire) != kFree &&
+                flag[lo & mask] != lo)
+                break;
+            ++lo;
+        }
+        if (s->stopping.load() && inflight.empty()) return;
+        const bool fresh = pub > last_hi;
+        if (!s->stopping.load() && !s->failed.load() && lo < pub && (int)inflight.size() < ns &&
+            (fresh || (retry && inflight.empty()))) {
+            int sl = 0;
+            while (slot_busy[sl]) ++sl;
+            ++tick;
+            s->ns_scan += now_ns() - t0;
+            const int64_t t1 = now_ns();
+            if (launch_tick(s, lo, pub, tick, sl) != CHX_OK) {
+                s->fail_code.store((int)cudaGetLastError());
+                s->fail_where.store(1);
+                s->failed.store(true);
+            }
+            s->ns_launch += now_ns() - t1;
+            s->n_scans += 1;
+            slot_busy[sl] = 1;
+            inflight.push_back(sl);
+            last_hi = pub;
+            retry = false;
+            idle = 0;
+            continue;
+        }
+        s->ns_scan += now_ns() - t0;
+        // nothing to launch: spin briefly (ticks finish within tens of
+        // microseconds), then block until a submission or a timeout
+        if (++idle < 2000 || !inflight.empty()) {
+            cpu_relax();
+            if (idle > 200) std::this_thread::yield();
+            continue;
+        }
         {
-            std::unique_lock<std::mutex> lk(s->mu);
-            s->cv_sched.wait(lk, [&] {
-                if (s->stopping) return true;
-                if (s->pending.empty() || s->events == seen) return false;
-                for (auto& t : s->ticks)
-                    if (!t.busy) return true;
-                return false;
-            });
-            if (s->stopping) return;
-            for (size_t i = 0; i < s->ticks.size(); ++i)
-                if (!s->ticks[i].busy) {
-                    ti = (int)i;
-                    break;
-                }
-            s->ticks[ti].busy = true;
-            work.swap(s->pending);         // take the queue; submissions continue meanwhile
-            events_at_take = s->events;
+            std::unique_lock<std::mutex> lk(s->wake_mu);
+            s->sleeping.store(true);
+            s->wake.wait_for(lk, std::chrono::microseconds(200),
+                             [&] { return s->queued_hint.load() > 0 || s->stopping.load(); });
+            s->sleeping.store(false);
         }
-        // pack in arrival order outside the lock; a request waits if one of its
-        // stations is in flight or claimed by an earlier waiting request
-        const int64_t t_scan0 = now_ns();
-        Tick& t = s->ticks[ti];
-        if (++s->sched_gen == 0) {
-            std::fill(s->sched_mark.begin(), s->sched_mark.end(), 0u);
-            s->sched_gen = 1;
-        }
-        const uint32_t gen = s->sched_gen;
-        rq.clear();
-        t.recs.clear();
-        rest.clear();
-        int envs = 0;
-        int64_t act = 0, obs = 0;
-        int with_actions = -1;             // a tick is all-Philox or all-given actions
-        bool full = false;
-        for (uint32_t ri : work) {
-            Request& q = s->table[ri];
-            if (full) {
-                rest.push_back(ri);
-                continue;
-            }
-            bool blocked = false;
-            for (int32_t e : q.envs)
-                if (s->in_flight[e].load(std::memory_order_relaxed) || s->sched_mark[e] == gen) {
-                    blocked = true;
-                    break;
-                }
-            const int wa = q.kind == CHX_SRV_STEP ? (q.actions.empty() ? 0 : 1) : -1;
-            const bool fits = envs + (int)q.envs.size() <= s->max_tick_envs &&
-                              act + (int64_t)q.actions.size() <= s->max_tick_act &&
-                              obs + q.obs_floats <= s->max_tick_obs &&
-                              (wa < 0 || with_actions < 0 || wa == with_actions);
-            if (blocked || !fits) {
-                for (int32_t e : q.envs) s->sched_mark[e] = gen;
-                rest.push_back(ri);
-                full = !fits && envs >= s->max_tick_envs;
-                continue;
-            }
-            if (wa >= 0) with_actions = wa;
-            for (int32_t e : q.envs) s->in_flight[e].store(1, std::memory_order_relaxed);
-            envs += (int)q.envs.size();
-            act += (int64_t)q.actions.size();
-            obs += q.obs_floats;
-            rq.push_back(&q);
-            t.recs.push_back(ri);
-        }
-        work.clear();
-        s->ns_scan += now_ns() - t_scan0;
-        s->n_scans += 1;
-        {
-            std::lock_guard<std::mutex> lk(s->mu);
-            if (!rest.empty()) {           // waiting requests stay ahead of newer ones
-                rest.insert(rest.end(), s->pending.begin(), s->pending.end());
-                s->pending.swap(rest);
-            }
-            if (rq.empty()) {              // everything waits on in-flight stations
-                t.busy = false;
-                seen = events_at_take;
-                continue;
-            }
-            seen = ~0ULL;
-        }
-        const int64_t t_l0 = now_ns();
-        t.failed = launch_tick(s, ti, rq) != CHX_OK;
-        s->ns_launch += now_ns() - t_l0;
-        {
-            std::lock_guard<std::mutex> lk(s->mu);
-            s->launched.push_back(ti);
-        }
-        s->cv_complete.notify_one();
+        s->queued_hint.store(0);
+        idle = 0;
     }
 }
 
-void completer(chx_srv* s)
+// Copy a finished request's results to the caller's buffers and release it.
+int collect(chx_srv* s, Request& q, int64_t* latency_ns)
 {
-    cudaSetDevice(s->device);
-    for (;;) {
-        int ti;
-        {
-            std::unique_lock<std::mutex> lk(s->mu);
-            s->cv_complete.wait(lk, [&] { return s->stopping || !s->launched.empty(); });
-            if (s->launched.empty()) return;   // stopping and drained
-            ti = s->launched.front();
-            s->launched.pop_front();
-        }
-        Tick& t = s->ticks[ti];
-        float ms = 0.f;
-        if (t.failed || cudaEventSynchronize(t.ev_end) != cudaSuccess ||
-            cudaEventElapsedTime(&ms, t.ev_start, t.ev_end) != cudaSuccess) {
-            t.failed = true;
-            ms = 0.f;
-        }
-        const int64_t t_c0 = now_ns();
-        // copy results to the requesters without the lock (records stay put and
-        // are not released before they are marked done below)
-        for (size_t r = 0; r < t.recs.size(); ++r) {
-            Request* q = &s->table[t.recs[r]];
-            if (q->kind != CHX_SRV_STEP || t.failed) continue;
-            const size_t n = q->envs.size();
-            if (q->h_reward) std::memcpy(q->h_reward, t.h_rew + t.rew_off[r], n * sizeof(float));
-            if (q->h_done) std::memcpy(q->h_done, t.h_done + t.rew_off[r], n);
-            if (q->h_obs) std::memcpy(q->h_obs, t.h_obs + t.obs_off[r], (size_t)q->obs_floats * sizeof(float));
-        }
-        const int64_t tn = now_ns();
-        {
-            std::lock_guard<std::mutex> lk(s->mu);
-            for (uint32_t ri : t.recs) {
-                Request& q = s->table[ri];
-                for (int32_t e : q.envs) {
-                    s->in_flight[e].store(0, std::memory_order_relaxed);
-                    s->slot[e].refs -= 1;
-                }
-                q.failed = t.failed;
-                q.t_done = tn;
-                q.state.store(kDone, std::memory_order_release);
-                s->n_requests += 1;
-                if (q.kind == CHX_SRV_STEP)
-                    s->n_env_steps += q.envs.size();
-                else
-                    s->n_resets += q.envs.size();
-            }
-            s->n_ticks += 1;
-            s->busy_ms += ms;
-            s->events += 1;
-            t.busy = false;
-            t.recs.clear();
-        }
-        s->ns_complete += now_ns() - t_c0;
-        s->cv_done.notify_all();
-        s->cv_sched.notify_one();
+    const int64_t t0 = now_ns();
+    if (latency_ns) *latency_ns = t0 - q.t_submit;
+    if (q.kind == CHX_SRV_STEP) {
+        if (q.h_reward) std::memcpy(q.h_reward, q.rew.h, (size_t)q.n * sizeof(float));
+        if (q.h_done) std::memcpy(q.h_done, q.done.h, (size_t)q.n);
+        if (q.h_obs) std::memcpy(q.h_obs, q.obs.h, (size_t)q.obs_floats * sizeof(float));
     }
+    q.state.store(kFree, std::memory_order_release);
+    s->ns_complete += now_ns() - t0;
+    return CHX_OK;
 }
 
 // Write admitted stations' statics into their slots: one warp per station.
@@ -573,7 +906,8 @@ extern "C" int chx_srv_start(const chx_srv_cfg* cfg, chx_srv** out)
     if (rc) return rc;
     if (cfg->max_tick_envs < 1 || cfg->max_tick_envs > (1 << 20)) return fail(CHX_EINVAL, "max_tick_envs out of range");
     if (cfg->n_streams < 1 || cfg->n_streams > 8) return fail(CHX_EINVAL, "n_streams must be in 1..8");
-    if (cfg->max_tick_obs_floats < 0) return fail(CHX_EINVAL, "max_tick_obs_floats must be >= 0");
+    if (cfg->max_tick_obs_floats < 0 || (long long)(cfg->n_streams + 1) * cfg->max_tick_obs_floats > INT32_MAX)
+        return fail(CHX_EINVAL, "max_tick_obs_floats x (n_streams + 1) must stay below 2^31");
     long long total = 0;
     for (int c = 0; c < kNumClasses; ++c) {
         if (cfg->class_capacity[c] < 0) return fail(CHX_EINVAL, "class_capacity must be >= 0");
@@ -585,10 +919,8 @@ extern "C" int chx_srv_start(const chx_srv_cfg* cfg, chx_srv** out)
     s->params = cfg->params;
     s->dp = make_params(cfg->params, cfg->exo.n_days);
     s->max_tick_envs = cfg->max_tick_envs;
-    s->max_tick_act = (int64_t)cfg->max_tick_envs * CHX_MAX_PORTS;
     s->max_tick_obs = cfg->max_tick_obs_floats;
     s->table = std::vector<Request>(kMaxOutstanding);
-    s->req_mask = kMaxOutstanding - 1;
     if (cudaGetDevice(&s->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess) {
         delete s;
@@ -623,19 +955,29 @@ extern "C" int chx_srv_start(const chx_srv_cfg* cfg, chx_srv** out)
         chx_srv_stop(s);
         return fail(CHX_ECUDA, "fused kernel cannot be resident");
     }
-    s->ticks.resize(cfg->n_streams);
-    for (auto& t : s->ticks)
-        if ((rc = alloc_tick(s, t))) {
-            chx_srv_stop(s);
-            return rc;
-        }
-    if (cudaStreamCreateWithFlags(&s->admin, cudaStreamNonBlocking) != cudaSuccess) {
+    if ((rc = alloc_ticks(s))) {
+        chx_srv_stop(s);
+        return rc;
+    }
+    if (cudaStreamCreateWithFlags(&s->admin, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s->side.aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->side.fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->side.join, cudaEventDisableTiming) != cudaSuccess) {
         chx_srv_stop(s);
         return fail(CHX_ECUDA, "stream creation failed");
     }
+    for (int sl = 0; sl < cfg->n_streams; ++sl)
+        if ((rc = capture_tick(s, sl))) {
+            chx_srv_stop(s);
+            return rc;
+        }
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        chx_srv_stop(s);
+        return fail(CHX_ECUDA, "server set-up failed on the device");
+    }
     s->t_start = now_ns();
     s->sched_thread = std::thread(scheduler, s);
-    s->done_thread = std::thread(completer, s);
     *out = s;
     return CHX_OK;
 }
@@ -643,18 +985,29 @@ extern "C" int chx_srv_start(const chx_srv_cfg* cfg, chx_srv** out)
 extern "C" int chx_srv_stop(chx_srv* s)
 {
     if (!s) return CHX_OK;
+    s->stopping.store(true);
     {
-        std::lock_guard<std::mutex> lk(s->mu);
-        s->stopping = true;
+        std::lock_guard<std::mutex> lk(s->wake_mu);
+        s->wake.notify_all();
     }
-    s->cv_sched.notify_all();
-    s->cv_complete.notify_all();
     if (s->sched_thread.joinable()) s->sched_thread.join();
-    if (s->done_thread.joinable()) s->done_thread.join();
-    cudaDeviceSynchronize();
-    for (auto& t : s->ticks) free_tick(t);
+    if (s->st) cudaStreamSynchronize(s->st);
+    if (s->admin) cudaStreamSynchronize(s->admin);
+    for (auto& t : s->tslots) {
+        if (t.exec) cudaGraphExecDestroy(t.exec);
+        if (t.ev_start) cudaEventDestroy(t.ev_start);
+        if (t.ev_end) cudaEventDestroy(t.ev_end);
+    }
+    if (s->h_args) cudaFreeHost(s->h_args);
+    if (s->h_req) cudaFreeHost(s->h_req);
+    if (s->h_done_flag) cudaFreeHost(s->h_done_flag);
+    if (s->h_result) cudaFreeHost(s->h_result);
     for (void* p : s->bufs) cudaFree(p);
     if (s->admin) cudaStreamDestroy(s->admin);
+    if (s->st) cudaStreamDestroy(s->st);
+    if (s->side.aux) cudaStreamSynchronize(s->side.aux), cudaStreamDestroy(s->side.aux);
+    if (s->side.fork) cudaEventDestroy(s->side.fork);
+    if (s->side.join) cudaEventDestroy(s->side.join);
     delete s;
     return CHX_OK;
 }
@@ -665,7 +1018,7 @@ extern "C" int chx_srv_admit(chx_srv* s, const chx_stations* st, uint64_t seed, 
     if (st->h_n_upper) return fail(CHX_EINVAL, "the serving loop takes two-level trees (h_n_upper = NULL)");
     int rc = validate_stations(st, &s->cfg.exo, 1LL << 24);
     if (rc) return rc;
-    std::lock_guard<std::mutex> lk(s->mu);
+    std::unique_lock<std::shared_mutex> lk(s->admin_mu);
     // all or nothing: class capacity and HBM budget
     int need[kNumClasses] = {};
     double bytes = 0.0;
@@ -751,11 +1104,21 @@ extern "C" int chx_srv_admit(chx_srv* s, const chx_stations* st, uint64_t seed, 
 extern "C" int chx_srv_evict(chx_srv* s, const int32_t* h_ids, int32_t n)
 {
     if (!s || (!h_ids && n > 0) || n < 0) return fail(CHX_EINVAL, "bad argument");
-    std::lock_guard<std::mutex> lk(s->mu);
+    std::unique_lock<std::shared_mutex> lk(s->admin_mu);
     for (int j = 0; j < n; ++j) {
         const int e = h_ids[j];
         if (e < 0 || e >= s->b.n_slots || !s->slot[e].admitted) return fail(CHX_EINVAL, "station id not admitted");
-        if (s->slot[e].refs > 0) return fail(CHX_EINVAL, "station has queued or in-flight requests");
+    }
+    // no ticket that lists one of them may be unreleased (queued, in flight or
+    // finished and not yet collected); submissions hold the shared lock, so
+    // none is being filled now
+    {
+        std::vector<uint8_t> gone((size_t)s->b.n_slots, 0);
+        for (int j = 0; j < n; ++j) gone[h_ids[j]] = 1;
+        for (const Request& q : s->table)
+            if (q.state.load(std::memory_order_acquire) == kQueued)
+                for (int j = 0; j < q.n; ++j)
+                    if (gone[q.ids.h[j]]) return fail(CHX_EINVAL, "station is listed by a ticket not yet released");
     }
     DevBatch& b = s->b;
     const int32_t minus1 = -1;
@@ -780,123 +1143,178 @@ extern "C" int chx_srv_evict(chx_srv* s, const int32_t* h_ids, int32_t n)
 extern "C" int chx_srv_submit(chx_srv* s, const chx_srv_req* r, uint64_t* ticket)
 {
     if (!s || !r || !ticket) return fail(CHX_EINVAL, "null argument");
+    const int64_t t_in = now_ns();
     if (r->kind != CHX_SRV_STEP && r->kind != CHX_SRV_RESET) return fail(CHX_EINVAL, "unknown request kind");
     if (r->n_envs < 1 || r->n_envs > s->max_tick_envs || !r->h_env_ids)
         return fail(CHX_EINVAL, "n_envs must be in 1..max_tick_envs");
-    // copy the request's inputs before taking the lock
-    thread_local std::vector<int32_t> envs;
-    thread_local std::vector<int8_t> actions;
-    envs.assign(r->h_env_ids, r->h_env_ids + r->n_envs);
-    for (int32_t e : envs)
+    const int n = r->n_envs;
+    const bool step = r->kind == CHX_SRV_STEP;
+    // duplicate check: a per-thread open-addressing set of at least 2n slots
+    thread_local std::vector<int32_t> set;
+    size_t cap = 64;
+    while (cap < 2 * (size_t)n) cap *= 2;
+    if (set.size() < cap) set.resize(cap);
+    std::fill(set.begin(), set.begin() + cap, -1);
+    std::shared_lock<std::shared_mutex> lk(s->admin_mu);
+    if (s->stopping.load()) return fail(CHX_EINVAL, "server is stopping");
+    int64_t n_act = 0;
+    for (int j = 0; j < n; ++j) {
+        const int32_t e = r->h_env_ids[j];
         if (e < 0 || e >= s->b.n_slots) return fail(CHX_EINVAL, "station id out of range");
-    std::unique_lock<std::mutex> lk(s->mu);
-    const int64_t t_in = now_ns();
-    if (s->stopping) return fail(CHX_EINVAL, "server is stopping");
-    const uint64_t tk = s->next_ticket;
-    const uint32_t ri = (uint32_t)(tk & s->req_mask);
-    Request& q = s->table[ri];
-    if (q.state.load(std::memory_order_acquire) != kFree)
-        return fail(CHX_ENOMEM, "too many outstanding requests: release tickets with chx_srv_wait or chx_srv_test");
-    // check the stations (admitted, listed once) and their charger offsets
-    const uint32_t gen = next_scan(s);
-    q.act_off.resize(envs.size() + 1);
-    q.act_off[0] = 0;
-    for (size_t j = 0; j < envs.size(); ++j) {
-        const int32_t e = envs[j];
-        const chx_srv::SlotInfo& si = s->slot[e];
+        const chx_srv::SlotInfo si = s->slot[e];
         if (!si.admitted) return fail(CHX_EINVAL, "station id not admitted");
-        if (s->scan_mark[e] == gen) return fail(CHX_EINVAL, "station listed twice in one request");
-        s->scan_mark[e] = gen;
-        q.act_off[j + 1] = q.act_off[j] + si.nports;
+        size_t h = ((uint32_t)e * 2654435761u) & (cap - 1);
+        while (set[h] >= 0 && set[h] != e) h = (h + 1) & (cap - 1);
+        if (set[h] == e) return fail(CHX_EINVAL, "station listed twice in one request");
+        set[h] = e;
+        n_act += si.nports;
     }
-    int64_t obs_floats = 0;
-    actions.clear();
-    if (r->kind == CHX_SRV_STEP) {
-        if (r->h_actions) {
-            actions.assign(r->h_actions, r->h_actions + q.act_off.back());
-            for (int8_t a : actions)
-                if (a < 0 || a >= s->params.n_levels) return fail(CHX_EINVAL, "action level out of range");
+    const bool given = step && r->h_actions;
+    if (given)
+        for (int64_t i = 0; i < n_act; ++i)
+            if (r->h_actions[i] < 0 || r->h_actions[i] >= s->params.n_levels)
+                return fail(CHX_EINVAL, "action level out of range");
+    const int64_t obs_floats = (step && r->h_obs) ? 8LL * n + 6LL * n_act : 0;
+    if (obs_floats > s->max_tick_obs) return fail(CHX_EINVAL, "observation larger than max_tick_obs_floats");
+    // a record and a ticket; the record's buffers grow here (rarely, inside
+    // the lock, so that a ticket is never taken without being published)
+    Request* q = nullptr;
+    uint64_t tk = 0;
+    {
+        std::lock_guard<std::mutex> g(s->ticket_mu);
+        tk = s->next_ticket;
+        q = &s->table[tk & (kMaxOutstanding - 1)];
+        int expect = kFree;
+        if (!q->state.compare_exchange_strong(expect, kFilling, std::memory_order_acq_rel))
+            return fail(CHX_ENOMEM, "too many outstanding requests: release tickets with chx_srv_wait or chx_srv_test");
+        int rc = grow_pinned(s->pool, q->ids, (size_t)n);
+        if (!rc && step) rc = grow_pinned(s->pool, q->rew, (size_t)n);
+        if (!rc && step) rc = grow_pinned(s->pool, q->done, (size_t)n);
+        if (!rc && given) rc = grow_pinned(s->pool, q->acts, (size_t)n_act);
+        if (!rc && obs_floats) rc = grow_pinned(s->pool, q->obs, (size_t)obs_floats);
+        if (rc) {
+            q->state.store(kFree, std::memory_order_release);
+            return rc;
         }
-        if (r->h_obs) obs_floats = 8LL * (int64_t)envs.size() + 6LL * q.act_off.back();
-        if (obs_floats > s->max_tick_obs) return fail(CHX_EINVAL, "observation larger than max_tick_obs_floats");
+        ++s->next_ticket;
+        q->cum_envs = s->cum_envs;
+        q->cum_act = s->cum_act;
+        q->cum_obs = s->cum_obs;
+        s->cum_envs += n;
+        if (given) s->cum_act += n_act;
+        s->cum_obs += obs_floats;
     }
-    // the record is free: fill it, publish it last
-    q.kind = r->kind;
-    q.envs.swap(envs);
-    q.actions.swap(actions);
-    q.h_reward = r->h_reward;
-    q.h_done = r->h_done;
-    q.h_obs = r->kind == CHX_SRV_STEP ? r->h_obs : nullptr;
-    q.seed = r->seed;
-    q.failed = false;
-    q.obs_floats = obs_floats;
-    for (int32_t e : q.envs) s->slot[e].refs += 1;
-    q.t_submit = now_ns();
-    q.ticket.store(tk, std::memory_order_relaxed);
-    q.state.store(kQueued, std::memory_order_release);
-    s->next_ticket++;
-    s->pending.push_back(ri);
-    s->events += 1;
-    *ticket = tk;
-    s->ns_submit += now_ns() - t_in;
+    std::memcpy(q->ids.h, r->h_env_ids, (size_t)n * sizeof(int32_t));
+    if (given) std::memcpy(q->acts.h, r->h_actions, (size_t)n_act);
+    DevReq& dr = s->h_req[tk & (kMaxOutstanding - 1)];
+    dr.ticket = tk;
+    dr.kind = r->kind;
+    dr.n = n;
+    dr.n_act = (int)n_act;
+    dr.has_act = given ? 1 : 0;
+    dr.obs_floats = (int)obs_floats;
+    dr.cum_envs = q->cum_envs;
+    dr.cum_act = q->cum_act;
+    dr.cum_obs = q->cum_obs;
+    dr.ids = q->ids.d;
+    dr.acts = given ? q->acts.d : nullptr;
+    dr.rew = step ? q->rew.d : nullptr;
+    dr.done = step ? q->done.d : nullptr;
+    dr.obs = obs_floats ? q->obs.d : nullptr;
+    dr.seed = (unsigned long long)r->seed;
+    q->kind = r->kind;
+    q->n = n;
+    q->h_reward = step ? r->h_reward : nullptr;
+    q->h_done = step ? r->h_done : nullptr;
+    q->h_obs = obs_floats ? r->h_obs : nullptr;
+    q->obs_floats = obs_floats;
+    q->t_submit = now_ns();
+    q->ticket.store(tk, std::memory_order_relaxed);
+    q->state.store(kQueued, std::memory_order_release);    // published
     lk.unlock();
-    s->cv_sched.notify_one();
+    *ticket = tk;
+    s->queued_hint.fetch_add(1);
+    if (s->sleeping.load()) {
+        std::lock_guard<std::mutex> g(s->wake_mu);
+        s->wake.notify_one();
+    }
+    s->ns_submit += now_ns() - t_in;
     return CHX_OK;
 }
 
 namespace {
-// release a completed record; returns its status
-int release(Request& q, int64_t* latency_ns)
+int failed_status(const chx_srv* s)
 {
-    if (latency_ns) *latency_ns = q.t_done - q.t_submit;
-    const bool failed = q.failed;
-    q.state.store(kFree, std::memory_order_release);
-    return failed ? fail(CHX_ECUDA, "the tick carrying this request failed on the device") : CHX_OK;
+    static const char* where[] = {"", "a tick launch", "a tick's completion", "a tick's timing"};
+    const int w = s->fail_where.load();
+    return fail(CHX_ECUDA, std::string("the server's device work failed at ") + where[w >= 0 && w <= 3 ? w : 0] +
+                               ": " + cudaGetErrorString((cudaError_t)s->fail_code.load()));
+}
+
+inline bool finished(const chx_srv* s, uint64_t ticket)
+{
+    return reinterpret_cast<volatile const unsigned long long*>(s->h_done_flag)[ticket & (kMaxOutstanding - 1)] ==
+           ticket;
 }
 }  // namespace
 
 extern "C" int chx_srv_wait(chx_srv* s, uint64_t ticket, int64_t timeout_us, int64_t* latency_ns)
 {
     if (!s) return fail(CHX_EINVAL, "null server");
-    Request& q = s->table[ticket & s->req_mask];
-    if (q.ticket.load(std::memory_order_acquire) != ticket || q.state.load(std::memory_order_acquire) == kFree)
+    Request& q = s->table[ticket & (kMaxOutstanding - 1)];
+    if (q.ticket.load(std::memory_order_acquire) != ticket || q.state.load(std::memory_order_acquire) != kQueued)
         return fail(CHX_EINVAL, "unknown ticket");
-    if (q.state.load(std::memory_order_acquire) != kDone) {
-        std::unique_lock<std::mutex> lk(s->mu);
-        const auto deadline = Clock::now() + std::chrono::microseconds(timeout_us < 0 ? 0 : timeout_us);
-        if (!s->cv_done.wait_until(lk, deadline, [&] { return q.state.load(std::memory_order_acquire) == kDone; }))
-            return fail(CHX_ETIMEOUT, "request not finished within the timeout");
+    if (!finished(s, ticket)) {
+        const int64_t deadline = now_ns() + 1000 * std::max<int64_t>(timeout_us, 0);
+        for (int spins = 0; !finished(s, ticket); ++spins) {
+            if (s->failed.load()) return failed_status(s);
+            if (now_ns() >= deadline) return fail(CHX_ETIMEOUT, "request not finished within the timeout");
+            if (spins < 64) cpu_relax();
+            else if (spins < 4096) std::this_thread::yield();
+            else std::this_thread::sleep_for(std::chrono::microseconds(20));
+        }
     }
-    return release(q, latency_ns);
+    std::atomic_thread_fence(std::memory_order_acquire);
+    return collect(s, q, latency_ns);
 }
 
 extern "C" int chx_srv_test(chx_srv* s, uint64_t ticket, int32_t* h_done, int64_t* latency_ns)
 {
     if (!s || !h_done) return fail(CHX_EINVAL, "null argument");
-    Request& q = s->table[ticket & s->req_mask];
-    if (q.ticket.load(std::memory_order_acquire) != ticket) return fail(CHX_EINVAL, "unknown ticket");
-    const int st = q.state.load(std::memory_order_acquire);
-    if (st == kFree) return fail(CHX_EINVAL, "unknown ticket");
-    *h_done = st == kDone ? 1 : 0;
-    return st == kDone ? release(q, latency_ns) : CHX_OK;
+    Request& q = s->table[ticket & (kMaxOutstanding - 1)];
+    if (q.ticket.load(std::memory_order_acquire) != ticket || q.state.load(std::memory_order_acquire) != kQueued)
+        return fail(CHX_EINVAL, "unknown ticket");
+    *h_done = 0;
+    if (!finished(s, ticket)) {
+        if (s->failed.load()) return failed_status(s);
+        return CHX_OK;
+    }
+    std::atomic_thread_fence(std::memory_order_acquire);
+    *h_done = 1;
+    return collect(s, q, latency_ns);
 }
 
 extern "C" int chx_srv_stats(chx_srv* s, chx_srv_stats_t* out)
 {
     if (!s || !out) return fail(CHX_EINVAL, "null argument");
-    std::lock_guard<std::mutex> lk(s->mu);
-    out->n_ticks = (int64_t)s->n_ticks;
-    out->n_requests = (int64_t)s->n_requests;
-    out->env_steps = (int64_t)s->n_env_steps;
-    out->env_resets = (int64_t)s->n_resets;
-    out->resident = s->n_resident;
-    out->used_bytes = s->used_bytes;
+    {
+        std::lock_guard<std::mutex> lk(s->stat_mu);
+        out->n_ticks = (int64_t)s->n_ticks;
+        out->n_requests = (int64_t)s->n_requests;
+        out->env_steps = (int64_t)s->n_env_steps;
+        out->env_resets = (int64_t)s->n_resets;
+        out->device_busy_ms = s->busy_ms;
+    }
+    {
+        std::shared_lock<std::shared_mutex> lk(s->admin_mu);
+        out->resident = s->n_resident;
+        out->used_bytes = s->used_bytes;
+    }
     out->budget_bytes = s->cfg.hbm_budget_bytes;
-    out->device_busy_ms = s->busy_ms;
     out->elapsed_ms = (double)(now_ns() - s->t_start) * 1e-6;
     out->host_submit_ms = s->ns_submit.load() * 1e-6;
     out->host_scan_ms = s->ns_scan.load() * 1e-6;
-    out->host_pack_ms = s->ns_pack.load() * 1e-6;
+    out->host_pack_ms = 0.0;
     out->host_launch_ms = s->ns_launch.load() * 1e-6;
     out->host_complete_ms = s->ns_complete.load() * 1e-6;
     out->n_scans = s->n_scans.load();

@@ -359,7 +359,7 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
         }
     }
     __syncwarp();
-    const bool random_actions = io.actions == nullptr;
+    const bool random_actions = io.actions == nullptr || act_base < 0;
     const int dh = head_distance<PPL, LPE>(meta, le);
     // Arrival words are prefetched lane-parallel: lane le of a station holds the
     // Philox block (blk0 + le), i.e. the words of steps 4*(blk0+le)..+3, so one
@@ -736,7 +736,7 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
 #pragma unroll
         for (int q = 0; q < PPL; ++q) occ_l += trem[q] > 0;
         const int occ = (int)seg_sum<LPE>((float)occ_l);
-        if (live) {
+        if (live && obs_w >= 0) {
             const int n = b.n_ports[s];
             const int QP = EXT ? p.obs_port : 6;   // features per charger
             float* ob = io.obs + (io.gather ? (long long)obs_w
@@ -782,13 +782,27 @@ __global__ void __launch_bounds__(256, MINB) k_step_fused(DevBatch b, DevParams 
         int tile_id = 0;
         if (lane == 0) tile_id = atomicAdd(io.counter, 1);
         tile_id = __shfl_sync(0xFFFFFFFFu, tile_id, 0);
-        if (tile_id >= io.total_tiles) break;
-        int cls = 0, tile = 0;
+        int cls = -1, tile = 0;
+        if (io.dcount) {                   // device-side schedule: classes CHI down to CLO
+            int rest = tile_id;
 #pragma unroll
-        for (int i = 0; i < kNumClasses; ++i) {
-            if (i < io.n_sched && tile_id >= io.sched_tile_base[i] && tile_id < io.sched_tile_base[i + 1]) {
-                cls = io.sched_cls[i];
-                tile = tile_id - io.sched_tile_base[i];
+            for (int c = CHI; c >= CLO; --c) {
+                const int nt = (__ldg(io.dcount + c) + tile_epw(c) - 1) / tile_epw(c);
+                if (cls < 0 && rest < nt) {
+                    cls = c;
+                    tile = rest;
+                }
+                rest -= nt;
+            }
+            if (cls < 0) break;
+        } else {
+            if (tile_id >= io.total_tiles) break;
+#pragma unroll
+            for (int i = 0; i < kNumClasses; ++i) {
+                if (i < io.n_sched && tile_id >= io.sched_tile_base[i] && tile_id < io.sched_tile_base[i + 1]) {
+                    cls = io.sched_cls[i];
+                    tile = tile_id - io.sched_tile_base[i];
+                }
             }
         }
         if (CLO <= 0 && 0 <= CHI && cls == 0) run_tile<8, V2G, EXT, TREE>(b, p, io, tile, ws);
@@ -892,6 +906,31 @@ void launch_step_fused(const DevBatch& b, const DevParams& p, const FusedIO& io,
     const int warps = threads / 32;
     const int v = (p.v2g ? 1 : 0) | ((p.delta || p.cs_share) ? 2 : 0) | (p.tree_levels ? 4 : 0);
     const size_t smem = (size_t)warps * smem_per_warp(v);
+    if (io.dcount) {                       // the tile count is on the device: grids from the host's bounds
+        FusedIO o = io;
+        const bool fork2 = side && side->aux && io.dmax_large > 0 && io.dmax_small > 0;
+        if (io.dmax_large > 0) {
+            cudaStream_t sb = st;
+            if (fork2) {
+                cudaEventRecord(side->fork, st);
+                cudaStreamWaitEvent(side->aux, side->fork, 0);
+                sb = side->aux;
+            }
+            o.counter = io.counter;
+            const int blocks = std::max(1, std::min(blocks_per_sm_memo(true, v, threads) * sm_count,
+                                                    (io.dmax_large + warps - 1) / warps));
+            kLargeKernel[v]<<<blocks, threads, smem, sb>>>(b, p, o);
+            if (fork2) cudaEventRecord(side->join, side->aux);
+        }
+        if (io.dmax_small > 0) {
+            o.counter = io.counter + 1;
+            const int blocks = std::max(1, std::min(blocks_per_sm_memo(false, v, threads) * sm_count,
+                                                    (io.dmax_small + warps - 1) / warps));
+            kSmallKernel[v]<<<blocks, threads, smem, st>>>(b, p, o);
+        }
+        if (fork2) cudaStreamWaitEvent(st, side->join, 0);
+        return;
+    }
     const FusedIO big = sub_schedule(io, 4, 4, io.counter);
     const FusedIO small = sub_schedule(io, 0, 3, io.counter + 1);
     // the heavy class first; beside the others when a side stream is given
