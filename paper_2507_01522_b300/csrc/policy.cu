@@ -64,8 +64,8 @@ constexpr int kColPw = 0;                  // last applied power, parked in accu
 struct Sync {
     uint64_t full[kMaxStages], empty[kMaxStages];
     uint64_t acc;                          // a layer is accumulated (3 completions per pass)
-    uint64_t xrdy;                         // layer-1 operand written (kWorkers arrivals)
-    uint64_t hrdy;                         // h1 / h2 written (kWorkers arrivals, 2 per pass)
+    uint64_t xrdy;                         // layer-1 operand written (one arrival per worker thread)
+    uint64_t hrdy;                         // h1 / h2 written (one arrival per worker thread, 2 per pass)
     uint64_t fin;                          // every MMA of the CTA finished
     uint32_t tmem;
     int bad;                               // a wait timed out: skip everything
@@ -100,7 +100,7 @@ __device__ __forceinline__ bool wait_sync(uint64_t* bar, uint32_t parity, Sync& 
     }
 }
 
-__device__ __forceinline__ void init_sync(Sync& S, int n_stages)
+__device__ __forceinline__ void init_sync(Sync& S, int n_stages, int n_workers)
 {
     for (int s = 0; s < n_stages; ++s) {
         mbar_init(&S.full[s], 1);
@@ -108,8 +108,8 @@ __device__ __forceinline__ void init_sync(Sync& S, int n_stages)
     }
     mbar_init(&S.acc, 1);
     mbar_init(&S.fin, 1);
-    mbar_init(&S.xrdy, kWorkers);
-    mbar_init(&S.hrdy, kWorkers);
+    mbar_init(&S.xrdy, n_workers);
+    mbar_init(&S.hrdy, n_workers);
     S.bad = 0;
     mbar_fence_init();
 }
@@ -228,11 +228,12 @@ __device__ __forceinline__ void layer_bias(const PolicyArgs& a, const float* bia
     tmem_wait_st();
 }
 
-// ---- epilogue of layers 1 and 2: ReLU, BF16 into A ------------------------
+// ---- epilogue of layers 1 and 2: ReLU, BF16 into A (NB blocks of 32 columns)
+template <int NB>
 __device__ __forceinline__ void hidden_epilogue(uint32_t taddr, uint32_t abase, int row, int col0)
 {
 #pragma unroll 1
-    for (int blk = 0; blk < 4; ++blk) {
+    for (int blk = 0; blk < NB; ++blk) {
         const int c = col0 + 32 * blk;
         uint32_t v[32];
         tmem_ld32(taddr + (uint32_t)(32 * blk), v);
@@ -361,7 +362,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_policy(const __grid_constant__ 
     __shared__ __align__(16) float bias_s[2 * kPolicyHidden + kPolicyMaxPorts * kPolicyGroup];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int j = threadIdx.x; j < 2 * kPolicyHidden + a.n_out_pad; j += blockDim.x) bias_s[j] = a.bias[j];
-    if (threadIdx.x == 0) init_sync(S, kPolStages);
+    if (threadIdx.x == 0) init_sync(S, kPolStages, kWorkers);
     if (warp == 1) tmem_alloc(&S.tmem, kTmemCols);
     fence_before();
     __syncthreads();
@@ -430,7 +431,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_policy(const __grid_constant__ 
             for (int L = 0; L < 2; ++L) {
                 wait_sync(&S.acc, (3 * i + L) & 1, S, a.err);
                 fence_after();
-                hidden_epilogue(tl + (uint32_t)(128 * h), abase, row, 128 * h);
+                hidden_epilogue<4>(tl + (uint32_t)(128 * h), abase, row, 128 * h);
                 layer_bias(a, bias_s, tl, L + 1, h);
                 worker_arrive(&S.hrdy);
             }
@@ -455,72 +456,211 @@ __global__ void __launch_bounds__(kThreads, 1) k_policy(const __grid_constant__ 
 // =============================================================================
 // k_rollout: observe -> MLP -> sample -> environment step, T times
 // =============================================================================
+//
+// Sixteen worker warps: warp 2 + w serves TMEM lane quadrant (2 + w) % 4 and
+// part p = w / 4 of every station row there: chargers 8p .. 8p + 7 in the
+// sampling, the environment step and the observation, and hidden columns
+// 64p .. 64p + 63 in the epilogues.  So a station is served by four threads,
+// and every CUDA-core phase has twice the warps of k_policy to hide latency.
 
-// Per-station state, held in registers by BOTH worker threads of a station
-// (warps 2-5 take its chargers 0-15, warps 6-9 chargers 16-31: "half" 0 and
-// 1).  Both halves apply the same station-level updates from the same
-// exchanged totals, so their copies stay identical; half 0 writes the
-// station's outputs.
+constexpr int kRollWorkerWarps = 16;
+constexpr int kRollWorkers = kRollWorkerWarps * 32;
+constexpr int kRollThreads = (2 + kRollWorkerWarps) * 32;
+constexpr int kParts = 4;                  // threads per station
+constexpr int kPartPorts = 8;              // chargers per part
+
+// A station's scalars between steps, one record per row in shared memory:
+// part 0 writes it at the end of a step, every part reads it (the phases are
+// barrier-separated), so registers hold them only inside the step.
+struct RowState {
+    int slot[kM], t[kM], day[kM], occ[kM], cls_row[kM];
+    uint32_t uid[kM], k0[kM], k1[kM], g[kM], ncar[kM], ablk[kM];
+    uint4 aw[kM];
+    float ret[kM];
+};
+
+// The station's state during a step, in the registers of all four threads
+// of the station.  They apply the same station-level updates from the same
+// exchanged totals, so their copies stay identical; part 0 writes the
+// station's outputs and its record.
 struct Owner {
     long long e;
     bool live;
-    int half, slot, t, day, cls_row, occ;
+    int part, slot, t, day, cls_row, occ;
     long long pb;
     uint32_t uid, k0, k1, g, ncar, ablk;
     uint4 aw;
     float grid_cap, grid_inv_eta, ret, price;
-    uint32_t st_arr, st_rej, st_eps;
-    float st_miss, st_chg, last_ret;
-    bool ended;
 };
 
-// Observation staging: one 8-charger chunk (plus the 8 station features in
-// chunk 0) of 16 rows per worker warp; row stride kStageRow floats.
-constexpr int kStageRow = 8 + 48 + 4;      // 16-byte aligned rows
-constexpr int kObsRows = 16;               // rows per staging round
+// the station's running statistics of the rollout, kept by part 0
+struct RowStats {
+    uint32_t arr[kM], rej[kM], eps[kM], ended[kM];
+    float miss[kM], chg[kM], last_ret[kM];
+};
 
-// values the two halves of a station exchange during a step (per row)
+// Observation staging: kObsRows rows of one part's chunk (8 chargers, plus
+// the 8 station features in chunk 0) per worker warp; row stride kStageRow
+// floats.  It shares its space with the step's group scales and exchanges.
+constexpr int kStageRow = 8 + 48 + 4;      // 16-byte aligned rows
+constexpr int kObsRows = 8;                // rows per staging round
+
+// values the four parts of a station exchange during a step (per part, row);
+// the second members of the unions are written only after every read of the
+// first (the exchanges are barrier-separated)
 struct Xchg {
-    float trail[kM];                       // half 0: power of the group still open after charger 15
-    float lead[kM];                        // half 1: power up to its first tail charger
-    int first_gs[kM];                      // half 1: group slot of that tail (-1: none)
-    float raw[2][kM], over[2][kM], sp[2][kM], se[2][kM], csat[2][kM];
-    int nfree[2][kM], occ[2][kM];
+    union { float lead[kParts][kM]; float sp[kParts][kM]; };      // sum up to the part's first tail when
+                                                                   // that group began earlier | scaled sum
+    union { float trail[kParts][kM]; float se[kParts][kM]; };     // sum after the part's last tail (all of
+                                                                   // the part if it has none) | grid energy
+    union { int first_gs[kParts][kM]; float csat[kParts][kM]; };  // slot of that first tail (-1) | c_sat
+    union { int has_tail[kParts][kM]; int occ[kParts][kM]; };
+    float raw[kParts][kM], over[kParts][kM];
+    int nfree[kParts][kM];
 };
 
 struct RollSmem {
-    float gcap[32 * kM];                   // group slot x row: eta_H * I_H of the group of a tail charger
-    union {                                // the step's group scales, then the observation staging
-        float gscale[32 * kM];             // group slot x row
-        float stage[kWorkerWarps][kObsRows * kStageRow];
+    union {                                // the step's group scales and exchanges, then the observation staging
+        struct {
+            float gscale[32 * kM];         // group slot x row
+            Xchg x;
+        };
+        float stage[kRollWorkerWarps][kObsRows * kStageRow];
     } u;
-    Xchg x;
+    RowStats st;
+    RowState rw;
     uint32_t act[kM * kPolicyMaxPorts / 4]; // sampled levels, row-major [row][charger] bytes
-    uint32_t gstep[kM], key0[kM], key1[kM];
 };
+
+// the station's record -> registers (every part, at the start of a step)
+__device__ __forceinline__ void owner_get(Owner& o, const RolloutArgs& R, long long e, int row, int part,
+                                          const RollSmem& rs)
+{
+    const DevBatch& b = R.b;
+    const RowState& w = rs.rw;
+    o.e = e;
+    o.live = e < R.pol.E;
+    o.part = part;
+    o.slot = w.slot[row];
+    o.t = w.t[row];
+    o.day = w.day[row];
+    o.occ = w.occ[row];
+    o.cls_row = w.cls_row[row];
+    o.uid = w.uid[row];
+    o.k0 = w.k0[row];
+    o.k1 = w.k1[row];
+    o.g = w.g[row];
+    o.ncar = w.ncar[row];
+    o.ablk = w.ablk[row];
+    o.aw = w.aw[row];
+    o.ret = w.ret[row];
+    o.pb = R.port_base + (long long)(o.slot - R.env_base) * R.C;
+    o.grid_cap = o.live ? __ldg(b.grid_cap + o.slot) : 1.f;
+    o.grid_inv_eta = o.live ? __ldg(b.grid_inv_eta + o.slot) : 1.f;
+    o.price = o.live ? __ldg(b.price + (size_t)o.day * (size_t)R.p.ep_len + (size_t)o.t) : 0.f;
+}
+
+// registers -> the station's record (part 0)
+__device__ __forceinline__ void owner_put(const Owner& o, int row, RollSmem& rs)
+{
+    RowState& w = rs.rw;
+    w.slot[row] = o.slot;
+    w.t[row] = o.t;
+    w.day[row] = o.day;
+    w.occ[row] = o.occ;
+    w.cls_row[row] = o.cls_row;
+    w.uid[row] = o.uid;
+    w.k0[row] = o.k0;
+    w.k1[row] = o.k1;
+    w.g[row] = o.g;
+    w.ncar[row] = o.ncar;
+    w.ablk[row] = o.ablk;
+    w.aw[row] = o.aw;
+    w.ret[row] = o.ret;
+}
 
 __device__ __forceinline__ uint32_t taddr_of(uint32_t tl, int col) { return tl + (uint32_t)col; }
 
-// car words for the rare step with more than kPreCars arrivals (kept out of line)
+// car words beyond the pre-drawn ones (kept out of line)
 __device__ __noinline__ uint4 car_words_late(uint32_t uid, uint32_t n, uint32_t k0, uint32_t k1)
 {
     return car_words(uid, n, k0, k1);
 }
 
-// Load the station's state (both halves: station fields; each half: its 16
+// bias of layer L into the accumulator columns part `part` may write: hidden
+// columns 64 part .. +63 (those its layer-2 epilogue reads) and, for layer 3,
+// the block 256 + 32 part .. +31 of the columns beyond the hidden ones
+__device__ __forceinline__ void layer_bias_part(const PolicyArgs& a, const float* bias_s, uint32_t tl, int L, int part)
+{
+    const float* b = bias_s + kPolicyHidden * L;
+    const int n = L < 2 ? kPolicyHidden : a.n_out_pad;
+#pragma unroll 1
+    for (int c = 64 * part; c < 64 * part + 64; c += 32)
+        if (c < n) bias_to_tmem(tl + (uint32_t)c, b + c);
+    if (L == 2) {
+        const int c = 256 + 32 * part;
+        if (c < n) bias_to_tmem(tl + (uint32_t)c, b + c);
+    }
+    tmem_wait_st();
+}
+
+// Levels of chargers 8 part .. 8 part + 7 of the env in TMEM lane `tl`, four
+// per block; returns them packed 4 per word.
+template <int LT>
+__device__ __forceinline__ void sample_part(const PolicyArgs& a, uint32_t tl, int part, long long env, bool live,
+                                            uint32_t g, uint32_t k0, uint32_t k1, float* logits_env,
+                                            uint32_t (&packed)[2])
+{
+    const int L = LT ? LT : a.n_levels;
+    uint4 words[2];
+#pragma unroll
+    for (int blk = 0; blk < 2; ++blk)
+        words[blk] = philox4x32_10(make_uint4((uint32_t)env, g, (uint32_t)(2 * part + blk), kPurposePolicy), k0, k1);
+#pragma unroll 1
+    for (int blk = 0; blk < 2; ++blk) {
+        packed[blk] = 0;
+        const int c0 = 8 * part + 4 * blk;
+        if (c0 >= a.n_ports) break;                    // uniform across the warp
+        uint32_t v[48];
+        tmem_ld32(tl + (uint32_t)(L * c0), *reinterpret_cast<uint32_t(*)[32]>(v));
+        tmem_ld16(tl + (uint32_t)(L * c0 + 32), v + 32);
+        tmem_wait_ld();
+        if (!live) continue;
+        packed[blk] = sample4<LT>(v, c0, a.n_ports, a.n_levels, blk == 0 ? words[0] : words[1],
+                                  logits_env ? logits_env + (long long)c0 * L : nullptr);
+    }
+}
+
+__device__ __forceinline__ void store_levels_part(int8_t* dst, int part, int n_ports, const uint32_t (&packed)[2])
+{
+    if (n_ports == 32) {
+        *reinterpret_cast<uint2*>(dst + 8 * part) = make_uint2(packed[0], packed[1]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int c = 8 * part + j;
+            if (c < n_ports) dst[c] = (int8_t)((packed[j >> 2] >> (8 * (j & 3))) & 0xFFu);
+        }
+    }
+}
+
+// Load the station's state (every part: station fields; each part: its 8
 // chargers into TMEM).  Ends with the workers' named barrier (occupancy).
-__device__ __forceinline__ void owner_load(Owner& o, const RolloutArgs& R, int tile, int row, int half, uint32_t tl,
+__device__ __forceinline__ void owner_load(Owner& o, const RolloutArgs& R, int tile, int row, int part, uint32_t tl,
                                            RollSmem& rs)
 {
     const DevBatch& b = R.b;
     o.e = (long long)tile * kM + row;
     o.live = o.e < R.pol.E;
-    o.half = half;
+    o.part = part;
     o.slot = 0; o.pb = 0; o.uid = 0; o.k0 = o.k1 = o.g = o.ncar = 0;
     o.t = 0; o.day = 0; o.cls_row = 0; o.occ = 0;
     o.grid_cap = 1.f; o.grid_inv_eta = 1.f; o.ret = 0.f; o.price = 0.f;
-    o.st_arr = o.st_rej = o.st_eps = 0; o.st_miss = o.st_chg = 0.f; o.last_ret = 0.f; o.ended = false;
     o.ablk = 0xFFFFFFFFu;
+    if (part == 0) {
+        rs.st.arr[row] = rs.st.rej[row] = rs.st.eps[row] = rs.st.ended[row] = 0u;
+        rs.st.miss[row] = rs.st.chg[row] = rs.st.last_ret[row] = 0.f;
+    }
     o.aw = make_uint4(0, 0, 0, 0);
     if (o.live) {
         o.slot = R.pol.user_to_slot[o.e];
@@ -539,55 +679,52 @@ __device__ __forceinline__ void owner_load(Owner& o, const RolloutArgs& R, int t
         o.price = __ldg(b.price + (size_t)o.day * (size_t)R.p.ep_len + (size_t)o.t);
     }
     int occ = 0;
-#pragma unroll 1
-    for (int kk = 0; kk < 2; ++kk) {
-        const int k = 2 * half + kk;
-        uint32_t vs[8], ve[8], vc[8], vr[8], vp[8], vw[8];
+    uint32_t vs[8], ve[8], vc[8], vr[8], vp[8], vw[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int c = 8 * k + i;
-            vs[i] = ve[i] = vc[i] = vr[i] = vp[i] = vw[i] = 0u;
-            if (o.live && c < R.C) {
-                const long long x = o.pb + c;
-                vs[i] = __float_as_uint(b.soc[x]);
-                ve[i] = __float_as_uint(b.erem[x]);
-                vc[i] = __float_as_uint(b.cap[x]);
-                vr[i] = __float_as_uint(b.rbar[x]);
-                vw[i] = __float_as_uint(b.pw[x]);
-                const uint32_t meta = b.meta[x];
-                vp[i] = (uint32_t)b.trem[x] | (meta << 8);
-                occ += b.trem[x] > 0 ? 1 : 0;
-                if (meta & kMetaTail) rs.gcap[((meta >> kMetaGroupShift) & 31u) * kM + row] = b.gcap[x];
-            }
+    for (int i = 0; i < 8; ++i) {
+        const int c = 8 * part + i;
+        vs[i] = ve[i] = vc[i] = vr[i] = vp[i] = vw[i] = 0u;
+        if (o.live && c < R.C) {
+            const long long x = o.pb + c;
+            vs[i] = __float_as_uint(b.soc[x]);
+            ve[i] = __float_as_uint(b.erem[x]);
+            vc[i] = __float_as_uint(b.cap[x]);
+            vr[i] = __float_as_uint(b.rbar[x]);
+            vw[i] = __float_as_uint(b.pw[x]);
+            const uint32_t meta = b.meta[x];
+            vp[i] = (uint32_t)b.trem[x] | (meta << 8);
+            occ += b.trem[x] > 0 ? 1 : 0;
         }
-        tmem_st8(taddr_of(tl, kColSoc + 8 * k), vs);
-        tmem_st8(taddr_of(tl, kColErem + 8 * k), ve);
-        tmem_st8(taddr_of(tl, kColCap + 8 * k), vc);
-        tmem_st8(taddr_of(tl, kColRbar + 8 * k), vr);
-        tmem_st8(taddr_of(tl, kColPack + 8 * k), vp);
-        tmem_st8(taddr_of(tl, kColPw + 8 * k), vw);
     }
+    tmem_st8(taddr_of(tl, kColSoc + 8 * part), vs);
+    tmem_st8(taddr_of(tl, kColErem + 8 * part), ve);
+    tmem_st8(taddr_of(tl, kColCap + 8 * part), vc);
+    tmem_st8(taddr_of(tl, kColRbar + 8 * part), vr);
+    tmem_st8(taddr_of(tl, kColPack + 8 * part), vp);
+    tmem_st8(taddr_of(tl, kColPw + 8 * part), vw);
     tmem_wait_st();
-    rs.x.occ[half][row] = occ;
-    if (half == 0) {
-        rs.gstep[row] = o.g;
-        rs.key0[row] = o.k0;
-        rs.key1[row] = o.k1;
-    }
+    rs.u.x.occ[part][row] = occ;
     fence_before();
-    named_sync(kBarWorkers, kWorkers);
+    named_sync(kBarWorkers, kRollWorkers);
     fence_after();
-    o.occ = rs.x.occ[0][row] + rs.x.occ[1][row];
+    o.occ = 0;
+#pragma unroll
+    for (int j = 0; j < kParts; ++j) o.occ += rs.u.x.occ[j][row];
+    if (part == 0) owner_put(o, row, rs);
+    named_sync(kBarWorkers, kRollWorkers);           // every read done: the staging may reuse the space
 }
 
 // One environment step of the station with this step's sampled levels
 // (Appendix A.2 then A.3; the operations of the fused step kernel), this
-// thread's half of the chargers, three exchanges with the other half.
-__device__ __forceinline__ void owner_step(Owner& o, const RolloutArgs& R, int it, int row, uint32_t tl, RollSmem& rs)
+// thread's 8 chargers, four exchanges with the other parts.
+__device__ __forceinline__ void owner_step(const RolloutArgs& R, long long e, int part, int it, int row, uint32_t tl,
+                                           RollSmem& rs)
 {
+    Owner o;
+    owner_get(o, R, e, row, part, rs);
     const DevParams& p = R.p;
     const DevBatch& b = R.b;
-    const int h = o.half;
+    const int h = o.part;
     // arrival count of this step (Philox word, Poisson CDF row)
     const uint32_t blk = o.g >> 2;
     if (blk != o.ablk) {
@@ -597,105 +734,113 @@ __device__ __forceinline__ void owner_step(Owner& o, const RolloutArgs& R, int i
     const float* F = b.cdf + ((size_t)o.cls_row * (size_t)p.ep_len + (size_t)o.t) * kCdfLen;
     const float4 f0 = __ldg(reinterpret_cast<const float4*>(F));
     const float4 f1 = __ldg(reinterpret_cast<const float4*>(F + 4));
-    uint32_t lv[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) lv[j] = rs.act[row * (kPolicyMaxPorts / 4) + 4 * h + j];
+    const uint32_t lv0 = rs.act[row * (kPolicyMaxPorts / 4) + 2 * h];
+    const uint32_t lv1 = rs.act[row * (kPolicyMaxPorts / 4) + 2 * h + 1];
 
-    // (i) per-charger clip; sums of the groups whose tail is in this half
-    float P[16];
-    float gacc = 0.f, raw = 0.f, over = 0.f;
-    int nfree = 0, last_tail = -1, first_tail = -1, first_gs = -1;
-    float lead = 0.f;
+    // (i) per-charger clip; sums of the groups that close in this part
+    float P[8];
+    float gacc = 0.f, raw = 0.f, over = 0.f, lead = 0.f;
+    int nfree = 0, first_gs = -1, first_tail = -1;
+    bool head_seen = h == 0, any_tail = false;   // part 0 starts at the station's first group head
 #pragma unroll
-    for (int kk = 0; kk < 2; ++kk) {
-        const int k = 2 * h + kk;
-        uint32_t vs[8], ve[8], vc[8], vr[8], vp[8];
-        tmem_ld8(taddr_of(tl, kColSoc + 8 * k), vs);
-        tmem_ld8(taddr_of(tl, kColErem + 8 * k), ve);
-        tmem_ld8(taddr_of(tl, kColCap + 8 * k), vc);
-        tmem_ld8(taddr_of(tl, kColRbar + 8 * k), vr);
-        tmem_ld8(taddr_of(tl, kColPack + 8 * k), vp);
+    for (int hh = 0; hh < 2; ++hh) {
+        uint32_t vs[4], ve[4], vc[4], vr[4], vp[4];
+        const int c4 = 8 * h + 4 * hh;
+        tmem_ld4(taddr_of(tl, kColSoc + c4), vs);
+        tmem_ld4(taddr_of(tl, kColErem + c4), ve);
+        tmem_ld4(taddr_of(tl, kColCap + c4), vc);
+        tmem_ld4(taddr_of(tl, kColRbar + c4), vr);
+        tmem_ld4(taddr_of(tl, kColPack + c4), vp);
         tmem_wait_ld();
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int ci = 8 * kk + i;
-            const int trem = (int)(vp[i] & 0xFFu);
-            const uint32_t meta = vp[i] >> 8;
-            const int lvl = (int)((lv[ci >> 2] >> (8 * (ci & 3))) & 0xFFu);
+        for (int ii = 0; ii < 4; ++ii) {
+            const int i = 4 * hh + ii;
+            const int trem = (int)(vp[ii] & 0xFFu);
+            const uint32_t meta = vp[ii] >> 8;
+            const int lvl = (int)(((hh == 0 ? lv0 : lv1) >> (8 * ii)) & 0xFFu);
             const bool dc = meta & kMetaDC;
-            P[ci] = trem > 0 ? clip_power((float)lvl * (dc ? p.lvl1 : p.lvl0), dc, __uint_as_float(vs[i]), __uint_as_float(ve[i]),
-                                          __uint_as_float(vc[i]), __uint_as_float(vr[i]), p)
-                             : 0.f;
-            raw += P[ci];
-            gacc += P[ci];
+            P[i] = trem > 0 ? clip_power((float)lvl * (dc ? p.lvl1 : p.lvl0), dc, __uint_as_float(vs[ii]),
+                                         __uint_as_float(ve[ii]), __uint_as_float(vc[ii]), __uint_as_float(vr[ii]), p)
+                            : 0.f;
+            raw += P[i];
+            if (meta & kMetaHead) head_seen = true;
+            gacc += P[i];
             nfree += ((meta & kMetaValid) && trem <= 1) ? 1 : 0;    // free once this step's departures left
             if (meta & kMetaTail) {
                 const int gs = (int)((meta >> kMetaGroupShift) & 31u);
-                if (h == 1 && first_tail < 0) {                      // may close a group opened in half 0
-                    first_tail = ci;
+                if (!head_seen) {                                    // closes a group begun in an earlier part
                     first_gs = gs;
+                    first_tail = i;
                     lead = gacc;
                 } else {
-                    const float gc = rs.gcap[gs * kM + row];
+                    const float gc = __ldg(b.gcap + o.pb + 8 * h + i);
                     rs.u.gscale[gs * kM + row] = gacc > gc ? __fdividef(gc, gacc) : 1.0f;
-                    if (p.a_con != 0.f) over = fmaxf(over, (gacc - gc) * __ldg(b.ginv_eta + o.pb + 16 * h + ci));
+                    if (p.a_con != 0.f) over = fmaxf(over, (gacc - gc) * __ldg(b.ginv_eta + o.pb + 8 * h + i));
                 }
-                last_tail = ci;
+                any_tail = true;
+                head_seen = false;                                   // until the next group's head
                 gacc = 0.f;
             }
         }
     }
-    if (h == 0) rs.x.trail[row] = gacc;
-    else {
-        rs.x.lead[row] = lead;
-        rs.x.first_gs[row] = first_gs;
-    }
-    rs.x.raw[h][row] = raw;
-    rs.x.over[h][row] = over;
-    rs.x.nfree[h][row] = nfree;
-    named_sync(kBarWorkers, kWorkers);                               // exchange A
+    rs.u.x.lead[h][row] = lead;
+    rs.u.x.trail[h][row] = gacc;
+    rs.u.x.first_gs[h][row] = first_gs;
+    rs.u.x.has_tail[h][row] = any_tail ? 1 : 0;
+    rs.u.x.raw[h][row] = raw;
+    rs.u.x.nfree[h][row] = nfree;
+    named_sync(kBarWorkers, kRollWorkers);                           // exchange A
 
-    // the group that closes at half 1's first tail charger (it may have
-    // started in half 0): both halves compute its scale
-    const int sgs = rs.x.first_gs[row];
-    float s_scale = 1.f, s_over = 0.f;
-    if (sgs >= 0) {
-        const float S = rs.x.trail[row] + rs.x.lead[row];
-        const float gc = rs.gcap[sgs * kM + row];
-        s_scale = S > gc ? __fdividef(gc, S) : 1.0f;
-        // its tail charger is half 1's first tail (an index only half 1 has)
-        if (h == 1 && p.a_con != 0.f) s_over = (S - gc) * __ldg(b.ginv_eta + o.pb + 16 + first_tail);
+    // a group that closes here but began in an earlier part: its sum is this
+    // part's lead plus the open sums of the parts back to the one it began in
+    if (first_gs >= 0) {
+        float S = lead;
+        for (int j = h - 1; j >= 0; --j) {
+            S += rs.u.x.trail[j][row];
+            if (rs.u.x.has_tail[j][row]) break;
+        }
+        const float gc = __ldg(b.gcap + o.pb + 8 * h + first_tail);
+        rs.u.gscale[first_gs * kM + row] = S > gc ? __fdividef(gc, S) : 1.0f;
+        if (p.a_con != 0.f) over = fmaxf(over, (S - gc) * __ldg(b.ginv_eta + o.pb + 8 * h + first_tail));
     }
-    const int nfree0 = rs.x.nfree[0][row], nfree1 = rs.x.nfree[1][row];
+    rs.u.x.over[h][row] = over;
+    int nfree_all = 0, before = 0;
+#pragma unroll
+    for (int j = 0; j < kParts; ++j) {
+        const int nf = rs.u.x.nfree[j][row];
+        nfree_all += nf;
+        before += j < h ? nf : 0;
+    }
+    float raw_all = 0.f;
+#pragma unroll
+    for (int j = 0; j < kParts; ++j) raw_all += rs.u.x.raw[j][row];
+    named_sync(kBarWorkers, kRollWorkers);                           // exchange B: every group's scale
+
     // architecture constraint: charger power scaled by its group
     float sp = 0.f;
-#pragma unroll
-    for (int kk = 0; kk < 2; ++kk) {
-        const int k = 2 * h + kk;
+    {
         uint32_t vp[8];
-        tmem_ld8(taddr_of(tl, kColPack + 8 * k), vp);
+        tmem_ld8(taddr_of(tl, kColPack + 8 * h), vp);
         tmem_wait_ld();
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            const int ci = 8 * kk + i;
             const uint32_t meta = vp[i] >> 8;
-            const bool in_split = h == 0 ? ci > last_tail : (first_tail >= 0 && ci <= first_tail);
-            float sc = 1.f;
-            if (in_split) sc = s_scale;
-            else if (meta & kMetaValid) sc = rs.u.gscale[((meta >> kMetaGroupShift) & 31u) * kM + row];
-            P[ci] *= sc;
-            sp += P[ci];
+            if (meta & kMetaValid) P[i] *= rs.u.gscale[((meta >> kMetaGroupShift) & 31u) * kM + row];
+            sp += P[i];
         }
     }
-    rs.x.sp[h][row] = sp;
-    named_sync(kBarWorkers, kWorkers);                               // exchange B
-    const float sp_all = rs.x.sp[0][row] + rs.x.sp[1][row];
-    const float raw_all = rs.x.raw[0][row] + rs.x.raw[1][row];
+    rs.u.x.sp[h][row] = sp;
+    named_sync(kBarWorkers, kRollWorkers);                           // exchange C
+    float sp_all = 0.f;
+#pragma unroll
+    for (int j = 0; j < kParts; ++j) sp_all += rs.u.x.sp[j][row];
     const float s_root = sp_all > o.grid_cap ? __fdividef(o.grid_cap, sp_all) : 1.0f;
     float c_con = 0.f;
     if (p.a_con != 0.f) {
-        // s_over was formed by half 1 with the right tail; half 0 takes it from the exchange
-        if (h == 1) rs.x.over[1][row] = fmaxf(rs.x.over[1][row], s_over);
+        float over_all = 0.f;
+#pragma unroll
+        for (int j = 0; j < kParts; ++j) over_all = fmaxf(over_all, rs.u.x.over[j][row]);
+        c_con = fmaxf(fmaxf(over_all, (raw_all - o.grid_cap) * o.grid_inv_eta), 0.f);
     }
 
     // Poisson count: the smallest k with u < F_k (F nondecreasing, F_127 = inf)
@@ -705,40 +850,36 @@ __device__ __forceinline__ void owner_step(Owner& o, const RolloutArgs& R, int i
             (u >= f1.w);
     if (M == 8)
         while (u >= __ldg(F + M)) ++M;
-    // first come first served: half 0's free chargers take the first cars
-    const int adm0 = min(M, nfree0), adm1 = min(M - adm0, nfree1);
-    const int quota = h == 0 ? adm0 : adm1;
-    const uint32_t car0 = o.ncar + (uint32_t)(h == 0 ? 0 : adm0);
-    constexpr int kPreCars = 4;
-    uint4 cw[kPreCars];
-#pragma unroll
-    for (int j = 0; j < kPreCars; ++j)
-        cw[j] = j < quota ? car_words(o.uid, car0 + (uint32_t)j, o.k0, o.k1) : make_uint4(0, 0, 0, 0);
+    // first come first served: earlier parts' free chargers take the first cars
+    const int adm_all = min(M, nfree_all);
+    const int quota = max(0, min(adm_all - before, nfree));
+    const uint32_t car0 = o.ncar + (uint32_t)min(before, adm_all);
+    const uint4 cw0 = quota > 0 ? car_words(o.uid, car0, o.k0, o.k1) : make_uint4(0, 0, 0, 0);
 
     // (ii) charge, (iii) departures, (iv) arrivals, and the episode end
     const bool fin = o.t + 1 >= p.ep_len;
     float se = 0.f, c_sat = 0.f;
     int adm = 0, occ = 0;
 #pragma unroll
-    for (int kk = 0; kk < 2; ++kk) {
-        const int k = 2 * h + kk;
-        uint32_t vs[8], ve[8], vc[8], vr[8], vp[8], vw[8];
-        tmem_ld8(taddr_of(tl, kColSoc + 8 * k), vs);
-        tmem_ld8(taddr_of(tl, kColErem + 8 * k), ve);
-        tmem_ld8(taddr_of(tl, kColCap + 8 * k), vc);
-        tmem_ld8(taddr_of(tl, kColRbar + 8 * k), vr);
-        tmem_ld8(taddr_of(tl, kColPack + 8 * k), vp);
+    for (int hh = 0; hh < 2; ++hh) {
+        uint32_t vs[4], ve[4], vc[4], vr[4], vp[4], vw[4];
+        const int c4 = 8 * h + 4 * hh;
+        tmem_ld4(taddr_of(tl, kColSoc + c4), vs);
+        tmem_ld4(taddr_of(tl, kColErem + c4), ve);
+        tmem_ld4(taddr_of(tl, kColCap + c4), vc);
+        tmem_ld4(taddr_of(tl, kColRbar + c4), vr);
+        tmem_ld4(taddr_of(tl, kColPack + c4), vp);
         tmem_wait_ld();
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int ci = 8 * kk + i;
-            int trem = (int)(vp[i] & 0xFFu);
-            const uint32_t meta = vp[i] >> 8;
+        for (int ii = 0; ii < 4; ++ii) {
+            const int i = 4 * hh + ii;
+            int trem = (int)(vp[ii] & 0xFFu);
+            const uint32_t meta = vp[ii] >> 8;
             const bool dc = meta & kMetaDC;
-            float soc = __uint_as_float(vs[i]), erem = __uint_as_float(ve[i]);
-            float cap = __uint_as_float(vc[i]), rbar = __uint_as_float(vr[i]);
-            const float Pq = P[ci] * s_root;
-            se += P[ci] * (dc ? p.inv_eta1 : p.inv_eta0);
+            float soc = __uint_as_float(vs[ii]), erem = __uint_as_float(ve[ii]);
+            float cap = __uint_as_float(vc[ii]), rbar = __uint_as_float(vr[ii]);
+            const float Pq = P[i] * s_root;
+            se += P[i] * (dc ? p.inv_eta1 : p.inv_eta0);
             float pw = Pq;
             if (trem > 0) {
                 const float dE = Pq * p.dt;
@@ -751,11 +892,7 @@ __device__ __forceinline__ void owner_step(Owner& o, const RolloutArgs& R, int i
                 }
             }
             if ((meta & kMetaValid) && trem == 0 && adm < quota) {
-                const uint4 w = adm == 0 ? cw[0]
-                              : adm == 1 ? cw[1]
-                              : adm == 2 ? cw[2]
-                              : adm == 3 ? cw[3]
-                                         : car_words_late(o.uid, car0 + (uint32_t)adm, o.k0, o.k1);
+                const uint4 w = adm == 0 ? cw0 : car_words_late(o.uid, car0 + (uint32_t)adm, o.k0, o.k1);
                 const Car car = car_from_words(w, dc, p);
                 cap = car.cap; soc = car.soc; erem = car.erem; rbar = car.rbar;
                 trem = car.stay;
@@ -766,33 +903,34 @@ __device__ __forceinline__ void owner_step(Owner& o, const RolloutArgs& R, int i
                 trem = 0;
             }
             occ += trem > 0 ? 1 : 0;
-            vs[i] = __float_as_uint(soc);
-            ve[i] = __float_as_uint(erem);
-            vc[i] = __float_as_uint(cap);
-            vr[i] = __float_as_uint(rbar);
-            vp[i] = (uint32_t)trem | (meta << 8);
-            vw[i] = __float_as_uint(pw);
+            vs[ii] = __float_as_uint(soc);
+            ve[ii] = __float_as_uint(erem);
+            vc[ii] = __float_as_uint(cap);
+            vr[ii] = __float_as_uint(rbar);
+            vp[ii] = (uint32_t)trem | (meta << 8);
+            vw[ii] = __float_as_uint(pw);
         }
-        tmem_st8(taddr_of(tl, kColSoc + 8 * k), vs);
-        tmem_st8(taddr_of(tl, kColErem + 8 * k), ve);
-        tmem_st8(taddr_of(tl, kColCap + 8 * k), vc);
-        tmem_st8(taddr_of(tl, kColRbar + 8 * k), vr);
-        tmem_st8(taddr_of(tl, kColPack + 8 * k), vp);
-        tmem_st8(taddr_of(tl, kColPw + 8 * k), vw);
+        tmem_st4(taddr_of(tl, kColSoc + c4), vs);
+        tmem_st4(taddr_of(tl, kColErem + c4), ve);
+        tmem_st4(taddr_of(tl, kColCap + c4), vc);
+        tmem_st4(taddr_of(tl, kColRbar + c4), vr);
+        tmem_st4(taddr_of(tl, kColPack + c4), vp);
+        tmem_st4(taddr_of(tl, kColPw + c4), vw);
     }
     tmem_wait_st();
-    rs.x.se[h][row] = se;
-    rs.x.csat[h][row] = c_sat;
-    rs.x.occ[h][row] = occ;
-    named_sync(kBarWorkers, kWorkers);                               // exchange C
-    const float se_all = rs.x.se[0][row] + rs.x.se[1][row];
-    const float csat_all = rs.x.csat[0][row] + rs.x.csat[1][row];
-    const int adm_all = adm0 + adm1;
-    if (p.a_con != 0.f) {
-        const float over_all = fmaxf(rs.x.over[0][row], rs.x.over[1][row]);
-        c_con = fmaxf(fmaxf(over_all, (raw_all - o.grid_cap) * o.grid_inv_eta), 0.f);
+    rs.u.x.se[h][row] = se;
+    rs.u.x.csat[h][row] = c_sat;
+    rs.u.x.occ[h][row] = occ;
+    named_sync(kBarWorkers, kRollWorkers);                           // exchange D
+    float se_all = 0.f, csat_all = 0.f;
+    int occ_all = 0;
+#pragma unroll
+    for (int j = 0; j < kParts; ++j) {
+        se_all += rs.u.x.se[j][row];
+        csat_all += rs.u.x.csat[j][row];
+        occ_all += rs.u.x.occ[j][row];
     }
-    o.occ = rs.x.occ[0][row] + rs.x.occ[1][row];
+    o.occ = occ_all;
 
     // reward, Appendix A.3
     const float e_net = sp_all * s_root * p.dt;
@@ -802,14 +940,18 @@ __device__ __forceinline__ void owner_step(Owner& o, const RolloutArgs& R, int i
     const float r = profit - p.a_sat * csat_all - p.a_decl * (float)(M - adm_all) - p.a_con * c_con;
     o.ret += r;
     o.t += 1;
-    o.st_arr += (uint32_t)adm_all;
-    o.st_rej += (uint32_t)(M - adm_all);
-    o.st_miss += csat_all;
-    o.st_chg += e_net;
+    if (h == 0) {
+        rs.st.arr[row] += (uint32_t)adm_all;
+        rs.st.rej[row] += (uint32_t)(M - adm_all);
+        rs.st.miss[row] += csat_all;
+        rs.st.chg[row] += e_net;
+        if (fin) {
+            rs.st.last_ret[row] = o.ret;
+            rs.st.ended[row] = 1u;
+            rs.st.eps[row] += 1u;
+        }
+    }
     if (fin) {
-        o.last_ret = o.ret;
-        o.ended = true;
-        o.st_eps += 1u;
         o.ret = 0.f;
         o.t = 0;
         o.day = draw_day(o.uid, o.g, 0u, o.k0, o.k1, p.n_days);
@@ -823,152 +965,152 @@ __device__ __forceinline__ void owner_step(Owner& o, const RolloutArgs& R, int i
         }
         o.price = __ldg(b.price + (size_t)o.day * (size_t)p.ep_len + (size_t)o.t);
     }
-    if (h == 0) rs.gstep[row] = o.g;
+    if (h == 0) owner_put(o, row, rs);
 }
 
-// Observation after the step: this half's chunks (half 0 also the 8 station
+// Observation after the step: this part's chunk (part 0 also the 8 station
 // features), every lane on its own row; BF16 into the layer-1 operand, FP32
-// to HBM through the warp's staging buffer, 16 rows at a time, each row's
-// chunk a contiguous, 16-byte aligned run.
-__device__ __forceinline__ void owner_observe(const Owner& o, const RolloutArgs& R, int it, int q, int lane, uint32_t tl,
-                                              uint32_t abase, float* stage)
+// to HBM through the warp's staging buffer, kObsRows rows at a time, each
+// row's chunk a contiguous, 16-byte aligned run.
+__device__ __forceinline__ void owner_observe(const RolloutArgs& R, long long e, int part, int it, int q, int lane,
+                                              uint32_t tl, uint32_t abase, float* stage, const RollSmem& rs)
 {
     const DevParams& p = R.p;
     const int D = R.pol.obs_dim, N = R.pol.n_ports;
     const int row = 32 * q + lane;
-    const long long e0 = o.e - lane;                        // env of the warp's first row
+    const long long e0 = e - lane;                          // env of the warp's first row
+    const bool live = e < R.pol.E;
     const int n_chunks = (N + 7) >> 3;
+    const int k = part;
+    if (k >= n_chunks) return;                              // uniform across the warp
+    uint32_t vs[8], ve[8], vr[8], vp[8], vw[8];
+    tmem_ld8(taddr_of(tl, kColSoc + 8 * k), vs);
+    tmem_ld8(taddr_of(tl, kColErem + 8 * k), ve);
+    tmem_ld8(taddr_of(tl, kColRbar + 8 * k), vr);
+    tmem_ld8(taddr_of(tl, kColPack + 8 * k), vp);
+    tmem_ld8(taddr_of(tl, kColPw + 8 * k), vw);
+    tmem_wait_ld();
+    // features [f0, f1): the station's 8 in chunk 0, then 6 per charger
+    const int f0 = k == 0 ? 0 : 8 + 48 * k;
+    const int f1 = min(8 + 48 * (k + 1), D);
+    float st8[8], cf[48];
+    if (k == 0 && live) obs_env(st8, rs.rw.t[row], rs.rw.day[row], rs.rw.occ[row], N, 0.f, 0.f, R.b, p);   // charge-only mode
+    else
+#pragma unroll
+        for (int f = 0; f < 8; ++f) st8[f] = 0.f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int c = 8 * k + i;
+        if (live && c < N) {
+            obs_port<false>(cf + 6 * i, (int)(vp[i] & 0xFFu), 0, __uint_as_float(vs[i]), __uint_as_float(ve[i]),
+                            __uint_as_float(vr[i]), __uint_as_float(vw[i]), (vp[i] >> 8) & kMetaDC, p);
+        } else {
+#pragma unroll
+            for (int x = 0; x < 6; ++x) cf[6 * i + x] = 0.f;
+        }
+    }
+    // feature f0 + j (j a compile-time index after unrolling)
+    auto V = [&](int j) -> float {
+        if (k == 0) return j < 8 ? st8[j < 8 ? j : 0] : cf[j >= 8 && j < 56 ? j - 8 : 0];
+        return j < 48 ? cf[j < 48 ? j : 0] : 0.f;
+    };
+    // BF16 into the operand (pairs; the K padding up to 16 is zero)
+    const int n_f = f1 - f0;
+    const bool last = k == n_chunks - 1;
+    const int n_fp = last ? (((D + 15) & ~15) - f0) : n_f;
+#pragma unroll
+    for (int j = 0; j < 56; j += 2) {
+        if (j < n_fp) {
+            const float x0 = j < n_f ? V(j) : 0.f, x1 = j + 1 < n_f ? V(j + 1) : 0.f;
+            st_shared_u32(abase + sw128_offset(row, f0 + j, kChunkBytes), pack_bf16x2(x0, x1));
+        }
+    }
+    if (last && n_fp > 56) {                                 // padding beyond the chunk's own width
+        for (int j = 56; j < n_fp; j += 2) st_shared_u32(abase + sw128_offset(row, f0 + j, kChunkBytes), 0u);
+    }
+    if (!R.obs_out) return;
+    static_assert(kObsRows == 8, "4 lanes per staged row");
+    const int r = lane >> 2;                                // the staged row this lane copies
 #pragma unroll 1
-    for (int kk = 0; kk < 2; ++kk) {
-        const int k = 2 * o.half + kk;
-        if (k >= n_chunks) break;                           // uniform across the warp
-        uint32_t vs[8], ve[8], vr[8], vp[8], vw[8];
-        tmem_ld8(taddr_of(tl, kColSoc + 8 * k), vs);
-        tmem_ld8(taddr_of(tl, kColErem + 8 * k), ve);
-        tmem_ld8(taddr_of(tl, kColRbar + 8 * k), vr);
-        tmem_ld8(taddr_of(tl, kColPack + 8 * k), vp);
-        tmem_ld8(taddr_of(tl, kColPw + 8 * k), vw);
-        tmem_wait_ld();
-        // features [f0, f1): the station's 8 in chunk 0, then 6 per charger
-        const int f0 = k == 0 ? 0 : 8 + 48 * k;
-        const int f1 = min(8 + 48 * (k + 1), D);
-        float st8[8], cf[48];
-        if (k == 0 && o.live) obs_env(st8, o.t, o.day, o.occ, N, 0.f, 0.f, R.b, p);   // charge-only mode
-        else
+    for (int rnd = 0; rnd < 32 / kObsRows; ++rnd) {
+        if ((lane >> 3) == rnd) {
+            float* srow = stage + (lane & 7) * kStageRow;
 #pragma unroll
-            for (int f = 0; f < 8; ++f) st8[f] = 0.f;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int c = 8 * k + i;
-            if (o.live && c < N) {
-                obs_port<false>(cf + 6 * i, (int)(vp[i] & 0xFFu), 0, __uint_as_float(vs[i]), __uint_as_float(ve[i]),
-                         __uint_as_float(vr[i]), __uint_as_float(vw[i]), (vp[i] >> 8) & kMetaDC, p);
-            } else {
-#pragma unroll
-                for (int x = 0; x < 6; ++x) cf[6 * i + x] = 0.f;
-            }
+            for (int j = 0; j < 56; j += 4)
+                if (j < n_f) *reinterpret_cast<float4*>(srow + j) = make_float4(V(j), V(j + 1), V(j + 2), V(j + 3));
         }
-        // feature f0 + j (j a compile-time index after unrolling)
-        auto V = [&](int j) -> float {
-            if (k == 0) return j < 8 ? st8[j < 8 ? j : 0] : cf[j >= 8 && j < 56 ? j - 8 : 0];
-            return j < 48 ? cf[j < 48 ? j : 0] : 0.f;
-        };
-        // BF16 into the operand (pairs; the K padding up to 16 is zero)
-        const int n_f = f1 - f0;
-        const bool last = k == n_chunks - 1;
-        const int n_fp = last ? (((D + 15) & ~15) - f0) : n_f;
+        __syncwarp();
+        const long long eb = e0 + kObsRows * rnd;
+        if (eb + r < (long long)R.pol.E) {
+            float* dst = R.obs_out + ((long long)it * R.pol.E + eb + r) * D + f0;
+            const float* src = stage + r * kStageRow;
+            if ((D & 3) == 0) {                             // a row's run: at most 14 float4
 #pragma unroll
-        for (int j = 0; j < 56; j += 2) {
-            if (j < n_fp) {
-                const float x0 = j < n_f ? V(j) : 0.f, x1 = j + 1 < n_f ? V(j + 1) : 0.f;
-                st_shared_u32(abase + sw128_offset(row, f0 + j, kChunkBytes), pack_bf16x2(x0, x1));
-            }
-        }
-        if (last && n_fp > 56) {                             // padding beyond the chunk's own width
-            for (int j = 56; j < n_fp; j += 2) st_shared_u32(abase + sw128_offset(row, f0 + j, kChunkBytes), 0u);
-        }
-        if (R.obs_out) {
-#pragma unroll 1
-            for (int half_rows = 0; half_rows < 2; ++half_rows) {
-                if ((lane >> 4) == half_rows) {
-                    float* srow = stage + (lane & 15) * kStageRow;
-#pragma unroll
-                    for (int j = 0; j < 56; j += 4)
-                        if (j < n_f)
-                            *reinterpret_cast<float4*>(srow + j) = make_float4(V(j), V(j + 1), V(j + 2), V(j + 3));
+                for (int i = 0; i < 4; ++i) {
+                    const int c4 = (lane & 3) + 4 * i;
+                    if (4 * c4 < n_f)
+                        *reinterpret_cast<float4*>(dst + 4 * c4) = *reinterpret_cast<const float4*>(src + 4 * c4);
                 }
-                __syncwarp();
-                const long long eb = e0 + 16 * half_rows;
-                const int n_rows = (int)min(16LL, max(0LL, (long long)R.pol.E - eb));
-                float* dst0 = R.obs_out + ((long long)it * R.pol.E + eb) * D + f0;
-                // two rows per pass, 16 lanes per row (a row's run is at most 14 float4)
-                const int cl = lane & 15;
-                if ((D & 3) == 0) {
-                    if (4 * cl < n_f)
-#pragma unroll 4
-                        for (int r = lane >> 4; r < n_rows; r += 2)
-                            *reinterpret_cast<float4*>(dst0 + (long long)r * D + 4 * cl) =
-                                *reinterpret_cast<const float4*>(stage + r * kStageRow + 4 * cl);
-                } else {
-#pragma unroll 4
-                    for (int r = lane >> 4; r < n_rows; r += 2)
-                        for (int c2 = cl; 2 * c2 < n_f; c2 += 16)
-                            *reinterpret_cast<float2*>(dst0 + (long long)r * D + 2 * c2) =
-                                *reinterpret_cast<const float2*>(stage + r * kStageRow + 2 * c2);
+            } else {                                        // at most 28 float2
+#pragma unroll
+                for (int i = 0; i < 7; ++i) {
+                    const int c2 = (lane & 3) + 4 * i;
+                    if (2 * c2 < n_f)
+                        *reinterpret_cast<float2*>(dst + 2 * c2) = *reinterpret_cast<const float2*>(src + 2 * c2);
                 }
-                __syncwarp();
             }
         }
+        __syncwarp();
     }
 }
 
-// State back to HBM: each half its chargers, half 0 the station fields.
-__device__ __forceinline__ void owner_store(const Owner& o, const RolloutArgs& R, uint32_t tl)
+// State back to HBM: each part its chargers, part 0 the station fields.
+__device__ __forceinline__ void owner_store(const RolloutArgs& R, long long e, int part, uint32_t tl, int row,
+                                            const RollSmem& rs)
 {
+    Owner o;
+    owner_get(o, R, e, row, part, rs);
     const DevBatch& b = R.b;
-#pragma unroll 1
-    for (int kk = 0; kk < 2; ++kk) {
-        const int k = 2 * o.half + kk;
-        uint32_t vs[8], ve[8], vc[8], vr[8], vp[8], vw[8];
-        tmem_ld8(taddr_of(tl, kColSoc + 8 * k), vs);
-        tmem_ld8(taddr_of(tl, kColErem + 8 * k), ve);
-        tmem_ld8(taddr_of(tl, kColCap + 8 * k), vc);
-        tmem_ld8(taddr_of(tl, kColRbar + 8 * k), vr);
-        tmem_ld8(taddr_of(tl, kColPack + 8 * k), vp);
-        tmem_ld8(taddr_of(tl, kColPw + 8 * k), vw);
-        tmem_wait_ld();
-        if (!o.live) continue;
+    const int k = o.part;
+    uint32_t vs[8], ve[8], vc[8], vr[8], vp[8], vw[8];
+    tmem_ld8(taddr_of(tl, kColSoc + 8 * k), vs);
+    tmem_ld8(taddr_of(tl, kColErem + 8 * k), ve);
+    tmem_ld8(taddr_of(tl, kColCap + 8 * k), vc);
+    tmem_ld8(taddr_of(tl, kColRbar + 8 * k), vr);
+    tmem_ld8(taddr_of(tl, kColPack + 8 * k), vp);
+    tmem_ld8(taddr_of(tl, kColPw + 8 * k), vw);
+    tmem_wait_ld();
+    if (!o.live) return;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int c = 8 * k + i;
-            if (c < R.C) {
-                const long long x = o.pb + c;
-                b.soc[x] = __uint_as_float(vs[i]);
-                b.erem[x] = __uint_as_float(ve[i]);
-                b.cap[x] = __uint_as_float(vc[i]);
-                b.rbar[x] = __uint_as_float(vr[i]);
-                b.pw[x] = __uint_as_float(vw[i]);
-                b.trem[x] = (uint8_t)(vp[i] & 0xFFu);
-            }
+    for (int i = 0; i < 8; ++i) {
+        const int c = 8 * k + i;
+        if (c < R.C) {
+            const long long x = o.pb + c;
+            b.soc[x] = __uint_as_float(vs[i]);
+            b.erem[x] = __uint_as_float(ve[i]);
+            b.cap[x] = __uint_as_float(vc[i]);
+            b.rbar[x] = __uint_as_float(vr[i]);
+            b.pw[x] = __uint_as_float(vw[i]);
+            b.trem[x] = (uint8_t)(vp[i] & 0xFFu);
         }
     }
-    if (!o.live || o.half != 0) return;
+    if (k != 0) return;
     const int s = o.slot;
     b.tod[s] = o.t;
     b.day[s] = o.day;
     b.gstep[s] = o.g;
     b.ncar[s] = o.ncar;
     b.ep_ret[s] = o.ret;
-    if (o.ended) b.last_ret[s] = o.last_ret;
-    b.n_episodes[s] += o.st_eps;
-    b.st_arrived[s] += o.st_arr;
-    b.st_rejected[s] += o.st_rej;
-    b.st_missing[s] += o.st_miss;
-    b.st_charged[s] += o.st_chg;
+    if (rs.st.ended[row]) b.last_ret[s] = rs.st.last_ret[row];
+    b.n_episodes[s] += rs.st.eps[row];
+    b.st_arrived[s] += rs.st.arr[row];
+    b.st_rejected[s] += rs.st.rej[row];
+    b.st_missing[s] += rs.st.miss[row];
+    b.st_charged[s] += rs.st.chg[row];
 }
 
 template <int LT>
-__global__ void __launch_bounds__(kThreads, 1) k_rollout(const __grid_constant__ WMaps wm, const RolloutArgs R)
+__global__ void __launch_bounds__(kRollThreads, 1) k_rollout(const __grid_constant__ WMaps wm, const RolloutArgs R)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* A = aligned_smem(smem_raw);
@@ -979,7 +1121,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rollout(const __grid_constant__
     const PolicyArgs& a = R.pol;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int j = threadIdx.x; j < 2 * kPolicyHidden + a.n_out_pad; j += blockDim.x) bias_s[j] = a.bias[j];
-    if (threadIdx.x == 0) init_sync(S, kRollStages);
+    if (threadIdx.x == 0) init_sync(S, kRollStages, kRollWorkers);
     if (warp == 1) tmem_alloc(&S.tmem, kTmemCols);
     fence_before();
     __syncthreads();
@@ -993,46 +1135,48 @@ __global__ void __launch_bounds__(kThreads, 1) k_rollout(const __grid_constant__
         if (lane == 0) issue<kRollStages>(a, A, ring, S, tmem, R.T);
         __syncwarp();
     } else {
-        const int ew = warp - 2, q = warp & 3, h = ew >> 2;
+        const int ew = warp - 2, q = warp & 3, part = ew >> 2;
         const int row = 32 * q + lane;
         const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);
         const uint32_t abase = smem_addr(A);
         const long long env = (long long)tile * kM + row;
         const bool live = env < a.E;
-        Owner o;
-        owner_load(o, R, tile, row, h, tl, rs);
-        owner_observe(o, R, 0, q, lane, tl, abase, rs.u.stage[ew]);
+        {
+            Owner o;
+            owner_load(o, R, tile, row, part, tl, rs);
+        }
+        owner_observe(R, env, part, 0, q, lane, tl, abase, rs.u.stage[ew], rs);
         for (int it = 0; it < R.T; ++it) {
             fence_before();
-            named_sync(kBarWorkers, kWorkers);     // every observation (and its parked power) written
+            named_sync(kBarWorkers, kRollWorkers);   // every observation (and its parked power) written
             fence_after();
-            layer_bias(a, bias_s, tl, 0, h);
+            layer_bias_part(a, bias_s, tl, 0, part);
             worker_arrive(&S.xrdy);
             for (int L = 0; L < 2; ++L) {
                 wait_sync(&S.acc, (3 * it + L) & 1, S, a.err);
                 fence_after();
-                hidden_epilogue(tl + (uint32_t)(128 * h), abase, row, 128 * h);
-                layer_bias(a, bias_s, tl, L + 1, h);
+                hidden_epilogue<2>(tl + (uint32_t)(64 * part), abase, row, 64 * part);
+                layer_bias_part(a, bias_s, tl, L + 1, part);
                 worker_arrive(&S.hrdy);
             }
             wait_sync(&S.acc, (3 * it + 2) & 1, S, a.err);
             fence_after();
-            uint32_t packed[4];
-            sample_row<LT>(a, tl, h, env, live, rs.gstep[row], rs.key0[row], rs.key1[row],
-                           (a.logits && live) ? a.logits + ((long long)it * a.E + env) * a.n_ports * a.n_levels
-                                              : nullptr,
-                           packed);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) rs.act[row * (kPolicyMaxPorts / 4) + 4 * h + j] = packed[j];
-            if (live) store_levels(a.actions + ((long long)it * a.E + env) * a.n_ports, h, a.n_ports, packed);
+            uint32_t packed[2];
+            sample_part<LT>(a, tl, part, env, live, rs.rw.g[row], rs.rw.k0[row], rs.rw.k1[row],
+                            (a.logits && live) ? a.logits + ((long long)it * a.E + env) * a.n_ports * a.n_levels
+                                               : nullptr,
+                            packed);
+            rs.act[row * (kPolicyMaxPorts / 4) + 2 * part] = packed[0];
+            rs.act[row * (kPolicyMaxPorts / 4) + 2 * part + 1] = packed[1];
+            if (live) store_levels_part(a.actions + ((long long)it * a.E + env) * a.n_ports, part, a.n_ports, packed);
             fence_before();
-            named_sync(kBarWorkers, kWorkers);
+            named_sync(kBarWorkers, kRollWorkers);
             fence_after();
-            owner_step(o, R, it, row, tl, rs);
-            named_sync(kBarWorkers, kWorkers);                 // group scales done: the staging may overwrite them
-            if (it + 1 < R.T) owner_observe(o, R, it + 1, q, lane, tl, abase, rs.u.stage[ew]);
+            owner_step(R, env, part, it, row, tl, rs);
+            named_sync(kBarWorkers, kRollWorkers);               // group scales done: the staging may overwrite them
+            if (it + 1 < R.T) owner_observe(R, env, part, it + 1, q, lane, tl, abase, rs.u.stage[ew], rs);
         }
-        owner_store(o, R, tl);
+        owner_store(R, env, part, tl, row, rs);
     }
     fence_before();
     __syncthreads();
@@ -1107,9 +1251,9 @@ cudaError_t launch_rollout(const WMaps& wm, const RolloutArgs& r, cudaStream_t s
     const int n_tiles = (r.pol.E + kM - 1) / kM;
     if (n_tiles <= 0 || r.T <= 0) return cudaSuccess;
     if (r.pol.n_levels == 11)
-        k_rollout<11><<<n_tiles, kThreads, kRolloutSmem, st>>>(wm, r);
+        k_rollout<11><<<n_tiles, kRollThreads, kRolloutSmem, st>>>(wm, r);
     else
-        k_rollout<0><<<n_tiles, kThreads, kRolloutSmem, st>>>(wm, r);
+        k_rollout<0><<<n_tiles, kRollThreads, kRolloutSmem, st>>>(wm, r);
     return cudaGetLastError();
 }
 
