@@ -59,7 +59,6 @@ constexpr int kBarWorkers = 1;             // named barrier of the worker warps
 // k_rollout: TMEM columns of the env state, 32 per field (charger c at +c)
 constexpr int kColSoc = 352, kColErem = 384, kColCap = 416, kColRbar = 448;
 constexpr int kColPack = 480;              // remaining stay | meta << 8
-constexpr int kColPw = 0;                  // last applied power, parked in accumulator columns between MLP passes
 
 struct Sync {
     uint64_t full[kMaxStages], empty[kMaxStages];
@@ -529,6 +528,7 @@ struct RollSmem {
     } u;
     RowStats st;
     RowState rw;
+    float pw[kPolicyMaxPorts * kM];        // charger x row: the last applied power
     uint32_t act[kM * kPolicyMaxPorts / 4]; // sampled levels, row-major [row][charger] bytes
 };
 
@@ -701,7 +701,8 @@ __device__ __forceinline__ void owner_load(Owner& o, const RolloutArgs& R, int t
     tmem_st8(taddr_of(tl, kColCap + 8 * part), vc);
     tmem_st8(taddr_of(tl, kColRbar + 8 * part), vr);
     tmem_st8(taddr_of(tl, kColPack + 8 * part), vp);
-    tmem_st8(taddr_of(tl, kColPw + 8 * part), vw);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) rs.pw[(8 * part + i) * kM + row] = __uint_as_float(vw[i]);
     tmem_wait_st();
     rs.u.x.occ[part][row] = occ;
     fence_before();
@@ -915,7 +916,8 @@ __device__ __forceinline__ void owner_step(const RolloutArgs& R, long long e, in
         tmem_st4(taddr_of(tl, kColCap + c4), vc);
         tmem_st4(taddr_of(tl, kColRbar + c4), vr);
         tmem_st4(taddr_of(tl, kColPack + c4), vp);
-        tmem_st4(taddr_of(tl, kColPw + c4), vw);
+#pragma unroll
+        for (int ii = 0; ii < 4; ++ii) rs.pw[(c4 + ii) * kM + row] = __uint_as_float(vw[ii]);
     }
     tmem_wait_st();
     rs.u.x.se[h][row] = se;
@@ -972,6 +974,9 @@ __device__ __forceinline__ void owner_step(const RolloutArgs& R, long long e, in
 // features), every lane on its own row; BF16 into the layer-1 operand, FP32
 // to HBM through the warp's staging buffer, kObsRows rows at a time, each
 // row's chunk a contiguous, 16-byte aligned run.
+// kPass 0: the BF16 operand; kPass 1 / 2: the FP32 rows 0-15 / 16-31 of the
+// warp to HBM (issued while layers 1 / 3 run on the tensor core)
+template <int kPass>
 __device__ __forceinline__ void owner_observe(const RolloutArgs& R, long long e, int part, int it, int q, int lane,
                                               uint32_t tl, uint32_t abase, float* stage, const RollSmem& rs)
 {
@@ -983,12 +988,12 @@ __device__ __forceinline__ void owner_observe(const RolloutArgs& R, long long e,
     const int n_chunks = (N + 7) >> 3;
     const int k = part;
     if (k >= n_chunks) return;                              // uniform across the warp
-    uint32_t vs[8], ve[8], vr[8], vp[8], vw[8];
+    if (kPass > 0 && !R.obs_out) return;
+    uint32_t vs[8], ve[8], vr[8], vp[8];
     tmem_ld8(taddr_of(tl, kColSoc + 8 * k), vs);
     tmem_ld8(taddr_of(tl, kColErem + 8 * k), ve);
     tmem_ld8(taddr_of(tl, kColRbar + 8 * k), vr);
     tmem_ld8(taddr_of(tl, kColPack + 8 * k), vp);
-    tmem_ld8(taddr_of(tl, kColPw + 8 * k), vw);
     tmem_wait_ld();
     // features [f0, f1): the station's 8 in chunk 0, then 6 per charger
     const int f0 = k == 0 ? 0 : 8 + 48 * k;
@@ -1003,7 +1008,7 @@ __device__ __forceinline__ void owner_observe(const RolloutArgs& R, long long e,
         const int c = 8 * k + i;
         if (live && c < N) {
             obs_port<false>(cf + 6 * i, (int)(vp[i] & 0xFFu), 0, __uint_as_float(vs[i]), __uint_as_float(ve[i]),
-                            __uint_as_float(vr[i]), __uint_as_float(vw[i]), (vp[i] >> 8) & kMetaDC, p);
+                            __uint_as_float(vr[i]), rs.pw[c * kM + row], (vp[i] >> 8) & kMetaDC, p);
         } else {
 #pragma unroll
             for (int x = 0; x < 6; ++x) cf[6 * i + x] = 0.f;
@@ -1014,25 +1019,28 @@ __device__ __forceinline__ void owner_observe(const RolloutArgs& R, long long e,
         if (k == 0) return j < 8 ? st8[j < 8 ? j : 0] : cf[j >= 8 && j < 56 ? j - 8 : 0];
         return j < 48 ? cf[j < 48 ? j : 0] : 0.f;
     };
-    // BF16 into the operand (pairs; the K padding up to 16 is zero)
     const int n_f = f1 - f0;
-    const bool last = k == n_chunks - 1;
-    const int n_fp = last ? (((D + 15) & ~15) - f0) : n_f;
+    if (kPass == 0) {
+        // BF16 into the operand (pairs; the K padding up to 16 is zero)
+        const bool last = k == n_chunks - 1;
+        const int n_fp = last ? (((D + 15) & ~15) - f0) : n_f;
 #pragma unroll
-    for (int j = 0; j < 56; j += 2) {
-        if (j < n_fp) {
-            const float x0 = j < n_f ? V(j) : 0.f, x1 = j + 1 < n_f ? V(j + 1) : 0.f;
-            st_shared_u32(abase + sw128_offset(row, f0 + j, kChunkBytes), pack_bf16x2(x0, x1));
+        for (int j = 0; j < 56; j += 2) {
+            if (j < n_fp) {
+                const float x0 = j < n_f ? V(j) : 0.f, x1 = j + 1 < n_f ? V(j + 1) : 0.f;
+                st_shared_u32(abase + sw128_offset(row, f0 + j, kChunkBytes), pack_bf16x2(x0, x1));
+            }
         }
+        if (last && n_fp > 56) {                             // padding beyond the chunk's own width
+            for (int j = 56; j < n_fp; j += 2) st_shared_u32(abase + sw128_offset(row, f0 + j, kChunkBytes), 0u);
+        }
+        return;
     }
-    if (last && n_fp > 56) {                                 // padding beyond the chunk's own width
-        for (int j = 56; j < n_fp; j += 2) st_shared_u32(abase + sw128_offset(row, f0 + j, kChunkBytes), 0u);
-    }
-    if (!R.obs_out) return;
     static_assert(kObsRows == 8, "4 lanes per staged row");
     const int r = lane >> 2;                                // the staged row this lane copies
+    constexpr int kRounds = 32 / kObsRows / 2;
 #pragma unroll 1
-    for (int rnd = 0; rnd < 32 / kObsRows; ++rnd) {
+    for (int rnd = (kPass - 1) * kRounds; rnd < kPass * kRounds; ++rnd) {
         if ((lane >> 3) == rnd) {
             float* srow = stage + (lane & 7) * kStageRow;
 #pragma unroll
@@ -1072,13 +1080,12 @@ __device__ __forceinline__ void owner_store(const RolloutArgs& R, long long e, i
     owner_get(o, R, e, row, part, rs);
     const DevBatch& b = R.b;
     const int k = o.part;
-    uint32_t vs[8], ve[8], vc[8], vr[8], vp[8], vw[8];
+    uint32_t vs[8], ve[8], vc[8], vr[8], vp[8];
     tmem_ld8(taddr_of(tl, kColSoc + 8 * k), vs);
     tmem_ld8(taddr_of(tl, kColErem + 8 * k), ve);
     tmem_ld8(taddr_of(tl, kColCap + 8 * k), vc);
     tmem_ld8(taddr_of(tl, kColRbar + 8 * k), vr);
     tmem_ld8(taddr_of(tl, kColPack + 8 * k), vp);
-    tmem_ld8(taddr_of(tl, kColPw + 8 * k), vw);
     tmem_wait_ld();
     if (!o.live) return;
 #pragma unroll
@@ -1090,7 +1097,7 @@ __device__ __forceinline__ void owner_store(const RolloutArgs& R, long long e, i
             b.erem[x] = __uint_as_float(ve[i]);
             b.cap[x] = __uint_as_float(vc[i]);
             b.rbar[x] = __uint_as_float(vr[i]);
-            b.pw[x] = __uint_as_float(vw[i]);
+            b.pw[x] = rs.pw[c * kM + row];
             b.trem[x] = (uint8_t)(vp[i] & 0xFFu);
         }
     }
@@ -1145,19 +1152,22 @@ __global__ void __launch_bounds__(kRollThreads, 1) k_rollout(const __grid_consta
             Owner o;
             owner_load(o, R, tile, row, part, tl, rs);
         }
-        owner_observe(R, env, part, 0, q, lane, tl, abase, rs.u.stage[ew], rs);
+        owner_observe<0>(R, env, part, 0, q, lane, tl, abase, rs.u.stage[ew], rs);
         for (int it = 0; it < R.T; ++it) {
             fence_before();
-            named_sync(kBarWorkers, kRollWorkers);   // every observation (and its parked power) written
+            named_sync(kBarWorkers, kRollWorkers);   // every observation operand written
             fence_after();
             layer_bias_part(a, bias_s, tl, 0, part);
             worker_arrive(&S.xrdy);
+            // the observation's FP32 rows go to HBM while layers 1 and 3 run
+            owner_observe<1>(R, env, part, it, q, lane, tl, abase, rs.u.stage[ew], rs);
             for (int L = 0; L < 2; ++L) {
                 wait_sync(&S.acc, (3 * it + L) & 1, S, a.err);
                 fence_after();
                 hidden_epilogue<2>(tl + (uint32_t)(64 * part), abase, row, 64 * part);
                 layer_bias_part(a, bias_s, tl, L + 1, part);
                 worker_arrive(&S.hrdy);
+                if (L == 1) owner_observe<2>(R, env, part, it, q, lane, tl, abase, rs.u.stage[ew], rs);
             }
             wait_sync(&S.acc, (3 * it + 2) & 1, S, a.err);
             fence_after();
@@ -1174,7 +1184,7 @@ __global__ void __launch_bounds__(kRollThreads, 1) k_rollout(const __grid_consta
             fence_after();
             owner_step(R, env, part, it, row, tl, rs);
             named_sync(kBarWorkers, kRollWorkers);               // group scales done: the staging may overwrite them
-            if (it + 1 < R.T) owner_observe(R, env, part, it + 1, q, lane, tl, abase, rs.u.stage[ew], rs);
+            if (it + 1 < R.T) owner_observe<0>(R, env, part, it + 1, q, lane, tl, abase, rs.u.stage[ew], rs);
         }
         owner_store(R, env, part, tl, row, rs);
     }
