@@ -486,7 +486,8 @@ typedef struct chx_srv_stats_t {
 } chx_srv_stats_t;
 
 /* Start a server on the current device: allocate the pool and tick buffers,
- * start the scheduler and completion threads.  CHX_EINVAL, CHX_ENOMEM. */
+ * capture the tick graphs, start the scheduler thread.  CHX_EINVAL,
+ * CHX_ENOMEM. */
 int chx_srv_start(const chx_srv_cfg* cfg, chx_srv** out);
 /* Finish in-flight ticks, stop the threads, free everything. */
 int chx_srv_stop(chx_srv* s);
@@ -499,9 +500,11 @@ int chx_srv_admit(chx_srv* s, const chx_stations* st, uint64_t seed, int32_t* h_
  * else CHX_EINVAL and nothing is evicted. */
 int chx_srv_evict(chx_srv* s, const int32_t* h_ids, int32_t n);
 /* Queue a request; *ticket identifies it.  The output buffers must stay valid
- * until the ticket completes.  At most 65536 tickets may be outstanding
- * (submitted and not yet released by chx_srv_wait / chx_srv_test), else
- * CHX_ENOMEM.  A ticket is waited on or tested by one thread at a time. */
+ * until the ticket completes.  Ticket t uses request record t mod 65536: while
+ * the ticket 65536 before it is not yet released (by chx_srv_wait /
+ * chx_srv_test), the call waits for another thread to release it, up to
+ * 200 ms, then returns CHX_ENOMEM with no ticket taken.  A ticket is waited on
+ * or tested by one thread at a time. */
 int chx_srv_submit(chx_srv* s, const chx_srv_req* r, uint64_t* ticket);
 /* Block until the ticket completes (CHX_ETIMEOUT after timeout_us), copy its
  * results to the request's buffers and release the ticket.  latency_ns (may be

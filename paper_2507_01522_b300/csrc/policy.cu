@@ -467,6 +467,7 @@ constexpr int kRollWorkers = kRollWorkerWarps * 32;
 constexpr int kRollThreads = (2 + kRollWorkerWarps) * 32;
 constexpr int kParts = 4;                  // threads per station
 constexpr int kPartPorts = 8;              // chargers per part
+static_assert(kParts * kPartPorts == 32, "a part's chargers tile the 32 columns of a station's state block");
 
 // A station's scalars between steps, one record per row in shared memory:
 // part 0 writes it at the end of a step, every part reads it (the phases are

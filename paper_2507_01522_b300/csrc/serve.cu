@@ -46,7 +46,6 @@
 #include <memory>
 #include <mutex>
 #include <random>
-#include <shared_mutex>
 #include <string>
 #include <thread>
 #include <vector>
@@ -72,6 +71,7 @@ inline int64_t now_ns()
 }
 
 constexpr uint64_t kMaxOutstanding = 1u << 16;   // request records (power of two)
+constexpr int64_t kRecordWaitMs = 200;             // a submission's wait for its record to be released
 
 // bytes a station of class c occupies in the pool (state + statics)
 inline double slot_bytes(int c) { return (double)(8 << c) * 33.0 + 128.0; }
@@ -443,6 +443,88 @@ inline void cpu_relax()
 #endif
 }
 
+// Per-thread slots of the submission path: each host thread takes one (by a
+// thread-local index, shared by every server), so that the per-request
+// bookkeeping below touches a cache line that no other thread writes.
+constexpr int kThreadSlots = 64;
+inline int thread_slot()
+{
+    static std::atomic<int> next{0};
+    thread_local const int i = next.fetch_add(1, std::memory_order_relaxed) % kThreadSlots;
+    return i;
+}
+struct alignas(64) ThreadSlot {
+    std::atomic<int> readers{0};           // submissions of the slot's threads inside the admin lock
+    std::atomic<int64_t> ns_submit{0}, ns_complete{0};
+};
+
+// Admission and eviction against submissions: many readers (submissions, each
+// on its own thread slot), rare writers (admit / evict).  A reader announces
+// itself on its slot, then checks the writer flag; a writer raises the flag,
+// then waits until every slot is empty (both sides sequentially consistent,
+// so one of them always sees the other).
+struct AdminLock {
+    ThreadSlot slot[kThreadSlots];
+    alignas(64) std::atomic<int> writer{0};
+    std::mutex writers;                    // one writer at a time
+    void lock_shared(int i)
+    {
+        for (;;) {
+            slot[i].readers.fetch_add(1, std::memory_order_seq_cst);
+            if (!writer.load(std::memory_order_seq_cst)) return;
+            slot[i].readers.fetch_sub(1, std::memory_order_seq_cst);
+            for (int n = 0; writer.load(std::memory_order_acquire); ++n)
+                if (n < 64) cpu_relax();
+                else std::this_thread::yield();
+        }
+    }
+    void unlock_shared(int i) { slot[i].readers.fetch_sub(1, std::memory_order_release); }
+    void lock()
+    {
+        writers.lock();
+        writer.store(1, std::memory_order_seq_cst);
+        for (int i = 0; i < kThreadSlots; ++i)
+            for (int n = 0; slot[i].readers.load(std::memory_order_seq_cst) != 0; ++n)
+                if (n < 64) cpu_relax();
+                else std::this_thread::yield();
+    }
+    void unlock()
+    {
+        writer.store(0, std::memory_order_release);
+        writers.unlock();
+    }
+};
+struct SharedAdmin {                       // scoped reader
+    AdminLock& l;
+    int i;
+    bool held = true;
+    SharedAdmin(AdminLock& l_, int i_) : l(l_), i(i_) { l.lock_shared(i); }
+    void unlock()
+    {
+        if (held) l.unlock_shared(i);
+        held = false;
+    }
+    ~SharedAdmin() { unlock(); }
+};
+
+// The ticket counter and the running totals of submitted work, on one cache
+// line behind a spin lock: the critical section is a few stores, so a
+// waiting thread spins instead of sleeping in the kernel.
+struct alignas(64) TicketState {
+    std::atomic<int> busy{0};
+    uint64_t next_ticket = 1;
+    int64_t cum_envs = 0, cum_act = 0, cum_obs = 0;
+    void lock()
+    {
+        for (int n = 0;; ++n) {
+            if (!busy.load(std::memory_order_relaxed) && !busy.exchange(1, std::memory_order_acquire)) return;
+            if (n < 256) cpu_relax();
+            else std::this_thread::yield();
+        }
+    }
+    void unlock() { busy.store(0, std::memory_order_release); }
+};
+
 }  // namespace
 
 struct chx_srv {
@@ -467,7 +549,7 @@ struct chx_srv {
     cudaStream_t admin = nullptr;          // admission uploads
     cudaStream_t st = nullptr;             // the ticks, in order
     FusedSide side;                        // the 128-charger class's step beside the smaller classes'
-    std::shared_mutex admin_mu;            // admit / evict exclusive, submit shared
+    AdminLock admin_mu;                    // admit / evict exclusive, submit shared
 
     // requests
     PinnedPool pool;                       // the records' buffers
@@ -477,10 +559,7 @@ struct chx_srv {
     TickResult* h_result = nullptr;        // [n_streams] pinned, mapped
     TickArgs* h_args = nullptr;            // [n_streams] pinned, mapped: each tick slot's arguments
     TickArgs* d_args = nullptr;            // their device address
-    std::mutex ticket_mu;
-    uint64_t next_ticket = 1;
-    int64_t cum_envs = 0, cum_act = 0, cum_obs = 0;
-    std::atomic<int> queued_hint{0};       // submissions since the scheduler last looked
+    TicketState tk;                        // tickets and running totals
     std::atomic<bool> sleeping{false};     // the scheduler blocks on `wake`
 
     // ticks
@@ -502,7 +581,7 @@ struct chx_srv {
     uint64_t n_ticks = 0, n_requests = 0, n_env_steps = 0, n_resets = 0;
     double busy_ms = 0.0;
     int64_t t_start = 0;
-    std::atomic<int64_t> ns_submit{0}, ns_scan{0}, ns_launch{0}, ns_complete{0}, n_scans{0};
+    std::atomic<int64_t> ns_scan{0}, ns_launch{0}, n_scans{0};   // the scheduler's (submit and collect time: per thread slot)
 };
 
 namespace {
@@ -835,12 +914,15 @@ void scheduler(chx_srv* s)
         }
         {
             std::unique_lock<std::mutex> lk(s->wake_mu);
-            s->sleeping.store(true);
-            s->wake.wait_for(lk, std::chrono::microseconds(200),
-                             [&] { return s->queued_hint.load() > 0 || s->stopping.load(); });
-            s->sleeping.store(false);
+            s->sleeping.store(true, std::memory_order_seq_cst);
+            s->wake.wait_for(lk, std::chrono::microseconds(200), [&] {
+                const Request& q = s->table[pub & mask];
+                return (q.state.load(std::memory_order_seq_cst) == kQueued &&
+                        q.ticket.load(std::memory_order_relaxed) == pub) ||
+                       s->stopping.load();
+            });
+            s->sleeping.store(false, std::memory_order_relaxed);
         }
-        s->queued_hint.store(0);
         idle = 0;
     }
 }
@@ -856,7 +938,7 @@ int collect(chx_srv* s, Request& q, int64_t* latency_ns)
         if (q.h_obs) std::memcpy(q.h_obs, q.obs.h, (size_t)q.obs_floats * sizeof(float));
     }
     q.state.store(kFree, std::memory_order_release);
-    s->ns_complete += now_ns() - t0;
+    s->admin_mu.slot[thread_slot()].ns_complete.fetch_add(now_ns() - t0, std::memory_order_relaxed);
     return CHX_OK;
 }
 
@@ -1018,7 +1100,7 @@ extern "C" int chx_srv_admit(chx_srv* s, const chx_stations* st, uint64_t seed, 
     if (st->h_n_upper) return fail(CHX_EINVAL, "the serving loop takes two-level trees (h_n_upper = NULL)");
     int rc = validate_stations(st, &s->cfg.exo, 1LL << 24);
     if (rc) return rc;
-    std::unique_lock<std::shared_mutex> lk(s->admin_mu);
+    std::unique_lock<AdminLock> lk(s->admin_mu);
     // all or nothing: class capacity and HBM budget
     int need[kNumClasses] = {};
     double bytes = 0.0;
@@ -1104,7 +1186,7 @@ extern "C" int chx_srv_admit(chx_srv* s, const chx_stations* st, uint64_t seed, 
 extern "C" int chx_srv_evict(chx_srv* s, const int32_t* h_ids, int32_t n)
 {
     if (!s || (!h_ids && n > 0) || n < 0) return fail(CHX_EINVAL, "bad argument");
-    std::unique_lock<std::shared_mutex> lk(s->admin_mu);
+    std::unique_lock<AdminLock> lk(s->admin_mu);
     for (int j = 0; j < n; ++j) {
         const int e = h_ids[j];
         if (e < 0 || e >= s->b.n_slots || !s->slot[e].admitted) return fail(CHX_EINVAL, "station id not admitted");
@@ -1155,7 +1237,8 @@ extern "C" int chx_srv_submit(chx_srv* s, const chx_srv_req* r, uint64_t* ticket
     while (cap < 2 * (size_t)n) cap *= 2;
     if (set.size() < cap) set.resize(cap);
     std::fill(set.begin(), set.begin() + cap, -1);
-    std::shared_lock<std::shared_mutex> lk(s->admin_mu);
+    const int ts = thread_slot();
+    SharedAdmin lk(s->admin_mu, ts);
     if (s->stopping.load()) return fail(CHX_EINVAL, "server is stopping");
     int64_t n_act = 0;
     for (int j = 0; j < n; ++j) {
@@ -1181,12 +1264,24 @@ extern "C" int chx_srv_submit(chx_srv* s, const chx_srv_req* r, uint64_t* ticket
     Request* q = nullptr;
     uint64_t tk = 0;
     {
-        std::lock_guard<std::mutex> g(s->ticket_mu);
-        tk = s->next_ticket;
-        q = &s->table[tk & (kMaxOutstanding - 1)];
-        int expect = kFree;
-        if (!q->state.compare_exchange_strong(expect, kFilling, std::memory_order_acq_rel))
-            return fail(CHX_ENOMEM, "too many outstanding requests: release tickets with chx_srv_wait or chx_srv_test");
+        // The next ticket's record is still held when a request kMaxOutstanding
+        // tickets older is not yet released: wait for it (another thread
+        // releasing it), up to kRecordWaitMs, then give up.
+        TicketState& T = s->tk;
+        const int64_t deadline = t_in + kRecordWaitMs * 1000000LL;
+        for (int spins = 0;; ++spins) {
+            T.lock();
+            tk = T.next_ticket;
+            q = &s->table[tk & (kMaxOutstanding - 1)];
+            int expect = kFree;
+            if (q->state.compare_exchange_strong(expect, kFilling, std::memory_order_acq_rel)) break;
+            T.unlock();
+            if (now_ns() >= deadline)
+                return fail(CHX_ENOMEM,
+                            "too many outstanding requests: release tickets with chx_srv_wait or chx_srv_test");
+            if (spins < 64) cpu_relax();
+            else std::this_thread::sleep_for(std::chrono::microseconds(20));
+        }
         int rc = grow_pinned(s->pool, q->ids, (size_t)n);
         if (!rc && step) rc = grow_pinned(s->pool, q->rew, (size_t)n);
         if (!rc && step) rc = grow_pinned(s->pool, q->done, (size_t)n);
@@ -1194,15 +1289,17 @@ extern "C" int chx_srv_submit(chx_srv* s, const chx_srv_req* r, uint64_t* ticket
         if (!rc && obs_floats) rc = grow_pinned(s->pool, q->obs, (size_t)obs_floats);
         if (rc) {
             q->state.store(kFree, std::memory_order_release);
+            T.unlock();
             return rc;
         }
-        ++s->next_ticket;
-        q->cum_envs = s->cum_envs;
-        q->cum_act = s->cum_act;
-        q->cum_obs = s->cum_obs;
-        s->cum_envs += n;
-        if (given) s->cum_act += n_act;
-        s->cum_obs += obs_floats;
+        ++T.next_ticket;
+        q->cum_envs = T.cum_envs;
+        q->cum_act = T.cum_act;
+        q->cum_obs = T.cum_obs;
+        T.cum_envs += n;
+        if (given) T.cum_act += n_act;
+        T.cum_obs += obs_floats;
+        T.unlock();
     }
     std::memcpy(q->ids.h, r->h_env_ids, (size_t)n * sizeof(int32_t));
     if (given) std::memcpy(q->acts.h, r->h_actions, (size_t)n_act);
@@ -1230,15 +1327,17 @@ extern "C" int chx_srv_submit(chx_srv* s, const chx_srv_req* r, uint64_t* ticket
     q->obs_floats = obs_floats;
     q->t_submit = now_ns();
     q->ticket.store(tk, std::memory_order_relaxed);
-    q->state.store(kQueued, std::memory_order_release);    // published
+    // published; then, if the scheduler has gone to sleep, wake it (it raises
+    // `sleeping` before it looks for published records, both sequentially
+    // consistent, so either it sees this record or this thread sees the flag)
+    q->state.store(kQueued, std::memory_order_seq_cst);
     lk.unlock();
     *ticket = tk;
-    s->queued_hint.fetch_add(1);
-    if (s->sleeping.load()) {
+    if (s->sleeping.load(std::memory_order_seq_cst)) {
         std::lock_guard<std::mutex> g(s->wake_mu);
         s->wake.notify_one();
     }
-    s->ns_submit += now_ns() - t_in;
+    s->admin_mu.slot[ts].ns_submit.fetch_add(now_ns() - t_in, std::memory_order_relaxed);
     return CHX_OK;
 }
 
@@ -1306,17 +1405,22 @@ extern "C" int chx_srv_stats(chx_srv* s, chx_srv_stats_t* out)
         out->device_busy_ms = s->busy_ms;
     }
     {
-        std::shared_lock<std::shared_mutex> lk(s->admin_mu);
+        SharedAdmin lk(s->admin_mu, thread_slot());
         out->resident = s->n_resident;
         out->used_bytes = s->used_bytes;
     }
     out->budget_bytes = s->cfg.hbm_budget_bytes;
     out->elapsed_ms = (double)(now_ns() - s->t_start) * 1e-6;
-    out->host_submit_ms = s->ns_submit.load() * 1e-6;
+    int64_t ns_submit = 0, ns_complete = 0;
+    for (const ThreadSlot& t : s->admin_mu.slot) {
+        ns_submit += t.ns_submit.load(std::memory_order_relaxed);
+        ns_complete += t.ns_complete.load(std::memory_order_relaxed);
+    }
+    out->host_submit_ms = ns_submit * 1e-6;
     out->host_scan_ms = s->ns_scan.load() * 1e-6;
     out->host_pack_ms = 0.0;
     out->host_launch_ms = s->ns_launch.load() * 1e-6;
-    out->host_complete_ms = s->ns_complete.load() * 1e-6;
+    out->host_complete_ms = ns_complete * 1e-6;
     out->n_scans = s->n_scans.load();
     return CHX_OK;
 }
@@ -1335,6 +1439,13 @@ extern "C" int chx_srv_simulate(chx_srv* s, const chx_srv_sim_cfg* c, const int3
         return fail(CHX_EINVAL, "bad simulation configuration");
     const int A = c->n_actors, per = c->envs_per_actor;
     std::atomic<int> err{0};
+    std::mutex err_mu;
+    std::string err_msg;                   // the first failing call's message
+    auto record = [&](const char* call) {
+        std::lock_guard<std::mutex> g(err_mu);
+        if (err_msg.empty()) err_msg = std::string(call) + ": " + chx_last_error();
+        err = 1;
+    };
     std::vector<std::vector<int64_t>> lat(c->n_threads);
     std::vector<int64_t> steps(c->n_threads, 0), nreq(c->n_threads, 0);
     const int64_t t0 = now_ns();
@@ -1374,7 +1485,7 @@ extern "C" int chx_srv_simulate(chx_srv* s, const chx_srv_sim_cfg* c, const int3
                     int32_t d = 0;
                     int64_t l = 0;
                     if (chx_srv_test(s, x.ticket, &d, &l)) {
-                        err = 1;
+                        record("chx_srv_test");
                         return;
                     }
                     if (d) {
@@ -1399,8 +1510,10 @@ extern "C" int chx_srv_simulate(chx_srv* s, const chx_srv_sim_cfg* c, const int3
                     r.h_reward = x.rew.data();
                     r.h_done = x.done.data();
                     r.seed = c->seed + (uint64_t)x.count;
-                    if (chx_srv_submit(s, &r, &x.ticket)) {
-                        err = 2;
+                    const int rc = chx_srv_submit(s, &r, &x.ticket);
+                    if (rc == CHX_ENOMEM) continue;   // every record held: try again on the next pass
+                    if (rc) {
+                        record("chx_srv_submit");
                         return;
                     }
                     x.busy = true;
@@ -1416,7 +1529,7 @@ extern "C" int chx_srv_simulate(chx_srv* s, const chx_srv_sim_cfg* c, const int3
     for (int w = 0; w < c->n_threads; ++w) th.emplace_back(worker, w);
     for (auto& t : th) t.join();
     chx_srv_stats(s, &st1);
-    if (err.load()) return fail(CHX_EINVAL, "a simulated actor's call failed");
+    if (err.load()) return fail(CHX_EINVAL, "a simulated actor's call failed: " + err_msg);
     std::vector<int64_t> all;
     int64_t total_steps = 0, total_req = 0;
     for (int w = 0; w < c->n_threads; ++w) {
