@@ -194,6 +194,14 @@ __device__ __forceinline__ void st_shared_u32(uint32_t addr, uint32_t v)
 {
     asm volatile("st.shared.b32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
 }
+// one 32-byte global store (a full sector; the address 32-byte aligned)
+__device__ __forceinline__ void st_global_v8(float* p, float a, float b, float c, float d, float e, float f, float g,
+                                             float h)
+{
+    asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d),
+                 "f"(e), "f"(f), "f"(g), "f"(h)
+                 : "memory");
+}
 
 // two FP32 -> packed BF16 pair, round to nearest even (lo in bits 0-15)
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)

@@ -52,7 +52,7 @@ constexpr int kWorkers = kWorkerWarps * 32;
 constexpr int kThreads = (2 + kWorkerWarps) * 32;
 constexpr uint32_t kTmemCols = 512;
 constexpr int kPolStages = 4;              // weight ring of k_policy
-constexpr int kRollStages = 3;             // weight ring of k_rollout
+constexpr int kRollStages = 4;             // weight ring of k_rollout
 constexpr int kMaxStages = kPolStages;
 constexpr int kBarWorkers = 1;             // named barrier of the worker warps
 
@@ -156,15 +156,23 @@ __device__ void produce(const WMaps* wm, const PolicyArgs& a, unsigned char* rin
 }
 
 // ---- MMA issuer ------------------------------------------------------------
-template <int NS>
+// kBiasTmem: every layer accumulates onto the bias the workers placed in
+// TMEM; else each layer's first MMA overwrites the accumulator and the
+// workers add the bias when they read it.
+template <int NS, bool kBiasTmem = true>
 __device__ void issue(const PolicyArgs& a, unsigned char* A, unsigned char* ring, Sync& S, uint32_t tmem,
                       int n_passes)
 {
+    // descriptors of the operand's and the ring's first rows; a K = 16 step
+    // (32 bytes) or a chunk / stage further is an offset in 16-byte units
+    // (both buffers lie far below the field's 256 KB limit)
+    const uint64_t a0 = sdesc_sw128(A), r0 = sdesc_sw128(ring);
     uint32_t s = 0;
     for (int it = 0; it < n_passes; ++it) {
         wait_sync<false>(&S.xrdy, it & 1, S, a.err);
         fence_after();
-        for (int L = 0; L < 3; ++L) {
+#pragma unroll
+        for (int L = 0; L < 3; ++L) {      // unrolled: the issue sequence of each layer is straight-line code
             if (L > 0) {
                 wait_sync<false>(&S.hrdy, (2 * it + L - 1) & 1, S, a.err);
                 fence_after();
@@ -173,16 +181,18 @@ __device__ void issue(const PolicyArgs& a, unsigned char* A, unsigned char* ring
             const int chunks = L == 0 ? a.ch1 : 4;
             for (int p = 0; p < parts; ++p) {
                 const uint32_t id = idesc_bf16_f32(kM, part_rows(a, L, p));
+                const uint32_t dt = tmem + (uint32_t)(p * kStageRows);
                 for (int k = 0; k < chunks; ++k, ++s) {
                     const uint32_t slot = s % NS;
                     wait_sync<false>(&S.full[slot], (s / NS) & 1, S, a.err);
                     fence_after();
                     if (is_bad(S)) continue;
                     const int nks = (L == 0 && k == chunks - 1) ? a.ks1_last : 4;
-                    unsigned char* bst = ring + slot * kStageBytes;
-                    for (int j = 0; j < nks; ++j)          // onto the bias the workers placed in TMEM
-                        mma_bf16(tmem + (uint32_t)(p * kStageRows), sdesc_sw128(A + k * kChunkBytes + j * 32),
-                                 sdesc_sw128(bst + j * 32), id, true);
+                    const uint64_t ad = a0 + (uint64_t)((k * kChunkBytes) >> 4);
+                    const uint64_t bd = r0 + (uint64_t)((slot * kStageBytes) >> 4);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (j < nks) mma_bf16(dt, ad + 2 * j, bd + 2 * j, id, kBiasTmem || k > 0 || j > 0);
                     mma_commit(&S.empty[slot]);
                 }
             }
@@ -228,8 +238,11 @@ __device__ __forceinline__ void layer_bias(const PolicyArgs& a, const float* bia
 }
 
 // ---- epilogue of layers 1 and 2: ReLU, BF16 into A (NB blocks of 32 columns)
+// bias (layer's bias vector, or nullptr when it is already in TMEM) is
+// added to the accumulator before the ReLU
 template <int NB>
-__device__ __forceinline__ void hidden_epilogue(uint32_t taddr, uint32_t abase, int row, int col0)
+__device__ __forceinline__ void hidden_epilogue(uint32_t taddr, uint32_t abase, int row, int col0,
+                                                const float* bias = nullptr)
 {
 #pragma unroll 1
     for (int blk = 0; blk < NB; ++blk) {
@@ -237,6 +250,10 @@ __device__ __forceinline__ void hidden_epilogue(uint32_t taddr, uint32_t abase, 
         uint32_t v[32];
         tmem_ld32(taddr + (uint32_t)(32 * blk), v);
         tmem_wait_ld();
+        if (bias) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] = __float_as_uint(__uint_as_float(v[j]) + bias[c + j]);
+        }
         uint32_t q[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j)
@@ -466,6 +483,7 @@ constexpr int kRollWorkerWarps = 16;
 constexpr int kRollWorkers = kRollWorkerWarps * 32;
 constexpr int kRollThreads = (2 + kRollWorkerWarps) * 32;
 constexpr int kParts = 4;                  // threads per station
+constexpr int kBarQuad = 2;                // named barriers 2..5: the four warps that share rows 32q .. 32q + 31
 constexpr int kPartPorts = 8;              // chargers per part
 static_assert(kParts * kPartPorts == 32, "a part's chargers tile the 32 columns of a station's state block");
 
@@ -499,12 +517,6 @@ struct RowStats {
     float miss[kM], chg[kM], last_ret[kM];
 };
 
-// Observation staging: kObsRows rows of one part's chunk (8 chargers, plus
-// the 8 station features in chunk 0) per worker warp; row stride kStageRow
-// floats.  It shares its space with the step's group scales and exchanges.
-constexpr int kStageRow = 8 + 48 + 4;      // 16-byte aligned rows
-constexpr int kObsRows = 8;                // rows per staging round
-
 // values the four parts of a station exchange during a step (per part, row);
 // the second members of the unions are written only after every read of the
 // first (the exchanges are barrier-separated)
@@ -519,18 +531,23 @@ struct Xchg {
     int nfree[kParts][kM];
 };
 
+// What the sampling and the environment step share, placed in the
+// activation operand: from the completion of a step's last layer (the
+// tensor core has read the operand) until the next observation is written
+// into it (after the workers' barrier that ends the step), the operand
+// holds nothing live.
+struct StepScratch {
+    float gscale[32 * kM];                 // group slot x row
+    Xchg x;
+    uint32_t act[kM * kPolicyMaxPorts / 4]; // sampled levels, row-major [row][charger] bytes
+};
+static_assert(sizeof(StepScratch) <= kActBytes, "the step's scratch fits in the activation operand");
+
+// per-CTA state that lives for the whole rollout
 struct RollSmem {
-    union {                                // the step's group scales and exchanges, then the observation staging
-        struct {
-            float gscale[32 * kM];         // group slot x row
-            Xchg x;
-        };
-        float stage[kRollWorkerWarps][kObsRows * kStageRow];
-    } u;
     RowStats st;
     RowState rw;
     float pw[kPolicyMaxPorts * kM];        // charger x row: the last applied power
-    uint32_t act[kM * kPolicyMaxPorts / 4]; // sampled levels, row-major [row][charger] bytes
 };
 
 // the station's record -> registers (every part, at the start of a step)
@@ -588,29 +605,12 @@ __device__ __noinline__ uint4 car_words_late(uint32_t uid, uint32_t n, uint32_t 
     return car_words(uid, n, k0, k1);
 }
 
-// bias of layer L into the accumulator columns part `part` may write: hidden
-// columns 64 part .. +63 (those its layer-2 epilogue reads) and, for layer 3,
-// the block 256 + 32 part .. +31 of the columns beyond the hidden ones
-__device__ __forceinline__ void layer_bias_part(const PolicyArgs& a, const float* bias_s, uint32_t tl, int L, int part)
-{
-    const float* b = bias_s + kPolicyHidden * L;
-    const int n = L < 2 ? kPolicyHidden : a.n_out_pad;
-#pragma unroll 1
-    for (int c = 64 * part; c < 64 * part + 64; c += 32)
-        if (c < n) bias_to_tmem(tl + (uint32_t)c, b + c);
-    if (L == 2) {
-        const int c = 256 + 32 * part;
-        if (c < n) bias_to_tmem(tl + (uint32_t)c, b + c);
-    }
-    tmem_wait_st();
-}
-
 // Levels of chargers 8 part .. 8 part + 7 of the env in TMEM lane `tl`, four
 // per block; returns them packed 4 per word.
 template <int LT>
 __device__ __forceinline__ void sample_part(const PolicyArgs& a, uint32_t tl, int part, long long env, bool live,
                                             uint32_t g, uint32_t k0, uint32_t k1, float* logits_env,
-                                            uint32_t (&packed)[2])
+                                            uint32_t (&packed)[2], const float* bias3)
 {
     const int L = LT ? LT : a.n_levels;
     uint4 words[2];
@@ -627,6 +627,9 @@ __device__ __forceinline__ void sample_part(const PolicyArgs& a, uint32_t tl, in
         tmem_ld16(tl + (uint32_t)(L * c0 + 32), v + 32);
         tmem_wait_ld();
         if (!live) continue;
+#pragma unroll
+        for (int j = 0; j < 4 * kPolicyGroup; ++j)     // the output layer's bias (columns past the last used: 0)
+            if (j < 4 * L) v[j] = __float_as_uint(__uint_as_float(v[j]) + bias3[L * c0 + j]);
         packed[blk] = sample4<LT>(v, c0, a.n_ports, a.n_levels, blk == 0 ? words[0] : words[1],
                                   logits_env ? logits_env + (long long)c0 * L : nullptr);
     }
@@ -648,7 +651,7 @@ __device__ __forceinline__ void store_levels_part(int8_t* dst, int part, int n_p
 // Load the station's state (every part: station fields; each part: its 8
 // chargers into TMEM).  Ends with the workers' named barrier (occupancy).
 __device__ __forceinline__ void owner_load(Owner& o, const RolloutArgs& R, int tile, int row, int part, uint32_t tl,
-                                           RollSmem& rs)
+                                           RollSmem& rs, StepScratch& sx)
 {
     const DevBatch& b = R.b;
     o.e = (long long)tile * kM + row;
@@ -705,22 +708,23 @@ __device__ __forceinline__ void owner_load(Owner& o, const RolloutArgs& R, int t
 #pragma unroll
     for (int i = 0; i < 8; ++i) rs.pw[(8 * part + i) * kM + row] = __uint_as_float(vw[i]);
     tmem_wait_st();
-    rs.u.x.occ[part][row] = occ;
+    sx.x.occ[part][row] = occ;
     fence_before();
     named_sync(kBarWorkers, kRollWorkers);
     fence_after();
     o.occ = 0;
 #pragma unroll
-    for (int j = 0; j < kParts; ++j) o.occ += rs.u.x.occ[j][row];
+    for (int j = 0; j < kParts; ++j) o.occ += sx.x.occ[j][row];
     if (part == 0) owner_put(o, row, rs);
-    named_sync(kBarWorkers, kRollWorkers);           // every read done: the staging may reuse the space
+    named_sync(kBarWorkers, kRollWorkers);           // every read done: the operand may be written
 }
 
 // One environment step of the station with this step's sampled levels
 // (Appendix A.2 then A.3; the operations of the fused step kernel), this
-// thread's 8 chargers, four exchanges with the other parts.
+// thread's 8 chargers, four exchanges with the other parts (each a barrier
+// of the four warps that hold these rows only).
 __device__ __forceinline__ void owner_step(const RolloutArgs& R, long long e, int part, int it, int row, uint32_t tl,
-                                           RollSmem& rs)
+                                           RollSmem& rs, StepScratch& sx)
 {
     Owner o;
     owner_get(o, R, e, row, part, rs);
@@ -736,8 +740,8 @@ __device__ __forceinline__ void owner_step(const RolloutArgs& R, long long e, in
     const float* F = b.cdf + ((size_t)o.cls_row * (size_t)p.ep_len + (size_t)o.t) * kCdfLen;
     const float4 f0 = __ldg(reinterpret_cast<const float4*>(F));
     const float4 f1 = __ldg(reinterpret_cast<const float4*>(F + 4));
-    const uint32_t lv0 = rs.act[row * (kPolicyMaxPorts / 4) + 2 * h];
-    const uint32_t lv1 = rs.act[row * (kPolicyMaxPorts / 4) + 2 * h + 1];
+    const uint32_t lv0 = sx.act[row * (kPolicyMaxPorts / 4) + 2 * h];
+    const uint32_t lv1 = sx.act[row * (kPolicyMaxPorts / 4) + 2 * h + 1];
 
     // (i) per-charger clip; sums of the groups that close in this part
     float P[8];
@@ -776,7 +780,7 @@ __device__ __forceinline__ void owner_step(const RolloutArgs& R, long long e, in
                     lead = gacc;
                 } else {
                     const float gc = __ldg(b.gcap + o.pb + 8 * h + i);
-                    rs.u.gscale[gs * kM + row] = gacc > gc ? __fdividef(gc, gacc) : 1.0f;
+                    sx.gscale[gs * kM + row] = gacc > gc ? __fdividef(gc, gacc) : 1.0f;
                     if (p.a_con != 0.f) over = fmaxf(over, (gacc - gc) * __ldg(b.ginv_eta + o.pb + 8 * h + i));
                 }
                 any_tail = true;
@@ -785,38 +789,38 @@ __device__ __forceinline__ void owner_step(const RolloutArgs& R, long long e, in
             }
         }
     }
-    rs.u.x.lead[h][row] = lead;
-    rs.u.x.trail[h][row] = gacc;
-    rs.u.x.first_gs[h][row] = first_gs;
-    rs.u.x.has_tail[h][row] = any_tail ? 1 : 0;
-    rs.u.x.raw[h][row] = raw;
-    rs.u.x.nfree[h][row] = nfree;
-    named_sync(kBarWorkers, kRollWorkers);                           // exchange A
+    sx.x.lead[h][row] = lead;
+    sx.x.trail[h][row] = gacc;
+    sx.x.first_gs[h][row] = first_gs;
+    sx.x.has_tail[h][row] = any_tail ? 1 : 0;
+    sx.x.raw[h][row] = raw;
+    sx.x.nfree[h][row] = nfree;
+    named_sync(kBarQuad + (row >> 5), kParts * 32);                  // exchange A
 
     // a group that closes here but began in an earlier part: its sum is this
     // part's lead plus the open sums of the parts back to the one it began in
     if (first_gs >= 0) {
         float S = lead;
         for (int j = h - 1; j >= 0; --j) {
-            S += rs.u.x.trail[j][row];
-            if (rs.u.x.has_tail[j][row]) break;
+            S += sx.x.trail[j][row];
+            if (sx.x.has_tail[j][row]) break;
         }
         const float gc = __ldg(b.gcap + o.pb + 8 * h + first_tail);
-        rs.u.gscale[first_gs * kM + row] = S > gc ? __fdividef(gc, S) : 1.0f;
+        sx.gscale[first_gs * kM + row] = S > gc ? __fdividef(gc, S) : 1.0f;
         if (p.a_con != 0.f) over = fmaxf(over, (S - gc) * __ldg(b.ginv_eta + o.pb + 8 * h + first_tail));
     }
-    rs.u.x.over[h][row] = over;
+    sx.x.over[h][row] = over;
     int nfree_all = 0, before = 0;
 #pragma unroll
     for (int j = 0; j < kParts; ++j) {
-        const int nf = rs.u.x.nfree[j][row];
+        const int nf = sx.x.nfree[j][row];
         nfree_all += nf;
         before += j < h ? nf : 0;
     }
     float raw_all = 0.f;
 #pragma unroll
-    for (int j = 0; j < kParts; ++j) raw_all += rs.u.x.raw[j][row];
-    named_sync(kBarWorkers, kRollWorkers);                           // exchange B: every group's scale
+    for (int j = 0; j < kParts; ++j) raw_all += sx.x.raw[j][row];
+    named_sync(kBarQuad + (row >> 5), kParts * 32);                  // exchange B: every group's scale
 
     // architecture constraint: charger power scaled by its group
     float sp = 0.f;
@@ -827,21 +831,21 @@ __device__ __forceinline__ void owner_step(const RolloutArgs& R, long long e, in
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const uint32_t meta = vp[i] >> 8;
-            if (meta & kMetaValid) P[i] *= rs.u.gscale[((meta >> kMetaGroupShift) & 31u) * kM + row];
+            if (meta & kMetaValid) P[i] *= sx.gscale[((meta >> kMetaGroupShift) & 31u) * kM + row];
             sp += P[i];
         }
     }
-    rs.u.x.sp[h][row] = sp;
-    named_sync(kBarWorkers, kRollWorkers);                           // exchange C
+    sx.x.sp[h][row] = sp;
+    named_sync(kBarQuad + (row >> 5), kParts * 32);                  // exchange C
     float sp_all = 0.f;
 #pragma unroll
-    for (int j = 0; j < kParts; ++j) sp_all += rs.u.x.sp[j][row];
+    for (int j = 0; j < kParts; ++j) sp_all += sx.x.sp[j][row];
     const float s_root = sp_all > o.grid_cap ? __fdividef(o.grid_cap, sp_all) : 1.0f;
     float c_con = 0.f;
     if (p.a_con != 0.f) {
         float over_all = 0.f;
 #pragma unroll
-        for (int j = 0; j < kParts; ++j) over_all = fmaxf(over_all, rs.u.x.over[j][row]);
+        for (int j = 0; j < kParts; ++j) over_all = fmaxf(over_all, sx.x.over[j][row]);
         c_con = fmaxf(fmaxf(over_all, (raw_all - o.grid_cap) * o.grid_inv_eta), 0.f);
     }
 
@@ -921,17 +925,17 @@ __device__ __forceinline__ void owner_step(const RolloutArgs& R, long long e, in
         for (int ii = 0; ii < 4; ++ii) rs.pw[(c4 + ii) * kM + row] = __uint_as_float(vw[ii]);
     }
     tmem_wait_st();
-    rs.u.x.se[h][row] = se;
-    rs.u.x.csat[h][row] = c_sat;
-    rs.u.x.occ[h][row] = occ;
-    named_sync(kBarWorkers, kRollWorkers);                           // exchange D
+    sx.x.se[h][row] = se;
+    sx.x.csat[h][row] = c_sat;
+    sx.x.occ[h][row] = occ;
+    named_sync(kBarQuad + (row >> 5), kParts * 32);                  // exchange D
     float se_all = 0.f, csat_all = 0.f;
     int occ_all = 0;
 #pragma unroll
     for (int j = 0; j < kParts; ++j) {
-        se_all += rs.u.x.se[j][row];
-        csat_all += rs.u.x.csat[j][row];
-        occ_all += rs.u.x.occ[j][row];
+        se_all += sx.x.se[j][row];
+        csat_all += sx.x.csat[j][row];
+        occ_all += sx.x.occ[j][row];
     }
     o.occ = occ_all;
 
@@ -972,24 +976,19 @@ __device__ __forceinline__ void owner_step(const RolloutArgs& R, long long e, in
 }
 
 // Observation after the step: this part's chunk (part 0 also the 8 station
-// features), every lane on its own row; BF16 into the layer-1 operand, FP32
-// to HBM through the warp's staging buffer, kObsRows rows at a time, each
-// row's chunk a contiguous, 16-byte aligned run.
-// kPass 0: the BF16 operand; kPass 1 / 2: the FP32 rows 0-15 / 16-31 of the
-// warp to HBM (issued while layers 1 / 3 run on the tensor core)
-template <int kPass>
+// features), every lane on its own row: BF16 into the layer-1 operand, and
+// the FP32 row's chunk straight to HBM as the lane's own contiguous run
+// (32-byte sectors when the row length keeps them aligned).
 __device__ __forceinline__ void owner_observe(const RolloutArgs& R, long long e, int part, int it, int q, int lane,
-                                              uint32_t tl, uint32_t abase, float* stage, const RollSmem& rs)
+                                              uint32_t tl, uint32_t abase, const RollSmem& rs)
 {
     const DevParams& p = R.p;
     const int D = R.pol.obs_dim, N = R.pol.n_ports;
     const int row = 32 * q + lane;
-    const long long e0 = e - lane;                          // env of the warp's first row
     const bool live = e < R.pol.E;
     const int n_chunks = (N + 7) >> 3;
     const int k = part;
     if (k >= n_chunks) return;                              // uniform across the warp
-    if (kPass > 0 && !R.obs_out) return;
     uint32_t vs[8], ve[8], vr[8], vp[8];
     tmem_ld8(taddr_of(tl, kColSoc + 8 * k), vs);
     tmem_ld8(taddr_of(tl, kColErem + 8 * k), ve);
@@ -1021,55 +1020,36 @@ __device__ __forceinline__ void owner_observe(const RolloutArgs& R, long long e,
         return j < 48 ? cf[j < 48 ? j : 0] : 0.f;
     };
     const int n_f = f1 - f0;
-    if (kPass == 0) {
-        // BF16 into the operand (pairs; the K padding up to 16 is zero)
-        const bool last = k == n_chunks - 1;
-        const int n_fp = last ? (((D + 15) & ~15) - f0) : n_f;
+    // BF16 into the operand, one 16-byte swizzle unit (8 features) per store:
+    // f0 and the padded width are multiples of 8, so units never straddle a
+    // chunk; the K padding up to a multiple of 16 is zero
+    const bool last = k == n_chunks - 1;
+    const int n_fp = last ? (((D + 15) & ~15) - f0) : n_f;
+    auto B = [&](int j) -> float { return j < n_f ? V(j) : 0.f; };
 #pragma unroll
-        for (int j = 0; j < 56; j += 2) {
-            if (j < n_fp) {
-                const float x0 = j < n_f ? V(j) : 0.f, x1 = j + 1 < n_f ? V(j + 1) : 0.f;
-                st_shared_u32(abase + sw128_offset(row, f0 + j, kChunkBytes), pack_bf16x2(x0, x1));
-            }
-        }
-        if (last && n_fp > 56) {                             // padding beyond the chunk's own width
-            for (int j = 56; j < n_fp; j += 2) st_shared_u32(abase + sw128_offset(row, f0 + j, kChunkBytes), 0u);
-        }
-        return;
-    }
-    static_assert(kObsRows == 8, "4 lanes per staged row");
-    const int r = lane >> 2;                                // the staged row this lane copies
-    constexpr int kRounds = 32 / kObsRows / 2;
-#pragma unroll 1
-    for (int rnd = (kPass - 1) * kRounds; rnd < kPass * kRounds; ++rnd) {
-        if ((lane >> 3) == rnd) {
-            float* srow = stage + (lane & 7) * kStageRow;
+    for (int j = 0; j < 64; j += 8)
+        if (j < n_fp)
+            st_shared_v4(abase + sw128_offset(row, f0 + j, kChunkBytes), pack_bf16x2(B(j), B(j + 1)),
+                         pack_bf16x2(B(j + 2), B(j + 3)), pack_bf16x2(B(j + 4), B(j + 5)),
+                         pack_bf16x2(B(j + 6), B(j + 7)));
+    if (R.obs_out && live) {
+        // the FP32 row's run of this part: full 32-byte sectors when the
+        // row length keeps them aligned, else 8-byte pairs / single floats
+        float* dst = R.obs_out + ((long long)it * R.pol.E + e) * D + f0;
+        if ((D & 7) == 0 && (reinterpret_cast<uintptr_t>(R.obs_out) & 31) == 0) {
 #pragma unroll
-            for (int j = 0; j < 56; j += 4)
-                if (j < n_f) *reinterpret_cast<float4*>(srow + j) = make_float4(V(j), V(j + 1), V(j + 2), V(j + 3));
-        }
-        __syncwarp();
-        const long long eb = e0 + kObsRows * rnd;
-        if (eb + r < (long long)R.pol.E) {
-            float* dst = R.obs_out + ((long long)it * R.pol.E + eb + r) * D + f0;
-            const float* src = stage + r * kStageRow;
-            if ((D & 3) == 0) {                             // a row's run: at most 14 float4
+            for (int j = 0; j < 56; j += 8)
+                if (j < n_f) st_global_v8(dst + j, V(j), V(j + 1), V(j + 2), V(j + 3), V(j + 4), V(j + 5), V(j + 6),
+                                          V(j + 7));
+        } else if ((D & 1) == 0) {
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int c4 = (lane & 3) + 4 * i;
-                    if (4 * c4 < n_f)
-                        *reinterpret_cast<float4*>(dst + 4 * c4) = *reinterpret_cast<const float4*>(src + 4 * c4);
-                }
-            } else {                                        // at most 28 float2
+            for (int j = 0; j < 56; j += 2)
+                if (j < n_f) *reinterpret_cast<float2*>(dst + j) = make_float2(V(j), V(j + 1));
+        } else {
 #pragma unroll
-                for (int i = 0; i < 7; ++i) {
-                    const int c2 = (lane & 3) + 4 * i;
-                    if (2 * c2 < n_f)
-                        *reinterpret_cast<float2*>(dst + 2 * c2) = *reinterpret_cast<const float2*>(src + 2 * c2);
-                }
-            }
+            for (int j = 0; j < 56; ++j)
+                if (j < n_f) dst[j] = V(j);
         }
-        __syncwarp();
     }
 }
 
@@ -1124,6 +1104,7 @@ __global__ void __launch_bounds__(kRollThreads, 1) k_rollout(const __grid_consta
     unsigned char* A = aligned_smem(smem_raw);
     unsigned char* ring = A + kActBytes;
     RollSmem& rs = *reinterpret_cast<RollSmem*>(ring + kRollStages * kStageBytes);
+    StepScratch& sx = *reinterpret_cast<StepScratch*>(A);
     __shared__ Sync S;
     __shared__ __align__(16) float bias_s[2 * kPolicyHidden + kPolicyMaxPorts * kPolicyGroup];
     const PolicyArgs& a = R.pol;
@@ -1140,7 +1121,7 @@ __global__ void __launch_bounds__(kRollThreads, 1) k_rollout(const __grid_consta
         if (lane == 0) produce<kRollStages>(&wm, a, ring, S, R.T);
         __syncwarp();
     } else if (warp == 1) {
-        if (lane == 0) issue<kRollStages>(a, A, ring, S, tmem, R.T);
+        if (lane == 0) issue<kRollStages, false>(a, A, ring, S, tmem, R.T);
         __syncwarp();
     } else {
         const int ew = warp - 2, q = warp & 3, part = ew >> 2;
@@ -1151,24 +1132,19 @@ __global__ void __launch_bounds__(kRollThreads, 1) k_rollout(const __grid_consta
         const bool live = env < a.E;
         {
             Owner o;
-            owner_load(o, R, tile, row, part, tl, rs);
+            owner_load(o, R, tile, row, part, tl, rs, sx);
         }
-        owner_observe<0>(R, env, part, 0, q, lane, tl, abase, rs.u.stage[ew], rs);
+        owner_observe(R, env, part, 0, q, lane, tl, abase, rs);
         for (int it = 0; it < R.T; ++it) {
             fence_before();
             named_sync(kBarWorkers, kRollWorkers);   // every observation operand written
             fence_after();
-            layer_bias_part(a, bias_s, tl, 0, part);
             worker_arrive(&S.xrdy);
-            // the observation's FP32 rows go to HBM while layers 1 and 3 run
-            owner_observe<1>(R, env, part, it, q, lane, tl, abase, rs.u.stage[ew], rs);
             for (int L = 0; L < 2; ++L) {
                 wait_sync(&S.acc, (3 * it + L) & 1, S, a.err);
                 fence_after();
-                hidden_epilogue<2>(tl + (uint32_t)(64 * part), abase, row, 64 * part);
-                layer_bias_part(a, bias_s, tl, L + 1, part);
+                hidden_epilogue<2>(tl + (uint32_t)(64 * part), abase, row, 64 * part, bias_s + kPolicyHidden * L);
                 worker_arrive(&S.hrdy);
-                if (L == 1) owner_observe<2>(R, env, part, it, q, lane, tl, abase, rs.u.stage[ew], rs);
             }
             wait_sync(&S.acc, (3 * it + 2) & 1, S, a.err);
             fence_after();
@@ -1176,16 +1152,16 @@ __global__ void __launch_bounds__(kRollThreads, 1) k_rollout(const __grid_consta
             sample_part<LT>(a, tl, part, env, live, rs.rw.g[row], rs.rw.k0[row], rs.rw.k1[row],
                             (a.logits && live) ? a.logits + ((long long)it * a.E + env) * a.n_ports * a.n_levels
                                                : nullptr,
-                            packed);
-            rs.act[row * (kPolicyMaxPorts / 4) + 2 * part] = packed[0];
-            rs.act[row * (kPolicyMaxPorts / 4) + 2 * part + 1] = packed[1];
+                            packed, bias_s + 2 * kPolicyHidden);
+            sx.act[row * (kPolicyMaxPorts / 4) + 2 * part] = packed[0];
+            sx.act[row * (kPolicyMaxPorts / 4) + 2 * part + 1] = packed[1];
             if (live) store_levels_part(a.actions + ((long long)it * a.E + env) * a.n_ports, part, a.n_ports, packed);
             fence_before();
-            named_sync(kBarWorkers, kRollWorkers);
+            named_sync(kBarQuad + q, kParts * 32);              // the rows' sampled levels
             fence_after();
-            owner_step(R, env, part, it, row, tl, rs);
-            named_sync(kBarWorkers, kRollWorkers);               // group scales done: the staging may overwrite them
-            if (it + 1 < R.T) owner_observe<0>(R, env, part, it + 1, q, lane, tl, abase, rs.u.stage[ew], rs);
+            owner_step(R, env, part, it, row, tl, rs, sx);
+            named_sync(kBarWorkers, kRollWorkers);               // the step's scratch is read: the operand may be written
+            if (it + 1 < R.T) owner_observe(R, env, part, it + 1, q, lane, tl, abase, rs);
         }
         owner_store(R, env, part, tl, row, rs);
     }
