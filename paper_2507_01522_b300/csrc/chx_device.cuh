@@ -288,14 +288,14 @@ __device__ __forceinline__ int arrivals(const DevBatch& b, const DevParams& p, u
 
 // observation features of a station (p.obs_env floats: 8, + battery SoC and
 // power / rate in V2G mode) and of one charger (6 floats)
-__device__ __forceinline__ void obs_env(float* o, int t, int day, int occ, int n, float bsoc, float bpw,
-                                        const DevBatch& b, const DevParams& p)
+__device__ __forceinline__ void obs_env_at(float* o, int t, int day, int occ, int n, float bsoc, float bpw,
+                                           float price, const DevParams& p)
 {
     float s, c;
     sincospif(2.0f * (float)t * p.obs_inv_len, &s, &c);
     o[0] = s;
     o[1] = c;
-    o[2] = __ldg(b.price + (size_t)day * (size_t)p.ep_len + (size_t)t);
+    o[2] = price;
     o[3] = p.p_sell;
     o[4] = (float)occ / (float)n;
     o[5] = (float)day * p.obs_inv_days;
@@ -306,11 +306,34 @@ __device__ __forceinline__ void obs_env(float* o, int t, int day, int occ, int n
         o[9] = bpw * p.obs_inv_batt_rate;
     }
 }
+// the same with the price of (day, t) read from the batch's price table
+__device__ __forceinline__ void obs_env(float* o, int t, int day, int occ, int n, float bsoc, float bpw,
+                                        const DevBatch& b, const DevParams& p)
+{
+    obs_env_at(o, t, day, occ, n, bsoc, bpw, __ldg(b.price + (size_t)day * (size_t)p.ep_len + (size_t)t), p);
+}
 
 // per-charger features (p.obs_port of them): occupied, SoC, stay / max stay
 // (a charge-sensitive car's Delta t_remain), r_hat / P_max, last power /
 // P_max, remaining demand / max capacity, and with charge-sensitive users u
 // (CS = false: a caller that never runs with charge-sensitive users)
+// feature x (0..5, as obs_port orders them) of a charger without a
+// charge-sensitive user
+__device__ __forceinline__ float obs_port_feature(int x, int trem, float soc, float erem, float rbar, float pw, bool dc,
+                                                  const DevParams& p)
+{
+    const float inv_pmax = dc ? p.inv_pmax1 : p.inv_pmax0;
+    const bool on = trem > 0;
+    switch (x) {
+        case 0: return on ? 1.0f : 0.0f;
+        case 1: return soc;
+        case 2: return (float)trem * p.obs_inv_stay;
+        case 3: return on ? taper(soc, rbar, p) * inv_pmax : 0.0f;
+        case 4: return pw * inv_pmax;
+        default: return erem * p.obs_inv_cap;
+    }
+}
+
 template <bool CS = true>
 __device__ __forceinline__ void obs_port(float* o, int trem, int due, float soc, float erem, float rbar, float pw,
                                          bool dc, const DevParams& p)

@@ -719,6 +719,15 @@ __device__ __forceinline__ void owner_load(Owner& o, const RolloutArgs& R, int t
     named_sync(kBarWorkers, kRollWorkers);           // every read done: the operand may be written
 }
 
+// FP32 observation rows as 32-byte sectors: the row length and the buffer
+// keep every part's run, and each half of it, 32-byte aligned (uniform for
+// the launch).  The environment step then writes the next observation's
+// rows itself while its state is in registers.
+__device__ __forceinline__ bool obs_sectors(const RolloutArgs& R)
+{
+    return R.obs_out && (R.pol.obs_dim & 7) == 0 && (reinterpret_cast<uintptr_t>(R.obs_out) & 31) == 0;
+}
+
 // One environment step of the station with this step's sampled levels
 // (Appendix A.2 then A.3; the operations of the fused step kernel), this
 // thread's 8 chargers, four exchanges with the other parts (each a barrier
@@ -864,6 +873,9 @@ __device__ __forceinline__ void owner_step(const RolloutArgs& R, long long e, in
 
     // (ii) charge, (iii) departures, (iv) arrivals, and the episode end
     const bool fin = o.t + 1 >= p.ep_len;
+    // the next observation's FP32 rows go out from here (the BF16 operand is
+    // written after the step's last barrier, when the scratch is free)
+    const bool next_rows = o.live && it + 1 < R.T && obs_sectors(R);
     float se = 0.f, c_sat = 0.f;
     int adm = 0, occ = 0;
 #pragma unroll
@@ -923,6 +935,20 @@ __device__ __forceinline__ void owner_step(const RolloutArgs& R, long long e, in
         tmem_st4(taddr_of(tl, kColPack + c4), vp);
 #pragma unroll
         for (int ii = 0; ii < 4; ++ii) rs.pw[(c4 + ii) * kM + row] = __uint_as_float(vw[ii]);
+        if (next_rows && c4 < R.pol.n_ports) {   // chargers c4 .. c4 + 3: one aligned run of 24 floats
+            float* dst = R.obs_out + ((long long)(it + 1) * R.pol.E + o.e) * R.pol.obs_dim + 8 + 6 * c4;
+#pragma unroll
+            for (int j = 0; j < 24; j += 8) {
+                float f[8];
+#pragma unroll
+                for (int x = 0; x < 8; ++x) {
+                    const int ii = (j + x) / 6, fx = (j + x) % 6;   // charger, feature (compile-time)
+                    f[x] = obs_port_feature(fx, (int)(vp[ii] & 0xFFu), __uint_as_float(vs[ii]), __uint_as_float(ve[ii]),
+                                            __uint_as_float(vr[ii]), __uint_as_float(vw[ii]), (vp[ii] >> 8) & kMetaDC, p);
+                }
+                st_global_v8(dst + j, f[0], f[1], f[2], f[3], f[4], f[5], f[6], f[7]);
+            }
+        }
     }
     tmem_wait_st();
     sx.x.se[h][row] = se;
@@ -972,6 +998,12 @@ __device__ __forceinline__ void owner_step(const RolloutArgs& R, long long e, in
         }
         o.price = __ldg(b.price + (size_t)o.day * (size_t)p.ep_len + (size_t)o.t);
     }
+    if (h == 0 && next_rows) {             // the next observation's station features
+        float st8[8];
+        obs_env_at(st8, o.t, o.day, o.occ, R.pol.n_ports, 0.f, 0.f, o.price, p);   // charge-only mode
+        st_global_v8(R.obs_out + ((long long)(it + 1) * R.pol.E + o.e) * R.pol.obs_dim, st8[0], st8[1], st8[2], st8[3],
+                     st8[4], st8[5], st8[6], st8[7]);
+    }
     if (h == 0) owner_put(o, row, rs);
 }
 
@@ -980,7 +1012,7 @@ __device__ __forceinline__ void owner_step(const RolloutArgs& R, long long e, in
 // the FP32 row's chunk straight to HBM as the lane's own contiguous run
 // (32-byte sectors when the row length keeps them aligned).
 __device__ __forceinline__ void owner_observe(const RolloutArgs& R, long long e, int part, int it, int q, int lane,
-                                              uint32_t tl, uint32_t abase, const RollSmem& rs)
+                                              uint32_t tl, uint32_t abase, const RollSmem& rs, bool fp32)
 {
     const DevParams& p = R.p;
     const int D = R.pol.obs_dim, N = R.pol.n_ports;
@@ -1032,11 +1064,11 @@ __device__ __forceinline__ void owner_observe(const RolloutArgs& R, long long e,
             st_shared_v4(abase + sw128_offset(row, f0 + j, kChunkBytes), pack_bf16x2(B(j), B(j + 1)),
                          pack_bf16x2(B(j + 2), B(j + 3)), pack_bf16x2(B(j + 4), B(j + 5)),
                          pack_bf16x2(B(j + 6), B(j + 7)));
-    if (R.obs_out && live) {
+    if (fp32 && R.obs_out && live) {
         // the FP32 row's run of this part: full 32-byte sectors when the
         // row length keeps them aligned, else 8-byte pairs / single floats
         float* dst = R.obs_out + ((long long)it * R.pol.E + e) * D + f0;
-        if ((D & 7) == 0 && (reinterpret_cast<uintptr_t>(R.obs_out) & 31) == 0) {
+        if (obs_sectors(R)) {
 #pragma unroll
             for (int j = 0; j < 56; j += 8)
                 if (j < n_f) st_global_v8(dst + j, V(j), V(j + 1), V(j + 2), V(j + 3), V(j + 4), V(j + 5), V(j + 6),
@@ -1134,7 +1166,7 @@ __global__ void __launch_bounds__(kRollThreads, 1) k_rollout(const __grid_consta
             Owner o;
             owner_load(o, R, tile, row, part, tl, rs, sx);
         }
-        owner_observe(R, env, part, 0, q, lane, tl, abase, rs);
+        owner_observe(R, env, part, 0, q, lane, tl, abase, rs, true);
         for (int it = 0; it < R.T; ++it) {
             fence_before();
             named_sync(kBarWorkers, kRollWorkers);   // every observation operand written
@@ -1161,7 +1193,7 @@ __global__ void __launch_bounds__(kRollThreads, 1) k_rollout(const __grid_consta
             fence_after();
             owner_step(R, env, part, it, row, tl, rs, sx);
             named_sync(kBarWorkers, kRollWorkers);               // the step's scratch is read: the operand may be written
-            if (it + 1 < R.T) owner_observe(R, env, part, it + 1, q, lane, tl, abase, rs);
+            if (it + 1 < R.T) owner_observe(R, env, part, it + 1, q, lane, tl, abase, rs, !obs_sectors(R));
         }
         owner_store(R, env, part, tl, row, rs);
     }
