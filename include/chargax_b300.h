@@ -391,6 +391,8 @@ int chx_load(chx_handle* h, const void* h_buf, size_t size);
  *   d_actions [n_steps][E][N]  sampled levels
  *   d_reward [n_steps][E], d_done [n_steps][E] (each NULL to skip)
  *   d_logits NULL or [n_steps][E][N][n_levels].
+ *   d_obs, d_actions and d_logits (also in chx_policy_act) must start on a
+ *   16-byte boundary, else CHX_EINVAL.
  *   form CHX_ROLLOUT_FUSED: one kernel launch; each CTA keeps 128 envs on
  *   its SM for all n_steps (state in tensor memory, weights streamed from
  *   L2), needs N * n_levels <= 352 (else CHX_EINVAL).  CHX_ROLLOUT_SPLIT:

@@ -59,6 +59,11 @@ constexpr int kBarWorkers = 1;             // named barrier of the worker warps
 // k_rollout: TMEM columns of the env state, 32 per field (charger c at +c)
 constexpr int kColSoc = 352, kColErem = 384, kColCap = 416, kColRbar = 448;
 constexpr int kColPack = 480;              // remaining stay | meta << 8
+// k_rollout: the next observation's BF16 operand rows, packed in pairs,
+// parked by the environment step (columns the output layer's accumulator
+// has left free) until the observation pass copies them into the operand;
+// part k's run at columns kColObs + 32 k ..
+constexpr int kColObs = 0;
 
 struct Sync {
     uint64_t full[kMaxStages], empty[kMaxStages];
@@ -728,6 +733,14 @@ __device__ __forceinline__ bool obs_sectors(const RolloutArgs& R)
     return R.obs_out && (R.pol.obs_dim & 7) == 0 && (reinterpret_cast<uintptr_t>(R.obs_out) & 31) == 0;
 }
 
+// The environment step parks the next observation's operand rows in TMEM
+// when every half part (4 chargers, 24 features) is complete or empty.
+// (The FP32 rows then come from the environment step too, or are not asked for.)
+__device__ __forceinline__ bool obs_parked(const RolloutArgs& R)
+{
+    return (R.pol.n_ports & 3) == 0 && (R.obs_out == nullptr || obs_sectors(R));
+}
+
 // One environment step of the station with this step's sampled levels
 // (Appendix A.2 then A.3; the operations of the fused step kernel), this
 // thread's 8 chargers, four exchanges with the other parts (each a barrier
@@ -876,6 +889,7 @@ __device__ __forceinline__ void owner_step(const RolloutArgs& R, long long e, in
     // the next observation's FP32 rows go out from here (the BF16 operand is
     // written after the step's last barrier, when the scratch is free)
     const bool next_rows = o.live && it + 1 < R.T && obs_sectors(R);
+    const bool park = it + 1 < R.T && obs_parked(R);   // uniform across the CTA
     float se = 0.f, c_sat = 0.f;
     int adm = 0, occ = 0;
 #pragma unroll
@@ -935,6 +949,21 @@ __device__ __forceinline__ void owner_step(const RolloutArgs& R, long long e, in
         tmem_st4(taddr_of(tl, kColPack + c4), vp);
 #pragma unroll
         for (int ii = 0; ii < 4; ++ii) rs.pw[(c4 + ii) * kM + row] = __uint_as_float(vw[ii]);
+        if (park && c4 < R.pol.n_ports) {  // BF16 pairs of chargers c4 .. c4 + 3
+            uint32_t u[12];
+#pragma unroll
+            for (int x = 0; x < 12; ++x) {
+                const int ia = (2 * x) / 6, fa = (2 * x) % 6, ib = (2 * x + 1) / 6, fb = (2 * x + 1) % 6;
+                const float a0 = obs_port_feature(fa, (int)(vp[ia] & 0xFFu), __uint_as_float(vs[ia]), __uint_as_float(ve[ia]),
+                                                  __uint_as_float(vr[ia]), __uint_as_float(vw[ia]), (vp[ia] >> 8) & kMetaDC, p);
+                const float a1 = obs_port_feature(fb, (int)(vp[ib] & 0xFFu), __uint_as_float(vs[ib]), __uint_as_float(ve[ib]),
+                                                  __uint_as_float(vr[ib]), __uint_as_float(vw[ib]), (vp[ib] >> 8) & kMetaDC, p);
+                u[x] = o.live ? pack_bf16x2(a0, a1) : 0u;
+            }
+            const uint32_t col = kColObs + 32 * h + (h == 0 ? 4 : 0) + 12 * hh;
+            tmem_st8(taddr_of(tl, col), *reinterpret_cast<const uint32_t(*)[8]>(u));
+            tmem_st4(taddr_of(tl, col + 8), *reinterpret_cast<const uint32_t(*)[4]>(u + 8));
+        }
         if (next_rows && c4 < R.pol.n_ports) {   // chargers c4 .. c4 + 3: one aligned run of 24 floats
             float* dst = R.obs_out + ((long long)(it + 1) * R.pol.E + o.e) * R.pol.obs_dim + 8 + 6 * c4;
 #pragma unroll
@@ -998,11 +1027,19 @@ __device__ __forceinline__ void owner_step(const RolloutArgs& R, long long e, in
         }
         o.price = __ldg(b.price + (size_t)o.day * (size_t)p.ep_len + (size_t)o.t);
     }
-    if (h == 0 && next_rows) {             // the next observation's station features
+    if (h == 0 && (next_rows || park)) {   // the next observation's station features
         float st8[8];
         obs_env_at(st8, o.t, o.day, o.occ, R.pol.n_ports, 0.f, 0.f, o.price, p);   // charge-only mode
-        st_global_v8(R.obs_out + ((long long)(it + 1) * R.pol.E + o.e) * R.pol.obs_dim, st8[0], st8[1], st8[2], st8[3],
-                     st8[4], st8[5], st8[6], st8[7]);
+        if (next_rows)
+            st_global_v8(R.obs_out + ((long long)(it + 1) * R.pol.E + o.e) * R.pol.obs_dim, st8[0], st8[1], st8[2],
+                         st8[3], st8[4], st8[5], st8[6], st8[7]);
+        if (park) {
+            uint32_t u[4];
+#pragma unroll
+            for (int x = 0; x < 4; ++x) u[x] = o.live ? pack_bf16x2(st8[2 * x], st8[2 * x + 1]) : 0u;
+            tmem_st4(taddr_of(tl, kColObs), u);
+            tmem_wait_st();
+        }
     }
     if (h == 0) owner_put(o, row, rs);
 }
@@ -1012,7 +1049,7 @@ __device__ __forceinline__ void owner_step(const RolloutArgs& R, long long e, in
 // the FP32 row's chunk straight to HBM as the lane's own contiguous run
 // (32-byte sectors when the row length keeps them aligned).
 __device__ __forceinline__ void owner_observe(const RolloutArgs& R, long long e, int part, int it, int q, int lane,
-                                              uint32_t tl, uint32_t abase, const RollSmem& rs, bool fp32)
+                                              uint32_t tl, uint32_t abase, const RollSmem& rs, bool fp32, bool parked)
 {
     const DevParams& p = R.p;
     const int D = R.pol.obs_dim, N = R.pol.n_ports;
@@ -1021,6 +1058,27 @@ __device__ __forceinline__ void owner_observe(const RolloutArgs& R, long long e,
     const int n_chunks = (N + 7) >> 3;
     const int k = part;
     if (k >= n_chunks) return;                              // uniform across the warp
+    if (parked) {
+        // the environment step left this part's BF16 pairs in TMEM: copy
+        // them into the operand, zero units past the features (K padding)
+        const int f0 = k == 0 ? 0 : 8 + 48 * k;
+        const int n_f = min(8 + 48 * (k + 1), D) - f0;
+        const int n_fp = k == n_chunks - 1 ? (((D + 15) & ~15) - f0) : n_f;
+        uint32_t u[32];
+        u[28] = u[29] = u[30] = u[31] = 0u;
+        tmem_ld16(taddr_of(tl, kColObs + 32 * k), u);
+        tmem_ld8(taddr_of(tl, kColObs + 32 * k + 16), *reinterpret_cast<uint32_t(*)[8]>(u + 16));
+        tmem_ld4(taddr_of(tl, kColObs + 32 * k + 24), *reinterpret_cast<uint32_t(*)[4]>(u + 24));
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 64; j += 8)
+            if (j < n_fp) {
+                const bool in = j < n_f;
+                st_shared_v4(abase + sw128_offset(row, f0 + j, kChunkBytes), in ? u[j >> 1] : 0u,
+                             in ? u[(j >> 1) + 1] : 0u, in ? u[(j >> 1) + 2] : 0u, in ? u[(j >> 1) + 3] : 0u);
+            }
+        return;
+    }
     uint32_t vs[8], ve[8], vr[8], vp[8];
     tmem_ld8(taddr_of(tl, kColSoc + 8 * k), vs);
     tmem_ld8(taddr_of(tl, kColErem + 8 * k), ve);
@@ -1166,7 +1224,7 @@ __global__ void __launch_bounds__(kRollThreads, 1) k_rollout(const __grid_consta
             Owner o;
             owner_load(o, R, tile, row, part, tl, rs, sx);
         }
-        owner_observe(R, env, part, 0, q, lane, tl, abase, rs, true);
+        owner_observe(R, env, part, 0, q, lane, tl, abase, rs, true, false);
         for (int it = 0; it < R.T; ++it) {
             fence_before();
             named_sync(kBarWorkers, kRollWorkers);   // every observation operand written
@@ -1193,7 +1251,7 @@ __global__ void __launch_bounds__(kRollThreads, 1) k_rollout(const __grid_consta
             fence_after();
             owner_step(R, env, part, it, row, tl, rs, sx);
             named_sync(kBarWorkers, kRollWorkers);               // the step's scratch is read: the operand may be written
-            if (it + 1 < R.T) owner_observe(R, env, part, it + 1, q, lane, tl, abase, rs, !obs_sectors(R));
+            if (it + 1 < R.T) owner_observe(R, env, part, it + 1, q, lane, tl, abase, rs, !obs_sectors(R), obs_parked(R));
         }
         owner_store(R, env, part, tl, row, rs);
     }

@@ -212,10 +212,16 @@ extern "C" int chx_policy_load(chx_handle* h, int32_t hidden, const uint16_t* h_
     return CHX_OK;
 }
 
+// the policy kernels move observations, levels and logits in 8- to 32-byte
+// vectors: their buffers must start on a 16-byte boundary (NULL passes)
+static bool misaligned(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) != 0; }
+
 extern "C" int chx_policy_act(chx_handle* h, const float* d_obs, int8_t* d_actions, float* d_logits, void* stream)
 {
     if (!h || !d_obs || !d_actions) return fail(CHX_EINVAL, "null argument");
     if (!h->policy.loaded) return fail(CHX_EINVAL, "no policy loaded");
+    if (misaligned(d_obs) || misaligned(d_actions) || misaligned(d_logits))
+        return fail(CHX_EINVAL, "observation, level and logit buffers must be 16-byte aligned");
     return enqueue_policy(h, d_obs, d_actions, d_logits, (cudaStream_t)stream);
 }
 
@@ -241,6 +247,8 @@ extern "C" int chx_policy_rollout(chx_handle* h, int32_t n_steps, float* d_obs, 
     if (!h->policy.loaded) return fail(CHX_EINVAL, "no policy loaded");
     if (n_steps < 1) return fail(CHX_EINVAL, "n_steps must be >= 1");
     if (form != CHX_ROLLOUT_FUSED && form != CHX_ROLLOUT_SPLIT) return fail(CHX_EINVAL, "unknown rollout form");
+    if (misaligned(d_obs) || misaligned(d_actions) || misaligned(d_logits))
+        return fail(CHX_EINVAL, "observation, level and logit buffers must be 16-byte aligned");
     const chx::PolicyState& P = h->policy;
     if (form == CHX_ROLLOUT_FUSED) {
         if (!chx::rollout_fits(P.n_out_pad))

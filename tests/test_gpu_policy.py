@@ -199,11 +199,15 @@ def test_policy_rollout_matches_oracle(cuda_lib, form):
     assert len(np.unique(out[1])) == L                     # a spread of levels was sampled
 
 
-@pytest.mark.parametrize("N,E", [(20, 300), (8, 130), (32, 129)])
+@pytest.mark.parametrize("N,E", [(20, 300), (8, 130), (32, 129), (13, 70)])
 def test_fused_rollout_stressed(cuda_lib, N, E):
     """Padding charger slots (N = 20 in the 32 class), a small class (N = 8),
     ragged tiles, per-station group layouts, every reward term; two
-    rollouts back to back (the second starts from the first one's state)."""
+    rollouts back to back (the second starts from the first one's state).
+    N = 13 (a row length of 86 floats) takes the kernel's other observation
+    path: rows written from the observation pass in 8-byte pairs, the
+    operand rebuilt from the state, instead of 32-byte sectors and parked
+    operand rows from the environment step."""
     w = stressed_uniform(E, N, seed=N)
     b, pw, _ = batch_with_policy(w, seed=N, head_gain=1.0, bias_scale=0.5)
     o = Oracle(w)
@@ -294,6 +298,18 @@ def test_policy_rejects_unsupported_batches(cuda_lib):
     b.policy_rollout(2, obs, acts, form=1)
     b.check()
     assert int(acts.max()) <= 11
+    # buffers off a 16-byte boundary are refused before any launch
+    w = uniform_workload(10, 32)
+    b, pw, N = batch_with_policy(w)
+    big = torch.zeros(2 * 10 * 200 + 1, device="cuda")
+    skewed = big[1:].view(2, 10, 200)                       # 4 bytes past the allocation's start
+    for form in (0, 1):
+        with pytest.raises(ChxError) as ei:
+            b.policy_rollout(2, skewed, acts, form=form)
+        assert ei.value.code == CHX_EINVAL
+    with pytest.raises(ChxError) as ei:
+        b.policy_act(skewed[0], acts[0])
+    assert ei.value.code == CHX_EINVAL
 
 
 def test_policy_rollout_fullsize_sampled(cuda_lib):
