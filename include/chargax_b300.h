@@ -267,6 +267,15 @@ int chx_rollout_host(chx_handle* h, int32_t n_steps, float* h_reward, uint8_t* h
  * h_actions NULL: CHX_EINVAL. */
 int chx_rollout_host_actions(chx_handle* h, int32_t n_steps, const int8_t* h_actions, float* h_reward,
                              uint8_t* h_done, float* h_obs, void* stream);
+/* chx_rollout_host_actions with the levels packed two per byte (the copy in
+ * is half as large, and it is the part that bounds the call): step k's levels
+ * take ceil(n_act / 2) bytes starting at byte k * ceil(n_act / 2); slot q is
+ * the low nibble of byte q / 2 for even q, the high nibble for odd q.  Needs
+ * n_levels <= 16 (else CHX_EINVAL); nibbles of n_levels or more are clamped
+ * and flagged (chx_check).  Results equal chx_rollout_host_actions' on the
+ * same levels. */
+int chx_rollout_host_levels4(chx_handle* h, int32_t n_steps, const uint8_t* h_levels4, float* h_reward,
+                             uint8_t* h_done, float* h_obs, void* stream);
 
 /* One plain step with HOST buffers: actions are copied in (h_actions NULL =
  * Philox levels), reward/done/observation copied out; returns when done. */

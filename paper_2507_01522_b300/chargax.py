@@ -24,7 +24,7 @@ CHX_OK, CHX_EINVAL, CHX_ENOMEM, CHX_ECUDA, CHX_ETIMEOUT, CHX_EFAULT = 0, -1, -2,
 EXPORTS = (
     "chx_create", "chx_destroy", "chx_last_error", "chx_n_envs", "chx_n_ports_total", "chx_port_offsets",
     "chx_obs_size", "chx_reset", "chx_step", "chx_step_n", "chx_rollout", "chx_rollout_host", "chx_rollout_host_actions",
-    "chx_step_host",
+    "chx_rollout_host_levels4", "chx_step_host",
     "chx_autotune", "chx_set_launch", "chx_observe", "chx_get_state", "chx_set_state", "chx_stats", "chx_save",
     "chx_load", "chx_check", "chx_rollout_noalloc", "chx_policy_load", "chx_policy_act", "chx_policy_rollout",
     "chx_get_battery", "chx_set_battery", "chx_get_due", "chx_set_due", "chx_selftest_wait",
@@ -123,7 +123,7 @@ def load_library(path: str = LIB_PATH):
         "chx_reset": [vp, vp, i32, u64, vp], "chx_step": [vp, vp, i64, vp, vp, vp],
         "chx_step_n": [vp, i32, vp, i64, vp, vp, i64, vp, vp], "chx_rollout": [vp, i32, vp, vp, vp, vp],
         "chx_rollout_host": [vp, i32, vp, vp, vp, vp], "chx_step_host": [vp, vp, vp, vp, vp, vp],
-        "chx_rollout_host_actions": [vp, i32, vp, vp, vp, vp, vp],
+        "chx_rollout_host_actions": [vp, i32, vp, vp, vp, vp, vp], "chx_rollout_host_levels4": [vp, i32, vp, vp, vp, vp, vp],
         "chx_autotune": [vp, i32, vp, vp], "chx_set_launch": [vp, i32, i32], "chx_observe": [vp, vp, vp],
         "chx_get_state": [vp] + [vp] * 13, "chx_set_state": [vp] + [vp] * 13, "chx_stats": [vp] + [vp] * 6,
         "chx_save": [vp, vp, vp], "chx_load": [vp, vp, C.c_size_t], "chx_check": [vp, vp],
@@ -277,6 +277,13 @@ class Batch:
         _check(_lib.chx_rollout_host_actions(self.h, n_steps, _np_ptr(actions), _np_ptr(reward), _np_ptr(done),
                                              _np_ptr(obs), _stream_ptr(stream)))
 
+    def rollout_host_levels4(self, n_steps: int, levels4, reward=None, done=None, obs=None, stream=None):
+        """chx_rollout_host_levels4: host levels packed two per byte
+        ([n_steps][ceil(n_act / 2)] uint8, see pack_levels4) in, outputs as
+        rollout_host_actions."""
+        _check(_lib.chx_rollout_host_levels4(self.h, n_steps, _np_ptr(levels4), _np_ptr(reward), _np_ptr(done),
+                                             _np_ptr(obs), _stream_ptr(stream)))
+
     def step_host(self, actions=None, reward=None, done=None, obs=None, stream=None):
         _check(_lib.chx_step_host(self.h, _np_ptr(actions), _np_ptr(reward), _np_ptr(done), _np_ptr(obs),
                                   _stream_ptr(stream)))
@@ -382,6 +389,17 @@ class Batch:
         form = CHX_ROLLOUT_FUSED if form is None else form
         _check(_lib.chx_policy_rollout(self.h, n_steps, _dev_ptr(obs), _dev_ptr(actions), _dev_ptr(reward),
                                        _dev_ptr(done), _dev_ptr(logits), form, _stream_ptr(stream)))
+
+
+def pack_levels4(levels: np.ndarray) -> np.ndarray:
+    """[n_steps][n_act] levels 0..15 -> [n_steps][ceil(n_act / 2)] uint8, two
+    per byte (even slot in the low nibble), the layout of
+    chx_rollout_host_levels4."""
+    lv = np.asarray(levels).astype(np.uint8)
+    n_steps, n_act = lv.shape
+    if n_act % 2:
+        lv = np.concatenate([lv, np.zeros((n_steps, 1), np.uint8)], axis=1)
+    return np.ascontiguousarray(lv[:, 0::2] | (lv[:, 1::2] << 4))
 
 
 def _stations_struct(st, keep):

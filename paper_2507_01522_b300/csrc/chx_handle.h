@@ -112,7 +112,7 @@ int build_handle(const chx_stations* st, const chx_env_params* prm, const chx_ex
                  int min_pad_envs_per_class, chx_handle** out);
 int enqueue_fused(chx_handle* h, int k_steps, const int8_t* actions, long long lda, float* reward, uint8_t* done,
                   long long ld_out, float* obs, int warps, cudaStream_t st, long long ld_step = 1,
-                  long long lda_step = 1);
+                  long long lda_step = 1, int act_bits = 8);
 void free_graph(chx_handle* h);
 void free_policy(chx_handle* h);
 }  // namespace chx

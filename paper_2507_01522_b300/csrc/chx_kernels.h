@@ -16,6 +16,8 @@ struct FusedIO {
     const int8_t* actions;                 // given level of action slot q at step k: actions[q * lda + k * lda_step]
     long long lda;
     long long lda_step;
+    int act_bits;                          // 8: one int8 level per byte; 4: two levels per byte, the index
+                                           // above counting nibbles, the even one in the low nibble
     float* reward;
     uint8_t* done;
     long long ld_out;                      // env e, step k at e * ld_out + k * ld_step

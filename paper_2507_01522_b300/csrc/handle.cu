@@ -668,13 +668,15 @@ extern "C" int chx_step(chx_handle* h, const int8_t* d_actions, int64_t lda, flo
 namespace chx {
 
 int enqueue_fused(chx_handle* h, int k_steps, const int8_t* actions, long long lda, float* reward, uint8_t* done,
-                  long long ld_out, float* obs, int warps, cudaStream_t st, long long ld_step, long long lda_step)
+                  long long ld_out, float* obs, int warps, cudaStream_t st, long long ld_step, long long lda_step,
+                  int act_bits)
 {
     FusedIO io = h->sched;
     io.k_steps = k_steps;
     io.actions = actions;
     io.lda = lda;
     io.lda_step = lda_step;
+    io.act_bits = act_bits;
     io.reward = reward;
     io.done = done;
     io.ld_out = ld_out;
@@ -843,16 +845,19 @@ extern "C" int chx_rollout_host(chx_handle* h, int32_t n_steps, float* h_reward,
 // step-major) to device staging while chunk c - 1 computes; the copy stream
 // brings chunk c's rewards and done flags back while chunk c + 1 computes;
 // the observation follows the last chunk.
-extern "C" int chx_rollout_host_actions(chx_handle* h, int32_t n_steps, const int8_t* h_actions, float* h_reward,
-                                        uint8_t* h_done, float* h_obs, void* stream)
+namespace {
+// The host-actions rollout: n_steps of given levels from pinned host memory
+// (bits 8: one int8 per action slot; 4: two per byte, rows of whole bytes per
+// step), copied in kActChunks pieces on the input stream; each launch waits
+// only for its own piece, and its outputs go back while the next computes.
+int rollout_host_levels(chx_handle* h, int32_t n_steps, const void* h_levels, int bits, float* h_reward,
+                        uint8_t* h_done, float* h_obs, void* stream)
 {
-    if (!h) return fail(CHX_EINVAL, "null handle");
-    if (!h_actions) return fail(CHX_EINVAL, "h_actions is null (use chx_rollout_host for Philox actions)");
-    if (n_steps < 1) return fail(CHX_EINVAL, "n_steps must be >= 1");
     const size_t E = (size_t)h->E, ne = E * (size_t)n_steps;
     const size_t nact = (size_t)h->P + (h->dp.v2g ? E : 0);
+    const size_t row = bits == 4 ? (nact + 1) / 2 : nact;   // bytes of one step's levels
     const size_t nobs = (size_t)h->dp.obs_env * E + (size_t)h->dp.obs_port * (size_t)h->P;
-    int8_t* da = (int8_t*)staging(h, 6, nact * (size_t)n_steps);
+    char* da = (char*)staging(h, 6, row * (size_t)n_steps);
     float* dr = h_reward ? (float*)staging(h, 0, ne * sizeof(float)) : nullptr;
     uint8_t* dd = h_done ? (uint8_t*)staging(h, 1, ne) : nullptr;
     float* dob = h_obs ? (float*)staging(h, 2, nobs * sizeof(float)) : nullptr;
@@ -860,12 +865,13 @@ extern "C" int chx_rollout_host_actions(chx_handle* h, int32_t n_steps, const in
         return fail(CHX_ENOMEM, "staging allocation failed");
     cudaStream_t st = (cudaStream_t)stream, cs = h->copy_stream, is = h->in_stream;
     const int n_chunks = n_steps < kActChunks ? n_steps : kActChunks;
+    const char* hl = static_cast<const char*>(h_levels);
     // the staging of the previous call may still be read by its last launch
     CUDA_TRY(cudaEventRecord(h->act_done[0], st));
     CUDA_TRY(cudaStreamWaitEvent(is, h->act_done[0], 0));
     for (int c = 0; c < n_chunks; ++c) {
         const int k0 = (int)((long long)n_steps * c / n_chunks), k1 = (int)((long long)n_steps * (c + 1) / n_chunks);
-        CUDA_TRY(cudaMemcpyAsync(da + (size_t)k0 * nact, h_actions + (size_t)k0 * nact, (size_t)(k1 - k0) * nact,
+        CUDA_TRY(cudaMemcpyAsync(da + (size_t)k0 * row, hl + (size_t)k0 * row, (size_t)(k1 - k0) * row,
                                  cudaMemcpyHostToDevice, is));
         CUDA_TRY(cudaEventRecord(h->act_in[c], is));
     }
@@ -874,9 +880,10 @@ extern "C" int chx_rollout_host_actions(chx_handle* h, int32_t n_steps, const in
         const bool last = c == n_chunks - 1;
         const size_t off = (size_t)k0 * E, n = (size_t)(k1 - k0) * E;
         CUDA_TRY(cudaStreamWaitEvent(st, h->act_in[c], 0));
-        int rc = enqueue_fused(h, k1 - k0, da + (size_t)k0 * nact, 1, dr ? dr + off : nullptr,
-                               dd ? dd + off : nullptr, 1, last ? dob : nullptr, h->warps_per_block, st,
-                               (long long)E, (long long)nact);
+        // index of slot q at step k: q + k * (row in level units)
+        int rc = enqueue_fused(h, k1 - k0, reinterpret_cast<const int8_t*>(da + (size_t)k0 * row), 1,
+                               dr ? dr + off : nullptr, dd ? dd + off : nullptr, 1, last ? dob : nullptr,
+                               h->warps_per_block, st, (long long)E, (long long)(bits == 4 ? 2 * row : row), bits);
         if (rc) return rc;
         CUDA_TRY(cudaEventRecord(h->act_done[c], st));
         CUDA_TRY(cudaStreamWaitEvent(cs, h->act_done[c], 0));
@@ -887,6 +894,26 @@ extern "C" int chx_rollout_host_actions(chx_handle* h, int32_t n_steps, const in
     CUDA_TRY(cudaStreamSynchronize(cs));
     CUDA_TRY(cudaStreamSynchronize(st));
     return CHX_OK;
+}
+}  // namespace
+
+extern "C" int chx_rollout_host_actions(chx_handle* h, int32_t n_steps, const int8_t* h_actions, float* h_reward,
+                                        uint8_t* h_done, float* h_obs, void* stream)
+{
+    if (!h) return fail(CHX_EINVAL, "null handle");
+    if (!h_actions) return fail(CHX_EINVAL, "h_actions is null (use chx_rollout_host for Philox actions)");
+    if (n_steps < 1) return fail(CHX_EINVAL, "n_steps must be >= 1");
+    return rollout_host_levels(h, n_steps, h_actions, 8, h_reward, h_done, h_obs, stream);
+}
+
+extern "C" int chx_rollout_host_levels4(chx_handle* h, int32_t n_steps, const uint8_t* h_levels4, float* h_reward,
+                                        uint8_t* h_done, float* h_obs, void* stream)
+{
+    if (!h) return fail(CHX_EINVAL, "null handle");
+    if (!h_levels4) return fail(CHX_EINVAL, "h_levels4 is null (use chx_rollout_host for Philox actions)");
+    if (n_steps < 1) return fail(CHX_EINVAL, "n_steps must be >= 1");
+    if (h->params.n_levels > 16) return fail(CHX_EINVAL, "4-bit levels need n_levels <= 16");
+    return rollout_host_levels(h, n_steps, h_levels4, 4, h_reward, h_done, h_obs, stream);
 }
 
 extern "C" int chx_step_host(chx_handle* h, const int8_t* h_actions, float* h_reward, uint8_t* h_done, float* h_obs,

@@ -240,6 +240,18 @@ __device__ __forceinline__ uint32_t level_meta(uint32_t m2, int j)
     return ((b8 & 1u) ? kMetaHead : 0u) | ((b8 & 2u) ? kMetaTail : 0u) | (((b8 >> 2) & 31u) << kMetaGroupShift);
 }
 
+// A given action level: action slot a at step k of the launch (int8, or a
+// nibble of two-per-byte packed levels)
+__device__ __forceinline__ int given_level(const FusedIO& io, long long a, int k)
+{
+    const long long i = a * io.lda + (long long)k * io.lda_step;
+    if (io.act_bits == 4) {
+        const uint32_t byte = reinterpret_cast<const uint8_t*>(io.actions)[i >> 1];
+        return (int)((i & 1) ? byte >> 4 : byte & 15u);
+    }
+    return io.actions[i];
+}
+
 // V2G: signed levels, the station battery at the root (state in the
 // station's lanes, its level after the chargers' or drawn at charger index
 // n), signed limits, discharge energy after the port loss, two-case profit,
@@ -386,7 +398,7 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
                 const uint32_t half = (g & 1u) ? (word >> 16) : (word & 0xFFFFu);
                 lvl = (int)((half * (uint32_t)p.n_levels) >> 16);
             } else if (trem[q] > 0) {
-                lvl = io.actions[((long long)act_base + port) * io.lda + (long long)k * io.lda_step];
+                lvl = given_level(io, (long long)act_base + port, k);
                 if (lvl < 0 || lvl >= p.n_levels) {
                     atomicOr(b.err, kErrActionRange);
                     lvl = min(max(lvl, 0), p.n_levels - 1);
@@ -410,7 +422,7 @@ __device__ __forceinline__ void run_tile(const DevBatch& b, const DevParams& p, 
                     bwords = philox4x32_10(make_uint4(uidu, g >> 3, (uint32_t)n_st, kPurposeAction), k0, k1);
                 lvl = random_level(bwords, g, p.n_levels);
             } else {
-                lvl = io.actions[((long long)act_base + n_st) * io.lda + (long long)k * io.lda_step];
+                lvl = given_level(io, (long long)act_base + n_st, k);
                 if (lvl < 0 || lvl >= p.n_levels) {
                     atomicOr(b.err, kErrActionRange);
                     lvl = min(max(lvl, 0), p.n_levels - 1);

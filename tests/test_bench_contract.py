@@ -60,7 +60,10 @@ def test_gpu_arm_json_line():
     assert abs(rf["achieved"] - rf["algorithmic_bytes_per_launch"] / (rf["launch_ms"] * 1e-3) / 1e9) < 1e-6 * rf["achieved"]
     e2e = d["e2e"]
     assert e2e["value"] > 0 and e2e["d2h_bytes_per_step"] > 0
-    assert e2e["h2d_bytes_per_step"] == d["config"]["n_chargers"] * d["config"]["horizon_steps"]
+    # levels in, two per byte, then the same levels as int8
+    P, T = d["config"]["n_chargers"], d["config"]["horizon_steps"]
+    assert e2e["h2d_bytes_per_step"] == (P + 1) // 2 * T
+    assert d["e2e_int8_actions"]["h2d_bytes_per_step"] == P * T
     assert d["e2e_philox_actions"]["h2d_bytes_per_step"] == 0
     assert d["gpu_launches"] > 0 and d["plain"]["value"] > 0
     assert {"sm_mhz", "sm_max_mhz", "reasons"} <= set(d["clocks"])

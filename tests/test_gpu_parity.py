@@ -376,6 +376,51 @@ def test_host_actions_rollout(cuda_lib, n, v2g):
     b1.check()
 
 
+@pytest.mark.parametrize("n,v2g,n_envs", [(30, False, 150), (7, False, 151), (26, True, 150)])
+def test_host_levels4_rollout_equals_int8(cuda_lib, n, v2g, n_envs):
+    """Levels packed two per byte (chx_rollout_host_levels4) give bit for bit
+    what the int8 host-actions rollout gives on the same levels (itself
+    checked against the oracle above), on the class-edge stations, over two
+    calls in a row (151 stations: an odd number of action slots, so each
+    step's row ends in a half-used byte); a nibble of n_levels or more is
+    flagged."""
+    import torch
+    from paper_2507_01522_b300.chargax import CHX_EFAULT, Batch, ChxError, pack_levels4
+    from paper_2507_01522_b300.chargax import CHX_EINVAL
+    w = odd_sizes(n_envs=n_envs)
+    if v2g:
+        w = I.v2g_variant(w)                                # 21 levels: too many for a nibble
+        with pytest.raises(ChxError) as ei:
+            Batch(w).rollout_host_levels4(1, np.zeros(w.stations.n_ports.sum() + n_envs, np.uint8))
+        assert ei.value.code == CHX_EINVAL
+        w.params.n_levels = 15
+    b1, b2 = Batch(w), Batch(w)
+    E, P = b1.E, b1.P
+    n_act = P + (E if v2g else 0)
+    rng = np.random.default_rng(29 + n)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    out = [[pin(np.zeros(n * E, np.float32)), pin(np.zeros(n * E, np.uint8)), pin(np.zeros(b1.obs_size, np.float32))]
+           for _ in range(2)]
+    for call in range(2):
+        acts = rng.integers(0, w.params.n_levels, size=(n, n_act), dtype=np.int8)
+        packed = pack_levels4(acts)
+        assert packed.shape == (n, (n_act + 1) // 2)
+        b1.rollout_host_actions(n, pin(acts.reshape(-1)), *out[0])
+        b2.rollout_host_levels4(n, pin(packed.reshape(-1)), *out[1])
+        for x, y, name in zip(out[0], out[1], ("reward", "done", "observation")):
+            np.testing.assert_array_equal(x, y, err_msg=f"{name}, call {call}")
+        s1, s2 = b1.get_state(), b2.get_state()
+        for k in s1:
+            np.testing.assert_array_equal(s1[k], s2[k], err_msg=f"state {k}, call {call}")
+    b2.check()
+    bad = packed.copy()
+    bad[0, 0] = 0xF0 | (bad[0, 0] & 0x0F)             # slot 1 of step 0 at level 15
+    b2.rollout_host_levels4(n, pin(bad.reshape(-1)), *out[1])
+    with pytest.raises(ChxError) as ei:
+        b2.check()
+    assert ei.value.code == CHX_EFAULT
+
+
 def test_host_actions_rollout_rejects_null_actions(cuda_lib):
     from paper_2507_01522_b300.chargax import CHX_EINVAL, Batch, ChxError
     b = Batch(I.small_uniform())
