@@ -838,7 +838,7 @@ constexpr size_t smem_per_warp(int v) { return (v & 4) ? sizeof(WarpSmemExt) : s
      &k_step_fused<CLO, CHI, MINB, false, false, true>, &k_step_fused<CLO, CHI, MINB, true, false, true>,    \
      &k_step_fused<CLO, CHI, MINB, false, true, true>, &k_step_fused<CLO, CHI, MINB, true, true, true>}
 void (*const kSmallKernel[kForms])(DevBatch, DevParams, FusedIO) = CHX_FORMS(0, 3, 3);
-void (*const kLargeKernel[kForms])(DevBatch, DevParams, FusedIO) = CHX_FORMS(4, 4, 2);
+void (*const kLargeKernel[kForms])(DevBatch, DevParams, FusedIO) = CHX_FORMS(4, 4, 3);
 #undef CHX_FORMS
 
 // the part of a schedule whose classes lie in [clo, chi], tiles renumbered
