@@ -43,3 +43,19 @@ def test_binding_loads_library(lib_path):
 def test_build_targets_sm103a_only():
     assert B.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
     assert "--use_fast_math" not in B.FLAGS
+
+
+def test_pack_levels4_layout():
+    """Two levels per byte, the even slot in the low nibble, each step's row
+    padded to whole bytes (the layout chx_rollout_host_levels4 reads)."""
+    import numpy as np
+    from paper_2507_01522_b300.chargax import pack_levels4
+    lv = np.array([[1, 2, 3, 4, 5], [10, 0, 15, 7, 9]], dtype=np.int8)
+    p = pack_levels4(lv)
+    assert p.dtype == np.uint8 and p.shape == (2, 3)
+    np.testing.assert_array_equal(p, [[0x21, 0x43, 0x05], [0x0A, 0x7F, 0x09]])
+    rng = np.random.default_rng(3)
+    lv = rng.integers(0, 16, size=(7, 12), dtype=np.int8)
+    p = pack_levels4(lv)
+    np.testing.assert_array_equal(p & 15, lv[:, 0::2])
+    np.testing.assert_array_equal(p >> 4, lv[:, 1::2])
