@@ -196,6 +196,31 @@ def test_serving_admission_budget_and_errors():
     srv.stop()
 
 
+def test_serving_full_record_table_waits_then_refuses():
+    """Ticket t uses record t mod 65536: with 65536 tickets unreleased, the
+    next submission waits for a record (about 200 ms) and then returns
+    CHX_ENOMEM without taking a ticket; once one ticket is released the
+    submission goes through."""
+    import time
+    from paper_2507_01522_b300.chargax import CHX_ENOMEM, ChxError
+    w = I.fixed_station(n_envs=4)
+    srv = server_for(w, cap=(0, 4, 0, 0, 0))
+    ids = srv.admit(w.stations)
+    tickets = [srv.submit(ids[i % 4:i % 4 + 1]) for i in range(65536)]
+    t0 = time.perf_counter()
+    with pytest.raises(ChxError) as ei:
+        srv.submit(ids[:1])
+    waited = time.perf_counter() - t0
+    assert ei.value.code == CHX_ENOMEM
+    assert 0.15 <= waited <= 5.0
+    srv.wait(tickets[0])                                 # releases the record the next ticket uses
+    t = srv.submit(ids[:1])
+    assert t == tickets[-1] + 1
+    for k in tickets[1:] + [t]:
+        srv.wait(k)
+    srv.stop()
+
+
 def test_serving_simulation_reports_latency():
     w = I.serving_pool(n_envs=2048, seed=1)
     cap = [int(np.sum((w.stations.n_ports > (4 << c)) & (w.stations.n_ports <= (8 << c)))) for c in range(5)]
