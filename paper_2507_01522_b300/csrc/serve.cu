@@ -13,6 +13,9 @@
 // * Ticks: one scheduler thread hands the device a window of tickets [lo, hi)
 //   -- the requests not yet known to be finished -- and the device does the
 //   rest, on one stream, in order:
+//     window   the window's end moves past every request published since the
+//              launch (a tick queued behind a running one takes what arrived
+//              meanwhile);
 //     claim    each open request of the window copies its list into a device
 //              arena and writes its rank (arrival order) into every station
 //              it lists with atomicMin;
@@ -30,7 +33,7 @@
 //   Each of the n_streams tick slots is one CUDA graph, captured at start,
 //   whose kernels read the window from the slot's pinned argument record; up
 //   to n_streams ticks are queued on the device at once, and requests that
-//   arrive while a tick runs join the next one.
+//   arrive while a tick runs join the next one to start.
 // * Completion: chx_srv_wait / chx_srv_test read the request's completion
 //   flag and copy its results to the caller's buffers in the caller's thread.
 // * A station's result depends only on its own state and its position inside
@@ -155,6 +158,7 @@ static_assert(kCntWork + kFusedCounters <= kCnt, "counter layout");
 // what a tick reports to the host (pinned, mapped)
 struct TickResult {
     int admitted, stepped, resets, blocked;
+    unsigned long long hi;                 // end of the window the tick took (its arguments' hi or beyond)
 };
 
 struct TickArgs {
@@ -196,18 +200,51 @@ __device__ __forceinline__ long long warp_global()
 }
 __device__ __forceinline__ long long warps_total() { return ((long long)gridDim.x * blockDim.x) >> 5; }
 
+// A request's ticket as published in its pinned record (the submitter
+// stores it last, with release order, after every other field)
+__device__ __forceinline__ unsigned long long published_ticket(const DevReq* r)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(&r->ticket) : "memory");
+    return v;
+}
+
+// window: the tick's arguments from the slot's pinned record into device
+// memory, the window's end moved past every request published since the
+// host launched the tick (so a tick queued behind a running one takes what
+// arrived meanwhile), the tick's counters zeroed.  One warp; records are
+// read 32 at a time while all 32 are published, at most kWindowRounds times.
+constexpr int kWindowRounds = 8;
+__global__ void k_tick_window(DevSrv d, const TickArgs* __restrict__ host_args, int slot)
+{
+    TickArgs a = host_args[slot];
+    const int lane = threadIdx.x & 31;
+    if (lane < kCnt) d.cnt[lane] = 0;
+    unsigned long long hi = a.hi;
+    for (int r = 0; r < kWindowRounds; ++r) {
+        const unsigned long long t = hi + (unsigned long long)lane;
+        const bool ok = t - a.lo < (unsigned long long)(d.mask + 1) &&
+                        published_ticket(d.req + (t & d.mask)) == t;
+        const unsigned bal = __ballot_sync(0xFFFFFFFFu, ok);
+        const int run = bal == 0xFFFFFFFFu ? 32 : __ffs(~bal) - 1;   // published prefix
+        hi += (unsigned long long)run;
+        if (run < 32) break;
+    }
+    if (lane == 0) {
+        a.hi = hi;
+        d.targs[slot] = a;
+        *reinterpret_cast<volatile unsigned long long*>(&d.result[a.slot].hi) = hi;
+    }
+}
+
 // claim: copy each open request's list (and levels) into the arenas and mark
 // its stations with its rank.  A request whose arena span does not fit waits
 // for a later tick; spans grow with the ticket, so every later one waits too.
 // Host memory is read in two dependent rounds per record (descriptor, then
 // its list with up to 8 loads in flight per lane).
-__global__ void k_tick_claim(DevSrv d, const TickArgs* __restrict__ host_args, int slot)
+__global__ void k_tick_claim(DevSrv d, int slot)
 {
-    // the tick's arguments: written by the host into pinned memory before
-    // the launch; kept in device memory for the tick's later kernels
-    const TickArgs a = host_args[slot];
-    if (blockIdx.x == 0 && threadIdx.x == 0) d.targs[slot] = a;
-    if (blockIdx.x == 0 && threadIdx.x < kCnt) d.cnt[threadIdx.x] = 0;
+    const TickArgs a = d.targs[slot];      // the window as k_tick_window extended it
     const int lane = threadIdx.x & 31;
     const long long nw = (long long)(a.hi - a.lo);
     for (long long w = warp_global(); w < nw; w += warps_total()) {
@@ -772,7 +809,8 @@ int capture_tick(chx_srv* s, int slot)
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        k_tick_claim<<<g, 256, 0, cs>>>(s->d, s->d_args, slot);
+        k_tick_window<<<1, 32, 0, cs>>>(s->d, s->d_args, slot);
+        k_tick_claim<<<g, 256, 0, cs>>>(s->d, slot);
         k_tick_select<<<g, 256, 0, cs>>>(s->d, s->b, slot);
         k_tick_prep<<<g, 32 * kNumClasses, 0, cs>>>(s->d, s->b, s->dp);
         FusedIO io{};
@@ -839,14 +877,22 @@ void scheduler(chx_srv* s)
     bool retry = false;
     int idle = 0;
     volatile unsigned long long* flag = s->h_done_flag;
+    // Ticket t is published once its record carries t and is no longer being
+    // filled, or carries a later ticket.  A tick's window kernel may take and
+    // finish a request as soon as its descriptor is published, so its caller
+    // may have released it (state free) or even reused the record before
+    // this thread looks.  The ticket is read before the state: the record
+    // goes filling -> queued -> free under one ticket, so a ticket t read
+    // with any state but filling was published.
+    auto published = [&](uint64_t t) {
+        const Request& q = s->table[t & mask];
+        const uint64_t qt = q.ticket.load(std::memory_order_acquire);
+        if (qt != t) return qt > t;
+        return q.state.load(std::memory_order_seq_cst) != kFilling;
+    };
     for (;;) {
         const int64_t t0 = now_ns();
-        for (;;) {                         // published requests extend the window
-            const Request& q = s->table[pub & mask];
-            if (q.state.load(std::memory_order_acquire) != kQueued || q.ticket.load(std::memory_order_relaxed) != pub)
-                break;
-            ++pub;
-        }
+        while (published(pub)) ++pub;      // published requests extend the window
         while (!inflight.empty()) {        // finished ticks
             const int sl = inflight.front();
             TickSlot& ts = s->tslots[sl];
@@ -861,7 +907,11 @@ void scheduler(chx_srv* s)
                 ms = 0.f;
             }
             const volatile int* src = reinterpret_cast<const volatile int*>(s->h_result + sl);
-            const TickResult r{src[0], src[1], src[2], src[3]};
+            const TickResult r{src[0], src[1], src[2], src[3], 0ull};
+            // requests the device found published beyond the launched window
+            // were taken by this tick: no new tick for them
+            last_hi = std::max<uint64_t>(
+                last_hi, *reinterpret_cast<const volatile unsigned long long*>(&s->h_result[sl].hi));
             {
                 std::lock_guard<std::mutex> g(s->stat_mu);
                 if (r.admitted > 0) s->n_ticks += 1;
@@ -899,7 +949,7 @@ void scheduler(chx_srv* s)
             s->n_scans += 1;
             slot_busy[sl] = 1;
             inflight.push_back(sl);
-            last_hi = pub;
+            last_hi = std::max(last_hi, pub);
             retry = false;
             idle = 0;
             continue;
@@ -915,12 +965,8 @@ void scheduler(chx_srv* s)
         {
             std::unique_lock<std::mutex> lk(s->wake_mu);
             s->sleeping.store(true, std::memory_order_seq_cst);
-            s->wake.wait_for(lk, std::chrono::microseconds(200), [&] {
-                const Request& q = s->table[pub & mask];
-                return (q.state.load(std::memory_order_seq_cst) == kQueued &&
-                        q.ticket.load(std::memory_order_relaxed) == pub) ||
-                       s->stopping.load();
-            });
+            s->wake.wait_for(lk, std::chrono::microseconds(200),
+                             [&] { return published(pub) || s->stopping.load(); });
             s->sleeping.store(false, std::memory_order_relaxed);
         }
         idle = 0;
@@ -1304,7 +1350,6 @@ extern "C" int chx_srv_submit(chx_srv* s, const chx_srv_req* r, uint64_t* ticket
     std::memcpy(q->ids.h, r->h_env_ids, (size_t)n * sizeof(int32_t));
     if (given) std::memcpy(q->acts.h, r->h_actions, (size_t)n_act);
     DevReq& dr = s->h_req[tk & (kMaxOutstanding - 1)];
-    dr.ticket = tk;
     dr.kind = r->kind;
     dr.n = n;
     dr.n_act = (int)n_act;
@@ -1319,6 +1364,8 @@ extern "C" int chx_srv_submit(chx_srv* s, const chx_srv_req* r, uint64_t* ticket
     dr.done = step ? q->done.d : nullptr;
     dr.obs = obs_floats ? q->obs.d : nullptr;
     dr.seed = (unsigned long long)r->seed;
+    // the device takes a record as published when it reads this ticket
+    __atomic_store_n(&dr.ticket, (unsigned long long)tk, __ATOMIC_RELEASE);
     q->kind = r->kind;
     q->n = n;
     q->h_reward = step ? r->h_reward : nullptr;
