@@ -442,9 +442,10 @@ int chx_policy_rollout(chx_handle* h, int32_t n_steps, float* d_obs, int8_t* d_a
  *     once) takes, in arrival order, every request whose stations no earlier
  *     request of the window lists, steps or resets them (the fused kernel in
  *     gather mode), writes each taken request's results into its record and
- *     then raises the record's completion flag.  Requests that arrive while a
- *     tick runs join the next one; requests for one station are applied in
- *     submission order.
+ *     then raises the record's completion flag.  A tick's first kernel moves
+ *     its window's end past every request published since the launch, so
+ *     requests that arrive while a tick runs join the next tick to start;
+ *     requests for one station are applied in submission order.
  *   - chx_srv_wait / chx_srv_test read the flag and copy the results to the
  *     caller's buffers (in the caller's thread).
  * A request's results do not depend on what else shares its tick.  All server
