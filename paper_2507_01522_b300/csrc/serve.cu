@@ -158,7 +158,6 @@ static_assert(kCntWork + kFusedCounters <= kCnt, "counter layout");
 // what a tick reports to the host (pinned, mapped)
 struct TickResult {
     int admitted, stepped, resets, blocked;
-    unsigned long long hi;                 // end of the window the tick took (its arguments' hi or beyond)
 };
 
 struct TickArgs {
@@ -214,6 +213,9 @@ __device__ __forceinline__ unsigned long long published_ticket(const DevReq* r)
 // host launched the tick (so a tick queued behind a running one takes what
 // arrived meanwhile), the tick's counters zeroed.  One warp; records are
 // read 32 at a time while all 32 are published, at most kWindowRounds times.
+// The scheduler does not learn the extended end: it launches a tick for any
+// request it sees newly published, and a tick whose window holds only
+// requests an earlier tick already took finds them executed and skips them.
 constexpr int kWindowRounds = 8;
 __global__ void k_tick_window(DevSrv d, const TickArgs* __restrict__ host_args, int slot)
 {
@@ -233,7 +235,6 @@ __global__ void k_tick_window(DevSrv d, const TickArgs* __restrict__ host_args, 
     if (lane == 0) {
         a.hi = hi;
         d.targs[slot] = a;
-        *reinterpret_cast<volatile unsigned long long*>(&d.result[a.slot].hi) = hi;
     }
 }
 
@@ -907,11 +908,7 @@ void scheduler(chx_srv* s)
                 ms = 0.f;
             }
             const volatile int* src = reinterpret_cast<const volatile int*>(s->h_result + sl);
-            const TickResult r{src[0], src[1], src[2], src[3], 0ull};
-            // requests the device found published beyond the launched window
-            // were taken by this tick: no new tick for them
-            last_hi = std::max<uint64_t>(
-                last_hi, *reinterpret_cast<const volatile unsigned long long*>(&s->h_result[sl].hi));
+            const TickResult r{src[0], src[1], src[2], src[3]};
             {
                 std::lock_guard<std::mutex> g(s->stat_mu);
                 if (r.admitted > 0) s->n_ticks += 1;
@@ -949,7 +946,7 @@ void scheduler(chx_srv* s)
             s->n_scans += 1;
             slot_busy[sl] = 1;
             inflight.push_back(sl);
-            last_hi = std::max(last_hi, pub);
+            last_hi = pub;
             retry = false;
             idle = 0;
             continue;
