@@ -514,9 +514,9 @@ int chx_srv_evict(chx_srv* s, const int32_t* h_ids, int32_t n);
 /* Queue a request; *ticket identifies it.  The output buffers must stay valid
  * until the ticket completes.  Ticket t uses request record t mod 65536: while
  * the ticket 65536 before it is not yet released (by chx_srv_wait /
- * chx_srv_test), the call waits for another thread to release it, up to
- * 200 ms, then returns CHX_ENOMEM with no ticket taken.  A ticket is waited on
- * or tested by one thread at a time. */
+ * chx_srv_test), the call returns CHX_ENOMEM at once with no ticket taken
+ * (release tickets, then submit again).  A ticket is waited on or tested by
+ * one thread at a time. */
 int chx_srv_submit(chx_srv* s, const chx_srv_req* r, uint64_t* ticket);
 /* Block until the ticket completes (CHX_ETIMEOUT after timeout_us), copy its
  * results to the request's buffers and release the ticket.  latency_ns (may be

@@ -74,7 +74,6 @@ inline int64_t now_ns()
 }
 
 constexpr uint64_t kMaxOutstanding = 1u << 16;   // request records (power of two)
-constexpr int64_t kRecordWaitMs = 200;             // a submission's wait for its record to be released
 
 // bytes a station of class c occupies in the pool (state + statics)
 inline double slot_bytes(int c) { return (double)(8 << c) * 33.0 + 128.0; }
@@ -1307,23 +1306,18 @@ extern "C" int chx_srv_submit(chx_srv* s, const chx_srv_req* r, uint64_t* ticket
     Request* q = nullptr;
     uint64_t tk = 0;
     {
-        // The next ticket's record is still held when a request kMaxOutstanding
-        // tickets older is not yet released: wait for it (another thread
-        // releasing it), up to kRecordWaitMs, then give up.
+        // The next ticket's record is still held while the request
+        // kMaxOutstanding tickets older is unreleased: refuse at once (a
+        // submission that waited here would stop its thread from releasing
+        // the tickets it holds itself, and threads could wait on each other)
         TicketState& T = s->tk;
-        const int64_t deadline = t_in + kRecordWaitMs * 1000000LL;
-        for (int spins = 0;; ++spins) {
-            T.lock();
-            tk = T.next_ticket;
-            q = &s->table[tk & (kMaxOutstanding - 1)];
-            int expect = kFree;
-            if (q->state.compare_exchange_strong(expect, kFilling, std::memory_order_acq_rel)) break;
+        T.lock();
+        tk = T.next_ticket;
+        q = &s->table[tk & (kMaxOutstanding - 1)];
+        int expect = kFree;
+        if (!q->state.compare_exchange_strong(expect, kFilling, std::memory_order_acq_rel)) {
             T.unlock();
-            if (now_ns() >= deadline)
-                return fail(CHX_ENOMEM,
-                            "too many outstanding requests: release tickets with chx_srv_wait or chx_srv_test");
-            if (spins < 64) cpu_relax();
-            else std::this_thread::sleep_for(std::chrono::microseconds(20));
+            return fail(CHX_ENOMEM, "too many outstanding requests: release tickets with chx_srv_wait or chx_srv_test");
         }
         int rc = grow_pinned(s->pool, q->ids, (size_t)n);
         if (!rc && step) rc = grow_pinned(s->pool, q->rew, (size_t)n);

@@ -196,11 +196,10 @@ def test_serving_admission_budget_and_errors():
     srv.stop()
 
 
-def test_serving_full_record_table_waits_then_refuses():
+def test_serving_full_record_table_refuses():
     """Ticket t uses record t mod 65536: with 65536 tickets unreleased, the
-    next submission waits for a record (about 200 ms) and then returns
-    CHX_ENOMEM without taking a ticket; once one ticket is released the
-    submission goes through."""
+    next submission returns CHX_ENOMEM at once without taking a ticket; once
+    one ticket is released the submission goes through."""
     import time
     from paper_2507_01522_b300.chargax import CHX_ENOMEM, ChxError
     w = I.fixed_station(n_envs=4)
@@ -210,9 +209,8 @@ def test_serving_full_record_table_waits_then_refuses():
     t0 = time.perf_counter()
     with pytest.raises(ChxError) as ei:
         srv.submit(ids[:1])
-    waited = time.perf_counter() - t0
     assert ei.value.code == CHX_ENOMEM
-    assert 0.15 <= waited <= 5.0
+    assert time.perf_counter() - t0 < 0.1
     srv.wait(tickets[0])                                 # releases the record the next ticket uses
     t = srv.submit(ids[:1])
     assert t == tickets[-1] + 1
