@@ -259,8 +259,10 @@ int chx_rollout_host(chx_handle* h, int32_t n_steps, float* h_reward, uint8_t* h
  * step k, n_act = total chargers (+ n_envs in V2G mode), each station's
  * slots in batch order (its chargers, then its battery); levels outside
  * 0..n_levels-1 are clamped and flagged (chx_check).  Outputs as
- * chx_rollout_host.  The steps run in up to 12 fused launches of near-equal
- * size: the levels of launch c are copied in while launch c - 1 computes and
+ * chx_rollout_host.  The steps run in up to 12 fused launches, each 0.85 of
+ * the size of the one before (the copy in bounds the call, so the launches
+ * left after it are short): the levels of launch c are copied in while
+ * launch c - 1 computes and
  * its rewards and done flags are copied out while launch c + 1 computes
  * (pinned host memory gives full copy bandwidth); the observation follows
  * the last launch.  The call returns when everything is on the host.
@@ -272,8 +274,9 @@ int chx_rollout_host_actions(chx_handle* h, int32_t n_steps, const int8_t* h_act
  * take ceil(n_act / 2) bytes starting at byte k * ceil(n_act / 2); slot q is
  * the low nibble of byte q / 2 for even q, the high nibble for odd q.  Needs
  * n_levels <= 16 (else CHX_EINVAL); nibbles of n_levels or more are clamped
- * and flagged (chx_check).  Results equal chx_rollout_host_actions' on the
- * same levels. */
+ * and flagged (chx_check).  The launches are of near-equal size (this copy
+ * in takes about as long as the compute).  Results equal
+ * chx_rollout_host_actions' on the same levels. */
 int chx_rollout_host_levels4(chx_handle* h, int32_t n_steps, const uint8_t* h_levels4, float* h_reward,
                              uint8_t* h_done, float* h_obs, void* stream);
 

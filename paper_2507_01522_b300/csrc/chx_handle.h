@@ -14,6 +14,7 @@ using Buffers = std::vector<void*>;
 
 constexpr int kHostChunks = 4;            // launches of a host-call rollout (copies overlap the next)
 constexpr int kActChunks = 12;            // launches of a host-actions rollout (copies in and out overlap)
+constexpr double kActShrink8 = 0.85;      // size ratio of consecutive launches of an int8 host-actions rollout
 
 struct GraphKey {
     int n_steps = 0;

@@ -840,12 +840,44 @@ extern "C" int chx_rollout_host(chx_handle* h, int32_t n_steps, float* h_reward,
 }
 
 // Host-actions rollout: the given levels of every step come from the host.
-// The steps run in up to kActChunks fused launches of near-equal size on the
-// caller's stream.  The input stream copies chunk c's levels (contiguous,
+// The steps run in up to kActChunks fused launches on the caller's stream,
+// of near-equal size but for a short last one.  The input stream copies chunk c's levels (contiguous,
 // step-major) to device staging while chunk c - 1 computes; the copy stream
 // brings chunk c's rewards and done flags back while chunk c + 1 computes;
 // the observation follows the last chunk.
 namespace {
+// Step ranges of a host-levels rollout: chunk c runs steps start[c] ..
+// start[c + 1] - 1, each launch starting when its levels have arrived.
+// With int8 levels the copy in is the slowest stream (a step's levels take
+// about twice as long to copy as to step), so what follows the last copy in
+// (the last launch, its outputs' copy out, the final observation's copy) is
+// on the critical path: consecutive chunks shrink by `shrink`, each launch
+// still ending before the next chunk's levels arrive, and the last is short.
+// Packed 4-bit levels copy about as fast as the kernel steps: there equal
+// chunks (shrink 1) keep the first launch's wait short, which measured
+// better than shrinking ones.
+int act_chunks(int n_steps, double shrink, int* start)
+{
+    const int n = n_steps < kActChunks ? n_steps : kActChunks;
+    double wc[kActChunks], tot = 0.0, w = 1.0;
+    for (int c = 0; c < n; ++c) {
+        wc[c] = w;
+        tot += w;
+        w *= shrink;
+    }
+    double acc = 0.0;
+    start[0] = 0;
+    for (int c = 1; c < n; ++c) {
+        acc += wc[c - 1];
+        int x = (int)std::lround((double)n_steps * acc / tot);
+        x = std::max(x, start[c - 1] + 1);       // every chunk at least one step
+        x = std::min(x, n_steps - (n - c));      // and room for the ones after it
+        start[c] = x;
+    }
+    start[n] = n_steps;
+    return n;
+}
+
 // The host-actions rollout: n_steps of given levels from pinned host memory
 // (bits 8: one int8 per action slot; 4: two per byte, rows of whole bytes per
 // step), copied in kActChunks pieces on the input stream; each launch waits
@@ -864,19 +896,20 @@ int rollout_host_levels(chx_handle* h, int32_t n_steps, const void* h_levels, in
     if (!da || (h_reward && !dr) || (h_done && !dd) || (h_obs && !dob))
         return fail(CHX_ENOMEM, "staging allocation failed");
     cudaStream_t st = (cudaStream_t)stream, cs = h->copy_stream, is = h->in_stream;
-    const int n_chunks = n_steps < kActChunks ? n_steps : kActChunks;
+    int start[kActChunks + 1];
+    const int n_chunks = act_chunks(n_steps, bits == 8 ? kActShrink8 : 1.0, start);
     const char* hl = static_cast<const char*>(h_levels);
     // the staging of the previous call may still be read by its last launch
     CUDA_TRY(cudaEventRecord(h->act_done[0], st));
     CUDA_TRY(cudaStreamWaitEvent(is, h->act_done[0], 0));
     for (int c = 0; c < n_chunks; ++c) {
-        const int k0 = (int)((long long)n_steps * c / n_chunks), k1 = (int)((long long)n_steps * (c + 1) / n_chunks);
+        const int k0 = start[c], k1 = start[c + 1];
         CUDA_TRY(cudaMemcpyAsync(da + (size_t)k0 * row, hl + (size_t)k0 * row, (size_t)(k1 - k0) * row,
                                  cudaMemcpyHostToDevice, is));
         CUDA_TRY(cudaEventRecord(h->act_in[c], is));
     }
     for (int c = 0; c < n_chunks; ++c) {
-        const int k0 = (int)((long long)n_steps * c / n_chunks), k1 = (int)((long long)n_steps * (c + 1) / n_chunks);
+        const int k0 = start[c], k1 = start[c + 1];
         const bool last = c == n_chunks - 1;
         const size_t off = (size_t)k0 * E, n = (size_t)(k1 - k0) * E;
         CUDA_TRY(cudaStreamWaitEvent(st, h->act_in[c], 0));

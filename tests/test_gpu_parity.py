@@ -326,7 +326,7 @@ def test_host_api_matches_device(cuda_lib, n, pinned):
     np.testing.assert_array_equal(hr1, r1.cpu().numpy())
 
 
-@pytest.mark.parametrize("n,v2g", [(30, False), (5, False), (1, False), (26, True)])
+@pytest.mark.parametrize("n,v2g", [(30, False), (5, False), (1, False), (26, True), (61, False)])
 def test_host_actions_rollout(cuda_lib, n, v2g):
     """The host-actions rollout (step-major host levels in, launches whose
     copies in and out overlap their neighbours) equals the device fused form
