@@ -936,7 +936,11 @@ void scheduler(chx_srv* s)
             ++tick;
             s->ns_scan += now_ns() - t0;
             const int64_t t1 = now_ns();
-            if (launch_tick(s, lo, pub, tick, sl) != CHX_OK) {
+            // at most one ticket per record in a window: an index whose
+            // record a later ticket reuses is then one that was executed and
+            // still marked so (the later ticket lies past every earlier window)
+            const uint64_t hi = std::min(pub, lo + kMaxOutstanding);
+            if (launch_tick(s, lo, hi, tick, sl) != CHX_OK) {
                 s->fail_code.store((int)cudaGetLastError());
                 s->fail_where.store(1);
                 s->failed.store(true);
@@ -945,7 +949,7 @@ void scheduler(chx_srv* s)
             s->n_scans += 1;
             slot_busy[sl] = 1;
             inflight.push_back(sl);
-            last_hi = pub;
+            last_hi = hi;                  // requests past a clamped window stay fresh
             retry = false;
             idle = 0;
             continue;
