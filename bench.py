@@ -464,7 +464,7 @@ def run_b300(args):
                        "actions": "Philox uniform 11 levels in-kernel", "parallelism": f"replicas x{ws}",
                        "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MB write)"},
             "charger_steps_per_s": P * T * args.steps * ws / total_s,
-            "roofline": roofline, "gpu_launches": launches_per_step * args.steps}
+            "roofline": roofline, "gpu_launches": launches_per_step * fused_kernels_per_launch(w) * args.steps}
 
     # plain form, same protocol: one launch per step, replayed as a graph
     if not args.no_plain:
@@ -660,6 +660,22 @@ def run_config_leg(args, rank, ws, timed, wc, pk, dev):
     return out
 
 
+def fused_kernels_per_launch(w):
+    """Kernels one fused launch of workload w runs: one per class range that
+    holds stations.  The 128-charger class has an instance of its own, and so
+    has the 64-charger class in the V2G and extended forms without upper
+    tree levels; the other classes share one."""
+    import numpy as np
+    st = w.stations
+    cls = set(int(c) for c in np.unique(np.searchsorted([8, 16, 32, 64, 128], np.asarray(st.n_ports))))
+    n_upper = getattr(st, "n_upper", None)
+    tree = n_upper is not None and int(np.sum(n_upper)) > 0
+    p = w.params
+    split = bool(p.v2g or p.action_delta or p.cs_share_256 > 0) and not tree
+    ranges = ([(0, 2), (3, 3)] if split else [(0, 3)]) + [(4, 4)]
+    return sum(any(lo <= c <= hi for c in cls) for lo, hi in ranges)
+
+
 def run_variant(args, rank, ws, timed, wv, charge_only_value, dev):
     """A variant of the method on the same scale, fused form, the headline
     leg's timing protocol: vehicle-to-grid mode (signed levels, discharge
@@ -693,7 +709,7 @@ def run_variant(args, rank, ws, timed, wv, charge_only_value, dev):
            "actions": f"Philox uniform {wv.params.n_levels} levels per charger" + (" and battery" if wv.params.v2g else "")
                       + ", in-kernel",
            "over_charge_only": value / charge_only_value,
-           "gpu_launches": math.ceil(T / K) * args.steps}
+           "gpu_launches": math.ceil(T / K) * fused_kernels_per_launch(wv) * args.steps}
     del b
     return out
 

@@ -37,22 +37,24 @@ struct FusedIO {
     int gather_base[kNumClasses];
     // gather mode with a device-side schedule (NULL = the host schedule
     // above): entries of class c in dcount[c]; tiles run largest class first.
-    // dmax_small / dmax_large bound the tiles of the classes of 8..64 and of
-    // 128 chargers (grid sizes; 0 = no launch for that range)
+    // dmax_small / dmax_mid / dmax_large bound the tiles of the classes of
+    // 8..32, of 64 and of 128 chargers (grid sizes; 0 = no launch for that range)
     const int* dcount;
-    int dmax_small, dmax_large;
+    int dmax_small, dmax_mid, dmax_large;
 };
 
 void launch_step_plain(const DevBatch& b, const DevParams& p, const int8_t* actions, long long lda, float* reward,
                        uint8_t* done, const int* slot_list, int n_list, cudaStream_t st);
 // The fused step over io's schedule: the 128-charger class (if any) by one
-// persistent kernel, the other classes by a second one, each grid sized to
-// the resident blocks on sm_count SMs.  io.counter must point to
-// kFusedCounters zeroed ints (one work counter per kernel).
-constexpr int kFusedCounters = 2;
-// A side stream for the 128-charger class: with one, that launch runs beside
-// the smaller classes' (forked from and joined back to st by the two events,
-// which CUDA-graph capture supports); without, the two launches run in turn.
+// persistent kernel, the smaller classes by a second; in the V2G and extended
+// forms without upper tree levels the 64-charger class by a third of its own.
+// Each grid is sized to the resident blocks on sm_count SMs.  io.counter must
+// point to kFusedCounters zeroed ints (one work counter per kernel).
+constexpr int kFusedCounters = 3;
+// A side stream for the 128-charger class and a 64-charger instance: with
+// one, those launches run (in turn) beside the smaller classes' (forked from
+// and joined back to st by the two events, which CUDA-graph capture
+// supports); without, all the launches run in turn.
 struct FusedSide {
     cudaStream_t aux = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;

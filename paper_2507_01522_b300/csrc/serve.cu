@@ -151,7 +151,7 @@ struct RecMeta {
 };
 
 // counters of a tick, in device memory (zeroed by the claim kernel)
-enum { kCntClass = 0, kCntAdmitted = 5, kCntReset = 6, kCntBlocked = 7, kCntWork = 8, kCnt = 10 };
+enum { kCntClass = 0, kCntAdmitted = 5, kCntReset = 6, kCntBlocked = 7, kCntWork = 8, kCnt = 11 };
 static_assert(kCntWork + kFusedCounters <= kCnt, "counter layout");
 
 // what a tick reports to the host (pinned, mapped)
@@ -828,6 +828,7 @@ int capture_tick(chx_srv* s, int slot)
         for (int c = 0; c < kNumClasses; ++c) io.gather_base[c] = c * s->d.G;
         io.dcount = s->d.cnt + kCntClass;
         io.dmax_small = 1 << 28;           // every resident block
+        io.dmax_mid = s->cap[3] > 0 ? 1 << 28 : 0;
         io.dmax_large = s->cap[4] > 0 ? 1 << 28 : 0;
         launch_step_fused(s->b, s->dp, io, s->threads, s->sm_count, cs, &s->side);
         k_tick_finish<<<g, 256, 0, cs>>>(s->d, slot);
