@@ -293,7 +293,7 @@ int chx_step_host(chx_handle* h, const int8_t* h_actions, float* h_reward, uint8
  * Same transitions and outputs as chx_rollout (Philox actions, fused launches
  * of the handle's steps per launch and warps per block), launched directly
  * without a CUDA graph.  The call allocates nothing: its only scratch, the
- * work counters of each launch (two per launch), lives in an 8 KB static
+ * work counters of each launch (three per launch), lives in a 12 KB static
  * device array that every GPU loading this library keeps until the process
  * exits.  n_steps may need at most that many launches
  * (ceil(n_steps / steps per launch)); more returns CHX_EINVAL.
