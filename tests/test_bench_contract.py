@@ -67,3 +67,20 @@ def test_gpu_arm_json_line():
     assert d["e2e_philox_actions"]["h2d_bytes_per_step"] == 0
     assert d["gpu_launches"] > 0 and d["plain"]["value"] > 0
     assert {"sm_mhz", "sm_max_mhz", "reasons"} <= set(d["clocks"])
+
+
+def test_kernels_per_fused_launch():
+    """The launch count the benchmark claims: one kernel per class range that
+    holds stations (the 128-charger class alone; the 64-charger class alone
+    in the V2G and extended forms without upper tree levels)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2507_01522_b300 import inputs as I
+    w = I.heterogeneous(n_envs=256)
+    assert bench.fused_kernels_per_launch(w) == 1
+    assert bench.fused_kernels_per_launch(I.v2g_variant(w)) == 2
+    cs = I.Workload(w.name, I.EnvParams(**{**w.params.__dict__, "cs_share_256": 128}), w.stations, w.exo, w.seed)
+    assert bench.fused_kernels_per_launch(cs) == 2
+    small = I.Workload(w.name, I.v2g_variant(w).params, w.stations.subset(
+        [e for e in range(w.stations.n_envs) if w.stations.n_ports[e] <= 32]), w.exo, w.seed)
+    assert bench.fused_kernels_per_launch(small) == 1
